@@ -1,0 +1,282 @@
+/*
+ * mcx.h -- C ABI of libmcx: event-based Monte Carlo particle transport and the
+ * macroscopic cross-section lookup on one NVIDIA B300 (sm_103a).
+ *
+ * Paper: "Integrating ytopt and libEnsemble to Autotune OpenMC" (arXiv
+ * 2402.09222).  Sec. 4.1 describes what is computed here: OpenMC's
+ * event-based mode, a buffer of particles in flight refilled after each
+ * kernel call, the macroscopic cross-section lookup ("the most expensive
+ * kernel": a search of every species' energy grid, narrowed by a logarithmic
+ * hash grid), queued or queueless event logic, and sorting by material and
+ * energy above a minimum queue size.  Table 1 lists the tunable parameters.
+ *
+ * Conventions (all entry points):
+ *   - every call returns an int status (MCX_OK or a negative MCX_ERR_*);
+ *     nothing aborts or throws across the ABI; mcx_last_error() returns a
+ *     thread-local message for the last failing call on the calling thread;
+ *   - input arrays passed as host pointers are copied; the caller keeps
+ *     ownership and may free them when the call returns;
+ *   - arguments documented as DEVICE pointers must be device memory on the
+ *     problem's device (e.g. from torch.empty(..., device="cuda")); they are
+ *     borrowed until the asynchronous work queued on `stream` completes;
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream);
+ *   - an mcx_problem is not thread-safe: one thread at a time per handle.
+ */
+#ifndef MCX_H
+#define MCX_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define MCX_OK 0
+#define MCX_ERR_ARG (-1)        /* invalid argument (message says which) */
+#define MCX_ERR_CUDA (-2)       /* a CUDA runtime call failed */
+#define MCX_ERR_OOM (-3)        /* device or host allocation failed */
+#define MCX_ERR_ITER_LIMIT (-4) /* the event loop reached its iteration cap */
+#define MCX_ERR_STATE (-5)      /* call out of order (e.g. run before tables) */
+#define MCX_ERR_BOUNDS (-6)     /* a device-side bounds check fired */
+
+/* ---- enumerations ---------------------------------------------------- */
+/* Geometry of a problem.  NONE: a handle that only holds cross-section
+ * tables (for the lookup entry points). */
+#define MCX_GEOM_INFINITE 0 /* one material everywhere, source at origin */
+#define MCX_GEOM_LATTICE 1  /* n x n pin lattice in a box, see below */
+#define MCX_GEOM_SLAB 2     /* x in [0, L], pencil beam along +x */
+#define MCX_GEOM_NONE 3
+
+/* Storage precision of the sigma tables (energies are always FP64). */
+#define MCX_FP64 0
+#define MCX_FP32 1
+
+/* Event logic (Sec. 4.1, "queuing logic"). */
+#define MCX_QUEUELESS 0 /* every event kernel visits every slot */
+#define MCX_QUEUED 1    /* kernels visit device-built compacted queues */
+
+/* Lookup options for mcx_xs_lookup (bit flags). */
+#define MCX_LOOKUP_EXACT 0 /* FP64 arithmetic, bit-identical to the plain definition */
+#define MCX_LOOKUP_FAST 1  /* FP32 interpolation weights, compensated sums (<= 1e-6 rel) */
+#define MCX_LOOKUP_SORT 2  /* bin lookups by (material, log-energy) before the gather */
+
+/* Problem flags. */
+#define MCX_FLAG_DERIVATIVES 1   /* likelihood-ratio density-derivative tallies */
+#define MCX_FLAG_HISTORY_DEBUG 2 /* keep per-history collision counts */
+
+/* Tallies (mcx_read_tallies `which`).  Shapes, with B batches, nb bins
+ * (energy bins for INFINITE, regions for LATTICE, 1 for SLAB) and M
+ * materials:  FLUX, ABSORB [B][nb];  OUTCOME [B][5] = {absorbed, leaked
+ * through the +x face, leaked elsewhere, cut off, collisions};  DFLUX,
+ * DABSORB [B][nb][M];  DOUTCOME [B][5][M]. */
+#define MCX_TALLY_FLUX 0
+#define MCX_TALLY_ABSORB 1
+#define MCX_TALLY_OUTCOME 2
+#define MCX_TALLY_DFLUX 3
+#define MCX_TALLY_DABSORB 4
+#define MCX_TALLY_DOUTCOME 5
+
+#define MCX_MAX_DMAT 4 /* materials supported by the derivative tallies */
+
+typedef struct mcx_problem mcx_problem; /* opaque, owned by the library */
+
+/* Problem description.  All pointers are HOST pointers and are copied.
+ *
+ * LATTICE (the 17x17 pin-cell workload of the paper's benchmark class): pins
+ * of radius `radius` on a square lattice of `lattice_n`^2 cells of side
+ * `pitch`, centred on the origin; the box's x/y faces are vacuum, the planes
+ * z = 0 and z = height are reflective.  Regions: pin (i, j) = i * n + j,
+ * moderator = n^2; `region_material` has n^2 + 1 entries.  Each history
+ * starts at the centre of a uniformly chosen pin at z = height / 2.
+ * INFINITE: `region_material` has 1 entry; tallies bin by energy with the
+ * `n_ebins` + 1 increasing edges.  SLAB: 1 region, tally bin 0.
+ * All histories start with energy E0, isotropic (LATTICE, INFINITE) or along
+ * +x (SLAB), and die when a scattering leaves them below E_cut.
+ * History h belongs to batch floor(h * n_batches / n_histories). */
+typedef struct {
+    int32_t geometry;
+    int32_t lattice_n;
+    double pitch, radius, height, slab_length;
+    int32_t n_regions;
+    const int32_t* region_material;
+    double E0, E_cut;
+    int32_t n_ebins;
+    const double* ebin_edges;
+    int32_t n_batches;
+    uint32_t problem_id; /* part of the random-number key */
+    int64_t n_histories; /* total histories of the problem (defines batches) */
+    int32_t flags;       /* MCX_FLAG_* */
+    int32_t device;      /* CUDA device ordinal */
+} mcx_problem_desc;
+
+/* Event-loop tuning (Table 1 of the paper, mapped to this GPU).
+ *   mode            MCX_QUEUELESS or MCX_QUEUED
+ *   block_size      threads per block of the event kernels (32..1024, /32)
+ *   sort_period     bin the lookup and collision queues every this many
+ *                   iterations (0 = never); queued mode only
+ *   sort_threshold  ...and only when a queue holds at least this many
+ *                   particles (the paper's minimum sorting threshold)
+ *   iters_per_sync  event-loop iterations captured per CUDA graph launch
+ *                   between host checks of the termination flag (>= 1)
+ *   max_event_iters iteration cap of one run (0 = automatic); reaching it
+ *                   returns MCX_ERR_ITER_LIMIT instead of looping on
+ *   use_graph       1 = replay the captured loop body, 0 = plain launches */
+typedef struct {
+    int32_t mode;
+    int32_t block_size;
+    int32_t sort_period;
+    int64_t sort_threshold;
+    int32_t iters_per_sync;
+    int64_t max_event_iters;
+    int32_t use_graph;
+} mcx_tune;
+
+/* Create a problem on desc->device.  Validates the description (geometry
+ * sizes, region materials in range once tables are loaded, batches >= 1,
+ * n_histories >= 1, increasing energy-bin edges).  *out receives the handle.
+ * Errors: MCX_ERR_ARG, MCX_ERR_CUDA, MCX_ERR_OOM. */
+int mcx_init_problem(const mcx_problem_desc* desc, mcx_problem** out);
+
+/* Load the species library and materials (Sec. 4.1: per-species energy grids
+ * and reaction cross sections; materials as lists of species with atom
+ * densities).  HOST pointers, copied:
+ *   grid_offsets [n_species+1]  species s owns points [off[s], off[s+1]),
+ *                               at least 2 per species
+ *   energies     [P]            FP64, positive, finite, strictly increasing
+ *                               within each species
+ *   sigma        [P][n_ch]      FP64 cross sections, finite and >= 0;
+ *                               n_ch = 2 (scatter, absorb) or 5 (total,
+ *                               scatter, absorb, fission, nu-fission)
+ *   awr          [n_species]    mass ratio A >= 1 (used by transport)
+ *   mat_offsets  [n_materials+1], mat_species [nnz] (ids in range),
+ *   mat_dens     [nnz]          atom densities, finite and >= 0
+ *   precision    MCX_FP64 or MCX_FP32 (sigma is rounded to FP32 on upload)
+ *   hash_bins    number of logarithmic hash-grid bins over [min, max] of all
+ *                grids (0 = no hash: full binary searches); Table 1 range
+ *                100..100000, default 4000
+ * Replaces previously loaded tables.  Errors: MCX_ERR_ARG (with the first
+ * offending index in the message), MCX_ERR_OOM, MCX_ERR_CUDA. */
+int mcx_load_xs_tables(mcx_problem* p, int32_t n_species, const int64_t* grid_offsets,
+                       const double* energies, const double* sigma, int32_t n_ch,
+                       const double* awr, int32_t n_materials, const int32_t* mat_offsets,
+                       const int32_t* mat_species, const double* mat_dens, int32_t precision,
+                       int32_t hash_bins);
+
+/* Make `dst` use the tables and materials already loaded into `src` (no
+ * copy; `src` must outlive `dst`'s use of them).  Used for many problems over
+ * one library.  Errors: MCX_ERR_ARG, MCX_ERR_STATE (src has no tables). */
+int mcx_share_xs_tables(mcx_problem* dst, const mcx_problem* src);
+
+/* Rebuild the hash grid with a new bin count (0 = none) without reloading
+ * the tables.  Results of every entry point are independent of it. */
+int mcx_set_hash_bins(mcx_problem* p, int32_t hash_bins);
+
+/* Replace the atom densities (same sparsity as loaded), HOST pointer. */
+int mcx_set_densities(mcx_problem* p, const double* mat_dens, int64_t nnz);
+
+/* Set / get the event-loop tuning.  mcx_default_tuning fills the plain form:
+ * queueless, block 256, no sorting, threshold 20000, 16 iterations per sync,
+ * automatic cap, graphs on. */
+void mcx_default_tuning(mcx_tune* t);
+int mcx_set_tuning(mcx_problem* p, const mcx_tune* t);
+
+/* Run histories [first_history, first_history + n_histories) of the problem
+ * with a buffer of `particles_in_flight` slots (Sec. 4.1: dead slots are
+ * refilled from the remaining histories after every event iteration; the
+ * count does not change any history).  Scores add to the problem's tallies.
+ * Random numbers: Philox4x32-10 keyed by (seed, problem_id), one stream per
+ * history, so results do not depend on the slot count, tuning or order.
+ * Queued on `stream`; returns after the last iteration has been issued and
+ * the termination flag read (the host synchronises with `stream` once per
+ * `iters_per_sync` iterations).  Errors: MCX_ERR_ARG, MCX_ERR_STATE (no
+ * tables), MCX_ERR_ITER_LIMIT, MCX_ERR_BOUNDS, MCX_ERR_CUDA, MCX_ERR_OOM. */
+int mcx_run_batch(mcx_problem* p, int64_t first_history, int64_t n_histories,
+                  int64_t particles_in_flight, uint64_t seed, void* stream);
+
+/* Many independent problems in one persistent event loop (one slot buffer,
+ * one CUDA graph): histories of all problems are drawn from one global work
+ * list.  All problems must share one set of tables (mcx_share_xs_tables) and
+ * have the derivative flag off.  Each problem's histories [0, n_hist[i]) are
+ * run and scored into that problem's own tallies; problems[0]'s tuning is
+ * used.  Errors as mcx_run_batch. */
+int mcx_batch_run(int32_t n_problems, mcx_problem* const* problems, const int64_t* n_hist,
+                  int64_t particles_in_flight, uint64_t seed, void* stream);
+
+/* Size in doubles of a tally, and a synchronous copy of it to HOST memory
+ * (n must equal the size).  mcx_zero_tallies clears all tallies. */
+int mcx_tally_size(const mcx_problem* p, int32_t which, int64_t* n);
+int mcx_read_tallies(mcx_problem* p, int32_t which, double* host_out, int64_t n);
+int mcx_zero_tallies(mcx_problem* p);
+
+/* Per-history collision counts of the last mcx_run_batch (requires
+ * MCX_FLAG_HISTORY_DEBUG): ncoll[i] for history first_history + i, HOST
+ * pointer, n <= that run's n_histories.  Synchronous. */
+int mcx_read_history_debug(mcx_problem* p, uint32_t* ncoll, int64_t n);
+
+/* Event-loop statistics of the last run: out[0] iterations, out[1] graph
+ * launches, out[2] kernel launches.  HOST pointer, n >= 3. */
+int mcx_last_run_stats(const mcx_problem* p, int64_t* out, int32_t n);
+
+/* Macroscopic cross-section lookup (Sec. 4.1, "the most expensive kernel"):
+ *   out[l][r] = sum over the species i of material mat[l] of
+ *               N_i * sigma_{r,i}(E[l]),  r = 0..n_ch-1,
+ * where sigma_{r,i} interpolates species i's table linearly in energy on the
+ * grid interval [g[k], g[k+1]] with k the largest index in [0, n-2] such
+ * that g[k] <= E (k = 0 below the grid, n-2 at or above its top; the
+ * fraction is clamped to [0, 1]).  E (FP64 [n]), mat (int32 [n]) and out
+ * (FP64 [n][n_ch], row-major) are DEVICE pointers.  flags: MCX_LOOKUP_EXACT
+ * gives the plain definition's FP64 result bit for bit (species in stored
+ * order, sums from +0.0, no fused multiply-add); MCX_LOOKUP_FAST stays within
+ * 1e-6 relative of it; MCX_LOOKUP_SORT first bins the lookups by material and
+ * log-energy (results unchanged; uses library-owned scratch memory sized for
+ * n).  A material id out of range gives NaN outputs for that lookup.
+ * Errors: MCX_ERR_ARG, MCX_ERR_STATE, MCX_ERR_CUDA, MCX_ERR_OOM. */
+int mcx_xs_lookup(mcx_problem* p, int64_t n, const double* E, const int32_t* mat, double* out,
+                  int32_t flags, void* stream);
+
+/* The same lookup from HOST buffers: copies in, computes and copies out in
+ * chunks pipelined over two streams; synchronous.  Host buffers should be
+ * pinned (cudaHostAlloc / torch pin_memory) for full copy speed. */
+int mcx_xs_lookup_host(mcx_problem* p, int64_t n, const double* E_host, const int32_t* mat_host,
+                       double* out_host, int32_t flags);
+
+/* Grid indices used by the lookup, for parity tests: kout[l * max_species +
+ * i] = k of the i-th species of material mat[l], -1 past its species count.
+ * DEVICE pointers.  max_species must be >= the largest material. */
+int mcx_xs_indices(mcx_problem* p, int64_t n, const double* E, const int32_t* mat,
+                   int32_t max_species, int32_t* kout, void* stream);
+
+/* Adjoint of mcx_xs_lookup (exact arithmetic) for a cotangent grad_out
+ * [n][n_ch]:
+ *   grad_dens[j]             += sum_l sum_r grad_out[l][r] * sigma_{r,s}(E_l)
+ *   grad_sigma[p_k][r]       += N_j (1 - f) grad_out[l][r]
+ *   grad_sigma[p_{k+1}][r]   += N_j f grad_out[l][r]
+ * for every lookup l whose material holds entry j (species s, density N_j).
+ * grad_dens [nnz] and grad_sigma [P][n_ch] are FP64 DEVICE buffers that are
+ * accumulated into (zero them first).  E, mat, grad_out are DEVICE pointers.
+ * Summation order is not fixed (atomics), so results match a sequential sum
+ * to rounding. */
+int mcx_xs_lookup_backward(mcx_problem* p, int64_t n, const double* E, const int32_t* mat,
+                           const double* grad_out, double* grad_dens, double* grad_sigma,
+                           void* stream);
+
+/* Test hook: n Philox4x32-10 uniforms of one history stream, as the
+ * transport kernels draw them (uniform first+i of history `hist`), into a
+ * DEVICE buffer out [n]. */
+int mcx_debug_uniforms(uint64_t seed, uint32_t problem_id, uint64_t hist, uint32_t first,
+                       int64_t n, double* out, void* stream);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* mcx_last_error(void);
+
+/* Library version string. */
+const char* mcx_version(void);
+
+/* Release the problem and all device memory it owns.  NULL is ignored. */
+void mcx_destroy(mcx_problem* p);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MCX_H */

@@ -1,0 +1,132 @@
+// kernels.h -- internal kernel-launch interface between the C-ABI layer
+// (mcx_api.cu) and the kernel translation units.  Not part of the public ABI.
+#pragma once
+
+#include "mcx_internal.cuh"
+
+namespace mcx {
+
+// ---------------------------------------------------------------- lookups
+int launch_xs_lookup_exact(const Tables& t, int64_t n, const double* E, const int32_t* mat,
+                           const int32_t* perm, double* out, int grid, cudaStream_t st);
+int launch_xs_lookup_fast(const Tables& t, const float* mden32, int64_t n, const double* E,
+                          const int32_t* mat, const int32_t* perm, double* out, int grid,
+                          cudaStream_t st);
+int launch_xs_indices(const Tables& t, int64_t n, const double* E, const int32_t* mat,
+                      int32_t max_species, int32_t* kout, int grid, cudaStream_t st);
+int launch_build_hash(const Tables& t, int32_t* hidx, int grid, cudaStream_t st);
+int launch_xs_backward(const Tables& t, int64_t n, const double* E, const int32_t* mat,
+                       const double* grad_out, double* grad_dens, double* grad_sigma, int grid,
+                       cudaStream_t st);
+int launch_debug_uniforms(uint2 key, uint64_t hist, uint32_t first, int64_t n, double* out,
+                          cudaStream_t st);
+
+// Counting sort of lookups by key = material * n_ebuckets + log-energy bucket.
+// Scratch: bins [n_materials * n_ebuckets + 1] uint32.  perm receives the
+// lookup indices in bin order.
+struct SortParams {
+    int32_t n_materials = 1;
+    int32_t n_ebuckets = 1;
+    float ln_lo = 0.f, scale = 0.f;  // bucket = (ln E - ln_lo) * scale
+};
+int launch_lookup_sort(const SortParams& sp, int64_t n, const double* E, const int32_t* mat,
+                       uint32_t* bins, int32_t* perm, int grid, cudaStream_t st);
+
+// ------------------------------------------------------------- transport
+enum : uint8_t {
+    PF_ALIVE = 1,
+    PF_NEED_XS = 2,
+    PF_INPIN = 4,
+    PF_COLLIDE = 8,
+    PF_RETIRED = 16,
+};
+
+enum { OUT_ABSORBED = 0, OUT_LEAK_XHI = 1, OUT_LEAK_OTHER = 2, OUT_CUTOFF = 3, OUT_COLLISIONS = 4,
+       N_OUT = 5 };
+
+// One transport problem as the kernels see it (device array, one per
+// problem of a run).
+struct ProblemDev {
+    int32_t geometry;
+    int32_t lattice_n;
+    int32_t nb;          // tally bins
+    int32_t n_batches;
+    int32_t n_ebins;
+    int32_t M;           // materials with derivative tallies (0 = off)
+    double pitch, radius, height, slab_length, half, E0, E_cut;
+    const int32_t* region_material;
+    const double* ebin_edges;
+    uint2 key;            // Philox key (seed, problem id)
+    int64_t n_hist_total; // defines batches
+    int64_t first;        // first history of this run
+    double* flux;
+    double* absorb;
+    double* outcome;
+    double* dflux;
+    double* dabsorb;
+    double* doutcome;
+    uint32_t* ncoll_debug;  // [run histories] or null
+};
+
+// Structure-of-arrays particle buffer (one slot per particle in flight) and
+// the event queues.
+struct Particles {
+    int64_t cap = 0;
+    double *x = nullptr, *y = nullptr, *z = nullptr;
+    double *u = nullptr, *v = nullptr, *w = nullptr;
+    double *E = nullptr, *sig_t = nullptr, *sig_a = nullptr;
+    double* W = nullptr;  // [MCX_MAX_DMAT][cap] (derivative runs)
+    int64_t* hist = nullptr;
+    uint32_t* rng_n = nullptr;
+    uint32_t* ncoll = nullptr;
+    int32_t* cell = nullptr;  // ci * n + cj
+    int32_t* mat = nullptr;
+    int32_t* prob = nullptr;
+    uint8_t* flags = nullptr;
+    int32_t* q_xs[2] = {nullptr, nullptr};
+    int32_t* q_adv[2] = {nullptr, nullptr};
+    int32_t* q_dead[2] = {nullptr, nullptr};
+    int32_t* q_coll = nullptr;
+    int32_t* q_sorted = nullptr;  // binned copy of a queue
+    uint32_t* bins = nullptr;     // counting-sort bins
+};
+
+// Device-resident loop control: counters, queue sizes, termination.
+struct RunCtl {
+    unsigned long long next;  // next work item
+    long long total;          // work items of the run
+    long long iters;
+    long long max_iters;
+    int n_prob;
+    int n_alive;
+    int done;
+    int error;                // 0 or an MCX_ERR_* code
+    int parity;
+    int n_xs[2], n_adv[2], n_dead[2];
+    int n_coll;
+    int sorted;               // this iteration's queue was binned
+    int pad;
+};
+
+struct LoopConfig {
+    int mode = MCX_QUEUELESS;
+    int block = 256;
+    int grid = 148;
+    int sort_period = 0;
+    long long sort_threshold = 20000;
+    int n_ebuckets = 128;
+    int n_sort_bins = 0;     // materials * n_ebuckets
+    float sort_ln_lo = 0.f, sort_scale = 0.f;
+    int derivatives = 0;
+};
+
+// Kernels of one event-loop iteration, issued on `st` (capturable).
+// Returns the number of kernels launched, or -1 on a launch error.
+int launch_iteration(const LoopConfig& c, const Tables& t, const Particles& P,
+                     const ProblemDev* probs, const int64_t* work_off, RunCtl* ctl,
+                     cudaStream_t st);
+// Reset the particle buffer and loop control for a run of `total` work items.
+int launch_run_init(const LoopConfig& c, const Particles& P, RunCtl* ctl, long long total,
+                    int n_prob, long long max_iters, cudaStream_t st);
+
+}  // namespace mcx

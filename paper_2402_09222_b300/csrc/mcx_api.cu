@@ -1,0 +1,1131 @@
+// mcx_api.cu -- the C ABI of libmcx (declared in include/mcx.h): argument
+// validation, device memory, the event-loop driver (CUDA-graph replay with a
+// device-side termination flag and iteration cap) and the lookup entry
+// points.  No exception or abort crosses the ABI: every failure becomes a
+// status code plus a thread-local message.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+
+using namespace mcx;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define CUDA_TRY(expr)                                                                    \
+    do {                                                                                  \
+        cudaError_t e_ = (expr);                                                          \
+        if (e_ != cudaSuccess) {                                                          \
+            if (e_ == cudaErrorMemoryAllocation) {                                        \
+                cudaGetLastError();                                                       \
+                return fail(MCX_ERR_OOM, "%s: %s", #expr, cudaGetErrorString(e_));        \
+            }                                                                             \
+            return fail(MCX_ERR_CUDA, "%s: %s", #expr, cudaGetErrorString(e_));           \
+        }                                                                                 \
+    } while (0)
+
+#define TRY(expr)                  \
+    do {                           \
+        int r_ = (expr);           \
+        if (r_ != MCX_OK) return r_; \
+    } while (0)
+
+// Selects a device for the duration of a call and restores the caller's.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+template <typename T>
+int dev_alloc(T** p, size_t count)
+{
+    *p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void**)p, sizeof(T) * count);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(e == cudaErrorMemoryAllocation ? MCX_ERR_OOM : MCX_ERR_CUDA,
+                    "cudaMalloc(%zu bytes): %s", sizeof(T) * count, cudaGetErrorString(e));
+    }
+    return MCX_OK;
+}
+
+template <typename T>
+void dev_free(T*& p)
+{
+    if (p) cudaFree((void*)p);
+    p = nullptr;
+}
+
+// Tables and materials on the device, shared by reference count.
+struct TableStore {
+    int refs = 1;
+    int device = 0;
+    Tables view;
+    int64_t* goff = nullptr;
+    double* E = nullptr;
+    void* sigma = nullptr;
+    double* awr = nullptr;
+    int32_t* moff = nullptr;
+    int32_t* msp = nullptr;
+    double* mden = nullptr;
+    float* mden32 = nullptr;
+    int32_t* hidx = nullptr;
+    double* hbound = nullptr;
+    double emin = 0.0, emax = 0.0;
+    int64_t nnz = 0;
+    std::vector<int32_t> h_moff;
+
+    ~TableStore()
+    {
+        dev_free(goff);
+        dev_free(E);
+        if (sigma) cudaFree(sigma);
+        dev_free(awr);
+        dev_free(moff);
+        dev_free(msp);
+        dev_free(mden);
+        dev_free(mden32);
+        dev_free(hidx);
+        dev_free(hbound);
+    }
+};
+
+int sm_count_of(int device)
+{
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || n <= 0)
+        n = 148;
+    return n;
+}
+
+}  // namespace
+
+struct mcx_problem {
+    mcx_problem_desc desc{};
+    std::vector<int32_t> region_material;
+    std::vector<double> ebin_edges;
+    int device = 0;
+    int sm_count = 148;
+    int nb = 0;  // tally bins
+    int M = 0;   // derivative materials (0 = off)
+    TableStore* tables = nullptr;
+    mcx_tune tune{};
+    // device copies of the description
+    int32_t* d_region_material = nullptr;
+    double* d_ebin_edges = nullptr;
+    // tallies
+    double* flux = nullptr;
+    double* absorb = nullptr;
+    double* outcome = nullptr;
+    double* dflux = nullptr;
+    double* dabsorb = nullptr;
+    double* doutcome = nullptr;
+    // run resources
+    Particles P;
+    void* p_block = nullptr;
+    int64_t p_cap = 0;
+    bool p_has_w = false;
+    size_t bins_cap = 0;
+    ProblemDev* d_probs = nullptr;
+    int64_t* d_work_off = nullptr;
+    int probs_cap = 0;
+    RunCtl* d_ctl = nullptr;
+    RunCtl* h_ctl = nullptr;
+    cudaStream_t stream = nullptr;
+    cudaStream_t stream2 = nullptr;
+    cudaEvent_t ev_a = nullptr, ev_b = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    std::vector<unsigned char> graph_key;
+    uint32_t* ncoll_debug = nullptr;
+    int64_t debug_cap = 0;
+    int64_t debug_n = 0;
+    // lookup scratch
+    int32_t* perm = nullptr;
+    uint32_t* lbins = nullptr;
+    int64_t perm_cap = 0;
+    size_t lbins_cap = 0;
+    double* h_buf = nullptr;  // host-path device staging
+    int64_t h_buf_cap = 0;
+    int64_t stats[3] = {0, 0, 0};
+};
+
+namespace {
+
+void release_tables(mcx_problem* p)
+{
+    if (p->tables && --p->tables->refs == 0) delete p->tables;
+    p->tables = nullptr;
+}
+
+void free_particles(mcx_problem* p)
+{
+    if (p->p_block) cudaFree(p->p_block);
+    p->p_block = nullptr;
+    p->P = Particles{};
+    p->p_cap = 0;
+    p->bins_cap = 0;
+}
+
+void drop_graph(mcx_problem* p)
+{
+    if (p->gexec) cudaGraphExecDestroy(p->gexec);
+    p->gexec = nullptr;
+    p->graph_key.clear();
+}
+
+// One device block for the whole particle buffer (SoA arrays + queues + bins).
+int ensure_particles(mcx_problem* p, int64_t cap, bool with_w, size_t n_bins)
+{
+    if (p->p_block && p->p_cap >= cap && (p->p_has_w || !with_w) && p->bins_cap >= n_bins)
+        return MCX_OK;
+    drop_graph(p);
+    int64_t want = cap > p->p_cap ? cap : p->p_cap;
+    size_t bins = n_bins > p->bins_cap ? n_bins : p->bins_cap;
+    bool w = with_w || p->p_has_w;
+    free_particles(p);
+    const size_t c = (size_t)want;
+    auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    size_t bytes = al(c * 8) * 9 + (w ? al(c * 8 * MCX_MAX_DMAT) : 0) + al(c * 8) + al(c * 4) * 2 +
+                   al(c * 4) * 3 + al(c) + al(c * 4) * 8 + al((bins + 1) * 4);
+    void* blk = nullptr;
+    cudaError_t e = cudaMalloc(&blk, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(MCX_ERR_OOM, "particle buffer of %lld slots (%zu bytes): %s", (long long)want,
+                    bytes, cudaGetErrorString(e));
+    }
+    char* q = (char*)blk;
+    auto take = [&](size_t b) {
+        char* r = q;
+        q += al(b);
+        return (void*)r;
+    };
+    Particles& P = p->P;
+    P.cap = want;
+    P.x = (double*)take(c * 8);
+    P.y = (double*)take(c * 8);
+    P.z = (double*)take(c * 8);
+    P.u = (double*)take(c * 8);
+    P.v = (double*)take(c * 8);
+    P.w = (double*)take(c * 8);
+    P.E = (double*)take(c * 8);
+    P.sig_t = (double*)take(c * 8);
+    P.sig_a = (double*)take(c * 8);
+    P.W = w ? (double*)take(c * 8 * MCX_MAX_DMAT) : nullptr;
+    P.hist = (int64_t*)take(c * 8);
+    P.rng_n = (uint32_t*)take(c * 4);
+    P.ncoll = (uint32_t*)take(c * 4);
+    P.cell = (int32_t*)take(c * 4);
+    P.mat = (int32_t*)take(c * 4);
+    P.prob = (int32_t*)take(c * 4);
+    P.flags = (uint8_t*)take(c);
+    for (int k = 0; k < 2; ++k) {
+        P.q_xs[k] = (int32_t*)take(c * 4);
+        P.q_adv[k] = (int32_t*)take(c * 4);
+        P.q_dead[k] = (int32_t*)take(c * 4);
+    }
+    P.q_coll = (int32_t*)take(c * 4);
+    P.q_sorted = (int32_t*)take(c * 4);
+    P.bins = (uint32_t*)take((bins + 1) * 4);
+    p->p_block = blk;
+    p->p_cap = want;
+    p->p_has_w = w;
+    p->bins_cap = bins;
+    return MCX_OK;
+}
+
+bool is_finite(double x) { return std::isfinite(x); }
+
+int validate_desc(const mcx_problem_desc* d)
+{
+    if (!d) return fail(MCX_ERR_ARG, "desc is NULL");
+    if (d->geometry < 0 || d->geometry > MCX_GEOM_NONE)
+        return fail(MCX_ERR_ARG, "unknown geometry %d", d->geometry);
+    if (d->geometry == MCX_GEOM_NONE) return MCX_OK;
+    if (!(d->E0 > 0.0) || !is_finite(d->E0)) return fail(MCX_ERR_ARG, "E0 must be positive and finite");
+    if (!(d->E_cut >= 0.0) || !is_finite(d->E_cut)) return fail(MCX_ERR_ARG, "E_cut must be >= 0");
+    if (d->n_batches < 1) return fail(MCX_ERR_ARG, "n_batches must be >= 1");
+    if (d->n_histories < 1) return fail(MCX_ERR_ARG, "n_histories must be >= 1");
+    if ((int64_t)d->n_batches > d->n_histories)
+        return fail(MCX_ERR_ARG, "n_batches (%d) exceeds n_histories", d->n_batches);
+    if (d->n_histories >= ((int64_t)1 << 40)) return fail(MCX_ERR_ARG, "n_histories too large");
+    if (!d->region_material) return fail(MCX_ERR_ARG, "region_material is NULL");
+    if (d->geometry == MCX_GEOM_LATTICE) {
+        if (d->lattice_n < 1 || d->lattice_n > 4096) return fail(MCX_ERR_ARG, "lattice_n out of range");
+        if (!(d->pitch > 0.0) || !is_finite(d->pitch)) return fail(MCX_ERR_ARG, "pitch must be > 0");
+        if (!(d->radius > 0.0) || !(2.0 * d->radius < d->pitch))
+            return fail(MCX_ERR_ARG, "radius must be in (0, pitch/2)");
+        if (!(d->height > 0.0) || !is_finite(d->height)) return fail(MCX_ERR_ARG, "height must be > 0");
+        if (d->n_regions != d->lattice_n * d->lattice_n + 1)
+            return fail(MCX_ERR_ARG, "lattice needs n^2 + 1 = %d regions, got %d",
+                        d->lattice_n * d->lattice_n + 1, d->n_regions);
+    } else {
+        if (d->n_regions != 1) return fail(MCX_ERR_ARG, "this geometry has exactly 1 region");
+    }
+    if (d->geometry == MCX_GEOM_SLAB && (!(d->slab_length > 0.0) || !is_finite(d->slab_length)))
+        return fail(MCX_ERR_ARG, "slab_length must be > 0");
+    if (d->geometry == MCX_GEOM_INFINITE) {
+        if (d->n_ebins < 1 || !d->ebin_edges) return fail(MCX_ERR_ARG, "infinite medium needs energy bins");
+        for (int i = 0; i <= d->n_ebins; ++i) {
+            if (!(d->ebin_edges[i] > 0.0) || !is_finite(d->ebin_edges[i]))
+                return fail(MCX_ERR_ARG, "ebin_edges[%d] must be positive and finite", i);
+            if (i > 0 && !(d->ebin_edges[i] > d->ebin_edges[i - 1]))
+                return fail(MCX_ERR_ARG, "ebin_edges not strictly increasing at %d", i);
+        }
+    }
+    for (int r = 0; r < d->n_regions; ++r)
+        if (d->region_material[r] < 0) return fail(MCX_ERR_ARG, "region_material[%d] < 0", r);
+    return MCX_OK;
+}
+
+int alloc_tallies(mcx_problem* p)
+{
+    const int64_t B = p->desc.n_batches;
+    TRY(dev_alloc(&p->flux, (size_t)(B * p->nb)));
+    TRY(dev_alloc(&p->absorb, (size_t)(B * p->nb)));
+    TRY(dev_alloc(&p->outcome, (size_t)(B * N_OUT)));
+    CUDA_TRY(cudaMemset(p->flux, 0, sizeof(double) * B * p->nb));
+    CUDA_TRY(cudaMemset(p->absorb, 0, sizeof(double) * B * p->nb));
+    CUDA_TRY(cudaMemset(p->outcome, 0, sizeof(double) * B * N_OUT));
+    return MCX_OK;
+}
+
+int alloc_derivative_tallies(mcx_problem* p, int M)
+{
+    dev_free(p->dflux);
+    dev_free(p->dabsorb);
+    dev_free(p->doutcome);
+    p->M = M;
+    if (M == 0) return MCX_OK;
+    const int64_t B = p->desc.n_batches;
+    TRY(dev_alloc(&p->dflux, (size_t)(B * p->nb * M)));
+    TRY(dev_alloc(&p->dabsorb, (size_t)(B * p->nb * M)));
+    TRY(dev_alloc(&p->doutcome, (size_t)(B * N_OUT * M)));
+    CUDA_TRY(cudaMemset(p->dflux, 0, sizeof(double) * B * p->nb * M));
+    CUDA_TRY(cudaMemset(p->dabsorb, 0, sizeof(double) * B * p->nb * M));
+    CUDA_TRY(cudaMemset(p->doutcome, 0, sizeof(double) * B * N_OUT * M));
+    return MCX_OK;
+}
+
+int build_hash(TableStore* ts, int32_t H, int sm_count)
+{
+    dev_free(ts->hidx);
+    dev_free(ts->hbound);
+    ts->view.H = 0;
+    ts->view.hidx = nullptr;
+    ts->view.hbound = nullptr;
+    if (H == 0) return MCX_OK;
+    std::vector<double> hb((size_t)H + 1);
+    const double lo = std::log(ts->emin), hi = std::log(ts->emax);
+    hb[0] = ts->emin;
+    hb[H] = ts->emax;
+    for (int b = 1; b < H; ++b) {
+        double v = std::exp(lo + (hi - lo) * ((double)b / (double)H));
+        if (!(v > hb[b - 1])) v = std::nextafter(hb[b - 1], INFINITY);
+        hb[b] = v;
+    }
+    if (!(hb[H] > hb[H - 1])) return fail(MCX_ERR_ARG, "hash_bins too large for the energy range");
+    TRY(dev_alloc(&ts->hbound, (size_t)H + 1));
+    TRY(dev_alloc(&ts->hidx, (size_t)ts->view.n_species * ((size_t)H + 1)));
+    CUDA_TRY(cudaMemcpy(ts->hbound, hb.data(), sizeof(double) * (H + 1), cudaMemcpyHostToDevice));
+    ts->view.H = H;
+    ts->view.hbound = ts->hbound;
+    ts->view.hash_ln_lo = (float)lo;
+    ts->view.hash_scale = (float)((double)H / (hi - lo));
+    Tables tmp = ts->view;
+    if (launch_build_hash(tmp, ts->hidx, sm_count * 8, 0)) return fail(MCX_ERR_CUDA, "hash build launch failed");
+    CUDA_TRY(cudaDeviceSynchronize());
+    ts->view.hidx = ts->hidx;
+    return MCX_OK;
+}
+
+int check_handle(const mcx_problem* p)
+{
+    if (!p) return fail(MCX_ERR_ARG, "problem handle is NULL");
+    return MCX_OK;
+}
+
+int check_tables(const mcx_problem* p)
+{
+    TRY(check_handle(p));
+    if (!p->tables) return fail(MCX_ERR_STATE, "no cross-section tables loaded");
+    return MCX_OK;
+}
+
+ProblemDev make_problem_dev(mcx_problem* p, uint64_t seed, int64_t first, bool deriv)
+{
+    ProblemDev d{};
+    const mcx_problem_desc& s = p->desc;
+    d.geometry = s.geometry;
+    d.lattice_n = s.geometry == MCX_GEOM_LATTICE ? s.lattice_n : 0;
+    d.nb = p->nb;
+    d.n_batches = s.n_batches;
+    d.n_ebins = s.n_ebins;
+    d.M = deriv ? p->M : 0;
+    d.pitch = s.pitch;
+    d.radius = s.radius;
+    d.height = s.height;
+    d.slab_length = s.slab_length;
+    d.half = 0.5 * (double)d.lattice_n * s.pitch;
+    d.E0 = s.E0;
+    d.E_cut = s.E_cut;
+    d.region_material = p->d_region_material;
+    d.ebin_edges = p->d_ebin_edges;
+    d.key = rng_key(seed, s.problem_id);
+    d.n_hist_total = s.n_histories;
+    d.first = first;
+    d.flux = p->flux;
+    d.absorb = p->absorb;
+    d.outcome = p->outcome;
+    d.dflux = p->dflux;
+    d.dabsorb = p->dabsorb;
+    d.doutcome = p->doutcome;
+    d.ncoll_debug = (s.flags & MCX_FLAG_HISTORY_DEBUG) ? p->ncoll_debug : nullptr;
+    return d;
+}
+
+int blocks_per_sm(int block)
+{
+    // the event kernels use <= 64 registers per thread at 1024 threads; keep
+    // 2048 resident threads per SM
+    int b = 2048 / block;
+    return b < 1 ? 1 : b;
+}
+
+// The event-loop driver shared by mcx_run_batch and mcx_batch_run.
+int run_loop(mcx_problem* owner, int n_prob, mcx_problem* const* probs, const int64_t* first,
+             const int64_t* count, int64_t pif, uint64_t seed, void* user_stream)
+{
+    const TableStore* ts = owner->tables;
+    const Tables& t = ts->view;
+    if (t.n_ch != 2 && t.n_ch != 5) return fail(MCX_ERR_ARG, "transport needs 2 or 5 channels");
+    const mcx_tune& tu = owner->tune;
+    long long total = 0;
+    for (int i = 0; i < n_prob; ++i) total += count[i];
+    if (pif < 1) return fail(MCX_ERR_ARG, "particles_in_flight must be >= 1");
+    if (pif > (int64_t)1 << 30) return fail(MCX_ERR_ARG, "particles_in_flight too large");
+    const bool deriv = n_prob == 1 && owner->M > 0;
+    int64_t cap = pif < total ? pif : total;
+    if (cap < 1) cap = 1;
+    LoopConfig c;
+    c.mode = tu.mode;
+    c.block = tu.block_size;
+    c.grid = owner->sm_count * blocks_per_sm(tu.block_size);
+    c.sort_period = tu.mode == MCX_QUEUED ? tu.sort_period : 0;
+    c.sort_threshold = tu.sort_threshold;
+    c.n_ebuckets = 128;
+    c.n_sort_bins = t.n_materials * c.n_ebuckets;
+    c.sort_ln_lo = (float)std::log(ts->emin);
+    c.sort_scale = (float)((double)c.n_ebuckets / (std::log(ts->emax) - std::log(ts->emin)));
+    c.derivatives = deriv ? owner->M : 0;
+    if ((size_t)c.n_sort_bins * 4 > 48 * 1024) c.sort_period = 0;  // bins must fit shared memory
+    TRY(ensure_particles(owner, cap, deriv, (size_t)c.n_sort_bins));
+    // problems and work offsets
+    if (owner->probs_cap < n_prob) {
+        drop_graph(owner);
+        dev_free(owner->d_probs);
+        dev_free(owner->d_work_off);
+        TRY(dev_alloc(&owner->d_probs, (size_t)n_prob));
+        TRY(dev_alloc(&owner->d_work_off, (size_t)n_prob + 1));
+        owner->probs_cap = n_prob;
+    }
+    std::vector<ProblemDev> hp((size_t)n_prob);
+    std::vector<int64_t> wo((size_t)n_prob + 1, 0);
+    for (int i = 0; i < n_prob; ++i) {
+        mcx_problem* q = probs[i];
+        if (q->desc.flags & MCX_FLAG_HISTORY_DEBUG) {
+            if (q->debug_cap < count[i]) {
+                dev_free(q->ncoll_debug);
+                TRY(dev_alloc(&q->ncoll_debug, (size_t)count[i]));
+                q->debug_cap = count[i];
+            }
+            q->debug_n = count[i];
+        }
+        hp[i] = make_problem_dev(q, seed, first[i], deriv);
+        wo[i + 1] = wo[i] + count[i];
+    }
+    cudaStream_t us = (cudaStream_t)user_stream;
+    cudaStream_t st = owner->stream;
+    CUDA_TRY(cudaEventRecord(owner->ev_a, us));
+    CUDA_TRY(cudaStreamWaitEvent(st, owner->ev_a, 0));
+    CUDA_TRY(cudaMemcpyAsync(owner->d_probs, hp.data(), sizeof(ProblemDev) * n_prob,
+                             cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(owner->d_work_off, wo.data(), sizeof(int64_t) * (n_prob + 1),
+                             cudaMemcpyHostToDevice, st));
+    const long long max_iters = tu.max_event_iters > 0 ? tu.max_event_iters : 4000000LL;
+    if (launch_run_init(c, owner->P, owner->d_ctl, total, n_prob, max_iters, st))
+        return fail(MCX_ERR_CUDA, "run init launch failed");
+    const int K = tu.iters_per_sync;
+    // graph key: everything the captured kernels see by value
+    std::vector<unsigned char> key;
+    auto put = [&](const void* v, size_t n) {
+        key.insert(key.end(), (const unsigned char*)v, (const unsigned char*)v + n);
+    };
+    put(&c, sizeof(c));
+    put(&t, sizeof(t));
+    put(&owner->P, sizeof(Particles));
+    put(&owner->d_probs, sizeof(void*));
+    put(&owner->d_work_off, sizeof(void*));
+    put(&K, sizeof(K));
+    int kernels_per_iter = 0;
+    if (tu.use_graph) {
+        if (!owner->gexec || owner->graph_key != key) {
+            drop_graph(owner);
+            cudaGraph_t g = nullptr;
+            CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+            int bad = 0;
+            for (int k = 0; k < K; ++k) {
+                const int r = launch_iteration(c, t, owner->P, owner->d_probs, owner->d_work_off,
+                                               owner->d_ctl, st);
+                if (r < 0) bad = 1;
+                kernels_per_iter = r;
+            }
+            cudaError_t ec = cudaStreamEndCapture(st, &g);
+            if (bad || ec != cudaSuccess) {
+                if (g) cudaGraphDestroy(g);
+                cudaGetLastError();
+                return fail(MCX_ERR_CUDA, "capturing the event loop failed: %s", cudaGetErrorString(ec));
+            }
+            cudaError_t ei = cudaGraphInstantiate(&owner->gexec, g, 0);
+            cudaGraphDestroy(g);
+            if (ei != cudaSuccess) {
+                owner->gexec = nullptr;
+                return fail(MCX_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(ei));
+            }
+            owner->graph_key = key;
+        }
+    }
+    if (kernels_per_iter == 0) {
+        kernels_per_iter = 5 + ((c.mode == MCX_QUEUED && c.sort_period > 0) ? 8 : 0);
+    }
+    int64_t launches = 0, kernels = 0;
+    const int64_t max_launches = max_iters / K + 4;
+    int status = MCX_OK;
+    for (;;) {
+        if (tu.use_graph) {
+            CUDA_TRY(cudaGraphLaunch(owner->gexec, st));
+        } else {
+            for (int k = 0; k < K; ++k)
+                if (launch_iteration(c, t, owner->P, owner->d_probs, owner->d_work_off, owner->d_ctl, st) < 0)
+                    return fail(MCX_ERR_CUDA, "event kernel launch failed");
+        }
+        ++launches;
+        kernels += (int64_t)K * kernels_per_iter;
+        CUDA_TRY(cudaMemcpyAsync(owner->h_ctl, owner->d_ctl, sizeof(RunCtl), cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+        if (owner->h_ctl->error) {
+            status = owner->h_ctl->error == MCX_ERR_ITER_LIMIT
+                         ? fail(MCX_ERR_ITER_LIMIT, "event loop reached its cap of %lld iterations",
+                                (long long)max_iters)
+                         : fail(owner->h_ctl->error, "device error %d", owner->h_ctl->error);
+            break;
+        }
+        if (owner->h_ctl->done) break;
+        if (launches >= max_launches) {
+            status = fail(MCX_ERR_ITER_LIMIT, "host loop reached its launch cap");
+            break;
+        }
+    }
+    owner->stats[0] = owner->h_ctl->iters;
+    owner->stats[1] = launches;
+    owner->stats[2] = kernels;
+    CUDA_TRY(cudaEventRecord(owner->ev_b, st));
+    CUDA_TRY(cudaStreamWaitEvent(us, owner->ev_b, 0));
+    return status;
+}
+
+int lookup_grid(const mcx_problem* p) { return p->sm_count * 8; }
+
+int ensure_lookup_scratch(mcx_problem* p, int64_t n, size_t bins)
+{
+    if (p->perm_cap < n) {
+        dev_free(p->perm);
+        TRY(dev_alloc(&p->perm, (size_t)n));
+        p->perm_cap = n;
+    }
+    if (p->lbins_cap < bins + 1) {
+        dev_free(p->lbins);
+        TRY(dev_alloc(&p->lbins, bins + 1));
+        p->lbins_cap = bins + 1;
+    }
+    return MCX_OK;
+}
+
+// Lookup on device buffers, queued on `st`.
+int lookup_device(mcx_problem* p, int64_t n, const double* E, const int32_t* mat, double* out,
+                  int32_t flags, cudaStream_t st)
+{
+    const TableStore* ts = p->tables;
+    const int32_t* perm = nullptr;
+    if (flags & MCX_LOOKUP_SORT) {
+        SortParams sp;
+        sp.n_materials = ts->view.n_materials;
+        sp.n_ebuckets = 1024;
+        while (sp.n_ebuckets > 1 && (size_t)sp.n_materials * sp.n_ebuckets * 4 > 48 * 1024) sp.n_ebuckets >>= 1;
+        sp.ln_lo = (float)std::log(ts->emin);
+        sp.scale = (float)((double)sp.n_ebuckets / (std::log(ts->emax) - std::log(ts->emin)));
+        TRY(ensure_lookup_scratch(p, n, (size_t)sp.n_materials * sp.n_ebuckets));
+        if (launch_lookup_sort(sp, n, E, mat, p->lbins, p->perm, lookup_grid(p), st))
+            return fail(MCX_ERR_CUDA, "lookup sort launch failed");
+        perm = p->perm;
+    }
+    int r = (flags & MCX_LOOKUP_FAST)
+                ? launch_xs_lookup_fast(ts->view, ts->mden32, n, E, mat, perm, out, lookup_grid(p), st)
+                : launch_xs_lookup_exact(ts->view, n, E, mat, perm, out, lookup_grid(p), st);
+    if (r) return fail(MCX_ERR_CUDA, "lookup launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+    return MCX_OK;
+}
+
+}  // namespace
+
+// ===================================================================== ABI
+
+extern "C" {
+
+const char* mcx_last_error(void) { return g_err.c_str(); }
+
+const char* mcx_version(void) { return "libmcx 0.1 (sm_103a)"; }
+
+void mcx_default_tuning(mcx_tune* t)
+{
+    if (!t) return;
+    t->mode = MCX_QUEUELESS;
+    t->block_size = 256;
+    t->sort_period = 0;
+    t->sort_threshold = 20000;
+    t->iters_per_sync = 16;
+    t->max_event_iters = 0;
+    t->use_graph = 1;
+}
+
+int mcx_init_problem(const mcx_problem_desc* desc, mcx_problem** out)
+{
+    g_err.clear();
+    if (!out) return fail(MCX_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    TRY(validate_desc(desc));
+    int ndev = 0;
+    CUDA_TRY(cudaGetDeviceCount(&ndev));
+    if (desc->device < 0 || desc->device >= ndev)
+        return fail(MCX_ERR_ARG, "device %d not present (%d devices)", desc->device, ndev);
+    DeviceGuard dg(desc->device);
+    if (!dg.ok) return fail(MCX_ERR_CUDA, "cudaSetDevice(%d) failed", desc->device);
+    mcx_problem* p = new (std::nothrow) mcx_problem();
+    if (!p) return fail(MCX_ERR_OOM, "host allocation failed");
+    p->desc = *desc;
+    p->device = desc->device;
+    p->sm_count = sm_count_of(desc->device);
+    mcx_default_tuning(&p->tune);
+    int rc = MCX_OK;
+    auto bail = [&](int code) {
+        mcx_destroy(p);
+        return code;
+    };
+    if (desc->geometry != MCX_GEOM_NONE) {
+        p->region_material.assign(desc->region_material, desc->region_material + desc->n_regions);
+        if (desc->geometry == MCX_GEOM_INFINITE)
+            p->ebin_edges.assign(desc->ebin_edges, desc->ebin_edges + desc->n_ebins + 1);
+        p->desc.region_material = p->region_material.data();
+        p->desc.ebin_edges = p->ebin_edges.empty() ? nullptr : p->ebin_edges.data();
+        p->nb = desc->geometry == MCX_GEOM_INFINITE ? desc->n_ebins
+                : desc->geometry == MCX_GEOM_LATTICE ? desc->n_regions
+                                                     : 1;
+        if ((rc = dev_alloc(&p->d_region_material, p->region_material.size())) != MCX_OK) return bail(rc);
+        if (cudaMemcpy(p->d_region_material, p->region_material.data(),
+                       sizeof(int32_t) * p->region_material.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+            return bail(fail(MCX_ERR_CUDA, "copying region materials failed"));
+        if (!p->ebin_edges.empty()) {
+            if ((rc = dev_alloc(&p->d_ebin_edges, p->ebin_edges.size())) != MCX_OK) return bail(rc);
+            if (cudaMemcpy(p->d_ebin_edges, p->ebin_edges.data(), sizeof(double) * p->ebin_edges.size(),
+                           cudaMemcpyHostToDevice) != cudaSuccess)
+                return bail(fail(MCX_ERR_CUDA, "copying energy bins failed"));
+        }
+        if ((rc = alloc_tallies(p)) != MCX_OK) return bail(rc);
+    } else {
+        p->desc.region_material = nullptr;
+        p->desc.ebin_edges = nullptr;
+    }
+    if (cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&p->stream2, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->ev_a, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->ev_b, cudaEventDisableTiming) != cudaSuccess)
+        return bail(fail(MCX_ERR_CUDA, "stream/event creation failed"));
+    if ((rc = dev_alloc(&p->d_ctl, 1)) != MCX_OK) return bail(rc);
+    if (cudaMallocHost((void**)&p->h_ctl, sizeof(RunCtl)) != cudaSuccess)
+        return bail(fail(MCX_ERR_OOM, "pinned host allocation failed"));
+    memset(p->h_ctl, 0, sizeof(RunCtl));
+    *out = p;
+    return MCX_OK;
+}
+
+void mcx_destroy(mcx_problem* p)
+{
+    if (!p) return;
+    DeviceGuard dg(p->device);
+    if (p->stream) cudaStreamSynchronize(p->stream);
+    drop_graph(p);
+    release_tables(p);
+    free_particles(p);
+    dev_free(p->d_region_material);
+    dev_free(p->d_ebin_edges);
+    dev_free(p->flux);
+    dev_free(p->absorb);
+    dev_free(p->outcome);
+    dev_free(p->dflux);
+    dev_free(p->dabsorb);
+    dev_free(p->doutcome);
+    dev_free(p->d_probs);
+    dev_free(p->d_work_off);
+    dev_free(p->d_ctl);
+    dev_free(p->ncoll_debug);
+    dev_free(p->perm);
+    dev_free(p->lbins);
+    dev_free(p->h_buf);
+    if (p->h_ctl) cudaFreeHost(p->h_ctl);
+    if (p->ev_a) cudaEventDestroy(p->ev_a);
+    if (p->ev_b) cudaEventDestroy(p->ev_b);
+    if (p->stream) cudaStreamDestroy(p->stream);
+    if (p->stream2) cudaStreamDestroy(p->stream2);
+    delete p;
+}
+
+int mcx_load_xs_tables(mcx_problem* p, int32_t n_species, const int64_t* goff, const double* energies,
+                       const double* sigma, int32_t n_ch, const double* awr, int32_t n_materials,
+                       const int32_t* moff, const int32_t* msp, const double* mden,
+                       int32_t precision, int32_t hash_bins)
+{
+    g_err.clear();
+    TRY(check_handle(p));
+    if (n_species < 1) return fail(MCX_ERR_ARG, "n_species must be >= 1");
+    if (n_ch < 1 || n_ch > 5) return fail(MCX_ERR_ARG, "n_ch must be in 1..5");
+    if (!goff || !energies || !sigma || !awr || !moff || !msp || !mden)
+        return fail(MCX_ERR_ARG, "NULL table pointer");
+    if (precision != MCX_FP64 && precision != MCX_FP32) return fail(MCX_ERR_ARG, "unknown precision");
+    if (hash_bins < 0 || hash_bins > 10000000) return fail(MCX_ERR_ARG, "hash_bins out of range");
+    if (n_materials < 1) return fail(MCX_ERR_ARG, "n_materials must be >= 1");
+    if (goff[0] != 0) return fail(MCX_ERR_ARG, "grid_offsets[0] must be 0");
+    for (int s = 0; s < n_species; ++s)
+        if (goff[s + 1] - goff[s] < 2) return fail(MCX_ERR_ARG, "species %d has fewer than 2 points", s);
+    const int64_t P = goff[n_species];
+    if (P >= ((int64_t)1 << 31)) return fail(MCX_ERR_ARG, "too many grid points");
+    double emin = INFINITY, emax = -INFINITY;
+    for (int s = 0; s < n_species; ++s) {
+        for (int64_t i = goff[s]; i < goff[s + 1]; ++i) {
+            const double e = energies[i];
+            if (!(e > 0.0) || !is_finite(e))
+                return fail(MCX_ERR_ARG, "energies[%lld] must be positive and finite", (long long)i);
+            if (i > goff[s] && !(e > energies[i - 1]))
+                return fail(MCX_ERR_ARG, "grid of species %d not strictly increasing at point %lld", s,
+                            (long long)i);
+        }
+        emin = std::fmin(emin, energies[goff[s]]);
+        emax = std::fmax(emax, energies[goff[s + 1] - 1]);
+        if (!(awr[s] >= 1.0) || !is_finite(awr[s])) return fail(MCX_ERR_ARG, "awr[%d] must be >= 1", s);
+    }
+    for (int64_t i = 0; i < P * n_ch; ++i)
+        if (!(sigma[i] >= 0.0) || !is_finite(sigma[i]))
+            return fail(MCX_ERR_ARG, "sigma[%lld] must be finite and >= 0", (long long)i);
+    if (moff[0] != 0) return fail(MCX_ERR_ARG, "mat_offsets[0] must be 0");
+    int32_t maxs = 0;
+    for (int m = 0; m < n_materials; ++m) {
+        const int32_t c = moff[m + 1] - moff[m];
+        if (c < 1) return fail(MCX_ERR_ARG, "material %d has no species", m);
+        if (c > maxs) maxs = c;
+    }
+    const int64_t nnz = moff[n_materials];
+    for (int64_t i = 0; i < nnz; ++i) {
+        if (msp[i] < 0 || msp[i] >= n_species)
+            return fail(MCX_ERR_ARG, "mat_species[%lld] = %d out of range", (long long)i, msp[i]);
+        if (!(mden[i] >= 0.0) || !is_finite(mden[i]))
+            return fail(MCX_ERR_ARG, "mat_dens[%lld] must be finite and >= 0", (long long)i);
+    }
+    if (p->desc.geometry != MCX_GEOM_NONE) {
+        for (size_t r = 0; r < p->region_material.size(); ++r)
+            if (p->region_material[r] >= n_materials)
+                return fail(MCX_ERR_ARG, "region_material[%zu] = %d >= n_materials", r, p->region_material[r]);
+        if ((p->desc.flags & MCX_FLAG_DERIVATIVES) && n_materials > MCX_MAX_DMAT)
+            return fail(MCX_ERR_ARG, "derivative tallies support at most %d materials", MCX_MAX_DMAT);
+    }
+    DeviceGuard dg(p->device);
+    if (p->stream) CUDA_TRY(cudaStreamSynchronize(p->stream));
+    TableStore* ts = new (std::nothrow) TableStore();
+    if (!ts) return fail(MCX_ERR_OOM, "host allocation failed");
+    ts->device = p->device;
+    auto bail = [&](int code) {
+        delete ts;
+        return code;
+    };
+    int rc;
+    std::vector<float> d32((size_t)nnz);
+    for (int64_t i = 0; i < nnz; ++i) d32[i] = (float)mden[i];
+    if ((rc = dev_alloc(&ts->goff, (size_t)n_species + 1)) || (rc = dev_alloc(&ts->E, (size_t)P)) ||
+        (rc = dev_alloc(&ts->awr, (size_t)n_species)) || (rc = dev_alloc(&ts->moff, (size_t)n_materials + 1)) ||
+        (rc = dev_alloc(&ts->msp, (size_t)nnz)) || (rc = dev_alloc(&ts->mden, (size_t)nnz)) ||
+        (rc = dev_alloc(&ts->mden32, (size_t)nnz)))
+        return bail(rc);
+    const size_t sig_bytes = (size_t)P * n_ch * (precision == MCX_FP32 ? 4 : 8);
+    if (cudaMalloc(&ts->sigma, sig_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(MCX_ERR_OOM, "sigma table of %zu bytes", sig_bytes));
+    }
+    bool ok = cudaMemcpy(ts->goff, goff, 8 * (n_species + 1), cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaMemcpy(ts->E, energies, 8 * P, cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaMemcpy(ts->awr, awr, 8 * n_species, cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaMemcpy(ts->moff, moff, 4 * (n_materials + 1), cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaMemcpy(ts->msp, msp, 4 * nnz, cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaMemcpy(ts->mden, mden, 8 * nnz, cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaMemcpy(ts->mden32, d32.data(), 4 * nnz, cudaMemcpyHostToDevice) == cudaSuccess;
+    if (ok) {
+        if (precision == MCX_FP32) {
+            std::vector<float> s32((size_t)P * n_ch);
+            for (size_t i = 0; i < s32.size(); ++i) s32[i] = (float)sigma[i];
+            ok = cudaMemcpy(ts->sigma, s32.data(), sig_bytes, cudaMemcpyHostToDevice) == cudaSuccess;
+        } else {
+            ok = cudaMemcpy(ts->sigma, sigma, sig_bytes, cudaMemcpyHostToDevice) == cudaSuccess;
+        }
+    }
+    if (!ok) return bail(fail(MCX_ERR_CUDA, "uploading tables failed"));
+    Tables& v = ts->view;
+    v.n_species = n_species;
+    v.n_ch = n_ch;
+    v.precision = precision;
+    v.n_materials = n_materials;
+    v.max_mat_species = maxs;
+    v.ch_scatter = n_ch == 5 ? 1 : 0;
+    v.ch_absorb = n_ch == 5 ? 2 : 1;
+    v.n_points = P;
+    v.goff = ts->goff;
+    v.E = ts->E;
+    v.sigma = ts->sigma;
+    v.awr = ts->awr;
+    v.moff = ts->moff;
+    v.msp = ts->msp;
+    v.mden = ts->mden;
+    ts->emin = emin;
+    ts->emax = emax;
+    ts->nnz = nnz;
+    ts->h_moff.assign(moff, moff + n_materials + 1);
+    if ((rc = build_hash(ts, hash_bins, p->sm_count)) != MCX_OK) return bail(rc);
+    drop_graph(p);
+    release_tables(p);
+    p->tables = ts;
+    if (p->desc.geometry != MCX_GEOM_NONE)
+        TRY(alloc_derivative_tallies(p, (p->desc.flags & MCX_FLAG_DERIVATIVES) ? n_materials : 0));
+    return MCX_OK;
+}
+
+int mcx_share_xs_tables(mcx_problem* dst, const mcx_problem* src)
+{
+    g_err.clear();
+    TRY(check_handle(dst));
+    TRY(check_tables(src));
+    if (dst->device != src->device) return fail(MCX_ERR_ARG, "problems live on different devices");
+    TableStore* ts = src->tables;
+    if (dst->desc.geometry != MCX_GEOM_NONE) {
+        for (size_t r = 0; r < dst->region_material.size(); ++r)
+            if (dst->region_material[r] >= ts->view.n_materials)
+                return fail(MCX_ERR_ARG, "region_material[%zu] out of range of the shared materials", r);
+        if ((dst->desc.flags & MCX_FLAG_DERIVATIVES) && ts->view.n_materials > MCX_MAX_DMAT)
+            return fail(MCX_ERR_ARG, "derivative tallies support at most %d materials", MCX_MAX_DMAT);
+    }
+    DeviceGuard dg(dst->device);
+    if (dst == src) return MCX_OK;
+    ts->refs += 1;
+    drop_graph(dst);
+    release_tables(dst);
+    dst->tables = ts;
+    if (dst->desc.geometry != MCX_GEOM_NONE)
+        TRY(alloc_derivative_tallies(dst, (dst->desc.flags & MCX_FLAG_DERIVATIVES) ? ts->view.n_materials : 0));
+    return MCX_OK;
+}
+
+int mcx_set_hash_bins(mcx_problem* p, int32_t hash_bins)
+{
+    g_err.clear();
+    TRY(check_tables(p));
+    if (hash_bins < 0 || hash_bins > 10000000) return fail(MCX_ERR_ARG, "hash_bins out of range");
+    DeviceGuard dg(p->device);
+    CUDA_TRY(cudaDeviceSynchronize());
+    drop_graph(p);
+    return build_hash(p->tables, hash_bins, p->sm_count);
+}
+
+int mcx_set_densities(mcx_problem* p, const double* mden, int64_t nnz)
+{
+    g_err.clear();
+    TRY(check_tables(p));
+    TableStore* ts = p->tables;
+    if (!mden || nnz != ts->nnz) return fail(MCX_ERR_ARG, "expected %lld densities", (long long)ts->nnz);
+    for (int64_t i = 0; i < nnz; ++i)
+        if (!(mden[i] >= 0.0) || !is_finite(mden[i])) return fail(MCX_ERR_ARG, "mat_dens[%lld] invalid", (long long)i);
+    DeviceGuard dg(p->device);
+    CUDA_TRY(cudaDeviceSynchronize());
+    std::vector<float> d32((size_t)nnz);
+    for (int64_t i = 0; i < nnz; ++i) d32[i] = (float)mden[i];
+    CUDA_TRY(cudaMemcpy(ts->mden, mden, 8 * nnz, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(ts->mden32, d32.data(), 4 * nnz, cudaMemcpyHostToDevice));
+    return MCX_OK;
+}
+
+int mcx_set_tuning(mcx_problem* p, const mcx_tune* t)
+{
+    g_err.clear();
+    TRY(check_handle(p));
+    if (!t) return fail(MCX_ERR_ARG, "tuning is NULL");
+    if (t->mode != MCX_QUEUELESS && t->mode != MCX_QUEUED) return fail(MCX_ERR_ARG, "unknown mode");
+    if (t->block_size < 32 || t->block_size > 1024 || t->block_size % 32)
+        return fail(MCX_ERR_ARG, "block_size must be a multiple of 32 in 32..1024");
+    if (t->sort_period < 0) return fail(MCX_ERR_ARG, "sort_period must be >= 0");
+    if (t->sort_threshold < 0) return fail(MCX_ERR_ARG, "sort_threshold must be >= 0");
+    if (t->iters_per_sync < 1 || t->iters_per_sync > 4096) return fail(MCX_ERR_ARG, "iters_per_sync out of range");
+    if (t->max_event_iters < 0) return fail(MCX_ERR_ARG, "max_event_iters must be >= 0");
+    p->tune = *t;
+    p->tune.use_graph = t->use_graph ? 1 : 0;
+    return MCX_OK;
+}
+
+int mcx_run_batch(mcx_problem* p, int64_t first, int64_t n, int64_t pif, uint64_t seed, void* stream)
+{
+    g_err.clear();
+    TRY(check_tables(p));
+    if (p->desc.geometry == MCX_GEOM_NONE) return fail(MCX_ERR_STATE, "problem has no geometry");
+    if (first < 0 || n < 0 || first + n > p->desc.n_histories)
+        return fail(MCX_ERR_ARG, "histories [%lld, %lld) outside [0, %lld)", (long long)first,
+                    (long long)(first + n), (long long)p->desc.n_histories);
+    DeviceGuard dg(p->device);
+    if (n == 0) return MCX_OK;
+    mcx_problem* probs[1] = {p};
+    return run_loop(p, 1, probs, &first, &n, pif, seed, stream);
+}
+
+int mcx_batch_run(int32_t n_problems, mcx_problem* const* problems, const int64_t* n_hist, int64_t pif,
+                  uint64_t seed, void* stream)
+{
+    g_err.clear();
+    if (n_problems < 1 || !problems || !n_hist) return fail(MCX_ERR_ARG, "empty problem list");
+    TRY(check_tables(problems[0]));
+    for (int i = 0; i < n_problems; ++i) {
+        TRY(check_handle(problems[i]));
+        if (problems[i]->tables != problems[0]->tables)
+            return fail(MCX_ERR_ARG, "problem %d does not share problem 0's tables", i);
+        if (problems[i]->device != problems[0]->device) return fail(MCX_ERR_ARG, "problem %d on another device", i);
+        if (problems[i]->desc.geometry == MCX_GEOM_NONE) return fail(MCX_ERR_ARG, "problem %d has no geometry", i);
+        if (problems[i]->M > 0 && n_problems > 1)
+            return fail(MCX_ERR_ARG, "problem %d has derivative tallies (single-problem runs only)", i);
+        if (n_hist[i] < 0 || n_hist[i] > problems[i]->desc.n_histories)
+            return fail(MCX_ERR_ARG, "n_hist[%d] outside [0, n_histories]", i);
+        for (int j = 0; j < i; ++j)
+            if (problems[j] == problems[i]) return fail(MCX_ERR_ARG, "problem %d listed twice", i);
+    }
+    DeviceGuard dg(problems[0]->device);
+    std::vector<int64_t> first((size_t)n_problems, 0);
+    long long total = 0;
+    for (int i = 0; i < n_problems; ++i) total += n_hist[i];
+    if (total == 0) return MCX_OK;
+    return run_loop(problems[0], n_problems, problems, first.data(), n_hist, pif, seed, stream);
+}
+
+int mcx_tally_size(const mcx_problem* p, int32_t which, int64_t* n)
+{
+    g_err.clear();
+    TRY(check_handle(p));
+    if (!n) return fail(MCX_ERR_ARG, "n is NULL");
+    const int64_t B = p->desc.n_batches;
+    switch (which) {
+    case MCX_TALLY_FLUX:
+    case MCX_TALLY_ABSORB: *n = B * p->nb; break;
+    case MCX_TALLY_OUTCOME: *n = B * N_OUT; break;
+    case MCX_TALLY_DFLUX:
+    case MCX_TALLY_DABSORB: *n = B * p->nb * p->M; break;
+    case MCX_TALLY_DOUTCOME: *n = B * N_OUT * p->M; break;
+    default: return fail(MCX_ERR_ARG, "unknown tally %d", which);
+    }
+    if (p->desc.geometry == MCX_GEOM_NONE) *n = 0;
+    return MCX_OK;
+}
+
+int mcx_read_tallies(mcx_problem* p, int32_t which, double* host_out, int64_t n)
+{
+    g_err.clear();
+    int64_t size = 0;
+    TRY(mcx_tally_size(p, which, &size));
+    if (n != size) return fail(MCX_ERR_ARG, "tally %d has %lld entries, not %lld", which, (long long)size, (long long)n);
+    if (n == 0) return MCX_OK;
+    if (!host_out) return fail(MCX_ERR_ARG, "host_out is NULL");
+    const double* src = which == MCX_TALLY_FLUX ? p->flux
+                        : which == MCX_TALLY_ABSORB ? p->absorb
+                        : which == MCX_TALLY_OUTCOME ? p->outcome
+                        : which == MCX_TALLY_DFLUX ? p->dflux
+                        : which == MCX_TALLY_DABSORB ? p->dabsorb
+                                                     : p->doutcome;
+    DeviceGuard dg(p->device);
+    CUDA_TRY(cudaStreamSynchronize(p->stream));
+    CUDA_TRY(cudaMemcpy(host_out, src, sizeof(double) * n, cudaMemcpyDeviceToHost));
+    return MCX_OK;
+}
+
+int mcx_zero_tallies(mcx_problem* p)
+{
+    g_err.clear();
+    TRY(check_handle(p));
+    if (p->desc.geometry == MCX_GEOM_NONE) return MCX_OK;
+    DeviceGuard dg(p->device);
+    CUDA_TRY(cudaStreamSynchronize(p->stream));
+    const int64_t B = p->desc.n_batches;
+    CUDA_TRY(cudaMemset(p->flux, 0, sizeof(double) * B * p->nb));
+    CUDA_TRY(cudaMemset(p->absorb, 0, sizeof(double) * B * p->nb));
+    CUDA_TRY(cudaMemset(p->outcome, 0, sizeof(double) * B * N_OUT));
+    if (p->M > 0) {
+        CUDA_TRY(cudaMemset(p->dflux, 0, sizeof(double) * B * p->nb * p->M));
+        CUDA_TRY(cudaMemset(p->dabsorb, 0, sizeof(double) * B * p->nb * p->M));
+        CUDA_TRY(cudaMemset(p->doutcome, 0, sizeof(double) * B * N_OUT * p->M));
+    }
+    return MCX_OK;
+}
+
+int mcx_read_history_debug(mcx_problem* p, uint32_t* ncoll, int64_t n)
+{
+    g_err.clear();
+    TRY(check_handle(p));
+    if (!(p->desc.flags & MCX_FLAG_HISTORY_DEBUG)) return fail(MCX_ERR_STATE, "problem was created without MCX_FLAG_HISTORY_DEBUG");
+    if (n < 0 || n > p->debug_n) return fail(MCX_ERR_ARG, "last run had %lld histories", (long long)p->debug_n);
+    if (n == 0) return MCX_OK;
+    if (!ncoll) return fail(MCX_ERR_ARG, "ncoll is NULL");
+    DeviceGuard dg(p->device);
+    CUDA_TRY(cudaStreamSynchronize(p->stream));
+    CUDA_TRY(cudaMemcpy(ncoll, p->ncoll_debug, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost));
+    return MCX_OK;
+}
+
+int mcx_last_run_stats(const mcx_problem* p, int64_t* out, int32_t n)
+{
+    g_err.clear();
+    TRY(check_handle(p));
+    if (!out || n < 3) return fail(MCX_ERR_ARG, "need room for 3 values");
+    for (int i = 0; i < 3; ++i) out[i] = p->stats[i];
+    return MCX_OK;
+}
+
+int mcx_xs_lookup(mcx_problem* p, int64_t n, const double* E, const int32_t* mat, double* out,
+                  int32_t flags, void* stream)
+{
+    g_err.clear();
+    TRY(check_tables(p));
+    if (n < 0) return fail(MCX_ERR_ARG, "n must be >= 0");
+    if (n >= ((int64_t)1 << 31)) return fail(MCX_ERR_ARG, "n must be < 2^31");
+    if (flags & ~(MCX_LOOKUP_FAST | MCX_LOOKUP_SORT)) return fail(MCX_ERR_ARG, "unknown lookup flags");
+    if (n == 0) return MCX_OK;
+    if (!E || !mat || !out) return fail(MCX_ERR_ARG, "NULL buffer");
+    DeviceGuard dg(p->device);
+    return lookup_device(p, n, E, mat, out, flags, (cudaStream_t)stream);
+}
+
+int mcx_xs_lookup_host(mcx_problem* p, int64_t n, const double* E_host, const int32_t* mat_host,
+                       double* out_host, int32_t flags)
+{
+    g_err.clear();
+    TRY(check_tables(p));
+    if (n < 0 || n >= ((int64_t)1 << 31)) return fail(MCX_ERR_ARG, "n out of range");
+    if (flags & ~(MCX_LOOKUP_FAST | MCX_LOOKUP_SORT)) return fail(MCX_ERR_ARG, "unknown lookup flags");
+    if (n == 0) return MCX_OK;
+    if (!E_host || !mat_host || !out_host) return fail(MCX_ERR_ARG, "NULL buffer");
+    DeviceGuard dg(p->device);
+    const int nc = p->tables->view.n_ch;
+    const int64_t chunk = n < (int64_t)(8 << 20) ? n : (int64_t)(8 << 20);
+    // staging: per stream E [chunk], mat [chunk], out [chunk * nc] doubles
+    const int64_t per = chunk * (2 + nc);
+    if (p->h_buf_cap < 2 * per) {
+        dev_free(p->h_buf);
+        TRY(dev_alloc(&p->h_buf, (size_t)(2 * per)));
+        p->h_buf_cap = 2 * per;
+    }
+    cudaStream_t ss[2] = {p->stream, p->stream2};
+    for (int64_t off = 0, c = 0; off < n; off += chunk, ++c) {
+        const int64_t m = n - off < chunk ? n - off : chunk;
+        cudaStream_t st = ss[c & 1];
+        double* base = p->h_buf + (c & 1) * per;
+        double* dE = base;
+        int32_t* dM = (int32_t*)(base + chunk);
+        double* dO = base + 2 * chunk;
+        CUDA_TRY(cudaMemcpyAsync(dE, E_host + off, 8 * m, cudaMemcpyHostToDevice, st));
+        CUDA_TRY(cudaMemcpyAsync(dM, mat_host + off, 4 * m, cudaMemcpyHostToDevice, st));
+        TRY(lookup_device(p, m, dE, dM, dO, flags & ~MCX_LOOKUP_SORT, st));
+        CUDA_TRY(cudaMemcpyAsync(out_host + off * nc, dO, 8 * m * nc, cudaMemcpyDeviceToHost, st));
+    }
+    CUDA_TRY(cudaStreamSynchronize(ss[0]));
+    CUDA_TRY(cudaStreamSynchronize(ss[1]));
+    return MCX_OK;
+}
+
+int mcx_xs_indices(mcx_problem* p, int64_t n, const double* E, const int32_t* mat, int32_t max_species,
+                   int32_t* kout, void* stream)
+{
+    g_err.clear();
+    TRY(check_tables(p));
+    if (n < 0 || n >= ((int64_t)1 << 31)) return fail(MCX_ERR_ARG, "n out of range");
+    if (max_species < p->tables->view.max_mat_species)
+        return fail(MCX_ERR_ARG, "max_species must be >= %d", p->tables->view.max_mat_species);
+    if (n == 0) return MCX_OK;
+    if (!E || !mat || !kout) return fail(MCX_ERR_ARG, "NULL buffer");
+    DeviceGuard dg(p->device);
+    if (launch_xs_indices(p->tables->view, n, E, mat, max_species, kout, lookup_grid(p), (cudaStream_t)stream))
+        return fail(MCX_ERR_CUDA, "index kernel launch failed");
+    return MCX_OK;
+}
+
+int mcx_xs_lookup_backward(mcx_problem* p, int64_t n, const double* E, const int32_t* mat,
+                           const double* grad_out, double* grad_dens, double* grad_sigma, void* stream)
+{
+    g_err.clear();
+    TRY(check_tables(p));
+    if (n < 0 || n >= ((int64_t)1 << 31)) return fail(MCX_ERR_ARG, "n out of range");
+    if (n == 0) return MCX_OK;
+    if (!E || !mat || !grad_out || !grad_dens || !grad_sigma) return fail(MCX_ERR_ARG, "NULL buffer");
+    DeviceGuard dg(p->device);
+    if (launch_xs_backward(p->tables->view, n, E, mat, grad_out, grad_dens, grad_sigma, lookup_grid(p),
+                           (cudaStream_t)stream))
+        return fail(MCX_ERR_CUDA, "backward kernel launch failed");
+    return MCX_OK;
+}
+
+int mcx_debug_uniforms(uint64_t seed, uint32_t problem_id, uint64_t hist, uint32_t first, int64_t n,
+                       double* out, void* stream)
+{
+    g_err.clear();
+    if (n < 0) return fail(MCX_ERR_ARG, "n must be >= 0");
+    if (n == 0) return MCX_OK;
+    if (!out) return fail(MCX_ERR_ARG, "out is NULL");
+    if (launch_debug_uniforms(rng_key(seed, problem_id), hist, first, n, out, (cudaStream_t)stream))
+        return fail(MCX_ERR_CUDA, "uniforms kernel launch failed");
+    return MCX_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,159 @@
+// mcx_internal.cuh -- shared device-side definitions of libmcx (not part of
+// the public ABI).  Everything here is written for sm_103a.
+//
+// Translation units that include the EXACT arithmetic helpers below
+// (transport.cu, xs_exact.cu, adjoint.cu) are compiled with --fmad=false so
+// that every FP64 expression is evaluated as written: one IEEE operation per
+// operator, no fused multiply-add.  That is what makes grid indices, species
+// choices and collision counts reproducible bit for bit.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "mcx.h"
+
+namespace mcx {
+
+// ---------------------------------------------------------------------------
+// Cross-section tables as seen by the kernels.
+// Layout in HBM:
+//   goff  int64 [S+1]     species s owns points [goff[s], goff[s+1])
+//   E     f64   [P]       concatenated per-species energy grids
+//   sigma f32|f64 [P][n_ch]  interleaved channels: the two points k, k+1 of
+//                            one species are one contiguous 2*n_ch run
+//   hidx  int32 [S][H+1]  hash grid: hidx[s][b] = grid index k of bin
+//                         boundary b in species s (window of bin b is
+//                         [hidx[s][b], hidx[s][b+1]])
+//   hbound f64  [H+1]     bin boundaries, increasing, shared by all species
+//   moff/msp/mden         CSR materials (offsets, species ids, densities)
+// ---------------------------------------------------------------------------
+struct Tables {
+    int32_t n_species = 0;
+    int32_t n_ch = 0;
+    int32_t precision = MCX_FP64;
+    int32_t n_materials = 0;
+    int32_t max_mat_species = 0;
+    int32_t ch_scatter = 0, ch_absorb = 1;
+    int64_t n_points = 0;
+    const int64_t* goff = nullptr;
+    const double* E = nullptr;
+    const void* sigma = nullptr;
+    const double* awr = nullptr;
+    const int32_t* moff = nullptr;
+    const int32_t* msp = nullptr;
+    const double* mden = nullptr;
+    // hash grid (H == 0: none)
+    int32_t H = 0;
+    const int32_t* hidx = nullptr;
+    const double* hbound = nullptr;
+    float hash_ln_lo = 0.f;    // ln of hbound[0]
+    float hash_scale = 0.f;    // H / (ln hbound[H] - ln hbound[0])
+};
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds of the
+// multiply-xor S-box with Weyl-sequence round keys.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
+{
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k.x += W0;
+            k.y += W1;
+        }
+        const uint32_t lo0 = M0 * c.x, hi0 = __umulhi(M0, c.x);
+        const uint32_t lo1 = M1 * c.z, hi1 = __umulhi(M1, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    }
+    return c;
+}
+
+// Uniform number `n` of a history's stream.  Block n/2 of the stream keyed by
+// (seed, problem) with counter (n/2, hist low word, hist high word, 0); even n
+// uses words 0,1, odd n words 2,3.  Two words a, b map to (k + 1/2) 2^-52,
+// k = (a >> 6) << 26 | (b >> 6): exact, strictly inside (0, 1).
+__device__ __forceinline__ double uniform_at(uint2 key, uint64_t hist, uint32_t n)
+{
+    const uint4 w = philox4x32_10(
+        make_uint4(n >> 1, (uint32_t)hist, (uint32_t)(hist >> 32), 0u), key);
+    const uint32_t a = (n & 1u) ? w.z : w.x;
+    const uint32_t b = (n & 1u) ? w.w : w.y;
+    const uint64_t k = ((uint64_t)(a >> 6) << 26) | (uint64_t)(b >> 6);
+    return __dmul_rn(__dadd_rn((double)k, 0.5), 0x1.0p-52);
+}
+
+__host__ __device__ __forceinline__ uint2 rng_key(uint64_t seed, uint32_t problem_id)
+{
+    return make_uint2((uint32_t)seed, (uint32_t)(seed >> 32) ^ problem_id);
+}
+
+// ---------------------------------------------------------------------------
+// Grid search.  Energies are positive finite doubles, so their IEEE bit
+// patterns, read as signed 64-bit integers, order exactly as the values do;
+// comparing the integers runs on the integer pipes instead of B300's narrow
+// FP64 pipe and gives the same decisions.  A negative or zero E orders below
+// every grid point; NaN is mapped to k = 0 by the callers.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int64_t ebits(double x) { return __double_as_longlong(x); }
+
+// Largest k in [lo, hi] with g[k] <= E (lo if none).  Requires the answer of
+// the full search to lie in [lo, hi].
+__device__ __forceinline__ int64_t bsearch_window(const double* __restrict__ g, int64_t lo,
+                                                  int64_t hi, int64_t eb)
+{
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (ebits(__ldg(g + mid)) <= eb) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Hash bin of E: the b with hbound[b] <= E < hbound[b+1] (clamped to
+// [0, H-1]).  The float logarithm only proposes a bin; two comparisons with
+// the stored FP64 boundaries fix it, so the bin is exact whatever the
+// rounding of logf.
+__device__ __forceinline__ int32_t hash_bin(const Tables& t, double E)
+{
+    const float lf = logf((float)E);
+    float fb = (lf - t.hash_ln_lo) * t.hash_scale;
+    int32_t b;
+    if (!(fb >= 0.f)) b = 0;                       // also NaN, -inf, tiny E
+    else if (fb >= (float)(t.H - 1)) b = t.H - 1;
+    else b = (int32_t)fb;
+    const int64_t eb = ebits(E);
+    // at most a couple of steps: the float estimate is within a bin or two
+    while (b > 0 && eb < ebits(__ldg(t.hbound + b))) --b;
+    while (b < t.H - 1 && eb >= ebits(__ldg(t.hbound + b + 1))) ++b;
+    return b;
+}
+
+// Grid index of species s at E: the largest k in [0, n-2] with g[k] <= E,
+// k = 0 below the grid or for NaN, n-2 at or above its top.
+__device__ __forceinline__ int64_t species_index(const Tables& t, int32_t s, double E,
+                                                 int64_t eb, int32_t hbin)
+{
+    const int64_t base = __ldg(t.goff + s);
+    const int64_t n = __ldg(t.goff + s + 1) - base;
+    int64_t lo = 0, hi = n - 2;
+    if (t.H > 0) {
+        const int32_t* h = t.hidx + (int64_t)s * (t.H + 1) + hbin;
+        lo = __ldg(h);
+        hi = __ldg(h + 1);
+    }
+    int64_t k = bsearch_window(t.E + base, lo, hi, eb);
+    if (E != E) k = 0;
+    return k;
+}
+
+template <typename T>
+__device__ __forceinline__ double sig_at(const void* sigma, int64_t i)
+{
+    return (double)__ldg(static_cast<const T*>(sigma) + i);
+}
+
+}  // namespace mcx

@@ -1,0 +1,865 @@
+// transport.cu -- event-based fixed-source transport kernels (compiled with
+// --fmad=false: every FP64 expression below is evaluated as written, which
+// keeps per-history decisions identical to a sequential FP64 evaluation).
+//
+// Event-based mode (Sec. 4.1 of the paper): a buffer of particles in flight is
+// advanced one event at a time, one kernel per event type over all particles
+// that need it; dead slots are refilled from the remaining histories after
+// every iteration.  One iteration here is
+//     refill -> [bin XS queue] -> lookup -> advance (flight, tally, surface
+//     crossing) -> [bin collision queue] -> collide -> bookkeeping
+// In queueless mode each kernel visits every slot and returns early for
+// particles that do not need its event; in queued mode the kernels visit
+// device-built index queues (warp-ballot compaction) and never read a slot
+// they do not need.  Queue sizes stay on the device: no host round trip per
+// kernel.  Tally scores are reduced within each warp (lanes that hit the same
+// tally cell are found with __match_any_sync and summed with shuffles) and a
+// single FP64 atomicAdd per distinct cell is issued.
+#include "kernels.h"
+#include "xs_exact.cuh"
+
+namespace mcx {
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr double INF = __builtin_huge_val();
+
+enum { S_NONE = 0, S_ZTOP, S_ZBOT, S_CYL, S_XLO, S_XHI, S_YLO, S_YHI };
+constexpr int MAX_AZIMUTH_TRIES = 64;
+
+__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+__device__ __forceinline__ unsigned lanes_below() { return (1u << lane_id()) - 1u; }
+
+// Warp-aggregated append: every lane of the (converged) warp calls it; each
+// lane with `want` receives a distinct slot of the queue behind `counter`.
+__device__ __forceinline__ int warp_append(int* counter, bool want)
+{
+    const unsigned b = __ballot_sync(FULL, want);
+    if (b == 0u) return -1;
+    const int leader = __ffs(b) - 1;
+    int base = 0;
+    if (lane_id() == leader) base = atomicAdd(counter, __popc(b));
+    base = __shfl_sync(FULL, base, leader);
+    return want ? base + __popc(b & lanes_below()) : -1;
+}
+
+// Azimuth (cos phi, sin phi) by rejection on pairs (2u-1, 2u-1) inside the
+// unit disc.
+__device__ __forceinline__ void azimuth(uint2 key, uint64_t h, uint32_t& n, double& c, double& s)
+{
+    for (int t = 0; t < MAX_AZIMUTH_TRIES; ++t) {
+        const double a = 2.0 * uniform_at(key, h, n) - 1.0;
+        const double b = 2.0 * uniform_at(key, h, n + 1) - 1.0;
+        n += 2;
+        const double rho = a * a + b * b;
+        if (rho > 0.0 && rho <= 1.0) {
+            c = (a * a - b * b) / rho;
+            s = 2.0 * a * b / rho;
+            return;
+        }
+    }
+    c = 1.0;
+    s = 0.0;
+}
+
+struct State {
+    double x, y, z, u, v, w;
+    int32_t ci, cj, inpin;
+};
+
+// Distance to the nearest surface along the flight.  Candidates are compared
+// in a fixed order with strict '<' (earlier candidates win ties).
+__device__ double surface_distance(const ProblemDev& pd, const State& q, int& surf)
+{
+    double d = INF;
+    surf = S_NONE;
+    if (pd.geometry == MCX_GEOM_INFINITE) return d;
+    if (pd.geometry == MCX_GEOM_SLAB) {
+        if (q.u > 0.0) {
+            d = (pd.slab_length - q.x) / q.u;
+            surf = S_XHI;
+        } else if (q.u < 0.0) {
+            d = (0.0 - q.x) / q.u;
+            surf = S_XLO;
+        }
+        if (d < 0.0) d = 0.0;
+        return d;
+    }
+    if (q.w > 0.0) {
+        d = (pd.height - q.z) / q.w;
+        surf = S_ZTOP;
+    } else if (q.w < 0.0) {
+        d = (0.0 - q.z) / q.w;
+        surf = S_ZBOT;
+    }
+    const double half = pd.half;
+    const double cx = -half + pd.pitch * ((double)q.ci + 0.5);
+    const double cy = -half + pd.pitch * ((double)q.cj + 0.5);
+    const double dx = q.x - cx, dy = q.y - cy;
+    const double a = q.u * q.u + q.v * q.v;
+    const double k = dx * q.u + dy * q.v;
+    const double c = dx * dx + dy * dy - pd.radius * pd.radius;
+    double dc = INF;
+    if (q.inpin) {
+        if (a > 0.0) {
+            double disc = k * k - a * c;
+            if (disc < 0.0) disc = 0.0;
+            dc = (-k + sqrt(disc)) / a;
+        }
+    } else if (a > 0.0 && k < 0.0) {
+        const double disc = k * k - a * c;
+        if (disc >= 0.0) dc = (-k - sqrt(disc)) / a;
+    }
+    if (dc < d) {
+        d = dc;
+        surf = S_CYL;
+    }
+    if (!q.inpin) {
+        const double xl = -half + pd.pitch * (double)q.ci;
+        const double xh = -half + pd.pitch * (double)(q.ci + 1);
+        const double yl = -half + pd.pitch * (double)q.cj;
+        const double yh = -half + pd.pitch * (double)(q.cj + 1);
+        if (q.u > 0.0) {
+            const double t = (xh - q.x) / q.u;
+            if (t < d) { d = t; surf = S_XHI; }
+        } else if (q.u < 0.0) {
+            const double t = (xl - q.x) / q.u;
+            if (t < d) { d = t; surf = S_XLO; }
+        }
+        if (q.v > 0.0) {
+            const double t = (yh - q.y) / q.v;
+            if (t < d) { d = t; surf = S_YHI; }
+        } else if (q.v < 0.0) {
+            const double t = (yl - q.y) / q.v;
+            if (t < d) { d = t; surf = S_YLO; }
+        }
+    }
+    if (d < 0.0) d = 0.0;
+    return d;
+}
+
+// Logical crossing; returns the outcome if the particle leaves, else -1.
+__device__ __forceinline__ int cross_surface(const ProblemDev& pd, State& q, int surf)
+{
+    const int32_t n = pd.lattice_n;
+    switch (surf) {
+    case S_ZTOP:
+    case S_ZBOT:
+        q.w = -q.w;
+        return -1;
+    case S_CYL:
+        q.inpin = !q.inpin;
+        return -1;
+    case S_XHI:
+        if (pd.geometry == MCX_GEOM_SLAB || q.ci == n - 1) return OUT_LEAK_XHI;
+        q.ci += 1;
+        return -1;
+    case S_XLO:
+        if (pd.geometry == MCX_GEOM_SLAB || q.ci == 0) return OUT_LEAK_OTHER;
+        q.ci -= 1;
+        return -1;
+    case S_YHI:
+        if (q.cj == n - 1) return OUT_LEAK_OTHER;
+        q.cj += 1;
+        return -1;
+    case S_YLO:
+        if (q.cj == 0) return OUT_LEAK_OTHER;
+        q.cj -= 1;
+        return -1;
+    default:
+        return OUT_LEAK_OTHER;
+    }
+}
+
+__device__ __forceinline__ int32_t region_of(const ProblemDev& pd, const State& q)
+{
+    if (pd.geometry != MCX_GEOM_LATTICE) return 0;
+    return q.inpin ? q.ci * pd.lattice_n + q.cj : pd.lattice_n * pd.lattice_n;
+}
+
+__device__ __forceinline__ void rotate(double& u, double& v, double& w, double mu, double c, double s)
+{
+    const double u0 = u, v0 = v, w0 = w;
+    const double a = sqrt(1.0 - mu * mu);
+    if (fabs(w0) < 0.9999) {
+        const double b = sqrt(1.0 - w0 * w0);
+        u = mu * u0 + a * (u0 * w0 * c - v0 * s) / b;
+        v = mu * v0 + a * (v0 * w0 * c + u0 * s) / b;
+        w = mu * w0 - a * b * c;
+    } else {
+        const double b = sqrt(1.0 - v0 * v0);
+        u = mu * u0 + a * (u0 * v0 * c + w0 * s) / b;
+        v = mu * v0 - a * b * c;
+        w = mu * w0 + a * (v0 * w0 * c - u0 * s) / b;
+    }
+}
+
+__device__ __forceinline__ int64_t batch_of(const ProblemDev& pd, int64_t h)
+{
+    return (h * (int64_t)pd.n_batches) / pd.n_hist_total;
+}
+
+// Map a work item to (problem, history).
+__device__ __forceinline__ int problem_of_work(const int64_t* work_off, int n_prob, long long wk)
+{
+    int lo = 0, hi = n_prob - 1;  // largest p with work_off[p] <= wk
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (work_off[mid] <= wk) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Source particle of history h (lattice: centre of a uniformly chosen pin at
+// mid-height; infinite medium: origin; both isotropic; slab: pencil along +x).
+__device__ void init_particle(const Particles& P, int64_t slot, const ProblemDev& pd,
+                              int32_t pidx, int64_t h, int M)
+{
+    const uint2 key = pd.key;
+    uint32_t n = 0;
+    State q = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0, 0, 0};
+    if (pd.geometry == MCX_GEOM_SLAB) {
+        q.u = 1.0;
+    } else {
+        if (pd.geometry == MCX_GEOM_LATTICE) {
+            const int32_t ln = pd.lattice_n;
+            const int64_t n2 = (int64_t)ln * ln;
+            int64_t pin = (int64_t)(uniform_at(key, h, n) * (double)n2);
+            n += 1;
+            if (pin >= n2) pin = n2 - 1;
+            q.ci = (int32_t)(pin / ln);
+            q.cj = (int32_t)(pin % ln);
+            q.x = -pd.half + pd.pitch * ((double)q.ci + 0.5);
+            q.y = -pd.half + pd.pitch * ((double)q.cj + 0.5);
+            q.z = 0.5 * pd.height;
+            q.inpin = 1;
+        }
+        const double mu = 2.0 * uniform_at(key, h, n) - 1.0;
+        n += 1;
+        double c, s;
+        azimuth(key, h, n, c, s);
+        const double st = sqrt(1.0 - mu * mu);
+        q.u = st * c;
+        q.v = st * s;
+        q.w = mu;
+    }
+    P.x[slot] = q.x; P.y[slot] = q.y; P.z[slot] = q.z;
+    P.u[slot] = q.u; P.v[slot] = q.v; P.w[slot] = q.w;
+    P.E[slot] = pd.E0;
+    P.hist[slot] = h;
+    P.rng_n[slot] = n;
+    P.ncoll[slot] = 0u;
+    P.cell[slot] = q.ci * (pd.lattice_n > 0 ? pd.lattice_n : 1) + q.cj;
+    P.mat[slot] = __ldg(pd.region_material + region_of(pd, q));
+    P.prob[slot] = pidx;
+    P.flags[slot] = (uint8_t)(PF_ALIVE | PF_NEED_XS | (q.inpin ? PF_INPIN : 0));
+    for (int mm = 0; mm < M; ++mm) P.W[(int64_t)mm * P.cap + slot] = 0.0;
+}
+
+__device__ __forceinline__ State load_state(const Particles& P, int64_t slot, int32_t ln)
+{
+    State q;
+    q.x = P.x[slot]; q.y = P.y[slot]; q.z = P.z[slot];
+    q.u = P.u[slot]; q.v = P.v[slot]; q.w = P.w[slot];
+    const int32_t cell = P.cell[slot];
+    const int32_t n = ln > 0 ? ln : 1;
+    q.ci = cell / n;
+    q.cj = cell % n;
+    q.inpin = (P.flags[slot] & PF_INPIN) ? 1 : 0;
+    return q;
+}
+
+// Deaths of this warp: outcome tallies (one atomic per distinct tally cell),
+// derivative outcome tallies, per-history debug counts, slot release, alive
+// count and (queued) the dead queue.  Every lane of the warp calls it.
+__device__ void finish_deaths(bool dies, int outcome, int64_t slot, int32_t pidx,
+                              const ProblemDev* probs, const Particles& P, RunCtl* ctl, int M,
+                              bool queued, int par)
+{
+    const unsigned dm = __ballot_sync(FULL, dies);
+    if (dm == 0u) return;
+    if (dies) {
+        const ProblemDev& pd = probs[pidx];
+        const int64_t h = P.hist[slot];
+        const int64_t b = batch_of(pd, h);
+        double* a = pd.outcome + b * N_OUT + outcome;
+        const unsigned grp = __match_any_sync(dm, (unsigned long long)a);
+        const int leader = __ffs(grp) - 1;
+        if (lane_id() == leader) atomicAdd(a, (double)__popc(grp));
+        for (int mm = 0; mm < M; ++mm) {
+            const double wv = P.W[(int64_t)mm * P.cap + slot];
+            double sum = 0.0;
+            for (unsigned g = grp; g; g &= g - 1u) sum += __shfl_sync(grp, wv, __ffs(g) - 1);
+            if (lane_id() == leader)
+                atomicAdd(pd.doutcome + (b * N_OUT + outcome) * M + mm, sum);
+        }
+        if (pd.ncoll_debug) pd.ncoll_debug[h - pd.first] = P.ncoll[slot];
+        P.flags[slot] = 0;
+    }
+    if (lane_id() == 0) atomicSub(&ctl->n_alive, __popc(dm));
+    if (queued) {
+        const int pos = warp_append(&ctl->n_dead[par ^ 1], dies);
+        if (dies) P.q_dead[par ^ 1][pos] = (int32_t)slot;
+    }
+}
+
+// ------------------------------------------------------------------ kernels
+
+__global__ void k_run_init(Particles P, RunCtl* ctl, long long total, int n_prob,
+                           long long max_iters, int queued)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P.cap; i += stride) {
+        P.flags[i] = 0;
+        if (queued) P.q_dead[0][i] = (int32_t)i;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ctl->next = 0ull;
+        ctl->total = total;
+        ctl->iters = 0;
+        ctl->max_iters = max_iters;
+        ctl->n_prob = n_prob;
+        ctl->n_alive = 0;
+        ctl->done = total > 0 ? 0 : 1;
+        ctl->error = 0;
+        ctl->parity = 0;
+        for (int k = 0; k < 2; ++k) {
+            ctl->n_xs[k] = 0;
+            ctl->n_adv[k] = 0;
+            ctl->n_dead[k] = 0;
+        }
+        ctl->n_dead[0] = queued ? (int)P.cap : 0;
+        ctl->n_coll = 0;
+        ctl->sorted = 0;
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_refill(LoopConfig c, Particles P, const ProblemDev* probs,
+                                                 const int64_t* work_off, RunCtl* ctl)
+{
+    if (ctl->error || ctl->done) return;
+    const bool queued = c.mode == MCX_QUEUED;
+    const int par = ctl->parity;
+    const long long total = ctl->total;
+    const int n_prob = ctl->n_prob;
+    const int64_t count = queued ? (int64_t)ctl->n_dead[par] : P.cap;
+    if ((long long)ctl->next >= total && queued) {
+        // nothing left to start: retire the dead slots
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+             i += (int64_t)gridDim.x * blockDim.x)
+            P.flags[P.q_dead[par][i]] = PF_RETIRED;
+        return;
+    }
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int added = 0;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < count; base += stride) {
+        const int64_t i = base + threadIdx.x;
+        int64_t slot = -1;
+        bool want = false;
+        if (i < count) {
+            if (queued) {
+                slot = P.q_dead[par][i];
+                want = true;
+            } else {
+                slot = i;
+                want = (P.flags[slot] & (PF_ALIVE | PF_RETIRED)) == 0;
+            }
+        }
+        const unsigned b = __ballot_sync(FULL, want);
+        if (b == 0u) continue;
+        const int leader = __ffs(b) - 1;
+        unsigned long long wbase = 0ull;
+        if (lane_id() == leader) wbase = atomicAdd(&ctl->next, (unsigned long long)__popc(b));
+        wbase = __shfl_sync(FULL, wbase, leader);
+        bool got = false;
+        if (want) {
+            const long long wk = (long long)(wbase + __popc(b & lanes_below()));
+            if (wk < total) {
+                const int p = problem_of_work(work_off, n_prob, wk);
+                const ProblemDev& pd = probs[p];
+                init_particle(P, slot, pd, p, pd.first + (wk - work_off[p]), c.derivatives ? pd.M : 0);
+                got = true;
+            } else {
+                P.flags[slot] = PF_RETIRED;
+            }
+        }
+        if (queued) {
+            int pos = warp_append(&ctl->n_xs[par], got);
+            if (got) P.q_xs[par][pos] = (int32_t)slot;
+            pos = warp_append(&ctl->n_adv[par], got);
+            if (got) P.q_adv[par][pos] = (int32_t)slot;
+        }
+        const unsigned gm = __ballot_sync(FULL, got);
+        if (lane_id() == 0) added += __popc(gm);
+    }
+    if (lane_id() == 0 && added) atomicAdd(&ctl->n_alive, added);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_lookup(LoopConfig c, Tables t, Particles P, RunCtl* ctl)
+{
+    if (ctl->error) return;
+    const bool queued = c.mode == MCX_QUEUED;
+    const int par = ctl->parity;
+    const int64_t count = queued ? (int64_t)ctl->n_xs[par] : P.cap;
+    const int32_t* list = queued ? (ctl->sorted ? P.q_sorted : P.q_xs[par]) : nullptr;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t slot = list ? list[i] : i;
+        const uint8_t f = P.flags[slot];
+        if (!(f & PF_NEED_XS)) continue;
+        double st, sa;
+        macro_transport<T>(t, P.mat[slot], P.E[slot], st, sa);
+        P.sig_t[slot] = st;
+        P.sig_a[slot] = sa;
+        P.flags[slot] = f & (uint8_t)~PF_NEED_XS;
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_advance(LoopConfig c, Particles P, const ProblemDev* probs,
+                                                  RunCtl* ctl)
+{
+    if (ctl->error) return;
+    const bool queued = c.mode == MCX_QUEUED;
+    const int par = ctl->parity;
+    const int64_t count = queued ? (int64_t)ctl->n_adv[par] : P.cap;
+    const int32_t* list = queued ? P.q_adv[par] : nullptr;
+    const int M = c.derivatives;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < count; base += stride) {
+        const int64_t i = base + threadIdx.x;
+        int64_t slot = -1;
+        bool act = false;
+        if (i < count) {
+            slot = list ? list[i] : i;
+            act = list ? true : (P.flags[slot] & PF_ALIVE) != 0;
+        }
+        bool scored = false, dies = false, coll = false, survive = false, need_xs = false;
+        int outcome = -1;
+        int32_t pidx = 0;
+        double d = 0.0, xabs = 0.0;
+        double* tal_flux = nullptr;
+        double* tal_abs = nullptr;
+        int64_t tal_i = 0;
+        double Wl[MCX_MAX_DMAT] = {0.0, 0.0, 0.0, 0.0};
+        int32_t m = 0;
+        if (act) {
+            pidx = P.prob[slot];
+            const ProblemDev& pd = probs[pidx];
+            State q = load_state(P, slot, pd.lattice_n);
+            const int64_t h = P.hist[slot];
+            uint32_t n = P.rng_n[slot];
+            const double xi = uniform_at(pd.key, h, n);
+            n += 1;
+            const double sig_t = P.sig_t[slot], sig_a = P.sig_a[slot];
+            m = P.mat[slot];
+            const double dcol = sig_t > 0.0 ? -log(xi) / sig_t : INF;
+            int surf;
+            const double dsurf = surface_distance(pd, q, surf);
+            const bool collide = !(dsurf <= dcol);
+            d = collide ? dcol : dsurf;
+            uint8_t fl = P.flags[slot];
+            if (isinf(d)) {
+                dies = true;
+                outcome = OUT_LEAK_OTHER;
+            } else {
+                q.x = q.x + d * q.u;
+                q.y = q.y + d * q.v;
+                q.z = q.z + d * q.w;
+                int32_t bin;
+                if (pd.geometry == MCX_GEOM_INFINITE)
+                    bin = (int32_t)bsearch_window(pd.ebin_edges, 0, pd.n_ebins - 1, ebits(P.E[slot]));
+                else
+                    bin = region_of(pd, q);
+                const int64_t b = batch_of(pd, h);
+                tal_i = b * pd.nb + bin;
+                tal_flux = pd.flux + tal_i;
+                tal_abs = pd.absorb + tal_i;
+                scored = true;
+                xabs = d * sig_a;
+                if (M > 0) {
+                    for (int mm = 0; mm < M; ++mm) Wl[mm] = P.W[(int64_t)mm * P.cap + slot];
+                    for (int mm = 0; mm < M; ++mm) {
+                        if (mm == m) {
+                            Wl[mm] = Wl[mm] - sig_t * d;
+                            if (collide) Wl[mm] = Wl[mm] + 1.0;
+                        }
+                    }
+                    for (int mm = 0; mm < M; ++mm) P.W[(int64_t)mm * P.cap + slot] = Wl[mm];
+                }
+                if (!collide) {
+                    const int o = cross_surface(pd, q, surf);
+                    if (o >= 0) {
+                        dies = true;
+                        outcome = o;
+                    } else {
+                        survive = true;
+                        const int32_t nm = __ldg(pd.region_material + region_of(pd, q));
+                        if (nm != m) {
+                            need_xs = true;
+                            P.mat[slot] = nm;
+                        }
+                        fl = (uint8_t)((fl & ~(PF_INPIN | PF_NEED_XS)) | (q.inpin ? PF_INPIN : 0) |
+                                       (need_xs ? PF_NEED_XS : 0));
+                        P.cell[slot] = q.ci * (pd.lattice_n > 0 ? pd.lattice_n : 1) + q.cj;
+                        P.w[slot] = q.w;
+                    }
+                } else {
+                    coll = true;
+                    fl |= PF_COLLIDE;
+                }
+                P.x[slot] = q.x;
+                P.y[slot] = q.y;
+                P.z[slot] = q.z;
+            }
+            P.rng_n[slot] = n;
+            P.flags[slot] = fl;
+        }
+        // ---- warp-first tally reduction
+        const unsigned sm = __ballot_sync(FULL, scored);
+        if (scored) {
+            const unsigned grp = __match_any_sync(sm, (unsigned long long)tal_flux);
+            const int leader = __ffs(grp) - 1;
+            double sf = 0.0, sa = 0.0;
+            for (unsigned g = grp; g; g &= g - 1u) {
+                const int src = __ffs(g) - 1;
+                sf += __shfl_sync(grp, d, src);
+                sa += __shfl_sync(grp, xabs, src);
+            }
+            if (lane_id() == leader) {
+                atomicAdd(tal_flux, sf);
+                atomicAdd(tal_abs, sa);
+            }
+            if (M > 0) {
+                const ProblemDev& pd = probs[pidx];
+                for (int mm = 0; mm < M; ++mm) {
+                    const double vf = d * Wl[mm];
+                    const double va = xabs * Wl[mm] + (mm == m ? xabs : 0.0);
+                    double s1 = 0.0, s2 = 0.0;
+                    for (unsigned g = grp; g; g &= g - 1u) {
+                        const int src = __ffs(g) - 1;
+                        s1 += __shfl_sync(grp, vf, src);
+                        s2 += __shfl_sync(grp, va, src);
+                    }
+                    if (lane_id() == leader) {
+                        atomicAdd(pd.dflux + tal_i * M + mm, s1);
+                        atomicAdd(pd.dabsorb + tal_i * M + mm, s2);
+                    }
+                }
+            }
+        }
+        finish_deaths(dies, outcome, slot, pidx, probs, P, ctl, M, queued, par);
+        if (queued) {
+            int pos = warp_append(&ctl->n_coll, coll);
+            if (coll) P.q_coll[pos] = (int32_t)slot;
+            pos = warp_append(&ctl->n_adv[par ^ 1], survive);
+            if (survive) P.q_adv[par ^ 1][pos] = (int32_t)slot;
+            pos = warp_append(&ctl->n_xs[par ^ 1], need_xs);
+            if (need_xs) P.q_xs[par ^ 1][pos] = (int32_t)slot;
+        }
+    }
+}
+
+// Collision: species j = the first with xi1 * Sigma_t < C_j (C_j the running
+// sum of N_i (sigma_s,i + sigma_a,i) in stored order; the last species if
+// none); absorption if xi2 * sigma_t,j < sigma_a,j (analog); otherwise
+// elastic scattering isotropic in the centre-of-mass frame, killed below
+// E_cut.
+template <typename T>
+__global__ void __launch_bounds__(1024) k_collide(LoopConfig c, Tables t, Particles P,
+                                                  const ProblemDev* probs, RunCtl* ctl)
+{
+    if (ctl->error) return;
+    const bool queued = c.mode == MCX_QUEUED;
+    const int par = ctl->parity;
+    const int64_t count = queued ? (int64_t)ctl->n_coll : P.cap;
+    const int32_t* list = queued ? (ctl->sorted ? P.q_sorted : P.q_coll) : nullptr;
+    const int M = c.derivatives;
+    const int nc = t.n_ch, cs = t.ch_scatter, ca = t.ch_absorb;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < count; base += stride) {
+        const int64_t i = base + threadIdx.x;
+        int64_t slot = -1;
+        bool act = false;
+        if (i < count) {
+            slot = list ? list[i] : i;
+            act = list ? true : (P.flags[slot] & PF_COLLIDE) != 0;
+        }
+        bool dies = false, survive = false;
+        int outcome = -1;
+        int32_t pidx = 0;
+        double* tal_coll = nullptr;
+        int64_t tal_i = 0;
+        if (act) {
+            pidx = P.prob[slot];
+            const ProblemDev& pd = probs[pidx];
+            const int64_t h = P.hist[slot];
+            uint32_t n = P.rng_n[slot];
+            P.ncoll[slot] += 1u;
+            tal_i = batch_of(pd, h) * N_OUT + OUT_COLLISIONS;
+            tal_coll = pd.outcome + tal_i;
+            const double xi1 = uniform_at(pd.key, h, n);
+            const double xi2 = uniform_at(pd.key, h, n + 1);
+            const double xi3 = uniform_at(pd.key, h, n + 2);
+            n += 3;
+            const double E = P.E[slot];
+            const int32_t m = P.mat[slot];
+            const double target = xi1 * P.sig_t[slot];
+            const int64_t eb = ebits(E);
+            const int32_t hb = t.H > 0 ? hash_bin(t, E) : 0;
+            double cum = 0.0, ss_j = 0.0, sa_j = 0.0;
+            int32_t j = 0;
+            const int32_t i0 = __ldg(t.moff + m), i1 = __ldg(t.moff + m + 1);
+            for (int32_t ii = i0; ii < i1; ++ii) {
+                const int32_t s = __ldg(t.msp + ii);
+                const int64_t k = species_index(t, s, E, eb, hb);
+                const int64_t p = __ldg(t.goff + s) + k;
+                const double f = fraction_exact(E, __ldg(t.E + p), __ldg(t.E + p + 1));
+                ss_j = interp_exact(sig_at<T>(t.sigma, p * nc + cs), sig_at<T>(t.sigma, (p + 1) * nc + cs), f);
+                sa_j = interp_exact(sig_at<T>(t.sigma, p * nc + ca), sig_at<T>(t.sigma, (p + 1) * nc + ca), f);
+                j = s;
+                cum = cum + __ldg(t.mden + ii) * (ss_j + sa_j);
+                if (target < cum) break;
+            }
+            const double st_j = ss_j + sa_j;
+            uint8_t fl = (uint8_t)(P.flags[slot] & ~PF_COLLIDE);
+            if (xi2 * st_j < sa_j) {
+                dies = true;
+                outcome = OUT_ABSORBED;
+            } else {
+                const double A = __ldg(t.awr + j);
+                const double mu = 2.0 * xi3 - 1.0;
+                const double num = A * A + 2.0 * A * mu + 1.0;
+                const double den = (A + 1.0) * (A + 1.0);
+                const double E_new = E * (num / den);
+                if (E_new < pd.E_cut) {
+                    dies = true;
+                    outcome = OUT_CUTOFF;
+                } else {
+                    double mu_lab = (1.0 + A * mu) / sqrt(num);
+                    if (mu_lab > 1.0) mu_lab = 1.0;
+                    if (mu_lab < -1.0) mu_lab = -1.0;
+                    double cphi, sphi;
+                    azimuth(pd.key, h, n, cphi, sphi);
+                    double u = P.u[slot], v = P.v[slot], w = P.w[slot];
+                    rotate(u, v, w, mu_lab, cphi, sphi);
+                    P.u[slot] = u;
+                    P.v[slot] = v;
+                    P.w[slot] = w;
+                    P.E[slot] = E_new;
+                    fl |= PF_NEED_XS;
+                    survive = true;
+                }
+            }
+            P.rng_n[slot] = n;
+            P.flags[slot] = fl;
+        }
+        // collision-count tally (+ derivative), warp-first
+        const unsigned am = __ballot_sync(FULL, act);
+        if (act) {
+            const unsigned grp = __match_any_sync(am, (unsigned long long)tal_coll);
+            const int leader = __ffs(grp) - 1;
+            if (lane_id() == leader) atomicAdd(tal_coll, (double)__popc(grp));
+            if (M > 0) {
+                const ProblemDev& pd = probs[pidx];
+                for (int mm = 0; mm < M; ++mm) {
+                    const double wv = P.W[(int64_t)mm * P.cap + slot];
+                    double sum = 0.0;
+                    for (unsigned g = grp; g; g &= g - 1u) sum += __shfl_sync(grp, wv, __ffs(g) - 1);
+                    if (lane_id() == leader) atomicAdd(pd.doutcome + tal_i * M + mm, sum);
+                }
+            }
+        }
+        finish_deaths(dies, outcome, slot, pidx, probs, P, ctl, M, queued, par);
+        if (queued) {
+            int pos = warp_append(&ctl->n_xs[par ^ 1], survive);
+            if (survive) P.q_xs[par ^ 1][pos] = (int32_t)slot;
+            pos = warp_append(&ctl->n_adv[par ^ 1], survive);
+            if (survive) P.q_adv[par ^ 1][pos] = (int32_t)slot;
+        }
+    }
+}
+
+__global__ void k_bookkeep(RunCtl* ctl)
+{
+    const int p = ctl->parity;
+    ctl->n_xs[p] = 0;
+    ctl->n_adv[p] = 0;
+    ctl->n_dead[p] = 0;
+    ctl->n_coll = 0;
+    ctl->parity = p ^ 1;
+    ctl->sorted = 0;
+    if (!ctl->done) {
+        ctl->iters += 1;
+        if (ctl->n_alive == 0 && (long long)ctl->next >= ctl->total) {
+            ctl->done = 1;
+        } else if (ctl->iters >= ctl->max_iters) {
+            ctl->error = MCX_ERR_ITER_LIMIT;
+            ctl->done = 1;
+        }
+    }
+}
+
+// ---- binning of a queue by (material, log-energy bucket)
+__device__ __forceinline__ int sort_key(const LoopConfig& c, double E, int32_t m)
+{
+    float fb = (logf((float)E) - c.sort_ln_lo) * c.sort_scale;
+    int b = fb >= 0.f ? (int)fb : 0;
+    if (b >= c.n_ebuckets) b = c.n_ebuckets - 1;
+    return m * c.n_ebuckets + b;
+}
+
+// which: 0 = XS queue (consumed side), 1 = collision queue
+__global__ void k_sort_decide(LoopConfig c, RunCtl* ctl, int which)
+{
+    const int par = ctl->parity;
+    const long long n = which == 0 ? ctl->n_xs[par] : ctl->n_coll;
+    ctl->sorted = (!ctl->error && c.sort_period > 0 && (ctl->iters % c.sort_period) == 0 &&
+                   n >= c.sort_threshold && n > 0)
+                      ? 1
+                      : 0;
+}
+
+__global__ void k_sort_count(LoopConfig c, Particles P, RunCtl* ctl, int which)
+{
+    extern __shared__ uint32_t hist[];
+    if (!ctl->sorted) return;
+    const int par = ctl->parity;
+    const int64_t n = which == 0 ? ctl->n_xs[par] : ctl->n_coll;
+    const int32_t* list = which == 0 ? P.q_xs[par] : P.q_coll;
+    for (int i = threadIdx.x; i < c.n_sort_bins; i += blockDim.x) hist[i] = 0u;
+    __syncthreads();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t s = list[i];
+        atomicAdd(&hist[sort_key(c, P.E[s], P.mat[s])], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < c.n_sort_bins; i += blockDim.x)
+        if (hist[i]) atomicAdd(&P.bins[i], hist[i]);
+}
+
+// Exclusive scan of the bin counts (one block).
+__global__ void k_sort_scan(LoopConfig c, Particles P, RunCtl* ctl)
+{
+    __shared__ uint32_t warp_sums[32];
+    __shared__ uint32_t carry;
+    if (!ctl->sorted) return;
+    if (threadIdx.x == 0) carry = 0u;
+    __syncthreads();
+    const int nb = c.n_sort_bins;
+    for (int base = 0; base < nb; base += blockDim.x) {
+        const int i = base + threadIdx.x;
+        const uint32_t v = i < nb ? P.bins[i] : 0u;
+        uint32_t x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(FULL, x, o);
+            if (lane_id() >= o) x += y;
+        }
+        if (lane_id() == 31) warp_sums[threadIdx.x >> 5] = x;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            const int nw = blockDim.x >> 5;
+            uint32_t s = threadIdx.x < nw ? warp_sums[threadIdx.x] : 0u;
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(FULL, s, o);
+                if (lane_id() >= o) s += y;
+            }
+            if (threadIdx.x < nw) warp_sums[threadIdx.x] = s;
+        }
+        __syncthreads();
+        const uint32_t before = (threadIdx.x >> 5) ? warp_sums[(threadIdx.x >> 5) - 1] : 0u;
+        if (i < nb) P.bins[i] = carry + before + x - v;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry += before + x;
+        __syncthreads();
+    }
+}
+
+__global__ void k_sort_scatter(LoopConfig c, Particles P, RunCtl* ctl, int which)
+{
+    if (!ctl->sorted) return;
+    const int par = ctl->parity;
+    const int64_t n = which == 0 ? ctl->n_xs[par] : ctl->n_coll;
+    const int32_t* list = which == 0 ? P.q_xs[par] : P.q_coll;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
+        const int64_t i = base + threadIdx.x;
+        const bool valid = i < n;
+        const unsigned vm = __ballot_sync(FULL, valid);
+        if (!valid) continue;
+        const int32_t s = list[i];
+        const int key = sort_key(c, P.E[s], P.mat[s]);
+        const unsigned grp = __match_any_sync(vm, key);
+        const int leader = __ffs(grp) - 1;
+        uint32_t pos = 0u;
+        if (lane_id() == leader) pos = atomicAdd(&P.bins[key], (uint32_t)__popc(grp));
+        pos = __shfl_sync(grp, pos, leader);
+        P.q_sorted[pos + __popc(grp & lanes_below())] = s;
+    }
+}
+
+}  // namespace
+
+int launch_run_init(const LoopConfig& c, const Particles& P, RunCtl* ctl, long long total,
+                    int n_prob, long long max_iters, cudaStream_t st)
+{
+    k_run_init<<<c.grid, 256, 0, st>>>(P, ctl, total, n_prob, max_iters, c.mode == MCX_QUEUED);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+static int launch_sort(const LoopConfig& c, const Particles& P, RunCtl* ctl, int which,
+                       cudaStream_t st)
+{
+    if (cudaMemsetAsync(P.bins, 0, sizeof(uint32_t) * (size_t)(c.n_sort_bins + 1), st) != cudaSuccess)
+        return -1;
+    k_sort_decide<<<1, 1, 0, st>>>(c, ctl, which);
+    k_sort_count<<<c.grid, c.block, sizeof(uint32_t) * c.n_sort_bins, st>>>(c, P, ctl, which);
+    k_sort_scan<<<1, 1024, 0, st>>>(c, P, ctl);
+    k_sort_scatter<<<c.grid, c.block, 0, st>>>(c, P, ctl, which);
+    return 4;
+}
+
+int launch_iteration(const LoopConfig& c, const Tables& t, const Particles& P,
+                     const ProblemDev* probs, const int64_t* work_off, RunCtl* ctl,
+                     cudaStream_t st)
+{
+    int k = 0;
+    const bool sorting = c.mode == MCX_QUEUED && c.sort_period > 0 && c.n_sort_bins > 0;
+    k_refill<<<c.grid, c.block, 0, st>>>(c, P, probs, work_off, ctl);
+    ++k;
+    if (sorting) k += launch_sort(c, P, ctl, 0, st);
+    if (t.precision == MCX_FP32) k_lookup<float><<<c.grid, c.block, 0, st>>>(c, t, P, ctl);
+    else k_lookup<double><<<c.grid, c.block, 0, st>>>(c, t, P, ctl);
+    ++k;
+    k_advance<<<c.grid, c.block, 0, st>>>(c, P, probs, ctl);
+    ++k;
+    if (sorting) k += launch_sort(c, P, ctl, 1, st);
+    if (t.precision == MCX_FP32) k_collide<float><<<c.grid, c.block, 0, st>>>(c, t, P, probs, ctl);
+    else k_collide<double><<<c.grid, c.block, 0, st>>>(c, t, P, probs, ctl);
+    ++k;
+    k_bookkeep<<<1, 1, 0, st>>>(ctl);
+    ++k;
+    if (cudaGetLastError() != cudaSuccess) return -1;
+    return k;
+}
+
+// Philox uniforms of one history stream (test hook).
+__global__ void k_debug_uniforms(uint2 key, uint64_t hist, uint32_t first, int64_t n, double* out)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = uniform_at(key, hist, first + (uint32_t)i);
+}
+
+int launch_debug_uniforms(uint2 key, uint64_t hist, uint32_t first, int64_t n, double* out,
+                          cudaStream_t st)
+{
+    const int grid = (int)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024);
+    k_debug_uniforms<<<grid > 0 ? grid : 1, 256, 0, st>>>(key, hist, first, n, out);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+}  // namespace mcx

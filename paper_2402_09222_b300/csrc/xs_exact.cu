@@ -1,0 +1,108 @@
+// xs_exact.cu -- macroscopic lookup with the plain definition's FP64
+// arithmetic (compiled with --fmad=false), the grid-index debug kernel and
+// the hash-grid builder.
+#include "xs_exact.cuh"
+#include "kernels.h"
+
+namespace mcx {
+
+// One thread per lookup.  For lookup l: out[l][r] = sum_i N_i sigma_{r,i}(E).
+// `perm` (optional) is a processing order: thread j handles lookup perm[j];
+// results land at the lookup's own row, so the order changes nothing.
+template <typename T>
+__global__ void __launch_bounds__(256) k_xs_lookup_exact(Tables t, int64_t n,
+                                                         const double* __restrict__ Ein,
+                                                         const int32_t* __restrict__ mat,
+                                                         const int32_t* __restrict__ perm,
+                                                         double* __restrict__ out)
+{
+    const int nc = t.n_ch;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t l = perm ? (int64_t)__ldg(perm + j) : j;
+        const double E = __ldg(Ein + l);
+        const int32_t m = __ldg(mat + l);
+        double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+        if (m < 0 || m >= t.n_materials) {
+            for (int r = 0; r < nc; ++r) out[l * nc + r] = __longlong_as_double(0x7ff8000000000000LL);
+            continue;
+        }
+        const int64_t eb = ebits(E);
+        const int32_t hb = t.H > 0 ? hash_bin(t, E) : 0;
+        const int32_t i0 = __ldg(t.moff + m), i1 = __ldg(t.moff + m + 1);
+        for (int32_t i = i0; i < i1; ++i) {
+            const int32_t s = __ldg(t.msp + i);
+            const double N = __ldg(t.mden + i);
+            const int64_t k = species_index(t, s, E, eb, hb);
+            const int64_t p = __ldg(t.goff + s) + k;
+            const double f = fraction_exact(E, __ldg(t.E + p), __ldg(t.E + p + 1));
+#pragma unroll
+            for (int r = 0; r < 5; ++r) {
+                if (r < nc) {
+                    const double sg = interp_exact(sig_at<T>(t.sigma, p * nc + r),
+                                                   sig_at<T>(t.sigma, (p + 1) * nc + r), f);
+                    acc[r] = acc[r] + N * sg;
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < 5; ++r)
+            if (r < nc) out[l * nc + r] = acc[r];
+    }
+}
+
+__global__ void k_xs_indices(Tables t, int64_t n, const double* __restrict__ Ein,
+                             const int32_t* __restrict__ mat, int32_t max_species,
+                             int32_t* __restrict__ kout)
+{
+    for (int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; l < n;
+         l += (int64_t)gridDim.x * blockDim.x) {
+        const double E = Ein[l];
+        const int32_t m = mat[l];
+        const bool ok = m >= 0 && m < t.n_materials;
+        const int32_t i0 = ok ? t.moff[m] : 0, cnt = ok ? t.moff[m + 1] - i0 : 0;
+        const int64_t eb = ebits(E);
+        const int32_t hb = t.H > 0 ? hash_bin(t, E) : 0;
+        for (int32_t i = 0; i < max_species; ++i)
+            kout[l * max_species + i] =
+                i < cnt ? (int32_t)species_index(t, t.msp[i0 + i], E, eb, hb) : -1;
+    }
+}
+
+// hidx[s][b] = largest k in [0, n_s-2] with g_s[k] <= hbound[b] (full search).
+__global__ void k_build_hash(Tables t, int32_t* __restrict__ hidx)
+{
+    const int64_t total = (int64_t)t.n_species * (t.H + 1);
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t s = (int32_t)(q / (t.H + 1));
+        const int32_t b = (int32_t)(q % (t.H + 1));
+        const int64_t base = t.goff[s], n = t.goff[s + 1] - base;
+        hidx[q] = (int32_t)bsearch_window(t.E + base, 0, n - 2, ebits(t.hbound[b]));
+    }
+}
+
+int launch_xs_lookup_exact(const Tables& t, int64_t n, const double* E, const int32_t* mat,
+                           const int32_t* perm, double* out, int grid, cudaStream_t st)
+{
+    if (t.precision == MCX_FP32)
+        k_xs_lookup_exact<float><<<grid, 256, 0, st>>>(t, n, E, mat, perm, out);
+    else
+        k_xs_lookup_exact<double><<<grid, 256, 0, st>>>(t, n, E, mat, perm, out);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int launch_xs_indices(const Tables& t, int64_t n, const double* E, const int32_t* mat,
+                      int32_t max_species, int32_t* kout, int grid, cudaStream_t st)
+{
+    k_xs_indices<<<grid, 256, 0, st>>>(t, n, E, mat, max_species, kout);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int launch_build_hash(const Tables& t, int32_t* hidx, int grid, cudaStream_t st)
+{
+    k_build_hash<<<grid, 256, 0, st>>>(t, hidx);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+}  // namespace mcx

@@ -1,0 +1,197 @@
+"""GPU parity of the macroscopic cross-section lookup against the CPU oracle.
+
+Exact mode must reproduce the plain FP64 definition bit for bit (indices and
+values); fast mode must stay within 1e-6 relative; hash bins and binning must
+change nothing.  Sizes span several 256-thread tiles with a ragged tail, and
+the full 355-species / 1e8-lookup workload is checked on sampled outputs in
+the launch configuration the benchmark times.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2402_09222_b300 import synth
+
+pytestmark = pytest.mark.gpu
+
+FAST_RTOL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+@pytest.fixture(scope="module")
+def small_case():
+    lib = synth.species_library(40, 700, 101)
+    mats = synth.lookup_materials(40, 102, n_materials=6)
+    E, mat = synth.lookup_inputs(50_011, mats.n_materials, 103)
+    rng = np.random.default_rng(104)
+    E[:300] = lib.energies[rng.integers(0, len(lib.energies), 300)]       # exact grid points
+    E[300:310] = [1e-7, 1e-6, 9.99e-6, 1e-5, 2e7, 2.0000001e7, 3e7, 1e9, 5e-6, 1e-5]
+    return lib, mats, E, mat
+
+
+def _dev(torch, a, dtype):
+    return torch.as_tensor(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype)
+
+
+def _handle(lib, mats, precision, H):
+    from paper_2402_09222_b300 import mcx
+    p = mcx.Problem(None)
+    p.load_tables(lib, mats, precision=precision, hash_bins=H)
+    return p
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("H", [0, 4000])
+def test_exact_lookup_is_bit_identical(torch_cuda, small_case, precision, H):
+    from paper_2402_09222_b300 import mcx
+    torch = torch_cuda
+    lib, mats, E, mat = small_case
+    prec = mcx.FP64 if precision == "fp64" else mcx.FP32
+    ref_lib = lib if precision == "fp64" else lib.fp32_rounded()
+    ref = oracle.xs_lookup(ref_lib, mats, E, mat, n_threads=8)
+    p = _handle(lib, mats, prec, H)
+    out = p.xs_lookup(_dev(torch, E, torch.float64), _dev(torch, mat, torch.int32)).cpu().numpy()
+    assert np.array_equal(out.view(np.uint64), ref.view(np.uint64))
+
+
+@pytest.mark.parametrize("H", [0, 1, 100, 4000, 100_000])
+def test_grid_indices_match_for_every_hash_size(torch_cuda, small_case, H):
+    torch = torch_cuda
+    lib, mats, E, mat = small_case
+    ref = oracle.xs_indices(lib, mats, E, mat)
+    p = _handle(lib, mats, 0, H)
+    k = p.xs_indices(_dev(torch, E, torch.float64), _dev(torch, mat, torch.int32)).cpu().numpy()
+    assert np.array_equal(k, ref)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_fast_lookup_within_tolerance(torch_cuda, small_case, precision):
+    from paper_2402_09222_b300 import mcx
+    torch = torch_cuda
+    lib, mats, E, mat = small_case
+    prec = mcx.FP64 if precision == "fp64" else mcx.FP32
+    ref = oracle.xs_lookup(lib if precision == "fp64" else lib.fp32_rounded(), mats, E, mat, n_threads=8)
+    p = _handle(lib, mats, prec, 4000)
+    out = p.xs_lookup(_dev(torch, E, torch.float64), _dev(torch, mat, torch.int32),
+                      flags=mcx.LOOKUP_FAST).cpu().numpy()
+    rel = np.abs(out - ref) / np.maximum(np.abs(ref), 1e-300)
+    assert np.all(np.isfinite(out))
+    assert rel.max() <= FAST_RTOL, rel.max()
+
+
+@pytest.mark.parametrize("flags", [2, 3])
+def test_binning_changes_nothing(torch_cuda, small_case, flags):
+    torch = torch_cuda
+    lib, mats, E, mat = small_case
+    p = _handle(lib, mats, 1, 4000)
+    dE, dm = _dev(torch, E, torch.float64), _dev(torch, mat, torch.int32)
+    a = p.xs_lookup(dE, dm, flags=flags & 1).cpu().numpy()
+    b = p.xs_lookup(dE, dm, flags=flags).cpu().numpy()
+    assert np.array_equal(a.view(np.uint64), b.view(np.uint64))
+
+
+def test_degenerate_inputs(torch_cuda, small_case):
+    from paper_2402_09222_b300 import mcx
+    torch = torch_cuda
+    lib, mats, E, mat = small_case
+    p = _handle(lib, mats, 0, 100)
+    # empty and single lookups
+    empty = torch.empty(0, dtype=torch.float64, device="cuda")
+    assert p.xs_lookup(empty, torch.empty(0, dtype=torch.int32, device="cuda")).shape == (0, 5)
+    one = p.xs_lookup(_dev(torch, E[:1], torch.float64), _dev(torch, mat[:1], torch.int32)).cpu().numpy()
+    assert np.array_equal(one, oracle.xs_lookup(lib, mats, E[:1], mat[:1]))
+    # out-of-range materials and NaN energies
+    Eb = np.array([1.0, 2.0, float("nan"), 3.0])
+    mb = np.array([-1, mats.n_materials, 0, 1], np.int32)
+    for fl in (mcx.LOOKUP_EXACT, mcx.LOOKUP_FAST):
+        o = p.xs_lookup(_dev(torch, Eb, torch.float64), _dev(torch, mb, torch.int32), flags=fl).cpu().numpy()
+        assert np.all(np.isnan(o[:3])) and np.all(np.isfinite(o[3]))
+    # a library whose materials hold one species and whose grids have 2 points
+    lib2 = synth.flat_library(3.0, 4.0)
+    mats2 = synth.make_materials([[0]], [[0.5]])
+    p2 = _handle(lib2, mats2, 0, 7)
+    Es = np.array([1e-9, 1e-5, 1.0, 2e7, 1e12])
+    o = p2.xs_lookup(_dev(torch, Es, torch.float64), _dev(torch, np.zeros(5, np.int32), torch.int32))
+    np.testing.assert_array_equal(o.cpu().numpy(), np.tile([1.5, 2.0], (5, 1)))
+
+
+def test_wrong_arguments_raise(torch_cuda, small_case):
+    from paper_2402_09222_b300 import mcx
+    torch = torch_cuda
+    lib, mats, E, mat = small_case
+    p = _handle(lib, mats, 0, 0)
+    with pytest.raises(TypeError):
+        p.xs_lookup(torch.zeros(4, dtype=torch.float32, device="cuda"), torch.zeros(4, dtype=torch.int32, device="cuda"))
+    with pytest.raises(mcx.McxError):
+        p.xs_indices(_dev(torch, E[:4], torch.float64), _dev(torch, mat[:4], torch.int32), max_species=1)
+    bad = synth.Library(lib.grid_offsets, lib.energies.copy(), lib.sigma, lib.awr)
+    bad.energies[5] = bad.energies[4]
+    with pytest.raises(mcx.McxError, match="not strictly increasing"):
+        mcx.Problem(None).load_tables(bad, mats)
+    negs = synth.Library(lib.grid_offsets, lib.energies, lib.sigma.copy(), lib.awr)
+    negs.sigma[7, 1] = -1.0
+    with pytest.raises(mcx.McxError, match="sigma"):
+        mcx.Problem(None).load_tables(negs, mats)
+
+
+def test_host_path_matches_device_path(torch_cuda, small_case):
+    from paper_2402_09222_b300 import mcx
+    torch = torch_cuda
+    lib, mats, E, mat = small_case
+    p = _handle(lib, mats, 1, 4000)
+    dev = p.xs_lookup(_dev(torch, E, torch.float64), _dev(torch, mat, torch.int32), flags=mcx.LOOKUP_FAST)
+    Eh = torch.as_tensor(E).pin_memory()
+    mh = torch.as_tensor(mat).pin_memory()
+    host = p.xs_lookup_host(Eh, mh, flags=mcx.LOOKUP_FAST)
+    assert torch.equal(host, dev.cpu())
+    host2 = p.xs_lookup_host(E, mat, flags=mcx.LOOKUP_FAST)
+    assert np.array_equal(host2, dev.cpu().numpy())
+
+
+def test_backward_matches_oracle_adjoint(torch_cuda):
+    torch = torch_cuda
+    lib = synth.species_library(12, 300, 211)
+    mats = synth.lookup_materials(12, 212, n_materials=4)
+    E, mat = synth.lookup_inputs(20_003, mats.n_materials, 213)
+    G = np.random.default_rng(214).normal(size=(len(E), lib.n_ch))
+    gd_ref, gs_ref = oracle.xs_lookup_backward(lib, mats, E, mat, G)
+    p = _handle(lib, mats, 0, 4000)
+    gd, gs = p.xs_lookup_backward(_dev(torch, E, torch.float64), _dev(torch, mat, torch.int32),
+                                  _dev(torch, G, torch.float64))
+    gd, gs = gd.cpu().numpy(), gs.cpu().numpy()
+    np.testing.assert_allclose(gd, gd_ref, rtol=1e-11, atol=1e-11 * np.abs(gd_ref).max())
+    np.testing.assert_allclose(gs, gs_ref, rtol=1e-11, atol=1e-11 * np.abs(gs_ref).max())
+
+
+def test_config2_full_size_sampled(torch_cuda):
+    """355 species x 11,303 points, 12 materials, 1e8 lookups with FP32 tables
+    in the benchmark's tuned launch (fast arithmetic, hash 4000, binning);
+    20,000 sampled outputs checked against the oracle, and the exact FP64
+    path on the same sample bit for bit."""
+    from paper_2402_09222_b300 import mcx
+    torch = torch_cuda
+    lib = synth.species_library(355, 11_303, 1236)
+    mats = synth.lookup_materials(355, 1236)
+    n = 100_000_000
+    E, mat = synth.lookup_inputs(n, mats.n_materials, 1336)
+    dE, dm = _dev(torch, E, torch.float64), _dev(torch, mat, torch.int32)
+    idx = np.random.default_rng(5).choice(n, 20_000, replace=False)
+    p32 = _handle(lib, mats, mcx.FP32, 4000)
+    out = p32.xs_lookup(dE, dm, flags=mcx.LOOKUP_FAST | mcx.LOOKUP_SORT)
+    got = out[torch.as_tensor(idx, device="cuda")].cpu().numpy()
+    ref = oracle.xs_lookup(lib.fp32_rounded(), mats, E[idx], mat[idx], n_threads=8)
+    rel = np.abs(got - ref) / np.abs(ref)
+    assert rel.max() <= FAST_RTOL, rel.max()
+    del out
+    p64 = _handle(lib, mats, mcx.FP64, 0)
+    out64 = p64.xs_lookup(dE, dm)
+    got64 = out64[torch.as_tensor(idx, device="cuda")].cpu().numpy()
+    ref64 = oracle.xs_lookup(lib, mats, E[idx], mat[idx], n_threads=8)
+    assert np.array_equal(got64.view(np.uint64), ref64.view(np.uint64))
