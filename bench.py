@@ -1,0 +1,346 @@
+#!/usr/bin/env python
+"""Benchmark of the macroscopic cross-section lookup (and, alongside it, the
+event-based transport) on one B300 per rank.
+
+One step = one pass of the lookup hot path over one batch of 1e8 synthetic
+lookups (355 species x 11,303 points, 5 channels, 12 materials of 4-321
+species; energies log-uniform on [1e-5, 2e7] eV, materials uniform): binning
+by material and log-energy, then the gather-interpolate-sum kernel, FP32
+tables, 4000 hash bins.  Inputs (1.2 GB) and outputs (4 GB) are far larger
+than the 126 MB L2, so no flush is needed between steps.
+
+Printed: one JSON line (rank 0) with the contract keys plus `roofline`
+(lookup kernel, algorithmic bytes over its CUDA-event time against the
+measured HBM copy bandwidth), `cpu_baseline` (the CPU oracle on a bounded
+sample of the same workload), `e2e` (the same lookups through the C-ABI host
+entry point, copies included), `plain` (the FP64 exact full-search form) and
+`transport` (particles/s on the 17x17 lattice, tuned and plain).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mcx|reference]
+Under torchrun each rank runs its own batch (weak scaling, no collective on
+the data path; a barrier and a max-reduction of the timings only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_LOOKUPS = 100_000_000
+N_SPECIES, N_POINTS = 355, 11_303
+LIB_SEED, MAT_SEED, INPUT_SEED = 1236, 1236, 1336
+TUNED = dict(precision=1, hash_bins=4000, flags=1)        # FP32 tables, fast arithmetic, binned
+PLAIN = dict(precision=0, hash_bins=0, flags=0)           # FP64 tables, exact, full binary search
+TRANSPORT_HIST = 10_000_000
+TRANSPORT_TUNED = dict(precision=1, hash_bins=4000, pif=2_000_000,
+                       tune=dict(mode=1, block_size=256, sort_period=4, sort_threshold=20_000))
+TRANSPORT_PLAIN = dict(precision=0, hash_bins=0, pif=1_000_000, tune=dict(mode=0, block_size=256))
+WORKLOAD = ("macroscopic XS lookup, 355 species x 11,303 points x 5 channels, 12 materials "
+            "(4-321 species), 1e8 lookups per step")
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (SM clock, throttle reasons)."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4)
+                          if len(r) > 5 + i and r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+def workload_inputs(rank: int):
+    from paper_2402_09222_b300 import synth
+    lib = synth.species_library(N_SPECIES, N_POINTS, LIB_SEED)
+    mats = synth.lookup_materials(N_SPECIES, MAT_SEED)
+    E, mat = synth.lookup_inputs(N_LOOKUPS, mats.n_materials, INPUT_SEED + rank)
+    return lib, mats, E, mat
+
+
+def algorithmic_bytes(mats, mat, sigma_bytes: int, n_ch: int = 5) -> float:
+    """Per-lookup bytes of the definition: per species the two bracketing
+    energies (16 B) and the two table rows (2 n_ch sigma), plus E (8), the
+    material id (4) and the output row (8 n_ch)."""
+    counts = np.bincount(mat, minlength=mats.n_materials)
+    sizes = np.diff(mats.offsets)
+    species_visits = float((counts * sizes).sum())
+    return species_visits * (16 + 2 * n_ch * sigma_bytes) + len(mat) * (8 + 4 + 8 * n_ch)
+
+
+def cpu_baseline(lib, mats, E, mat, n_sample: int = 8_000_000):
+    import oracle
+    cores = os.cpu_count() or 1
+    oracle.xs_lookup(lib, mats, E[:1000], mat[:1000], n_threads=cores)   # warm
+    t0 = time.perf_counter()
+    oracle.xs_lookup(lib, mats, E[:n_sample], mat[:n_sample], n_threads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": n_sample / dt, "unit": "lookups/s", "cores": cores, "kind": "oracle",
+            "sample": f"first {n_sample:,} lookups of the step's batch, FP64 tables, "
+                      f"full binary search, OpenMP over lookups on {cores} host cores ({dt:.1f} s)"}
+
+
+def run_reference(args, rank: int, world: int):
+    """The reference arm: the CPU oracle, as it stands, on the host cores."""
+    if rank != 0:
+        return
+    lib, mats, E, mat = workload_inputs(0)
+    import oracle
+    cores = os.cpu_count() or 1
+    sample = 1_000_000
+    times = []
+    for s in range(args.warmup + args.steps):
+        lo = (s * sample) % (N_LOOKUPS - sample)
+        t0 = time.perf_counter()
+        oracle.xs_lookup(lib, mats, E[lo:lo + sample], mat[lo:lo + sample], n_threads=cores)
+        if s >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = sample * args.steps / tot
+    line = {"impl": "reference", "metric": "XS lookups/s", "value": value, "unit": "lookups/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "reference": "CPU FP64 oracle, bounded sample per step"},
+            "cpu_baseline": {"value": value, "unit": "lookups/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{sample:,} lookups of the workload per step"},
+            "e2e": {"value": value, "unit": "lookups/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def time_transport(mcx, synth, lib3, spec, seed, reps=1):
+    import torch
+    prob = synth.config3_problem(n_histories=TRANSPORT_HIST, lib=lib3)
+    p = mcx.make_problem(prob, precision=spec["precision"], hash_bins=spec["hash_bins"])
+    p.set_tuning(**spec["tune"])
+    p.run(count=TRANSPORT_HIST // 10, particles_in_flight=spec["pif"], seed=seed)   # warm-up
+    best = None
+    for _ in range(reps):
+        p.zero_tallies()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        p.run(particles_in_flight=spec["pif"], seed=seed)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        best = ms if best is None else min(best, ms)
+    st = p.stats()
+    out = p.tallies()["outcome"].sum(0)
+    p.close()
+    return {"particles_per_s": TRANSPORT_HIST / (best / 1e3), "ms": best,
+            "collisions_per_history": float(out[4] / TRANSPORT_HIST),
+            "iterations": st["iterations"], "kernels": st["kernels"]}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mcx", choices=["mcx", "reference"])
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the plain form, e2e, transport and CPU legs (profiling runs)")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import torch.distributed as dist
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2402_09222_b300 import mcx, synth
+
+    lib, mats, E, mat = workload_inputs(rank)
+    dE = torch.as_tensor(E, device="cuda")
+    dm = torch.as_tensor(mat, device="cuda")
+    out = torch.empty((N_LOOKUPS, 5), dtype=torch.float64, device="cuda")
+    perm = torch.empty(N_LOOKUPS, dtype=torch.int32, device="cuda")
+    p = mcx.Problem(None, device=local).load_tables(lib, mats, precision=TUNED["precision"],
+                                                    hash_bins=TUNED["hash_bins"])
+    stream = torch.cuda.current_stream()
+
+    def step(evs=None):
+        if evs:
+            evs[0].record(stream)
+        p.xs_sort(dE, dm, perm)
+        if evs:
+            evs[1].record(stream)
+        p.xs_lookup_ordered(dE, dm, perm, out=out, flags=TUNED["flags"])
+        if evs:
+            evs[2].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for k in range(args.steps):
+            step(evs[k])
+        t1.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    total_ms = t0.elapsed_time(t1)
+    lookup_ms = [e[1].elapsed_time(e[2]) for e in evs]
+    sort_ms = [e[0].elapsed_time(e[1]) for e in evs]
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * N_LOOKUPS * args.steps / (total_ms / 1e3)
+
+    peak, peak_kind = measured_peaks()
+    alg = algorithmic_bytes(mats, mat, 4)
+    lk = sum(lookup_ms) / len(lookup_ms)
+    achieved = alg / (lk / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": "k_xs_lookup_fast<float> (binned order)",
+                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "peak_source": f"{peak_kind} HBM copy bandwidth (MEASURED_PEAKS.json)" if peak_kind == "measured"
+                else "fallback 6400 GB/s",
+                "traffic": None, "algorithmic_bytes_per_launch": alg,
+                "lookup_kernel_ms": lk, "sort_ms": sum(sort_ms) / len(sort_ms)}
+    tpath = os.path.join(ROOT, "profiles", "lookup_traffic.json")
+    if os.path.exists(tpath):
+        tr = json.load(open(tpath))
+        if tr.get("kernel_source_hash") == kernel_source_hash():
+            roofline["traffic"] = tr["dram_bytes_per_launch"]
+
+    line = {"metric": "XS lookups/s (tuned lookup; particles/s of the transport in 'transport')",
+            "value": value, "unit": "lookups/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 tables, f64 energies and search",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "tables": "FP32", "hash_bins": TUNED["hash_bins"],
+                       "arithmetic": "fast (<=1e-6 rel)", "binning": "material x 1024 log-E buckets",
+                       "l2": "inputs 1.2 GB + outputs 4 GB per step exceed the 126 MB L2",
+                       "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+            "roofline": roofline, "gpu_launches": 4 * args.steps,
+            "clocks": clocks.summary()}
+
+    if not args.no_extras:
+        # end to end through the C ABI with host buffers (copies in the timed region)
+        Eh = torch.as_tensor(E).pin_memory()
+        mh = torch.as_tensor(mat).pin_memory()
+        oh = torch.empty((N_LOOKUPS, 5), dtype=torch.float64).pin_memory()
+        p.xs_lookup_host(Eh[:1_000_000], mh[:1_000_000], oh[:1_000_000], flags=TUNED["flags"])
+        if world > 1:
+            dist.barrier()
+        t0w = time.perf_counter()
+        p.xs_lookup_host(Eh, mh, oh, flags=TUNED["flags"])
+        e2e_s = time.perf_counter() - t0w
+        if world > 1:
+            t = torch.tensor([e2e_s], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        line["e2e"] = {"value": world * N_LOOKUPS / e2e_s, "unit": "lookups/s",
+                       "h2d_bytes_per_step": N_LOOKUPS * 12, "d2h_bytes_per_step": N_LOOKUPS * 40,
+                       "path": "mcx_xs_lookup_host, pinned host buffers, 8M-lookup chunks on 2 streams"}
+        del Eh, mh, oh
+    if rank == 0 and world == 1 and not args.no_extras:
+        # plain form: FP64 tables, exact arithmetic, full binary search, natural order
+        pp = mcx.Problem(None, device=local).load_tables(lib, mats, precision=0, hash_bins=0)
+        pp.xs_lookup(dE, dm, out=out)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        pp.xs_lookup(dE, dm, out=out)
+        b.record(stream)
+        torch.cuda.synchronize()
+        pms = a.elapsed_time(b)
+        line["plain"] = {"lookups_per_s": N_LOOKUPS / (pms / 1e3), "ms": pms,
+                         "form": "FP64 tables, exact FP64 arithmetic, full binary search, unsorted",
+                         "achieved_alg_GBs": algorithmic_bytes(mats, mat, 8) / (pms / 1e3) / 1e9}
+        pp.close()
+        # transport, 17x17 lattice, 1e7 histories
+        lib3 = synth.config3_library()
+        line["transport"] = {
+            "metric": "particles/s", "config": "17x17 lattice, 40/4/3-species materials, 1e7 histories",
+            "tuned": time_transport(mcx, synth, lib3, TRANSPORT_TUNED, seed=5),
+            "plain": time_transport(mcx, synth, lib3, TRANSPORT_PLAIN, seed=5),
+            "tuned_settings": {k: v for k, v in TRANSPORT_TUNED.items()},
+        }
+        line["cpu_baseline"] = cpu_baseline(lib, mats, E, mat)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def kernel_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("xs_fast.cu", "mcx_internal.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2402_09222_b300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+if __name__ == "__main__":
+    main()

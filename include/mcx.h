@@ -39,6 +39,7 @@ extern "C" {
 #define MCX_ERR_ITER_LIMIT (-4) /* the event loop reached its iteration cap */
 #define MCX_ERR_STATE (-5)      /* call out of order (e.g. run before tables) */
 #define MCX_ERR_BOUNDS (-6)     /* a device-side bounds check fired */
+#define MCX_ERR_TIMEOUT (-7)    /* the run exceeded its host time limit */
 
 /* ---- enumerations ---------------------------------------------------- */
 /* Geometry of a problem.  NONE: a handle that only holds cross-section
@@ -121,7 +122,13 @@ typedef struct {
  *                   between host checks of the termination flag (>= 1)
  *   max_event_iters iteration cap of one run (0 = automatic); reaching it
  *                   returns MCX_ERR_ITER_LIMIT instead of looping on
- *   use_graph       1 = replay the captured loop body, 0 = plain launches */
+ *   use_graph       1 = replay the captured loop body, 0 = plain launches
+ *   time_limit_s    wall-clock budget of one run in seconds (0 = none),
+ *                   checked by the host between graph launches; when it is
+ *                   exceeded the run stops after the iterations in flight and
+ *                   returns MCX_ERR_TIMEOUT (tallies then hold a partial run).
+ *                   Used by the autotuner for the paper's evaluation time
+ *                   limit (1.5 x the baseline run time). */
 typedef struct {
     int32_t mode;
     int32_t block_size;
@@ -130,6 +137,7 @@ typedef struct {
     int32_t iters_per_sync;
     int64_t max_event_iters;
     int32_t use_graph;
+    double time_limit_s;
 } mcx_tune;
 
 /* Create a problem on desc->device.  Validates the description (geometry
@@ -174,6 +182,15 @@ int mcx_set_hash_bins(mcx_problem* p, int32_t hash_bins);
 
 /* Replace the atom densities (same sparsity as loaded), HOST pointer. */
 int mcx_set_densities(mcx_problem* p, const double* mat_dens, int64_t nnz);
+
+/* Replace densities and/or cross sections from DEVICE buffers (same shapes
+ * as loaded: mat_dens [nnz] FP64, sigma [P][n_ch] FP64; either may be NULL to
+ * keep the current values), queued on `stream`.  FP32 tables receive the
+ * values rounded to FP32.  No validation of the values is done on this path
+ * (it serves gradient checks and optimisation loops that own the buffers).
+ * Errors: MCX_ERR_ARG, MCX_ERR_STATE, MCX_ERR_CUDA. */
+int mcx_update_tables_device(mcx_problem* p, const double* mat_dens, const double* sigma,
+                             void* stream);
 
 /* Set / get the event-loop tuning.  mcx_default_tuning fills the plain form:
  * queueless, block 256, no sorting, threshold 20000, 16 iterations per sync,
@@ -234,6 +251,23 @@ int mcx_last_run_stats(const mcx_problem* p, int64_t* out, int32_t n);
  * Errors: MCX_ERR_ARG, MCX_ERR_STATE, MCX_ERR_CUDA, MCX_ERR_OOM. */
 int mcx_xs_lookup(mcx_problem* p, int64_t n, const double* E, const int32_t* mat, double* out,
                   int32_t flags, void* stream);
+
+/* Binning of lookups by material and energy (Sec. 4.1: sorting so that
+ * neighbouring threads work on the same material and nearby energies):
+ * perm (int32 [n], DEVICE) receives 0..n-1 ordered by (material, bucket of
+ * log E) with 1024 buckets per material (fewer when materials x buckets would
+ * exceed 12288 bins).  Order within a bucket is unspecified.  E and mat are
+ * DEVICE pointers.  Uses a small library-owned bin array (allocated on first
+ * use).  Errors: MCX_ERR_ARG, MCX_ERR_STATE, MCX_ERR_CUDA, MCX_ERR_OOM. */
+int mcx_xs_sort(mcx_problem* p, int64_t n, const double* E, const int32_t* mat, int32_t* perm,
+                void* stream);
+
+/* mcx_xs_lookup processing the lookups in the order perm (a permutation of
+ * 0..n-1, e.g. from mcx_xs_sort; NULL = natural order).  Results land in each
+ * lookup's own row of out, so the order changes no value.  flags may hold
+ * MCX_LOOKUP_FAST only.  DEVICE pointers. */
+int mcx_xs_lookup_ordered(mcx_problem* p, int64_t n, const double* E, const int32_t* mat,
+                          const int32_t* perm, double* out, int32_t flags, void* stream);
 
 /* The same lookup from HOST buffers: copies in, computes and copies out in
  * chunks pipelined over two streams; synchronous.  Host buffers should be

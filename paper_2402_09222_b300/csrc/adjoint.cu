@@ -27,13 +27,13 @@ __global__ void __launch_bounds__(256) k_xs_backward(Tables t, int64_t n, const 
         if (m < 0 || m >= t.n_materials) continue;
         double g[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
         for (int r = 0; r < nc && r < 5; ++r) g[r] = __ldg(gout + l * nc + r);
-        const int64_t eb = ebits(E);
-        const int32_t hb = t.H > 0 ? hash_bin(t, E) : 0;
+        const int64_t eb = search_key(E);
+        const int32_t hb = t.H > 0 ? hash_bin(t, E, eb) : 0;
         const int32_t i0 = __ldg(t.moff + m), i1 = __ldg(t.moff + m + 1);
         for (int32_t i = i0; i < i1; ++i) {
             const int32_t s = __ldg(t.msp + i);
             const double N = __ldg(t.mden + i);
-            const int64_t k = species_index(t, s, E, eb, hb);
+            const int64_t k = species_index(t, s, eb, hb);
             const int64_t p = __ldg(t.goff + s) + k;
             const double f = fraction_exact(E, __ldg(t.E + p), __ldg(t.E + p + 1));
             double dn = 0.0;

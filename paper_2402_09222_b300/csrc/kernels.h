@@ -18,6 +18,9 @@ int launch_build_hash(const Tables& t, int32_t* hidx, int grid, cudaStream_t st)
 int launch_xs_backward(const Tables& t, int64_t n, const double* E, const int32_t* mat,
                        const double* grad_out, double* grad_dens, double* grad_sigma, int grid,
                        cudaStream_t st);
+int launch_update_tables(const double* dens_src, int64_t nnz, double* mden, float* mden32,
+                         const double* sig_src, int64_t n_sig, void* sigma, int precision,
+                         cudaStream_t st);
 int launch_debug_uniforms(uint2 key, uint64_t hist, uint32_t first, int64_t n, double* out,
                           cudaStream_t st);
 

@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <chrono>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -529,6 +530,7 @@ int run_loop(mcx_problem* owner, int n_prob, mcx_problem* const* probs, const in
     int64_t launches = 0, kernels = 0;
     const int64_t max_launches = max_iters / K + 4;
     int status = MCX_OK;
+    const auto t_start = std::chrono::steady_clock::now();
     for (;;) {
         if (tu.use_graph) {
             CUDA_TRY(cudaGraphLaunch(owner->gexec, st));
@@ -549,6 +551,12 @@ int run_loop(mcx_problem* owner, int n_prob, mcx_problem* const* probs, const in
             break;
         }
         if (owner->h_ctl->done) break;
+        if (tu.time_limit_s > 0.0 &&
+            std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count() > tu.time_limit_s) {
+            status = fail(MCX_ERR_TIMEOUT, "run exceeded its time limit of %.3f s after %lld iterations",
+                          tu.time_limit_s, (long long)owner->h_ctl->iters);
+            break;
+        }
         if (launches >= max_launches) {
             status = fail(MCX_ERR_ITER_LIMIT, "host loop reached its launch cap");
             break;
@@ -564,44 +572,66 @@ int run_loop(mcx_problem* owner, int n_prob, mcx_problem* const* probs, const in
 
 int lookup_grid(const mcx_problem* p) { return p->sm_count * 8; }
 
-int ensure_lookup_scratch(mcx_problem* p, int64_t n, size_t bins)
+int ensure_lookup_scratch(mcx_problem* p, int64_t n, size_t)
 {
     if (p->perm_cap < n) {
         dev_free(p->perm);
         TRY(dev_alloc(&p->perm, (size_t)n));
         p->perm_cap = n;
     }
-    if (p->lbins_cap < bins + 1) {
-        dev_free(p->lbins);
-        TRY(dev_alloc(&p->lbins, bins + 1));
-        p->lbins_cap = bins + 1;
-    }
     return MCX_OK;
 }
 
-// Lookup on device buffers, queued on `st`.
-int lookup_device(mcx_problem* p, int64_t n, const double* E, const int32_t* mat, double* out,
-                  int32_t flags, cudaStream_t st)
+SortParams lookup_sort_params(const TableStore* ts)
+{
+    SortParams sp;
+    sp.n_materials = ts->view.n_materials;
+    sp.n_ebuckets = 1024;
+    while (sp.n_ebuckets > 1 && (size_t)sp.n_materials * sp.n_ebuckets * 4 > 48 * 1024) sp.n_ebuckets >>= 1;
+    sp.ln_lo = (float)std::log(ts->emin);
+    sp.scale = (float)((double)sp.n_ebuckets / (std::log(ts->emax) - std::log(ts->emin)));
+    return sp;
+}
+
+// Bin lookups into perm (device, [n]); bins scratch owned by the problem.
+int sort_device(mcx_problem* p, int64_t n, const double* E, const int32_t* mat, int32_t* perm,
+                cudaStream_t st)
+{
+    const SortParams sp = lookup_sort_params(p->tables);
+    const size_t nb = (size_t)sp.n_materials * sp.n_ebuckets;
+    if (p->lbins_cap < nb + 1) {
+        dev_free(p->lbins);
+        TRY(dev_alloc(&p->lbins, nb + 1));
+        p->lbins_cap = nb + 1;
+    }
+    if (launch_lookup_sort(sp, n, E, mat, p->lbins, perm, lookup_grid(p), st))
+        return fail(MCX_ERR_CUDA, "lookup sort launch failed");
+    return MCX_OK;
+}
+
+// Lookup on device buffers, queued on `st`, in the order `perm` (or natural).
+int lookup_device_ordered(mcx_problem* p, int64_t n, const double* E, const int32_t* mat,
+                          const int32_t* perm, double* out, int32_t flags, cudaStream_t st)
 {
     const TableStore* ts = p->tables;
-    const int32_t* perm = nullptr;
-    if (flags & MCX_LOOKUP_SORT) {
-        SortParams sp;
-        sp.n_materials = ts->view.n_materials;
-        sp.n_ebuckets = 1024;
-        while (sp.n_ebuckets > 1 && (size_t)sp.n_materials * sp.n_ebuckets * 4 > 48 * 1024) sp.n_ebuckets >>= 1;
-        sp.ln_lo = (float)std::log(ts->emin);
-        sp.scale = (float)((double)sp.n_ebuckets / (std::log(ts->emax) - std::log(ts->emin)));
-        TRY(ensure_lookup_scratch(p, n, (size_t)sp.n_materials * sp.n_ebuckets));
-        if (launch_lookup_sort(sp, n, E, mat, p->lbins, p->perm, lookup_grid(p), st))
-            return fail(MCX_ERR_CUDA, "lookup sort launch failed");
-        perm = p->perm;
-    }
     int r = (flags & MCX_LOOKUP_FAST)
                 ? launch_xs_lookup_fast(ts->view, ts->mden32, n, E, mat, perm, out, lookup_grid(p), st)
                 : launch_xs_lookup_exact(ts->view, n, E, mat, perm, out, lookup_grid(p), st);
     if (r) return fail(MCX_ERR_CUDA, "lookup launch failed: %s", cudaGetErrorString(cudaGetLastError()));
     return MCX_OK;
+}
+
+// Lookup on device buffers, queued on `st` (binned first with MCX_LOOKUP_SORT).
+int lookup_device(mcx_problem* p, int64_t n, const double* E, const int32_t* mat, double* out,
+                  int32_t flags, cudaStream_t st)
+{
+    const int32_t* perm = nullptr;
+    if (flags & MCX_LOOKUP_SORT) {
+        TRY(ensure_lookup_scratch(p, n, 0));
+        TRY(sort_device(p, n, E, mat, p->perm, st));
+        perm = p->perm;
+    }
+    return lookup_device_ordered(p, n, E, mat, perm, out, flags & MCX_LOOKUP_FAST, st);
 }
 
 }  // namespace
@@ -624,6 +654,7 @@ void mcx_default_tuning(mcx_tune* t)
     t->iters_per_sync = 16;
     t->max_event_iters = 0;
     t->use_graph = 1;
+    t->time_limit_s = 0.0;
 }
 
 int mcx_init_problem(const mcx_problem_desc* desc, mcx_problem** out)
@@ -750,9 +781,12 @@ int mcx_load_xs_tables(mcx_problem* p, int32_t n_species, const int64_t* goff, c
         emax = std::fmax(emax, energies[goff[s + 1] - 1]);
         if (!(awr[s] >= 1.0) || !is_finite(awr[s])) return fail(MCX_ERR_ARG, "awr[%d] must be >= 1", s);
     }
-    for (int64_t i = 0; i < P * n_ch; ++i)
+    for (int64_t i = 0; i < P * n_ch; ++i) {
         if (!(sigma[i] >= 0.0) || !is_finite(sigma[i]))
             return fail(MCX_ERR_ARG, "sigma[%lld] must be finite and >= 0", (long long)i);
+        if (precision == MCX_FP32 && !(sigma[i] <= 3.4028234663852886e38))
+            return fail(MCX_ERR_ARG, "sigma[%lld] exceeds the FP32 range", (long long)i);
+    }
     if (moff[0] != 0) return fail(MCX_ERR_ARG, "mat_offsets[0] must be 0");
     int32_t maxs = 0;
     for (int m = 0; m < n_materials; ++m) {
@@ -895,6 +929,20 @@ int mcx_set_densities(mcx_problem* p, const double* mden, int64_t nnz)
     return MCX_OK;
 }
 
+int mcx_update_tables_device(mcx_problem* p, const double* mat_dens, const double* sigma, void* stream)
+{
+    g_err.clear();
+    TRY(check_tables(p));
+    if (!mat_dens && !sigma) return MCX_OK;
+    TableStore* ts = p->tables;
+    DeviceGuard dg(p->device);
+    if (launch_update_tables(mat_dens, mat_dens ? ts->nnz : 0, ts->mden, ts->mden32, sigma,
+                             sigma ? ts->view.n_points * ts->view.n_ch : 0, ts->sigma, ts->view.precision,
+                             (cudaStream_t)stream))
+        return fail(MCX_ERR_CUDA, "table update launch failed");
+    return MCX_OK;
+}
+
 int mcx_set_tuning(mcx_problem* p, const mcx_tune* t)
 {
     g_err.clear();
@@ -907,6 +955,7 @@ int mcx_set_tuning(mcx_problem* p, const mcx_tune* t)
     if (t->sort_threshold < 0) return fail(MCX_ERR_ARG, "sort_threshold must be >= 0");
     if (t->iters_per_sync < 1 || t->iters_per_sync > 4096) return fail(MCX_ERR_ARG, "iters_per_sync out of range");
     if (t->max_event_iters < 0) return fail(MCX_ERR_ARG, "max_event_iters must be >= 0");
+    if (!(t->time_limit_s >= 0.0)) return fail(MCX_ERR_ARG, "time_limit_s must be >= 0");
     p->tune = *t;
     p->tune.use_graph = t->use_graph ? 1 : 0;
     return MCX_OK;
@@ -1046,6 +1095,31 @@ int mcx_xs_lookup(mcx_problem* p, int64_t n, const double* E, const int32_t* mat
     if (!E || !mat || !out) return fail(MCX_ERR_ARG, "NULL buffer");
     DeviceGuard dg(p->device);
     return lookup_device(p, n, E, mat, out, flags, (cudaStream_t)stream);
+}
+
+int mcx_xs_sort(mcx_problem* p, int64_t n, const double* E, const int32_t* mat, int32_t* perm,
+                void* stream)
+{
+    g_err.clear();
+    TRY(check_tables(p));
+    if (n < 0 || n >= ((int64_t)1 << 31)) return fail(MCX_ERR_ARG, "n out of range");
+    if (n == 0) return MCX_OK;
+    if (!E || !mat || !perm) return fail(MCX_ERR_ARG, "NULL buffer");
+    DeviceGuard dg(p->device);
+    return sort_device(p, n, E, mat, perm, (cudaStream_t)stream);
+}
+
+int mcx_xs_lookup_ordered(mcx_problem* p, int64_t n, const double* E, const int32_t* mat,
+                          const int32_t* perm, double* out, int32_t flags, void* stream)
+{
+    g_err.clear();
+    TRY(check_tables(p));
+    if (n < 0 || n >= ((int64_t)1 << 31)) return fail(MCX_ERR_ARG, "n out of range");
+    if (flags & ~MCX_LOOKUP_FAST) return fail(MCX_ERR_ARG, "flags may hold MCX_LOOKUP_FAST only");
+    if (n == 0) return MCX_OK;
+    if (!E || !mat || !out) return fail(MCX_ERR_ARG, "NULL buffer");
+    DeviceGuard dg(p->device);
+    return lookup_device_ordered(p, n, E, mat, perm, out, flags, (cudaStream_t)stream);
 }
 
 int mcx_xs_lookup_host(mcx_problem* p, int64_t n, const double* E_host, const int32_t* mat_host,

@@ -100,6 +100,13 @@ __host__ __device__ __forceinline__ uint2 rng_key(uint64_t seed, uint32_t proble
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int64_t ebits(double x) { return __double_as_longlong(x); }
 
+// Search key of a lookup energy: its bit pattern, or the lowest key for NaN
+// (so a NaN energy takes grid index 0, as E < g[0] does).
+__device__ __forceinline__ int64_t search_key(double E)
+{
+    return E != E ? (int64_t)0x8000000000000000LL : ebits(E);
+}
+
 // Largest k in [lo, hi] with g[k] <= E (lo if none).  Requires the answer of
 // the full search to lie in [lo, hi].
 __device__ __forceinline__ int64_t bsearch_window(const double* __restrict__ g, int64_t lo,
@@ -117,7 +124,7 @@ __device__ __forceinline__ int64_t bsearch_window(const double* __restrict__ g, 
 // [0, H-1]).  The float logarithm only proposes a bin; two comparisons with
 // the stored FP64 boundaries fix it, so the bin is exact whatever the
 // rounding of logf.
-__device__ __forceinline__ int32_t hash_bin(const Tables& t, double E)
+__device__ __forceinline__ int32_t hash_bin(const Tables& t, double E, int64_t eb)
 {
     const float lf = logf((float)E);
     float fb = (lf - t.hash_ln_lo) * t.hash_scale;
@@ -125,17 +132,17 @@ __device__ __forceinline__ int32_t hash_bin(const Tables& t, double E)
     if (!(fb >= 0.f)) b = 0;                       // also NaN, -inf, tiny E
     else if (fb >= (float)(t.H - 1)) b = t.H - 1;
     else b = (int32_t)fb;
-    const int64_t eb = ebits(E);
     // at most a couple of steps: the float estimate is within a bin or two
     while (b > 0 && eb < ebits(__ldg(t.hbound + b))) --b;
     while (b < t.H - 1 && eb >= ebits(__ldg(t.hbound + b + 1))) ++b;
     return b;
 }
 
-// Grid index of species s at E: the largest k in [0, n-2] with g[k] <= E,
-// k = 0 below the grid or for NaN, n-2 at or above its top.
-__device__ __forceinline__ int64_t species_index(const Tables& t, int32_t s, double E,
-                                                 int64_t eb, int32_t hbin)
+// Grid index of species s for search key eb = search_key(E): the largest k
+// in [0, n-2] with g[k] <= E, k = 0 below the grid or for NaN, n-2 at or
+// above its top.
+__device__ __forceinline__ int64_t species_index(const Tables& t, int32_t s, int64_t eb,
+                                                 int32_t hbin)
 {
     const int64_t base = __ldg(t.goff + s);
     const int64_t n = __ldg(t.goff + s + 1) - base;
@@ -145,15 +152,37 @@ __device__ __forceinline__ int64_t species_index(const Tables& t, int32_t s, dou
         lo = __ldg(h);
         hi = __ldg(h + 1);
     }
-    int64_t k = bsearch_window(t.E + base, lo, hi, eb);
-    if (E != E) k = 0;
-    return k;
+    return bsearch_window(t.E + base, lo, hi, eb);
+}
+
+// Exact FP32 -> FP64 widening with integer operations.  Table entries are
+// validated finite and >= 0 at load time, so the sign bit is clear and the
+// exponent field is below 255; a normal float 1.m * 2^(e-127) becomes the
+// double with exponent field e + 896 and the 23 mantissa bits on top of the
+// 52.  Zero and subnormals take the conversion instruction.  This keeps the
+// widening off B300's FP64 pipe, which the FP64 arithmetic already saturates.
+__device__ __forceinline__ double widen_f32(float f)
+{
+    const uint32_t u = __float_as_uint(f);
+    const uint32_t e = u >> 23;
+    if (e == 0u) return u == 0u ? 0.0 : (double)f;
+    const uint32_t hi = ((e + 896u) << 20) | ((u & 0x7FFFFFu) >> 3);
+    return __hiloint2double((int)hi, (int)(u << 29));
 }
 
 template <typename T>
-__device__ __forceinline__ double sig_at(const void* sigma, int64_t i)
+__device__ __forceinline__ double sig_at(const void* sigma, int64_t i);
+
+template <>
+__device__ __forceinline__ double sig_at<double>(const void* sigma, int64_t i)
 {
-    return (double)__ldg(static_cast<const T*>(sigma) + i);
+    return __ldg(static_cast<const double*>(sigma) + i);
+}
+
+template <>
+__device__ __forceinline__ double sig_at<float>(const void* sigma, int64_t i)
+{
+    return widen_f32(__ldg(static_cast<const float*>(sigma) + i));
 }
 
 }  // namespace mcx

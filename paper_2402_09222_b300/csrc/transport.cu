@@ -607,14 +607,14 @@ __global__ void __launch_bounds__(1024) k_collide(LoopConfig c, Tables t, Partic
             const double E = P.E[slot];
             const int32_t m = P.mat[slot];
             const double target = xi1 * P.sig_t[slot];
-            const int64_t eb = ebits(E);
-            const int32_t hb = t.H > 0 ? hash_bin(t, E) : 0;
+            const int64_t eb = search_key(E);
+            const int32_t hb = t.H > 0 ? hash_bin(t, E, eb) : 0;
             double cum = 0.0, ss_j = 0.0, sa_j = 0.0;
             int32_t j = 0;
             const int32_t i0 = __ldg(t.moff + m), i1 = __ldg(t.moff + m + 1);
             for (int32_t ii = i0; ii < i1; ++ii) {
                 const int32_t s = __ldg(t.msp + ii);
-                const int64_t k = species_index(t, s, E, eb, hb);
+                const int64_t k = species_index(t, s, eb, hb);
                 const int64_t p = __ldg(t.goff + s) + k;
                 const double f = fraction_exact(E, __ldg(t.E + p), __ldg(t.E + p + 1));
                 ss_j = interp_exact(sig_at<T>(t.sigma, p * nc + cs), sig_at<T>(t.sigma, (p + 1) * nc + cs), f);

@@ -27,13 +27,13 @@ __global__ void __launch_bounds__(256) k_xs_lookup_exact(Tables t, int64_t n,
             for (int r = 0; r < nc; ++r) out[l * nc + r] = __longlong_as_double(0x7ff8000000000000LL);
             continue;
         }
-        const int64_t eb = ebits(E);
-        const int32_t hb = t.H > 0 ? hash_bin(t, E) : 0;
+        const int64_t eb = search_key(E);
+        const int32_t hb = t.H > 0 ? hash_bin(t, E, eb) : 0;
         const int32_t i0 = __ldg(t.moff + m), i1 = __ldg(t.moff + m + 1);
         for (int32_t i = i0; i < i1; ++i) {
             const int32_t s = __ldg(t.msp + i);
             const double N = __ldg(t.mden + i);
-            const int64_t k = species_index(t, s, E, eb, hb);
+            const int64_t k = species_index(t, s, eb, hb);
             const int64_t p = __ldg(t.goff + s) + k;
             const double f = fraction_exact(E, __ldg(t.E + p), __ldg(t.E + p + 1));
 #pragma unroll
@@ -61,11 +61,11 @@ __global__ void k_xs_indices(Tables t, int64_t n, const double* __restrict__ Ein
         const int32_t m = mat[l];
         const bool ok = m >= 0 && m < t.n_materials;
         const int32_t i0 = ok ? t.moff[m] : 0, cnt = ok ? t.moff[m + 1] - i0 : 0;
-        const int64_t eb = ebits(E);
-        const int32_t hb = t.H > 0 ? hash_bin(t, E) : 0;
+        const int64_t eb = search_key(E);
+        const int32_t hb = t.H > 0 ? hash_bin(t, E, eb) : 0;
         for (int32_t i = 0; i < max_species; ++i)
             kout[l * max_species + i] =
-                i < cnt ? (int32_t)species_index(t, t.msp[i0 + i], E, eb, hb) : -1;
+                i < cnt ? (int32_t)species_index(t, t.msp[i0 + i], eb, hb) : -1;
     }
 }
 
@@ -80,6 +80,38 @@ __global__ void k_build_hash(Tables t, int32_t* __restrict__ hidx)
         const int64_t base = t.goff[s], n = t.goff[s + 1] - base;
         hidx[q] = (int32_t)bsearch_window(t.E + base, 0, n - 2, ebits(t.hbound[b]));
     }
+}
+
+// Copy new densities (with their FP32 mirror) and cross sections (rounded
+// to the table precision) from device buffers.
+__global__ void k_update_tables(const double* __restrict__ dens_src, int64_t nnz,
+                                double* __restrict__ mden, float* __restrict__ mden32,
+                                const double* __restrict__ sig_src, int64_t n_sig,
+                                void* __restrict__ sigma, int precision)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nnz || i < n_sig; i += stride) {
+        if (dens_src && i < nnz) {
+            mden[i] = dens_src[i];
+            mden32[i] = (float)dens_src[i];
+        }
+        if (sig_src && i < n_sig) {
+            if (precision == MCX_FP32) static_cast<float*>(sigma)[i] = (float)sig_src[i];
+            else static_cast<double*>(sigma)[i] = sig_src[i];
+        }
+    }
+}
+
+int launch_update_tables(const double* dens_src, int64_t nnz, double* mden, float* mden32,
+                         const double* sig_src, int64_t n_sig, void* sigma, int precision,
+                         cudaStream_t st)
+{
+    const int64_t n = nnz > n_sig ? nnz : n_sig;
+    int grid = (int)((n + 255) / 256);
+    if (grid > 4096) grid = 4096;
+    if (grid < 1) grid = 1;
+    k_update_tables<<<grid, 256, 0, st>>>(dens_src, nnz, mden, mden32, sig_src, n_sig, sigma, precision);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 int launch_xs_lookup_exact(const Tables& t, int64_t n, const double* E, const int32_t* mat,

@@ -31,15 +31,15 @@ template <typename T>
 __device__ __forceinline__ void macro_transport(const Tables& t, int32_t m, double E,
                                                 double& sig_t, double& sig_a)
 {
-    const int64_t eb = ebits(E);
-    const int32_t hb = t.H > 0 ? hash_bin(t, E) : 0;
+    const int64_t eb = search_key(E);
+    const int32_t hb = t.H > 0 ? hash_bin(t, E, eb) : 0;
     const int32_t i0 = __ldg(t.moff + m), i1 = __ldg(t.moff + m + 1);
     const int32_t nc = t.n_ch, cs = t.ch_scatter, ca = t.ch_absorb;
     double st = 0.0, sa = 0.0;
     for (int32_t i = i0; i < i1; ++i) {
         const int32_t s = __ldg(t.msp + i);
         const double N = __ldg(t.mden + i);
-        const int64_t k = species_index(t, s, E, eb, hb);
+        const int64_t k = species_index(t, s, eb, hb);
         const int64_t p = __ldg(t.goff + s) + k;
         const double f = fraction_exact(E, __ldg(t.E + p), __ldg(t.E + p + 1));
         const double ss = interp_exact(sig_at<T>(t.sigma, p * nc + cs),

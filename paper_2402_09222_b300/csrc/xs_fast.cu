@@ -50,13 +50,13 @@ __global__ void __launch_bounds__(256) k_xs_lookup_fast(Tables t, const float* _
             continue;
         }
         float hi[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, lo[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-        const int64_t eb = ebits(E);
-        const int32_t hb = t.H > 0 ? hash_bin(t, E) : 0;
+        const int64_t eb = search_key(E);
+        const int32_t hb = t.H > 0 ? hash_bin(t, E, eb) : 0;
         const int32_t i0 = __ldg(t.moff + m), i1 = __ldg(t.moff + m + 1);
         for (int32_t i = i0; i < i1; ++i) {
             const int32_t s = __ldg(t.msp + i);
             const float N = __ldg(mden32 + i);
-            const int64_t k = species_index(t, s, E, eb, hb);
+            const int64_t k = species_index(t, s, eb, hb);
             const int64_t p = __ldg(t.goff + s) + k;
             const float a = fmaxf((float)(E - __ldg(t.E + p)), 0.f);
             const float b = fmaxf((float)(__ldg(t.E + p + 1) - E), 0.f);

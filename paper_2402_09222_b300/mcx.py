@@ -19,7 +19,8 @@ LIB_PATH = os.path.join(_HERE, "libmcx.so")
 
 MCX_OK = 0
 ERR_NAMES = {-1: "MCX_ERR_ARG", -2: "MCX_ERR_CUDA", -3: "MCX_ERR_OOM", -4: "MCX_ERR_ITER_LIMIT",
-             -5: "MCX_ERR_STATE", -6: "MCX_ERR_BOUNDS"}
+             -5: "MCX_ERR_STATE", -6: "MCX_ERR_BOUNDS", -7: "MCX_ERR_TIMEOUT"}
+ERR_ITER_LIMIT, ERR_TIMEOUT = -4, -7
 FP64, FP32 = 0, 1
 QUEUELESS, QUEUED = 0, 1
 LOOKUP_EXACT, LOOKUP_FAST, LOOKUP_SORT = 0, 1, 2
@@ -59,7 +60,8 @@ class ProblemDesc(C.Structure):
 class Tune(C.Structure):
     _fields_ = [("mode", C.c_int32), ("block_size", C.c_int32), ("sort_period", C.c_int32),
                 ("sort_threshold", C.c_int64), ("iters_per_sync", C.c_int32),
-                ("max_event_iters", C.c_int64), ("use_graph", C.c_int32)]
+                ("max_event_iters", C.c_int64), ("use_graph", C.c_int32),
+                ("time_limit_s", C.c_double)]
 
 
 def _sig(name, res, *args):
@@ -77,6 +79,7 @@ _sig("mcx_load_xs_tables", C.c_int, _vp, _i32, _vp, _vp, _vp, _i32, _vp, _i32, _
 _sig("mcx_share_xs_tables", C.c_int, _vp, _vp)
 _sig("mcx_set_hash_bins", C.c_int, _vp, _i32)
 _sig("mcx_set_densities", C.c_int, _vp, _vp, _i64)
+_sig("mcx_update_tables_device", C.c_int, _vp, _vp, _vp, _vp)
 _sig("mcx_default_tuning", None, C.POINTER(Tune))
 _sig("mcx_set_tuning", C.c_int, _vp, C.POINTER(Tune))
 _sig("mcx_run_batch", C.c_int, _vp, _i64, _i64, _i64, C.c_uint64, _vp)
@@ -87,6 +90,8 @@ _sig("mcx_zero_tallies", C.c_int, _vp)
 _sig("mcx_read_history_debug", C.c_int, _vp, _vp, _i64)
 _sig("mcx_last_run_stats", C.c_int, _vp, _vp, _i32)
 _sig("mcx_xs_lookup", C.c_int, _vp, _i64, _vp, _vp, _vp, _i32, _vp)
+_sig("mcx_xs_sort", C.c_int, _vp, _i64, _vp, _vp, _vp, _vp)
+_sig("mcx_xs_lookup_ordered", C.c_int, _vp, _i64, _vp, _vp, _vp, _vp, _i32, _vp)
 _sig("mcx_xs_lookup_host", C.c_int, _vp, _i64, _vp, _vp, _vp, _i32)
 _sig("mcx_xs_indices", C.c_int, _vp, _i64, _vp, _vp, _i32, _vp, _vp)
 _sig("mcx_xs_lookup_backward", C.c_int, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp)
@@ -216,6 +221,17 @@ class Problem:
         d = np.ascontiguousarray(dens, np.float64)
         _check(_lib.mcx_set_densities(self.h, _np_ptr(d), len(d)))
 
+    def update_tables_device(self, dens=None, sigma=None, stream=None):
+        """Replace densities [nnz] and/or cross sections [P][n_ch] from FP64 CUDA tensors."""
+        import torch
+        pd = _vp(0) if dens is None else _dev_ptr(dens, torch.float64, "dens")
+        ps = _vp(0) if sigma is None else _dev_ptr(sigma, torch.float64, "sigma")
+        if dens is not None and dens.numel() != self.nnz:
+            raise ValueError(f"dens must have {self.nnz} entries")
+        if sigma is not None and sigma.numel() != self.n_points * self.n_ch:
+            raise ValueError(f"sigma must have {self.n_points} x {self.n_ch} entries")
+        _check(_lib.mcx_update_tables_device(self.h, pd, ps, _stream_ptr(stream)))
+
     # -- transport
     def set_tuning(self, **kw):
         t = Tune()
@@ -223,7 +239,7 @@ class Problem:
         for k, v in kw.items():
             if not hasattr(t, k):
                 raise KeyError(k)
-            setattr(t, k, int(v))
+            setattr(t, k, float(v) if k == "time_limit_s" else int(v))
         _check(_lib.mcx_set_tuning(self.h, C.byref(t)))
         return self
 
@@ -274,6 +290,28 @@ class Problem:
         _check(_lib.mcx_xs_lookup(self.h, n, _dev_ptr(E, torch.float64, "E"),
                                   _dev_ptr(mat, torch.int32, "mat"),
                                   _dev_ptr(out, torch.float64, "out"), flags, _stream_ptr(stream)))
+        return out
+
+    def xs_sort(self, E, mat, perm=None, stream=None):
+        """Binning permutation of the lookups by (material, log-energy bucket)."""
+        import torch
+        if perm is None:
+            perm = torch.empty(E.numel(), dtype=torch.int32, device=E.device)
+        _check(_lib.mcx_xs_sort(self.h, E.numel(), _dev_ptr(E, torch.float64, "E"),
+                                _dev_ptr(mat, torch.int32, "mat"), _dev_ptr(perm, torch.int32, "perm"),
+                                _stream_ptr(stream)))
+        return perm
+
+    def xs_lookup_ordered(self, E, mat, perm, out=None, flags: int = LOOKUP_EXACT, stream=None):
+        """Lookup processed in the order `perm` (None: natural order)."""
+        import torch
+        n = E.numel()
+        if out is None:
+            out = torch.empty((n, self.n_ch), dtype=torch.float64, device=E.device)
+        pp = _vp(0) if perm is None else _dev_ptr(perm, torch.int32, "perm")
+        _check(_lib.mcx_xs_lookup_ordered(self.h, n, _dev_ptr(E, torch.float64, "E"),
+                                          _dev_ptr(mat, torch.int32, "mat"), pp,
+                                          _dev_ptr(out, torch.float64, "out"), flags, _stream_ptr(stream)))
         return out
 
     def xs_lookup_host(self, E, mat, out=None, flags: int = LOOKUP_EXACT):

@@ -1,0 +1,349 @@
+"""Autotuner for the event loop and the lookup (the role ytopt plays for OpenMC
+in the paper, Sec. 2-5, on this one GPU).
+
+Search space (Table 1 of the paper, mapped to this implementation):
+  mode              queued | queueless                     (P0)
+  particles_in_flight  1e5 .. 8e6, log scale, step 1000     (P1)
+  hash_bins         100 .. 100000, log scale, step 100      (P2)
+  sort_threshold    0 .. 1e6, step 1000; active only in queued mode (P3,
+                    the paper's EqualsCondition(P3, P0, queued))
+  sort_period       0, 1, 2, 4, 8, 16; queued mode only    (this GPU's binning)
+  block_size        64, 128, 256, 512                      (replaces the paper's
+                    host-thread and MPI-rank parameters P4-P6, which have no
+                    counterpart on one GPU)
+
+Strategies:
+  "random+cd"  the minimum tuner: the default configuration as baseline
+               (best of `baseline_repeats` runs, Sec. 5: best of five), then
+               random samples, then coordinate descent from the best point;
+  "bo"         Bayesian optimisation with a random-forest surrogate and the
+               lower-confidence-bound acquisition a(x) = mu(x) - kappa sigma(x),
+               kappa = 1.96 (Sec. 2.1, Eq. 1), minimising run time.
+Every evaluation runs under a time limit of `timeout_factor` x the baseline
+time (Sec. 3: 1.5x); a run that exceeds it is recorded as a timeout with a very
+bad objective and the search continues.  The performance database is a JSONL
+file; an interrupted search resumes without repeating recorded evaluations.
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+import random
+import time
+from dataclasses import dataclass, field
+from typing import Callable
+
+QUEUELESS, QUEUED = 0, 1
+
+
+@dataclass
+class Param:
+    name: str
+    kind: str                    # "int_log" | "int" | "choice"
+    lo: float = 0
+    hi: float = 0
+    q: int = 1
+    choices: tuple = ()
+    default: object = None
+    active_if: tuple | None = None   # (other_param, value)
+
+    def sample(self, rng: random.Random):
+        if self.kind == "choice":
+            return rng.choice(self.choices)
+        if self.kind == "int_log":
+            v = math.exp(rng.uniform(math.log(self.lo), math.log(self.hi)))
+        else:
+            v = rng.uniform(self.lo, self.hi)
+        return self.quantise(v)
+
+    def quantise(self, v):
+        if self.kind == "choice":
+            return v
+        v = int(round(v / self.q)) * self.q
+        return int(min(max(v, self.lo), self.hi))
+
+    def neighbours(self, v):
+        """Values one coordinate step away (for coordinate descent)."""
+        if self.kind == "choice":
+            return [c for c in self.choices if c != v]
+        if self.kind == "int_log":
+            return sorted({self.quantise(v * 2), self.quantise(v / 2)} - {v})
+        step = max(self.q, (self.hi - self.lo) / 8)
+        return sorted({self.quantise(v + step), self.quantise(v - step)} - {v})
+
+    def encode(self, v) -> float:
+        """Numeric feature for the surrogate."""
+        if self.kind == "choice":
+            return float(self.choices.index(v))
+        if self.kind == "int_log":
+            return math.log(max(v, 1))
+        return float(v)
+
+
+def transport_space(max_in_flight: int = 8_000_000) -> list[Param]:
+    return [
+        Param("mode", "choice", choices=(QUEUED, QUEUELESS), default=QUEUED),
+        Param("particles_in_flight", "int_log", 100_000, max_in_flight, 1000, default=1_000_000),
+        Param("hash_bins", "int_log", 100, 100_000, 100, default=4000),
+        Param("sort_threshold", "int", 0, 1_000_000, 1000, default=20_000, active_if=("mode", QUEUED)),
+        Param("sort_period", "choice", choices=(0, 1, 2, 4, 8, 16), default=4, active_if=("mode", QUEUED)),
+        Param("block_size", "choice", choices=(64, 128, 256, 512), default=256),
+    ]
+
+
+def lookup_space() -> list[Param]:
+    return [
+        Param("hash_bins", "int_log", 100, 100_000, 100, default=4000),
+        Param("binned", "choice", choices=(1, 0), default=1),
+    ]
+
+
+def canonical(space: list[Param], cfg: dict) -> dict:
+    """Inactive conditional parameters are dropped (the paper's 'nan')."""
+    out = {}
+    for p in space:
+        if p.active_if is not None and cfg.get(p.active_if[0]) != p.active_if[1]:
+            continue
+        out[p.name] = cfg[p.name]
+    return out
+
+
+def key_of(cfg: dict) -> str:
+    return json.dumps(cfg, sort_keys=True)
+
+
+@dataclass
+class Record:
+    config: dict
+    seconds: float | None      # None: timed out or failed
+    status: str                # "ok" | "timeout" | "error"
+    kind: str                  # "baseline" | "random" | "cd" | "bo"
+
+
+@dataclass
+class Tuner:
+    """objective(config, time_limit_s) -> seconds, or raises TimeoutError."""
+    space: list[Param]
+    objective: Callable[[dict, float], float]
+    db_path: str | None = None
+    seed: int = 1234
+    timeout_factor: float = 1.5
+    baseline_repeats: int = 5
+    bad_seconds: float = 1e9
+    records: list[Record] = field(default_factory=list)
+
+    def __post_init__(self):
+        self.rng = random.Random(self.seed)
+        self._done: dict[str, Record] = {}
+        if self.db_path and os.path.exists(self.db_path):
+            for line in open(self.db_path):
+                if line.strip():
+                    d = json.loads(line)
+                    r = Record(d["config"], d["seconds"], d["status"], d["kind"])
+                    self.records.append(r)
+                    if r.kind != "baseline":
+                        self._done[key_of(r.config)] = r
+        self.baseline = None
+        base = [r.seconds for r in self.records if r.kind == "baseline" and r.seconds]
+        if len(base) >= self.baseline_repeats:
+            self.baseline = min(base)
+
+    # -- bookkeeping
+    def default_config(self) -> dict:
+        return canonical(self.space, {p.name: p.default for p in self.space})
+
+    def _log(self, r: Record):
+        self.records.append(r)
+        if self.db_path:
+            with open(self.db_path, "a") as f:
+                f.write(json.dumps({"config": r.config, "seconds": r.seconds, "status": r.status,
+                                    "kind": r.kind, "time": time.time()}) + "\n")
+
+    def evaluate(self, cfg: dict, kind: str) -> Record:
+        cfg = canonical(self.space, cfg)
+        k = key_of(cfg)
+        if kind != "baseline" and k in self._done:
+            return self._done[k]
+        limit = self.timeout_factor * self.baseline if (self.baseline and kind != "baseline") else 0.0
+        try:
+            s = float(self.objective(cfg, limit))
+            r = Record(cfg, s, "ok", kind)
+        except TimeoutError:
+            r = Record(cfg, None, "timeout", kind)
+        except Exception as e:  # a configuration the library rejects counts as a failure
+            r = Record(cfg, None, f"error: {e}"[:200], kind)
+        self._log(r)
+        if kind != "baseline":
+            self._done[k] = r
+        return r
+
+    def score(self, r: Record) -> float:
+        return r.seconds if r.seconds is not None else self.bad_seconds
+
+    def best(self) -> Record:
+        cand = [r for r in self.records if r.seconds is not None]
+        return min(cand, key=lambda r: r.seconds)
+
+    # -- strategies
+    def run_baseline(self):
+        have = [r for r in self.records if r.kind == "baseline" and r.seconds]
+        for _ in range(self.baseline_repeats - len(have)):
+            self.evaluate(self.default_config(), "baseline")
+        base = [r.seconds for r in self.records if r.kind == "baseline" and r.seconds]
+        if not base:
+            raise RuntimeError("the default configuration failed")
+        self.baseline = min(base)
+        return self.baseline
+
+    def random_config(self) -> dict:
+        cfg = {p.name: p.sample(self.rng) for p in self.space}
+        return canonical(self.space, cfg)
+
+    def tune(self, n_random: int = 24, max_evals: int = 64, strategy: str = "random+cd") -> Record:
+        if self.baseline is None:
+            self.run_baseline()
+        n_eval = lambda: sum(1 for r in self.records if r.kind != "baseline")
+        if strategy == "bo":
+            return self._bo(n_random, max_evals, n_eval)
+        while n_eval() < min(n_random, max_evals):
+            self.evaluate(self.random_config(), "random")
+        improved = True
+        while improved and n_eval() < max_evals:
+            improved = False
+            cur = self.best()
+            full = {p.name: cur.config.get(p.name, p.default) for p in self.space}
+            for p in self.space:
+                if p.active_if is not None and full.get(p.active_if[0]) != p.active_if[1]:
+                    continue
+                for v in p.neighbours(full[p.name]):
+                    if n_eval() >= max_evals:
+                        break
+                    trial = dict(full)
+                    trial[p.name] = v
+                    r = self.evaluate(trial, "cd")
+                    if r.seconds is not None and r.seconds < cur.seconds:
+                        improved = True
+                        break
+                if improved:
+                    break
+        return self.best()
+
+    def _features(self, cfg: dict) -> list[float]:
+        return [p.encode(cfg.get(p.name, p.default)) for p in self.space]
+
+    def _bo(self, n_init, max_evals, n_eval, kappa: float = 1.96, n_candidates: int = 512):
+        from sklearn.ensemble import RandomForestRegressor
+        while n_eval() < min(n_init, max_evals):
+            self.evaluate(self.random_config(), "random")
+        while n_eval() < max_evals:
+            data = [(self._features(r.config), math.log(self.score(r)))
+                    for r in self.records]
+            X = [d[0] for d in data]
+            y = [d[1] for d in data]
+            rf = RandomForestRegressor(n_estimators=100, random_state=self.rng.randrange(2**31),
+                                       min_samples_leaf=1)
+            rf.fit(X, y)
+            cands = [self.random_config() for _ in range(n_candidates)]
+            best = self.best().config
+            full = {p.name: best.get(p.name, p.default) for p in self.space}
+            for p in self.space:           # local candidates around the incumbent
+                for v in p.neighbours(full[p.name]):
+                    c = dict(full)
+                    c[p.name] = v
+                    cands.append(canonical(self.space, c))
+            cands = [c for c in cands if key_of(c) not in self._done]
+            if not cands:
+                break
+            Xc = [self._features(c) for c in cands]
+            per_tree = [t.predict(Xc) for t in rf.estimators_]
+            mu = [sum(col) / len(col) for col in zip(*per_tree)]
+            sd = [math.sqrt(max(sum((v - m) ** 2 for v in col) / len(col), 0.0))
+                  for col, m in zip(zip(*per_tree), mu)]
+            acq = [m - kappa * s for m, s in zip(mu, sd)]
+            i = min(range(len(cands)), key=lambda j: acq[j])
+            self.evaluate(cands[i], "bo")
+        return self.best()
+
+    def report(self) -> dict:
+        b = self.best()
+        return {"baseline_s": self.baseline, "best_s": b.seconds, "best_config": b.config,
+                "improvement_pct": 100.0 * (self.baseline / b.seconds - 1.0),
+                "evaluations": sum(1 for r in self.records if r.kind != "baseline"),
+                "timeouts": sum(1 for r in self.records if r.status == "timeout")}
+
+
+# ---------------------------------------------------------------------------
+# objectives on the GPU
+# ---------------------------------------------------------------------------
+
+def transport_objective(prob, seed: int = 1, precision: int = 1, device: int = 0,
+                        max_in_flight: int | None = None):
+    """Seconds of one run of `prob` under a configuration (CUDA events around
+    mcx_run_batch).  Raises TimeoutError when the library reports its time
+    limit."""
+    import torch
+    from . import mcx
+    handles = {}
+
+    def objective(cfg: dict, limit: float) -> float:
+        H = cfg["hash_bins"]
+        if H not in handles:
+            handles.clear()
+            handles[H] = mcx.make_problem(prob, precision=precision, hash_bins=H, device=device)
+        p = handles[H]
+        p.set_tuning(mode=cfg["mode"], block_size=cfg["block_size"],
+                     sort_period=cfg.get("sort_period", 0), sort_threshold=cfg.get("sort_threshold", 0),
+                     time_limit_s=limit)
+        pif = cfg["particles_in_flight"]
+        if max_in_flight:
+            pif = min(pif, max_in_flight)
+        p.zero_tallies()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        try:
+            p.run(particles_in_flight=pif, seed=seed)
+        except mcx.McxError as e:
+            if e.code == mcx.ERR_TIMEOUT:
+                raise TimeoutError(str(e)) from e
+            raise
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / 1e3
+
+    return objective
+
+
+def lookup_objective(lib, mats, E, mat, precision: int = 1, device: int = 0, fast: bool = True):
+    """Seconds of one binned-or-not lookup pass over device inputs E, mat."""
+    import torch
+    from . import mcx
+    dE = torch.as_tensor(E, device=f"cuda:{device}")
+    dm = torch.as_tensor(mat, device=f"cuda:{device}")
+    out = torch.empty((len(E), lib.n_ch), dtype=torch.float64, device=dE.device)
+    perm = torch.empty(len(E), dtype=torch.int32, device=dE.device)
+    h = mcx.Problem(None, device=device).load_tables(lib, mats, precision=precision, hash_bins=4000)
+    state = {"H": 4000}
+
+    def objective(cfg: dict, limit: float) -> float:
+        if cfg["hash_bins"] != state["H"]:
+            h.set_hash_bins(cfg["hash_bins"])
+            state["H"] = cfg["hash_bins"]
+        flags = mcx.LOOKUP_FAST if fast else mcx.LOOKUP_EXACT
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        if cfg["binned"]:
+            h.xs_sort(dE, dm, perm)
+            h.xs_lookup_ordered(dE, dm, perm, out=out, flags=flags)
+        else:
+            h.xs_lookup_ordered(dE, dm, None, out=out, flags=flags)
+        b.record()
+        torch.cuda.synchronize()
+        s = a.elapsed_time(b) / 1e3
+        if limit and s > limit:
+            raise TimeoutError(f"{s:.3f} s > {limit:.3f} s")
+        return s
+
+    return objective

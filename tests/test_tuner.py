@@ -1,0 +1,116 @@
+"""Host logic of the autotuner: search space and conditional, baseline as
+best of repeats, time limit, resumable database, and that both strategies find
+the optimum of a synthetic objective (no GPU needed)."""
+import json
+import math
+
+import pytest
+
+from paper_2402_09222_b300 import tuner
+
+
+def synthetic_objective(calls=None, timeout_above=None):
+    """Run time with an optimum at queued, 2e6 in flight, 20000 bins, period 2."""
+    def f(cfg, limit):
+        if calls is not None:
+            calls.append(dict(cfg))
+        t = 1.0
+        t += 0.3 * (cfg["mode"] != tuner.QUEUED)
+        t += 0.2 * abs(math.log(cfg["particles_in_flight"] / 2e6))
+        t += 0.1 * abs(math.log(cfg["hash_bins"] / 2e4))
+        if cfg["mode"] == tuner.QUEUED:
+            t += 0.05 * abs(cfg["sort_period"] - 2)
+        t += 0.02 * (cfg["block_size"] != 256)
+        if limit and t > limit:
+            raise TimeoutError
+        return t
+    return f
+
+
+def test_space_defaults_and_condition():
+    space = tuner.transport_space()
+    d = {p.name: p.default for p in space}
+    assert d["mode"] == tuner.QUEUED and d["particles_in_flight"] == 1_000_000
+    assert d["hash_bins"] == 4000 and d["sort_threshold"] == 20_000
+    c = tuner.canonical(space, dict(d, mode=tuner.QUEUELESS))
+    assert "sort_threshold" not in c and "sort_period" not in c
+    c = tuner.canonical(space, d)
+    assert c["sort_threshold"] == 20_000
+    import random
+    rng = random.Random(0)
+    for p in space:
+        for _ in range(50):
+            v = p.sample(rng)
+            if p.kind != "choice":
+                assert p.lo <= v <= p.hi and v % p.q == 0
+
+
+def test_baseline_is_best_of_five_and_limit_is_one_and_a_half(tmp_path):
+    calls = []
+    seen_limits = []
+    f = synthetic_objective(calls)
+
+    def obj(cfg, limit):
+        seen_limits.append(limit)
+        return f(cfg, limit)
+
+    t = tuner.Tuner(tuner.transport_space(), obj, db_path=str(tmp_path / "db.jsonl"))
+    base = t.run_baseline()
+    assert len(calls) == 5 and seen_limits == [0.0] * 5
+    t.evaluate(t.random_config(), "random")
+    assert seen_limits[-1] == pytest.approx(1.5 * base)
+
+
+def test_random_plus_coordinate_descent_finds_the_optimum(tmp_path):
+    t = tuner.Tuner(tuner.transport_space(), synthetic_objective(), db_path=str(tmp_path / "db.jsonl"),
+                    seed=3)
+    best = t.tune(n_random=24, max_evals=120)
+    assert best.seconds < 1.12
+    assert best.config["mode"] == tuner.QUEUED
+    rep = t.report()
+    assert rep["improvement_pct"] > 0 and rep["evaluations"] <= 120
+
+
+def test_timeouts_are_recorded_and_the_search_continues(tmp_path):
+    t = tuner.Tuner(tuner.transport_space(), synthetic_objective(), seed=5, timeout_factor=1.05,
+                    db_path=str(tmp_path / "db.jsonl"))
+    t.tune(n_random=20, max_evals=30)
+    assert any(r.status == "timeout" for r in t.records)
+    assert t.best().seconds is not None
+
+
+def test_database_resumes_without_repeating(tmp_path):
+    db = str(tmp_path / "db.jsonl")
+    calls = []
+    t1 = tuner.Tuner(tuner.transport_space(), synthetic_objective(calls), db_path=db, seed=7)
+    t1.tune(n_random=10, max_evals=10)
+    n1 = len(calls)
+    lines = [json.loads(l) for l in open(db)]
+    assert len(lines) == n1
+    calls2 = []
+    t2 = tuner.Tuner(tuner.transport_space(), synthetic_objective(calls2), db_path=db, seed=7)
+    assert t2.baseline == t1.baseline
+    t2.tune(n_random=10, max_evals=14)
+    assert len(calls2) == 4            # only the new evaluations ran
+    keys = [tuner.key_of(c) for c in calls2]
+    old = {tuner.key_of(r.config) for r in t1.records if r.kind != "baseline"}
+    assert not (set(keys) & old)
+
+
+def test_bayesian_optimisation_with_random_forest_and_lcb(tmp_path):
+    t = tuner.Tuner(tuner.transport_space(), synthetic_objective(), seed=11,
+                    db_path=str(tmp_path / "db.jsonl"))
+    best = t.tune(n_random=12, max_evals=60, strategy="bo")
+    assert best.seconds < 1.2
+    assert any(r.kind == "bo" for r in t.records)
+
+
+def test_rejected_configurations_count_as_failures(tmp_path):
+    def obj(cfg, limit):
+        if cfg["block_size"] == 512:
+            raise ValueError("rejected")
+        return 1.0 + cfg["particles_in_flight"] * 1e-9
+    t = tuner.Tuner(tuner.transport_space(), obj, seed=2)
+    t.tune(n_random=16, max_evals=16)
+    assert all(r.seconds is not None or r.status.startswith("error") or r.status == "timeout"
+               for r in t.records)
