@@ -3,7 +3,7 @@
  * macroscopic cross-section lookup on one NVIDIA B300 (sm_103a).
  *
  * Paper: "Integrating ytopt and libEnsemble to Autotune OpenMC" (arXiv
- * 2402.09222).  Sec. 4.1 describes what is computed here: OpenMC's
+ * 2402.09222).  Sec. 5.1 describes what is computed here: OpenMC's
  * event-based mode, a buffer of particles in flight refilled after each
  * kernel call, the macroscopic cross-section lookup ("the most expensive
  * kernel": a search of every species' energy grid, narrowed by a logarithmic
@@ -53,7 +53,7 @@ extern "C" {
 #define MCX_FP64 0
 #define MCX_FP32 1
 
-/* Event logic (Sec. 4.1, "queuing logic"). */
+/* Event logic (Sec. 5.1, "queuing logic"). */
 #define MCX_QUEUELESS 0 /* every event kernel visits every slot */
 #define MCX_QUEUED 1    /* kernels visit device-built compacted queues */
 
@@ -146,7 +146,7 @@ typedef struct {
  * Errors: MCX_ERR_ARG, MCX_ERR_CUDA, MCX_ERR_OOM. */
 int mcx_init_problem(const mcx_problem_desc* desc, mcx_problem** out);
 
-/* Load the species library and materials (Sec. 4.1: per-species energy grids
+/* Load the species library and materials (Sec. 5.1: per-species energy grids
  * and reaction cross sections; materials as lists of species with atom
  * densities).  HOST pointers, copied:
  *   grid_offsets [n_species+1]  species s owns points [off[s], off[s+1]),
@@ -199,7 +199,7 @@ void mcx_default_tuning(mcx_tune* t);
 int mcx_set_tuning(mcx_problem* p, const mcx_tune* t);
 
 /* Run histories [first_history, first_history + n_histories) of the problem
- * with a buffer of `particles_in_flight` slots (Sec. 4.1: dead slots are
+ * with a buffer of `particles_in_flight` slots (Sec. 5.1: dead slots are
  * refilled from the remaining histories after every event iteration; the
  * count does not change any history).  Scores add to the problem's tallies.
  * Random numbers: Philox4x32-10 keyed by (seed, problem_id), one stream per
@@ -235,7 +235,7 @@ int mcx_read_history_debug(mcx_problem* p, uint32_t* ncoll, int64_t n);
  * launches, out[2] kernel launches.  HOST pointer, n >= 3. */
 int mcx_last_run_stats(const mcx_problem* p, int64_t* out, int32_t n);
 
-/* Macroscopic cross-section lookup (Sec. 4.1, "the most expensive kernel"):
+/* Macroscopic cross-section lookup (Sec. 5.1, "the most expensive kernel"):
  *   out[l][r] = sum over the species i of material mat[l] of
  *               N_i * sigma_{r,i}(E[l]),  r = 0..n_ch-1,
  * where sigma_{r,i} interpolates species i's table linearly in energy on the
@@ -252,7 +252,7 @@ int mcx_last_run_stats(const mcx_problem* p, int64_t* out, int32_t n);
 int mcx_xs_lookup(mcx_problem* p, int64_t n, const double* E, const int32_t* mat, double* out,
                   int32_t flags, void* stream);
 
-/* Binning of lookups by material and energy (Sec. 4.1: sorting so that
+/* Binning of lookups by material and energy (Sec. 5.1: sorting so that
  * neighbouring threads work on the same material and nearby energies):
  * perm (int32 [n], DEVICE) receives 0..n-1 ordered by (material, bucket of
  * log E) with 1024 buckets per material (fewer when materials x buckets would

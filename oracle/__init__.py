@@ -1,5 +1,5 @@
 """CPU FP64 oracle for the macroscopic cross-section lookup and the event-based
-transport it sits in (arXiv 2402.09222, Sec. 4.1).
+transport it sits in (arXiv 2402.09222, Sec. 5.1).
 
 TEST INFRASTRUCTURE ONLY: the test suite, the smoke check and the benchmark's
 CPU-baseline leg are the only callers.  The CUDA library never imports, links

@@ -9,7 +9,7 @@
  * operation is the IEEE binary64 operation written in the source (no fused
  * multiply-add contraction, no reassociation).
  *
- * What it computes (paper: arXiv 2402.09222, Sec. 4.1, the description of the
+ * What it computes (paper: arXiv 2402.09222, Sec. 5.1, the description of the
  * tunable parameters of OpenMC's event-based mode):
  *   - the macroscopic cross-section lookup, "the most expensive kernel":
  *     for every species of a material, find the energy-grid interval that
@@ -115,7 +115,7 @@ void orc_uniforms(uint64_t seed, uint32_t problem_id, uint64_t hist, uint32_t fi
 }
 
 /* ------------------------------------------------------------------------ */
-/* Grid search and interpolation (Sec. 4.1, hash-grid paragraph: a search of  */
+/* Grid search and interpolation (Sec. 5.1, hash-grid paragraph: a search of  */
 /* each species' energy grid, then interpolation).                            */
 /* ------------------------------------------------------------------------ */
 

@@ -1,5 +1,5 @@
 """B300-native event-based Monte Carlo transport and macroscopic cross-section
-lookup (the computation autotuned in arXiv 2402.09222, Sec. 4.1).
+lookup (the computation autotuned in arXiv 2402.09222, Sec. 5.1).
 
     from paper_2402_09222_b300 import mcx, synth
     prob = synth.config3_problem(n_histories=100_000)

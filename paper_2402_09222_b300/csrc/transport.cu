@@ -2,7 +2,7 @@
 // --fmad=false: every FP64 expression below is evaluated as written, which
 // keeps per-history decisions identical to a sequential FP64 evaluation).
 //
-// Event-based mode (Sec. 4.1 of the paper): a buffer of particles in flight is
+// Event-based mode (Sec. 5.1 of the paper): a buffer of particles in flight is
 // advanced one event at a time, one kernel per event type over all particles
 // that need it; dead slots are refilled from the remaining histories after
 // every iteration.  One iteration here is

@@ -2,7 +2,7 @@
 // definition is written (include only from translation units compiled with
 // --fmad=false).
 //
-// Per species i of a material (Sec. 4.1, the macroscopic lookup): grid index
+// Per species i of a material (Sec. 5.1, the macroscopic lookup): grid index
 // k_i, fraction f = (E - g[k]) / (g[k+1] - g[k]) clamped to [0, 1], channel
 // value sigma = s[k] + f * (s[k+1] - s[k]); sums run over the species in
 // stored order starting from +0.0.

@@ -6,7 +6,7 @@ none of the method's arithmetic (no grid search, interpolation, sampling or
 tallying), so both the CUDA path and the CPU oracle may consume what it makes.
 
 The paper tunes OpenMC on the Hoogenboom-Martin "large" reactor model
-(Sec. 4.1), whose nuclear data is not available here.  The generators below
+(Sec. 5.1), whose nuclear data is not available here.  The generators below
 stand in for it with the shapes of that problem: a library of a few hundred
 species with ~1e4-point energy grids, materials of 4 to 321 species, and a
 17x17 pin lattice.

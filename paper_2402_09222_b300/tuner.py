@@ -14,7 +14,7 @@ Search space (Table 1 of the paper, mapped to this implementation):
 
 Strategies:
   "random+cd"  the minimum tuner: the default configuration as baseline
-               (best of `baseline_repeats` runs, Sec. 5: best of five), then
+               (best of `baseline_repeats` runs; Sec. 6: best of five), then
                random samples, then coordinate descent from the best point;
   "bo"         Bayesian optimisation with a random-forest surrogate and the
                lower-confidence-bound acquisition a(x) = mu(x) - kappa sigma(x),
