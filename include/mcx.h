@@ -269,6 +269,29 @@ int mcx_xs_sort(mcx_problem* p, int64_t n, const double* E, const int32_t* mat, 
 int mcx_xs_lookup_ordered(mcx_problem* p, int64_t n, const double* E, const int32_t* mat,
                           const int32_t* perm, double* out, int32_t flags, void* stream);
 
+/* The binned lookup (mcx_xs_lookup with MCX_LOOKUP_SORT) for callers that
+ * cannot allocate device memory -- for example a process whose device memory
+ * is reserved up front by another allocator, or a latency-bound loop that
+ * cannot afford cudaMalloc's implicit synchronisation.  The paper has no
+ * counterpart; this is an interface convenience of the library.
+ * Its scratch (binning permutation and bin counters) lives in fixed-size
+ * device arrays of the library, about 4.05 MB per device, created when the
+ * library is loaded onto a device and kept until the process exits; the call
+ * itself allocates nothing.  Inputs and outputs are the caller's DEVICE
+ * buffers, as for mcx_xs_lookup; flags may hold MCX_LOOKUP_FAST.
+ * Limits: n <= MCX_STATIC_MAX_LOOKUPS, and materials x energy buckets <=
+ * MCX_STATIC_MAX_BINS; larger requests fail with MCX_ERR_ARG.
+ * The first call on a device looks up the scratch's device address (a
+ * one-time set-up per device); make that first call before any stream
+ * capture.  All calls on a device share the one scratch: calls that overlap
+ * on the GPU (e.g. on two streams at once) race and give wrong results; order
+ * them on one stream or with events.
+ * Errors: MCX_ERR_ARG, MCX_ERR_STATE, MCX_ERR_CUDA. */
+#define MCX_STATIC_MAX_LOOKUPS 1048576
+#define MCX_STATIC_MAX_BINS 12288
+int mcx_xs_lookup_binned_static(mcx_problem* p, int64_t n, const double* E, const int32_t* mat,
+                                double* out, int32_t flags, void* stream);
+
 /* The same lookup from HOST buffers: copies in, computes and copies out in
  * chunks pipelined over two streams; synchronous.  Host buffers should be
  * pinned (cudaHostAlloc / torch pin_memory) for full copy speed. */

@@ -35,6 +35,22 @@ struct SortParams {
 int launch_lookup_sort(const SortParams& sp, int64_t n, const double* E, const int32_t* mat,
                        uint32_t* bins, int32_t* perm, int grid, cudaStream_t st);
 
+// Tables, FP32 densities and binning parameters of a loaded problem, for
+// entry points defined outside the C-ABI translation unit.
+struct LookupView {
+    Tables tables;
+    const float* mden32 = nullptr;
+    SortParams sort;
+    int device = 0;
+    int grid = 0;
+};
+
+}  // namespace mcx
+struct mcx_problem;
+namespace mcx {
+int problem_lookup_view(const mcx_problem* p, LookupView* v);
+int set_error(int code, const char* msg);
+
 // ------------------------------------------------------------- transport
 enum : uint8_t {
     PF_ALIVE = 1,

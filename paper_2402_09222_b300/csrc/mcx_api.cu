@@ -636,6 +636,23 @@ int lookup_device(mcx_problem* p, int64_t n, const double* E, const int32_t* mat
 
 }  // namespace
 
+// Read-only view of a problem's lookup tables for other translation units of
+// the library (the static-scratch entry point).  Returns MCX_OK or an error.
+namespace mcx {
+int problem_lookup_view(const mcx_problem* p, LookupView* v)
+{
+    TRY(check_tables(p));
+    const TableStore* ts = p->tables;
+    v->tables = ts->view;
+    v->mden32 = ts->mden32;
+    v->sort = lookup_sort_params(ts);
+    v->device = p->device;
+    v->grid = lookup_grid(p);
+    return MCX_OK;
+}
+int set_error(int code, const char* msg) { return fail(code, "%s", msg); }
+}  // namespace mcx
+
 // ===================================================================== ABI
 
 extern "C" {
