@@ -20,15 +20,19 @@ from . import mcx
 class XsLookup(torch.autograd.Function):
     @staticmethod
     def forward(ctx, dens, sigma, handle, E, mat):
-        handle.update_tables_device(dens=dens.detach().contiguous(), sigma=sigma.detach().contiguous())
+        d, s = dens.detach().contiguous(), sigma.detach().contiguous()
+        handle.update_tables_device(dens=d, sigma=s)
         out = handle.xs_lookup(E, mat, flags=mcx.LOOKUP_EXACT)
         ctx.handle = handle
-        ctx.save_for_backward(E, mat)
+        ctx.save_for_backward(E, mat, d, s)
         return out
 
     @staticmethod
     def backward(ctx, grad_out):
-        E, mat = ctx.saved_tensors
+        E, mat, d, s = ctx.saved_tensors
+        # the library's tables may have been overwritten by later forward
+        # calls on the same handle: put back the values this forward used
+        ctx.handle.update_tables_device(dens=d, sigma=s)
         gd, gs = ctx.handle.xs_lookup_backward(E, mat, grad_out.contiguous().to(torch.float64))
         need_d, need_s = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
         return (gd if need_d else None), (gs if need_s else None), None, None, None
