@@ -20,7 +20,7 @@ from . import mcx
 class XsLookup(torch.autograd.Function):
     @staticmethod
     def forward(ctx, dens, sigma, handle, E, mat):
-        d, s = dens.detach().contiguous(), sigma.detach().contiguous()
+        d, s = dens.detach().clone().contiguous(), sigma.detach().clone().contiguous()
         handle.update_tables_device(dens=d, sigma=s)
         out = handle.xs_lookup(E, mat, flags=mcx.LOOKUP_EXACT)
         ctx.handle = handle
