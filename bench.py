@@ -192,6 +192,51 @@ def time_transport(mcx, synth, lib3, spec, seed, reps=1):
             "iterations": st["iterations"], "kernels": st["kernels"]}
 
 
+def time_batched(mcx, synth, seed=9):
+    """64 lattices of uneven size (3x3 .. 17x17, 1e4 .. 2e6 histories) over the
+    12-material set: one event loop over all problems (tuned) against one
+    plain run per problem (FP64, full search, queueless)."""
+    import torch
+    lib = synth.species_library(N_SPECIES, N_POINTS, LIB_SEED).channels([synth.CH_SCATTER, synth.CH_ABSORB])
+    mats = synth.lookup_materials(N_SPECIES, MAT_SEED)
+    probs = synth.config5_problems(lib, mats, n_problems=64)
+    total = sum(p.n_histories for p in probs)
+    res = {"config": f"64 lattices, n in 3..17, {total:,} histories, 12 materials of 4-321 species"}
+    # tuned: one persistent loop, shared FP32 tables
+    base = mcx.Problem(probs[0]).load_tables(lib, mats, precision=1, hash_bins=4000)
+    hs = [base] + [mcx.Problem(pr).share_tables(base) for pr in probs[1:]]
+    base.set_tuning(**TRANSPORT_TUNED["tune"])
+    nh = [pr.n_histories for pr in probs]
+    mcx.batch_run(hs, [max(1, n // 50) for n in nh], TRANSPORT_TUNED["pif"], seed)   # warm-up
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record()
+    mcx.batch_run(hs, nh, TRANSPORT_TUNED["pif"], seed)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    res["tuned"] = {"particles_per_s": total / (ms / 1e3), "ms": ms, "stats": base.stats()}
+    for h in hs:
+        h.close()
+    # plain: one run per problem
+    plain = mcx.Problem(probs[0]).load_tables(lib, mats, precision=0, hash_bins=0)
+    ph = [plain] + [mcx.Problem(pr).share_tables(plain) for pr in probs[1:]]
+    for h in ph:
+        h.set_tuning(**TRANSPORT_PLAIN["tune"])
+    ph[0].run(count=1000, particles_in_flight=TRANSPORT_PLAIN["pif"], seed=seed)     # warm-up
+    torch.cuda.synchronize()
+    a.record()
+    for h, pr in zip(ph, probs):
+        h.run(particles_in_flight=TRANSPORT_PLAIN["pif"], seed=seed)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    res["plain"] = {"particles_per_s": total / (ms / 1e3), "ms": ms}
+    for h in ph:
+        h.close()
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -253,9 +298,8 @@ def main():
     lookup_ms = [e[1].elapsed_time(e[2]) for e in evs]
     sort_ms = [e[0].elapsed_time(e[1]) for e in evs]
     if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+        from paper_2402_09222_b300 import shard
+        total_ms = shard.max_over_ranks(total_ms)
     value = world * N_LOOKUPS * args.steps / (total_ms / 1e3)
 
     peak, peak_kind = measured_peaks()
@@ -298,9 +342,8 @@ def main():
         p.xs_lookup_host(Eh, mh, oh, flags=TUNED["flags"])
         e2e_s = time.perf_counter() - t0w
         if world > 1:
-            t = torch.tensor([e2e_s], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
+            from paper_2402_09222_b300 import shard
+            e2e_s = shard.max_over_ranks(e2e_s)
         line["e2e"] = {"value": world * N_LOOKUPS / e2e_s, "unit": "lookups/s",
                        "h2d_bytes_per_step": N_LOOKUPS * 12, "d2h_bytes_per_step": N_LOOKUPS * 40,
                        "path": "mcx_xs_lookup_host, pinned host buffers, 8M-lookup chunks on 2 streams"}
@@ -327,6 +370,7 @@ def main():
             "plain": time_transport(mcx, synth, lib3, TRANSPORT_PLAIN, seed=5),
             "tuned_settings": {k: v for k, v in TRANSPORT_TUNED.items()},
         }
+        line["batched"] = time_batched(mcx, synth)
         line["cpu_baseline"] = cpu_baseline(lib, mats, E, mat)
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -15,6 +15,8 @@ int launch_xs_lookup_fast(const Tables& t, const float* mden32, int64_t n, const
 int launch_xs_indices(const Tables& t, int64_t n, const double* E, const int32_t* mat,
                       int32_t max_species, int32_t* kout, int grid, cudaStream_t st);
 int launch_build_hash(const Tables& t, int32_t* hidx, int grid, cudaStream_t st);
+// Widest hash window (in grid points, window end inclusive) into *out (device int).
+int launch_hash_max_window(const Tables& t, int32_t* out, int grid, cudaStream_t st);
 int launch_xs_backward(const Tables& t, int64_t n, const double* E, const int32_t* mat,
                        const double* grad_out, double* grad_dens, double* grad_sigma, int grid,
                        cudaStream_t st);
@@ -95,6 +97,8 @@ struct Particles {
     double *u = nullptr, *v = nullptr, *w = nullptr;
     double *E = nullptr, *sig_t = nullptr, *sig_a = nullptr;
     double* W = nullptr;  // [MCX_MAX_DMAT][cap] (derivative runs)
+    double* cum = nullptr;  // [cap][cum_stride]: running sums C_i of the last lookup
+    int64_t cum_stride = 0; // >= the largest material's species count
     int64_t* hist = nullptr;
     uint32_t* rng_n = nullptr;
     uint32_t* ncoll = nullptr;

@@ -92,12 +92,15 @@ struct TableStore {
     Tables view;
     int64_t* goff = nullptr;
     double* E = nullptr;
+    float2* Epair = nullptr;
     void* sigma = nullptr;
     double* awr = nullptr;
     int32_t* moff = nullptr;
     int32_t* msp = nullptr;
     double* mden = nullptr;
     float* mden32 = nullptr;
+    int4* ment = nullptr;
+    int32_t max_points = 0;
     int32_t* hidx = nullptr;
     double* hbound = nullptr;
     double emin = 0.0, emax = 0.0;
@@ -108,12 +111,14 @@ struct TableStore {
     {
         dev_free(goff);
         dev_free(E);
+        dev_free(Epair);
         if (sigma) cudaFree(sigma);
         dev_free(awr);
         dev_free(moff);
         dev_free(msp);
         dev_free(mden);
         dev_free(mden32);
+        dev_free(ment);
         dev_free(hidx);
         dev_free(hbound);
     }
@@ -203,19 +208,21 @@ void drop_graph(mcx_problem* p)
 }
 
 // One device block for the whole particle buffer (SoA arrays + queues + bins).
-int ensure_particles(mcx_problem* p, int64_t cap, bool with_w, size_t n_bins)
+int ensure_particles(mcx_problem* p, int64_t cap, bool with_w, size_t n_bins, int64_t cum_stride)
 {
-    if (p->p_block && p->p_cap >= cap && (p->p_has_w || !with_w) && p->bins_cap >= n_bins)
+    if (p->p_block && p->p_cap >= cap && (p->p_has_w || !with_w) && p->bins_cap >= n_bins &&
+        p->P.cum_stride >= cum_stride)
         return MCX_OK;
     drop_graph(p);
     int64_t want = cap > p->p_cap ? cap : p->p_cap;
     size_t bins = n_bins > p->bins_cap ? n_bins : p->bins_cap;
     bool w = with_w || p->p_has_w;
+    const int64_t cs = cum_stride > p->P.cum_stride ? cum_stride : p->P.cum_stride;
     free_particles(p);
     const size_t c = (size_t)want;
     auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
-    size_t bytes = al(c * 8) * 9 + (w ? al(c * 8 * MCX_MAX_DMAT) : 0) + al(c * 8) + al(c * 4) * 2 +
-                   al(c * 4) * 3 + al(c) + al(c * 4) * 8 + al((bins + 1) * 4);
+    size_t bytes = al(c * 8) * 9 + (w ? al(c * 8 * MCX_MAX_DMAT) : 0) + al(c * 8 * (size_t)cs) + al(c * 8) +
+                   al(c * 4) * 2 + al(c * 4) * 3 + al(c) + al(c * 4) * 8 + al((bins + 1) * 4);
     void* blk = nullptr;
     cudaError_t e = cudaMalloc(&blk, bytes);
     if (e != cudaSuccess) {
@@ -241,6 +248,8 @@ int ensure_particles(mcx_problem* p, int64_t cap, bool with_w, size_t n_bins)
     P.sig_t = (double*)take(c * 8);
     P.sig_a = (double*)take(c * 8);
     P.W = w ? (double*)take(c * 8 * MCX_MAX_DMAT) : nullptr;
+    P.cum = (double*)take(c * 8 * (size_t)cs);
+    P.cum_stride = cs;
     P.hist = (int64_t*)take(c * 8);
     P.rng_n = (uint32_t*)take(c * 4);
     P.ncoll = (uint32_t*)take(c * 4);
@@ -336,6 +345,16 @@ int alloc_derivative_tallies(mcx_problem* p, int M)
     return MCX_OK;
 }
 
+int steps_for(int32_t len)
+{
+    int steps = 0;
+    while (len > 1) {
+        len -= len >> 1;
+        ++steps;
+    }
+    return steps;
+}
+
 int build_hash(TableStore* ts, int32_t H, int sm_count)
 {
     dev_free(ts->hidx);
@@ -343,6 +362,7 @@ int build_hash(TableStore* ts, int32_t H, int sm_count)
     ts->view.H = 0;
     ts->view.hidx = nullptr;
     ts->view.hbound = nullptr;
+    ts->view.search_steps = steps_for(ts->max_points - 1);
     if (H == 0) return MCX_OK;
     std::vector<double> hb((size_t)H + 1);
     const double lo = std::log(ts->emin), hi = std::log(ts->emax);
@@ -365,6 +385,17 @@ int build_hash(TableStore* ts, int32_t H, int sm_count)
     if (launch_build_hash(tmp, ts->hidx, sm_count * 8, 0)) return fail(MCX_ERR_CUDA, "hash build launch failed");
     CUDA_TRY(cudaDeviceSynchronize());
     ts->view.hidx = ts->hidx;
+    // fixed step count of the fast path's search: enough for the widest window
+    int32_t* d_w = nullptr;
+    TRY(dev_alloc(&d_w, 1));
+    int32_t one = 1, maxw = 1;
+    cudaMemcpy(d_w, &one, 4, cudaMemcpyHostToDevice);
+    tmp.hidx = ts->hidx;
+    const int lr = launch_hash_max_window(tmp, d_w, sm_count * 8, 0);
+    const cudaError_t e = cudaMemcpy(&maxw, d_w, 4, cudaMemcpyDeviceToHost);
+    dev_free(d_w);
+    if (lr || e != cudaSuccess) return fail(MCX_ERR_CUDA, "hash window scan failed");
+    ts->view.search_steps = steps_for(maxw);
     return MCX_OK;
 }
 
@@ -448,7 +479,7 @@ int run_loop(mcx_problem* owner, int n_prob, mcx_problem* const* probs, const in
     c.sort_scale = (float)((double)c.n_ebuckets / (std::log(ts->emax) - std::log(ts->emin)));
     c.derivatives = deriv ? owner->M : 0;
     if ((size_t)c.n_sort_bins * 4 > 48 * 1024) c.sort_period = 0;  // bins must fit shared memory
-    TRY(ensure_particles(owner, cap, deriv, (size_t)c.n_sort_bins));
+    TRY(ensure_particles(owner, cap, deriv, (size_t)c.n_sort_bins, t.max_mat_species));
     // problems and work offsets
     if (owner->probs_cap < n_prob) {
         drop_graph(owner);
@@ -837,10 +868,24 @@ int mcx_load_xs_tables(mcx_problem* p, int32_t n_species, const int64_t* goff, c
     int rc;
     std::vector<float> d32((size_t)nnz);
     for (int64_t i = 0; i < nnz; ++i) d32[i] = (float)mden[i];
+    std::vector<int4> ment((size_t)nnz);
+    int32_t max_points = 0;
+    for (int64_t i = 0; i < nnz; ++i) {
+        const int32_t sp = msp[i];
+        ment[i] = make_int4((int32_t)goff[sp], (int32_t)(goff[sp + 1] - goff[sp]), sp, 0);
+    }
+    for (int s2 = 0; s2 < n_species; ++s2)
+        if (goff[s2 + 1] - goff[s2] > max_points) max_points = (int32_t)(goff[s2 + 1] - goff[s2]);
+    std::vector<float2> pairs((size_t)P);
+    for (int64_t i = 0; i < P; ++i) {
+        const float hi = (float)energies[i];
+        pairs[i] = make_float2(hi, (float)(energies[i] - (double)hi));
+    }
     if ((rc = dev_alloc(&ts->goff, (size_t)n_species + 1)) || (rc = dev_alloc(&ts->E, (size_t)P)) ||
+        (rc = dev_alloc(&ts->Epair, (size_t)P)) ||
         (rc = dev_alloc(&ts->awr, (size_t)n_species)) || (rc = dev_alloc(&ts->moff, (size_t)n_materials + 1)) ||
         (rc = dev_alloc(&ts->msp, (size_t)nnz)) || (rc = dev_alloc(&ts->mden, (size_t)nnz)) ||
-        (rc = dev_alloc(&ts->mden32, (size_t)nnz)))
+        (rc = dev_alloc(&ts->mden32, (size_t)nnz)) || (rc = dev_alloc(&ts->ment, (size_t)nnz)))
         return bail(rc);
     const size_t sig_bytes = (size_t)P * n_ch * (precision == MCX_FP32 ? 4 : 8);
     if (cudaMalloc(&ts->sigma, sig_bytes) != cudaSuccess) {
@@ -849,11 +894,13 @@ int mcx_load_xs_tables(mcx_problem* p, int32_t n_species, const int64_t* goff, c
     }
     bool ok = cudaMemcpy(ts->goff, goff, 8 * (n_species + 1), cudaMemcpyHostToDevice) == cudaSuccess &&
               cudaMemcpy(ts->E, energies, 8 * P, cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaMemcpy(ts->Epair, pairs.data(), 8 * P, cudaMemcpyHostToDevice) == cudaSuccess &&
               cudaMemcpy(ts->awr, awr, 8 * n_species, cudaMemcpyHostToDevice) == cudaSuccess &&
               cudaMemcpy(ts->moff, moff, 4 * (n_materials + 1), cudaMemcpyHostToDevice) == cudaSuccess &&
               cudaMemcpy(ts->msp, msp, 4 * nnz, cudaMemcpyHostToDevice) == cudaSuccess &&
               cudaMemcpy(ts->mden, mden, 8 * nnz, cudaMemcpyHostToDevice) == cudaSuccess &&
-              cudaMemcpy(ts->mden32, d32.data(), 4 * nnz, cudaMemcpyHostToDevice) == cudaSuccess;
+              cudaMemcpy(ts->mden32, d32.data(), 4 * nnz, cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaMemcpy(ts->ment, ment.data(), sizeof(int4) * nnz, cudaMemcpyHostToDevice) == cudaSuccess;
     if (ok) {
         if (precision == MCX_FP32) {
             std::vector<float> s32((size_t)P * n_ch);
@@ -875,11 +922,14 @@ int mcx_load_xs_tables(mcx_problem* p, int32_t n_species, const int64_t* goff, c
     v.n_points = P;
     v.goff = ts->goff;
     v.E = ts->E;
+    v.Epair = ts->Epair;
     v.sigma = ts->sigma;
     v.awr = ts->awr;
     v.moff = ts->moff;
     v.msp = ts->msp;
     v.mden = ts->mden;
+    v.ment = ts->ment;
+    ts->max_points = max_points;
     ts->emin = emin;
     ts->emax = emax;
     ts->nnz = nnz;

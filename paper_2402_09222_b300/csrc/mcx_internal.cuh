@@ -20,6 +20,9 @@ namespace mcx {
 // Layout in HBM:
 //   goff  int64 [S+1]     species s owns points [goff[s], goff[s+1])
 //   E     f64   [P]       concatenated per-species energy grids
+//   Epair f32x2 [P]       the same energies as unevaluated FP32 pairs
+//                         (hi, lo) = (float(g), float(g - float(g))), used by
+//                         the fast lookup to form E - g without FP64 work
 //   sigma f32|f64 [P][n_ch]  interleaved channels: the two points k, k+1 of
 //                            one species are one contiguous 2*n_ch run
 //   hidx  int32 [S][H+1]  hash grid: hidx[s][b] = grid index k of bin
@@ -38,11 +41,14 @@ struct Tables {
     int64_t n_points = 0;
     const int64_t* goff = nullptr;
     const double* E = nullptr;
+    const float2* Epair = nullptr;  // per point (float(g), float(g - float(g)))
     const void* sigma = nullptr;
     const double* awr = nullptr;
     const int32_t* moff = nullptr;
     const int32_t* msp = nullptr;
     const double* mden = nullptr;
+    const int4* ment = nullptr;   // per material entry: {first point, points, species, 0}
+    int32_t search_steps = 0;     // halvings that resolve the widest search window
     // hash grid (H == 0: none)
     int32_t H = 0;
     const int32_t* hidx = nullptr;

@@ -411,7 +411,7 @@ __global__ void __launch_bounds__(1024) k_lookup(LoopConfig c, Tables t, Particl
         const uint8_t f = P.flags[slot];
         if (!(f & PF_NEED_XS)) continue;
         double st, sa;
-        macro_transport<T>(t, P.mat[slot], P.E[slot], st, sa);
+        macro_transport<T>(t, P.mat[slot], P.E[slot], st, sa, P.cum + slot * P.cum_stride);
         P.sig_t[slot] = st;
         P.sig_a[slot] = sa;
         P.flags[slot] = f & (uint8_t)~PF_NEED_XS;
@@ -609,19 +609,28 @@ __global__ void __launch_bounds__(1024) k_collide(LoopConfig c, Tables t, Partic
             const double target = xi1 * P.sig_t[slot];
             const int64_t eb = search_key(E);
             const int32_t hb = t.H > 0 ? hash_bin(t, E, eb) : 0;
-            double cum = 0.0, ss_j = 0.0, sa_j = 0.0;
-            int32_t j = 0;
-            const int32_t i0 = __ldg(t.moff + m), i1 = __ldg(t.moff + m + 1);
-            for (int32_t ii = i0; ii < i1; ++ii) {
-                const int32_t s = __ldg(t.msp + ii);
-                const int64_t k = species_index(t, s, eb, hb);
-                const int64_t p = __ldg(t.goff + s) + k;
+            // species choice: the first i with target < C_i, C_i the running
+            // sums the lookup kernel stored for this energy and material (the
+            // same FP64 values a sequential pass would form); the last species
+            // if none.  C is non-decreasing and non-negative, so a binary
+            // search on the bit patterns finds the first C_i > target.
+            const int32_t i0 = __ldg(t.moff + m), n_sp = __ldg(t.moff + m + 1) - i0;
+            const double* cum = P.cum + slot * P.cum_stride;
+            const int64_t tb = ebits(target);
+            int32_t lo = 0, hi = n_sp - 1;
+            while (lo < hi) {
+                const int32_t mid = (lo + hi) >> 1;
+                if (tb < ebits(cum[mid])) hi = mid;
+                else lo = mid + 1;
+            }
+            const int32_t j = __ldg(t.msp + i0 + lo);
+            double ss_j, sa_j;
+            {
+                const int64_t k = species_index(t, j, eb, hb);
+                const int64_t p = __ldg(t.goff + j) + k;
                 const double f = fraction_exact(E, __ldg(t.E + p), __ldg(t.E + p + 1));
                 ss_j = interp_exact(sig_at<T>(t.sigma, p * nc + cs), sig_at<T>(t.sigma, (p + 1) * nc + cs), f);
                 sa_j = interp_exact(sig_at<T>(t.sigma, p * nc + ca), sig_at<T>(t.sigma, (p + 1) * nc + ca), f);
-                j = s;
-                cum = cum + __ldg(t.mden + ii) * (ss_j + sa_j);
-                if (target < cum) break;
             }
             const double st_j = ss_j + sa_j;
             uint8_t fl = (uint8_t)(P.flags[slot] & ~PF_COLLIDE);

@@ -82,6 +82,30 @@ __global__ void k_build_hash(Tables t, int32_t* __restrict__ hidx)
     }
 }
 
+__global__ void k_hash_max_window(Tables t, int32_t* __restrict__ out)
+{
+    const int64_t total = (int64_t)t.n_species * t.H;
+    int32_t best = 1;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = q / t.H, b = q % t.H;
+        const int32_t* h = t.hidx + s * (t.H + 1) + b;
+        const int32_t w = h[1] - h[0] + 1;
+        best = w > best ? w : best;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const int32_t v = __shfl_xor_sync(0xffffffffu, best, o);
+        best = v > best ? v : best;
+    }
+    if ((threadIdx.x & 31) == 0) atomicMax(out, best);
+}
+
+int launch_hash_max_window(const Tables& t, int32_t* out, int grid, cudaStream_t st)
+{
+    k_hash_max_window<<<grid, 256, 0, st>>>(t, out);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
 // Copy new densities (with their FP32 mirror) and cross sections (rounded
 // to the table precision) from device buffers.
 __global__ void k_update_tables(const double* __restrict__ dens_src, int64_t nnz,

@@ -26,10 +26,12 @@ __device__ __forceinline__ double interp_exact(double s0, double s1, double f)
 }
 
 // Transport lookup: Sigma_t = sum_i N_i (sigma_s,i + sigma_a,i) and
-// Sigma_a = sum_i N_i sigma_a,i, both sequential in species order.
+// Sigma_a = sum_i N_i sigma_a,i, both sequential in species order.  The
+// running sums C_i of Sigma_t are stored to cum[0..n-1] (the collision picks
+// its species from them).
 template <typename T>
 __device__ __forceinline__ void macro_transport(const Tables& t, int32_t m, double E,
-                                                double& sig_t, double& sig_a)
+                                                double& sig_t, double& sig_a, double* cum)
 {
     const int64_t eb = search_key(E);
     const int32_t hb = t.H > 0 ? hash_bin(t, E, eb) : 0;
@@ -48,6 +50,7 @@ __device__ __forceinline__ void macro_transport(const Tables& t, int32_t m, doub
                                         sig_at<T>(t.sigma, (p + 1) * nc + ca), f);
         st = st + N * (ss + sai);
         sa = sa + N * sai;
+        cum[i - i0] = st;
     }
     sig_t = st;
     sig_a = sa;

@@ -4,8 +4,13 @@
 // B300 runs FP64 at 1/64 of its FP32 rate, so the FP64 work of the plain
 // definition (a division and ~5 multiply-adds per channel and species) makes
 // the exact lookup FP64-bound long before HBM is.  Here the grid search stays
-// exact (integer compares of FP64 bit patterns), the distances E - g[k] and
-// g[k+1] - E are formed in FP64, and the rest is FP32:
+// exact (integer compares of FP64 bit patterns) and no FP64 operation is left
+// in the per-species loop:
+//   E - g[k] = (E_hi - g_hi) + (E_lo - g_lo)     with (hi, lo) FP32 pairs
+// where x_hi = float(x), x_lo = float(x - x_hi) (stored for the grid, formed
+// once per lookup for E).  For neighbouring energies E_hi - g_hi is exact
+// (Sterbenz) and the lo parts carry the remaining ~2^-24 of the value, so the
+// distance keeps a relative error of about 2^-23; then
 //   w1 = (E - g[k]) / (g[k+1] - g[k]),  w0 = (g[k+1] - E) / (g[k+1] - g[k])
 //   sigma = w0 * s[k] + w1 * s[k+1]          (both terms >= 0: no cancellation)
 //   Sigma_r accumulated as an unevaluated FP32 pair (hi, lo) with TwoSum.
@@ -16,6 +21,11 @@
 namespace mcx {
 
 namespace {
+
+#ifndef MCX_FAST_UNROLL
+#define MCX_FAST_UNROLL 2
+#endif
+constexpr int kFastUnroll = MCX_FAST_UNROLL;
 
 __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x)
 {
@@ -32,7 +42,15 @@ __device__ __forceinline__ float sig32(const void* sigma, int64_t i)
     return (float)__ldg(static_cast<const T*>(sigma) + i);
 }
 
-template <typename T>
+// One thread per lookup; the material's species are taken U at a time so
+// that the U independent chains of loads (window, search probes, energy pair,
+// table rows) overlap.  The search inside a window [lo, hi] keeps a candidate
+// range (base, len) and halves it a fixed number of times (the table's
+// widest window), branch-free: if g[base + len/2] <= E then base += len/2;
+// len -= len/2.  Steps after len reaches 1 re-read g[base] and change
+// nothing, so the result is the largest k in [lo, hi] with g[k] <= E (lo if
+// none) -- the exact index.  Slots past the material's end carry N = 0.
+template <typename T, int U>
 __global__ void __launch_bounds__(256) k_xs_lookup_fast(Tables t, const float* __restrict__ mden32,
                                                         int64_t n, const double* __restrict__ Ein,
                                                         const int32_t* __restrict__ mat,
@@ -40,6 +58,7 @@ __global__ void __launch_bounds__(256) k_xs_lookup_fast(Tables t, const float* _
                                                         double* __restrict__ out)
 {
     const int nc = t.n_ch;
+    const int64_t H1 = (int64_t)t.H + 1;
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
          j += (int64_t)gridDim.x * blockDim.x) {
         const int64_t l = perm ? (int64_t)__ldg(perm + j) : j;
@@ -50,24 +69,52 @@ __global__ void __launch_bounds__(256) k_xs_lookup_fast(Tables t, const float* _
             continue;
         }
         float hi[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, lo[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+        const float E_hi = (float)E;
+        const float E_lo = (float)(E - (double)E_hi);
         const int64_t eb = search_key(E);
         const int32_t hb = t.H > 0 ? hash_bin(t, E, eb) : 0;
         const int32_t i0 = __ldg(t.moff + m), i1 = __ldg(t.moff + m + 1);
-        for (int32_t i = i0; i < i1; ++i) {
-            const int32_t s = __ldg(t.msp + i);
-            const float N = __ldg(mden32 + i);
-            const int64_t k = species_index(t, s, eb, hb);
-            const int64_t p = __ldg(t.goff + s) + k;
-            const float a = fmaxf((float)(E - __ldg(t.E + p)), 0.f);
-            const float b = fmaxf((float)(__ldg(t.E + p + 1) - E), 0.f);
-            const float inv = __frcp_rn(a + b);
-            const float w1 = a * inv, w0 = b * inv;
-            const int64_t q = p * nc;
+        for (int32_t i = i0; i < i1; i += U) {
+            int32_t base[U], len[U];
+            float N[U];
 #pragma unroll
-            for (int r = 0; r < 5; ++r) {
-                if (r < nc) {
-                    const float sg = fmaf(w0, sig32<T>(t.sigma, q + r), w1 * sig32<T>(t.sigma, q + nc + r));
-                    two_sum_acc(hi[r], lo[r], N * sg);
+            for (int u = 0; u < U; ++u) {
+                const int32_t ii = i + u < i1 ? i + u : i1 - 1;
+                const int4 e = __ldg(t.ment + ii);
+                N[u] = i + u < i1 ? __ldg(mden32 + ii) : 0.f;
+                if (t.H > 0) {
+                    const int32_t* h = t.hidx + (int64_t)e.z * H1 + hb;
+                    const int32_t wlo = __ldg(h);
+                    base[u] = e.x + wlo;
+                    len[u] = __ldg(h + 1) - wlo + 1;
+                } else {
+                    base[u] = e.x;
+                    len[u] = e.y - 1;
+                }
+            }
+            for (int st = 0; st < t.search_steps; ++st) {
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int32_t h = len[u] >> 1;
+                    if (ebits(__ldg(t.E + base[u] + h)) <= eb) base[u] += h;
+                    len[u] -= h;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int32_t p = base[u];
+                const float2 g0 = __ldg(t.Epair + p), g1 = __ldg(t.Epair + p + 1);
+                const float a = fmaxf((E_hi - g0.x) + (E_lo - g0.y), 0.f);
+                const float b = fmaxf((g1.x - E_hi) + (g1.y - E_lo), 0.f);
+                const float inv = __frcp_rn(a + b);
+                const float w1 = a * inv, w0 = b * inv;
+                const int64_t q = (int64_t)p * nc;
+#pragma unroll
+                for (int r = 0; r < 5; ++r) {
+                    if (r < nc) {
+                        const float sg = fmaf(w0, sig32<T>(t.sigma, q + r), w1 * sig32<T>(t.sigma, q + nc + r));
+                        two_sum_acc(hi[r], lo[r], N[u] * sg);
+                    }
                 }
             }
         }
@@ -166,9 +213,9 @@ int launch_xs_lookup_fast(const Tables& t, const float* mden32, int64_t n, const
                           cudaStream_t st)
 {
     if (t.precision == MCX_FP32)
-        k_xs_lookup_fast<float><<<grid, 256, 0, st>>>(t, mden32, n, E, mat, perm, out);
+        k_xs_lookup_fast<float, kFastUnroll><<<grid, 256, 0, st>>>(t, mden32, n, E, mat, perm, out);
     else
-        k_xs_lookup_fast<double><<<grid, 256, 0, st>>>(t, mden32, n, E, mat, perm, out);
+        k_xs_lookup_fast<double, kFastUnroll><<<grid, 256, 0, st>>>(t, mden32, n, E, mat, perm, out);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

@@ -347,3 +347,36 @@ def lookup_objective(lib, mats, E, mat, precision: int = 1, device: int = 0, fas
         return s
 
     return objective
+
+
+def main(argv=None):
+    """python -m paper_2402_09222_b300.tuner --workload transport|lookup ..."""
+    import argparse
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--workload", choices=["transport", "lookup"], default="transport")
+    ap.add_argument("--histories", type=int, default=10_000_000)
+    ap.add_argument("--lookups", type=int, default=100_000_000)
+    ap.add_argument("--strategy", choices=["random+cd", "bo"], default="random+cd")
+    ap.add_argument("--random", type=int, default=24)
+    ap.add_argument("--evals", type=int, default=40)
+    ap.add_argument("--db", default=None, help="JSONL performance database (resumable)")
+    ap.add_argument("--seed", type=int, default=1234)
+    args = ap.parse_args(argv)
+    from . import synth
+    if args.workload == "transport":
+        prob = synth.config3_problem(n_histories=args.histories)
+        space = transport_space()
+        obj = transport_objective(prob, seed=5, precision=1)
+    else:
+        lib = synth.species_library(355, 11_303, 1236)
+        mats = synth.lookup_materials(355, 1236)
+        E, mat = synth.lookup_inputs(args.lookups, mats.n_materials, 1336)
+        space = lookup_space()
+        obj = lookup_objective(lib, mats, E, mat)
+    t = Tuner(space, obj, db_path=args.db, seed=args.seed)
+    t.tune(n_random=args.random, max_evals=args.evals, strategy=args.strategy)
+    print(json.dumps(t.report()))
+
+
+if __name__ == "__main__":
+    main()

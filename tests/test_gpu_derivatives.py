@@ -32,8 +32,11 @@ def test_autograd_gradcheck_fp64(torch_cuda):
     dm = torch.as_tensor(mat, device="cuda")
     dens = torch.as_tensor(mats.dens, device="cuda").clone().requires_grad_(True)
     sig = torch.as_tensor(lib.sigma, device="cuda").clone().requires_grad_(True)
+    # the map is linear in both inputs, so a large step is exact up to rounding;
+    # with cross sections up to ~1e4 b a 1e-6 step would leave ~1e-6 relative
+    # rounding noise in the central differences
     assert torch.autograd.gradcheck(lambda d, s: autograd.xs_lookup(h, d, s, dE, dm), (dens, sig),
-                                    eps=1e-6, atol=1e-7, rtol=1e-6)
+                                    eps=1e-3, atol=1e-9, rtol=1e-7)
     # forward equals the oracle, and the gradient of a weighted sum equals the oracle adjoint
     out = autograd.xs_lookup(h, dens, sig, dE, dm)
     assert np.array_equal(out.detach().cpu().numpy(), oracle.xs_lookup(lib, mats, E, mat))
