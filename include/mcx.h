@@ -293,7 +293,8 @@ int mcx_xs_lookup_binned_static(mcx_problem* p, int64_t n, const double* E, cons
                                 double* out, int32_t flags, void* stream);
 
 /* The same lookup from HOST buffers: copies in, computes and copies out in
- * chunks pipelined over two streams; synchronous.  Host buffers should be
+ * chunks of up to 8M lookups pipelined over two streams (with MCX_LOOKUP_SORT
+ * each chunk is binned on the device); synchronous.  Host buffers should be
  * pinned (cudaHostAlloc / torch pin_memory) for full copy speed. */
 int mcx_xs_lookup_host(mcx_problem* p, int64_t n, const double* E_host, const int32_t* mat_host,
                        double* out_host, int32_t flags);
@@ -313,7 +314,8 @@ int mcx_xs_indices(mcx_problem* p, int64_t n, const double* E, const int32_t* ma
  * grad_dens [nnz] and grad_sigma [P][n_ch] are FP64 DEVICE buffers that are
  * accumulated into (zero them first).  E, mat, grad_out are DEVICE pointers.
  * Summation order is not fixed (atomics), so results match a sequential sum
- * to rounding. */
+ * to rounding.  Lookups with an out-of-range material or a NaN energy
+ * contribute nothing. */
 int mcx_xs_lookup_backward(mcx_problem* p, int64_t n, const double* E, const int32_t* mat,
                            const double* grad_out, double* grad_dens, double* grad_sigma,
                            void* stream);

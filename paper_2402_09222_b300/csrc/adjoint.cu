@@ -24,7 +24,7 @@ __global__ void __launch_bounds__(256) k_xs_backward(Tables t, int64_t n, const 
          l += (int64_t)gridDim.x * blockDim.x) {
         const double E = __ldg(Ein + l);
         const int32_t m = __ldg(mat + l);
-        if (m < 0 || m >= t.n_materials) continue;
+        if (m < 0 || m >= t.n_materials || E != E) continue;   // such lookups have no gradient
         double g[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
         for (int r = 0; r < nc && r < 5; ++r) g[r] = __ldg(gout + l * nc + r);
         const int64_t eb = search_key(E);

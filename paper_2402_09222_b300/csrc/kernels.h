@@ -9,9 +9,8 @@ namespace mcx {
 // ---------------------------------------------------------------- lookups
 int launch_xs_lookup_exact(const Tables& t, int64_t n, const double* E, const int32_t* mat,
                            const int32_t* perm, double* out, int grid, cudaStream_t st);
-int launch_xs_lookup_fast(const Tables& t, const float* mden32, int64_t n, const double* E,
-                          const int32_t* mat, const int32_t* perm, double* out, int grid,
-                          cudaStream_t st);
+int launch_xs_lookup_fast(const Tables& t, int64_t n, const double* E, const int32_t* mat,
+                          const int32_t* perm, double* out, int grid, cudaStream_t st);
 int launch_xs_indices(const Tables& t, int64_t n, const double* E, const int32_t* mat,
                       int32_t max_species, int32_t* kout, int grid, cudaStream_t st);
 int launch_build_hash(const Tables& t, int32_t* hidx, int grid, cudaStream_t st);
@@ -20,8 +19,8 @@ int launch_hash_max_window(const Tables& t, int32_t* out, int grid, cudaStream_t
 int launch_xs_backward(const Tables& t, int64_t n, const double* E, const int32_t* mat,
                        const double* grad_out, double* grad_dens, double* grad_sigma, int grid,
                        cudaStream_t st);
-int launch_update_tables(const double* dens_src, int64_t nnz, double* mden, float* mden32,
-                         const double* sig_src, int64_t n_sig, void* sigma, int precision,
+int launch_update_tables(const Tables& t, const double* dens_src, int64_t nnz, double* mden,
+                         int4* ment, const double* sig_src, void* sigma, float4* frec,
                          cudaStream_t st);
 int launch_debug_uniforms(uint2 key, uint64_t hist, uint32_t first, int64_t n, double* out,
                           cudaStream_t st);
@@ -41,7 +40,6 @@ int launch_lookup_sort(const SortParams& sp, int64_t n, const double* E, const i
 // entry points defined outside the C-ABI translation unit.
 struct LookupView {
     Tables tables;
-    const float* mden32 = nullptr;
     SortParams sort;
     int device = 0;
     int grid = 0;
@@ -92,7 +90,8 @@ struct ProblemDev {
 // Structure-of-arrays particle buffer (one slot per particle in flight) and
 // the event queues.
 struct Particles {
-    int64_t cap = 0;
+    int64_t cap = 0;     // slots in use by this run (the particles-in-flight count)
+    int64_t stride = 0;  // slots allocated (row stride of W)
     double *x = nullptr, *y = nullptr, *z = nullptr;
     double *u = nullptr, *v = nullptr, *w = nullptr;
     double *E = nullptr, *sig_t = nullptr, *sig_a = nullptr;

@@ -92,14 +92,15 @@ struct TableStore {
     Tables view;
     int64_t* goff = nullptr;
     double* E = nullptr;
-    float2* Epair = nullptr;
+    float4* frec = nullptr;
     void* sigma = nullptr;
     double* awr = nullptr;
     int32_t* moff = nullptr;
     int32_t* msp = nullptr;
     double* mden = nullptr;
-    float* mden32 = nullptr;
     int4* ment = nullptr;
+    std::vector<int4> h_ment;
+    bool h_ment_stale = false;  // densities were last set from device buffers
     int32_t max_points = 0;
     int32_t* hidx = nullptr;
     double* hbound = nullptr;
@@ -111,13 +112,12 @@ struct TableStore {
     {
         dev_free(goff);
         dev_free(E);
-        dev_free(Epair);
+        dev_free(frec);
         if (sigma) cudaFree(sigma);
         dev_free(awr);
         dev_free(moff);
         dev_free(msp);
         dev_free(mden);
-        dev_free(mden32);
         dev_free(ment);
         dev_free(hidx);
         dev_free(hbound);
@@ -238,6 +238,7 @@ int ensure_particles(mcx_problem* p, int64_t cap, bool with_w, size_t n_bins, in
     };
     Particles& P = p->P;
     P.cap = want;
+    P.stride = want;
     P.x = (double*)take(c * 8);
     P.y = (double*)take(c * 8);
     P.z = (double*)take(c * 8);
@@ -273,6 +274,13 @@ int ensure_particles(mcx_problem* p, int64_t cap, bool with_w, size_t n_bins, in
 }
 
 bool is_finite(double x) { return std::isfinite(x); }
+
+int32_t float_bits(float f)
+{
+    int32_t b;
+    std::memcpy(&b, &f, sizeof(b));
+    return b;
+}
 
 int validate_desc(const mcx_problem_desc* d)
 {
@@ -480,6 +488,8 @@ int run_loop(mcx_problem* owner, int n_prob, mcx_problem* const* probs, const in
     c.derivatives = deriv ? owner->M : 0;
     if ((size_t)c.n_sort_bins * 4 > 48 * 1024) c.sort_period = 0;  // bins must fit shared memory
     TRY(ensure_particles(owner, cap, deriv, (size_t)c.n_sort_bins, t.max_mat_species));
+    // the buffer may be larger than this run needs: use exactly `cap` slots
+    owner->P.cap = cap;
     // problems and work offsets
     if (owner->probs_cap < n_prob) {
         drop_graph(owner);
@@ -646,7 +656,7 @@ int lookup_device_ordered(mcx_problem* p, int64_t n, const double* E, const int3
 {
     const TableStore* ts = p->tables;
     int r = (flags & MCX_LOOKUP_FAST)
-                ? launch_xs_lookup_fast(ts->view, ts->mden32, n, E, mat, perm, out, lookup_grid(p), st)
+                ? launch_xs_lookup_fast(ts->view, n, E, mat, perm, out, lookup_grid(p), st)
                 : launch_xs_lookup_exact(ts->view, n, E, mat, perm, out, lookup_grid(p), st);
     if (r) return fail(MCX_ERR_CUDA, "lookup launch failed: %s", cudaGetErrorString(cudaGetLastError()));
     return MCX_OK;
@@ -675,7 +685,6 @@ int problem_lookup_view(const mcx_problem* p, LookupView* v)
     TRY(check_tables(p));
     const TableStore* ts = p->tables;
     v->tables = ts->view;
-    v->mden32 = ts->mden32;
     v->sort = lookup_sort_params(ts);
     v->device = p->device;
     v->grid = lookup_grid(p);
@@ -866,26 +875,31 @@ int mcx_load_xs_tables(mcx_problem* p, int32_t n_species, const int64_t* goff, c
         return code;
     };
     int rc;
-    std::vector<float> d32((size_t)nnz);
-    for (int64_t i = 0; i < nnz; ++i) d32[i] = (float)mden[i];
+    // fast-path copies: per material entry {first point, points, species,
+    // FP32 density}; per point a 16-byte aligned record {g_hi, g_lo, sigma...}
     std::vector<int4> ment((size_t)nnz);
     int32_t max_points = 0;
     for (int64_t i = 0; i < nnz; ++i) {
         const int32_t sp = msp[i];
-        ment[i] = make_int4((int32_t)goff[sp], (int32_t)(goff[sp + 1] - goff[sp]), sp, 0);
+        ment[i] = make_int4((int32_t)goff[sp], (int32_t)(goff[sp + 1] - goff[sp]), sp,
+                            float_bits((float)mden[i]));
     }
     for (int s2 = 0; s2 < n_species; ++s2)
         if (goff[s2 + 1] - goff[s2] > max_points) max_points = (int32_t)(goff[s2 + 1] - goff[s2]);
-    std::vector<float2> pairs((size_t)P);
+    const int frec_w = n_ch <= 2 ? 1 : 2;
+    std::vector<float> rec((size_t)P * 4 * frec_w, 0.f);
     for (int64_t i = 0; i < P; ++i) {
+        float* r = &rec[(size_t)i * 4 * frec_w];
         const float hi = (float)energies[i];
-        pairs[i] = make_float2(hi, (float)(energies[i] - (double)hi));
+        r[0] = hi;
+        r[1] = (float)(energies[i] - (double)hi);
+        for (int c = 0; c < n_ch; ++c) r[2 + c] = (float)sigma[i * n_ch + c];
     }
     if ((rc = dev_alloc(&ts->goff, (size_t)n_species + 1)) || (rc = dev_alloc(&ts->E, (size_t)P)) ||
-        (rc = dev_alloc(&ts->Epair, (size_t)P)) ||
+        (rc = dev_alloc(&ts->frec, (size_t)P * frec_w)) ||
         (rc = dev_alloc(&ts->awr, (size_t)n_species)) || (rc = dev_alloc(&ts->moff, (size_t)n_materials + 1)) ||
         (rc = dev_alloc(&ts->msp, (size_t)nnz)) || (rc = dev_alloc(&ts->mden, (size_t)nnz)) ||
-        (rc = dev_alloc(&ts->mden32, (size_t)nnz)) || (rc = dev_alloc(&ts->ment, (size_t)nnz)))
+        (rc = dev_alloc(&ts->ment, (size_t)nnz)))
         return bail(rc);
     const size_t sig_bytes = (size_t)P * n_ch * (precision == MCX_FP32 ? 4 : 8);
     if (cudaMalloc(&ts->sigma, sig_bytes) != cudaSuccess) {
@@ -894,12 +908,11 @@ int mcx_load_xs_tables(mcx_problem* p, int32_t n_species, const int64_t* goff, c
     }
     bool ok = cudaMemcpy(ts->goff, goff, 8 * (n_species + 1), cudaMemcpyHostToDevice) == cudaSuccess &&
               cudaMemcpy(ts->E, energies, 8 * P, cudaMemcpyHostToDevice) == cudaSuccess &&
-              cudaMemcpy(ts->Epair, pairs.data(), 8 * P, cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaMemcpy(ts->frec, rec.data(), sizeof(float) * rec.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
               cudaMemcpy(ts->awr, awr, 8 * n_species, cudaMemcpyHostToDevice) == cudaSuccess &&
               cudaMemcpy(ts->moff, moff, 4 * (n_materials + 1), cudaMemcpyHostToDevice) == cudaSuccess &&
               cudaMemcpy(ts->msp, msp, 4 * nnz, cudaMemcpyHostToDevice) == cudaSuccess &&
               cudaMemcpy(ts->mden, mden, 8 * nnz, cudaMemcpyHostToDevice) == cudaSuccess &&
-              cudaMemcpy(ts->mden32, d32.data(), 4 * nnz, cudaMemcpyHostToDevice) == cudaSuccess &&
               cudaMemcpy(ts->ment, ment.data(), sizeof(int4) * nnz, cudaMemcpyHostToDevice) == cudaSuccess;
     if (ok) {
         if (precision == MCX_FP32) {
@@ -922,13 +935,15 @@ int mcx_load_xs_tables(mcx_problem* p, int32_t n_species, const int64_t* goff, c
     v.n_points = P;
     v.goff = ts->goff;
     v.E = ts->E;
-    v.Epair = ts->Epair;
+    v.frec = ts->frec;
+    v.frec_w = frec_w;
     v.sigma = ts->sigma;
     v.awr = ts->awr;
     v.moff = ts->moff;
     v.msp = ts->msp;
     v.mden = ts->mden;
     v.ment = ts->ment;
+    ts->h_ment = ment;
     ts->max_points = max_points;
     ts->emin = emin;
     ts->emax = emax;
@@ -989,10 +1004,9 @@ int mcx_set_densities(mcx_problem* p, const double* mden, int64_t nnz)
         if (!(mden[i] >= 0.0) || !is_finite(mden[i])) return fail(MCX_ERR_ARG, "mat_dens[%lld] invalid", (long long)i);
     DeviceGuard dg(p->device);
     CUDA_TRY(cudaDeviceSynchronize());
-    std::vector<float> d32((size_t)nnz);
-    for (int64_t i = 0; i < nnz; ++i) d32[i] = (float)mden[i];
+    for (int64_t i = 0; i < nnz; ++i) ts->h_ment[i].w = float_bits((float)mden[i]);
     CUDA_TRY(cudaMemcpy(ts->mden, mden, 8 * nnz, cudaMemcpyHostToDevice));
-    CUDA_TRY(cudaMemcpy(ts->mden32, d32.data(), 4 * nnz, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(ts->ment, ts->h_ment.data(), sizeof(int4) * nnz, cudaMemcpyHostToDevice));
     return MCX_OK;
 }
 
@@ -1003,9 +1017,10 @@ int mcx_update_tables_device(mcx_problem* p, const double* mat_dens, const doubl
     if (!mat_dens && !sigma) return MCX_OK;
     TableStore* ts = p->tables;
     DeviceGuard dg(p->device);
-    if (launch_update_tables(mat_dens, mat_dens ? ts->nnz : 0, ts->mden, ts->mden32, sigma,
-                             sigma ? ts->view.n_points * ts->view.n_ch : 0, ts->sigma, ts->view.precision,
-                             (cudaStream_t)stream))
+    // the host copy of the entry records no longer reflects device-side densities
+    if (mat_dens) ts->h_ment_stale = true;
+    if (launch_update_tables(ts->view, mat_dens, mat_dens ? ts->nnz : 0, ts->mden, ts->ment, sigma, ts->sigma,
+                             ts->frec, (cudaStream_t)stream))
         return fail(MCX_ERR_CUDA, "table update launch failed");
     return MCX_OK;
 }
@@ -1199,10 +1214,14 @@ int mcx_xs_lookup_host(mcx_problem* p, int64_t n, const double* E_host, const in
     if (n == 0) return MCX_OK;
     if (!E_host || !mat_host || !out_host) return fail(MCX_ERR_ARG, "NULL buffer");
     DeviceGuard dg(p->device);
-    const int nc = p->tables->view.n_ch;
+    const TableStore* ts = p->tables;
+    const int nc = ts->view.n_ch;
     const int64_t chunk = n < (int64_t)(8 << 20) ? n : (int64_t)(8 << 20);
-    // staging: per stream E [chunk], mat [chunk], out [chunk * nc] doubles
-    const int64_t per = chunk * (2 + nc);
+    const SortParams sp = lookup_sort_params(ts);
+    const int64_t nbins = (int64_t)sp.n_materials * sp.n_ebuckets + 1;
+    // staging per stream (in doubles): E [chunk], mat [chunk int32], out
+    // [chunk * nc], binning permutation [chunk int32], bin counters [nbins]
+    const int64_t per = chunk * (4 + nc) + nbins;
     if (p->h_buf_cap < 2 * per) {
         dev_free(p->h_buf);
         TRY(dev_alloc(&p->h_buf, (size_t)(2 * per)));
@@ -1216,9 +1235,17 @@ int mcx_xs_lookup_host(mcx_problem* p, int64_t n, const double* E_host, const in
         double* dE = base;
         int32_t* dM = (int32_t*)(base + chunk);
         double* dO = base + 2 * chunk;
+        int32_t* dP = (int32_t*)(base + chunk * (2 + nc));
+        uint32_t* dB = (uint32_t*)(base + chunk * (3 + nc));
         CUDA_TRY(cudaMemcpyAsync(dE, E_host + off, 8 * m, cudaMemcpyHostToDevice, st));
         CUDA_TRY(cudaMemcpyAsync(dM, mat_host + off, 4 * m, cudaMemcpyHostToDevice, st));
-        TRY(lookup_device(p, m, dE, dM, dO, flags & ~MCX_LOOKUP_SORT, st));
+        const int32_t* perm = nullptr;
+        if (flags & MCX_LOOKUP_SORT) {
+            if (launch_lookup_sort(sp, m, dE, dM, dB, dP, lookup_grid(p), st))
+                return fail(MCX_ERR_CUDA, "lookup sort launch failed");
+            perm = dP;
+        }
+        TRY(lookup_device_ordered(p, m, dE, dM, perm, dO, flags & MCX_LOOKUP_FAST, st));
         CUDA_TRY(cudaMemcpyAsync(out_host + off * nc, dO, 8 * m * nc, cudaMemcpyDeviceToHost, st));
     }
     CUDA_TRY(cudaStreamSynchronize(ss[0]));

@@ -20,9 +20,12 @@ namespace mcx {
 // Layout in HBM:
 //   goff  int64 [S+1]     species s owns points [goff[s], goff[s+1])
 //   E     f64   [P]       concatenated per-species energy grids
-//   Epair f32x2 [P]       the same energies as unevaluated FP32 pairs
-//                         (hi, lo) = (float(g), float(g - float(g))), used by
-//                         the fast lookup to form E - g without FP64 work
+//   frec  f32x4 [P][w]    fast-path record of each point, 16-byte aligned:
+//                         {g_hi, g_lo, s_0 .. s_{n_ch-1}, 0 ...} in w float4
+//                         (w = 1 for n_ch <= 2, else 2), where (g_hi, g_lo) =
+//                         (float(g), float(g - float(g))) is the energy as an
+//                         unevaluated FP32 pair; the two bracketing points of a
+//                         species are 2w consecutive float4
 //   sigma f32|f64 [P][n_ch]  interleaved channels: the two points k, k+1 of
 //                            one species are one contiguous 2*n_ch run
 //   hidx  int32 [S][H+1]  hash grid: hidx[s][b] = grid index k of bin
@@ -41,13 +44,14 @@ struct Tables {
     int64_t n_points = 0;
     const int64_t* goff = nullptr;
     const double* E = nullptr;
-    const float2* Epair = nullptr;  // per point (float(g), float(g - float(g)))
+    const float4* frec = nullptr;   // fast-path point records, frec_w float4 each
+    int32_t frec_w = 0;
     const void* sigma = nullptr;
     const double* awr = nullptr;
     const int32_t* moff = nullptr;
     const int32_t* msp = nullptr;
     const double* mden = nullptr;
-    const int4* ment = nullptr;   // per material entry: {first point, points, species, 0}
+    const int4* ment = nullptr;   // per material entry: {first point, points, species, FP32 density bits}
     int32_t search_steps = 0;     // halvings that resolve the widest search window
     // hash grid (H == 0: none)
     int32_t H = 0;
@@ -174,6 +178,34 @@ __device__ __forceinline__ double widen_f32(float f)
     if (e == 0u) return u == 0u ? 0.0 : (double)f;
     const uint32_t hi = ((e + 896u) << 20) | ((u & 0x7FFFFFu) >> 3);
     return __hiloint2double((int)hi, (int)(u << 29));
+}
+
+// Search window of species entry e = {first point, points, species, .} for
+// hash bin hb, as a global first candidate and a candidate count.
+__device__ __forceinline__ void search_window(const Tables& t, const int4& e, int32_t hb, int32_t& base,
+                                              int32_t& len)
+{
+    if (t.H > 0) {
+        const int32_t* h = t.hidx + (int64_t)e.z * ((int64_t)t.H + 1) + hb;
+        const int32_t wlo = __ldg(h);
+        base = e.x + wlo;
+        len = __ldg(h + 1) - wlo + 1;
+    } else {
+        base = e.x;
+        len = e.y - 1;
+    }
+}
+
+// One branch-free halving step of the fixed-step search: the candidate range
+// (base, len) keeps the largest k with g[k] <= E; after t.search_steps steps
+// len is 1 and base is that k (or the window start if none), exactly as
+// bsearch_window finds it.
+__device__ __forceinline__ void search_step(const double* __restrict__ E, int32_t& base, int32_t& len,
+                                            int64_t eb)
+{
+    const int32_t h = len >> 1;
+    if (ebits(__ldg(E + base + h)) <= eb) base += h;
+    len -= h;
 }
 
 template <typename T>

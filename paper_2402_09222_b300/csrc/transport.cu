@@ -255,7 +255,7 @@ __device__ void init_particle(const Particles& P, int64_t slot, const ProblemDev
     P.mat[slot] = __ldg(pd.region_material + region_of(pd, q));
     P.prob[slot] = pidx;
     P.flags[slot] = (uint8_t)(PF_ALIVE | PF_NEED_XS | (q.inpin ? PF_INPIN : 0));
-    for (int mm = 0; mm < M; ++mm) P.W[(int64_t)mm * P.cap + slot] = 0.0;
+    for (int mm = 0; mm < M; ++mm) P.W[(int64_t)mm * P.stride + slot] = 0.0;
 }
 
 __device__ __forceinline__ State load_state(const Particles& P, int64_t slot, int32_t ln)
@@ -289,7 +289,7 @@ __device__ void finish_deaths(bool dies, int outcome, int64_t slot, int32_t pidx
         const int leader = __ffs(grp) - 1;
         if (lane_id() == leader) atomicAdd(a, (double)__popc(grp));
         for (int mm = 0; mm < M; ++mm) {
-            const double wv = P.W[(int64_t)mm * P.cap + slot];
+            const double wv = P.W[(int64_t)mm * P.stride + slot];
             double sum = 0.0;
             for (unsigned g = grp; g; g &= g - 1u) sum += __shfl_sync(grp, wv, __ffs(g) - 1);
             if (lane_id() == leader)
@@ -480,14 +480,14 @@ __global__ void __launch_bounds__(1024) k_advance(LoopConfig c, Particles P, con
                 scored = true;
                 xabs = d * sig_a;
                 if (M > 0) {
-                    for (int mm = 0; mm < M; ++mm) Wl[mm] = P.W[(int64_t)mm * P.cap + slot];
+                    for (int mm = 0; mm < M; ++mm) Wl[mm] = P.W[(int64_t)mm * P.stride + slot];
                     for (int mm = 0; mm < M; ++mm) {
                         if (mm == m) {
                             Wl[mm] = Wl[mm] - sig_t * d;
                             if (collide) Wl[mm] = Wl[mm] + 1.0;
                         }
                     }
-                    for (int mm = 0; mm < M; ++mm) P.W[(int64_t)mm * P.cap + slot] = Wl[mm];
+                    for (int mm = 0; mm < M; ++mm) P.W[(int64_t)mm * P.stride + slot] = Wl[mm];
                 }
                 if (!collide) {
                     const int o = cross_surface(pd, q, surf);
@@ -674,7 +674,7 @@ __global__ void __launch_bounds__(1024) k_collide(LoopConfig c, Tables t, Partic
             if (M > 0) {
                 const ProblemDev& pd = probs[pidx];
                 for (int mm = 0; mm < M; ++mm) {
-                    const double wv = P.W[(int64_t)mm * P.cap + slot];
+                    const double wv = P.W[(int64_t)mm * P.stride + slot];
                     double sum = 0.0;
                     for (unsigned g = grp; g; g &= g - 1u) sum += __shfl_sync(grp, wv, __ffs(g) - 1);
                     if (lane_id() == leader) atomicAdd(pd.doutcome + tal_i * M + mm, sum);

@@ -23,7 +23,7 @@ __global__ void __launch_bounds__(256) k_xs_lookup_exact(Tables t, int64_t n,
         const double E = __ldg(Ein + l);
         const int32_t m = __ldg(mat + l);
         double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-        if (m < 0 || m >= t.n_materials) {
+        if (m < 0 || m >= t.n_materials || E != E) {
             for (int r = 0; r < nc; ++r) out[l * nc + r] = __longlong_as_double(0x7ff8000000000000LL);
             continue;
         }
@@ -106,35 +106,40 @@ int launch_hash_max_window(const Tables& t, int32_t* out, int grid, cudaStream_t
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-// Copy new densities (with their FP32 mirror) and cross sections (rounded
-// to the table precision) from device buffers.
-__global__ void k_update_tables(const double* __restrict__ dens_src, int64_t nnz,
-                                double* __restrict__ mden, float* __restrict__ mden32,
-                                const double* __restrict__ sig_src, int64_t n_sig,
-                                void* __restrict__ sigma, int precision)
+// Copy new densities and cross sections from device buffers into the exact
+// tables (sigma rounded to the table precision) and into the fast path's
+// copies (the FP32 density in each material entry, the FP32 point records).
+__global__ void k_update_tables(Tables t, const double* __restrict__ dens_src, int64_t nnz,
+                                double* __restrict__ mden, int4* __restrict__ ment,
+                                const double* __restrict__ sig_src, void* __restrict__ sigma,
+                                float4* __restrict__ frec)
 {
+    const int64_t n_sig = sig_src ? t.n_points * t.n_ch : 0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nnz || i < n_sig; i += stride) {
         if (dens_src && i < nnz) {
             mden[i] = dens_src[i];
-            mden32[i] = (float)dens_src[i];
+            ment[i].w = __float_as_int((float)dens_src[i]);
         }
-        if (sig_src && i < n_sig) {
-            if (precision == MCX_FP32) static_cast<float*>(sigma)[i] = (float)sig_src[i];
+        if (i < n_sig) {
+            if (t.precision == MCX_FP32) static_cast<float*>(sigma)[i] = (float)sig_src[i];
             else static_cast<double*>(sigma)[i] = sig_src[i];
+            const int64_t pt = i / t.n_ch, r = i % t.n_ch;
+            reinterpret_cast<float*>(frec)[pt * 4 * t.frec_w + 2 + r] = (float)sig_src[i];
         }
     }
 }
 
-int launch_update_tables(const double* dens_src, int64_t nnz, double* mden, float* mden32,
-                         const double* sig_src, int64_t n_sig, void* sigma, int precision,
+int launch_update_tables(const Tables& t, const double* dens_src, int64_t nnz, double* mden,
+                         int4* ment, const double* sig_src, void* sigma, float4* frec,
                          cudaStream_t st)
 {
+    const int64_t n_sig = sig_src ? t.n_points * t.n_ch : 0;
     const int64_t n = nnz > n_sig ? nnz : n_sig;
     int grid = (int)((n + 255) / 256);
     if (grid > 4096) grid = 4096;
     if (grid < 1) grid = 1;
-    k_update_tables<<<grid, 256, 0, st>>>(dens_src, nnz, mden, mden32, sig_src, n_sig, sigma, precision);
+    k_update_tables<<<grid, 256, 0, st>>>(t, dens_src, nnz, mden, ment, sig_src, sigma, frec);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

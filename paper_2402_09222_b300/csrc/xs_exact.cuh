@@ -12,11 +12,15 @@
 
 namespace mcx {
 
+// The clamps compare bit patterns on the integer pipes (f is never NaN here:
+// callers handle NaN energies before; a -0.0 clamped to +0.0 changes no
+// result because it only multiplies a finite difference added to s[k]).
 __device__ __forceinline__ double fraction_exact(double E, double g0, double g1)
 {
     double f = (E - g0) / (g1 - g0);
-    if (f < 0.0) f = 0.0;
-    if (f > 1.0) f = 1.0;
+    const int64_t fb = __double_as_longlong(f);
+    if (fb < 0) f = 0.0;
+    if (fb > 0x3FF0000000000000LL) f = 1.0;
     return f;
 }
 
@@ -28,7 +32,9 @@ __device__ __forceinline__ double interp_exact(double s0, double s1, double f)
 // Transport lookup: Sigma_t = sum_i N_i (sigma_s,i + sigma_a,i) and
 // Sigma_a = sum_i N_i sigma_a,i, both sequential in species order.  The
 // running sums C_i of Sigma_t are stored to cum[0..n-1] (the collision picks
-// its species from them).
+// its species from them).  Two species are evaluated at a time so their load
+// chains overlap; their terms are still added one after the other, in species
+// order, so every sum is the sequential FP64 value.
 template <typename T>
 __device__ __forceinline__ void macro_transport(const Tables& t, int32_t m, double E,
                                                 double& sig_t, double& sig_a, double* cum)
@@ -36,21 +42,41 @@ __device__ __forceinline__ void macro_transport(const Tables& t, int32_t m, doub
     const int64_t eb = search_key(E);
     const int32_t hb = t.H > 0 ? hash_bin(t, E, eb) : 0;
     const int32_t i0 = __ldg(t.moff + m), i1 = __ldg(t.moff + m + 1);
-    const int32_t nc = t.n_ch, cs = t.ch_scatter, ca = t.ch_absorb;
+    const int nc = t.n_ch, cs = t.ch_scatter, ca = t.ch_absorb;
     double st = 0.0, sa = 0.0;
-    for (int32_t i = i0; i < i1; ++i) {
-        const int32_t s = __ldg(t.msp + i);
-        const double N = __ldg(t.mden + i);
-        const int64_t k = species_index(t, s, eb, hb);
-        const int64_t p = __ldg(t.goff + s) + k;
-        const double f = fraction_exact(E, __ldg(t.E + p), __ldg(t.E + p + 1));
-        const double ss = interp_exact(sig_at<T>(t.sigma, p * nc + cs),
-                                       sig_at<T>(t.sigma, (p + 1) * nc + cs), f);
-        const double sai = interp_exact(sig_at<T>(t.sigma, p * nc + ca),
-                                        sig_at<T>(t.sigma, (p + 1) * nc + ca), f);
-        st = st + N * (ss + sai);
-        sa = sa + N * sai;
+    for (int32_t i = i0; i < i1; i += 2) {
+        int32_t base[2], len[2];
+        double N[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int32_t ii = i + u < i1 ? i + u : i1 - 1;
+            N[u] = __ldg(t.mden + ii);
+            search_window(t, __ldg(t.ment + ii), hb, base[u], len[u]);
+        }
+        for (int s = 0; s < t.search_steps; ++s) {
+            search_step(t.E, base[0], len[0], eb);
+            search_step(t.E, base[1], len[1], eb);
+        }
+        double c[2], a[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int64_t p = base[u];
+            const double f = fraction_exact(E, __ldg(t.E + p), __ldg(t.E + p + 1));
+            const double ss = interp_exact(sig_at<T>(t.sigma, p * nc + cs),
+                                           sig_at<T>(t.sigma, (p + 1) * nc + cs), f);
+            const double sai = interp_exact(sig_at<T>(t.sigma, p * nc + ca),
+                                            sig_at<T>(t.sigma, (p + 1) * nc + ca), f);
+            c[u] = N[u] * (ss + sai);
+            a[u] = N[u] * sai;
+        }
+        st = st + c[0];
+        sa = sa + a[0];
         cum[i - i0] = st;
+        if (i + 1 < i1) {
+            st = st + c[1];
+            sa = sa + a[1];
+            cum[i + 1 - i0] = st;
+        }
     }
     sig_t = st;
     sig_a = sa;

@@ -22,8 +22,14 @@ namespace mcx {
 
 namespace {
 
+// Species in flight per thread and minimum resident 256-thread blocks per SM
+// (the register cap that follows); 4 and 4 measured fastest on B300 among
+// U in {1, 2, 4} x blocks in {1, 4, 5}.
 #ifndef MCX_FAST_UNROLL
-#define MCX_FAST_UNROLL 2
+#define MCX_FAST_UNROLL 4
+#endif
+#ifndef MCX_FAST_MIN_BLOCKS
+#define MCX_FAST_MIN_BLOCKS 4
 #endif
 constexpr int kFastUnroll = MCX_FAST_UNROLL;
 
@@ -36,27 +42,37 @@ __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x)
     lo += e;
 }
 
-template <typename T>
-__device__ __forceinline__ float sig32(const void* sigma, int64_t i)
-{
-    return (float)__ldg(static_cast<const T*>(sigma) + i);
-}
-
 // One thread per lookup; the material's species are taken U at a time so
-// that the U independent chains of loads (window, search probes, energy pair,
-// table rows) overlap.  The search inside a window [lo, hi] keeps a candidate
+// that the U independent chains of loads (window, search probes, point
+// records) overlap.  The search inside a window [lo, hi] keeps a candidate
 // range (base, len) and halves it a fixed number of times (the table's
 // widest window), branch-free: if g[base + len/2] <= E then base += len/2;
 // len -= len/2.  Steps after len reaches 1 re-read g[base] and change
 // nothing, so the result is the largest k in [lo, hi] with g[k] <= E (lo if
-// none) -- the exact index.  Slots past the material's end carry N = 0.
-template <typename T, int U>
-__global__ void __launch_bounds__(256) k_xs_lookup_fast(Tables t, const float* __restrict__ mden32,
-                                                        int64_t n, const double* __restrict__ Ein,
+// none) -- the exact index.  The bracketing points' records (energy pair and
+// FP32 cross sections) are read with 16-byte loads; the density is folded
+// into the two weights, and the U species' terms are added before one
+// compensated accumulation.  Slots past the material's end carry N = 0.
+template <int W>
+__device__ __forceinline__ void load_records(const float4* __restrict__ rec, int32_t p, float (&r0)[4 * W],
+                                             float (&r1)[4 * W])
+{
+    const float4* q = rec + (int64_t)p * W;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        const float4 a = __ldg(q + w), b = __ldg(q + W + w);
+        r0[4 * w] = a.x; r0[4 * w + 1] = a.y; r0[4 * w + 2] = a.z; r0[4 * w + 3] = a.w;
+        r1[4 * w] = b.x; r1[4 * w + 1] = b.y; r1[4 * w + 2] = b.z; r1[4 * w + 3] = b.w;
+    }
+}
+
+template <int W, int U>
+__global__ void __launch_bounds__(256, MCX_FAST_MIN_BLOCKS) k_xs_lookup_fast(Tables t, int64_t n, const double* __restrict__ Ein,
                                                         const int32_t* __restrict__ mat,
                                                         const int32_t* __restrict__ perm,
                                                         double* __restrict__ out)
 {
+    constexpr int NCMAX = 4 * W - 2;   // channels a record can hold
     const int nc = t.n_ch;
     const int64_t H1 = (int64_t)t.H + 1;
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
@@ -68,7 +84,9 @@ __global__ void __launch_bounds__(256) k_xs_lookup_fast(Tables t, const float* _
             for (int r = 0; r < nc; ++r) out[l * nc + r] = __longlong_as_double(0x7ff8000000000000LL);
             continue;
         }
-        float hi[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, lo[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+        float hi[NCMAX], lo[NCMAX];
+#pragma unroll
+        for (int r = 0; r < NCMAX; ++r) hi[r] = lo[r] = 0.f;
         const float E_hi = (float)E;
         const float E_lo = (float)(E - (double)E_hi);
         const int64_t eb = search_key(E);
@@ -81,7 +99,7 @@ __global__ void __launch_bounds__(256) k_xs_lookup_fast(Tables t, const float* _
             for (int u = 0; u < U; ++u) {
                 const int32_t ii = i + u < i1 ? i + u : i1 - 1;
                 const int4 e = __ldg(t.ment + ii);
-                N[u] = i + u < i1 ? __ldg(mden32 + ii) : 0.f;
+                N[u] = i + u < i1 ? __int_as_float(e.w) : 0.f;
                 if (t.H > 0) {
                     const int32_t* h = t.hidx + (int64_t)e.z * H1 + hb;
                     const int32_t wlo = __ldg(h);
@@ -100,26 +118,25 @@ __global__ void __launch_bounds__(256) k_xs_lookup_fast(Tables t, const float* _
                     len[u] -= h;
                 }
             }
+            float part[NCMAX];
+#pragma unroll
+            for (int r = 0; r < NCMAX; ++r) part[r] = 0.f;
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                const int32_t p = base[u];
-                const float2 g0 = __ldg(t.Epair + p), g1 = __ldg(t.Epair + p + 1);
-                const float a = fmaxf((E_hi - g0.x) + (E_lo - g0.y), 0.f);
-                const float b = fmaxf((g1.x - E_hi) + (g1.y - E_lo), 0.f);
-                const float inv = __frcp_rn(a + b);
-                const float w1 = a * inv, w0 = b * inv;
-                const int64_t q = (int64_t)p * nc;
+                float r0[4 * W], r1[4 * W];
+                load_records<W>(t.frec, base[u], r0, r1);
+                const float a = fmaxf((E_hi - r0[0]) + (E_lo - r0[1]), 0.f);
+                const float b = fmaxf((r1[0] - E_hi) + (r1[1] - E_lo), 0.f);
+                const float nw = N[u] * __frcp_rn(a + b);
+                const float w1 = nw * a, w0 = nw * b;
 #pragma unroll
-                for (int r = 0; r < 5; ++r) {
-                    if (r < nc) {
-                        const float sg = fmaf(w0, sig32<T>(t.sigma, q + r), w1 * sig32<T>(t.sigma, q + nc + r));
-                        two_sum_acc(hi[r], lo[r], N[u] * sg);
-                    }
-                }
+                for (int r = 0; r < NCMAX; ++r) part[r] += fmaf(w0, r0[2 + r], w1 * r1[2 + r]);
             }
+#pragma unroll
+            for (int r = 0; r < NCMAX; ++r) two_sum_acc(hi[r], lo[r], part[r]);
         }
 #pragma unroll
-        for (int r = 0; r < 5; ++r)
+        for (int r = 0; r < NCMAX; ++r)
             if (r < nc) out[l * nc + r] = (double)hi[r] + (double)lo[r];
     }
 }
@@ -208,14 +225,13 @@ __global__ void k_lookup_sort_scatter(SortParams sp, int64_t n, const double* __
 
 }  // namespace
 
-int launch_xs_lookup_fast(const Tables& t, const float* mden32, int64_t n, const double* E,
-                          const int32_t* mat, const int32_t* perm, double* out, int grid,
-                          cudaStream_t st)
+int launch_xs_lookup_fast(const Tables& t, int64_t n, const double* E, const int32_t* mat,
+                          const int32_t* perm, double* out, int grid, cudaStream_t st)
 {
-    if (t.precision == MCX_FP32)
-        k_xs_lookup_fast<float, kFastUnroll><<<grid, 256, 0, st>>>(t, mden32, n, E, mat, perm, out);
+    if (t.frec_w == 1)
+        k_xs_lookup_fast<1, kFastUnroll><<<grid, 256, 0, st>>>(t, n, E, mat, perm, out);
     else
-        k_xs_lookup_fast<double, kFastUnroll><<<grid, 256, 0, st>>>(t, mden32, n, E, mat, perm, out);
+        k_xs_lookup_fast<2, kFastUnroll><<<grid, 256, 0, st>>>(t, n, E, mat, perm, out);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

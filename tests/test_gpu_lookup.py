@@ -153,6 +153,8 @@ def test_host_path_matches_device_path(torch_cuda, small_case):
     assert torch.equal(host, dev.cpu())
     host2 = p.xs_lookup_host(E, mat, flags=mcx.LOOKUP_FAST)
     assert np.array_equal(host2, dev.cpu().numpy())
+    host3 = p.xs_lookup_host(Eh, mh, flags=mcx.LOOKUP_FAST | mcx.LOOKUP_SORT)
+    assert torch.equal(host3, dev.cpu())
 
 
 def test_backward_matches_oracle_adjoint(torch_cuda):

@@ -134,6 +134,23 @@ def test_resume_from_a_history_offset(mcx, config1):
     assert_tallies_close(p.tallies(), ref)
 
 
+def test_reused_handle_honours_a_smaller_in_flight_count(mcx, config1):
+    """A handle keeps its largest particle buffer; a later run with fewer
+    particles in flight must still use only that many slots."""
+    prob, ref = config1
+    p = mcx.make_problem(prob, flags=mcx.FLAG_HISTORY_DEBUG)
+    p.run(particles_in_flight=5000, seed=7)
+    it_big = p.stats()["iterations"]
+    p.zero_tallies()
+    p.run(particles_in_flight=500, seed=7)
+    it_small = p.stats()["iterations"]
+    assert it_small > 2 * it_big, (it_small, it_big)
+    assert np.array_equal(p.history_debug(prob.n_histories), ref["ncoll"])
+    fresh = mcx.make_problem(prob)
+    fresh.run(particles_in_flight=500, seed=7)
+    assert abs(fresh.stats()["iterations"] - it_small) <= 0.05 * it_small
+
+
 def test_iteration_cap_returns_an_error_and_the_handle_stays_usable(mcx, config1):
     prob, ref = config1
     p = mcx.make_problem(prob)
