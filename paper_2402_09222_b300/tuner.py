@@ -116,14 +116,17 @@ def key_of(cfg: dict) -> str:
 @dataclass
 class Record:
     config: dict
-    seconds: float | None      # None: timed out or failed
+    seconds: float | None      # the objective (run time, energy or EDP); None: timed out or failed
     status: str                # "ok" | "timeout" | "error"
     kind: str                  # "baseline" | "random" | "cd" | "bo"
+    runtime: float | None = None   # wall seconds of the run (for the time limit)
 
 
 @dataclass
 class Tuner:
-    """objective(config, time_limit_s) -> seconds, or raises TimeoutError."""
+    """objective(config, time_limit_s) -> value, or (value, run seconds) when
+    the value is not a time (energy, EDP); raises TimeoutError past the limit.
+    The limit is timeout_factor x the baseline's run seconds."""
     space: list[Param]
     objective: Callable[[dict, float], float]
     db_path: str | None = None
@@ -140,14 +143,20 @@ class Tuner:
             for line in open(self.db_path):
                 if line.strip():
                     d = json.loads(line)
-                    r = Record(d["config"], d["seconds"], d["status"], d["kind"])
+                    r = Record(d["config"], d["seconds"], d["status"], d["kind"], d.get("runtime"))
                     self.records.append(r)
                     if r.kind != "baseline":
                         self._done[key_of(r.config)] = r
         self.baseline = None
-        base = [r.seconds for r in self.records if r.kind == "baseline" and r.seconds]
+        self.baseline_runtime = None
+        base = [r for r in self.records if r.kind == "baseline" and r.seconds]
         if len(base) >= self.baseline_repeats:
-            self.baseline = min(base)
+            self._set_baseline(base)
+
+    def _set_baseline(self, base):
+        self.baseline = min(r.seconds for r in base)
+        rts = [r.runtime for r in base if r.runtime]
+        self.baseline_runtime = min(rts) if rts else self.baseline
 
     # -- bookkeeping
     def default_config(self) -> dict:
@@ -158,17 +167,21 @@ class Tuner:
         if self.db_path:
             with open(self.db_path, "a") as f:
                 f.write(json.dumps({"config": r.config, "seconds": r.seconds, "status": r.status,
-                                    "kind": r.kind, "time": time.time()}) + "\n")
+                                    "kind": r.kind, "runtime": r.runtime, "time": time.time()}) + "\n")
 
     def evaluate(self, cfg: dict, kind: str) -> Record:
         cfg = canonical(self.space, cfg)
         k = key_of(cfg)
         if kind != "baseline" and k in self._done:
             return self._done[k]
-        limit = self.timeout_factor * self.baseline if (self.baseline and kind != "baseline") else 0.0
+        limit = (self.timeout_factor * self.baseline_runtime
+                 if (self.baseline_runtime and kind != "baseline") else 0.0)
         try:
-            s = float(self.objective(cfg, limit))
-            r = Record(cfg, s, "ok", kind)
+            v = self.objective(cfg, limit)
+            if isinstance(v, tuple):
+                r = Record(cfg, float(v[0]), "ok", kind, float(v[1]))
+            else:
+                r = Record(cfg, float(v), "ok", kind, float(v))
         except TimeoutError:
             r = Record(cfg, None, "timeout", kind)
         except Exception as e:  # a configuration the library rejects counts as a failure
@@ -190,10 +203,10 @@ class Tuner:
         have = [r for r in self.records if r.kind == "baseline" and r.seconds]
         for _ in range(self.baseline_repeats - len(have)):
             self.evaluate(self.default_config(), "baseline")
-        base = [r.seconds for r in self.records if r.kind == "baseline" and r.seconds]
+        base = [r for r in self.records if r.kind == "baseline" and r.seconds]
         if not base:
             raise RuntimeError("the default configuration failed")
-        self.baseline = min(base)
+        self._set_baseline(base)
         return self.baseline
 
     def random_config(self) -> dict:
@@ -278,12 +291,14 @@ class Tuner:
 # ---------------------------------------------------------------------------
 
 def transport_objective(prob, seed: int = 1, precision: int = 1, device: int = 0,
-                        max_in_flight: int | None = None):
-    """Seconds of one run of `prob` under a configuration (CUDA events around
-    mcx_run_batch).  Raises TimeoutError when the library reports its time
-    limit."""
+                        max_in_flight: int | None = None, metric: str = "time"):
+    """The objective of one run of `prob` under a configuration: its seconds
+    (CUDA events around mcx_run_batch), or with metric "energy"/"edp" the GPU
+    energy in joules (NVML counter) or energy x seconds (the paper's Sec. 7
+    objectives).  Raises TimeoutError when the library reports its time limit
+    (the limit is in seconds whatever the metric)."""
     import torch
-    from . import mcx
+    from . import energy, mcx
     handles = {}
 
     def objective(cfg: dict, limit: float) -> float:
@@ -301,16 +316,27 @@ def transport_objective(prob, seed: int = 1, precision: int = 1, device: int = 0
         p.zero_tallies()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
+        meter = energy.EnergyMeter(device) if metric != "time" else None
+        if meter:
+            meter.__enter__()
         a.record()
         try:
             p.run(particles_in_flight=pif, seed=seed)
         except mcx.McxError as e:
+            if meter:
+                meter.__exit__(None, None, None)
             if e.code == mcx.ERR_TIMEOUT:
                 raise TimeoutError(str(e)) from e
             raise
         b.record()
         torch.cuda.synchronize()
-        return a.elapsed_time(b) / 1e3
+        seconds = a.elapsed_time(b) / 1e3
+        joules = None
+        if meter:
+            meter.__exit__(None, None, None)
+            joules = meter.joules
+        value = energy.objective_value(metric, seconds, joules)
+        return value if metric == "time" else (value, seconds)
 
     return objective
 
@@ -361,12 +387,14 @@ def main(argv=None):
     ap.add_argument("--evals", type=int, default=40)
     ap.add_argument("--db", default=None, help="JSONL performance database (resumable)")
     ap.add_argument("--seed", type=int, default=1234)
+    ap.add_argument("--metric", choices=["time", "energy", "edp"], default="time",
+                    help="transport objective (the time limit is always 1.5x baseline seconds)")
     args = ap.parse_args(argv)
     from . import synth
     if args.workload == "transport":
         prob = synth.config3_problem(n_histories=args.histories)
         space = transport_space()
-        obj = transport_objective(prob, seed=5, precision=1)
+        obj = transport_objective(prob, seed=5, precision=1, metric=args.metric)
     else:
         lib = synth.species_library(355, 11_303, 1236)
         mats = synth.lookup_materials(355, 1236)

@@ -114,3 +114,57 @@ def test_rejected_configurations_count_as_failures(tmp_path):
     t.tune(n_random=16, max_evals=16)
     assert all(r.seconds is not None or r.status.startswith("error") or r.status == "timeout"
                for r in t.records)
+
+
+def test_energy_metric_keeps_the_time_limit_in_seconds(tmp_path):
+    """With an energy objective the limit is still 1.5 x the baseline's run
+    time, not 1.5 x its joules."""
+    limits = []
+
+    def obj(cfg, limit):
+        limits.append(limit)
+        t = 2.0 + 0.1 * (cfg["block_size"] != 256)
+        if limit and t > limit:
+            raise TimeoutError
+        return 500.0 * t, t          # (joules, seconds)
+
+    t = tuner.Tuner(tuner.transport_space(), obj, db_path=str(tmp_path / "db.jsonl"), seed=4)
+    t.run_baseline()
+    assert t.baseline == pytest.approx(1000.0) and t.baseline_runtime == pytest.approx(2.0)
+    t.tune(n_random=4, max_evals=4)
+    assert limits[-1] == pytest.approx(3.0)
+    t2 = tuner.Tuner(tuner.transport_space(), obj, db_path=str(tmp_path / "db.jsonl"), seed=4)
+    assert t2.baseline_runtime == pytest.approx(2.0)
+
+
+def test_energy_meter_with_a_fake_counter():
+    from paper_2402_09222_b300 import energy
+
+    class FakeNvml:
+        def __init__(self):
+            self.mj = 1_000_000
+            self.calls = []
+
+        def nvmlInit(self):
+            self.calls.append("init")
+
+        def nvmlShutdown(self):
+            self.calls.append("shutdown")
+
+        def nvmlDeviceGetHandleByIndex(self, i):
+            return ("dev", i)
+
+        def nvmlDeviceGetTotalEnergyConsumption(self, h):
+            self.mj += 250_000          # 250 J per reading
+            return self.mj
+
+    nv = FakeNvml()
+    with energy.EnergyMeter(3, nvml=nv) as m:
+        pass
+    assert m.joules == pytest.approx(250.0)
+    assert m.edp == pytest.approx(m.joules * m.seconds)
+    assert nv.calls == ["init", "shutdown"]
+    assert energy.objective_value("edp", 2.0, 10.0) == 20.0
+    assert energy.objective_value("time", 2.0, None) == 2.0
+    with pytest.raises(ValueError):
+        energy.objective_value("energy", 2.0, None)
