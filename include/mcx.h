@@ -255,8 +255,8 @@ int mcx_xs_lookup(mcx_problem* p, int64_t n, const double* E, const int32_t* mat
 /* Binning of lookups by material and energy (Sec. 5.1: sorting so that
  * neighbouring threads work on the same material and nearby energies):
  * perm (int32 [n], DEVICE) receives 0..n-1 ordered by (material, bucket of
- * log E) with 1024 buckets per material (fewer when materials x buckets would
- * exceed 12288 bins).  Order within a bucket is unspecified.  E and mat are
+ * log E) with 16384 buckets per material (fewer when materials x buckets
+ * would exceed 2^21 bins).  Order within a bucket is unspecified.  E and mat are
  * DEVICE pointers.  Uses a small library-owned bin array (allocated on first
  * use).  Errors: MCX_ERR_ARG, MCX_ERR_STATE, MCX_ERR_CUDA, MCX_ERR_OOM. */
 int mcx_xs_sort(mcx_problem* p, int64_t n, const double* E, const int32_t* mat, int32_t* perm,
@@ -279,8 +279,9 @@ int mcx_xs_lookup_ordered(mcx_problem* p, int64_t n, const double* E, const int3
  * library is loaded onto a device and kept until the process exits; the call
  * itself allocates nothing.  Inputs and outputs are the caller's DEVICE
  * buffers, as for mcx_xs_lookup; flags may hold MCX_LOOKUP_FAST.
- * Limits: n <= MCX_STATIC_MAX_LOOKUPS, and materials x energy buckets <=
- * MCX_STATIC_MAX_BINS; larger requests fail with MCX_ERR_ARG.
+ * Limits: n <= MCX_STATIC_MAX_LOOKUPS; the binning uses at most
+ * MCX_STATIC_MAX_BINS bins (energy buckets per material are reduced to fit),
+ * and more materials than that fail with MCX_ERR_ARG.
  * The first call on a device looks up the scratch's device address (a
  * one-time set-up per device); make that first call before any stream
  * capture.  All calls on a device share the one scratch: calls that overlap

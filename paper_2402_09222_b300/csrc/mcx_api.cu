@@ -623,12 +623,16 @@ int ensure_lookup_scratch(mcx_problem* p, int64_t n, size_t)
     return MCX_OK;
 }
 
-SortParams lookup_sort_params(const TableStore* ts)
+// Binning of lookups: 16384 log-energy buckets per material (about one per
+// grid interval of the benchmark's 11,303-point grids, so a warp of binned
+// lookups mostly shares its bracketing points), fewer when materials x
+// buckets would exceed max_bins.
+SortParams lookup_sort_params(const TableStore* ts, int64_t max_bins = (int64_t)1 << 21)
 {
     SortParams sp;
     sp.n_materials = ts->view.n_materials;
-    sp.n_ebuckets = 1024;
-    while (sp.n_ebuckets > 1 && (size_t)sp.n_materials * sp.n_ebuckets * 4 > 48 * 1024) sp.n_ebuckets >>= 1;
+    sp.n_ebuckets = 16384;
+    while (sp.n_ebuckets > 1 && (int64_t)sp.n_materials * sp.n_ebuckets > max_bins) sp.n_ebuckets >>= 1;
     sp.ln_lo = (float)std::log(ts->emin);
     sp.scale = (float)((double)sp.n_ebuckets / (std::log(ts->emax) - std::log(ts->emin)));
     return sp;
@@ -685,7 +689,7 @@ int problem_lookup_view(const mcx_problem* p, LookupView* v)
     TRY(check_tables(p));
     const TableStore* ts = p->tables;
     v->tables = ts->view;
-    v->sort = lookup_sort_params(ts);
+    v->sort = lookup_sort_params(ts, MCX_STATIC_MAX_BINS);
     v->device = p->device;
     v->grid = lookup_grid(p);
     return MCX_OK;

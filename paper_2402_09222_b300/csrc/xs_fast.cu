@@ -32,6 +32,7 @@ namespace {
 #define MCX_FAST_MIN_BLOCKS 4
 #endif
 constexpr int kFastUnroll = MCX_FAST_UNROLL;
+constexpr int kSmemBins = 12288;   // histograms up to this size count in shared memory
 
 __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x)
 {
@@ -167,6 +168,16 @@ __global__ void k_lookup_sort_count(SortParams sp, int64_t n, const double* __re
         if (hist[i]) atomicAdd(&bins[i], hist[i]);
 }
 
+// The same count with the histogram in global memory, for bin counts that do
+// not fit in shared memory.
+__global__ void k_lookup_sort_count_global(SortParams sp, int64_t n, const double* __restrict__ E,
+                                           const int32_t* __restrict__ mat, uint32_t* __restrict__ bins)
+{
+    for (int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; l < n;
+         l += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&bins[lookup_key(sp, __ldg(E + l), __ldg(mat + l))], 1u);
+}
+
 __global__ void k_exclusive_scan(uint32_t* __restrict__ bins, int nb)
 {
     __shared__ uint32_t warp_sums[32];
@@ -240,7 +251,10 @@ int launch_lookup_sort(const SortParams& sp, int64_t n, const double* E, const i
 {
     const int nb = sp.n_materials * sp.n_ebuckets;
     if (cudaMemsetAsync(bins, 0, sizeof(uint32_t) * (size_t)(nb + 1), st) != cudaSuccess) return -1;
-    k_lookup_sort_count<<<grid, 512, sizeof(uint32_t) * nb, st>>>(sp, n, E, mat, bins);
+    if (nb <= kSmemBins)
+        k_lookup_sort_count<<<grid, 512, sizeof(uint32_t) * nb, st>>>(sp, n, E, mat, bins);
+    else
+        k_lookup_sort_count_global<<<grid, 256, 0, st>>>(sp, n, E, mat, bins);
     k_exclusive_scan<<<1, 1024, 0, st>>>(bins, nb);
     k_lookup_sort_scatter<<<grid, 256, 0, st>>>(sp, n, E, mat, bins, perm);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;

@@ -81,6 +81,73 @@ class Param:
         return float(v)
 
 
+class RandomForest:
+    """A small random-forest regressor (the surrogate of Sec. 2.1): bootstrap
+    samples, CART regression trees split on the largest decrease of squared
+    error over a random subset of features, leaves of at least
+    `min_leaf` samples.  `predict_trees` returns each tree's predictions, whose
+    mean and spread give mu(x) and sigma(x) for the LCB acquisition."""
+
+    def __init__(self, n_trees: int = 100, max_features: float = 0.6, min_leaf: int = 1,
+                 max_depth: int = 12, seed: int = 0):
+        self.n_trees, self.max_features = n_trees, max_features
+        self.min_leaf, self.max_depth = min_leaf, max_depth
+        self.rng = random.Random(seed)
+        self.trees = []
+
+    def fit(self, X, y):
+        n = len(X)
+        self.trees = []
+        for _ in range(self.n_trees):
+            idx = [self.rng.randrange(n) for _ in range(n)]
+            self.trees.append(self._grow([X[i] for i in idx], [y[i] for i in idx], 0))
+        return self
+
+    def _grow(self, X, y, depth):
+        mean = sum(y) / len(y)
+        if depth >= self.max_depth or len(y) < 2 * self.min_leaf or max(y) - min(y) < 1e-12:
+            return mean
+        d = len(X[0])
+        feats = self.rng.sample(range(d), max(1, int(round(self.max_features * d))))
+        best = None
+        total_sq = sum(v * v for v in y)
+        for f in feats:
+            order = sorted(range(len(y)), key=lambda i: X[i][f])
+            s_left = sq_left = 0.0
+            s_all = sum(y)
+            for k in range(len(order) - 1):
+                v = y[order[k]]
+                s_left += v
+                sq_left += v * v
+                nl, nr = k + 1, len(order) - k - 1
+                if nl < self.min_leaf or nr < self.min_leaf:
+                    continue
+                a, b = X[order[k]][f], X[order[k + 1]][f]
+                if a == b:
+                    continue
+                s_right = s_all - s_left
+                sse = (sq_left - s_left * s_left / nl) + ((total_sq - sq_left) - s_right * s_right / nr)
+                if best is None or sse < best[0]:
+                    best = (sse, f, 0.5 * (a + b))
+        if best is None:
+            return mean
+        _, f, thr = best
+        left = [i for i in range(len(y)) if X[i][f] <= thr]
+        right = [i for i in range(len(y)) if X[i][f] > thr]
+        return (f, thr, self._grow([X[i] for i in left], [y[i] for i in left], depth + 1),
+                self._grow([X[i] for i in right], [y[i] for i in right], depth + 1))
+
+    @staticmethod
+    def _predict_one(node, x):
+        while isinstance(node, tuple):
+            f, thr, l, r = node
+            node = l if x[f] <= thr else r
+        return node
+
+    def predict_trees(self, X):
+        return [[self._predict_one(t, x) for x in X] for t in self.trees]
+
+
 def transport_space(max_in_flight: int = 8_000_000) -> list[Param]:
     return [
         Param("mode", "choice", choices=(QUEUED, QUEUELESS), default=QUEUED),
@@ -213,12 +280,15 @@ class Tuner:
         cfg = {p.name: p.sample(self.rng) for p in self.space}
         return canonical(self.space, cfg)
 
-    def tune(self, n_random: int = 24, max_evals: int = 64, strategy: str = "random+cd") -> Record:
+    def tune(self, n_random: int = 24, max_evals: int = 64, strategy: str = "random+cd",
+             kappa: float = 1.96) -> Record:
+        """kappa: exploration weight of the LCB acquisition (the paper's
+        default 1.96; 0 exploits the surrogate's mean only)."""
         if self.baseline is None:
             self.run_baseline()
         n_eval = lambda: sum(1 for r in self.records if r.kind != "baseline")
         if strategy == "bo":
-            return self._bo(n_random, max_evals, n_eval)
+            return self._bo(n_random, max_evals, n_eval, kappa=kappa)
         while n_eval() < min(n_random, max_evals):
             self.evaluate(self.random_config(), "random")
         improved = True
@@ -246,7 +316,6 @@ class Tuner:
         return [p.encode(cfg.get(p.name, p.default)) for p in self.space]
 
     def _bo(self, n_init, max_evals, n_eval, kappa: float = 1.96, n_candidates: int = 512):
-        from sklearn.ensemble import RandomForestRegressor
         while n_eval() < min(n_init, max_evals):
             self.evaluate(self.random_config(), "random")
         while n_eval() < max_evals:
@@ -254,22 +323,28 @@ class Tuner:
                     for r in self.records]
             X = [d[0] for d in data]
             y = [d[1] for d in data]
-            rf = RandomForestRegressor(n_estimators=100, random_state=self.rng.randrange(2**31),
-                                       min_samples_leaf=1)
-            rf.fit(X, y)
+            rf = RandomForest(n_trees=100, seed=self.rng.randrange(2**31)).fit(X, y)
             cands = [self.random_config() for _ in range(n_candidates)]
-            best = self.best().config
-            full = {p.name: best.get(p.name, p.default) for p in self.space}
-            for p in self.space:           # local candidates around the incumbent
-                for v in p.neighbours(full[p.name]):
+            # local candidates around the best configurations so far: every
+            # single-coordinate neighbour and random two-coordinate moves
+            top = sorted((r for r in self.records if r.seconds is not None), key=lambda r: r.seconds)[:5]
+            for rec in top:
+                full = {p.name: rec.config.get(p.name, p.default) for p in self.space}
+                for p in self.space:
+                    for v in p.neighbours(full[p.name]):
+                        c = dict(full)
+                        c[p.name] = v
+                        cands.append(canonical(self.space, c))
+                for _ in range(32):
                     c = dict(full)
-                    c[p.name] = v
+                    for p in self.rng.sample(self.space, 2):
+                        c[p.name] = self.rng.choice(p.neighbours(c[p.name]) or [c[p.name]])
                     cands.append(canonical(self.space, c))
             cands = [c for c in cands if key_of(c) not in self._done]
             if not cands:
                 break
             Xc = [self._features(c) for c in cands]
-            per_tree = [t.predict(Xc) for t in rf.estimators_]
+            per_tree = rf.predict_trees(Xc)
             mu = [sum(col) / len(col) for col in zip(*per_tree)]
             sd = [math.sqrt(max(sum((v - m) ** 2 for v in col) / len(col), 0.0))
                   for col, m in zip(zip(*per_tree), mu)]

@@ -198,3 +198,47 @@ def test_config2_full_size_sampled(torch_cuda):
     got64 = out64[torch.as_tensor(idx, device="cuda")].cpu().numpy()
     ref64 = oracle.xs_lookup(lib, mats, E[idx], mat[idx], n_threads=8)
     assert np.array_equal(got64.view(np.uint64), ref64.view(np.uint64))
+
+
+@pytest.mark.parametrize("n_ch", [1, 2, 3, 5])
+@pytest.mark.parametrize("H", [0, 1, 100_000])
+def test_fast_path_every_record_width_and_hash_size(torch_cuda, n_ch, H):
+    """Point records hold one float4 for n_ch <= 2 and two above; every width
+    and hash size must stay within the fast tolerance, binned or not."""
+    from paper_2402_09222_b300 import mcx
+    torch = torch_cuda
+    full = synth.species_library(25, 600, 601)
+    lib = full.channels(list(range(n_ch)))
+    mats = synth.lookup_materials(25, 602, n_materials=5)
+    E, mat = synth.lookup_inputs(30_001, mats.n_materials, 603)
+    ref = oracle.xs_lookup(lib.fp32_rounded(), mats, E, mat, n_threads=8)
+    p = _handle(lib, mats, mcx.FP32, H)
+    dE, dm = _dev(torch, E, torch.float64), _dev(torch, mat, torch.int32)
+    for flags in (mcx.LOOKUP_FAST, mcx.LOOKUP_FAST | mcx.LOOKUP_SORT):
+        out = p.xs_lookup(dE, dm, flags=flags).cpu().numpy()
+        rel = np.abs(out - ref) / np.maximum(np.abs(ref), 1e-300)
+        assert out.shape == (len(E), n_ch)
+        assert rel.max() <= FAST_RTOL, (flags, rel.max())
+    # exact path on the same handle stays bit-identical
+    out = p.xs_lookup(dE, dm).cpu().numpy()
+    assert np.array_equal(out.view(np.uint64), ref.view(np.uint64))
+
+
+def test_zero_and_subnormal_table_entries(torch_cuda):
+    """FP32 tables widen to FP64 with integer operations except for zero and
+    FP32-subnormal values; both must come out exact."""
+    from paper_2402_09222_b300 import mcx
+    torch = torch_cuda
+    lib = synth.species_library(6, 200, 611)
+    sig = lib.sigma.copy()
+    sig[::7, 3] = 0.0
+    sig[::11, 1] = 1e-40          # subnormal in FP32
+    sig[::13, 2] = 3e-39          # subnormal in FP32
+    lib = synth.Library(lib.grid_offsets, lib.energies, sig, lib.awr)
+    mats = synth.lookup_materials(6, 612, n_materials=3)
+    E, mat = synth.lookup_inputs(20_000, mats.n_materials, 613)
+    E[:500] = lib.energies[np.random.default_rng(1).integers(0, len(lib.energies), 500)]
+    ref = oracle.xs_lookup(lib.fp32_rounded(), mats, E, mat)
+    p = _handle(lib, mats, mcx.FP32, 300)
+    out = p.xs_lookup(_dev(torch, E, torch.float64), _dev(torch, mat, torch.int32)).cpu().numpy()
+    assert np.array_equal(out.view(np.uint64), ref.view(np.uint64))

