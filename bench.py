@@ -324,6 +324,22 @@ def main():
                 and tr.get("hash_bins") == TUNED["hash_bins"]):
             roofline["traffic"] = tr["dram_bytes_per_launch"]
 
+    # the same kernel on the natural (unbinned) order, where every species'
+    # records are a real gather from L2/HBM: the roofline of the gather itself
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p.xs_lookup_ordered(dE, dm, None, out=out, flags=TUNED["flags"])
+    a.record(stream)
+    p.xs_lookup_ordered(dE, dm, None, out=out, flags=TUNED["flags"])
+    b.record(stream)
+    torch.cuda.synchronize()
+    nat_ms = a.elapsed_time(b)
+    nat = alg / (nat_ms / 1e3) / 1e9
+    roofline["natural_order"] = {"lookup_kernel_ms": nat_ms, "achieved": nat, "frac": nat / peak,
+                                 "lookups_per_s": N_LOOKUPS / (nat_ms / 1e3)}
+    roofline["note"] = ("binning makes a warp's 32 lookups share each species' bracketing records, "
+                        "so the algorithmic bytes per second exceed HBM while measured DRAM traffic "
+                        "(`traffic`) is ~8 % of them; the binned kernel is bound by instruction issue")
+
     line = {"metric": "XS lookups/s (tuned lookup; particles/s of the transport in 'transport')",
             "value": value, "unit": "lookups/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,

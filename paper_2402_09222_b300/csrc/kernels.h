@@ -9,8 +9,13 @@ namespace mcx {
 // ---------------------------------------------------------------- lookups
 int launch_xs_lookup_exact(const Tables& t, int64_t n, const double* E, const int32_t* mat,
                            const int32_t* perm, double* out, int grid, cudaStream_t st);
+// resident 256-thread blocks per SM of the fast lookup (its register cap)
+constexpr int kFastBlocksPerSm = 4;
+// work: a device counter for in-order chunked scheduling of binned orders
+// (zeroed by the launch), or nullptr for a grid-stride loop.
 int launch_xs_lookup_fast(const Tables& t, int64_t n, const double* E, const int32_t* mat,
-                          const int32_t* perm, double* out, int grid, cudaStream_t st);
+                          const int32_t* perm, double* out, int grid, cudaStream_t st,
+                          unsigned long long* work = nullptr);
 int launch_xs_indices(const Tables& t, int64_t n, const double* E, const int32_t* mat,
                       int32_t max_species, int32_t* kout, int grid, cudaStream_t st);
 int launch_build_hash(const Tables& t, int32_t* hidx, int grid, cudaStream_t st);

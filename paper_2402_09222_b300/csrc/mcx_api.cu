@@ -179,6 +179,7 @@ struct mcx_problem {
     int64_t perm_cap = 0;
     size_t lbins_cap = 0;
     double* h_buf = nullptr;  // host-path device staging
+    unsigned long long* work_ctr = nullptr;  // chunk counters of the binned fast lookup (2)
     int64_t h_buf_cap = 0;
     int64_t stats[3] = {0, 0, 0};
 };
@@ -655,12 +656,22 @@ int sort_device(mcx_problem* p, int64_t n, const double* E, const int32_t* mat, 
 }
 
 // Lookup on device buffers, queued on `st`, in the order `perm` (or natural).
+// A binned order (perm != nullptr) on the fast path is swept in order by
+// warps claiming chunks from a counter (slot `ctr` of the problem's two),
+// with one resident grid of blocks.
 int lookup_device_ordered(mcx_problem* p, int64_t n, const double* E, const int32_t* mat,
-                          const int32_t* perm, double* out, int32_t flags, cudaStream_t st)
+                          const int32_t* perm, double* out, int32_t flags, cudaStream_t st,
+                          int ctr = 0)
 {
     const TableStore* ts = p->tables;
+    unsigned long long* work = nullptr;
+    if (perm && (flags & MCX_LOOKUP_FAST)) {
+        if (!p->work_ctr) TRY(dev_alloc(&p->work_ctr, 2));
+        work = p->work_ctr + ctr;
+    }
+    const int grid = work ? p->sm_count * kFastBlocksPerSm : lookup_grid(p);
     int r = (flags & MCX_LOOKUP_FAST)
-                ? launch_xs_lookup_fast(ts->view, n, E, mat, perm, out, lookup_grid(p), st)
+                ? launch_xs_lookup_fast(ts->view, n, E, mat, perm, out, grid, st, work)
                 : launch_xs_lookup_exact(ts->view, n, E, mat, perm, out, lookup_grid(p), st);
     if (r) return fail(MCX_ERR_CUDA, "lookup launch failed: %s", cudaGetErrorString(cudaGetLastError()));
     return MCX_OK;
@@ -801,6 +812,7 @@ void mcx_destroy(mcx_problem* p)
     dev_free(p->perm);
     dev_free(p->lbins);
     dev_free(p->h_buf);
+    dev_free(p->work_ctr);
     if (p->h_ctl) cudaFreeHost(p->h_ctl);
     if (p->ev_a) cudaEventDestroy(p->ev_a);
     if (p->ev_b) cudaEventDestroy(p->ev_b);
@@ -1249,7 +1261,7 @@ int mcx_xs_lookup_host(mcx_problem* p, int64_t n, const double* E_host, const in
                 return fail(MCX_ERR_CUDA, "lookup sort launch failed");
             perm = dP;
         }
-        TRY(lookup_device_ordered(p, m, dE, dM, perm, dO, flags & MCX_LOOKUP_FAST, st));
+        TRY(lookup_device_ordered(p, m, dE, dM, perm, dO, flags & MCX_LOOKUP_FAST, st, (int)(c & 1)));
         CUDA_TRY(cudaMemcpyAsync(out_host + off * nc, dO, 8 * m * nc, cudaMemcpyDeviceToHost, st));
     }
     CUDA_TRY(cudaStreamSynchronize(ss[0]));

@@ -33,6 +33,7 @@ namespace {
 #endif
 constexpr int kFastUnroll = MCX_FAST_UNROLL;
 constexpr int kSmemBins = 12288;   // histograms up to this size count in shared memory
+constexpr int kChunk = 128;        // lookups a warp claims at a time in binned order
 
 __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x)
 {
@@ -68,77 +69,108 @@ __device__ __forceinline__ void load_records(const float4* __restrict__ rec, int
 }
 
 template <int W, int U>
-__global__ void __launch_bounds__(256, MCX_FAST_MIN_BLOCKS) k_xs_lookup_fast(Tables t, int64_t n, const double* __restrict__ Ein,
-                                                        const int32_t* __restrict__ mat,
-                                                        const int32_t* __restrict__ perm,
-                                                        double* __restrict__ out)
+__device__ __forceinline__ void lookup_one(const Tables& t, int64_t j, const double* __restrict__ Ein,
+                                           const int32_t* __restrict__ mat,
+                                           const int32_t* __restrict__ perm, double* __restrict__ out)
 {
     constexpr int NCMAX = 4 * W - 2;   // channels a record can hold
     const int nc = t.n_ch;
     const int64_t H1 = (int64_t)t.H + 1;
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
-         j += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t l = perm ? (int64_t)__ldg(perm + j) : j;
-        const double E = __ldg(Ein + l);
-        const int32_t m = __ldg(mat + l);
-        if (m < 0 || m >= t.n_materials || E != E) {
-            for (int r = 0; r < nc; ++r) out[l * nc + r] = __longlong_as_double(0x7ff8000000000000LL);
-            continue;
-        }
-        float hi[NCMAX], lo[NCMAX];
+    const int64_t l = perm ? (int64_t)__ldg(perm + j) : j;
+    const double E = __ldg(Ein + l);
+    const int32_t m = __ldg(mat + l);
+    if (m < 0 || m >= t.n_materials || E != E) {
+        for (int r = 0; r < nc; ++r) out[l * nc + r] = __longlong_as_double(0x7ff8000000000000LL);
+        return;
+    }
+    float hi[NCMAX], lo[NCMAX];
 #pragma unroll
-        for (int r = 0; r < NCMAX; ++r) hi[r] = lo[r] = 0.f;
-        const float E_hi = (float)E;
-        const float E_lo = (float)(E - (double)E_hi);
-        const int64_t eb = search_key(E);
-        const int32_t hb = t.H > 0 ? hash_bin(t, E, eb) : 0;
-        const int32_t i0 = __ldg(t.moff + m), i1 = __ldg(t.moff + m + 1);
-        for (int32_t i = i0; i < i1; i += U) {
-            int32_t base[U], len[U];
-            float N[U];
+    for (int r = 0; r < NCMAX; ++r) hi[r] = lo[r] = 0.f;
+    const float E_hi = (float)E;
+    const float E_lo = (float)(E - (double)E_hi);
+    const int64_t eb = search_key(E);
+    const int32_t hb = t.H > 0 ? hash_bin(t, E, eb) : 0;
+    const int32_t i0 = __ldg(t.moff + m), i1 = __ldg(t.moff + m + 1);
+    for (int32_t i = i0; i < i1; i += U) {
+        int32_t base[U], len[U];
+        float N[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int32_t ii = i + u < i1 ? i + u : i1 - 1;
+            const int4 e = __ldg(t.ment + ii);
+            N[u] = i + u < i1 ? __int_as_float(e.w) : 0.f;
+            if (t.H > 0) {
+                const int32_t* h = t.hidx + (int64_t)e.z * H1 + hb;
+                const int32_t wlo = __ldg(h);
+                base[u] = e.x + wlo;
+                len[u] = __ldg(h + 1) - wlo + 1;
+            } else {
+                base[u] = e.x;
+                len[u] = e.y - 1;
+            }
+        }
+        for (int st = 0; st < t.search_steps; ++st) {
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                const int32_t ii = i + u < i1 ? i + u : i1 - 1;
-                const int4 e = __ldg(t.ment + ii);
-                N[u] = i + u < i1 ? __int_as_float(e.w) : 0.f;
-                if (t.H > 0) {
-                    const int32_t* h = t.hidx + (int64_t)e.z * H1 + hb;
-                    const int32_t wlo = __ldg(h);
-                    base[u] = e.x + wlo;
-                    len[u] = __ldg(h + 1) - wlo + 1;
-                } else {
-                    base[u] = e.x;
-                    len[u] = e.y - 1;
-                }
+                const int32_t h = len[u] >> 1;
+                if (ebits(__ldg(t.E + base[u] + h)) <= eb) base[u] += h;
+                len[u] -= h;
             }
-            for (int st = 0; st < t.search_steps; ++st) {
+        }
+        float part[NCMAX];
 #pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const int32_t h = len[u] >> 1;
-                    if (ebits(__ldg(t.E + base[u] + h)) <= eb) base[u] += h;
-                    len[u] -= h;
-                }
-            }
-            float part[NCMAX];
+        for (int r = 0; r < NCMAX; ++r) part[r] = 0.f;
 #pragma unroll
-            for (int r = 0; r < NCMAX; ++r) part[r] = 0.f;
+        for (int u = 0; u < U; ++u) {
+            float r0[4 * W], r1[4 * W];
+            load_records<W>(t.frec, base[u], r0, r1);
+            const float a = fmaxf((E_hi - r0[0]) + (E_lo - r0[1]), 0.f);
+            const float b = fmaxf((r1[0] - E_hi) + (r1[1] - E_lo), 0.f);
+            const float nw = N[u] * __frcp_rn(a + b);
+            const float w1 = nw * a, w0 = nw * b;
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                float r0[4 * W], r1[4 * W];
-                load_records<W>(t.frec, base[u], r0, r1);
-                const float a = fmaxf((E_hi - r0[0]) + (E_lo - r0[1]), 0.f);
-                const float b = fmaxf((r1[0] - E_hi) + (r1[1] - E_lo), 0.f);
-                const float nw = N[u] * __frcp_rn(a + b);
-                const float w1 = nw * a, w0 = nw * b;
-#pragma unroll
-                for (int r = 0; r < NCMAX; ++r) part[r] += fmaf(w0, r0[2 + r], w1 * r1[2 + r]);
-            }
-#pragma unroll
-            for (int r = 0; r < NCMAX; ++r) two_sum_acc(hi[r], lo[r], part[r]);
+            for (int r = 0; r < NCMAX; ++r) part[r] += fmaf(w0, r0[2 + r], w1 * r1[2 + r]);
         }
 #pragma unroll
-        for (int r = 0; r < NCMAX; ++r)
-            if (r < nc) out[l * nc + r] = (double)hi[r] + (double)lo[r];
+        for (int r = 0; r < NCMAX; ++r) two_sum_acc(hi[r], lo[r], part[r]);
+    }
+#pragma unroll
+    for (int r = 0; r < NCMAX; ++r)
+        if (r < nc) out[l * nc + r] = (double)hi[r] + (double)lo[r];
+}
+
+// Lookups are taken either with a grid-stride loop (work == nullptr) or, for
+// binned orders, in chunks of kChunk consecutive positions that warps claim
+// from the counter *work (zeroed before the launch): the whole GPU then
+// sweeps the binned order from front to back, so the lookups in flight at
+// any time sit in a narrow slice of (material, energy) and their tables stay
+// in L2.  With a grid-stride loop, warps in small materials run ahead of
+// those in large ones (up to 80x less work per lookup) and the lookups in
+// flight spread over all materials and energies.
+template <int W, int U>
+__global__ void __launch_bounds__(256, MCX_FAST_MIN_BLOCKS) k_xs_lookup_fast(Tables t, int64_t n, const double* __restrict__ Ein,
+                                                        const int32_t* __restrict__ mat,
+                                                        const int32_t* __restrict__ perm,
+                                                        double* __restrict__ out,
+                                                        unsigned long long* __restrict__ work)
+{
+    if (work == nullptr) {
+        for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+             j += (int64_t)gridDim.x * blockDim.x)
+            lookup_one<W, U>(t, j, Ein, mat, perm, out);
+        return;
+    }
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        unsigned long long base = 0ull;
+        if (lane == 0) base = atomicAdd(work, (unsigned long long)kChunk);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if ((int64_t)base >= n) break;
+#pragma unroll 1
+        for (int r = 0; r < kChunk / 32; ++r) {
+            const int64_t j = (int64_t)base + r * 32 + lane;
+            if (j < n) lookup_one<W, U>(t, j, Ein, mat, perm, out);
+        }
     }
 }
 
@@ -237,12 +269,14 @@ __global__ void k_lookup_sort_scatter(SortParams sp, int64_t n, const double* __
 }  // namespace
 
 int launch_xs_lookup_fast(const Tables& t, int64_t n, const double* E, const int32_t* mat,
-                          const int32_t* perm, double* out, int grid, cudaStream_t st)
+                          const int32_t* perm, double* out, int grid, cudaStream_t st,
+                          unsigned long long* work)
 {
+    if (work && cudaMemsetAsync(work, 0, sizeof(unsigned long long), st) != cudaSuccess) return -1;
     if (t.frec_w == 1)
-        k_xs_lookup_fast<1, kFastUnroll><<<grid, 256, 0, st>>>(t, n, E, mat, perm, out);
+        k_xs_lookup_fast<1, kFastUnroll><<<grid, 256, 0, st>>>(t, n, E, mat, perm, out, work);
     else
-        k_xs_lookup_fast<2, kFastUnroll><<<grid, 256, 0, st>>>(t, n, E, mat, perm, out);
+        k_xs_lookup_fast<2, kFastUnroll><<<grid, 256, 0, st>>>(t, n, E, mat, perm, out, work);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
