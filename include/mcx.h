@@ -54,8 +54,13 @@ extern "C" {
 #define MCX_FP32 1
 
 /* Event logic (Sec. 5.1, "queuing logic"). */
-#define MCX_QUEUELESS 0 /* every event kernel visits every slot */
-#define MCX_QUEUED 1    /* kernels visit device-built compacted queues */
+#define MCX_QUEUELESS 0       /* every event kernel visits every slot */
+#define MCX_QUEUED 1          /* every event kernel runs each iteration over its
+                                 device-built compacted queue */
+#define MCX_QUEUED_FULLEST 2  /* the paper's queued policy, decided on the device:
+                                 each step runs only the event kernel whose
+                                 queue (needs lookup / flight / collision /
+                                 refill) holds the most particles */
 
 /* Lookup options for mcx_xs_lookup (bit flags). */
 #define MCX_LOOKUP_EXACT 0 /* FP64 arithmetic, bit-identical to the plain definition */
@@ -112,14 +117,16 @@ typedef struct {
 } mcx_problem_desc;
 
 /* Event-loop tuning (Table 1 of the paper, mapped to this GPU).
- *   mode            MCX_QUEUELESS or MCX_QUEUED
+ *   mode            MCX_QUEUELESS, MCX_QUEUED or MCX_QUEUED_FULLEST
  *   block_size      threads per block of the event kernels (32..1024, /32)
  *   sort_period     bin the lookup and collision queues every this many
- *                   iterations (0 = never); queued mode only
+ *                   iterations (0 = never); queued modes only
  *   sort_threshold  ...and only when a queue holds at least this many
  *                   particles (the paper's minimum sorting threshold)
  *   iters_per_sync  event-loop iterations captured per CUDA graph launch
  *                   between host checks of the termination flag (>= 1)
+ *                   (in MCX_QUEUED_FULLEST an iteration is one step: a
+ *                   refill and the one event kernel selected)
  *   max_event_iters iteration cap of one run (0 = automatic); reaching it
  *                   returns MCX_ERR_ITER_LIMIT instead of looping on
  *   use_graph       1 = replay the captured loop body, 0 = plain launches
@@ -231,8 +238,12 @@ int mcx_zero_tallies(mcx_problem* p);
  * pointer, n <= that run's n_histories.  Synchronous. */
 int mcx_read_history_debug(mcx_problem* p, uint32_t* ncoll, int64_t n);
 
-/* Event-loop statistics of the last run: out[0] iterations, out[1] graph
- * launches, out[2] kernel launches.  HOST pointer, n >= 3. */
+/* Event-loop statistics of the last run: out[0] iterations (steps in
+ * MCX_QUEUED_FULLEST), out[1] graph launches, out[2] kernel launches, and
+ * when n >= 6, out[3..5] the steps that selected the lookup, flight and
+ * collision queue (MCX_QUEUED_FULLEST; 0 otherwise).  HOST pointer, n >= 3.
+ * An inconsistent queue state found on the device ends a run with
+ * MCX_ERR_STATE. */
 int mcx_last_run_stats(const mcx_problem* p, int64_t* out, int32_t n);
 
 /* Macroscopic cross-section lookup (Sec. 5.1, "the most expensive kernel"):

@@ -132,8 +132,22 @@ struct RunCtl {
     int n_xs[2], n_adv[2], n_dead[2];
     int n_coll;
     int sorted;               // this iteration's queue was binned
-    int pad;
+    int sort_which;           // queue binned this step (fullest mode): 0 XS, 1 collision
+    // fullest-queue mode: ring queues (absolute 64-bit positions, modulo the
+    // slot count), the ring of the flight queue that receives appends, and
+    // the step's selection
+    unsigned long long rq_head[5], rq_tail[5];
+    int adv_recv;
+    int sel;                  // SEL_* of this step, -1 = none
+    int sel_ring;             // RQ_* consumed this step
+    int pad2;
+    unsigned long long sel_begin, sel_end;
+    long long sel_count[3];   // steps that ran the lookup / flight / collision kernel
 };
+
+// Ring queues of the fullest-queue mode and the events that consume them.
+enum { RQ_XS = 0, RQ_ADV0 = 1, RQ_ADV1 = 2, RQ_COLL = 3, RQ_DEAD = 4, N_RQ = 5 };
+enum { SEL_XS = 0, SEL_ADV = 1, SEL_COLL = 2, SEL_DEAD = 3 };
 
 struct LoopConfig {
     int mode = MCX_QUEUELESS;

@@ -181,7 +181,7 @@ struct mcx_problem {
     double* h_buf = nullptr;  // host-path device staging
     unsigned long long* work_ctr = nullptr;  // chunk counters of the binned fast lookup (2)
     int64_t h_buf_cap = 0;
-    int64_t stats[3] = {0, 0, 0};
+    int64_t stats[6] = {0, 0, 0, 0, 0, 0};
 };
 
 namespace {
@@ -480,7 +480,7 @@ int run_loop(mcx_problem* owner, int n_prob, mcx_problem* const* probs, const in
     c.mode = tu.mode;
     c.block = tu.block_size;
     c.grid = owner->sm_count * blocks_per_sm(tu.block_size);
-    c.sort_period = tu.mode == MCX_QUEUED ? tu.sort_period : 0;
+    c.sort_period = tu.mode != MCX_QUEUELESS ? tu.sort_period : 0;
     c.sort_threshold = tu.sort_threshold;
     c.n_ebuckets = 128;
     c.n_sort_bins = t.n_materials * c.n_ebuckets;
@@ -567,7 +567,8 @@ int run_loop(mcx_problem* owner, int n_prob, mcx_problem* const* probs, const in
         }
     }
     if (kernels_per_iter == 0) {
-        kernels_per_iter = 5 + ((c.mode == MCX_QUEUED && c.sort_period > 0) ? 8 : 0);
+        const bool sorting = c.mode != MCX_QUEUELESS && c.sort_period > 0;
+        kernels_per_iter = c.mode == MCX_QUEUED_FULLEST ? 5 + (sorting ? 4 : 0) : 5 + (sorting ? 8 : 0);
     }
     int64_t launches = 0, kernels = 0;
     const int64_t max_launches = max_iters / K + 4;
@@ -607,6 +608,8 @@ int run_loop(mcx_problem* owner, int n_prob, mcx_problem* const* probs, const in
     owner->stats[0] = owner->h_ctl->iters;
     owner->stats[1] = launches;
     owner->stats[2] = kernels;
+    for (int e = 0; e < 3; ++e)
+        owner->stats[3 + e] = c.mode == MCX_QUEUED_FULLEST ? owner->h_ctl->sel_count[e] : 0;
     CUDA_TRY(cudaEventRecord(owner->ev_b, st));
     CUDA_TRY(cudaStreamWaitEvent(us, owner->ev_b, 0));
     return status;
@@ -1046,7 +1049,8 @@ int mcx_set_tuning(mcx_problem* p, const mcx_tune* t)
     g_err.clear();
     TRY(check_handle(p));
     if (!t) return fail(MCX_ERR_ARG, "tuning is NULL");
-    if (t->mode != MCX_QUEUELESS && t->mode != MCX_QUEUED) return fail(MCX_ERR_ARG, "unknown mode");
+    if (t->mode != MCX_QUEUELESS && t->mode != MCX_QUEUED && t->mode != MCX_QUEUED_FULLEST)
+        return fail(MCX_ERR_ARG, "unknown mode");
     if (t->block_size < 32 || t->block_size > 1024 || t->block_size % 32)
         return fail(MCX_ERR_ARG, "block_size must be a multiple of 32 in 32..1024");
     if (t->sort_period < 0) return fail(MCX_ERR_ARG, "sort_period must be >= 0");
@@ -1178,6 +1182,7 @@ int mcx_last_run_stats(const mcx_problem* p, int64_t* out, int32_t n)
     TRY(check_handle(p));
     if (!out || n < 3) return fail(MCX_ERR_ARG, "need room for 3 values");
     for (int i = 0; i < 3; ++i) out[i] = p->stats[i];
+    for (int i = 3; i < n && i < 6; ++i) out[i] = p->stats[i];
     return MCX_OK;
 }
 

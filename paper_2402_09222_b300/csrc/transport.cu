@@ -12,7 +12,19 @@
 // particles that do not need its event; in queued mode the kernels visit
 // device-built index queues (warp-ballot compaction) and never read a slot
 // they do not need.  Queue sizes stay on the device: no host round trip per
-// kernel.  Tally scores are reduced within each warp (lanes that hit the same
+// kernel.
+//
+// Fullest-queue mode (the paper's queued policy, Sec. 5.1, with the choice
+// made on the device instead of the host): every live particle sits in
+// exactly one state queue -- needs a lookup, needs a flight, needs a
+// collision -- and free slots sit in a fourth.  One step is
+//     refill (drains the free-slot queue) -> select -> [bin] -> the event
+//     kernel of the queue the select kernel found fullest
+// The queues are rings over the slot count with 64-bit head/tail positions;
+// the flight queue has two rings, so that the flight kernel, whose surviving
+// particles re-enter the flight queue, never appends into the ring it reads.
+// No kernel appends to the ring it consumes, and a slot is in at most one
+// ring, so a ring never holds more than the slot count.  Tally scores are reduced within each warp (lanes that hit the same
 // tally cell are found with __match_any_sync and summed with shuffles) and a
 // single FP64 atomicAdd per distinct cell is issued.
 #include "kernels.h"
@@ -42,6 +54,62 @@ __device__ __forceinline__ int warp_append(int* counter, bool want)
     if (lane_id() == leader) base = atomicAdd(counter, __popc(b));
     base = __shfl_sync(FULL, base, leader);
     return want ? base + __popc(b & lanes_below()) : -1;
+}
+
+// Where an event kernel takes its particles from: every slot (list == null),
+// a compacted list, or a segment of a ring (positions wrap at `wrap`).
+struct Src {
+    const int32_t* list;
+    int64_t n;
+    int64_t start;
+    int64_t wrap;
+};
+
+__device__ __forceinline__ Src all_slots(const Particles& P) { return Src{nullptr, P.cap, 0, 0}; }
+__device__ __forceinline__ Src plain_list(const int32_t* list, int64_t n)
+{
+    return Src{list, n, 0, INT64_MAX};
+}
+
+__device__ __forceinline__ int64_t src_at(const Src& s, int64_t i)
+{
+    if (!s.list) return i;
+    int64_t k = s.start + i;       // start < wrap and n <= wrap: one fold suffices
+    if (k >= s.wrap) k -= s.wrap;
+    return s.list[k];
+}
+
+__device__ __forceinline__ int32_t* ring_base(const Particles& P, int r)
+{
+    switch (r) {
+    case RQ_XS: return P.q_xs[0];
+    case RQ_ADV0: return P.q_adv[0];
+    case RQ_ADV1: return P.q_adv[1];
+    case RQ_COLL: return P.q_coll;
+    default: return P.q_dead[0];
+    }
+}
+
+// The segment the select kernel handed to this step's event kernel.
+__device__ __forceinline__ Src ring_segment(const Particles& P, const RunCtl* ctl)
+{
+    return Src{ring_base(P, ctl->sel_ring), (int64_t)(ctl->sel_end - ctl->sel_begin),
+               (int64_t)(ctl->sel_begin % (unsigned long long)P.cap), P.cap};
+}
+
+// Warp-aggregated append to ring r (every lane of the converged warp calls it).
+__device__ __forceinline__ void ring_push(const Particles& P, RunCtl* ctl, int r, bool want, int64_t slot)
+{
+    const unsigned b = __ballot_sync(FULL, want);
+    if (b == 0u) return;
+    const int leader = __ffs(b) - 1;
+    unsigned long long base = 0ull;
+    if (lane_id() == leader) base = atomicAdd(&ctl->rq_tail[r], (unsigned long long)__popc(b));
+    base = __shfl_sync(FULL, base, leader);
+    if (want) {
+        const unsigned long long pos = (base + __popc(b & lanes_below())) % (unsigned long long)P.cap;
+        ring_base(P, r)[pos] = (int32_t)slot;
+    }
 }
 
 // Azimuth (cos phi, sin phi) by rejection on pairs (2u-1, 2u-1) inside the
@@ -273,10 +341,10 @@ __device__ __forceinline__ State load_state(const Particles& P, int64_t slot, in
 
 // Deaths of this warp: outcome tallies (one atomic per distinct tally cell),
 // derivative outcome tallies, per-history debug counts, slot release, alive
-// count and (queued) the dead queue.  Every lane of the warp calls it.
+// count and (queued modes) the free-slot queue.  Every lane of the warp calls it.
 __device__ void finish_deaths(bool dies, int outcome, int64_t slot, int32_t pidx,
                               const ProblemDev* probs, const Particles& P, RunCtl* ctl, int M,
-                              bool queued, int par)
+                              int mode, int par)
 {
     const unsigned dm = __ballot_sync(FULL, dies);
     if (dm == 0u) return;
@@ -299,17 +367,20 @@ __device__ void finish_deaths(bool dies, int outcome, int64_t slot, int32_t pidx
         P.flags[slot] = 0;
     }
     if (lane_id() == 0) atomicSub(&ctl->n_alive, __popc(dm));
-    if (queued) {
+    if (mode == MCX_QUEUED) {
         const int pos = warp_append(&ctl->n_dead[par ^ 1], dies);
         if (dies) P.q_dead[par ^ 1][pos] = (int32_t)slot;
+    } else if (mode == MCX_QUEUED_FULLEST) {
+        ring_push(P, ctl, RQ_DEAD, dies, slot);
     }
 }
 
 // ------------------------------------------------------------------ kernels
 
 __global__ void k_run_init(Particles P, RunCtl* ctl, long long total, int n_prob,
-                           long long max_iters, int queued)
+                           long long max_iters, int mode)
 {
+    const bool queued = mode != MCX_QUEUELESS;   // every slot starts in the free-slot queue
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P.cap; i += stride) {
         P.flags[i] = 0;
@@ -333,6 +404,18 @@ __global__ void k_run_init(Particles P, RunCtl* ctl, long long total, int n_prob
         ctl->n_dead[0] = queued ? (int)P.cap : 0;
         ctl->n_coll = 0;
         ctl->sorted = 0;
+        ctl->sort_which = 0;
+        for (int r = 0; r < N_RQ; ++r) {
+            ctl->rq_head[r] = 0ull;
+            ctl->rq_tail[r] = 0ull;
+        }
+        ctl->rq_tail[RQ_DEAD] = mode == MCX_QUEUED_FULLEST ? (unsigned long long)P.cap : 0ull;
+        ctl->adv_recv = 0;
+        ctl->sel = -1;
+        ctl->sel_ring = 0;
+        ctl->sel_begin = 0ull;
+        ctl->sel_end = 0ull;
+        for (int e = 0; e < 3; ++e) ctl->sel_count[e] = 0;
     }
 }
 
@@ -341,15 +424,28 @@ __global__ void __launch_bounds__(1024) k_refill(LoopConfig c, Particles P, cons
 {
     if (ctl->error || ctl->done) return;
     const bool queued = c.mode == MCX_QUEUED;
+    const bool fq = c.mode == MCX_QUEUED_FULLEST;
     const int par = ctl->parity;
     const long long total = ctl->total;
     const int n_prob = ctl->n_prob;
-    const int64_t count = queued ? (int64_t)ctl->n_dead[par] : P.cap;
-    if ((long long)ctl->next >= total && queued) {
+    Src src = all_slots(P);
+    if (queued) {
+        src = plain_list(P.q_dead[par], ctl->n_dead[par]);
+    } else if (fq) {
+        // the whole free-slot ring; the select kernel that follows retires it
+        const unsigned long long h0 = ctl->rq_head[RQ_DEAD], t0 = ctl->rq_tail[RQ_DEAD];
+        src = Src{P.q_dead[0], (int64_t)(t0 - h0), (int64_t)(h0 % (unsigned long long)P.cap), P.cap};
+        if (src.n > P.cap) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) ctl->error = MCX_ERR_STATE;
+            return;
+        }
+    }
+    const int64_t count = src.n;
+    if ((long long)ctl->next >= total && (queued || fq)) {
         // nothing left to start: retire the dead slots
         for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
              i += (int64_t)gridDim.x * blockDim.x)
-            P.flags[P.q_dead[par][i]] = PF_RETIRED;
+            P.flags[src_at(src, i)] = PF_RETIRED;
         return;
     }
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -359,8 +455,8 @@ __global__ void __launch_bounds__(1024) k_refill(LoopConfig c, Particles P, cons
         int64_t slot = -1;
         bool want = false;
         if (i < count) {
-            if (queued) {
-                slot = P.q_dead[par][i];
+            if (queued || fq) {
+                slot = src_at(src, i);
                 want = true;
             } else {
                 slot = i;
@@ -390,6 +486,8 @@ __global__ void __launch_bounds__(1024) k_refill(LoopConfig c, Particles P, cons
             if (got) P.q_xs[par][pos] = (int32_t)slot;
             pos = warp_append(&ctl->n_adv[par], got);
             if (got) P.q_adv[par][pos] = (int32_t)slot;
+        } else if (fq) {
+            ring_push(P, ctl, RQ_XS, got, slot);
         }
         const unsigned gm = __ballot_sync(FULL, got);
         if (lane_id() == 0) added += __popc(gm);
@@ -401,20 +499,35 @@ template <typename T>
 __global__ void __launch_bounds__(1024) k_lookup(LoopConfig c, Tables t, Particles P, RunCtl* ctl)
 {
     if (ctl->error) return;
-    const bool queued = c.mode == MCX_QUEUED;
+    const bool fq = c.mode == MCX_QUEUED_FULLEST;
+    if (fq && ctl->sel != SEL_XS) return;
     const int par = ctl->parity;
-    const int64_t count = queued ? (int64_t)ctl->n_xs[par] : P.cap;
-    const int32_t* list = queued ? (ctl->sorted ? P.q_sorted : P.q_xs[par]) : nullptr;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t slot = list ? list[i] : i;
-        const uint8_t f = P.flags[slot];
-        if (!(f & PF_NEED_XS)) continue;
-        double st, sa;
-        macro_transport<T>(t, P.mat[slot], P.E[slot], st, sa, P.cum + slot * P.cum_stride);
-        P.sig_t[slot] = st;
-        P.sig_a[slot] = sa;
-        P.flags[slot] = f & (uint8_t)~PF_NEED_XS;
+    Src src = all_slots(P);
+    if (c.mode == MCX_QUEUED)
+        src = ctl->sorted ? plain_list(P.q_sorted, ctl->n_xs[par]) : plain_list(P.q_xs[par], ctl->n_xs[par]);
+    else if (fq)
+        src = ctl->sorted ? plain_list(P.q_sorted, (int64_t)(ctl->sel_end - ctl->sel_begin))
+                          : ring_segment(P, ctl);
+    const int adv = RQ_ADV0 + ctl->adv_recv;
+    const int64_t count = src.n;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < count; base += stride) {
+        const int64_t i = base + threadIdx.x;
+        int64_t slot = -1;
+        bool act = false;
+        if (i < count) {
+            slot = src_at(src, i);
+            const uint8_t f = P.flags[slot];
+            if (f & PF_NEED_XS) {
+                act = true;
+                double st, sa;
+                macro_transport<T>(t, P.mat[slot], P.E[slot], st, sa, P.cum + slot * P.cum_stride);
+                P.sig_t[slot] = st;
+                P.sig_a[slot] = sa;
+                P.flags[slot] = f & (uint8_t)~PF_NEED_XS;
+            }
+        }
+        if (fq) ring_push(P, ctl, adv, act, slot);
     }
 }
 
@@ -423,9 +536,14 @@ __global__ void __launch_bounds__(1024) k_advance(LoopConfig c, Particles P, con
 {
     if (ctl->error) return;
     const bool queued = c.mode == MCX_QUEUED;
+    const bool fq = c.mode == MCX_QUEUED_FULLEST;
+    if (fq && ctl->sel != SEL_ADV) return;
     const int par = ctl->parity;
-    const int64_t count = queued ? (int64_t)ctl->n_adv[par] : P.cap;
-    const int32_t* list = queued ? P.q_adv[par] : nullptr;
+    Src src = all_slots(P);
+    if (queued) src = plain_list(P.q_adv[par], ctl->n_adv[par]);
+    else if (fq) src = ring_segment(P, ctl);
+    const int adv = RQ_ADV0 + ctl->adv_recv;   // the ring not being read
+    const int64_t count = src.n;
     const int M = c.derivatives;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < count; base += stride) {
@@ -433,8 +551,8 @@ __global__ void __launch_bounds__(1024) k_advance(LoopConfig c, Particles P, con
         int64_t slot = -1;
         bool act = false;
         if (i < count) {
-            slot = list ? list[i] : i;
-            act = list ? true : (P.flags[slot] & PF_ALIVE) != 0;
+            slot = src_at(src, i);
+            act = src.list ? true : (P.flags[slot] & PF_ALIVE) != 0;
         }
         bool scored = false, dies = false, coll = false, survive = false, need_xs = false;
         int outcome = -1;
@@ -550,7 +668,7 @@ __global__ void __launch_bounds__(1024) k_advance(LoopConfig c, Particles P, con
                 }
             }
         }
-        finish_deaths(dies, outcome, slot, pidx, probs, P, ctl, M, queued, par);
+        finish_deaths(dies, outcome, slot, pidx, probs, P, ctl, M, c.mode, par);
         if (queued) {
             int pos = warp_append(&ctl->n_coll, coll);
             if (coll) P.q_coll[pos] = (int32_t)slot;
@@ -558,6 +676,10 @@ __global__ void __launch_bounds__(1024) k_advance(LoopConfig c, Particles P, con
             if (survive) P.q_adv[par ^ 1][pos] = (int32_t)slot;
             pos = warp_append(&ctl->n_xs[par ^ 1], need_xs);
             if (need_xs) P.q_xs[par ^ 1][pos] = (int32_t)slot;
+        } else if (fq) {
+            ring_push(P, ctl, RQ_COLL, coll, slot);
+            ring_push(P, ctl, RQ_XS, survive && need_xs, slot);
+            ring_push(P, ctl, adv, survive && !need_xs, slot);
         }
     }
 }
@@ -573,9 +695,16 @@ __global__ void __launch_bounds__(1024) k_collide(LoopConfig c, Tables t, Partic
 {
     if (ctl->error) return;
     const bool queued = c.mode == MCX_QUEUED;
+    const bool fq = c.mode == MCX_QUEUED_FULLEST;
+    if (fq && ctl->sel != SEL_COLL) return;
     const int par = ctl->parity;
-    const int64_t count = queued ? (int64_t)ctl->n_coll : P.cap;
-    const int32_t* list = queued ? (ctl->sorted ? P.q_sorted : P.q_coll) : nullptr;
+    Src src = all_slots(P);
+    if (queued)
+        src = ctl->sorted ? plain_list(P.q_sorted, ctl->n_coll) : plain_list(P.q_coll, ctl->n_coll);
+    else if (fq)
+        src = ctl->sorted ? plain_list(P.q_sorted, (int64_t)(ctl->sel_end - ctl->sel_begin))
+                          : ring_segment(P, ctl);
+    const int64_t count = src.n;
     const int M = c.derivatives;
     const int nc = t.n_ch, cs = t.ch_scatter, ca = t.ch_absorb;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -584,8 +713,8 @@ __global__ void __launch_bounds__(1024) k_collide(LoopConfig c, Tables t, Partic
         int64_t slot = -1;
         bool act = false;
         if (i < count) {
-            slot = list ? list[i] : i;
-            act = list ? true : (P.flags[slot] & PF_COLLIDE) != 0;
+            slot = src_at(src, i);
+            act = src.list ? true : (P.flags[slot] & PF_COLLIDE) != 0;
         }
         bool dies = false, survive = false;
         int outcome = -1;
@@ -681,12 +810,14 @@ __global__ void __launch_bounds__(1024) k_collide(LoopConfig c, Tables t, Partic
                 }
             }
         }
-        finish_deaths(dies, outcome, slot, pidx, probs, P, ctl, M, queued, par);
+        finish_deaths(dies, outcome, slot, pidx, probs, P, ctl, M, c.mode, par);
         if (queued) {
             int pos = warp_append(&ctl->n_xs[par ^ 1], survive);
             if (survive) P.q_xs[par ^ 1][pos] = (int32_t)slot;
             pos = warp_append(&ctl->n_adv[par ^ 1], survive);
             if (survive) P.q_adv[par ^ 1][pos] = (int32_t)slot;
+        } else if (fq) {
+            ring_push(P, ctl, RQ_XS, survive, slot);
         }
     }
 }
@@ -711,6 +842,57 @@ __global__ void k_bookkeep(RunCtl* ctl)
     }
 }
 
+// Fullest-queue mode: retire the free-slot ring the refill just drained, stop
+// when no particle is left in any queue, and hand the fullest of the lookup,
+// flight and collision queues to this step's event kernel (ties go to the
+// earlier event of the sequence lookup, flight, collision).  One thread.
+__global__ void k_fq_select(RunCtl* ctl, long long cap)
+{
+    ctl->sel = -1;
+    ctl->sorted = 0;
+    if (ctl->error || ctl->done) return;
+    ctl->rq_head[RQ_DEAD] = ctl->rq_tail[RQ_DEAD];
+    const int adv = RQ_ADV0 + ctl->adv_recv;
+    const unsigned long long nx = ctl->rq_tail[RQ_XS] - ctl->rq_head[RQ_XS];
+    const unsigned long long na = ctl->rq_tail[adv] - ctl->rq_head[adv];
+    const unsigned long long nc = ctl->rq_tail[RQ_COLL] - ctl->rq_head[RQ_COLL];
+    const unsigned long long idle = ctl->rq_tail[adv ^ 3] - ctl->rq_head[adv ^ 3];
+    if (nx > (unsigned long long)cap || na > (unsigned long long)cap || nc > (unsigned long long)cap ||
+        idle != 0ull) {
+        ctl->error = MCX_ERR_STATE;   // a queue invariant broke: stop before any wrapped read
+        ctl->done = 1;
+        return;
+    }
+    if (nx == 0ull && na == 0ull && nc == 0ull) {
+        ctl->done = 1;
+        return;
+    }
+    if (ctl->iters >= ctl->max_iters) {
+        ctl->error = MCX_ERR_ITER_LIMIT;
+        ctl->done = 1;
+        return;
+    }
+    ctl->iters += 1;
+    int sel = SEL_XS, ring = RQ_XS;
+    unsigned long long n = nx;
+    if (na > n) {
+        sel = SEL_ADV;
+        ring = adv;
+        n = na;
+    }
+    if (nc > n) {
+        sel = SEL_COLL;
+        ring = RQ_COLL;
+    }
+    ctl->sel = sel;
+    ctl->sel_count[sel] += 1;
+    ctl->sel_ring = ring;
+    ctl->sel_begin = ctl->rq_head[ring];
+    ctl->sel_end = ctl->rq_tail[ring];
+    ctl->rq_head[ring] = ctl->rq_tail[ring];
+    if (sel == SEL_ADV) ctl->adv_recv ^= 1;
+}
+
 // ---- binning of a queue by (material, log-energy bucket)
 __device__ __forceinline__ int sort_key(const LoopConfig& c, double E, int32_t m)
 {
@@ -720,11 +902,21 @@ __device__ __forceinline__ int sort_key(const LoopConfig& c, double E, int32_t m
     return m * c.n_ebuckets + b;
 }
 
-// which: 0 = XS queue (consumed side), 1 = collision queue
+// which: 0 = XS queue (consumed side), 1 = collision queue, 2 = the segment
+// the fullest-queue select kernel chose, when it is a lookup or collision one
+__device__ __forceinline__ Src sort_source(const Particles& P, const RunCtl* ctl, int which)
+{
+    const int par = ctl->parity;
+    if (which == 2) return ring_segment(P, ctl);
+    return which == 0 ? plain_list(P.q_xs[par], ctl->n_xs[par]) : plain_list(P.q_coll, ctl->n_coll);
+}
+
 __global__ void k_sort_decide(LoopConfig c, RunCtl* ctl, int which)
 {
     const int par = ctl->parity;
-    const long long n = which == 0 ? ctl->n_xs[par] : ctl->n_coll;
+    long long n = which == 0 ? ctl->n_xs[par] : ctl->n_coll;
+    if (which == 2)
+        n = (ctl->sel == SEL_XS || ctl->sel == SEL_COLL) ? (long long)(ctl->sel_end - ctl->sel_begin) : 0;
     ctl->sorted = (!ctl->error && c.sort_period > 0 && (ctl->iters % c.sort_period) == 0 &&
                    n >= c.sort_threshold && n > 0)
                       ? 1
@@ -735,14 +927,13 @@ __global__ void k_sort_count(LoopConfig c, Particles P, RunCtl* ctl, int which)
 {
     extern __shared__ uint32_t hist[];
     if (!ctl->sorted) return;
-    const int par = ctl->parity;
-    const int64_t n = which == 0 ? ctl->n_xs[par] : ctl->n_coll;
-    const int32_t* list = which == 0 ? P.q_xs[par] : P.q_coll;
+    const Src src = sort_source(P, ctl, which);
+    const int64_t n = src.n;
     for (int i = threadIdx.x; i < c.n_sort_bins; i += blockDim.x) hist[i] = 0u;
     __syncthreads();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t s = list[i];
+        const int32_t s = (int32_t)src_at(src, i);
         atomicAdd(&hist[sort_key(c, P.E[s], P.mat[s])], 1u);
     }
     __syncthreads();
@@ -790,16 +981,15 @@ __global__ void k_sort_scan(LoopConfig c, Particles P, RunCtl* ctl)
 __global__ void k_sort_scatter(LoopConfig c, Particles P, RunCtl* ctl, int which)
 {
     if (!ctl->sorted) return;
-    const int par = ctl->parity;
-    const int64_t n = which == 0 ? ctl->n_xs[par] : ctl->n_coll;
-    const int32_t* list = which == 0 ? P.q_xs[par] : P.q_coll;
+    const Src src = sort_source(P, ctl, which);
+    const int64_t n = src.n;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
         const int64_t i = base + threadIdx.x;
         const bool valid = i < n;
         const unsigned vm = __ballot_sync(FULL, valid);
         if (!valid) continue;
-        const int32_t s = list[i];
+        const int32_t s = (int32_t)src_at(src, i);
         const int key = sort_key(c, P.E[s], P.mat[s]);
         const unsigned grp = __match_any_sync(vm, key);
         const int leader = __ffs(grp) - 1;
@@ -815,7 +1005,7 @@ __global__ void k_sort_scatter(LoopConfig c, Particles P, RunCtl* ctl, int which
 int launch_run_init(const LoopConfig& c, const Particles& P, RunCtl* ctl, long long total,
                     int n_prob, long long max_iters, cudaStream_t st)
 {
-    k_run_init<<<c.grid, 256, 0, st>>>(P, ctl, total, n_prob, max_iters, c.mode == MCX_QUEUED);
+    k_run_init<<<c.grid, 256, 0, st>>>(P, ctl, total, n_prob, max_iters, c.mode);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -836,9 +1026,23 @@ int launch_iteration(const LoopConfig& c, const Tables& t, const Particles& P,
                      cudaStream_t st)
 {
     int k = 0;
-    const bool sorting = c.mode == MCX_QUEUED && c.sort_period > 0 && c.n_sort_bins > 0;
+    const bool sorting = c.mode != MCX_QUEUELESS && c.sort_period > 0 && c.n_sort_bins > 0;
     k_refill<<<c.grid, c.block, 0, st>>>(c, P, probs, work_off, ctl);
     ++k;
+    if (c.mode == MCX_QUEUED_FULLEST) {
+        // one step: the event kernels not selected return at once
+        k_fq_select<<<1, 1, 0, st>>>(ctl, (long long)P.cap);
+        ++k;
+        if (sorting) k += launch_sort(c, P, ctl, 2, st);
+        if (t.precision == MCX_FP32) k_lookup<float><<<c.grid, c.block, 0, st>>>(c, t, P, ctl);
+        else k_lookup<double><<<c.grid, c.block, 0, st>>>(c, t, P, ctl);
+        k_advance<<<c.grid, c.block, 0, st>>>(c, P, probs, ctl);
+        if (t.precision == MCX_FP32) k_collide<float><<<c.grid, c.block, 0, st>>>(c, t, P, probs, ctl);
+        else k_collide<double><<<c.grid, c.block, 0, st>>>(c, t, P, probs, ctl);
+        k += 3;
+        if (cudaGetLastError() != cudaSuccess) return -1;
+        return k;
+    }
     if (sorting) k += launch_sort(c, P, ctl, 0, st);
     if (t.precision == MCX_FP32) k_lookup<float><<<c.grid, c.block, 0, st>>>(c, t, P, ctl);
     else k_lookup<double><<<c.grid, c.block, 0, st>>>(c, t, P, ctl);

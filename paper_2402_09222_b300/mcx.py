@@ -22,7 +22,7 @@ ERR_NAMES = {-1: "MCX_ERR_ARG", -2: "MCX_ERR_CUDA", -3: "MCX_ERR_OOM", -4: "MCX_
              -5: "MCX_ERR_STATE", -6: "MCX_ERR_BOUNDS", -7: "MCX_ERR_TIMEOUT"}
 ERR_ITER_LIMIT, ERR_TIMEOUT = -4, -7
 FP64, FP32 = 0, 1
-QUEUELESS, QUEUED = 0, 1
+QUEUELESS, QUEUED, QUEUED_FULLEST = 0, 1, 2
 LOOKUP_EXACT, LOOKUP_FAST, LOOKUP_SORT = 0, 1, 2
 FLAG_DERIVATIVES, FLAG_HISTORY_DEBUG = 1, 2
 TALLY_FLUX, TALLY_ABSORB, TALLY_OUTCOME, TALLY_DFLUX, TALLY_DABSORB, TALLY_DOUTCOME = range(6)
@@ -277,9 +277,10 @@ class Problem:
         return out
 
     def stats(self) -> dict:
-        out = np.zeros(3, np.int64)
-        _check(_lib.mcx_last_run_stats(self.h, _np_ptr(out), 3))
-        return dict(iterations=int(out[0]), graph_launches=int(out[1]), kernels=int(out[2]))
+        out = np.zeros(6, np.int64)
+        _check(_lib.mcx_last_run_stats(self.h, _np_ptr(out), 6))
+        return dict(iterations=int(out[0]), graph_launches=int(out[1]), kernels=int(out[2]),
+                    selected=dict(lookup=int(out[3]), flight=int(out[4]), collision=int(out[5])))
 
     # -- lookups (device tensors)
     def xs_lookup(self, E, mat, out=None, flags: int = LOOKUP_EXACT, stream=None):

@@ -2,12 +2,14 @@
 in the paper, Sec. 2-5, on this one GPU).
 
 Search space (Table 1 of the paper, mapped to this implementation):
-  mode              queued | queueless                     (P0)
+  mode              queued | queueless                     (P0; with
+                    device_scheduling=True also the fullest-queue mode,
+                    the paper's queued policy decided on the device)
   particles_in_flight  1e5 .. 8e6, log scale, step 1000     (P1)
   hash_bins         100 .. 100000, log scale, step 100      (P2)
-  sort_threshold    0 .. 1e6, step 1000; active only in queued mode (P3,
+  sort_threshold    0 .. 1e6, step 1000; active only in queued modes (P3,
                     the paper's EqualsCondition(P3, P0, queued))
-  sort_period       0, 1, 2, 4, 8, 16; queued mode only    (this GPU's binning)
+  sort_period       0, 1, 2, 4, 8, 16; queued modes only   (this GPU's binning)
   block_size        64, 128, 256, 512                      (replaces the paper's
                     host-thread and MPI-rank parameters P4-P6, which have no
                     counterpart on one GPU)
@@ -34,7 +36,7 @@ import time
 from dataclasses import dataclass, field
 from typing import Callable
 
-QUEUELESS, QUEUED = 0, 1
+QUEUELESS, QUEUED, QUEUED_FULLEST = 0, 1, 2
 
 
 @dataclass
@@ -46,7 +48,13 @@ class Param:
     q: int = 1
     choices: tuple = ()
     default: object = None
-    active_if: tuple | None = None   # (other_param, value)
+    active_if: tuple | None = None   # (other_param, value or tuple of values)
+
+    def active(self, cfg: dict) -> bool:
+        if self.active_if is None:
+            return True
+        name, want = self.active_if
+        return cfg.get(name) in want if isinstance(want, tuple) else cfg.get(name) == want
 
     def sample(self, rng: random.Random):
         if self.kind == "choice":
@@ -148,13 +156,15 @@ class RandomForest:
         return [[self._predict_one(t, x) for x in X] for t in self.trees]
 
 
-def transport_space(max_in_flight: int = 8_000_000) -> list[Param]:
+def transport_space(max_in_flight: int = 8_000_000, device_scheduling: bool = False) -> list[Param]:
+    modes = (QUEUED, QUEUELESS, QUEUED_FULLEST) if device_scheduling else (QUEUED, QUEUELESS)
+    queued = (QUEUED, QUEUED_FULLEST)
     return [
-        Param("mode", "choice", choices=(QUEUED, QUEUELESS), default=QUEUED),
+        Param("mode", "choice", choices=modes, default=QUEUED),
         Param("particles_in_flight", "int_log", 100_000, max_in_flight, 1000, default=1_000_000),
         Param("hash_bins", "int_log", 100, 100_000, 100, default=4000),
-        Param("sort_threshold", "int", 0, 1_000_000, 1000, default=20_000, active_if=("mode", QUEUED)),
-        Param("sort_period", "choice", choices=(0, 1, 2, 4, 8, 16), default=4, active_if=("mode", QUEUED)),
+        Param("sort_threshold", "int", 0, 1_000_000, 1000, default=20_000, active_if=("mode", queued)),
+        Param("sort_period", "choice", choices=(0, 1, 2, 4, 8, 16), default=4, active_if=("mode", queued)),
         Param("block_size", "choice", choices=(64, 128, 256, 512), default=256),
     ]
 
@@ -170,7 +180,7 @@ def canonical(space: list[Param], cfg: dict) -> dict:
     """Inactive conditional parameters are dropped (the paper's 'nan')."""
     out = {}
     for p in space:
-        if p.active_if is not None and cfg.get(p.active_if[0]) != p.active_if[1]:
+        if not p.active(cfg):
             continue
         out[p.name] = cfg[p.name]
     return out
@@ -297,7 +307,7 @@ class Tuner:
             cur = self.best()
             full = {p.name: cur.config.get(p.name, p.default) for p in self.space}
             for p in self.space:
-                if p.active_if is not None and full.get(p.active_if[0]) != p.active_if[1]:
+                if not p.active(full):
                     continue
                 for v in p.neighbours(full[p.name]):
                     if n_eval() >= max_evals:
@@ -464,11 +474,13 @@ def main(argv=None):
     ap.add_argument("--seed", type=int, default=1234)
     ap.add_argument("--metric", choices=["time", "energy", "edp"], default="time",
                     help="transport objective (the time limit is always 1.5x baseline seconds)")
+    ap.add_argument("--device-scheduling", action="store_true",
+                    help="add the fullest-queue mode (queue chosen on the device) to the mode choices")
     args = ap.parse_args(argv)
     from . import synth
     if args.workload == "transport":
         prob = synth.config3_problem(n_histories=args.histories)
-        space = transport_space()
+        space = transport_space(device_scheduling=args.device_scheduling)
         obj = transport_objective(prob, seed=5, precision=1, metric=args.metric)
     else:
         lib = synth.species_library(355, 11_303, 1236)

@@ -60,6 +60,11 @@ TUNINGS = [
     dict(mode=1, pif=3000, sort_period=2, sort_threshold=0, block_size=512, H=4000, use_graph=1),
     dict(mode=1, pif=200_000, sort_period=1, sort_threshold=10, block_size=64, H=100_000, use_graph=1,
          iters_per_sync=3),
+    # fullest-queue mode: a small buffer makes every ring wrap many times
+    dict(mode=2, pif=10_000, sort_period=0, block_size=256, H=4000, use_graph=1),
+    dict(mode=2, pif=333, sort_period=1, sort_threshold=0, block_size=128, H=100, use_graph=1,
+         iters_per_sync=5),
+    dict(mode=2, pif=5000, sort_period=2, sort_threshold=100, block_size=64, H=0, use_graph=0),
 ]
 
 
@@ -90,7 +95,7 @@ def lattice():
     return prob, oracle.transport(prob, seed=11, history_debug=True, n_threads=8)
 
 
-@pytest.mark.parametrize("mode,sort_period", [(0, 0), (1, 0), (1, 1)])
+@pytest.mark.parametrize("mode,sort_period", [(0, 0), (1, 0), (1, 1), (2, 0), (2, 1)])
 def test_lattice_history_matched(mcx, lattice, mode, sort_period):
     prob, ref = lattice
     g = run_gpu(mcx, prob, pif=1234, seed=11, mode=mode, sort_period=sort_period, sort_threshold=0)
@@ -102,10 +107,11 @@ def test_lattice_history_matched(mcx, lattice, mode, sort_period):
     assert out[:4].sum() == prob.n_histories
 
 
-def test_lattice_derivative_tallies(mcx):
+@pytest.mark.parametrize("mode", [1, 2])
+def test_lattice_derivative_tallies(mcx, mode):
     prob = synth.config3_problem(n_histories=3000, lattice_n=9)
     ref = oracle.transport(prob, seed=13, derivatives=True, history_debug=True, n_threads=8)
-    g = run_gpu(mcx, prob, pif=1000, seed=13, flags=mcx.FLAG_DERIVATIVES | mcx.FLAG_HISTORY_DEBUG, mode=1)
+    g = run_gpu(mcx, prob, pif=1000, seed=13, flags=mcx.FLAG_DERIVATIVES | mcx.FLAG_HISTORY_DEBUG, mode=mode)
     assert np.array_equal(g["ncoll"], ref["ncoll"])
     assert_tallies_close(g, ref, keys=("flux", "absorb", "outcome", "dflux", "dabsorb", "doutcome"))
 
@@ -151,26 +157,43 @@ def test_reused_handle_honours_a_smaller_in_flight_count(mcx, config1):
     assert abs(fresh.stats()["iterations"] - it_small) <= 0.05 * it_small
 
 
-def test_iteration_cap_returns_an_error_and_the_handle_stays_usable(mcx, config1):
+@pytest.mark.parametrize("mode", [0, 2])
+def test_iteration_cap_returns_an_error_and_the_handle_stays_usable(mcx, config1, mode):
     prob, ref = config1
     p = mcx.make_problem(prob)
-    p.set_tuning(max_event_iters=5, iters_per_sync=2)
+    p.set_tuning(mode=mode, max_event_iters=5, iters_per_sync=2)
     with pytest.raises(mcx.McxError, match="ITER_LIMIT"):
         p.run(particles_in_flight=1000, seed=7)
     p.zero_tallies()
-    p.set_tuning()
+    p.set_tuning(mode=mode)
     p.run(particles_in_flight=1000, seed=7)
     assert_tallies_close(p.tallies(), ref)
 
 
-def test_batched_uneven_problems(mcx):
+def test_fullest_queue_steps(mcx, config1):
+    """Fullest-queue mode: every step runs exactly one event kernel, all three
+    are chosen, and the step count is close to three event sweeps per
+    iteration of the plain queued loop on the same buffer."""
+    prob, ref = config1
+    q = run_gpu(mcx, prob, pif=2000, mode=1)
+    f = run_gpu(mcx, prob, pif=2000, mode=2)
+    assert np.array_equal(f["ncoll"], ref["ncoll"])
+    sel = f["stats"]["selected"]
+    assert sum(sel.values()) == f["stats"]["iterations"]
+    assert min(sel.values()) > 0
+    assert q["stats"]["selected"] == dict(lookup=0, flight=0, collision=0)
+    assert f["stats"]["iterations"] <= 6 * q["stats"]["iterations"]
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_batched_uneven_problems(mcx, mode):
     lib = synth.species_library(60, 1500, 301).channels([synth.CH_SCATTER, synth.CH_ABSORB])
     mats = synth.lookup_materials(60, 302, n_materials=6)
     probs = synth.config5_problems(lib, mats, n_problems=7, seed=303, hist_lo=100, hist_hi=3000)
     refs = [oracle.transport(pr, seed=21, history_debug=True, n_threads=8) for pr in probs]
     base = mcx.Problem(probs[0], flags=mcx.FLAG_HISTORY_DEBUG).load_tables(lib, mats, hash_bins=1000)
     handles = [base] + [mcx.Problem(pr, flags=mcx.FLAG_HISTORY_DEBUG).share_tables(base) for pr in probs[1:]]
-    base.set_tuning(mode=1, sort_period=2, sort_threshold=0)
+    base.set_tuning(mode=mode, sort_period=2, sort_threshold=0)
     mcx.batch_run(handles, [pr.n_histories for pr in probs], particles_in_flight=2500, seed=21)
     for h, pr, ref in zip(handles, probs, refs):
         nc = h.history_debug(pr.n_histories)
@@ -179,11 +202,12 @@ def test_batched_uneven_problems(mcx):
             assert_tallies_close(h.tallies(), ref)
 
 
-def test_config3_full_size_sampled(mcx):
+@pytest.mark.parametrize("mode", [1, 2])
+def test_config3_full_size_sampled(mcx, mode):
     """1e7 histories of the 17x17 lattice in the benchmark's launch; sampled
     histories re-run one by one in the oracle; balance checked on the whole."""
     prob = synth.config3_problem(n_histories=10_000_000)
-    g = run_gpu(mcx, prob, precision=mcx.FP32, pif=2_000_000, seed=31, mode=1, sort_period=4,
+    g = run_gpu(mcx, prob, precision=mcx.FP32, pif=2_000_000, seed=31, mode=mode, sort_period=4,
                 sort_threshold=20_000)
     rp = synth.config3_problem(n_histories=10_000_000, lib=prob.lib.fp32_rounded())
     rng = np.random.default_rng(6)

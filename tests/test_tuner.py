@@ -188,3 +188,17 @@ def test_random_forest_surrogate_fits_and_spreads():
     # far from the data the trees disagree more than at a dense point
     spread = lambda i: max(p[i] for p in pred) - min(p[i] for p in pred)
     assert spread(0) >= 0.0 and len(pred) == 50
+
+
+def test_device_scheduling_space_keeps_sort_parameters_for_both_queued_modes():
+    space = tuner.transport_space(device_scheduling=True)
+    mode = next(p for p in space if p.name == "mode")
+    assert set(mode.choices) == {tuner.QUEUED, tuner.QUEUELESS, tuner.QUEUED_FULLEST}
+    d = {p.name: p.default for p in space}
+    for m in (tuner.QUEUED, tuner.QUEUED_FULLEST):
+        c = tuner.canonical(space, dict(d, mode=m))
+        assert "sort_threshold" in c and "sort_period" in c
+    c = tuner.canonical(space, dict(d, mode=tuner.QUEUELESS))
+    assert "sort_threshold" not in c
+    # the paper's two-mode space is unchanged by default
+    assert tuner.QUEUED_FULLEST not in next(p for p in tuner.transport_space() if p.name == "mode").choices
