@@ -69,7 +69,7 @@ class _Problem(C.Structure):
         ("awr", _dp),
         ("n_materials", C.c_int32), ("mat_offsets", _i32p), ("mat_species", _i32p),
         ("mat_dens", _dp),
-        ("derivatives", C.c_int32),
+        ("derivatives", C.c_int32), ("ch_nu_fission", C.c_int32),
     ]
 
 
@@ -92,6 +92,10 @@ def _declare(L):
     L.orc_transport.argtypes = [C.POINTER(_Problem), C.POINTER(_Tallies), C.c_int64, C.c_int64,
                                 C.c_uint64, C.c_int]
     L.orc_transport.restype = C.c_int64
+    L.orc_eigenvalue.argtypes = [C.POINTER(_Problem), C.POINTER(_Tallies), C.c_uint64, C.c_int64,
+                                 C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_int, _dp, _dp,
+                                 C.c_int64, _i64p, _dp, _u32p]
+    L.orc_eigenvalue.restype = C.c_int
     L.orc_max_threads.restype = C.c_int
 
 
@@ -179,28 +183,8 @@ def transport(prob, seed: int, first: int = 0, count: int | None = None, n_threa
     when requested, and 'capped' (histories that hit the event cap)."""
     L = lib()
     count = prob.n_histories - first if count is None else count
-    lib_, mats = prob.lib, prob.mats
-    if lib_.n_ch == 2:
-        chs, cha = 0, 1
-    elif lib_.n_ch == 5:
-        chs, cha = 1, 2
-    else:
-        raise ValueError("transport needs a 2- or 5-channel library")
-    keep = dict(
-        rm=_c(prob.region_material, np.int32), edges=_c(prob.ebin_edges, np.float64),
-        go=_c(lib_.grid_offsets, np.int64), en=_c(lib_.energies, np.float64),
-        sg=_c(lib_.sigma, np.float64), awr=_c(lib_.awr, np.float64),
-        mo=_c(mats.offsets, np.int32), ms=_c(mats.species, np.int32), md=_c(mats.dens, np.float64))
-    if len(keep["edges"]) == 0:
-        keep["edges"] = np.zeros(2)
-    P = _Problem(prob.geometry, prob.lattice_n, prob.pitch, prob.radius, prob.height,
-                 prob.slab_length, len(keep["rm"]), _ptr(keep["rm"], _i32p), prob.E0, prob.E_cut,
-                 max(len(prob.ebin_edges) - 1, 0), _ptr(keep["edges"], _dp), prob.n_batches,
-                 prob.problem_id, prob.n_histories, lib_.n_species, _ptr(keep["go"], _i64p),
-                 _ptr(keep["en"], _dp), _ptr(keep["sg"], _dp), lib_.n_ch, chs, cha,
-                 _ptr(keep["awr"], _dp), mats.n_materials, _ptr(keep["mo"], _i32p),
-                 _ptr(keep["ms"], _i32p), _ptr(keep["md"], _dp), int(derivatives))
-    B, nb, M = prob.n_batches, prob.n_tally_bins, mats.n_materials
+    P, keep = _problem(prob, derivatives)
+    B, nb, M = prob.n_batches, prob.n_tally_bins, prob.mats.n_materials
     res = dict(flux=np.zeros((B, nb)), absorb=np.zeros((B, nb)), outcome=np.zeros((B, N_OUT)))
     null = _dp()
     T = _Tallies(_ptr(res["flux"], _dp), _ptr(res["absorb"], _dp), _ptr(res["outcome"], _dp),
@@ -217,6 +201,88 @@ def transport(prob, seed: int, first: int = 0, count: int | None = None, n_threa
     if capped < 0:
         raise ValueError("oracle transport rejected its arguments")
     res["capped"] = int(capped)
+    return res
+
+
+def _channels(lib_):
+    """(scatter, absorb, nu-fission) channel indices of a 2-, 3- or 5-channel
+    library (2: scatter, absorb; 3: + nu-fission; 5: total, scatter, absorb,
+    fission, nu-fission); nu-fission -1 when absent."""
+    if lib_.n_ch == 2:
+        return 0, 1, -1
+    if lib_.n_ch == 3:
+        return 0, 1, 2
+    if lib_.n_ch == 5:
+        return 1, 2, 4
+    raise ValueError("transport needs a 2-, 3- or 5-channel library")
+
+
+def _problem(prob, derivatives=False):
+    lib_, mats = prob.lib, prob.mats
+    chs, cha, chnf = _channels(lib_)
+    keep = dict(
+        rm=_c(prob.region_material, np.int32), edges=_c(prob.ebin_edges, np.float64),
+        go=_c(lib_.grid_offsets, np.int64), en=_c(lib_.energies, np.float64),
+        sg=_c(lib_.sigma, np.float64), awr=_c(lib_.awr, np.float64),
+        mo=_c(mats.offsets, np.int32), ms=_c(mats.species, np.int32), md=_c(mats.dens, np.float64))
+    if len(keep["edges"]) == 0:
+        keep["edges"] = np.zeros(2)
+    P = _Problem(prob.geometry, prob.lattice_n, prob.pitch, prob.radius, prob.height,
+                 prob.slab_length, len(keep["rm"]), _ptr(keep["rm"], _i32p), prob.E0, prob.E_cut,
+                 max(len(prob.ebin_edges) - 1, 0), _ptr(keep["edges"], _dp), prob.n_batches,
+                 prob.problem_id, prob.n_histories, lib_.n_species, _ptr(keep["go"], _i64p),
+                 _ptr(keep["en"], _dp), _ptr(keep["sg"], _dp), lib_.n_ch, chs, cha,
+                 _ptr(keep["awr"], _dp), mats.n_materials, _ptr(keep["mo"], _i32p),
+                 _ptr(keep["ms"], _i32p), _ptr(keep["md"], _dp), int(derivatives), chnf)
+    return P, keep
+
+
+EIGEN_ERRORS = {-1: "bad arguments", -2: "a generation banked no fission site",
+                -3: "out of memory", -4: "a history hit the event cap"}
+
+
+def eigenvalue(prob, seed: int, n_per_gen: int, n_generations: int, n_inactive: int,
+               k0: float = 1.0, n_threads: int = 1, bank: bool = False,
+               history_debug: bool = False) -> dict:
+    """k-eigenvalue power iteration of a synthetic Problem (fission spectrum
+    temperature prob.T_fission).  Returns per generation k (site count),
+    k_col, k_tl and sites; the active generations' tallies (flux, absorb
+    [B][bins], outcome [B][5]); with bank=True the last generation's sites as
+    rows (x, y, z, ci, cj, inpin) in bank order and the sites it started from
+    ('source', N rows, when there are two or more generations); with
+    history_debug the last generation's per-history collision counts."""
+    L = lib()
+    P, keep = _problem(prob)
+    if P.ch_nu_fission < 0:
+        raise ValueError("an eigenvalue run needs a nu-fission channel")
+    B, nb = prob.n_batches, prob.n_tally_bins
+    res = dict(flux=np.zeros((B, nb)), absorb=np.zeros((B, nb)), outcome=np.zeros((B, N_OUT)))
+    null = _dp()
+    T = _Tallies(_ptr(res["flux"], _dp), _ptr(res["absorb"], _dp), _ptr(res["outcome"], _dp),
+                 null, null, null, _u32p())
+    gen = np.zeros((n_generations, 4))
+    cap = 8 * n_per_gen if bank else 0
+    rows = np.zeros((max(cap, 1), 6))
+    src = np.zeros((n_per_gen, 6)) if bank else None
+    bank_n = C.c_int64(0)
+    ncoll = np.zeros(n_per_gen, np.uint32) if history_debug else None
+    rc = L.orc_eigenvalue(C.byref(P), C.byref(T), seed, n_per_gen, n_generations, n_inactive,
+                          float(k0), float(prob.T_fission), n_threads, _ptr(gen, _dp),
+                          _ptr(rows, _dp) if bank else _dp(), cap, C.byref(bank_n),
+                          _ptr(src, _dp) if bank else _dp(),
+                          _ptr(ncoll, _u32p) if history_debug else _u32p())
+    if rc != 0:
+        raise RuntimeError(f"oracle eigenvalue run failed: {EIGEN_ERRORS.get(rc, rc)}")
+    res.update(k=gen[:, 0].copy(), k_col=gen[:, 1].copy(), k_tl=gen[:, 2].copy(),
+               sites=gen[:, 3].astype(np.int64))
+    if bank:
+        if bank_n.value > cap:
+            raise RuntimeError("bank larger than the buffer")
+        res["bank"] = rows[:bank_n.value].copy()
+        if n_generations > 1:
+            res["source"] = src
+    if history_debug:
+        res["ncoll"] = ncoll
     return res
 
 
@@ -248,24 +314,7 @@ class _Bound:
     """A Problem packed for the C side, with its arrays kept alive."""
 
     def __init__(self, prob, derivatives=False):
-        lib_, mats = prob.lib, prob.mats
-        chs, cha = (0, 1) if lib_.n_ch == 2 else (1, 2)
-        self.keep = dict(
-            rm=_c(prob.region_material, np.int32),
-            edges=_c(prob.ebin_edges if len(prob.ebin_edges) else np.zeros(2), np.float64),
-            go=_c(lib_.grid_offsets, np.int64), en=_c(lib_.energies, np.float64),
-            sg=_c(lib_.sigma, np.float64), awr=_c(lib_.awr, np.float64),
-            mo=_c(mats.offsets, np.int32), ms=_c(mats.species, np.int32),
-            md=_c(mats.dens, np.float64))
-        k = self.keep
-        self.P = _Problem(prob.geometry, prob.lattice_n, prob.pitch, prob.radius, prob.height,
-                          prob.slab_length, len(k["rm"]), _ptr(k["rm"], _i32p), prob.E0,
-                          prob.E_cut, max(len(prob.ebin_edges) - 1, 0), _ptr(k["edges"], _dp),
-                          prob.n_batches, prob.problem_id, prob.n_histories, lib_.n_species,
-                          _ptr(k["go"], _i64p), _ptr(k["en"], _dp), _ptr(k["sg"], _dp),
-                          lib_.n_ch, chs, cha, _ptr(k["awr"], _dp), mats.n_materials,
-                          _ptr(k["mo"], _i32p), _ptr(k["ms"], _i32p), _ptr(k["md"], _dp),
-                          int(derivatives))
+        self.P, self.keep = _problem(prob, derivatives)
 
 
 def source_state(prob, seed: int, h: int) -> np.ndarray:
@@ -275,6 +324,18 @@ def source_state(prob, seed: int, h: int) -> np.ndarray:
     L = lib()
     L.orc_source_state.argtypes = [C.POINTER(_Problem), C.c_uint64, C.c_int64, _dp]
     L.orc_source_state(C.byref(b.P), seed, h, _ptr(out, _dp))
+    return out
+
+
+def site_source_state(prob, seed: int, h: int, site) -> np.ndarray:
+    """{x, y, z, u, v, w, E, region, draws used} of history h started from a
+    fission site {x, y, z, ci, cj, inpin}."""
+    b = _Bound(prob)
+    s = _c(site, np.float64)
+    out = np.zeros(9)
+    L = lib()
+    L.orc_site_source_state.argtypes = [C.POINTER(_Problem), C.c_uint64, C.c_int64, _dp, C.c_double, _dp]
+    L.orc_site_source_state(C.byref(b.P), seed, h, _ptr(s, _dp), float(prob.T_fission), _ptr(out, _dp))
     return out
 
 
@@ -288,3 +349,12 @@ def surface_distance(prob, state):
     L.orc_surface_distance.restype = C.c_int
     s = L.orc_surface_distance(C.byref(b.P), _ptr(st, _dp), C.byref(d))
     return int(s), float(d.value)
+
+
+def fission_energies(seed: int, problem_id: int, hist: int, T: float, n: int) -> np.ndarray:
+    """n successive fission-spectrum energies drawn from one history's stream."""
+    out = np.zeros(n)
+    L = lib()
+    L.orc_fission_energies.argtypes = [C.c_uint64, C.c_uint32, C.c_uint64, C.c_double, C.c_int64, _dp]
+    L.orc_fission_energies(seed, problem_id, hist, T, n, _ptr(out, _dp))
+    return out

@@ -22,7 +22,10 @@
  *     crossing, collision, track-length tallies), history by history.  The
  *     particles-in-flight count, queueing mode and sorting threshold of the
  *     paper do not change any history, so the oracle has none of them;
- *   - likelihood-ratio derivative tallies w.r.t. material density scales.
+ *   - likelihood-ratio derivative tallies w.r.t. material density scales;
+ *   - the k-eigenvalue power iteration of the paper's reactor benchmark
+ *     (Sec. 5.1: Hoogenboom-Martin, a criticality problem): generations of
+ *     histories started from the previous generation's fission sites.
  * The paper gives no physics; the readings taken where it is silent are
  * stated beside each function.
  *
@@ -278,6 +281,7 @@ typedef struct {
     const int32_t* mat_species;
     const double* mat_dens;
     int32_t derivatives;
+    int32_t ch_nu_fission; /* channel of nu-fission, or -1 (eigenvalue runs only) */
 } orc_problem;
 
 typedef struct {
@@ -297,10 +301,12 @@ static int32_t orc_n_bins(const orc_problem* p)
 }
 
 /* Transport macroscopic lookup at energy E in material m: the sequential sums
- * Sigma_t = sum_i N_i (sigma_s,i + sigma_a,i) and Sigma_a = sum_i N_i sigma_a,i. */
-static void orc_macro(const orc_problem* p, int32_t m, double E, double* sig_t, double* sig_a)
+ * Sigma_t = sum_i N_i (sigma_s,i + sigma_a,i) and Sigma_a = sum_i N_i sigma_a,i,
+ * and, when sig_nf is given, nu Sigma_f = sum_i N_i nu sigma_f,i. */
+static void orc_macro(const orc_problem* p, int32_t m, double E, double* sig_t, double* sig_a,
+                      double* sig_nf)
 {
-    double st = 0.0, sa = 0.0;
+    double st = 0.0, sa = 0.0, nf = 0.0;
     for (int32_t i = p->mat_offsets[m]; i < p->mat_offsets[m + 1]; ++i) {
         int32_t s = p->mat_species[i];
         const double* g = p->energies + p->grid_offsets[s];
@@ -314,9 +320,14 @@ static void orc_macro(const orc_problem* p, int32_t m, double E, double* sig_t, 
         double sa_i = a0 + f * (a1 - a0);
         st = st + p->mat_dens[i] * (ss + sa_i);
         sa = sa + p->mat_dens[i] * sa_i;
+        if (sig_nf) {
+            double n0 = tab[k * p->n_ch + p->ch_nu_fission], n1 = tab[(k + 1) * p->n_ch + p->ch_nu_fission];
+            nf = nf + p->mat_dens[i] * (n0 + f * (n1 - n0));
+        }
     }
     *sig_t = st;
     *sig_a = sa;
+    if (sig_nf) *sig_nf = nf;
 }
 
 /* Azimuth (cos phi, sin phi) by rejection from pairs (a, b) = (2u-1, 2u-1)
@@ -342,10 +353,28 @@ typedef struct {
     int32_t ci, cj, inpin, region, material;
     int alive;
     int need_xs;
-    double sig_t, sig_a;
+    double sig_t, sig_a, sig_nf;
     double W[ORC_MAX_DMAT];
     uint32_t ncoll;
 } orc_particle;
+
+/* A fission site: where a collision produced fission neutrons, with the
+ * lattice cell and the inside-pin flag there (the region follows). */
+typedef struct {
+    double x, y, z;
+    int32_t ci, cj, inpin;
+} orc_site;
+
+/* Eigenvalue context of one history. */
+typedef struct {
+    double k_norm;        /* a collision banks floor(nuSigma_f / Sigma_t / k_norm + xi) sites */
+    double T;             /* temperature of the fission spectrum (eV) */
+    const orc_site* src;  /* this history's source site, or NULL (the fixed source) */
+    orc_site* sites;      /* sites this history banked (grown with realloc) */
+    int64_t n_sites, cap_sites;
+    double k_col, k_tl;   /* this history's collision and track-length k scores */
+    int failed;           /* out of memory */
+} orc_eigen;
 
 static void orc_set_region(const orc_problem* p, orc_particle* q)
 {
@@ -392,6 +421,44 @@ static void orc_source(const orc_problem* p, orc_rng* r, orc_particle* q)
     q->u = st * c;
     q->v = st * s;
     q->w = mu;
+    orc_set_region(p, q);
+}
+
+/* Fission-spectrum energy: the Maxwellian chi(E) ~ sqrt(E) exp(-E/T), a
+ * Gamma(3/2, T) variate, sampled as the sum of a Gamma(1) and a Gamma(1/2)
+ * variate: E = -T (ln xi1 + ln xi2 cos^2 phi) with phi uniform (the
+ * Box-Muller square of a normal; Everett and Cashwell's Monte Carlo sampler,
+ * rule C64).  cos phi comes from the same disc rejection as the azimuth. */
+static double orc_fission_energy(orc_rng* r, double T)
+{
+    double xi1 = orc_draw(r), xi2 = orc_draw(r);
+    double c, s;
+    orc_azimuth(r, &c, &s);
+    return -T * (log(xi1) + (c * c) * log(xi2));
+}
+
+/* A history started from a fission site: the site's position and cell,
+ * isotropic direction (mu, then azimuth), energy from the fission spectrum. */
+static void orc_site_source(const orc_problem* p, orc_rng* r, const orc_site* st, double T,
+                            orc_particle* q)
+{
+    memset(q, 0, sizeof(*q));
+    q->alive = 1;
+    q->need_xs = 1;
+    q->x = st->x;
+    q->y = st->y;
+    q->z = st->z;
+    q->ci = st->ci;
+    q->cj = st->cj;
+    q->inpin = st->inpin;
+    double mu = 2.0 * orc_draw(r) - 1.0;
+    double c, s;
+    orc_azimuth(r, &c, &s);
+    double sn = sqrt(1.0 - mu * mu);
+    q->u = sn * c;
+    q->v = sn * s;
+    q->w = mu;
+    q->E = orc_fission_energy(r, T);
     orc_set_region(p, q);
 }
 
@@ -529,10 +596,40 @@ static void orc_rotate(orc_particle* q, double mu, double c, double s)
  * sequential cumulative sum of N_i (sigma_s,i + sigma_a,i) (the last species
  * if none qualifies); absorption if xi2 * sigma_t,j < sigma_a,j; otherwise
  * elastic scattering, isotropic in the centre-of-mass frame.  Returns the
- * outcome index if the particle dies, else -1. */
-static int orc_collide(const orc_problem* p, orc_rng* r, orc_particle* q)
+ * outcome index if the particle dies, else -1.
+ * Eigenvalue runs draw a fourth uniform xi4 and, before the reaction is
+ * decided, bank floor(nuSigma_f / Sigma_t / k_norm + xi4) fission sites at
+ * the collision point (the expected number of fission neutrons of the
+ * collision, renormalised by the previous generation's k, rounded
+ * stochastically); the collision scores nuSigma_f / Sigma_t to k. */
+static int orc_collide(const orc_problem* p, orc_rng* r, orc_particle* q, orc_eigen* eig)
 {
     double xi1 = orc_draw(r), xi2 = orc_draw(r), xi3 = orc_draw(r);
+    if (eig) {
+        double xi4 = orc_draw(r);
+        double yield = q->sig_nf / q->sig_t;
+        eig->k_col += yield;
+        int64_t n_new = (int64_t)floor(yield / eig->k_norm + xi4);
+        for (int64_t k = 0; k < n_new; ++k) {
+            if (eig->n_sites == eig->cap_sites) {
+                int64_t nc = eig->cap_sites ? 2 * eig->cap_sites : 8;
+                orc_site* ns = (orc_site*)realloc(eig->sites, (size_t)nc * sizeof(orc_site));
+                if (!ns) {
+                    eig->failed = 1;
+                    break;
+                }
+                eig->sites = ns;
+                eig->cap_sites = nc;
+            }
+            orc_site* st = &eig->sites[eig->n_sites++];
+            st->x = q->x;
+            st->y = q->y;
+            st->z = q->z;
+            st->ci = q->ci;
+            st->cj = q->cj;
+            st->inpin = q->inpin;
+        }
+    }
     int32_t m = q->material;
     double target = xi1 * q->sig_t;
     double cum = 0.0, ss_j = 0.0, sa_j = 0.0;
@@ -571,22 +668,24 @@ static int orc_collide(const orc_problem* p, orc_rng* r, orc_particle* q)
     return -1;
 }
 
-/* One history, start to end.  Returns 0, or -1 if the per-history event cap
- * was reached (the history is then abandoned without a terminal score). */
-static int orc_history(const orc_problem* p, orc_tallies* t, uint64_t seed, int64_t h,
-                       uint32_t* ncoll_out)
+/* One history, start to end, scoring into batch b.  Returns 0, or -1 if the
+ * per-history event cap was reached (the history is then abandoned without a
+ * terminal score).  eig != NULL: an eigenvalue-run history (see orc_collide). */
+static int orc_history(const orc_problem* p, orc_tallies* t, uint64_t seed, int64_t h, int64_t b,
+                       uint32_t* ncoll_out, orc_eigen* eig)
 {
     int32_t nb = orc_n_bins(p), M = p->n_materials;
-    int64_t B = p->n_batches;
-    int64_t b = (h * B) / p->n_histories_total;
     orc_rng r;
     orc_rng_init(&r, seed, p->problem_id, (uint64_t)h);
     orc_particle q;
-    orc_source(p, &r, &q);
+    if (eig && eig->src)
+        orc_site_source(p, &r, eig->src, eig->T, &q);
+    else
+        orc_source(p, &r, &q);
     int outcome = -1;
     for (int64_t ev = 0; ev < ORC_MAX_EVENTS_PER_HISTORY; ++ev) {
         if (q.need_xs) {
-            orc_macro(p, q.material, q.E, &q.sig_t, &q.sig_a);
+            orc_macro(p, q.material, q.E, &q.sig_t, &q.sig_a, eig ? &q.sig_nf : NULL);
             q.need_xs = 0;
         }
         double xi = orc_draw(&r);
@@ -606,6 +705,7 @@ static int orc_history(const orc_problem* p, orc_tallies* t, uint64_t seed, int6
                           ? (int32_t)orc_grid_index(p->ebin_edges, p->n_ebins + 1, q.E)
                           : q.region;
         double x_abs = d * q.sig_a;
+        if (eig) eig->k_tl += d * q.sig_nf;
         t->flux[b * nb + bin] += d;
         t->absorb[b * nb + bin] += x_abs;
         if (p->derivatives) {
@@ -629,7 +729,7 @@ static int orc_history(const orc_problem* p, orc_tallies* t, uint64_t seed, int6
             if (p->derivatives)
                 for (int32_t mm = 0; mm < M; ++mm)
                     t->doutcome[(b * ORC_N_OUT + ORC_OUT_COLLISIONS) * M + mm] += q.W[mm];
-            int o = orc_collide(p, &r, &q);
+            int o = orc_collide(p, &r, &q, eig);
             if (o >= 0) {
                 outcome = o;
                 break;
@@ -660,7 +760,9 @@ int64_t orc_transport(const orc_problem* p, orc_tallies* t, int64_t first, int64
     int64_t capped = 0;
     if (n_threads <= 1) {
         for (int64_t h = first; h < first + count; ++h)
-            if (orc_history(p, t, seed, h, t->ncoll ? &t->ncoll[h - first] : NULL)) capped++;
+            if (orc_history(p, t, seed, h, (h * B) / p->n_histories_total,
+                            t->ncoll ? &t->ncoll[h - first] : NULL, NULL))
+                capped++;
         return capped;
     }
 #ifdef _OPENMP
@@ -683,7 +785,9 @@ int64_t orc_transport(const orc_problem* p, orc_tallies* t, int64_t first, int64
         mine.ncoll = NULL;
 #pragma omp for schedule(dynamic, 64)
         for (int64_t h = first; h < first + count; ++h)
-            if (orc_history(p, &mine, seed, h, t->ncoll ? &t->ncoll[h - first] : NULL)) capped++;
+            if (orc_history(p, &mine, seed, h, (h * B) / p->n_histories_total,
+                            t->ncoll ? &t->ncoll[h - first] : NULL, NULL))
+                capped++;
     }
     for (int tid = 0; tid < nt; ++tid) {
         double* base = priv + (size_t)tid * per;
@@ -704,9 +808,186 @@ int64_t orc_transport(const orc_problem* p, orc_tallies* t, int64_t first, int64
     free(priv);
 #else
     for (int64_t h = first; h < first + count; ++h)
-        if (orc_history(p, t, seed, h, t->ncoll ? &t->ncoll[h - first] : NULL)) capped++;
+        if (orc_history(p, t, seed, h, (h * B) / p->n_histories_total,
+                        t->ncoll ? &t->ncoll[h - first] : NULL, NULL))
+            capped++;
 #endif
     return capped;
+}
+
+/* ------------------------------------------------------------------------ */
+/* k-eigenvalue power iteration                                               */
+/* ------------------------------------------------------------------------ */
+/* Generation g runs N histories with ids g N .. g N + N - 1 (their own Philox
+ * streams).  Generation 0 starts from the fixed source; generation g > 0
+ * starts history g N + i from site i of its source, which is the previous
+ * generation's bank resampled to N sites by the systematic selection
+ * source[i] = bank[floor(i M / N)] (M banked sites, bank in the order of the
+ * parent history and, within a history, of banking).  The site-count k of
+ * generation g is k_g = M_g k_norm,g / N with k_norm,0 = k0 and
+ * k_norm,g+1 = k_g; the collision and track-length estimators are the sums of
+ * nuSigma_f / Sigma_t over collisions and of d nuSigma_f over flights, over
+ * N.  Tallies score only in the last n_active generations: active history
+ * j = (g - n_inactive) N + i falls in batch floor(j B / (n_active N)).
+ * gen_out[g] = {k_g, k_col,g, k_tl,g, M_g}.  last_bank (optional) receives
+ * the last generation's bank, up to bank_cap sites, as rows
+ * {x, y, z, ci, cj, inpin}; *bank_n its size.  last_source (optional, N
+ * rows of the same form) receives the sites the last generation started from
+ * (none for a one-generation run).  ncoll (optional): collision counts of the
+ * last generation's histories.
+ * Returns 0; -1 bad arguments; -2 a generation banked no site; -3 out of
+ * memory; -4 a history hit the event cap. */
+int orc_eigenvalue(const orc_problem* p, orc_tallies* t, uint64_t seed, int64_t N,
+                   int32_t n_generations, int32_t n_inactive, double k0, double T, int n_threads,
+                   double* gen_out, double* last_bank, int64_t bank_cap, int64_t* bank_n,
+                   double* last_source, uint32_t* ncoll)
+{
+    if (N < 1 || n_generations < 1 || n_inactive < 0 || n_inactive >= n_generations || !(k0 > 0.0) ||
+        !(T > 0.0) || p->ch_nu_fission < 0 || p->ch_nu_fission >= p->n_ch || p->derivatives)
+        return -1;
+    int32_t nb = orc_n_bins(p);
+    int64_t B = p->n_batches, n_active = n_generations - n_inactive;
+    size_t n_tal = (size_t)(B * nb), n_out = (size_t)(B * ORC_N_OUT);
+    double* scratch = (double*)calloc(2 * n_tal + n_out, sizeof(double));
+    orc_eigen* hist = (orc_eigen*)calloc((size_t)N, sizeof(orc_eigen));
+    orc_site* src = NULL;
+    int rc = 0;
+    if (!scratch || !hist) rc = -3;
+    orc_tallies dump;
+    memset(&dump, 0, sizeof(dump));
+    dump.flux = scratch;
+    dump.absorb = scratch ? scratch + n_tal : NULL;
+    dump.outcome = scratch ? scratch + 2 * n_tal : NULL;
+    double k_norm = k0;
+#ifdef _OPENMP
+    if (n_threads > 1) omp_set_num_threads(n_threads);
+#endif
+    for (int32_t g = 0; g < n_generations && rc == 0; ++g) {
+        int active = g >= n_inactive;
+        for (int64_t i = 0; i < N; ++i) {
+            hist[i].k_norm = k_norm;
+            hist[i].T = T;
+            hist[i].src = src ? &src[i] : NULL;
+            hist[i].n_sites = 0;
+            hist[i].k_col = 0.0;
+            hist[i].k_tl = 0.0;
+        }
+        int capped = 0;
+        int last = g == n_generations - 1;
+        if (last && last_source && src)
+            for (int64_t i = 0; i < N; ++i) {
+                double* row = last_source + 6 * i;
+                row[0] = src[i].x;
+                row[1] = src[i].y;
+                row[2] = src[i].z;
+                row[3] = (double)src[i].ci;
+                row[4] = (double)src[i].cj;
+                row[5] = (double)src[i].inpin;
+            }
+        /* tallies: the active generations into t (private per thread, summed
+         * in thread order), the inactive ones into a scratch that is dropped */
+        int nt = 1;
+#ifdef _OPENMP
+        nt = n_threads > 1 ? n_threads : 1;
+#endif
+        size_t per = 2 * n_tal + n_out;
+        double* priv = (double*)calloc((size_t)nt * per, sizeof(double));
+        if (!priv) {
+            rc = -3;
+            break;
+        }
+#ifdef _OPENMP
+#pragma omp parallel num_threads(nt) reduction(| : capped)
+#endif
+        {
+            int tid = 0;
+#ifdef _OPENMP
+            tid = omp_get_thread_num();
+#endif
+            orc_tallies mine;
+            memset(&mine, 0, sizeof(mine));
+            mine.flux = priv + (size_t)tid * per;
+            mine.absorb = mine.flux + n_tal;
+            mine.outcome = mine.flux + 2 * n_tal;
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 64)
+#endif
+            for (int64_t i = 0; i < N; ++i) {
+                int64_t j = active ? (int64_t)(g - n_inactive) * N + i : 0;
+                int64_t b = active ? (j * B) / (n_active * N) : 0;
+                if (orc_history(p, &mine, seed, (int64_t)g * N + i, b,
+                                (last && ncoll) ? &ncoll[i] : NULL, &hist[i]))
+                    capped |= 1;
+            }
+        }
+        orc_tallies* dst = active ? t : &dump;
+        for (int tid = 0; tid < nt; ++tid) {
+            double* base = priv + (size_t)tid * per;
+            for (size_t i = 0; i < n_tal; ++i) {
+                dst->flux[i] += base[i];
+                dst->absorb[i] += base[n_tal + i];
+            }
+            for (size_t i = 0; i < n_out; ++i) dst->outcome[i] += base[2 * n_tal + i];
+        }
+        free(priv);
+        if (capped) {
+            rc = -4;
+            break;
+        }
+        /* the bank in parent-history order, the estimators summed in that order */
+        int64_t M = 0;
+        double kc = 0.0, kt = 0.0;
+        for (int64_t i = 0; i < N; ++i) {
+            if (hist[i].failed) rc = -3;
+            M += hist[i].n_sites;
+            kc += hist[i].k_col;
+            kt += hist[i].k_tl;
+        }
+        if (rc) break;
+        double k_g = ((double)M * k_norm) / (double)N;
+        gen_out[4 * g + 0] = k_g;
+        gen_out[4 * g + 1] = kc / (double)N;
+        gen_out[4 * g + 2] = kt / (double)N;
+        gen_out[4 * g + 3] = (double)M;
+        if (M == 0) {
+            rc = -2;
+            break;
+        }
+        orc_site* bank = (orc_site*)malloc((size_t)M * sizeof(orc_site));
+        orc_site* next = (orc_site*)malloc((size_t)N * sizeof(orc_site));
+        if (!bank || !next) {
+            free(bank);
+            free(next);
+            rc = -3;
+            break;
+        }
+        int64_t pos = 0;
+        for (int64_t i = 0; i < N; ++i)
+            for (int64_t k = 0; k < hist[i].n_sites; ++k) bank[pos++] = hist[i].sites[k];
+        if (last) {
+            if (bank_n) *bank_n = M;
+            if (last_bank)
+                for (int64_t k = 0; k < M && k < bank_cap; ++k) {
+                    double* row = last_bank + 6 * k;
+                    row[0] = bank[k].x;
+                    row[1] = bank[k].y;
+                    row[2] = bank[k].z;
+                    row[3] = (double)bank[k].ci;
+                    row[4] = (double)bank[k].cj;
+                    row[5] = (double)bank[k].inpin;
+                }
+        }
+        for (int64_t i = 0; i < N; ++i) next[i] = bank[(i * M) / N];
+        free(bank);
+        free(src);
+        src = next;
+        k_norm = k_g;
+    }
+    for (int64_t i = 0; hist && i < N; ++i) free(hist[i].sites);
+    free(hist);
+    free(src);
+    free(scratch);
+    return rc;
 }
 
 int orc_max_threads(void)
@@ -755,6 +1036,29 @@ void orc_source_state(const orc_problem* p, uint64_t seed, int64_t h, double* ou
     out[7] = (double)r.n;
 }
 
+/* State {x, y, z, u, v, w, E, region, draws used} of history h started from
+ * the fission site {x, y, z, ci, cj, inpin} (pins). */
+void orc_site_source_state(const orc_problem* p, uint64_t seed, int64_t h, const double* site,
+                           double T, double* out)
+{
+    orc_rng r;
+    orc_particle q;
+    orc_site st;
+    st.x = site[0];
+    st.y = site[1];
+    st.z = site[2];
+    st.ci = (int32_t)site[3];
+    st.cj = (int32_t)site[4];
+    st.inpin = (int32_t)site[5];
+    orc_rng_init(&r, seed, p->problem_id, (uint64_t)h);
+    orc_site_source(p, &r, &st, T, &q);
+    out[0] = q.x; out[1] = q.y; out[2] = q.z;
+    out[3] = q.u; out[4] = q.v; out[5] = q.w;
+    out[6] = q.E;
+    out[7] = (double)q.region;
+    out[8] = (double)r.n;
+}
+
 /* Distance to the nearest surface from state st = {x, y, z, u, v, w, ci, cj,
  * inpin}; returns the surface id (ORC_S_*) and writes the distance. */
 int orc_surface_distance(const orc_problem* p, const double* st, double* dist)
@@ -767,4 +1071,13 @@ int orc_surface_distance(const orc_problem* p, const double* st, double* dist)
     int surf;
     *dist = orc_distance(p, &q, &surf);
     return surf;
+}
+
+/* n successive fission-spectrum energies from history hist's stream (pins). */
+void orc_fission_energies(uint64_t seed, uint32_t problem_id, uint64_t hist, double T, int64_t n,
+                          double* out)
+{
+    orc_rng r;
+    orc_rng_init(&r, seed, problem_id, hist);
+    for (int64_t i = 0; i < n; ++i) out[i] = orc_fission_energy(&r, T);
 }

@@ -201,6 +201,7 @@ class Problem:
     region_material: np.ndarray = field(default_factory=lambda: np.zeros(1, np.int32))
     E0: float = 2.0e6
     E_cut: float = 1.0e-5
+    T_fission: float = 1.2895e6     # Maxwellian temperature of fission neutrons (eV)
     ebin_edges: np.ndarray = field(default_factory=lambda: np.zeros(0))
     n_batches: int = 20
     problem_id: int = 0
@@ -291,6 +292,32 @@ def flat_library(sig_s: float, sig_a: float, A: float = 1.0) -> Library:
     g = np.array([E_MIN, E_MAX])
     return Library(np.array([0, 2], np.int64), g, np.array([[sig_s, sig_a], [sig_s, sig_a]]),
                    np.array([A]))
+
+
+def flat_fission_library(sig_s: float, sig_a: float, nu_sig_f: float, A: float = 1.0) -> Library:
+    """One species with constant 3-channel cross sections (scatter, absorb,
+    nu-fission): an infinite medium of it has k = nu_sig_f / sig_a."""
+    g = np.array([E_MIN, E_MAX])
+    row = [sig_s, sig_a, nu_sig_f]
+    return Library(np.array([0, 2], np.int64), g, np.array([row, row]), np.array([A]))
+
+
+def eigen_library(n_points: int = 11_303, seed: int = 1237) -> Library:
+    """The lattice library with scatter, absorb and nu-fission channels.
+    Only fuel species (0-39) keep their fission data; the moderator and
+    guide-tube species (40-46) are made non-fissile."""
+    lib = species_library(47, n_points, seed).channels([CH_SCATTER, CH_ABSORB, CH_NU_FISSION])
+    lib.sigma[lib.grid_offsets[40]:, 2] = 0.0
+    return lib
+
+
+def eigen_problem(n_per_gen: int, lattice_n: int = 17, n_points: int = 11_303, seed: int = 1237,
+                  lib: Library | None = None, n_batches: int = 20) -> Problem:
+    """The 17x17 lattice as a k-eigenvalue problem (fission channels kept)."""
+    lib = lib if lib is not None else eigen_library(n_points, seed)
+    return Problem(GEOM_LATTICE, lib, config3_materials(seed), lattice_n=lattice_n,
+                   region_material=lattice_region_material(lattice_n), n_histories=n_per_gen,
+                   n_batches=n_batches)
 
 
 def linear_library(n_species: int, n_points: int, seed: int, n_ch: int = 5,
