@@ -161,8 +161,10 @@ int mcx_init_problem(const mcx_problem_desc* desc, mcx_problem** out);
  *   energies     [P]            FP64, positive, finite, strictly increasing
  *                               within each species
  *   sigma        [P][n_ch]      FP64 cross sections, finite and >= 0;
- *                               n_ch = 2 (scatter, absorb) or 5 (total,
- *                               scatter, absorb, fission, nu-fission)
+ *                               n_ch = 2 (scatter, absorb), 3 (scatter,
+ *                               absorb, nu-fission) or 5 (total, scatter,
+ *                               absorb, fission, nu-fission); the lookup
+ *                               entry points take any n_ch in 1..5
  *   awr          [n_species]    mass ratio A >= 1 (used by transport)
  *   mat_offsets  [n_materials+1], mat_species [nnz] (ids in range),
  *   mat_dens     [nnz]          atom densities, finite and >= 0
@@ -226,6 +228,40 @@ int mcx_run_batch(mcx_problem* p, int64_t first_history, int64_t n_histories,
  * used.  Errors as mcx_run_batch. */
 int mcx_batch_run(int32_t n_problems, mcx_problem* const* problems, const int64_t* n_hist,
                   int64_t particles_in_flight, uint64_t seed, void* stream);
+
+/* k-eigenvalue power iteration (the paper's benchmark, Hoogenboom-Martin, is a
+ * criticality problem, Sec. 5.1).  Generation g runs n_per_gen histories with
+ * ids g * n_per_gen + i (their own random streams) through the event loop
+ * under the problem's tuning.  Generation 0 starts from the fixed source of
+ * the description; generation g > 0 starts history i at site i of its
+ * source: isotropic, with an energy from the Maxwellian fission spectrum of
+ * temperature T_fission (eV).  Every collision, before its reaction is
+ * decided, banks floor(nuSigma_f / Sigma_t / k_norm + xi) sites at the
+ * collision point (xi: the collision's fourth uniform); k_norm = k0 in
+ * generation 0 and the previous generation's k afterwards.  The M banked
+ * sites are put in the order of their parent history and, within a history,
+ * of banking; the next source is source[i] = bank[floor(i M / n_per_gen)].
+ * Per generation, HOST gen_out[4 g .. 4 g + 3] = {k = M k_norm / n_per_gen,
+ * collision estimate sum(nuSigma_f / Sigma_t) / n_per_gen, track-length
+ * estimate sum(d nuSigma_f) / n_per_gen, M}.  The tallies are cleared at the
+ * first active generation and then score the last n_generations - n_inactive
+ * generations: active history j = (g - n_inactive) n_per_gen + i falls in
+ * batch floor(j n_batches / ((n_generations - n_inactive) n_per_gen)).  The
+ * bank holds 4 n_per_gen sites (at least 4096) and grows when an inactive
+ * generation overflows it (the generation is run again).  Needs 3-channel
+ * (scatter, absorb, nu-fission) or 5-channel tables and no derivative flag.
+ * Synchronous.  Errors: MCX_ERR_ARG, MCX_ERR_STATE (a generation banked no
+ * site, or an inconsistent bank), MCX_ERR_BOUNDS (an active generation
+ * overflowed the bank), MCX_ERR_ITER_LIMIT, MCX_ERR_TIMEOUT, MCX_ERR_CUDA,
+ * MCX_ERR_OOM. */
+int mcx_run_eigenvalue(mcx_problem* p, int64_t n_per_gen, int32_t n_generations, int32_t n_inactive,
+                       double k0, double T_fission, int64_t particles_in_flight, uint64_t seed,
+                       double* gen_out, void* stream);
+
+/* The last eigenvalue generation's ordered bank: its size, and its first n
+ * sites as HOST rows {x, y, z, ci, cj, inpin} (n <= size).  Synchronous. */
+int mcx_fission_bank_size(const mcx_problem* p, int64_t* n);
+int mcx_read_fission_bank(mcx_problem* p, double* rows, int64_t n);
 
 /* Size in doubles of a tally, and a synchronous copy of it to HOST memory
  * (n must equal the size).  mcx_zero_tallies clears all tallies. */

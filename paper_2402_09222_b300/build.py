@@ -22,7 +22,8 @@ BUILD = os.path.join(ROOT, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 EXACT_TUS = {"transport.cu", "xs_exact.cu", "adjoint.cu"}
-SOURCES = ["mcx_api.cu", "xs_exact.cu", "xs_fast.cu", "transport.cu", "adjoint.cu", "noalloc.cu"]
+SOURCES = ["mcx_api.cu", "xs_exact.cu", "xs_fast.cu", "transport.cu", "adjoint.cu", "noalloc.cu",
+           "eigen.cu"]
 HEADERS = ["mcx_internal.cuh", "xs_exact.cuh", "kernels.h"]
 
 

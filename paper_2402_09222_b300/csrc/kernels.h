@@ -68,6 +68,21 @@ enum : uint8_t {
 enum { OUT_ABSORBED = 0, OUT_LEAK_XHI = 1, OUT_LEAK_OTHER = 2, OUT_CUTOFF = 3, OUT_COLLISIONS = 4,
        N_OUT = 5 };
 
+// A fission site: position, lattice cell (ci * n + cj) and inside-pin flag.
+struct FissionSite {
+    double x, y, z;
+    int32_t cell;
+    int32_t inpin;
+};
+
+// Per-generation device accumulators of an eigenvalue run.
+struct EigenCtl {
+    double k_col;                  // sum of nuSigma_f / Sigma_t over collisions
+    double k_tl;                   // sum of d nuSigma_f over flights
+    unsigned long long banked;     // sites banked (may exceed the bank capacity)
+    unsigned long long pad;
+};
+
 // One transport problem as the kernels see it (device array, one per
 // problem of a run).
 struct ProblemDev {
@@ -90,6 +105,16 @@ struct ProblemDev {
     double* dabsorb;
     double* doutcome;
     uint32_t* ncoll_debug;  // [run histories] or null
+    int64_t tally_off;      // batch of h = (h - tally_off) n_batches / n_hist_total
+    // eigenvalue generation (sites == null: fixed source, no banking)
+    const FissionSite* src; // [run histories] source sites, or null (fixed source)
+    double k_norm;          // a collision banks floor(nuSigma_f/Sigma_t/k_norm + xi) sites
+    double T_fission;       // Maxwellian temperature of fission neutrons (eV)
+    FissionSite* bank;      // staging bank [bank_cap], unordered
+    int2* bank_key;         // [bank_cap] {history - first, sequence within the history}
+    int64_t bank_cap;
+    uint32_t* site_count;   // [run histories] sites each history banked, or null
+    EigenCtl* eig;          // or null
 };
 
 // Structure-of-arrays particle buffer (one slot per particle in flight) and
@@ -100,6 +125,8 @@ struct Particles {
     double *x = nullptr, *y = nullptr, *z = nullptr;
     double *u = nullptr, *v = nullptr, *w = nullptr;
     double *E = nullptr, *sig_t = nullptr, *sig_a = nullptr;
+    double* sig_nf = nullptr;   // nuSigma_f of the last lookup (eigenvalue runs)
+    uint32_t* nsite = nullptr;  // sites banked by the slot's history so far
     double* W = nullptr;  // [MCX_MAX_DMAT][cap] (derivative runs)
     double* cum = nullptr;  // [cap][cum_stride]: running sums C_i of the last lookup
     int64_t cum_stride = 0; // >= the largest material's species count
@@ -159,6 +186,7 @@ struct LoopConfig {
     int n_sort_bins = 0;     // materials * n_ebuckets
     float sort_ln_lo = 0.f, sort_scale = 0.f;
     int derivatives = 0;
+    int eigen = 0;           // eigenvalue generation: nuSigma_f lookups, fission banking
 };
 
 // Kernels of one event-loop iteration, issued on `st` (capturable).
@@ -167,6 +195,18 @@ int launch_iteration(const LoopConfig& c, const Tables& t, const Particles& P,
                      const ProblemDev* probs, const int64_t* work_off, RunCtl* ctl,
                      cudaStream_t st);
 // Reset the particle buffer and loop control for a run of `total` work items.
+// Fission bank of an eigenvalue generation (eigen.cu): per-history site
+// offsets (exclusive scan of the counts; tile_sum needs bank_scan_tiles(n) + 1
+// entries, tile_sum[tiles] = total), placement by key, resampling.
+int64_t bank_scan_tiles(int64_t n);
+int launch_site_offsets(const uint32_t* cnt, int64_t n, unsigned long long* tile_sum,
+                        unsigned long long* off, cudaStream_t st);
+int launch_bank_order(const FissionSite* bank, const int2* key, int64_t n_banked,
+                      const unsigned long long* off, int64_t n_hist, int64_t M, FissionSite* ordered,
+                      unsigned long long* bad, int grid, cudaStream_t st);
+int launch_bank_resample(const FissionSite* ordered, int64_t M, int64_t N, FissionSite* src, int grid,
+                         cudaStream_t st);
+
 int launch_run_init(const LoopConfig& c, const Particles& P, RunCtl* ctl, long long total,
                     int n_prob, long long max_iters, cudaStream_t st);
 

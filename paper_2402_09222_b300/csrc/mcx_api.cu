@@ -3,6 +3,7 @@
 // device-side termination flag and iteration cap) and the lookup entry
 // points.  No exception or abort crosses the ABI: every failure becomes a
 // status code plus a thread-local message.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -182,6 +183,20 @@ struct mcx_problem {
     unsigned long long* work_ctr = nullptr;  // chunk counters of the binned fast lookup (2)
     int64_t h_buf_cap = 0;
     int64_t stats[6] = {0, 0, 0, 0, 0, 0};
+    // eigenvalue runs: staging bank, ordered bank, next source, per-history
+    // site counts and offsets, per-generation accumulators
+    EigenCtl* e_ctl = nullptr;
+    FissionSite* e_bank = nullptr;
+    int2* e_key = nullptr;
+    FissionSite* e_ordered = nullptr;
+    int64_t e_bank_cap = 0;
+    FissionSite* e_src = nullptr;
+    uint32_t* e_count = nullptr;
+    unsigned long long* e_off = nullptr;
+    unsigned long long* e_tiles = nullptr;
+    unsigned long long* e_bad = nullptr;
+    int64_t e_n_cap = 0;
+    int64_t e_last_M = 0;     // sites in e_ordered after the last generation
 };
 
 namespace {
@@ -222,8 +237,8 @@ int ensure_particles(mcx_problem* p, int64_t cap, bool with_w, size_t n_bins, in
     free_particles(p);
     const size_t c = (size_t)want;
     auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
-    size_t bytes = al(c * 8) * 9 + (w ? al(c * 8 * MCX_MAX_DMAT) : 0) + al(c * 8 * (size_t)cs) + al(c * 8) +
-                   al(c * 4) * 2 + al(c * 4) * 3 + al(c) + al(c * 4) * 8 + al((bins + 1) * 4);
+    size_t bytes = al(c * 8) * 10 + (w ? al(c * 8 * MCX_MAX_DMAT) : 0) + al(c * 8 * (size_t)cs) + al(c * 8) +
+                   al(c * 4) * 3 + al(c * 4) * 3 + al(c) + al(c * 4) * 8 + al((bins + 1) * 4);
     void* blk = nullptr;
     cudaError_t e = cudaMalloc(&blk, bytes);
     if (e != cudaSuccess) {
@@ -249,12 +264,14 @@ int ensure_particles(mcx_problem* p, int64_t cap, bool with_w, size_t n_bins, in
     P.E = (double*)take(c * 8);
     P.sig_t = (double*)take(c * 8);
     P.sig_a = (double*)take(c * 8);
+    P.sig_nf = (double*)take(c * 8);
     P.W = w ? (double*)take(c * 8 * MCX_MAX_DMAT) : nullptr;
     P.cum = (double*)take(c * 8 * (size_t)cs);
     P.cum_stride = cs;
     P.hist = (int64_t*)take(c * 8);
     P.rng_n = (uint32_t*)take(c * 4);
     P.ncoll = (uint32_t*)take(c * 4);
+    P.nsite = (uint32_t*)take(c * 4);
     P.cell = (int32_t*)take(c * 4);
     P.mat = (int32_t*)take(c * 4);
     P.prob = (int32_t*)take(c * 4);
@@ -461,13 +478,29 @@ int blocks_per_sm(int block)
     return b < 1 ? 1 : b;
 }
 
-// The event-loop driver shared by mcx_run_batch and mcx_batch_run.
+// What an eigenvalue generation changes in its (single) problem's view.
+struct EigenGen {
+    int64_t tally_off, n_hist_total;
+    const FissionSite* src;
+    double k_norm, T_fission;
+    FissionSite* bank;
+    int2* bank_key;
+    int64_t bank_cap;
+    uint32_t* site_count;
+    EigenCtl* eig;
+};
+
+// The event-loop driver shared by mcx_run_batch, mcx_batch_run and the
+// generations of mcx_run_eigenvalue (eg != null, one problem).
 int run_loop(mcx_problem* owner, int n_prob, mcx_problem* const* probs, const int64_t* first,
-             const int64_t* count, int64_t pif, uint64_t seed, void* user_stream)
+             const int64_t* count, int64_t pif, uint64_t seed, void* user_stream,
+             const EigenGen* eg = nullptr)
 {
     const TableStore* ts = owner->tables;
     const Tables& t = ts->view;
-    if (t.n_ch != 2 && t.n_ch != 5) return fail(MCX_ERR_ARG, "transport needs 2 or 5 channels");
+    if (t.n_ch != 2 && t.n_ch != 3 && t.n_ch != 5)
+        return fail(MCX_ERR_ARG, "transport needs 2, 3 or 5 channels");
+    if (eg && (n_prob != 1 || t.ch_nu_fission < 0)) return fail(MCX_ERR_ARG, "bad eigenvalue generation");
     const mcx_tune& tu = owner->tune;
     long long total = 0;
     for (int i = 0; i < n_prob; ++i) total += count[i];
@@ -487,6 +520,7 @@ int run_loop(mcx_problem* owner, int n_prob, mcx_problem* const* probs, const in
     c.sort_ln_lo = (float)std::log(ts->emin);
     c.sort_scale = (float)((double)c.n_ebuckets / (std::log(ts->emax) - std::log(ts->emin)));
     c.derivatives = deriv ? owner->M : 0;
+    c.eigen = eg ? 1 : 0;
     if ((size_t)c.n_sort_bins * 4 > 48 * 1024) c.sort_period = 0;  // bins must fit shared memory
     TRY(ensure_particles(owner, cap, deriv, (size_t)c.n_sort_bins, t.max_mat_species));
     // the buffer may be larger than this run needs: use exactly `cap` slots
@@ -514,6 +548,19 @@ int run_loop(mcx_problem* owner, int n_prob, mcx_problem* const* probs, const in
         }
         hp[i] = make_problem_dev(q, seed, first[i], deriv);
         wo[i + 1] = wo[i] + count[i];
+    }
+    if (eg) {
+        ProblemDev& d = hp[0];
+        d.tally_off = eg->tally_off;
+        d.n_hist_total = eg->n_hist_total;
+        d.src = eg->src;
+        d.k_norm = eg->k_norm;
+        d.T_fission = eg->T_fission;
+        d.bank = eg->bank;
+        d.bank_key = eg->bank_key;
+        d.bank_cap = eg->bank_cap;
+        d.site_count = eg->site_count;
+        d.eig = eg->eig;
     }
     cudaStream_t us = (cudaStream_t)user_stream;
     cudaStream_t st = owner->stream;
@@ -693,6 +740,40 @@ int lookup_device(mcx_problem* p, int64_t n, const double* E, const int32_t* mat
     return lookup_device_ordered(p, n, E, mat, perm, out, flags & MCX_LOOKUP_FAST, st);
 }
 
+// Eigenvalue scratch: per-history arrays for N histories and a staging and
+// an ordered bank of `bank_cap` sites (grown, never shrunk).
+int ensure_eigen(mcx_problem* p, int64_t N, int64_t bank_cap)
+{
+    if (!p->e_ctl) {
+        TRY(dev_alloc(&p->e_ctl, 1));
+        TRY(dev_alloc(&p->e_bad, 1));
+    }
+    if (p->e_n_cap < N) {
+        dev_free(p->e_src);
+        dev_free(p->e_count);
+        dev_free(p->e_off);
+        dev_free(p->e_tiles);
+        p->e_n_cap = 0;
+        TRY(dev_alloc(&p->e_src, (size_t)N));
+        TRY(dev_alloc(&p->e_count, (size_t)N));
+        TRY(dev_alloc(&p->e_off, (size_t)N));
+        TRY(dev_alloc(&p->e_tiles, (size_t)bank_scan_tiles(N) + 1));
+        p->e_n_cap = N;
+    }
+    if (p->e_bank_cap < bank_cap) {
+        dev_free(p->e_bank);
+        dev_free(p->e_key);
+        dev_free(p->e_ordered);
+        p->e_bank_cap = 0;
+        p->e_last_M = 0;
+        TRY(dev_alloc(&p->e_bank, (size_t)bank_cap));
+        TRY(dev_alloc(&p->e_key, (size_t)bank_cap));
+        TRY(dev_alloc(&p->e_ordered, (size_t)bank_cap));
+        p->e_bank_cap = bank_cap;
+    }
+    return MCX_OK;
+}
+
 }  // namespace
 
 // Read-only view of a problem's lookup tables for other translation units of
@@ -816,6 +897,15 @@ void mcx_destroy(mcx_problem* p)
     dev_free(p->lbins);
     dev_free(p->h_buf);
     dev_free(p->work_ctr);
+    dev_free(p->e_ctl);
+    dev_free(p->e_bank);
+    dev_free(p->e_key);
+    dev_free(p->e_ordered);
+    dev_free(p->e_src);
+    dev_free(p->e_count);
+    dev_free(p->e_off);
+    dev_free(p->e_tiles);
+    dev_free(p->e_bad);
     if (p->h_ctl) cudaFreeHost(p->h_ctl);
     if (p->ev_a) cudaEventDestroy(p->ev_a);
     if (p->ev_b) cudaEventDestroy(p->ev_b);
@@ -951,6 +1041,7 @@ int mcx_load_xs_tables(mcx_problem* p, int32_t n_species, const int64_t* goff, c
     v.max_mat_species = maxs;
     v.ch_scatter = n_ch == 5 ? 1 : 0;
     v.ch_absorb = n_ch == 5 ? 2 : 1;
+    v.ch_nu_fission = n_ch == 5 ? 4 : (n_ch == 3 ? 2 : -1);
     v.n_points = P;
     v.goff = ts->goff;
     v.E = ts->E;
@@ -1149,16 +1240,19 @@ int mcx_zero_tallies(mcx_problem* p)
     TRY(check_handle(p));
     if (p->desc.geometry == MCX_GEOM_NONE) return MCX_OK;
     DeviceGuard dg(p->device);
-    CUDA_TRY(cudaStreamSynchronize(p->stream));
+    // on the problem's own (non-blocking) stream, then wait: the next run on
+    // that stream cannot overtake the clearing
+    cudaStream_t st = p->stream;
     const int64_t B = p->desc.n_batches;
-    CUDA_TRY(cudaMemset(p->flux, 0, sizeof(double) * B * p->nb));
-    CUDA_TRY(cudaMemset(p->absorb, 0, sizeof(double) * B * p->nb));
-    CUDA_TRY(cudaMemset(p->outcome, 0, sizeof(double) * B * N_OUT));
+    CUDA_TRY(cudaMemsetAsync(p->flux, 0, sizeof(double) * B * p->nb, st));
+    CUDA_TRY(cudaMemsetAsync(p->absorb, 0, sizeof(double) * B * p->nb, st));
+    CUDA_TRY(cudaMemsetAsync(p->outcome, 0, sizeof(double) * B * N_OUT, st));
     if (p->M > 0) {
-        CUDA_TRY(cudaMemset(p->dflux, 0, sizeof(double) * B * p->nb * p->M));
-        CUDA_TRY(cudaMemset(p->dabsorb, 0, sizeof(double) * B * p->nb * p->M));
-        CUDA_TRY(cudaMemset(p->doutcome, 0, sizeof(double) * B * N_OUT * p->M));
+        CUDA_TRY(cudaMemsetAsync(p->dflux, 0, sizeof(double) * B * p->nb * p->M, st));
+        CUDA_TRY(cudaMemsetAsync(p->dabsorb, 0, sizeof(double) * B * p->nb * p->M, st));
+        CUDA_TRY(cudaMemsetAsync(p->doutcome, 0, sizeof(double) * B * N_OUT * p->M, st));
     }
+    CUDA_TRY(cudaStreamSynchronize(st));
     return MCX_OK;
 }
 
@@ -1314,6 +1408,134 @@ int mcx_debug_uniforms(uint64_t seed, uint32_t problem_id, uint64_t hist, uint32
     if (!out) return fail(MCX_ERR_ARG, "out is NULL");
     if (launch_debug_uniforms(rng_key(seed, problem_id), hist, first, n, out, (cudaStream_t)stream))
         return fail(MCX_ERR_CUDA, "uniforms kernel launch failed");
+    return MCX_OK;
+}
+
+int mcx_run_eigenvalue(mcx_problem* p, int64_t n_per_gen, int32_t n_generations, int32_t n_inactive,
+                       double k0, double T_fission, int64_t particles_in_flight, uint64_t seed,
+                       double* gen_out, void* stream)
+{
+    g_err.clear();
+    TRY(check_tables(p));
+    if (p->desc.geometry == MCX_GEOM_NONE) return fail(MCX_ERR_STATE, "problem has no geometry");
+    if (p->tables->view.ch_nu_fission < 0)
+        return fail(MCX_ERR_ARG, "an eigenvalue run needs a nu-fission channel (3- or 5-channel tables)");
+    if (n_per_gen < 1 || n_per_gen > INT32_MAX) return fail(MCX_ERR_ARG, "n_per_gen out of range");
+    if (n_generations < 1 || n_inactive < 0 || n_inactive >= n_generations)
+        return fail(MCX_ERR_ARG, "need 0 <= n_inactive < n_generations");
+    if (!(k0 > 0.0) || !is_finite(k0)) return fail(MCX_ERR_ARG, "k0 must be positive and finite");
+    if (!(T_fission > 0.0) || !is_finite(T_fission)) return fail(MCX_ERR_ARG, "T_fission must be positive");
+    if (!gen_out) return fail(MCX_ERR_ARG, "gen_out is NULL");
+    if (p->M > 0) return fail(MCX_ERR_ARG, "derivative tallies are not supported in eigenvalue runs");
+    if ((double)n_generations * (double)n_per_gen > 9.0e18) return fail(MCX_ERR_ARG, "too many histories");
+    DeviceGuard dg(p->device);
+    const int64_t N = n_per_gen;
+    const int64_t n_active = n_generations - n_inactive;
+    TRY(ensure_eigen(p, N, std::max<int64_t>(4 * N, 4096)));
+    cudaStream_t st = p->stream;
+    const int grid = p->sm_count * 8;
+    double k_norm = k0;
+    mcx_problem* probs[1] = {p};
+    for (int32_t g = 0; g < n_generations; ++g) {
+        const bool active = g >= n_inactive;
+        if (g == n_inactive) TRY(mcx_zero_tallies(p));
+        EigenCtl h{};
+        for (int attempt = 0;; ++attempt) {
+            CUDA_TRY(cudaMemsetAsync(p->e_ctl, 0, sizeof(EigenCtl), st));
+            CUDA_TRY(cudaMemsetAsync(p->e_count, 0, sizeof(uint32_t) * N, st));
+            EigenGen eg;
+            eg.tally_off = active ? (int64_t)n_inactive * N : (int64_t)g * N;
+            eg.n_hist_total = active ? n_active * N : N;
+            eg.src = g > 0 ? p->e_src : nullptr;
+            eg.k_norm = k_norm;
+            eg.T_fission = T_fission;
+            eg.bank = p->e_bank;
+            eg.bank_key = p->e_key;
+            eg.bank_cap = p->e_bank_cap;
+            eg.site_count = p->e_count;
+            eg.eig = p->e_ctl;
+            const int64_t first = (int64_t)g * N, count = N;
+            // the generation's histories run on the problem's stream after
+            // the memsets above (run_loop orders the user stream before it)
+            CUDA_TRY(cudaStreamSynchronize(st));
+            TRY(run_loop(p, 1, probs, &first, &count, particles_in_flight, seed, stream, &eg));
+            CUDA_TRY(cudaMemcpyAsync(&h, p->e_ctl, sizeof(EigenCtl), cudaMemcpyDeviceToHost, st));
+            CUDA_TRY(cudaStreamSynchronize(st));
+            if (h.banked <= (unsigned long long)p->e_bank_cap) break;
+            // the bank overflowed: the generation's histories are fixed by
+            // their keys, so an inactive generation is simply run again with
+            // room for every site; an active one has already scored
+            if (active || attempt >= 2)
+                return fail(MCX_ERR_BOUNDS, "fission bank overflow in generation %d: %llu sites, capacity %lld",
+                            g, h.banked, (long long)p->e_bank_cap);
+            const int64_t need = (int64_t)h.banked + (int64_t)(h.banked / 4) + 1024;
+            if (need > ((int64_t)1 << 31)) return fail(MCX_ERR_BOUNDS, "fission bank of %llu sites is too large", h.banked);
+            TRY(ensure_eigen(p, N, need));
+        }
+        const int64_t M = (int64_t)h.banked;
+        const double k_g = ((double)M * k_norm) / (double)N;
+        gen_out[4 * g + 0] = k_g;
+        gen_out[4 * g + 1] = h.k_col / (double)N;
+        gen_out[4 * g + 2] = h.k_tl / (double)N;
+        gen_out[4 * g + 3] = (double)M;
+        if (M == 0) {
+            p->e_last_M = 0;
+            return fail(MCX_ERR_STATE, "generation %d banked no fission site", g);
+        }
+        // canonical order (parent history, sequence), then the next source
+        unsigned long long total = 0ull, bad = 0ull;
+        if (launch_site_offsets(p->e_count, N, p->e_tiles, p->e_off, st))
+            return fail(MCX_ERR_CUDA, "site offset kernels failed to launch");
+        CUDA_TRY(cudaMemsetAsync(p->e_bad, 0, sizeof(unsigned long long), st));
+        if (launch_bank_order(p->e_bank, p->e_key, M, p->e_off, N, M, p->e_ordered, p->e_bad, grid, st))
+            return fail(MCX_ERR_CUDA, "bank order kernel failed to launch");
+        CUDA_TRY(cudaMemcpyAsync(&total, p->e_tiles + bank_scan_tiles(N), sizeof(total), cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaMemcpyAsync(&bad, p->e_bad, sizeof(bad), cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+        if (total != (unsigned long long)M || bad != 0ull)
+            return fail(MCX_ERR_STATE, "generation %d: %llu sites banked, %llu counted by histories, %llu misplaced",
+                        g, (unsigned long long)M, total, bad);
+        p->e_last_M = M;
+        if (g + 1 < n_generations) {
+            if (launch_bank_resample(p->e_ordered, M, N, p->e_src, grid, st))
+                return fail(MCX_ERR_CUDA, "resample kernel failed to launch");
+        }
+        k_norm = k_g;
+    }
+    CUDA_TRY(cudaStreamSynchronize(st));
+    return MCX_OK;
+}
+
+int mcx_fission_bank_size(const mcx_problem* p, int64_t* n)
+{
+    g_err.clear();
+    TRY(check_handle(p));
+    if (!n) return fail(MCX_ERR_ARG, "n is NULL");
+    *n = p->e_last_M;
+    return MCX_OK;
+}
+
+int mcx_read_fission_bank(mcx_problem* p, double* rows, int64_t n)
+{
+    g_err.clear();
+    TRY(check_handle(p));
+    if (n < 0 || n > p->e_last_M) return fail(MCX_ERR_ARG, "n must be in [0, %lld]", (long long)p->e_last_M);
+    if (n == 0) return MCX_OK;
+    if (!rows) return fail(MCX_ERR_ARG, "rows is NULL");
+    DeviceGuard dg(p->device);
+    std::vector<FissionSite> h((size_t)n);
+    CUDA_TRY(cudaMemcpyAsync(h.data(), p->e_ordered, sizeof(FissionSite) * n, cudaMemcpyDeviceToHost, p->stream));
+    CUDA_TRY(cudaStreamSynchronize(p->stream));
+    const int32_t ln = p->desc.geometry == MCX_GEOM_LATTICE && p->desc.lattice_n > 0 ? p->desc.lattice_n : 1;
+    for (int64_t i = 0; i < n; ++i) {
+        double* r = rows + 6 * i;
+        r[0] = h[i].x;
+        r[1] = h[i].y;
+        r[2] = h[i].z;
+        r[3] = (double)(h[i].cell / ln);
+        r[4] = (double)(h[i].cell % ln);
+        r[5] = (double)h[i].inpin;
+    }
     return MCX_OK;
 }
 

@@ -41,6 +41,7 @@ struct Tables {
     int32_t n_materials = 0;
     int32_t max_mat_species = 0;
     int32_t ch_scatter = 0, ch_absorb = 1;
+    int32_t ch_nu_fission = -1;   // -1: the tables carry no nu-fission channel
     int64_t n_points = 0;
     const int64_t* goff = nullptr;
     const double* E = nullptr;

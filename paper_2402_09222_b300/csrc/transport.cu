@@ -112,6 +112,17 @@ __device__ __forceinline__ void ring_push(const Particles& P, RunCtl* ctl, int r
     }
 }
 
+// Sum of v over the lanes with `on`, added to *a with one atomic (every lane
+// of the converged warp calls it).
+__device__ __forceinline__ void warp_add(double* a, double v, bool on)
+{
+    const unsigned m = __ballot_sync(FULL, on);
+    if (m == 0u) return;
+    double s = on ? v : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
+    if (lane_id() == __ffs(m) - 1) atomicAdd(a, s);
+}
+
 // Azimuth (cos phi, sin phi) by rejection on pairs (2u-1, 2u-1) inside the
 // unit disc.
 __device__ __forceinline__ void azimuth(uint2 key, uint64_t h, uint32_t& n, double& c, double& s)
@@ -129,6 +140,20 @@ __device__ __forceinline__ void azimuth(uint2 key, uint64_t h, uint32_t& n, doub
     }
     c = 1.0;
     s = 0.0;
+}
+
+// Fission-spectrum energy: the Maxwellian sqrt(E) exp(-E/T), a Gamma(3/2, T)
+// variate, as a Gamma(1) plus a Gamma(1/2) variate: E = -T (ln xi1 +
+// ln xi2 cos^2 phi), phi uniform (the square of a Box-Muller normal;
+// Everett and Cashwell's sampler, rule C64), cos phi from the disc rejection.
+__device__ __forceinline__ double fission_energy(uint2 key, uint64_t h, uint32_t& n, double T)
+{
+    const double xi1 = uniform_at(key, h, n);
+    const double xi2 = uniform_at(key, h, n + 1);
+    n += 2;
+    double c, s;
+    azimuth(key, h, n, c, s);
+    return -T * (log(xi1) + (c * c) * log(xi2));
 }
 
 struct State {
@@ -265,7 +290,7 @@ __device__ __forceinline__ void rotate(double& u, double& v, double& w, double m
 
 __device__ __forceinline__ int64_t batch_of(const ProblemDev& pd, int64_t h)
 {
-    return (h * (int64_t)pd.n_batches) / pd.n_hist_total;
+    return ((h - pd.tally_off) * (int64_t)pd.n_batches) / pd.n_hist_total;
 }
 
 // Map a work item to (problem, history).
@@ -282,13 +307,35 @@ __device__ __forceinline__ int problem_of_work(const int64_t* work_off, int n_pr
 
 // Source particle of history h (lattice: centre of a uniformly chosen pin at
 // mid-height; infinite medium: origin; both isotropic; slab: pencil along +x).
+template <bool EIG>
 __device__ void init_particle(const Particles& P, int64_t slot, const ProblemDev& pd,
                               int32_t pidx, int64_t h, int M)
 {
     const uint2 key = pd.key;
     uint32_t n = 0;
     State q = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0, 0, 0};
-    if (pd.geometry == MCX_GEOM_SLAB) {
+    double E0 = pd.E0;
+    if (EIG && pd.src) {
+        // eigenvalue generation: start at the history's fission site,
+        // isotropic, with a fission-spectrum energy
+        const FissionSite site = pd.src[h - pd.first];
+        const int32_t ln = pd.lattice_n > 0 ? pd.lattice_n : 1;
+        q.x = site.x;
+        q.y = site.y;
+        q.z = site.z;
+        q.ci = site.cell / ln;
+        q.cj = site.cell % ln;
+        q.inpin = site.inpin;
+        const double mu = 2.0 * uniform_at(key, h, n) - 1.0;
+        n += 1;
+        double c, s;
+        azimuth(key, h, n, c, s);
+        const double st = sqrt(1.0 - mu * mu);
+        q.u = st * c;
+        q.v = st * s;
+        q.w = mu;
+        E0 = fission_energy(key, h, n, pd.T_fission);
+    } else if (pd.geometry == MCX_GEOM_SLAB) {
         q.u = 1.0;
     } else {
         if (pd.geometry == MCX_GEOM_LATTICE) {
@@ -315,8 +362,9 @@ __device__ void init_particle(const Particles& P, int64_t slot, const ProblemDev
     }
     P.x[slot] = q.x; P.y[slot] = q.y; P.z[slot] = q.z;
     P.u[slot] = q.u; P.v[slot] = q.v; P.w[slot] = q.w;
-    P.E[slot] = pd.E0;
+    P.E[slot] = E0;
     P.hist[slot] = h;
+    if (EIG) P.nsite[slot] = 0u;
     P.rng_n[slot] = n;
     P.ncoll[slot] = 0u;
     P.cell[slot] = q.ci * (pd.lattice_n > 0 ? pd.lattice_n : 1) + q.cj;
@@ -342,6 +390,7 @@ __device__ __forceinline__ State load_state(const Particles& P, int64_t slot, in
 // Deaths of this warp: outcome tallies (one atomic per distinct tally cell),
 // derivative outcome tallies, per-history debug counts, slot release, alive
 // count and (queued modes) the free-slot queue.  Every lane of the warp calls it.
+template <bool EIG>
 __device__ void finish_deaths(bool dies, int outcome, int64_t slot, int32_t pidx,
                               const ProblemDev* probs, const Particles& P, RunCtl* ctl, int M,
                               int mode, int par)
@@ -364,6 +413,7 @@ __device__ void finish_deaths(bool dies, int outcome, int64_t slot, int32_t pidx
                 atomicAdd(pd.doutcome + (b * N_OUT + outcome) * M + mm, sum);
         }
         if (pd.ncoll_debug) pd.ncoll_debug[h - pd.first] = P.ncoll[slot];
+        if (EIG && pd.site_count) pd.site_count[h - pd.first] = P.nsite[slot];
         P.flags[slot] = 0;
     }
     if (lane_id() == 0) atomicSub(&ctl->n_alive, __popc(dm));
@@ -419,6 +469,7 @@ __global__ void k_run_init(Particles P, RunCtl* ctl, long long total, int n_prob
     }
 }
 
+template <bool EIG>
 __global__ void __launch_bounds__(1024) k_refill(LoopConfig c, Particles P, const ProblemDev* probs,
                                                  const int64_t* work_off, RunCtl* ctl)
 {
@@ -475,7 +526,7 @@ __global__ void __launch_bounds__(1024) k_refill(LoopConfig c, Particles P, cons
             if (wk < total) {
                 const int p = problem_of_work(work_off, n_prob, wk);
                 const ProblemDev& pd = probs[p];
-                init_particle(P, slot, pd, p, pd.first + (wk - work_off[p]), c.derivatives ? pd.M : 0);
+                init_particle<EIG>(P, slot, pd, p, pd.first + (wk - work_off[p]), c.derivatives ? pd.M : 0);
                 got = true;
             } else {
                 P.flags[slot] = PF_RETIRED;
@@ -495,7 +546,7 @@ __global__ void __launch_bounds__(1024) k_refill(LoopConfig c, Particles P, cons
     if (lane_id() == 0 && added) atomicAdd(&ctl->n_alive, added);
 }
 
-template <typename T>
+template <typename T, bool EIG>
 __global__ void __launch_bounds__(1024) k_lookup(LoopConfig c, Tables t, Particles P, RunCtl* ctl)
 {
     if (ctl->error) return;
@@ -521,7 +572,14 @@ __global__ void __launch_bounds__(1024) k_lookup(LoopConfig c, Tables t, Particl
             if (f & PF_NEED_XS) {
                 act = true;
                 double st, sa;
-                macro_transport<T>(t, P.mat[slot], P.E[slot], st, sa, P.cum + slot * P.cum_stride);
+                if (EIG) {
+                    double nf;
+                    macro_transport<T, true>(t, P.mat[slot], P.E[slot], st, sa,
+                                             P.cum + slot * P.cum_stride, &nf);
+                    P.sig_nf[slot] = nf;
+                } else {
+                    macro_transport<T>(t, P.mat[slot], P.E[slot], st, sa, P.cum + slot * P.cum_stride);
+                }
                 P.sig_t[slot] = st;
                 P.sig_a[slot] = sa;
                 P.flags[slot] = f & (uint8_t)~PF_NEED_XS;
@@ -531,6 +589,7 @@ __global__ void __launch_bounds__(1024) k_lookup(LoopConfig c, Tables t, Particl
     }
 }
 
+template <bool EIG>
 __global__ void __launch_bounds__(1024) k_advance(LoopConfig c, Particles P, const ProblemDev* probs,
                                                   RunCtl* ctl)
 {
@@ -561,6 +620,7 @@ __global__ void __launch_bounds__(1024) k_advance(LoopConfig c, Particles P, con
         double* tal_flux = nullptr;
         double* tal_abs = nullptr;
         int64_t tal_i = 0;
+        double k_tl = 0.0;
         double Wl[MCX_MAX_DMAT] = {0.0, 0.0, 0.0, 0.0};
         int32_t m = 0;
         if (act) {
@@ -597,6 +657,7 @@ __global__ void __launch_bounds__(1024) k_advance(LoopConfig c, Particles P, con
                 tal_abs = pd.absorb + tal_i;
                 scored = true;
                 xabs = d * sig_a;
+                if (EIG) k_tl = d * P.sig_nf[slot];
                 if (M > 0) {
                     for (int mm = 0; mm < M; ++mm) Wl[mm] = P.W[(int64_t)mm * P.stride + slot];
                     for (int mm = 0; mm < M; ++mm) {
@@ -635,6 +696,7 @@ __global__ void __launch_bounds__(1024) k_advance(LoopConfig c, Particles P, con
             P.rng_n[slot] = n;
             P.flags[slot] = fl;
         }
+        if (EIG) warp_add(&probs[0].eig->k_tl, k_tl, scored);
         // ---- warp-first tally reduction
         const unsigned sm = __ballot_sync(FULL, scored);
         if (scored) {
@@ -668,7 +730,7 @@ __global__ void __launch_bounds__(1024) k_advance(LoopConfig c, Particles P, con
                 }
             }
         }
-        finish_deaths(dies, outcome, slot, pidx, probs, P, ctl, M, c.mode, par);
+        finish_deaths<EIG>(dies, outcome, slot, pidx, probs, P, ctl, M, c.mode, par);
         if (queued) {
             int pos = warp_append(&ctl->n_coll, coll);
             if (coll) P.q_coll[pos] = (int32_t)slot;
@@ -689,7 +751,7 @@ __global__ void __launch_bounds__(1024) k_advance(LoopConfig c, Particles P, con
 // none); absorption if xi2 * sigma_t,j < sigma_a,j (analog); otherwise
 // elastic scattering isotropic in the centre-of-mass frame, killed below
 // E_cut.
-template <typename T>
+template <typename T, bool EIG>
 __global__ void __launch_bounds__(1024) k_collide(LoopConfig c, Tables t, Particles P,
                                                   const ProblemDev* probs, RunCtl* ctl)
 {
@@ -721,6 +783,10 @@ __global__ void __launch_bounds__(1024) k_collide(LoopConfig c, Tables t, Partic
         int32_t pidx = 0;
         double* tal_coll = nullptr;
         int64_t tal_i = 0;
+        double k_col = 0.0;
+        int64_t n_new = 0;
+        uint32_t seq0 = 0u;
+        FissionSite site;
         if (act) {
             pidx = P.prob[slot];
             const ProblemDev& pd = probs[pidx];
@@ -733,6 +799,24 @@ __global__ void __launch_bounds__(1024) k_collide(LoopConfig c, Tables t, Partic
             const double xi2 = uniform_at(pd.key, h, n + 1);
             const double xi3 = uniform_at(pd.key, h, n + 2);
             n += 3;
+            if (EIG) {
+                // fission sites of this collision, banked before the reaction
+                // is decided: floor(nuSigma_f / Sigma_t / k_norm + xi4)
+                const double xi4 = uniform_at(pd.key, h, n);
+                n += 1;
+                const double yield = P.sig_nf[slot] / P.sig_t[slot];
+                k_col = yield;
+                const double fl = floor(yield / pd.k_norm + xi4);
+                const double lim = (double)pd.bank_cap + 1.0;   // overflow is reported, not looped on
+                n_new = fl > 0.0 ? (int64_t)(fl < lim ? fl : lim) : 0;
+                site.x = P.x[slot];
+                site.y = P.y[slot];
+                site.z = P.z[slot];
+                site.cell = P.cell[slot];
+                site.inpin = (P.flags[slot] & PF_INPIN) ? 1 : 0;
+                seq0 = P.nsite[slot];
+                P.nsite[slot] = seq0 + (uint32_t)n_new;
+            }
             const double E = P.E[slot];
             const int32_t m = P.mat[slot];
             const double target = xi1 * P.sig_t[slot];
@@ -794,6 +878,27 @@ __global__ void __launch_bounds__(1024) k_collide(LoopConfig c, Tables t, Partic
             P.rng_n[slot] = n;
             P.flags[slot] = fl;
         }
+        if (EIG) {
+            const ProblemDev& p0 = probs[0];
+            warp_add(&p0.eig->k_col, k_col, act);
+            const int64_t hrel = act ? P.hist[slot] - p0.first : 0;
+            for (int64_t s = 0;; ++s) {
+                const bool want = act && s < n_new;
+                const unsigned b = __ballot_sync(FULL, want);
+                if (b == 0u) break;
+                const int leader = __ffs(b) - 1;
+                unsigned long long base = 0ull;
+                if (lane_id() == leader) base = atomicAdd(&p0.eig->banked, (unsigned long long)__popc(b));
+                base = __shfl_sync(FULL, base, leader);
+                if (want) {
+                    const unsigned long long pos = base + __popc(b & lanes_below());
+                    if (pos < (unsigned long long)p0.bank_cap) {
+                        p0.bank[pos] = site;
+                        p0.bank_key[pos] = make_int2((int32_t)hrel, (int32_t)(seq0 + (uint32_t)s));
+                    }
+                }
+            }
+        }
         // collision-count tally (+ derivative), warp-first
         const unsigned am = __ballot_sync(FULL, act);
         if (act) {
@@ -810,7 +915,7 @@ __global__ void __launch_bounds__(1024) k_collide(LoopConfig c, Tables t, Partic
                 }
             }
         }
-        finish_deaths(dies, outcome, slot, pidx, probs, P, ctl, M, c.mode, par);
+        finish_deaths<EIG>(dies, outcome, slot, pidx, probs, P, ctl, M, c.mode, par);
         if (queued) {
             int pos = warp_append(&ctl->n_xs[par ^ 1], survive);
             if (survive) P.q_xs[par ^ 1][pos] = (int32_t)slot;
@@ -1021,42 +1126,54 @@ static int launch_sort(const LoopConfig& c, const Particles& P, RunCtl* ctl, int
     return 4;
 }
 
-int launch_iteration(const LoopConfig& c, const Tables& t, const Particles& P,
-                     const ProblemDev* probs, const int64_t* work_off, RunCtl* ctl,
-                     cudaStream_t st)
+template <bool EIG>
+static int launch_iteration_t(const LoopConfig& c, const Tables& t, const Particles& P,
+                              const ProblemDev* probs, const int64_t* work_off, RunCtl* ctl,
+                              cudaStream_t st)
 {
     int k = 0;
     const bool sorting = c.mode != MCX_QUEUELESS && c.sort_period > 0 && c.n_sort_bins > 0;
-    k_refill<<<c.grid, c.block, 0, st>>>(c, P, probs, work_off, ctl);
+    const bool f32 = t.precision == MCX_FP32;
+    k_refill<EIG><<<c.grid, c.block, 0, st>>>(c, P, probs, work_off, ctl);
     ++k;
     if (c.mode == MCX_QUEUED_FULLEST) {
         // one step: the event kernels not selected return at once
         k_fq_select<<<1, 1, 0, st>>>(ctl, (long long)P.cap);
         ++k;
         if (sorting) k += launch_sort(c, P, ctl, 2, st);
-        if (t.precision == MCX_FP32) k_lookup<float><<<c.grid, c.block, 0, st>>>(c, t, P, ctl);
-        else k_lookup<double><<<c.grid, c.block, 0, st>>>(c, t, P, ctl);
-        k_advance<<<c.grid, c.block, 0, st>>>(c, P, probs, ctl);
-        if (t.precision == MCX_FP32) k_collide<float><<<c.grid, c.block, 0, st>>>(c, t, P, probs, ctl);
-        else k_collide<double><<<c.grid, c.block, 0, st>>>(c, t, P, probs, ctl);
+        if (f32) k_lookup<float, EIG><<<c.grid, c.block, 0, st>>>(c, t, P, ctl);
+        else k_lookup<double, EIG><<<c.grid, c.block, 0, st>>>(c, t, P, ctl);
+        k_advance<EIG><<<c.grid, c.block, 0, st>>>(c, P, probs, ctl);
+        if (f32) k_collide<float, EIG><<<c.grid, c.block, 0, st>>>(c, t, P, probs, ctl);
+        else k_collide<double, EIG><<<c.grid, c.block, 0, st>>>(c, t, P, probs, ctl);
         k += 3;
         if (cudaGetLastError() != cudaSuccess) return -1;
         return k;
     }
     if (sorting) k += launch_sort(c, P, ctl, 0, st);
-    if (t.precision == MCX_FP32) k_lookup<float><<<c.grid, c.block, 0, st>>>(c, t, P, ctl);
-    else k_lookup<double><<<c.grid, c.block, 0, st>>>(c, t, P, ctl);
+    if (f32) k_lookup<float, EIG><<<c.grid, c.block, 0, st>>>(c, t, P, ctl);
+    else k_lookup<double, EIG><<<c.grid, c.block, 0, st>>>(c, t, P, ctl);
     ++k;
-    k_advance<<<c.grid, c.block, 0, st>>>(c, P, probs, ctl);
+    k_advance<EIG><<<c.grid, c.block, 0, st>>>(c, P, probs, ctl);
     ++k;
     if (sorting) k += launch_sort(c, P, ctl, 1, st);
-    if (t.precision == MCX_FP32) k_collide<float><<<c.grid, c.block, 0, st>>>(c, t, P, probs, ctl);
-    else k_collide<double><<<c.grid, c.block, 0, st>>>(c, t, P, probs, ctl);
+    if (f32) k_collide<float, EIG><<<c.grid, c.block, 0, st>>>(c, t, P, probs, ctl);
+    else k_collide<double, EIG><<<c.grid, c.block, 0, st>>>(c, t, P, probs, ctl);
     ++k;
     k_bookkeep<<<1, 1, 0, st>>>(ctl);
     ++k;
     if (cudaGetLastError() != cudaSuccess) return -1;
     return k;
+}
+
+// Kernels of one iteration; eigenvalue generations use the instantiations
+// that bank fission sites, fixed-source runs the ones without that code.
+int launch_iteration(const LoopConfig& c, const Tables& t, const Particles& P,
+                     const ProblemDev* probs, const int64_t* work_off, RunCtl* ctl,
+                     cudaStream_t st)
+{
+    return c.eigen ? launch_iteration_t<true>(c, t, P, probs, work_off, ctl, st)
+                   : launch_iteration_t<false>(c, t, P, probs, work_off, ctl, st);
 }
 
 // Philox uniforms of one history stream (test hook).

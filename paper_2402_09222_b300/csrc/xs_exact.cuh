@@ -34,16 +34,18 @@ __device__ __forceinline__ double interp_exact(double s0, double s1, double f)
 // running sums C_i of Sigma_t are stored to cum[0..n-1] (the collision picks
 // its species from them).  Two species are evaluated at a time so their load
 // chains overlap; their terms are still added one after the other, in species
-// order, so every sum is the sequential FP64 value.
-template <typename T>
+// order, so every sum is the sequential FP64 value.  With NF the nu-fission
+// sum nuSigma_f = sum_i N_i nu sigma_f,i is formed the same way.
+template <typename T, bool NF = false>
 __device__ __forceinline__ void macro_transport(const Tables& t, int32_t m, double E,
-                                                double& sig_t, double& sig_a, double* cum)
+                                                double& sig_t, double& sig_a, double* cum,
+                                                double* sig_nf = nullptr)
 {
     const int64_t eb = search_key(E);
     const int32_t hb = t.H > 0 ? hash_bin(t, E, eb) : 0;
     const int32_t i0 = __ldg(t.moff + m), i1 = __ldg(t.moff + m + 1);
-    const int nc = t.n_ch, cs = t.ch_scatter, ca = t.ch_absorb;
-    double st = 0.0, sa = 0.0;
+    const int nc = t.n_ch, cs = t.ch_scatter, ca = t.ch_absorb, cf = t.ch_nu_fission;
+    double st = 0.0, sa = 0.0, nf = 0.0;
     for (int32_t i = i0; i < i1; i += 2) {
         int32_t base[2], len[2];
         double N[2];
@@ -57,7 +59,7 @@ __device__ __forceinline__ void macro_transport(const Tables& t, int32_t m, doub
             search_step(t.E, base[0], len[0], eb);
             search_step(t.E, base[1], len[1], eb);
         }
-        double c[2], a[2];
+        double c[2], a[2], v[2] = {0.0, 0.0};
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
             const int64_t p = base[u];
@@ -68,18 +70,24 @@ __device__ __forceinline__ void macro_transport(const Tables& t, int32_t m, doub
                                             sig_at<T>(t.sigma, (p + 1) * nc + ca), f);
             c[u] = N[u] * (ss + sai);
             a[u] = N[u] * sai;
+            if (NF)
+                v[u] = N[u] * interp_exact(sig_at<T>(t.sigma, p * nc + cf),
+                                           sig_at<T>(t.sigma, (p + 1) * nc + cf), f);
         }
         st = st + c[0];
         sa = sa + a[0];
+        if (NF) nf = nf + v[0];
         cum[i - i0] = st;
         if (i + 1 < i1) {
             st = st + c[1];
             sa = sa + a[1];
+            if (NF) nf = nf + v[1];
             cum[i + 1 - i0] = st;
         }
     }
     sig_t = st;
     sig_a = sa;
+    if (NF) *sig_nf = nf;
 }
 
 }  // namespace mcx

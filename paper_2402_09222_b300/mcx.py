@@ -89,6 +89,10 @@ _sig("mcx_read_tallies", C.c_int, _vp, _i32, _vp, _i64)
 _sig("mcx_zero_tallies", C.c_int, _vp)
 _sig("mcx_read_history_debug", C.c_int, _vp, _vp, _i64)
 _sig("mcx_last_run_stats", C.c_int, _vp, _vp, _i32)
+_sig("mcx_run_eigenvalue", C.c_int, _vp, _i64, _i32, _i32, C.c_double, C.c_double, _i64, C.c_uint64,
+     _vp, _vp)
+_sig("mcx_fission_bank_size", C.c_int, _vp, C.POINTER(_i64))
+_sig("mcx_read_fission_bank", C.c_int, _vp, _vp, _i64)
 _sig("mcx_xs_lookup", C.c_int, _vp, _i64, _vp, _vp, _vp, _i32, _vp)
 _sig("mcx_xs_sort", C.c_int, _vp, _i64, _vp, _vp, _vp, _vp)
 _sig("mcx_xs_lookup_ordered", C.c_int, _vp, _i64, _vp, _vp, _vp, _vp, _i32, _vp)
@@ -281,6 +285,25 @@ class Problem:
         _check(_lib.mcx_last_run_stats(self.h, _np_ptr(out), 6))
         return dict(iterations=int(out[0]), graph_launches=int(out[1]), kernels=int(out[2]),
                     selected=dict(lookup=int(out[3]), flight=int(out[4]), collision=int(out[5])))
+
+    def run_eigenvalue(self, n_per_gen: int, n_generations: int, n_inactive: int, k0: float = 1.0,
+                       particles_in_flight: int = 1_000_000, seed: int = 1, stream=None) -> dict:
+        """k-eigenvalue power iteration (see mcx_run_eigenvalue): per generation
+        k (site count), k_col, k_tl and the number of banked sites."""
+        gen = np.zeros((n_generations, 4))
+        T = self.prob.T_fission if self.prob is not None else 1.2895e6
+        _check(_lib.mcx_run_eigenvalue(self.h, n_per_gen, n_generations, n_inactive, float(k0), float(T),
+                                       particles_in_flight, seed, _np_ptr(gen), _stream_ptr(stream)))
+        return dict(k=gen[:, 0].copy(), k_col=gen[:, 1].copy(), k_tl=gen[:, 2].copy(),
+                    sites=gen[:, 3].astype(np.int64))
+
+    def fission_bank(self) -> np.ndarray:
+        """The last generation's ordered bank, rows (x, y, z, ci, cj, inpin)."""
+        n = _i64()
+        _check(_lib.mcx_fission_bank_size(self.h, C.byref(n)))
+        rows = np.zeros((n.value, 6))
+        _check(_lib.mcx_read_fission_bank(self.h, _np_ptr(rows), n.value))
+        return rows
 
     # -- lookups (device tensors)
     def xs_lookup(self, E, mat, out=None, flags: int = LOOKUP_EXACT, stream=None):
