@@ -263,6 +263,32 @@ def time_infinite_medium(mcx, synth, n_hist=10_000_000, seed=3):
     return res
 
 
+def time_eigenvalue(mcx, synth, n=1_000_000, gens=12, inactive=2, seed=11):
+    """k-eigenvalue power iteration of the 17x17 lattice (fuel species
+    fissile): 1e6 histories per generation, 12 generations (2 inactive),
+    FP32 tables and the tuned transport settings."""
+    import torch
+    prob = synth.eigen_problem(n_per_gen=n)
+    p = mcx.make_problem(prob, precision=1, hash_bins=TRANSPORT_TUNED["hash_bins"])
+    p.set_tuning(**TRANSPORT_TUNED["tune"])
+    p.run_eigenvalue(n // 10, 2, 1, particles_in_flight=TRANSPORT_TUNED["pif"], seed=seed)   # warm-up
+    p.zero_tallies()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    r = p.run_eigenvalue(n, gens, inactive, particles_in_flight=TRANSPORT_TUNED["pif"], seed=seed)
+    s = time.perf_counter() - t0        # synchronous call: the host clock brackets the device work
+    p.close()
+    act = slice(inactive, None)
+    se = lambda a: float(a[act].std(ddof=1) / np.sqrt(len(a[act])))
+    return {"config": "17x17 lattice, fuel species fissile (nu = 2.43), Maxwellian T = 1.2895 MeV, "
+                      f"{n:.0e} histories x {gens} generations ({inactive} inactive), FP32 tables",
+            "particles_per_s": n * gens / s, "s": s,
+            "k": {"site_count": float(r["k"][act].mean()), "se": se(r["k"]),
+                  "collision": float(r["k_col"][act].mean()), "collision_se": se(r["k_col"]),
+                  "track_length": float(r["k_tl"][act].mean()), "track_length_se": se(r["k_tl"])},
+            "sites_per_generation": [int(x) for x in r["sites"]]}
+
+
 def time_batched(mcx, synth, seed=9):
     """64 lattices of uneven size (3x3 .. 17x17, 1e4 .. 2e6 histories) over the
     12-material set: one event loop over all problems (tuned) against one
@@ -461,6 +487,7 @@ def main():
             "tuned_fullest_queue": time_transport(mcx, synth, lib3, TRANSPORT_FULLEST, seed=5),
         }
         line["infinite_medium"] = time_infinite_medium(mcx, synth)
+        line["eigenvalue"] = time_eigenvalue(mcx, synth)
         line["large_library"] = time_large_library(mcx, synth, dE, dm, mat, out, perm, stream)
         line["batched"] = time_batched(mcx, synth)
         line["cpu_baseline"] = cpu_baseline(lib, mats, E, mat)
