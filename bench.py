@@ -335,6 +335,7 @@ def time_batched(mcx, synth, seed=9):
 
 
 def main():
+    global N_LOOKUPS, WORKLOAD
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
@@ -342,7 +343,12 @@ def main():
     ap.add_argument("--impl", default="mcx", choices=["mcx", "reference"])
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the plain form, e2e, transport and CPU legs (profiling runs)")
+    ap.add_argument("--lookups", type=int, default=N_LOOKUPS,
+                    help="lookups per step (smaller cases for profiler captures)")
     args = ap.parse_args()
+    if args.lookups != N_LOOKUPS:
+        N_LOOKUPS = args.lookups
+        WORKLOAD = WORKLOAD.replace("1e8 lookups", f"{N_LOOKUPS:.3g} lookups")
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     local = int(os.environ.get("LOCAL_RANK", 0))
@@ -413,7 +419,7 @@ def main():
     if os.path.exists(tpath):
         tr = json.load(open(tpath))
         if (tr.get("kernel_source_hash") == kernel_source_hash()
-                and tr.get("hash_bins") == TUNED["hash_bins"]):
+                and tr.get("hash_bins") == TUNED["hash_bins"] and N_LOOKUPS == 100_000_000):
             roofline["traffic"] = tr["dram_bytes_per_launch"]
 
     # the same kernel on the natural (unbinned) order, where every species'
