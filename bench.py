@@ -334,6 +334,18 @@ def time_batched(mcx, synth, seed=9):
     return res
 
 
+def run_leg(args):
+    """One transport or eigenvalue leg alone (tuned settings), one JSON line."""
+    global TRANSPORT_HIST
+    from paper_2402_09222_b300 import mcx, synth
+    TRANSPORT_HIST = args.histories
+    if args.workload == "transport":
+        r = time_transport(mcx, synth, synth.config3_library(), TRANSPORT_TUNED, seed=5)
+    else:
+        r = time_eigenvalue(mcx, synth, n=args.histories)
+    print(json.dumps({"workload": args.workload, **r}), flush=True)
+
+
 def main():
     global N_LOOKUPS, WORKLOAD
     ap = argparse.ArgumentParser()
@@ -345,6 +357,10 @@ def main():
                     help="skip the plain form, e2e, transport and CPU legs (profiling runs)")
     ap.add_argument("--lookups", type=int, default=N_LOOKUPS,
                     help="lookups per step (smaller cases for profiler captures)")
+    ap.add_argument("--workload", default="lookup", choices=["lookup", "transport", "eigenvalue"],
+                    help="transport / eigenvalue: time only that leg (profiler captures)")
+    ap.add_argument("--histories", type=int, default=TRANSPORT_HIST,
+                    help="histories of the transport leg")
     args = ap.parse_args()
     if args.lookups != N_LOOKUPS:
         N_LOOKUPS = args.lookups
@@ -354,6 +370,8 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", 0))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.workload != "lookup":
+        return run_leg(args)
 
     import torch
     import torch.distributed as dist

@@ -93,6 +93,7 @@ struct TableStore {
     Tables view;
     int64_t* goff = nullptr;
     double* E = nullptr;
+    double* winv = nullptr;   // per interval 1 / (g[k+1] - g[k]) (transport)
     float4* frec = nullptr;
     void* sigma = nullptr;
     double* awr = nullptr;
@@ -113,6 +114,7 @@ struct TableStore {
     {
         dev_free(goff);
         dev_free(E);
+        dev_free(winv);
         dev_free(frec);
         if (sigma) cudaFree(sigma);
         dev_free(awr);
@@ -1004,7 +1006,13 @@ int mcx_load_xs_tables(mcx_problem* p, int32_t n_species, const int64_t* goff, c
         r[1] = (float)(energies[i] - (double)hi);
         for (int c = 0; c < n_ch; ++c) r[2 + c] = (float)sigma[i * n_ch + c];
     }
+    // reciprocal interval widths for the transport lookup's fraction (0 after
+    // a species' last point, which never starts an interval)
+    std::vector<double> winv((size_t)P, 0.0);
+    for (int32_t s2 = 0; s2 < n_species; ++s2)
+        for (int64_t k = goff[s2]; k + 1 < goff[s2 + 1]; ++k) winv[k] = 1.0 / (energies[k + 1] - energies[k]);
     if ((rc = dev_alloc(&ts->goff, (size_t)n_species + 1)) || (rc = dev_alloc(&ts->E, (size_t)P)) ||
+        (rc = dev_alloc(&ts->winv, (size_t)P)) ||
         (rc = dev_alloc(&ts->frec, (size_t)P * frec_w)) ||
         (rc = dev_alloc(&ts->awr, (size_t)n_species)) || (rc = dev_alloc(&ts->moff, (size_t)n_materials + 1)) ||
         (rc = dev_alloc(&ts->msp, (size_t)nnz)) || (rc = dev_alloc(&ts->mden, (size_t)nnz)) ||
@@ -1017,6 +1025,7 @@ int mcx_load_xs_tables(mcx_problem* p, int32_t n_species, const int64_t* goff, c
     }
     bool ok = cudaMemcpy(ts->goff, goff, 8 * (n_species + 1), cudaMemcpyHostToDevice) == cudaSuccess &&
               cudaMemcpy(ts->E, energies, 8 * P, cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaMemcpy(ts->winv, winv.data(), 8 * P, cudaMemcpyHostToDevice) == cudaSuccess &&
               cudaMemcpy(ts->frec, rec.data(), sizeof(float) * rec.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
               cudaMemcpy(ts->awr, awr, 8 * n_species, cudaMemcpyHostToDevice) == cudaSuccess &&
               cudaMemcpy(ts->moff, moff, 4 * (n_materials + 1), cudaMemcpyHostToDevice) == cudaSuccess &&
@@ -1045,6 +1054,7 @@ int mcx_load_xs_tables(mcx_problem* p, int32_t n_species, const int64_t* goff, c
     v.n_points = P;
     v.goff = ts->goff;
     v.E = ts->E;
+    v.winv = ts->winv;
     v.frec = ts->frec;
     v.frec_w = frec_w;
     v.sigma = ts->sigma;

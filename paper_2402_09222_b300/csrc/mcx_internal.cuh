@@ -45,6 +45,7 @@ struct Tables {
     int64_t n_points = 0;
     const int64_t* goff = nullptr;
     const double* E = nullptr;
+    const double* winv = nullptr;   // per interval 1 / (g[k+1] - g[k])
     const float4* frec = nullptr;   // fast-path point records, frec_w float4 each
     int32_t frec_w = 0;
     const void* sigma = nullptr;

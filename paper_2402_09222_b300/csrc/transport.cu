@@ -841,9 +841,9 @@ __global__ void __launch_bounds__(1024) k_collide(LoopConfig c, Tables t, Partic
             {
                 const int64_t k = species_index(t, j, eb, hb);
                 const int64_t p = __ldg(t.goff + j) + k;
-                const double f = fraction_exact(E, __ldg(t.E + p), __ldg(t.E + p + 1));
-                ss_j = interp_exact(sig_at<T>(t.sigma, p * nc + cs), sig_at<T>(t.sigma, (p + 1) * nc + cs), f);
-                sa_j = interp_exact(sig_at<T>(t.sigma, p * nc + ca), sig_at<T>(t.sigma, (p + 1) * nc + ca), f);
+                const double f = fraction_transport(t, E, p);
+                ss_j = interp_transport(sig_at<T>(t.sigma, p * nc + cs), sig_at<T>(t.sigma, (p + 1) * nc + cs), f);
+                sa_j = interp_transport(sig_at<T>(t.sigma, p * nc + ca), sig_at<T>(t.sigma, (p + 1) * nc + ca), f);
             }
             const double st_j = ss_j + sa_j;
             uint8_t fl = (uint8_t)(P.flags[slot] & ~PF_COLLIDE);
