@@ -94,6 +94,8 @@ struct ProblemDev {
     int32_t M;           // materials with derivative tallies (0 = off)
     double pitch, radius, height, slab_length, half, E0, E_cut;
     const int32_t* region_material;
+    const double* lat_plane;   // lattice: x (and y) of cell plane i = -half + pitch i, i = 0..n
+    const double* lat_centre;  // lattice: centre of cell i = -half + pitch (i + 1/2)
     const double* ebin_edges;
     uint2 key;            // Philox key (seed, problem id)
     int64_t n_hist_total; // defines batches

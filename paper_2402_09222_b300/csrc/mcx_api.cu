@@ -149,6 +149,7 @@ struct mcx_problem {
     mcx_tune tune{};
     // device copies of the description
     int32_t* d_region_material = nullptr;
+    double* d_lattice = nullptr;   // lattice plane and centre coordinates (2 n + 1)
     double* d_ebin_edges = nullptr;
     // tallies
     double* flux = nullptr;
@@ -458,6 +459,8 @@ ProblemDev make_problem_dev(mcx_problem* p, uint64_t seed, int64_t first, bool d
     d.E0 = s.E0;
     d.E_cut = s.E_cut;
     d.region_material = p->d_region_material;
+    d.lat_plane = p->d_lattice;
+    d.lat_centre = p->d_lattice ? p->d_lattice + d.lattice_n + 1 : nullptr;
     d.ebin_edges = p->d_ebin_edges;
     d.key = rng_key(seed, s.problem_id);
     d.n_hist_total = s.n_histories;
@@ -851,6 +854,20 @@ int mcx_init_problem(const mcx_problem_desc* desc, mcx_problem** out)
         if (cudaMemcpy(p->d_region_material, p->region_material.data(),
                        sizeof(int32_t) * p->region_material.size(), cudaMemcpyHostToDevice) != cudaSuccess)
             return bail(fail(MCX_ERR_CUDA, "copying region materials failed"));
+        if (desc->geometry == MCX_GEOM_LATTICE) {
+            // cell planes -half + pitch i (i = 0..n) and centres
+            // -half + pitch (i + 0.5), the FP64 expressions the kernels
+            // would otherwise evaluate every flight (same values, bit for bit)
+            const int32_t n = desc->lattice_n;
+            const double half = 0.5 * (double)n * desc->pitch;
+            std::vector<double> lat((size_t)2 * n + 1);
+            for (int32_t i = 0; i <= n; ++i) lat[i] = -half + desc->pitch * (double)i;
+            for (int32_t i = 0; i < n; ++i) lat[n + 1 + i] = -half + desc->pitch * ((double)i + 0.5);
+            if ((rc = dev_alloc(&p->d_lattice, lat.size())) != MCX_OK) return bail(rc);
+            if (cudaMemcpy(p->d_lattice, lat.data(), sizeof(double) * lat.size(), cudaMemcpyHostToDevice) !=
+                cudaSuccess)
+                return bail(fail(MCX_ERR_CUDA, "copying lattice coordinates failed"));
+        }
         if (!p->ebin_edges.empty()) {
             if ((rc = dev_alloc(&p->d_ebin_edges, p->ebin_edges.size())) != MCX_OK) return bail(rc);
             if (cudaMemcpy(p->d_ebin_edges, p->ebin_edges.data(), sizeof(double) * p->ebin_edges.size(),
@@ -884,6 +901,7 @@ void mcx_destroy(mcx_problem* p)
     release_tables(p);
     free_particles(p);
     dev_free(p->d_region_material);
+    dev_free(p->d_lattice);
     dev_free(p->d_ebin_edges);
     dev_free(p->flux);
     dev_free(p->absorb);

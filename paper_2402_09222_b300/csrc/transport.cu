@@ -186,9 +186,8 @@ __device__ double surface_distance(const ProblemDev& pd, const State& q, int& su
         d = (0.0 - q.z) / q.w;
         surf = S_ZBOT;
     }
-    const double half = pd.half;
-    const double cx = -half + pd.pitch * ((double)q.ci + 0.5);
-    const double cy = -half + pd.pitch * ((double)q.cj + 0.5);
+    const double cx = __ldg(pd.lat_centre + q.ci);
+    const double cy = __ldg(pd.lat_centre + q.cj);
     const double dx = q.x - cx, dy = q.y - cy;
     const double a = q.u * q.u + q.v * q.v;
     const double k = dx * q.u + dy * q.v;
@@ -209,10 +208,10 @@ __device__ double surface_distance(const ProblemDev& pd, const State& q, int& su
         surf = S_CYL;
     }
     if (!q.inpin) {
-        const double xl = -half + pd.pitch * (double)q.ci;
-        const double xh = -half + pd.pitch * (double)(q.ci + 1);
-        const double yl = -half + pd.pitch * (double)q.cj;
-        const double yh = -half + pd.pitch * (double)(q.cj + 1);
+        const double xl = __ldg(pd.lat_plane + q.ci);
+        const double xh = __ldg(pd.lat_plane + q.ci + 1);
+        const double yl = __ldg(pd.lat_plane + q.cj);
+        const double yh = __ldg(pd.lat_plane + q.cj + 1);
         if (q.u > 0.0) {
             const double t = (xh - q.x) / q.u;
             if (t < d) { d = t; surf = S_XHI; }
@@ -346,8 +345,8 @@ __device__ void init_particle(const Particles& P, int64_t slot, const ProblemDev
             if (pin >= n2) pin = n2 - 1;
             q.ci = (int32_t)(pin / ln);
             q.cj = (int32_t)(pin % ln);
-            q.x = -pd.half + pd.pitch * ((double)q.ci + 0.5);
-            q.y = -pd.half + pd.pitch * ((double)q.cj + 0.5);
+            q.x = __ldg(pd.lat_centre + q.ci);
+            q.y = __ldg(pd.lat_centre + q.cj);
             q.z = 0.5 * pd.height;
             q.inpin = 1;
         }
