@@ -133,16 +133,97 @@ def algorithmic_bytes(mats, mat, sigma_bytes: int, n_ch: int = 5) -> float:
     return species_visits * (16 + 2 * n_ch * sigma_bytes) + len(mat) * (8 + 4 + 8 * n_ch)
 
 
-def cpu_baseline(lib, mats, E, mat, n_sample: int = 8_000_000):
+def cpu_baseline(lib, mats, E, mat, n_sample: int = 8_000_000, n_single: int = 200_000):
     import oracle
     cores = os.cpu_count() or 1
     oracle.xs_lookup(lib, mats, E[:1000], mat[:1000], n_threads=cores)   # warm
     t0 = time.perf_counter()
     oracle.xs_lookup(lib, mats, E[:n_sample], mat[:n_sample], n_threads=cores)
     dt = time.perf_counter() - t0
+    t1 = time.perf_counter()
+    oracle.xs_lookup(lib, mats, E[:n_single], mat[:n_single], n_threads=1)
+    d1 = time.perf_counter() - t1
     return {"value": n_sample / dt, "unit": "lookups/s", "cores": cores, "kind": "oracle",
             "sample": f"first {n_sample:,} lookups of the step's batch, FP64 tables, "
-                      f"full binary search, OpenMP over lookups on {cores} host cores ({dt:.1f} s)"}
+                      f"full binary search, OpenMP over lookups on {cores} host cores ({dt:.1f} s)",
+            "single_thread": {"value": n_single / d1, "unit": "lookups/s",
+                              "sample": f"first {n_single:,} lookups, 1 thread ({d1:.1f} s)"}}
+
+
+def cpu_transport(synth, lib3, n_sample: int = 200_000):
+    """The oracle's lattice transport on all host cores (a bounded sample of
+    the 1e7-history workload)."""
+    import oracle
+    cores = os.cpu_count() or 1
+    prob = synth.config3_problem(n_histories=TRANSPORT_HIST, lib=lib3)
+    t0 = time.perf_counter()
+    oracle.transport(prob, seed=5, first=0, count=n_sample, n_threads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": n_sample / dt, "unit": "particles/s", "cores": cores, "kind": "oracle",
+            "sample": f"first {n_sample:,} histories of the 17x17 lattice, FP64, "
+                      f"OpenMP over histories ({dt:.1f} s)"}
+
+
+def time_inflight_sweep(mcx, synth, lib3, seed=5):
+    """Particles/s of the tuned lattice transport against the number of
+    particles in flight (the paper's P1 range, 1e5 to 8e6)."""
+    import torch
+    prob = synth.config3_problem(n_histories=TRANSPORT_HIST, lib=lib3)
+    p = mcx.make_problem(prob, precision=1, hash_bins=TRANSPORT_TUNED["hash_bins"])
+    p.set_tuning(**TRANSPORT_TUNED["tune"])
+    out = {}
+    for pif in (100_000, 250_000, 500_000, 1_000_000, 2_000_000, 4_000_000, 8_000_000):
+        p.run(count=TRANSPORT_HIST // 20, particles_in_flight=pif, seed=seed)   # warm-up
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        p.run(particles_in_flight=pif, seed=seed)
+        b.record()
+        torch.cuda.synchronize()
+        out[str(pif)] = TRANSPORT_HIST / (a.elapsed_time(b) / 1e3)
+    p.close()
+    return {"unit": "particles/s", "histories": TRANSPORT_HIST, "by_particles_in_flight": out}
+
+
+def time_derivatives(mcx, synth, lib3, n=2_000_000, seed=13, n_lookups=10_000_000):
+    """Overhead of the likelihood-ratio derivative tallies (3 material
+    density scales) on the lattice, and the lookup's backward pass into the
+    FP32 sigma tables."""
+    import torch
+    prob = synth.config3_problem(n_histories=n, lib=lib3)
+    res = {}
+    for name, flags in (("plain", 0), ("derivatives", mcx.FLAG_DERIVATIVES)):
+        p = mcx.make_problem(prob, precision=1, hash_bins=TRANSPORT_TUNED["hash_bins"], flags=flags)
+        p.set_tuning(**TRANSPORT_TUNED["tune"])
+        p.run(count=n // 10, particles_in_flight=TRANSPORT_TUNED["pif"], seed=seed)
+        p.zero_tallies()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        p.run(particles_in_flight=TRANSPORT_TUNED["pif"], seed=seed)
+        b.record()
+        torch.cuda.synchronize()
+        res[name] = n / (a.elapsed_time(b) / 1e3)
+        p.close()
+    lib = synth.species_library(N_SPECIES, N_POINTS, LIB_SEED)
+    mats = synth.lookup_materials(N_SPECIES, MAT_SEED)
+    E, mat = synth.lookup_inputs(n_lookups, mats.n_materials, INPUT_SEED)
+    q = mcx.Problem(None).load_tables(lib, mats, precision=1, hash_bins=TUNED["hash_bins"])
+    dE = torch.as_tensor(E, device="cuda")
+    dm = torch.as_tensor(mat, device="cuda")
+    g = torch.ones((n_lookups, 5), dtype=torch.float64, device="cuda")
+    gd, gs = q.xs_lookup_backward(dE, dm, g)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    q.xs_lookup_backward(dE, dm, g, gd, gs)
+    b.record()
+    torch.cuda.synchronize()
+    q.close()
+    return {"unit": "particles/s", "histories": n, "plain": res["plain"],
+            "with_derivative_tallies": res["derivatives"],
+            "overhead": res["plain"] / res["derivatives"] - 1.0,
+            "lookup_backward": {"lookups_per_s": n_lookups / (a.elapsed_time(b) / 1e3),
+                                "form": "natural order, FP64 atomics into dsigma and ddensity"}}
 
 
 def run_reference(args, rank: int, world: int):
@@ -510,6 +591,9 @@ def main():
             # the same settings with the fullest-queue policy decided on the device
             "tuned_fullest_queue": time_transport(mcx, synth, lib3, TRANSPORT_FULLEST, seed=5),
         }
+        line["transport"]["cpu_baseline"] = cpu_transport(synth, lib3)
+        line["transport"]["inflight_sweep"] = time_inflight_sweep(mcx, synth, lib3)
+        line["derivatives"] = time_derivatives(mcx, synth, lib3)
         line["infinite_medium"] = time_infinite_medium(mcx, synth)
         line["eigenvalue"] = time_eigenvalue(mcx, synth)
         line["large_library"] = time_large_library(mcx, synth, dE, dm, mat, out, perm, stream)
