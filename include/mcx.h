@@ -66,6 +66,9 @@ extern "C" {
 #define MCX_LOOKUP_EXACT 0 /* FP64 arithmetic, bit-identical to the plain definition */
 #define MCX_LOOKUP_FAST 1  /* FP32 interpolation weights, compensated sums (<= 1e-6 rel) */
 #define MCX_LOOKUP_SORT 2  /* bin lookups by (material, log-energy) before the gather */
+#define MCX_LOOKUP_STAGED 4 /* with FAST and a binned order: stage each chunk's grid
+                               points in shared memory by TMA bulk copies (same
+                               results, bit for bit) */
 
 /* Problem flags. */
 #define MCX_FLAG_DERIVATIVES 1   /* likelihood-ratio density-derivative tallies */
@@ -258,6 +261,12 @@ int mcx_run_eigenvalue(mcx_problem* p, int64_t n_per_gen, int32_t n_generations,
                        double k0, double T_fission, int64_t particles_in_flight, uint64_t seed,
                        double* gen_out, void* stream);
 
+/* Waits for `stream` and reports whether a staged lookup (MCX_LOOKUP_STAGED)
+ * on this handle gave up on its shared-memory pipeline since the last check
+ * (a bounded wait ran out; never expected): MCX_ERR_TIMEOUT, and the flag is
+ * cleared; MCX_OK otherwise.  Host-synchronous. */
+int mcx_check_device(mcx_problem* p, void* stream);
+
 /* The last eigenvalue generation's ordered bank: its size, and its first n
  * sites as HOST rows {x, y, z, ci, cj, inpin} (n <= size).  Synchronous. */
 int mcx_fission_bank_size(const mcx_problem* p, int64_t* n);
@@ -312,7 +321,9 @@ int mcx_xs_sort(mcx_problem* p, int64_t n, const double* E, const int32_t* mat, 
 /* mcx_xs_lookup processing the lookups in the order perm (a permutation of
  * 0..n-1, e.g. from mcx_xs_sort; NULL = natural order).  Results land in each
  * lookup's own row of out, so the order changes no value.  flags may hold
- * MCX_LOOKUP_FAST only.  DEVICE pointers. */
+ * MCX_LOOKUP_FAST and MCX_LOOKUP_STAGED (the latter applies to a binned
+ * perm with MCX_LOOKUP_FAST; mcx_check_device reports a pipeline that gave
+ * up).  DEVICE pointers. */
 int mcx_xs_lookup_ordered(mcx_problem* p, int64_t n, const double* E, const int32_t* mat,
                           const int32_t* perm, double* out, int32_t flags, void* stream);
 

@@ -16,6 +16,18 @@ constexpr int kFastBlocksPerSm = 4;
 int launch_xs_lookup_fast(const Tables& t, int64_t n, const double* E, const int32_t* mat,
                           const int32_t* perm, double* out, int grid, cudaStream_t st,
                           unsigned long long* work = nullptr);
+struct SortParams {
+    int32_t n_materials = 1;
+    int32_t n_ebuckets = 1;
+    float ln_lo = 0.f, scale = 0.f;  // bucket = (ln E - ln_lo) * scale
+};
+
+// The TMA-staged form of the binned fast lookup (perm and work required; err
+// receives 1 if a bounded wait ran out).  Returns -2 when a material is too
+// large for a stage (use launch_xs_lookup_fast), -1 on a launch error.
+int launch_xs_lookup_staged(const Tables& t, const SortParams& sp, int64_t n, const double* E,
+                            const int32_t* mat, const int32_t* perm, double* out, int sm_count, cudaStream_t st,
+                            unsigned long long* work, unsigned int* err);
 int launch_xs_indices(const Tables& t, int64_t n, const double* E, const int32_t* mat,
                       int32_t max_species, int32_t* kout, int grid, cudaStream_t st);
 int launch_build_hash(const Tables& t, int32_t* hidx, int grid, cudaStream_t st);
@@ -33,11 +45,6 @@ int launch_debug_uniforms(uint2 key, uint64_t hist, uint32_t first, int64_t n, d
 // Counting sort of lookups by key = material * n_ebuckets + log-energy bucket.
 // Scratch: bins [n_materials * n_ebuckets + 1] uint32.  perm receives the
 // lookup indices in bin order.
-struct SortParams {
-    int32_t n_materials = 1;
-    int32_t n_ebuckets = 1;
-    float ln_lo = 0.f, scale = 0.f;  // bucket = (ln E - ln_lo) * scale
-};
 int launch_lookup_sort(const SortParams& sp, int64_t n, const double* E, const int32_t* mat,
                        uint32_t* bins, int32_t* perm, int grid, cudaStream_t st);
 

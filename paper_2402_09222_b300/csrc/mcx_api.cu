@@ -721,13 +721,22 @@ int lookup_device_ordered(mcx_problem* p, int64_t n, const double* E, const int3
     const TableStore* ts = p->tables;
     unsigned long long* work = nullptr;
     if (perm && (flags & MCX_LOOKUP_FAST)) {
-        if (!p->work_ctr) TRY(dev_alloc(&p->work_ctr, 2));
+        if (!p->work_ctr) {
+            TRY(dev_alloc(&p->work_ctr, 3));   // two chunk counters and the staged kernel's error word
+            CUDA_TRY(cudaMemset(p->work_ctr, 0, 3 * sizeof(unsigned long long)));
+        }
         work = p->work_ctr + ctr;
     }
-    const int grid = work ? p->sm_count * kFastBlocksPerSm : lookup_grid(p);
-    int r = (flags & MCX_LOOKUP_FAST)
-                ? launch_xs_lookup_fast(ts->view, n, E, mat, perm, out, grid, st, work)
-                : launch_xs_lookup_exact(ts->view, n, E, mat, perm, out, lookup_grid(p), st);
+    int r = -2;
+    if (work && (flags & MCX_LOOKUP_STAGED))
+        r = launch_xs_lookup_staged(ts->view, lookup_sort_params(ts), n, E, mat, perm, out,
+                                    p->sm_count, st, work,
+                                    reinterpret_cast<unsigned int*>(p->work_ctr + 2));
+    if (r == -2) {
+        const int grid = work ? p->sm_count * kFastBlocksPerSm : lookup_grid(p);
+        r = (flags & MCX_LOOKUP_FAST) ? launch_xs_lookup_fast(ts->view, n, E, mat, perm, out, grid, st, work)
+                                      : launch_xs_lookup_exact(ts->view, n, E, mat, perm, out, lookup_grid(p), st);
+    }
     if (r) return fail(MCX_ERR_CUDA, "lookup launch failed: %s", cudaGetErrorString(cudaGetLastError()));
     return MCX_OK;
 }
@@ -742,7 +751,7 @@ int lookup_device(mcx_problem* p, int64_t n, const double* E, const int32_t* mat
         TRY(sort_device(p, n, E, mat, p->perm, st));
         perm = p->perm;
     }
-    return lookup_device_ordered(p, n, E, mat, perm, out, flags & MCX_LOOKUP_FAST, st);
+    return lookup_device_ordered(p, n, E, mat, perm, out, flags & (MCX_LOOKUP_FAST | MCX_LOOKUP_STAGED), st);
 }
 
 // Eigenvalue scratch: per-history arrays for N histories and a staging and
@@ -1029,7 +1038,9 @@ int mcx_load_xs_tables(mcx_problem* p, int32_t n_species, const int64_t* goff, c
     std::vector<double> winv((size_t)P, 0.0);
     for (int32_t s2 = 0; s2 < n_species; ++s2)
         for (int64_t k = goff[s2]; k + 1 < goff[s2 + 1]; ++k) winv[k] = 1.0 / (energies[k + 1] - energies[k]);
-    if ((rc = dev_alloc(&ts->goff, (size_t)n_species + 1)) || (rc = dev_alloc(&ts->E, (size_t)P)) ||
+    // two padding entries past the last energy: the staged lookup copies FP64
+    // energies in 16-byte pairs and may read one entry past a species' end
+    if ((rc = dev_alloc(&ts->goff, (size_t)n_species + 1)) || (rc = dev_alloc(&ts->E, (size_t)P + 2)) ||
         (rc = dev_alloc(&ts->winv, (size_t)P)) ||
         (rc = dev_alloc(&ts->frec, (size_t)P * frec_w)) ||
         (rc = dev_alloc(&ts->awr, (size_t)n_species)) || (rc = dev_alloc(&ts->moff, (size_t)n_materials + 1)) ||
@@ -1043,6 +1054,7 @@ int mcx_load_xs_tables(mcx_problem* p, int32_t n_species, const int64_t* goff, c
     }
     bool ok = cudaMemcpy(ts->goff, goff, 8 * (n_species + 1), cudaMemcpyHostToDevice) == cudaSuccess &&
               cudaMemcpy(ts->E, energies, 8 * P, cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaMemset(ts->E + P, 0x7f, 16) == cudaSuccess &&
               cudaMemcpy(ts->winv, winv.data(), 8 * P, cudaMemcpyHostToDevice) == cudaSuccess &&
               cudaMemcpy(ts->frec, rec.data(), sizeof(float) * rec.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
               cudaMemcpy(ts->awr, awr, 8 * n_species, cudaMemcpyHostToDevice) == cudaSuccess &&
@@ -1315,7 +1327,7 @@ int mcx_xs_lookup(mcx_problem* p, int64_t n, const double* E, const int32_t* mat
     TRY(check_tables(p));
     if (n < 0) return fail(MCX_ERR_ARG, "n must be >= 0");
     if (n >= ((int64_t)1 << 31)) return fail(MCX_ERR_ARG, "n must be < 2^31");
-    if (flags & ~(MCX_LOOKUP_FAST | MCX_LOOKUP_SORT)) return fail(MCX_ERR_ARG, "unknown lookup flags");
+    if (flags & ~(MCX_LOOKUP_FAST | MCX_LOOKUP_SORT | MCX_LOOKUP_STAGED)) return fail(MCX_ERR_ARG, "unknown lookup flags");
     if (n == 0) return MCX_OK;
     if (!E || !mat || !out) return fail(MCX_ERR_ARG, "NULL buffer");
     DeviceGuard dg(p->device);
@@ -1340,7 +1352,7 @@ int mcx_xs_lookup_ordered(mcx_problem* p, int64_t n, const double* E, const int3
     g_err.clear();
     TRY(check_tables(p));
     if (n < 0 || n >= ((int64_t)1 << 31)) return fail(MCX_ERR_ARG, "n out of range");
-    if (flags & ~MCX_LOOKUP_FAST) return fail(MCX_ERR_ARG, "flags may hold MCX_LOOKUP_FAST only");
+    if (flags & ~(MCX_LOOKUP_FAST | MCX_LOOKUP_STAGED)) return fail(MCX_ERR_ARG, "flags may hold MCX_LOOKUP_FAST and MCX_LOOKUP_STAGED only");
     if (n == 0) return MCX_OK;
     if (!E || !mat || !out) return fail(MCX_ERR_ARG, "NULL buffer");
     DeviceGuard dg(p->device);
@@ -1353,7 +1365,7 @@ int mcx_xs_lookup_host(mcx_problem* p, int64_t n, const double* E_host, const in
     g_err.clear();
     TRY(check_tables(p));
     if (n < 0 || n >= ((int64_t)1 << 31)) return fail(MCX_ERR_ARG, "n out of range");
-    if (flags & ~(MCX_LOOKUP_FAST | MCX_LOOKUP_SORT)) return fail(MCX_ERR_ARG, "unknown lookup flags");
+    if (flags & ~(MCX_LOOKUP_FAST | MCX_LOOKUP_SORT | MCX_LOOKUP_STAGED)) return fail(MCX_ERR_ARG, "unknown lookup flags");
     if (n == 0) return MCX_OK;
     if (!E_host || !mat_host || !out_host) return fail(MCX_ERR_ARG, "NULL buffer");
     DeviceGuard dg(p->device);
@@ -1388,11 +1400,13 @@ int mcx_xs_lookup_host(mcx_problem* p, int64_t n, const double* E_host, const in
                 return fail(MCX_ERR_CUDA, "lookup sort launch failed");
             perm = dP;
         }
-        TRY(lookup_device_ordered(p, m, dE, dM, perm, dO, flags & MCX_LOOKUP_FAST, st, (int)(c & 1)));
+        TRY(lookup_device_ordered(p, m, dE, dM, perm, dO, flags & (MCX_LOOKUP_FAST | MCX_LOOKUP_STAGED), st,
+                                  (int)(c & 1)));
         CUDA_TRY(cudaMemcpyAsync(out_host + off * nc, dO, 8 * m * nc, cudaMemcpyDeviceToHost, st));
     }
     CUDA_TRY(cudaStreamSynchronize(ss[0]));
     CUDA_TRY(cudaStreamSynchronize(ss[1]));
+    if (flags & MCX_LOOKUP_STAGED) return mcx_check_device(p, nullptr);
     return MCX_OK;
 }
 
@@ -1532,6 +1546,20 @@ int mcx_run_eigenvalue(mcx_problem* p, int64_t n_per_gen, int32_t n_generations,
     }
     CUDA_TRY(cudaStreamSynchronize(st));
     return MCX_OK;
+}
+
+int mcx_check_device(mcx_problem* p, void* stream)
+{
+    g_err.clear();
+    TRY(check_handle(p));
+    if (!p->work_ctr) return MCX_OK;
+    DeviceGuard dg(p->device);
+    unsigned long long w = 0ull;
+    CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    CUDA_TRY(cudaMemcpy(&w, p->work_ctr + 2, sizeof(w), cudaMemcpyDeviceToHost));
+    if (w == 0ull) return MCX_OK;
+    CUDA_TRY(cudaMemset(p->work_ctr + 2, 0, sizeof(w)));
+    return fail(MCX_ERR_TIMEOUT, "a staged lookup kernel gave up waiting on its pipeline");
 }
 
 int mcx_fission_bank_size(const mcx_problem* p, int64_t* n)

@@ -114,6 +114,32 @@ __device__ __forceinline__ void store_out(double* p, double v)
 #endif
 }
 
+// One species' weighted terms added into part[]: the bracketing records r0
+// (point k) and r1 (point k + 1), the lookup energy as the FP32 pair
+// (E_hi, E_lo) and the FP32 density N.  Shared by every form of the fast
+// lookup, so they agree bit for bit.
+template <int W, int NC>
+__device__ __forceinline__ void species_term(const float (&r0)[4 * W], const float (&r1)[4 * W], float E_hi,
+                                             float E_lo, float N, float (&part)[NC])
+{
+    const float a = fmaxf((E_hi - r0[0]) + (E_lo - r0[1]), 0.f);
+    const float b = fmaxf((r1[0] - E_hi) + (r1[1] - E_lo), 0.f);
+#if MCX_FAST_FDIV
+    const float nw = __fdividef(N, a + b);   // <= 2 ulp: within the budget above
+#else
+    const float nw = N * __frcp_rn(a + b);
+#endif
+    const float w1 = nw * a, w0 = nw * b;
+#pragma unroll
+    for (int r = 0; r < NC; ++r) {
+#if MCX_FAST_FMA2
+        part[r] = fmaf(w1, r1[2 + r], fmaf(w0, r0[2 + r], part[r]));
+#else
+        part[r] += fmaf(w0, r0[2 + r], w1 * r1[2 + r]);
+#endif
+    }
+}
+
 template <int W, int U, int NC>
 __device__ __forceinline__ void lookup_one(const Tables& t, int64_t j, const double* __restrict__ Ein,
                                            const int32_t* __restrict__ mat,
@@ -178,22 +204,7 @@ __device__ __forceinline__ void lookup_one(const Tables& t, int64_t j, const dou
         for (int u = 0; u < U; ++u) {
             float r0[4 * W], r1[4 * W];
             load_records<W>(t.frec, base[u], r0, r1);
-            const float a = fmaxf((E_hi - r0[0]) + (E_lo - r0[1]), 0.f);
-            const float b = fmaxf((r1[0] - E_hi) + (r1[1] - E_lo), 0.f);
-#if MCX_FAST_FDIV
-            const float nw = __fdividef(N[u], a + b);   // <= 2 ulp: within the budget above
-#else
-            const float nw = N[u] * __frcp_rn(a + b);
-#endif
-            const float w1 = nw * a, w0 = nw * b;
-#pragma unroll
-            for (int r = 0; r < NCMAX; ++r) {
-#if MCX_FAST_FMA2
-                part[r] = fmaf(w1, r1[2 + r], fmaf(w0, r0[2 + r], part[r]));
-#else
-                part[r] += fmaf(w0, r0[2 + r], w1 * r1[2 + r]);
-#endif
-            }
+            species_term<W, NC>(r0, r1, E_hi, E_lo, N[u], part);
         }
 #pragma unroll
         for (int r = 0; r < NCMAX; ++r) two_sum_acc(hi[r], lo[r], part[r]);
@@ -237,8 +248,8 @@ __global__ void __launch_bounds__(256, MCX_FAST_MIN_BLOCKS) k_xs_lookup_fast(Tab
     }
 }
 
-constexpr unsigned FULL = 0xffffffffu;
 
+// Bin key of a lookup: material major, then the log-energy bucket.
 __device__ __forceinline__ int lookup_key(const SortParams& sp, double E, int32_t m)
 {
     const float fb = (logf((float)E) - sp.ln_lo) * sp.scale;
@@ -247,6 +258,375 @@ __device__ __forceinline__ int lookup_key(const SortParams& sp, double E, int32_
     if (m < 0 || m >= sp.n_materials) m = 0;
     return m * sp.n_ebuckets + b;
 }
+
+// ------------------------------------------------------------------------
+// Staged binned lookup: a producer warp stages the records each chunk needs
+// into shared memory with TMA bulk copies, eight consumer warps compute.
+//
+// The binned order puts 256 consecutive lookups in one material and a narrow
+// slice of energy, so for each species of that material they need only the
+// few grid points between the slice's lowest and highest energy.  Per chunk
+// the producer reads the bin keys of the chunk's first and last lookup (the
+// order is sorted by key, so they bound the chunk: one material, buckets
+// b0..b1), widens the buckets' energy edges by a relative 1e-4 (the float
+// logarithm of the bin key is within a few ulps), takes per species the
+// union of the hash-grid windows over that energy range, and issues one
+// cp.async.bulk for those point records into a shared-memory stage, arming
+// the stage's mbarrier with the byte count.  A consumer whose own lookup is
+// not in the chunk's material or energy range (or is invalid) takes the
+// global-memory form for it.  One stage per block: while one block's producer
+// stages, the SM's other blocks compute.
+// Consumers wait on the mbarrier, search each species' few staged points and
+// evaluate the same per-species terms as the global-memory form, in the same
+// order, so the two agree bit for bit.  The search compares the energies'
+// FP32 pairs (hi, lo) from the records: rounding to nearest is monotone, so
+// hi (and on a tie of hi, lo) decides g <= E exactly whenever they differ;
+// when both parts tie, the FP64 energy is read from global memory.  Two stages alternate: the producer fills one
+// while the consumers work on the other.  A chunk that spans two materials,
+// holds an invalid lookup or needs more points than a stage holds is done by
+// the consumers with the global-memory form instead.
+//
+// Every wait is bounded in time; a wait that runs out sets *err, and the
+// producer waits (again bounded) for its copies in flight before returning.
+// ------------------------------------------------------------------------
+constexpr int kStChunk = 256;                 // lookups per chunk (one per consumer thread)
+constexpr int kStConsumerWarps = kStChunk / 32;
+constexpr int kStThreads = 32 * (1 + kStConsumerWarps);
+constexpr int kStMaxSpecies = 384;            // material entries a stage can describe
+constexpr int kStMaxPoints = 1536;            // staged grid points (records) per stage
+constexpr long long kStWaitCycles = 4000000000LL;   // ~2 s at 2 GHz
+// Stages per block and blocks per SM (the blocks of an SM also overlap one
+// another's staging and computing).  Measured per 1e8 binned lookups: 1
+// stage x 3 blocks 33.7 ms, 2 x 2 34.2 ms, 1 x 2 43.9 ms, 3 x 1 53.0 ms --
+// all slower than the global-memory form (28.4 ms), whose L1 already holds
+// most records; the producer alone needs 12.2 ms, the consumers are the
+// bound.  The staged form is kept as an option (MCX_LOOKUP_STAGED).
+#ifndef MCX_STAGED_STAGES
+#define MCX_STAGED_STAGES 1
+#endif
+#ifndef MCX_STAGED_BLOCKS
+#define MCX_STAGED_BLOCKS 3
+#endif
+constexpr int kStStages = MCX_STAGED_STAGES;
+
+enum { ST_NORMAL = 0, ST_FALLBACK = 1, ST_END = 2 };
+
+struct StageInfo {
+    long long base;   // first position of the chunk in the binned order
+    int mode;
+    int n_entries;    // species entries of the chunk's material
+    int material;
+    int pad;
+    double E_min, E_max;   // every lookup staged for lies in [E_min, E_max]
+};
+
+template <int W>
+struct StageLayout {
+    static constexpr size_t kMeta = 0;                                     // int4 [kStMaxSpecies]
+    static constexpr size_t kRec = kMeta + sizeof(int4) * kStMaxSpecies;   // float4 [kStMaxPoints * W]
+    static constexpr size_t kInfo = kRec + sizeof(float4) * kStMaxPoints * W;   // StageInfo
+    static constexpr size_t kBytes = (kInfo + sizeof(StageInfo) + 127) / 128 * 128;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
+{
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0u;
+}
+
+// Wait for the phase of `parity` to complete, for at most kStWaitCycles.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > kStWaitCycles) return false;
+    return true;
+}
+
+// 1-D bulk copy global -> shared, completing on `bar` (both addresses 16-byte
+// aligned, bytes a multiple of 16).
+__device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ int warp_excl_scan(int v, int& total)
+{
+    const int lane = threadIdx.x & 31;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    total = __shfl_sync(0xffffffffu, x, 31);
+    return x - v;
+}
+
+// Producer: fill a stage with chunk `base` (the binned positions base ..
+// base + kStChunk - 1).  Returns the bytes the stage's copies will deliver
+// (0: nothing issued).
+template <int W>
+__device__ int producer_fill(const Tables& t, const SortParams& sp, int64_t n, const double* __restrict__ Ein,
+                             const int32_t* __restrict__ mat, const int32_t* __restrict__ perm, long long base,
+                             unsigned char* stage, uint64_t* full)
+{
+    using LY = StageLayout<W>;
+    const int lane = threadIdx.x & 31;
+    int4* meta = reinterpret_cast<int4*>(stage + LY::kMeta);
+    float4* rec = reinterpret_cast<float4*>(stage + LY::kRec);
+    StageInfo* info = reinterpret_cast<StageInfo*>(stage + LY::kInfo);
+    // bin keys of the chunk's first and last lookup (lanes 0 and 1)
+    int key = 0;
+    if (lane < 2) {
+        const int64_t j = lane == 0 ? (int64_t)base : ((int64_t)base + kStChunk - 1 < n ? (int64_t)base + kStChunk - 1 : n - 1);
+        const int32_t l = __ldg(perm + j);
+        key = lookup_key(sp, __ldg(Ein + l), __ldg(mat + l));
+    }
+    const int k0 = __shfl_sync(0xffffffffu, key, 0), k1 = __shfl_sync(0xffffffffu, key, 1);
+    const int m = k0 / sp.n_ebuckets, b0 = k0 % sp.n_ebuckets, b1 = k1 % sp.n_ebuckets;
+    int mode = (k1 / sp.n_ebuckets != m || b1 < b0 || t.H == 0) ? ST_FALLBACK : ST_NORMAL;
+    // the buckets' energy range, widened by a relative 1e-4
+    const double E_min = b0 == 0 ? 0.0 : exp((double)sp.ln_lo + (double)b0 / (double)sp.scale) * (1.0 - 1e-4);
+    const double E_max = b1 == sp.n_ebuckets - 1 ? __longlong_as_double(0x7ff0000000000000LL)
+                                                 : exp((double)sp.ln_lo + (double)(b1 + 1) / (double)sp.scale) * (1.0 + 1e-4);
+    int ne = 0, rec_total = 0;
+    if (mode == ST_NORMAL) {
+        const int32_t i0 = __ldg(t.moff + m);
+        ne = __ldg(t.moff + m + 1) - i0;
+        if (ne > kStMaxSpecies) mode = ST_FALLBACK;
+        const int64_t H1 = (int64_t)t.H + 1;
+        const int32_t hb_min = hash_bin(t, E_min, search_key(E_min));
+        const int32_t hb_max = hash_bin(t, E_max, search_key(E_max));
+        for (int q0 = 0; mode == ST_NORMAL && q0 < ne; q0 += 32) {
+            const int q = q0 + lane;
+            int L = 0, gp = 0, dens = 0;
+            if (q < ne) {
+                // every energy of bins hb_min..hb_max has its grid index in
+                // [hidx[hb_min], hidx[hb_max + 1]]
+                const int4 e = __ldg(t.ment + i0 + q);
+                const int32_t* h = t.hidx + (int64_t)e.z * H1;
+                const int32_t k_lo = __ldg(h + hb_min), k_hi = __ldg(h + hb_max + 1);
+                gp = e.x + k_lo;
+                L = k_hi - k_lo + 2;
+                dens = e.w;
+            }
+            int rsum;
+            const int roff = warp_excl_scan(L, rsum);
+            if (q < ne) meta[q] = make_int4(rec_total + roff, gp, L, dens);
+            rec_total += rsum;
+            if (rec_total > kStMaxPoints) mode = ST_FALLBACK;
+        }
+    }
+    int bytes = 0;
+    if (mode == ST_NORMAL) {
+        bytes = rec_total * W * 16;
+        if (lane == 0) mbar_expect_tx(full, (uint32_t)bytes);
+        __syncwarp();
+        for (int q = lane; q < ne; q += 32) {
+            const int4 md = meta[q];
+            tma_load_1d(rec + (size_t)md.x * W, t.frec + (int64_t)md.y * W, (uint32_t)(md.z * W * 16), full);
+        }
+        __syncwarp();
+    }
+    if (lane == 0) {
+        info->base = base;
+        info->mode = mode;
+        info->n_entries = ne;
+        info->material = m;
+        info->E_min = E_min;
+        info->E_max = E_max;
+    }
+    __syncwarp();
+    return bytes;
+}
+
+// g <= E for the grid energy g of a staged record (FP32 pair rec.x, rec.y)
+// and the lookup energy E (pair E_hi, E_lo, key eb); exact (see above).
+__device__ __forceinline__ bool staged_le(float g_hi, float g_lo, float E_hi, float E_lo, int64_t eb,
+                                          const double* __restrict__ g_exact)
+{
+    if (g_hi != E_hi) return g_hi < E_hi;
+    if (g_lo != E_lo) return g_lo < E_lo;
+    return ebits(__ldg(g_exact)) <= eb;
+}
+
+// Consumer: lookup `l` (energy E) of a staged chunk.
+template <int W, int U, int NC>
+__device__ __forceinline__ void consume_one(const Tables& t, const unsigned char* stage, int ne, int32_t l,
+                                            double E, double* __restrict__ out)
+{
+    using LY = StageLayout<W>;
+    const int4* meta = reinterpret_cast<const int4*>(stage + LY::kMeta);
+    const float4* rec = reinterpret_cast<const float4*>(stage + LY::kRec);
+    float hi[NC], lo[NC];
+#pragma unroll
+    for (int r = 0; r < NC; ++r) hi[r] = lo[r] = 0.f;
+    const float E_hi = (float)E;
+    const float E_lo = (float)(E - (double)E_hi);
+    const int64_t eb = search_key(E);
+    for (int i = 0; i < ne; i += U) {
+        float part[NC];
+#pragma unroll
+        for (int r = 0; r < NC; ++r) part[r] = 0.f;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int ii = i + u < ne ? i + u : ne - 1;
+            const int4 md = meta[ii];
+            const float N = i + u < ne ? __int_as_float(md.w) : 0.f;
+            // largest q in [0, L-2] with staged energy q <= E (0 if none)
+            int q = 0;
+            for (int qq = 1; qq <= md.z - 2; ++qq) {
+                const float4 g = rec[(size_t)(md.x + qq) * W];
+                if (staged_le(g.x, g.y, E_hi, E_lo, eb, t.E + md.y + qq)) q = qq;
+                else break;
+            }
+            float r0[4 * W], r1[4 * W];
+            const float4* p = rec + (size_t)(md.x + q) * W;
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                const float4 a = p[w], b = p[W + w];
+                r0[4 * w] = a.x; r0[4 * w + 1] = a.y; r0[4 * w + 2] = a.z; r0[4 * w + 3] = a.w;
+                r1[4 * w] = b.x; r1[4 * w + 1] = b.y; r1[4 * w + 2] = b.z; r1[4 * w + 3] = b.w;
+            }
+            species_term<W, NC>(r0, r1, E_hi, E_lo, N, part);
+        }
+#pragma unroll
+        for (int r = 0; r < NC; ++r) two_sum_acc(hi[r], lo[r], part[r]);
+    }
+#pragma unroll
+    for (int r = 0; r < NC; ++r) store_out(out + (int64_t)l * NC + r, (double)hi[r] + (double)lo[r]);
+}
+
+template <int W, int U, int NC>
+__global__ void __launch_bounds__(kStThreads, MCX_STAGED_BLOCKS) k_xs_lookup_staged(Tables t, SortParams sp, int64_t n,
+                                                                    const double* __restrict__ Ein,
+                                                                    const int32_t* __restrict__ mat,
+                                                                    const int32_t* __restrict__ perm,
+                                                                    double* __restrict__ out,
+                                                                    unsigned long long* __restrict__ work,
+                                                                    unsigned int* __restrict__ err)
+{
+    using LY = StageLayout<W>;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t full[kStStages], empty[kStStages];
+    // stages start on a 128-byte boundary (the launch adds 128 bytes of slack)
+    unsigned char* smem = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], kStConsumerWarps);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (warp == 0) {
+        // ---- producer
+        bool issued[kStStages];
+        uint32_t issued_parity[kStStages];
+        for (int s = 0; s < kStStages; ++s) {
+            issued[s] = false;
+            issued_parity[s] = 0u;
+        }
+        bool failed = false;
+        for (int k = 0;; ++k) {
+            const int s = k % kStStages, use = k / kStStages;
+            if (use > 0) {
+                if (!mbar_wait(&empty[s], (uint32_t)((use - 1) & 1))) {
+                    failed = true;
+                    break;
+                }
+                issued[s] = false;   // the consumers waited for those copies before releasing
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            unsigned long long b = 0ull;
+            if (lane == 0) b = atomicAdd(work, (unsigned long long)kStChunk);
+            b = __shfl_sync(0xffffffffu, b, 0);
+            unsigned char* stage = smem + (size_t)s * LY::kBytes;
+            if ((int64_t)b >= n) {
+                if (lane == 0) {
+                    reinterpret_cast<StageInfo*>(stage + LY::kInfo)->mode = ST_END;
+                    mbar_arrive(&full[s]);
+                }
+                break;
+            }
+            const int bytes = producer_fill<W>(t, sp, n, Ein, mat, perm, (long long)b, stage, &full[s]);
+            if (bytes > 0) {
+                issued[s] = true;
+                issued_parity[s] = (uint32_t)(use & 1);
+            }
+            if (lane == 0) mbar_arrive(&full[s]);
+        }
+        if (failed && lane == 0) atomicExch(err, 1u);
+        // copies still in flight land before this block may exit (no later
+        // phase of a slot with copies was started, so its parity is current)
+        for (int s = 0; s < kStStages; ++s)
+            if (issued[s] && !mbar_wait(&full[s], issued_parity[s]) && lane == 0) atomicExch(err, 1u);
+        return;
+    }
+    // ---- consumers
+    const int c = threadIdx.x - 32;
+    for (int k = 0;; ++k) {
+        const int s = k % kStStages, use = k / kStStages;
+        if (!mbar_wait(&full[s], (uint32_t)(use & 1))) {
+            if (lane == 0) atomicExch(err, 1u);
+            break;
+        }
+        const unsigned char* stage = smem + (size_t)s * LY::kBytes;
+        const StageInfo info = *reinterpret_cast<const StageInfo*>(stage + LY::kInfo);
+        if (info.mode == ST_END) break;
+        const int64_t j = info.base + c;
+        if (j < n) {
+            const int32_t l = load_in(perm + j);
+            const double E = load_in(Ein + l);
+            const int32_t m = load_in(mat + l);
+            // E >= E_min && E <= E_max is false for a NaN energy
+            if (info.mode == ST_NORMAL && m == info.material && E >= info.E_min && E <= info.E_max)
+                consume_one<W, U, NC>(t, stage, info.n_entries, l, E, out);
+            else
+                lookup_one<W, U, NC>(t, j, Ein, mat, perm, out);
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);
+    }
+}
+
+constexpr unsigned FULL = 0xffffffffu;
+
 
 __global__ void k_lookup_sort_count(SortParams sp, int64_t n, const double* __restrict__ E,
                                     const int32_t* __restrict__ mat, uint32_t* __restrict__ bins)
@@ -346,6 +726,37 @@ int launch_xs_lookup_fast(const Tables& t, int64_t n, const double* E, const int
     default: return -1;
     }
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+template <int W, int NC>
+static int launch_staged_nc(const Tables& t, const SortParams& sp, int64_t n, const double* E, const int32_t* mat,
+                            const int32_t* perm, double* out, int grid, cudaStream_t st, unsigned long long* work,
+                            unsigned int* err)
+{
+    const size_t smem = kStStages * StageLayout<W>::kBytes + 128;
+    if (cudaFuncSetAttribute(k_xs_lookup_staged<W, kFastUnroll, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+        return -1;
+    k_xs_lookup_staged<W, kFastUnroll, NC><<<grid, kStThreads, smem, st>>>(t, sp, n, E, mat, perm, out, work, err);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int launch_xs_lookup_staged(const Tables& t, const SortParams& sp, int64_t n, const double* E,
+                            const int32_t* mat, const int32_t* perm, double* out, int sm_count, cudaStream_t st,
+                            unsigned long long* work, unsigned int* err)
+{
+    const int grid = sm_count * MCX_STAGED_BLOCKS;
+    if (!perm || !work || !err) return -1;
+    if (t.max_mat_species > kStMaxSpecies || t.H == 0) return -2;   // the caller uses the global-memory form
+    if (cudaMemsetAsync(work, 0, sizeof(unsigned long long), st) != cudaSuccess) return -1;
+    switch (t.n_ch) {
+    case 1: return launch_staged_nc<1, 1>(t, sp, n, E, mat, perm, out, grid, st, work, err);
+    case 2: return launch_staged_nc<1, 2>(t, sp, n, E, mat, perm, out, grid, st, work, err);
+    case 3: return launch_staged_nc<2, 3>(t, sp, n, E, mat, perm, out, grid, st, work, err);
+    case 4: return launch_staged_nc<2, 4>(t, sp, n, E, mat, perm, out, grid, st, work, err);
+    case 5: return launch_staged_nc<2, 5>(t, sp, n, E, mat, perm, out, grid, st, work, err);
+    default: return -1;
+    }
 }
 
 int launch_lookup_sort(const SortParams& sp, int64_t n, const double* E, const int32_t* mat,

@@ -23,7 +23,7 @@ ERR_NAMES = {-1: "MCX_ERR_ARG", -2: "MCX_ERR_CUDA", -3: "MCX_ERR_OOM", -4: "MCX_
 ERR_ITER_LIMIT, ERR_TIMEOUT = -4, -7
 FP64, FP32 = 0, 1
 QUEUELESS, QUEUED, QUEUED_FULLEST = 0, 1, 2
-LOOKUP_EXACT, LOOKUP_FAST, LOOKUP_SORT = 0, 1, 2
+LOOKUP_EXACT, LOOKUP_FAST, LOOKUP_SORT, LOOKUP_STAGED = 0, 1, 2, 4
 FLAG_DERIVATIVES, FLAG_HISTORY_DEBUG = 1, 2
 TALLY_FLUX, TALLY_ABSORB, TALLY_OUTCOME, TALLY_DFLUX, TALLY_DABSORB, TALLY_DOUTCOME = range(6)
 GEOM_NONE = 3
@@ -92,6 +92,7 @@ _sig("mcx_last_run_stats", C.c_int, _vp, _vp, _i32)
 _sig("mcx_run_eigenvalue", C.c_int, _vp, _i64, _i32, _i32, C.c_double, C.c_double, _i64, C.c_uint64,
      _vp, _vp)
 _sig("mcx_fission_bank_size", C.c_int, _vp, C.POINTER(_i64))
+_sig("mcx_check_device", C.c_int, _vp, _vp)
 _sig("mcx_read_fission_bank", C.c_int, _vp, _vp, _i64)
 _sig("mcx_xs_lookup", C.c_int, _vp, _i64, _vp, _vp, _vp, _i32, _vp)
 _sig("mcx_xs_sort", C.c_int, _vp, _i64, _vp, _vp, _vp, _vp)
@@ -296,6 +297,11 @@ class Problem:
                                        particles_in_flight, seed, _np_ptr(gen), _stream_ptr(stream)))
         return dict(k=gen[:, 0].copy(), k_col=gen[:, 1].copy(), k_tl=gen[:, 2].copy(),
                     sites=gen[:, 3].astype(np.int64))
+
+    def check_device(self, stream=None):
+        """Raise if a staged lookup on this handle gave up on its pipeline."""
+        _check(_lib.mcx_check_device(self.h, _stream_ptr(stream)))
+        return self
 
     def fission_bank(self) -> np.ndarray:
         """The last generation's ordered bank, rows (x, y, z, ci, cj, inpin)."""

@@ -242,3 +242,59 @@ def test_zero_and_subnormal_table_entries(torch_cuda):
     p = _handle(lib, mats, mcx.FP32, 300)
     out = p.xs_lookup(_dev(torch, E, torch.float64), _dev(torch, mat, torch.int32)).cpu().numpy()
     assert np.array_equal(out.view(np.uint64), ref.view(np.uint64))
+
+
+@pytest.mark.parametrize("n_ch,H", [(5, 68_400), (5, 0), (2, 4000), (3, 100)])
+def test_staged_lookup_matches_the_direct_form_bit_for_bit(torch_cuda, n_ch, H):
+    """The TMA-staged binned lookup evaluates the same per-species terms in the
+    same order as the global-memory form: identical outputs, on a binned order
+    with chunks that span materials, a ragged tail, NaN energies and invalid
+    materials (those chunks take the global-memory form), exact grid points
+    and energies outside the grid."""
+    from paper_2402_09222_b300 import mcx
+    torch = torch_cuda
+    chans = {5: None, 2: [synth.CH_SCATTER, synth.CH_ABSORB],
+             3: [synth.CH_SCATTER, synth.CH_ABSORB, synth.CH_NU_FISSION]}[n_ch]
+    lib = synth.species_library(120, 3000, 111)
+    if chans:
+        lib = lib.channels(chans)
+    mats = synth.lookup_materials(120, 112, n_materials=9)
+    E, mat = synth.lookup_inputs(300_017, mats.n_materials, 113)
+    rng = np.random.default_rng(114)
+    E[:500] = lib.energies[rng.integers(0, len(lib.energies), 500)]
+    E[500:510] = [1e-7, 1e-6, 9.99e-6, 1e-5, 2e7, 2.0000001e7, 3e7, 1e9, 5e-6, 1e-5]
+    E[600] = np.nan
+    mat[700] = -1
+    mat[701] = mats.n_materials
+    p = _handle(lib, mats, mcx.FP32, H)
+    dE, dm = _dev(torch, E, torch.float64), _dev(torch, mat, torch.int32)
+    perm = p.xs_sort(dE, dm)
+    direct = p.xs_lookup_ordered(dE, dm, perm, flags=mcx.LOOKUP_FAST).cpu().numpy()
+    staged = p.xs_lookup_ordered(dE, dm, perm, flags=mcx.LOOKUP_FAST | mcx.LOOKUP_STAGED).cpu().numpy()
+    p.check_device()
+    assert np.array_equal(staged.view(np.uint64), direct.view(np.uint64))
+    # and against the definition on the FP32-rounded tables
+    ok = np.isfinite(E) & (mat >= 0) & (mat < mats.n_materials)
+    ref = oracle.xs_lookup(lib.fp32_rounded(), mats, E[ok], mat[ok], n_threads=8)
+    rel = np.abs(staged[ok] - ref) / np.maximum(np.abs(ref), 1e-300)
+    assert rel.max() <= FAST_RTOL
+    assert np.all(np.isnan(staged[~ok]))
+    p.close()
+
+
+def test_staged_lookup_on_the_benchmark_tables(torch_cuda):
+    """355 species x 11,303 points, materials up to 321 species, 4e6 binned
+    lookups: staged and direct forms agree bit for bit."""
+    from paper_2402_09222_b300 import mcx
+    torch = torch_cuda
+    lib = synth.species_library(355, 11_303, 1236)
+    mats = synth.lookup_materials(355, 1236)
+    E, mat = synth.lookup_inputs(4_000_000, mats.n_materials, 1336)
+    p = _handle(lib, mats, mcx.FP32, 68_400)
+    dE, dm = _dev(torch, E, torch.float64), _dev(torch, mat, torch.int32)
+    perm = p.xs_sort(dE, dm)
+    direct = p.xs_lookup_ordered(dE, dm, perm, flags=mcx.LOOKUP_FAST)
+    staged = p.xs_lookup_ordered(dE, dm, perm, flags=mcx.LOOKUP_FAST | mcx.LOOKUP_STAGED)
+    p.check_device()
+    assert torch.equal(direct.view(torch.int64), staged.view(torch.int64))
+    p.close()
