@@ -69,6 +69,9 @@ extern "C" {
 #define MCX_LOOKUP_STAGED 4 /* with FAST and a binned order: stage each chunk's grid
                                points in shared memory by TMA bulk copies (same
                                results, bit for bit) */
+#define MCX_LOOKUP_OUT32 8  /* with FAST: out holds FP32 values (the compensated
+                               sum rounded once; still within 1e-6 relative),
+                               half the output bytes */
 
 /* Problem flags. */
 #define MCX_FLAG_DERIVATIVES 1   /* likelihood-ratio density-derivative tallies */
@@ -298,14 +301,15 @@ int mcx_last_run_stats(const mcx_problem* p, int64_t* out, int32_t n);
  * grid interval [g[k], g[k+1]] with k the largest index in [0, n-2] such
  * that g[k] <= E (k = 0 below the grid, n-2 at or above its top; the
  * fraction is clamped to [0, 1]).  E (FP64 [n]), mat (int32 [n]) and out
- * (FP64 [n][n_ch], row-major) are DEVICE pointers.  flags: MCX_LOOKUP_EXACT
+ * (FP64 [n][n_ch], row-major; FP32 with MCX_LOOKUP_OUT32) are DEVICE
+ * pointers.  flags: MCX_LOOKUP_EXACT
  * gives the plain definition's FP64 result bit for bit (species in stored
  * order, sums from +0.0, no fused multiply-add); MCX_LOOKUP_FAST stays within
  * 1e-6 relative of it; MCX_LOOKUP_SORT first bins the lookups by material and
  * log-energy (results unchanged; uses library-owned scratch memory sized for
  * n).  A material id out of range gives NaN outputs for that lookup.
  * Errors: MCX_ERR_ARG, MCX_ERR_STATE, MCX_ERR_CUDA, MCX_ERR_OOM. */
-int mcx_xs_lookup(mcx_problem* p, int64_t n, const double* E, const int32_t* mat, double* out,
+int mcx_xs_lookup(mcx_problem* p, int64_t n, const double* E, const int32_t* mat, void* out,
                   int32_t flags, void* stream);
 
 /* Binning of lookups by material and energy (Sec. 5.1: sorting so that
@@ -321,11 +325,11 @@ int mcx_xs_sort(mcx_problem* p, int64_t n, const double* E, const int32_t* mat, 
 /* mcx_xs_lookup processing the lookups in the order perm (a permutation of
  * 0..n-1, e.g. from mcx_xs_sort; NULL = natural order).  Results land in each
  * lookup's own row of out, so the order changes no value.  flags may hold
- * MCX_LOOKUP_FAST and MCX_LOOKUP_STAGED (the latter applies to a binned
- * perm with MCX_LOOKUP_FAST; mcx_check_device reports a pipeline that gave
- * up).  DEVICE pointers. */
+ * MCX_LOOKUP_FAST, MCX_LOOKUP_STAGED (applies to a binned perm with
+ * MCX_LOOKUP_FAST; mcx_check_device reports a pipeline that gave up) and
+ * MCX_LOOKUP_OUT32.  DEVICE pointers. */
 int mcx_xs_lookup_ordered(mcx_problem* p, int64_t n, const double* E, const int32_t* mat,
-                          const int32_t* perm, double* out, int32_t flags, void* stream);
+                          const int32_t* perm, void* out, int32_t flags, void* stream);
 
 /* The binned lookup (mcx_xs_lookup with MCX_LOOKUP_SORT) for callers that
  * cannot allocate device memory -- for example a process whose device memory
@@ -353,10 +357,12 @@ int mcx_xs_lookup_binned_static(mcx_problem* p, int64_t n, const double* E, cons
 
 /* The same lookup from HOST buffers: copies in, computes and copies out in
  * chunks of up to 8M lookups pipelined over two streams (with MCX_LOOKUP_SORT
- * each chunk is binned on the device); synchronous.  Host buffers should be
- * pinned (cudaHostAlloc / torch pin_memory) for full copy speed. */
+ * each chunk is binned on the device); synchronous.  out_host is FP64
+ * [n][n_ch], or FP32 with MCX_LOOKUP_OUT32 (half the device-to-host bytes,
+ * which bound this path).  Host buffers should be pinned (cudaHostAlloc /
+ * torch pin_memory) for full copy speed. */
 int mcx_xs_lookup_host(mcx_problem* p, int64_t n, const double* E_host, const int32_t* mat_host,
-                       double* out_host, int32_t flags);
+                       void* out_host, int32_t flags);
 
 /* Grid indices used by the lookup, for parity tests: kout[l * max_species +
  * i] = k of the i-th species of material mat[l], -1 past its species count.

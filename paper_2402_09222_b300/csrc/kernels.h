@@ -14,7 +14,7 @@ constexpr int kFastBlocksPerSm = 4;
 // work: a device counter for in-order chunked scheduling of binned orders
 // (zeroed by the launch), or nullptr for a grid-stride loop.
 int launch_xs_lookup_fast(const Tables& t, int64_t n, const double* E, const int32_t* mat,
-                          const int32_t* perm, double* out, int grid, cudaStream_t st,
+                          const int32_t* perm, void* out, bool out32, int grid, cudaStream_t st,
                           unsigned long long* work = nullptr);
 struct SortParams {
     int32_t n_materials = 1;
@@ -26,8 +26,8 @@ struct SortParams {
 // receives 1 if a bounded wait ran out).  Returns -2 when a material is too
 // large for a stage (use launch_xs_lookup_fast), -1 on a launch error.
 int launch_xs_lookup_staged(const Tables& t, const SortParams& sp, int64_t n, const double* E,
-                            const int32_t* mat, const int32_t* perm, double* out, int sm_count, cudaStream_t st,
-                            unsigned long long* work, unsigned int* err);
+                            const int32_t* mat, const int32_t* perm, void* out, bool out32, int sm_count,
+                            cudaStream_t st, unsigned long long* work, unsigned int* err);
 int launch_xs_indices(const Tables& t, int64_t n, const double* E, const int32_t* mat,
                       int32_t max_species, int32_t* kout, int grid, cudaStream_t st);
 int launch_build_hash(const Tables& t, int32_t* hidx, int grid, cudaStream_t st);

@@ -715,9 +715,10 @@ int sort_device(mcx_problem* p, int64_t n, const double* E, const int32_t* mat, 
 // warps claiming chunks from a counter (slot `ctr` of the problem's two),
 // with one resident grid of blocks.
 int lookup_device_ordered(mcx_problem* p, int64_t n, const double* E, const int32_t* mat,
-                          const int32_t* perm, double* out, int32_t flags, cudaStream_t st,
+                          const int32_t* perm, void* out, int32_t flags, cudaStream_t st,
                           int ctr = 0)
 {
+    const bool out32 = (flags & MCX_LOOKUP_OUT32) != 0;
     const TableStore* ts = p->tables;
     unsigned long long* work = nullptr;
     if (perm && (flags & MCX_LOOKUP_FAST)) {
@@ -729,20 +730,21 @@ int lookup_device_ordered(mcx_problem* p, int64_t n, const double* E, const int3
     }
     int r = -2;
     if (work && (flags & MCX_LOOKUP_STAGED))
-        r = launch_xs_lookup_staged(ts->view, lookup_sort_params(ts), n, E, mat, perm, out,
+        r = launch_xs_lookup_staged(ts->view, lookup_sort_params(ts), n, E, mat, perm, out, out32,
                                     p->sm_count, st, work,
                                     reinterpret_cast<unsigned int*>(p->work_ctr + 2));
     if (r == -2) {
         const int grid = work ? p->sm_count * kFastBlocksPerSm : lookup_grid(p);
-        r = (flags & MCX_LOOKUP_FAST) ? launch_xs_lookup_fast(ts->view, n, E, mat, perm, out, grid, st, work)
-                                      : launch_xs_lookup_exact(ts->view, n, E, mat, perm, out, lookup_grid(p), st);
+        r = (flags & MCX_LOOKUP_FAST)
+                ? launch_xs_lookup_fast(ts->view, n, E, mat, perm, out, out32, grid, st, work)
+                : launch_xs_lookup_exact(ts->view, n, E, mat, perm, static_cast<double*>(out), lookup_grid(p), st);
     }
     if (r) return fail(MCX_ERR_CUDA, "lookup launch failed: %s", cudaGetErrorString(cudaGetLastError()));
     return MCX_OK;
 }
 
 // Lookup on device buffers, queued on `st` (binned first with MCX_LOOKUP_SORT).
-int lookup_device(mcx_problem* p, int64_t n, const double* E, const int32_t* mat, double* out,
+int lookup_device(mcx_problem* p, int64_t n, const double* E, const int32_t* mat, void* out,
                   int32_t flags, cudaStream_t st)
 {
     const int32_t* perm = nullptr;
@@ -751,7 +753,8 @@ int lookup_device(mcx_problem* p, int64_t n, const double* E, const int32_t* mat
         TRY(sort_device(p, n, E, mat, p->perm, st));
         perm = p->perm;
     }
-    return lookup_device_ordered(p, n, E, mat, perm, out, flags & (MCX_LOOKUP_FAST | MCX_LOOKUP_STAGED), st);
+    return lookup_device_ordered(p, n, E, mat, perm, out,
+                                 flags & (MCX_LOOKUP_FAST | MCX_LOOKUP_STAGED | MCX_LOOKUP_OUT32), st);
 }
 
 // Eigenvalue scratch: per-history arrays for N histories and a staging and
@@ -1320,14 +1323,17 @@ int mcx_last_run_stats(const mcx_problem* p, int64_t* out, int32_t n)
     return MCX_OK;
 }
 
-int mcx_xs_lookup(mcx_problem* p, int64_t n, const double* E, const int32_t* mat, double* out,
+int mcx_xs_lookup(mcx_problem* p, int64_t n, const double* E, const int32_t* mat, void* out,
                   int32_t flags, void* stream)
 {
     g_err.clear();
     TRY(check_tables(p));
     if (n < 0) return fail(MCX_ERR_ARG, "n must be >= 0");
     if (n >= ((int64_t)1 << 31)) return fail(MCX_ERR_ARG, "n must be < 2^31");
-    if (flags & ~(MCX_LOOKUP_FAST | MCX_LOOKUP_SORT | MCX_LOOKUP_STAGED)) return fail(MCX_ERR_ARG, "unknown lookup flags");
+    if (flags & ~(MCX_LOOKUP_FAST | MCX_LOOKUP_SORT | MCX_LOOKUP_STAGED | MCX_LOOKUP_OUT32))
+        return fail(MCX_ERR_ARG, "unknown lookup flags");
+    if ((flags & MCX_LOOKUP_OUT32) && !(flags & MCX_LOOKUP_FAST))
+        return fail(MCX_ERR_ARG, "MCX_LOOKUP_OUT32 needs MCX_LOOKUP_FAST");
     if (n == 0) return MCX_OK;
     if (!E || !mat || !out) return fail(MCX_ERR_ARG, "NULL buffer");
     DeviceGuard dg(p->device);
@@ -1347,12 +1353,15 @@ int mcx_xs_sort(mcx_problem* p, int64_t n, const double* E, const int32_t* mat, 
 }
 
 int mcx_xs_lookup_ordered(mcx_problem* p, int64_t n, const double* E, const int32_t* mat,
-                          const int32_t* perm, double* out, int32_t flags, void* stream)
+                          const int32_t* perm, void* out, int32_t flags, void* stream)
 {
     g_err.clear();
     TRY(check_tables(p));
     if (n < 0 || n >= ((int64_t)1 << 31)) return fail(MCX_ERR_ARG, "n out of range");
-    if (flags & ~(MCX_LOOKUP_FAST | MCX_LOOKUP_STAGED)) return fail(MCX_ERR_ARG, "flags may hold MCX_LOOKUP_FAST and MCX_LOOKUP_STAGED only");
+    if (flags & ~(MCX_LOOKUP_FAST | MCX_LOOKUP_STAGED | MCX_LOOKUP_OUT32))
+        return fail(MCX_ERR_ARG, "flags may hold MCX_LOOKUP_FAST, MCX_LOOKUP_STAGED and MCX_LOOKUP_OUT32 only");
+    if ((flags & MCX_LOOKUP_OUT32) && !(flags & MCX_LOOKUP_FAST))
+        return fail(MCX_ERR_ARG, "MCX_LOOKUP_OUT32 needs MCX_LOOKUP_FAST");
     if (n == 0) return MCX_OK;
     if (!E || !mat || !out) return fail(MCX_ERR_ARG, "NULL buffer");
     DeviceGuard dg(p->device);
@@ -1360,14 +1369,18 @@ int mcx_xs_lookup_ordered(mcx_problem* p, int64_t n, const double* E, const int3
 }
 
 int mcx_xs_lookup_host(mcx_problem* p, int64_t n, const double* E_host, const int32_t* mat_host,
-                       double* out_host, int32_t flags)
+                       void* out_host, int32_t flags)
 {
     g_err.clear();
     TRY(check_tables(p));
     if (n < 0 || n >= ((int64_t)1 << 31)) return fail(MCX_ERR_ARG, "n out of range");
-    if (flags & ~(MCX_LOOKUP_FAST | MCX_LOOKUP_SORT | MCX_LOOKUP_STAGED)) return fail(MCX_ERR_ARG, "unknown lookup flags");
+    if (flags & ~(MCX_LOOKUP_FAST | MCX_LOOKUP_SORT | MCX_LOOKUP_STAGED | MCX_LOOKUP_OUT32))
+        return fail(MCX_ERR_ARG, "unknown lookup flags");
+    if ((flags & MCX_LOOKUP_OUT32) && !(flags & MCX_LOOKUP_FAST))
+        return fail(MCX_ERR_ARG, "MCX_LOOKUP_OUT32 needs MCX_LOOKUP_FAST");
     if (n == 0) return MCX_OK;
     if (!E_host || !mat_host || !out_host) return fail(MCX_ERR_ARG, "NULL buffer");
+    const size_t es = (flags & MCX_LOOKUP_OUT32) ? sizeof(float) : sizeof(double);
     DeviceGuard dg(p->device);
     const TableStore* ts = p->tables;
     const int nc = ts->view.n_ch;
@@ -1400,9 +1413,10 @@ int mcx_xs_lookup_host(mcx_problem* p, int64_t n, const double* E_host, const in
                 return fail(MCX_ERR_CUDA, "lookup sort launch failed");
             perm = dP;
         }
-        TRY(lookup_device_ordered(p, m, dE, dM, perm, dO, flags & (MCX_LOOKUP_FAST | MCX_LOOKUP_STAGED), st,
-                                  (int)(c & 1)));
-        CUDA_TRY(cudaMemcpyAsync(out_host + off * nc, dO, 8 * m * nc, cudaMemcpyDeviceToHost, st));
+        TRY(lookup_device_ordered(p, m, dE, dM, perm, dO,
+                                  flags & (MCX_LOOKUP_FAST | MCX_LOOKUP_STAGED | MCX_LOOKUP_OUT32), st, (int)(c & 1)));
+        CUDA_TRY(cudaMemcpyAsync(static_cast<char*>(out_host) + (size_t)off * nc * es, dO, es * m * nc,
+                                 cudaMemcpyDeviceToHost, st));
     }
     CUDA_TRY(cudaStreamSynchronize(ss[0]));
     CUDA_TRY(cudaStreamSynchronize(ss[1]));

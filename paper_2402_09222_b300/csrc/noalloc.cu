@@ -92,7 +92,7 @@ extern "C" int mcx_xs_lookup_binned_static(mcx_problem* p, int64_t n, const doub
         if (mcx::launch_lookup_sort(v.sort, n, E, mat, a.bins, a.perm, v.grid, st))
             rc = mcx::set_error(MCX_ERR_CUDA, "binning launch failed");
         else if ((flags & MCX_LOOKUP_FAST)
-                     ? mcx::launch_xs_lookup_fast(v.tables, n, E, mat, a.perm, out, v.grid, st)
+                     ? mcx::launch_xs_lookup_fast(v.tables, n, E, mat, a.perm, out, false, v.grid, st)
                      : mcx::launch_xs_lookup_exact(v.tables, n, E, mat, a.perm, out, v.grid, st))
             rc = mcx::set_error(MCX_ERR_CUDA, "lookup launch failed");
     }

@@ -105,7 +105,8 @@ __device__ __forceinline__ V load_in(const V* p)
 #endif
 }
 
-__device__ __forceinline__ void store_out(double* p, double v)
+template <typename V>
+__device__ __forceinline__ void store_stream(V* p, V v)
 {
 #if MCX_FAST_STREAM
     __stcs(p, v);
@@ -113,6 +114,13 @@ __device__ __forceinline__ void store_out(double* p, double v)
     *p = v;
 #endif
 }
+
+// An output channel from its compensated pair (hi, lo): the FP64 value
+// hi + lo (exact), or that value rounded once to FP32.
+__device__ __forceinline__ void store_out(double* p, float hi, float lo) { store_stream(p, (double)hi + (double)lo); }
+__device__ __forceinline__ void store_out(float* p, float hi, float lo) { store_stream(p, hi + lo); }
+__device__ __forceinline__ void store_nan(double* p) { store_stream(p, __longlong_as_double(0x7ff8000000000000LL)); }
+__device__ __forceinline__ void store_nan(float* p) { store_stream(p, __int_as_float(0x7fc00000)); }
 
 // One species' weighted terms added into part[]: the bracketing records r0
 // (point k) and r1 (point k + 1), the lookup energy as the FP32 pair
@@ -140,10 +148,10 @@ __device__ __forceinline__ void species_term(const float (&r0)[4 * W], const flo
     }
 }
 
-template <int W, int U, int NC>
+template <int W, int U, int NC, typename OutT>
 __device__ __forceinline__ void lookup_one(const Tables& t, int64_t j, const double* __restrict__ Ein,
                                            const int32_t* __restrict__ mat,
-                                           const int32_t* __restrict__ perm, double* __restrict__ out)
+                                           const int32_t* __restrict__ perm, OutT* __restrict__ out)
 {
     constexpr int NCMAX = NC;   // channels (a record holds up to 4 W - 2)
     static_assert(NC <= 4 * W - 2, "record too narrow for the channel count");
@@ -153,7 +161,7 @@ __device__ __forceinline__ void lookup_one(const Tables& t, int64_t j, const dou
     const double E = load_in(Ein + l);
     const int32_t m = load_in(mat + l);
     if (m < 0 || m >= t.n_materials || E != E) {
-        for (int r = 0; r < nc; ++r) store_out(out + l * nc + r, __longlong_as_double(0x7ff8000000000000LL));
+        for (int r = 0; r < nc; ++r) store_nan(out + l * nc + r);
         return;
     }
     float hi[NCMAX], lo[NCMAX];
@@ -210,7 +218,7 @@ __device__ __forceinline__ void lookup_one(const Tables& t, int64_t j, const dou
         for (int r = 0; r < NCMAX; ++r) two_sum_acc(hi[r], lo[r], part[r]);
     }
 #pragma unroll
-    for (int r = 0; r < NCMAX; ++r) store_out(out + l * nc + r, (double)hi[r] + (double)lo[r]);
+    for (int r = 0; r < NCMAX; ++r) store_out(out + l * nc + r, hi[r], lo[r]);
 }
 
 // Lookups are taken either with a grid-stride loop (work == nullptr) or, for
@@ -221,17 +229,17 @@ __device__ __forceinline__ void lookup_one(const Tables& t, int64_t j, const dou
 // in L2.  With a grid-stride loop, warps in small materials run ahead of
 // those in large ones (up to 80x less work per lookup) and the lookups in
 // flight spread over all materials and energies.
-template <int W, int U, int NC>
+template <int W, int U, int NC, typename OutT>
 __global__ void __launch_bounds__(256, MCX_FAST_MIN_BLOCKS) k_xs_lookup_fast(Tables t, int64_t n, const double* __restrict__ Ein,
                                                         const int32_t* __restrict__ mat,
                                                         const int32_t* __restrict__ perm,
-                                                        double* __restrict__ out,
+                                                        OutT* __restrict__ out,
                                                         unsigned long long* __restrict__ work)
 {
     if (work == nullptr) {
         for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
              j += (int64_t)gridDim.x * blockDim.x)
-            lookup_one<W, U, NC>(t, j, Ein, mat, perm, out);
+            lookup_one<W, U, NC, OutT>(t, j, Ein, mat, perm, out);
         return;
     }
     const int lane = threadIdx.x & 31;
@@ -243,7 +251,7 @@ __global__ void __launch_bounds__(256, MCX_FAST_MIN_BLOCKS) k_xs_lookup_fast(Tab
 #pragma unroll 1
         for (int r = 0; r < kChunk / 32; ++r) {
             const int64_t j = (int64_t)base + r * 32 + lane;
-            if (j < n) lookup_one<W, U, NC>(t, j, Ein, mat, perm, out);
+            if (j < n) lookup_one<W, U, NC, OutT>(t, j, Ein, mat, perm, out);
         }
     }
 }
@@ -485,9 +493,9 @@ __device__ __forceinline__ bool staged_le(float g_hi, float g_lo, float E_hi, fl
 }
 
 // Consumer: lookup `l` (energy E) of a staged chunk.
-template <int W, int U, int NC>
+template <int W, int U, int NC, typename OutT>
 __device__ __forceinline__ void consume_one(const Tables& t, const unsigned char* stage, int ne, int32_t l,
-                                            double E, double* __restrict__ out)
+                                            double E, OutT* __restrict__ out)
 {
     using LY = StageLayout<W>;
     const int4* meta = reinterpret_cast<const int4*>(stage + LY::kMeta);
@@ -528,15 +536,15 @@ __device__ __forceinline__ void consume_one(const Tables& t, const unsigned char
         for (int r = 0; r < NC; ++r) two_sum_acc(hi[r], lo[r], part[r]);
     }
 #pragma unroll
-    for (int r = 0; r < NC; ++r) store_out(out + (int64_t)l * NC + r, (double)hi[r] + (double)lo[r]);
+    for (int r = 0; r < NC; ++r) store_out(out + (int64_t)l * NC + r, hi[r], lo[r]);
 }
 
-template <int W, int U, int NC>
+template <int W, int U, int NC, typename OutT>
 __global__ void __launch_bounds__(kStThreads, MCX_STAGED_BLOCKS) k_xs_lookup_staged(Tables t, SortParams sp, int64_t n,
                                                                     const double* __restrict__ Ein,
                                                                     const int32_t* __restrict__ mat,
                                                                     const int32_t* __restrict__ perm,
-                                                                    double* __restrict__ out,
+                                                                    OutT* __restrict__ out,
                                                                     unsigned long long* __restrict__ work,
                                                                     unsigned int* __restrict__ err)
 {
@@ -616,9 +624,9 @@ __global__ void __launch_bounds__(kStThreads, MCX_STAGED_BLOCKS) k_xs_lookup_sta
             const int32_t m = load_in(mat + l);
             // E >= E_min && E <= E_max is false for a NaN energy
             if (info.mode == ST_NORMAL && m == info.material && E >= info.E_min && E <= info.E_max)
-                consume_one<W, U, NC>(t, stage, info.n_entries, l, E, out);
+                consume_one<W, U, NC, OutT>(t, stage, info.n_entries, l, E, out);
             else
-                lookup_one<W, U, NC>(t, j, Ein, mat, perm, out);
+                lookup_one<W, U, NC, OutT>(t, j, Ein, mat, perm, out);
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);
@@ -711,44 +719,50 @@ __global__ void k_lookup_sort_scatter(SortParams sp, int64_t n, const double* __
 
 }  // namespace
 
-int launch_xs_lookup_fast(const Tables& t, int64_t n, const double* E, const int32_t* mat,
-                          const int32_t* perm, double* out, int grid, cudaStream_t st,
-                          unsigned long long* work)
+template <typename OutT>
+static int launch_fast_t(const Tables& t, int64_t n, const double* E, const int32_t* mat, const int32_t* perm,
+                         OutT* out, int grid, cudaStream_t st, unsigned long long* work)
 {
-    if (work && cudaMemsetAsync(work, 0, sizeof(unsigned long long), st) != cudaSuccess) return -1;
     // one instantiation per channel count: no work on unused record slots
     switch (t.n_ch) {
-    case 1: k_xs_lookup_fast<1, kFastUnroll, 1><<<grid, 256, 0, st>>>(t, n, E, mat, perm, out, work); break;
-    case 2: k_xs_lookup_fast<1, kFastUnroll, 2><<<grid, 256, 0, st>>>(t, n, E, mat, perm, out, work); break;
-    case 3: k_xs_lookup_fast<2, kFastUnroll, 3><<<grid, 256, 0, st>>>(t, n, E, mat, perm, out, work); break;
-    case 4: k_xs_lookup_fast<2, kFastUnroll, 4><<<grid, 256, 0, st>>>(t, n, E, mat, perm, out, work); break;
-    case 5: k_xs_lookup_fast<2, kFastUnroll, 5><<<grid, 256, 0, st>>>(t, n, E, mat, perm, out, work); break;
+    case 1: k_xs_lookup_fast<1, kFastUnroll, 1, OutT><<<grid, 256, 0, st>>>(t, n, E, mat, perm, out, work); break;
+    case 2: k_xs_lookup_fast<1, kFastUnroll, 2, OutT><<<grid, 256, 0, st>>>(t, n, E, mat, perm, out, work); break;
+    case 3: k_xs_lookup_fast<2, kFastUnroll, 3, OutT><<<grid, 256, 0, st>>>(t, n, E, mat, perm, out, work); break;
+    case 4: k_xs_lookup_fast<2, kFastUnroll, 4, OutT><<<grid, 256, 0, st>>>(t, n, E, mat, perm, out, work); break;
+    case 5: k_xs_lookup_fast<2, kFastUnroll, 5, OutT><<<grid, 256, 0, st>>>(t, n, E, mat, perm, out, work); break;
     default: return -1;
     }
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-template <int W, int NC>
+int launch_xs_lookup_fast(const Tables& t, int64_t n, const double* E, const int32_t* mat,
+                          const int32_t* perm, void* out, bool out32, int grid, cudaStream_t st,
+                          unsigned long long* work)
+{
+    if (work && cudaMemsetAsync(work, 0, sizeof(unsigned long long), st) != cudaSuccess) return -1;
+    return out32 ? launch_fast_t(t, n, E, mat, perm, static_cast<float*>(out), grid, st, work)
+                 : launch_fast_t(t, n, E, mat, perm, static_cast<double*>(out), grid, st, work);
+}
+
+template <int W, int NC, typename OutT>
 static int launch_staged_nc(const Tables& t, const SortParams& sp, int64_t n, const double* E, const int32_t* mat,
-                            const int32_t* perm, double* out, int grid, cudaStream_t st, unsigned long long* work,
+                            const int32_t* perm, OutT* out, int grid, cudaStream_t st, unsigned long long* work,
                             unsigned int* err)
 {
     const size_t smem = kStStages * StageLayout<W>::kBytes + 128;
-    if (cudaFuncSetAttribute(k_xs_lookup_staged<W, kFastUnroll, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess)
+    if (cudaFuncSetAttribute(k_xs_lookup_staged<W, kFastUnroll, NC, OutT>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return -1;
-    k_xs_lookup_staged<W, kFastUnroll, NC><<<grid, kStThreads, smem, st>>>(t, sp, n, E, mat, perm, out, work, err);
+    k_xs_lookup_staged<W, kFastUnroll, NC, OutT><<<grid, kStThreads, smem, st>>>(t, sp, n, E, mat, perm, out, work,
+                                                                                 err);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-int launch_xs_lookup_staged(const Tables& t, const SortParams& sp, int64_t n, const double* E,
-                            const int32_t* mat, const int32_t* perm, double* out, int sm_count, cudaStream_t st,
-                            unsigned long long* work, unsigned int* err)
+template <typename OutT>
+static int launch_staged_t(const Tables& t, const SortParams& sp, int64_t n, const double* E, const int32_t* mat,
+                           const int32_t* perm, OutT* out, int grid, cudaStream_t st, unsigned long long* work,
+                           unsigned int* err)
 {
-    const int grid = sm_count * MCX_STAGED_BLOCKS;
-    if (!perm || !work || !err) return -1;
-    if (t.max_mat_species > kStMaxSpecies || t.H == 0) return -2;   // the caller uses the global-memory form
-    if (cudaMemsetAsync(work, 0, sizeof(unsigned long long), st) != cudaSuccess) return -1;
     switch (t.n_ch) {
     case 1: return launch_staged_nc<1, 1>(t, sp, n, E, mat, perm, out, grid, st, work, err);
     case 2: return launch_staged_nc<1, 2>(t, sp, n, E, mat, perm, out, grid, st, work, err);
@@ -757,6 +771,18 @@ int launch_xs_lookup_staged(const Tables& t, const SortParams& sp, int64_t n, co
     case 5: return launch_staged_nc<2, 5>(t, sp, n, E, mat, perm, out, grid, st, work, err);
     default: return -1;
     }
+}
+
+int launch_xs_lookup_staged(const Tables& t, const SortParams& sp, int64_t n, const double* E,
+                            const int32_t* mat, const int32_t* perm, void* out, bool out32, int sm_count,
+                            cudaStream_t st, unsigned long long* work, unsigned int* err)
+{
+    const int grid = sm_count * MCX_STAGED_BLOCKS;
+    if (!perm || !work || !err) return -1;
+    if (t.max_mat_species > kStMaxSpecies || t.H == 0) return -2;   // the caller uses the global-memory form
+    if (cudaMemsetAsync(work, 0, sizeof(unsigned long long), st) != cudaSuccess) return -1;
+    return out32 ? launch_staged_t(t, sp, n, E, mat, perm, static_cast<float*>(out), grid, st, work, err)
+                 : launch_staged_t(t, sp, n, E, mat, perm, static_cast<double*>(out), grid, st, work, err);
 }
 
 int launch_lookup_sort(const SortParams& sp, int64_t n, const double* E, const int32_t* mat,

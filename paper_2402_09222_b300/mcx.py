@@ -23,7 +23,7 @@ ERR_NAMES = {-1: "MCX_ERR_ARG", -2: "MCX_ERR_CUDA", -3: "MCX_ERR_OOM", -4: "MCX_
 ERR_ITER_LIMIT, ERR_TIMEOUT = -4, -7
 FP64, FP32 = 0, 1
 QUEUELESS, QUEUED, QUEUED_FULLEST = 0, 1, 2
-LOOKUP_EXACT, LOOKUP_FAST, LOOKUP_SORT, LOOKUP_STAGED = 0, 1, 2, 4
+LOOKUP_EXACT, LOOKUP_FAST, LOOKUP_SORT, LOOKUP_STAGED, LOOKUP_OUT32 = 0, 1, 2, 4, 8
 FLAG_DERIVATIVES, FLAG_HISTORY_DEBUG = 1, 2
 TALLY_FLUX, TALLY_ABSORB, TALLY_OUTCOME, TALLY_DFLUX, TALLY_DABSORB, TALLY_DOUTCOME = range(6)
 GEOM_NONE = 3
@@ -315,11 +315,12 @@ class Problem:
     def xs_lookup(self, E, mat, out=None, flags: int = LOOKUP_EXACT, stream=None):
         import torch
         n = E.numel()
+        odt = torch.float32 if flags & LOOKUP_OUT32 else torch.float64
         if out is None:
-            out = torch.empty((n, self.n_ch), dtype=torch.float64, device=E.device)
+            out = torch.empty((n, self.n_ch), dtype=odt, device=E.device)
         _check(_lib.mcx_xs_lookup(self.h, n, _dev_ptr(E, torch.float64, "E"),
                                   _dev_ptr(mat, torch.int32, "mat"),
-                                  _dev_ptr(out, torch.float64, "out"), flags, _stream_ptr(stream)))
+                                  _dev_ptr(out, odt, "out"), flags, _stream_ptr(stream)))
         return out
 
     def xs_sort(self, E, mat, perm=None, stream=None):
@@ -336,28 +337,35 @@ class Problem:
         """Lookup processed in the order `perm` (None: natural order)."""
         import torch
         n = E.numel()
+        odt = torch.float32 if flags & LOOKUP_OUT32 else torch.float64
         if out is None:
-            out = torch.empty((n, self.n_ch), dtype=torch.float64, device=E.device)
+            out = torch.empty((n, self.n_ch), dtype=odt, device=E.device)
         pp = _vp(0) if perm is None else _dev_ptr(perm, torch.int32, "perm")
         _check(_lib.mcx_xs_lookup_ordered(self.h, n, _dev_ptr(E, torch.float64, "E"),
                                           _dev_ptr(mat, torch.int32, "mat"), pp,
-                                          _dev_ptr(out, torch.float64, "out"), flags, _stream_ptr(stream)))
+                                          _dev_ptr(out, odt, "out"), flags, _stream_ptr(stream)))
         return out
 
     def xs_lookup_host(self, E, mat, out=None, flags: int = LOOKUP_EXACT):
         """Lookup from host buffers (numpy arrays or CPU tensors, ideally pinned)."""
         import torch
+        out32 = bool(flags & LOOKUP_OUT32)
         if isinstance(E, torch.Tensor):
             n = E.numel()
             if out is None:
-                out = torch.empty((n, self.n_ch), dtype=torch.float64, pin_memory=True)
+                out = torch.empty((n, self.n_ch), dtype=torch.float32 if out32 else torch.float64,
+                                  pin_memory=True)
+            if out.dtype != (torch.float32 if out32 else torch.float64):
+                raise TypeError("out has the wrong dtype for these flags")
             pe, pm, po = _vp(E.data_ptr()), _vp(mat.data_ptr()), _vp(out.data_ptr())
         else:
             E = np.ascontiguousarray(E, np.float64)
             mat = np.ascontiguousarray(mat, np.int32)
             n = len(E)
             if out is None:
-                out = np.empty((n, self.n_ch))
+                out = np.empty((n, self.n_ch), np.float32 if out32 else np.float64)
+            if out.dtype != (np.float32 if out32 else np.float64):
+                raise TypeError("out has the wrong dtype for these flags")
             pe, pm, po = _np_ptr(E), _np_ptr(mat), _np_ptr(out)
         _check(_lib.mcx_xs_lookup_host(self.h, n, pe, pm, po, flags))
         return out

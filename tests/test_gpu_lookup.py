@@ -298,3 +298,27 @@ def test_staged_lookup_on_the_benchmark_tables(torch_cuda):
     p.check_device()
     assert torch.equal(direct.view(torch.int64), staged.view(torch.int64))
     p.close()
+
+
+def test_fp32_outputs_are_the_fp64_outputs_rounded_once(torch_cuda, small_case):
+    """MCX_LOOKUP_OUT32 writes the compensated sum rounded once to FP32: the
+    FP64 fast output rounded to FP32, bit for bit, on device and host paths,
+    direct and staged; the exact form refuses it."""
+    from paper_2402_09222_b300 import mcx
+    torch = torch_cuda
+    lib, mats, E, mat = small_case
+    p = _handle(lib, mats, mcx.FP32, 4000)
+    dE, dm = _dev(torch, E, torch.float64), _dev(torch, mat, torch.int32)
+    ref = p.xs_lookup(dE, dm, flags=mcx.LOOKUP_FAST | mcx.LOOKUP_SORT).float()
+    for fl in (mcx.LOOKUP_FAST, mcx.LOOKUP_FAST | mcx.LOOKUP_SORT,
+               mcx.LOOKUP_FAST | mcx.LOOKUP_SORT | mcx.LOOKUP_STAGED):
+        got = p.xs_lookup(dE, dm, flags=fl | mcx.LOOKUP_OUT32)
+        assert got.dtype == torch.float32
+        assert torch.equal(got.view(torch.int32), ref.view(torch.int32)), fl
+    host = p.xs_lookup_host(torch.as_tensor(E), torch.as_tensor(mat),
+                            flags=mcx.LOOKUP_FAST | mcx.LOOKUP_SORT | mcx.LOOKUP_OUT32)
+    assert host.dtype == torch.float32 and torch.equal(host.view(torch.int32), ref.cpu().view(torch.int32))
+    with pytest.raises(mcx.McxError, match="ARG"):
+        p.xs_lookup(dE, dm, out=torch.empty((len(E), lib.n_ch), dtype=torch.float32, device="cuda"),
+                    flags=mcx.LOOKUP_OUT32)
+    p.close()
