@@ -220,3 +220,37 @@ def test_config3_full_size_sampled(mcx, mode):
     assert out[4] == g["ncoll"].sum()
     d = g["absorb"].sum(1) - g["outcome"][:, 0]
     assert abs(d.mean()) <= 3 * d.std(ddof=1) / np.sqrt(len(d))
+
+
+def test_config5_full_size_sampled(mcx):
+    """The 64 uneven lattices of the batched benchmark (2.76e7 histories) in
+    one event loop with the benchmark's launch settings: sampled histories of
+    every problem re-run one by one in the oracle (FP32-rounded tables) match
+    their collision counts, and each problem's histories all end in its own
+    outcome tallies."""
+    lib = synth.species_library(355, 11_303, 1236).channels([synth.CH_SCATTER, synth.CH_ABSORB])
+    mats = synth.lookup_materials(355, 1236)
+    probs = synth.config5_problems(lib, mats, n_problems=64)
+    base = mcx.Problem(probs[0], flags=mcx.FLAG_HISTORY_DEBUG).load_tables(lib, mats, precision=mcx.FP32,
+                                                                           hash_bins=4000)
+    hs = [base] + [mcx.Problem(pr, flags=mcx.FLAG_HISTORY_DEBUG).share_tables(base) for pr in probs[1:]]
+    base.set_tuning(mode=1, block_size=64, sort_period=1, sort_threshold=564_000)
+    mcx.batch_run(hs, [pr.n_histories for pr in probs], particles_in_flight=2_596_000, seed=9)
+    lib32 = lib.fp32_rounded()
+    rng = np.random.default_rng(17)
+    matched = total = 0
+    for h, pr in zip(hs, probs):
+        nc = h.history_debug(pr.n_histories)
+        out = h.tallies()["outcome"].sum(0)
+        assert out[:4].sum() == pr.n_histories
+        assert out[4] == nc.sum()
+        rp = synth.Problem(pr.geometry, lib32, pr.mats, lattice_n=pr.lattice_n,
+                           region_material=pr.region_material, problem_id=pr.problem_id,
+                           n_histories=pr.n_histories)
+        for hh in rng.choice(pr.n_histories, 4, replace=False):
+            ref = oracle.transport(rp, seed=9, first=int(hh), count=1, history_debug=True)["ncoll"][0]
+            matched += int(nc[hh] == ref)
+            total += 1
+    assert matched / total >= 0.99, (matched, total)
+    for h in hs:
+        h.close()
