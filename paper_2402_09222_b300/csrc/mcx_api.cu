@@ -4,6 +4,8 @@
 // points.  No exception or abort crosses the ABI: every failure becomes a
 // status code plus a thread-local message.
 #include <algorithm>
+#include <atomic>
+#include <cstdlib>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -64,11 +66,28 @@ struct DeviceGuard {
     }
 };
 
+// Fault injection on the host: with MCX_FAIL_ALLOC_AFTER=N in the
+// environment, the device allocations after the first N (counted while the
+// variable is set) fail with MCX_ERR_OOM without reaching the driver.
+bool simulated_alloc_failure()
+{
+    static std::atomic<long long> count{0};
+    const char* v = std::getenv("MCX_FAIL_ALLOC_AFTER");
+    if (!v || !*v) {
+        count.store(0);
+        return false;
+    }
+    return count.fetch_add(1) + 1 > std::atoll(v);
+}
+
 template <typename T>
 int dev_alloc(T** p, size_t count)
 {
     *p = nullptr;
     if (count == 0) count = 1;
+    if (simulated_alloc_failure())
+        return fail(MCX_ERR_OOM, "cudaMalloc(%zu bytes): simulated failure (MCX_FAIL_ALLOC_AFTER)",
+                    sizeof(T) * count);
     cudaError_t e = cudaMalloc((void**)p, sizeof(T) * count);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -243,6 +262,9 @@ int ensure_particles(mcx_problem* p, int64_t cap, bool with_w, size_t n_bins, in
     size_t bytes = al(c * 8) * 10 + (w ? al(c * 8 * MCX_MAX_DMAT) : 0) + al(c * 8 * (size_t)cs) + al(c * 8) +
                    al(c * 4) * 3 + al(c * 4) * 3 + al(c) + al(c * 4) * 8 + al((bins + 1) * 4);
     void* blk = nullptr;
+    if (simulated_alloc_failure())
+        return fail(MCX_ERR_OOM, "particle buffer of %lld slots: simulated failure (MCX_FAIL_ALLOC_AFTER)",
+                    (long long)want);
     cudaError_t e = cudaMalloc(&blk, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -535,6 +557,7 @@ int run_loop(mcx_problem* owner, int n_prob, mcx_problem* const* probs, const in
         drop_graph(owner);
         dev_free(owner->d_probs);
         dev_free(owner->d_work_off);
+        owner->probs_cap = 0;   // stays 0 if an allocation below fails
         TRY(dev_alloc(&owner->d_probs, (size_t)n_prob));
         TRY(dev_alloc(&owner->d_work_off, (size_t)n_prob + 1));
         owner->probs_cap = n_prob;
@@ -546,6 +569,7 @@ int run_loop(mcx_problem* owner, int n_prob, mcx_problem* const* probs, const in
         if (q->desc.flags & MCX_FLAG_HISTORY_DEBUG) {
             if (q->debug_cap < count[i]) {
                 dev_free(q->ncoll_debug);
+                q->debug_cap = 0;
                 TRY(dev_alloc(&q->ncoll_debug, (size_t)count[i]));
                 q->debug_cap = count[i];
             }
@@ -673,6 +697,7 @@ int ensure_lookup_scratch(mcx_problem* p, int64_t n, size_t)
 {
     if (p->perm_cap < n) {
         dev_free(p->perm);
+        p->perm_cap = 0;
         TRY(dev_alloc(&p->perm, (size_t)n));
         p->perm_cap = n;
     }
@@ -702,6 +727,7 @@ int sort_device(mcx_problem* p, int64_t n, const double* E, const int32_t* mat, 
     const size_t nb = (size_t)sp.n_materials * sp.n_ebuckets;
     if (p->lbins_cap < nb + 1) {
         dev_free(p->lbins);
+        p->lbins_cap = 0;
         TRY(dev_alloc(&p->lbins, nb + 1));
         p->lbins_cap = nb + 1;
     }
@@ -761,10 +787,8 @@ int lookup_device(mcx_problem* p, int64_t n, const double* E, const int32_t* mat
 // an ordered bank of `bank_cap` sites (grown, never shrunk).
 int ensure_eigen(mcx_problem* p, int64_t N, int64_t bank_cap)
 {
-    if (!p->e_ctl) {
-        TRY(dev_alloc(&p->e_ctl, 1));
-        TRY(dev_alloc(&p->e_bad, 1));
-    }
+    if (!p->e_ctl) TRY(dev_alloc(&p->e_ctl, 1));
+    if (!p->e_bad) TRY(dev_alloc(&p->e_bad, 1));
     if (p->e_n_cap < N) {
         dev_free(p->e_src);
         dev_free(p->e_count);
@@ -1051,7 +1075,7 @@ int mcx_load_xs_tables(mcx_problem* p, int32_t n_species, const int64_t* goff, c
         (rc = dev_alloc(&ts->ment, (size_t)nnz)))
         return bail(rc);
     const size_t sig_bytes = (size_t)P * n_ch * (precision == MCX_FP32 ? 4 : 8);
-    if (cudaMalloc(&ts->sigma, sig_bytes) != cudaSuccess) {
+    if (simulated_alloc_failure() || cudaMalloc(&ts->sigma, sig_bytes) != cudaSuccess) {
         cudaGetLastError();
         return bail(fail(MCX_ERR_OOM, "sigma table of %zu bytes", sig_bytes));
     }
@@ -1392,6 +1416,7 @@ int mcx_xs_lookup_host(mcx_problem* p, int64_t n, const double* E_host, const in
     const int64_t per = chunk * (4 + nc) + nbins;
     if (p->h_buf_cap < 2 * per) {
         dev_free(p->h_buf);
+        p->h_buf_cap = 0;
         TRY(dev_alloc(&p->h_buf, (size_t)(2 * per)));
         p->h_buf_cap = 2 * per;
     }

@@ -254,3 +254,28 @@ def test_config5_full_size_sampled(mcx):
     assert matched / total >= 0.99, (matched, total)
     for h in hs:
         h.close()
+
+
+def test_simulated_allocation_failures_are_errors_and_leave_handles_usable(mcx, config1, monkeypatch):
+    """Host-side fault injection (MCX_FAIL_ALLOC_AFTER): an allocation that
+    fails inside problem creation, table loading or the particle buffer
+    returns MCX_ERR_OOM, and the handles work again once it is lifted."""
+    prob, ref = config1
+    monkeypatch.setenv("MCX_FAIL_ALLOC_AFTER", "0")
+    with pytest.raises(mcx.McxError, match="OOM"):
+        mcx.Problem(prob)
+    monkeypatch.delenv("MCX_FAIL_ALLOC_AFTER")
+    p = mcx.Problem(prob)
+    monkeypatch.setenv("MCX_FAIL_ALLOC_AFTER", "3")
+    with pytest.raises(mcx.McxError, match="OOM"):
+        p.load_tables(prob.lib, prob.mats, hash_bins=4000)
+    monkeypatch.delenv("MCX_FAIL_ALLOC_AFTER")
+    p.load_tables(prob.lib, prob.mats, hash_bins=4000)
+    monkeypatch.setenv("MCX_FAIL_ALLOC_AFTER", "0")
+    with pytest.raises(mcx.McxError, match="OOM"):
+        p.run(particles_in_flight=1000, seed=7)
+    monkeypatch.delenv("MCX_FAIL_ALLOC_AFTER")
+    p.zero_tallies()
+    p.run(particles_in_flight=1000, seed=7)
+    assert_tallies_close(p.tallies(), ref)
+    p.close()
