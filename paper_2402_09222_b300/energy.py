@@ -11,7 +11,36 @@ any GPU setting; it only reads a counter.
 """
 from __future__ import annotations
 
+import ctypes
 import time
+
+
+class _NvmlLib:
+    """The four NVML calls the meter needs, through ctypes on the driver's
+    libnvidia-ml (for machines without the pynvml module).  Read-only."""
+
+    def __init__(self):
+        self._l = ctypes.CDLL("libnvidia-ml.so.1")
+
+    def _ok(self, rc, what):
+        if rc != 0:
+            raise RuntimeError(f"NVML {what} failed with code {rc}")
+
+    def nvmlInit(self):
+        self._ok(self._l.nvmlInit_v2(), "init")
+
+    def nvmlShutdown(self):
+        self._ok(self._l.nvmlShutdown(), "shutdown")
+
+    def nvmlDeviceGetHandleByIndex(self, i):
+        h = ctypes.c_void_p()
+        self._ok(self._l.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(i), ctypes.byref(h)), "device handle")
+        return h
+
+    def nvmlDeviceGetTotalEnergyConsumption(self, h):
+        mj = ctypes.c_ulonglong()
+        self._ok(self._l.nvmlDeviceGetTotalEnergyConsumption(h, ctypes.byref(mj)), "energy counter")
+        return mj.value
 
 
 class EnergyMeter:
@@ -23,8 +52,11 @@ class EnergyMeter:
 
     def _lib(self):
         if self._nvml is None:
-            import pynvml
-            self._nvml = pynvml
+            try:
+                import pynvml
+                self._nvml = pynvml
+            except ImportError:
+                self._nvml = _NvmlLib()
         return self._nvml
 
     def __enter__(self):
