@@ -42,3 +42,20 @@ def test_short_search_on_the_lattice(mcx, tmp_path):
     assert best.seconds <= t.baseline * 1.05
     assert rep["evaluations"] == 8
     assert all(r.status in ("ok", "timeout") for r in t.records), [r.status for r in t.records]
+
+
+def test_energy_meter_reads_the_board_counter(mcx):
+    """The NVML total-energy counter (pynvml, or the driver library through
+    ctypes) brackets a run: positive joules at a plausible board power."""
+    from paper_2402_09222_b300 import energy
+    prob = synth.config3_problem(n_histories=300_000, lattice_n=9, n_points=2000)
+    p = mcx.make_problem(prob, precision=mcx.FP32, hash_bins=4000)
+    p.set_tuning(mode=mcx.QUEUED)
+    import time
+    with energy.EnergyMeter(0) as m:
+        t0 = time.perf_counter()
+        while time.perf_counter() - t0 < 0.6:     # the counter ticks every few tens of ms
+            p.run(particles_in_flight=300_000, seed=2)
+    p.close()
+    assert m.joules > 0 and m.seconds > 0
+    assert 20.0 < m.watts < 2000.0, m.watts
