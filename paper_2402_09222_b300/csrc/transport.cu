@@ -829,7 +829,6 @@ __global__ void __launch_bounds__(1024) k_collide(LoopConfig c, Tables t, Partic
                           : ring_segment(P, ctl);
     const int64_t count = src.n;
     const int M = c.derivatives;
-    const int nc = t.n_ch, cs = t.ch_scatter, ca = t.ch_absorb;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < count; base += stride) {
         const int64_t i = base + threadIdx.x;
@@ -901,10 +900,10 @@ __global__ void __launch_bounds__(1024) k_collide(LoopConfig c, Tables t, Partic
             double ss_j, sa_j;
             {
                 const int64_t k = species_index(t, j, eb, hb);
-                const int64_t p = __ldg(t.goff + j) + k;
-                const double f = fraction_transport(t, E, p);
-                ss_j = interp_transport(sig_at<T>(t.sigma, p * nc + cs), sig_at<T>(t.sigma, (p + 1) * nc + cs), f);
-                sa_j = interp_transport(sig_at<T>(t.sigma, p * nc + ca), sig_at<T>(t.sigma, (p + 1) * nc + ca), f);
+                const int64_t g0 = __ldg(t.goff + j);
+                const int64_t last = __ldg(t.goff + j + 1) - 2;
+                double unused = 0.0;
+                species_transport<T, false>(t, E, g0 + k, last, ss_j, sa_j, unused);
             }
             const double st_j = ss_j + sa_j;
             uint8_t fl = (uint8_t)(P.flags[slot] & ~PF_COLLIDE);

@@ -130,6 +130,28 @@ __global__ void k_update_tables(Tables t, const double* __restrict__ dens_src, i
     }
 }
 
+template <typename T>
+__global__ void k_build_slopes(Tables t, double* __restrict__ slope)
+{
+    const int64_t n = t.n_points * t.n_ch;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const int64_t p = i / t.n_ch;
+        // winv is 0 exactly at a species' last point, which starts no interval
+        double v = 0.0;
+        if (t.winv[p] != 0.0)
+            v = (sig_at<T>(t.sigma, i + t.n_ch) - sig_at<T>(t.sigma, i)) / (t.E[p + 1] - t.E[p]);
+        slope[i] = v;
+    }
+}
+
+int launch_build_slopes(const Tables& t, double* slope, int grid, cudaStream_t st)
+{
+    if (t.precision == MCX_FP32) k_build_slopes<float><<<grid, 256, 0, st>>>(t, slope);
+    else k_build_slopes<double><<<grid, 256, 0, st>>>(t, slope);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
 int launch_update_tables(const Tables& t, const double* dens_src, int64_t nnz, double* mden,
                          int4* ment, const double* sig_src, void* sigma, float4* frec,
                          cudaStream_t st)

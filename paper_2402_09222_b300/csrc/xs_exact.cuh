@@ -71,6 +71,59 @@ __device__ __forceinline__ double interp_transport(double s0, double s1, double 
 #endif
 }
 
+// Transport value of channel ch of the interval starting at point p, for an
+// energy with g[p] <= E < g[p+1] (or E below the grid at a species' first
+// point): s[p] + (E - g[p]) * slope[p] with the slope stored per interval --
+// one fused multiply-add per channel instead of a subtraction and one, and no
+// fraction (its multiply and clamps) -- a difference in the last bits from
+// s[p] + f (s[p+1] - s[p]), like the reciprocal width above.  d < 0 (below
+// the grid) clamps to 0, giving s[p] as the clamped fraction does.  The last
+// interval of a species, where E may lie above the grid, keeps the fraction
+// form and its clamp to 1.
+#ifndef MCX_TRANSPORT_SLOPE
+#define MCX_TRANSPORT_SLOPE 1
+#endif
+__device__ __forceinline__ double offset_transport(const Tables& t, double E, int64_t p)
+{
+    double d = E - __ldg(t.E + p);
+    if (__double_as_longlong(d) < 0) d = 0.0;
+    return d;
+}
+
+template <typename T>
+__device__ __forceinline__ double slope_value(const Tables& t, double d, int64_t p, int nc, int ch)
+{
+    return fma(d, __ldg(t.slope + p * nc + ch), sig_at<T>(t.sigma, p * nc + ch));
+}
+
+template <typename T>
+__device__ __forceinline__ double fraction_value(const Tables& t, double f, int64_t p, int nc, int ch)
+{
+    return interp_transport(sig_at<T>(t.sigma, p * nc + ch), sig_at<T>(t.sigma, (p + 1) * nc + ch), f);
+}
+
+// Scatter and absorption (and with NF nu-fission) cross sections of one
+// species at E, its interval starting at point p, `last` its last interval.
+template <typename T, bool NF>
+__device__ __forceinline__ void species_transport(const Tables& t, double E, int64_t p, int64_t last, double& ss,
+                                                  double& sa, double& sf)
+{
+    const int nc = t.n_ch, cs = t.ch_scatter, ca = t.ch_absorb, cf = t.ch_nu_fission;
+#if MCX_TRANSPORT_SLOPE
+    if (p < last) {
+        const double d = offset_transport(t, E, p);
+        ss = slope_value<T>(t, d, p, nc, cs);
+        sa = slope_value<T>(t, d, p, nc, ca);
+        if (NF) sf = slope_value<T>(t, d, p, nc, cf);
+        return;
+    }
+#endif
+    const double f = fraction_transport(t, E, p);
+    ss = fraction_value<T>(t, f, p, nc, cs);
+    sa = fraction_value<T>(t, f, p, nc, ca);
+    if (NF) sf = fraction_value<T>(t, f, p, nc, cf);
+}
+
 // Transport lookup: Sigma_t = sum_i N_i (sigma_s,i + sigma_a,i) and
 // Sigma_a = sum_i N_i sigma_a,i, both sequential in species order.  The
 // running sums C_i of Sigma_t are stored to cum[0..n-1] (the collision picks
@@ -86,16 +139,17 @@ __device__ __forceinline__ void macro_transport(const Tables& t, int32_t m, doub
     const int64_t eb = search_key(E);
     const int32_t hb = t.H > 0 ? hash_bin(t, E, eb) : 0;
     const int32_t i0 = __ldg(t.moff + m), i1 = __ldg(t.moff + m + 1);
-    const int nc = t.n_ch, cs = t.ch_scatter, ca = t.ch_absorb, cf = t.ch_nu_fission;
     double st = 0.0, sa = 0.0, nf = 0.0;
     for (int32_t i = i0; i < i1; i += 2) {
-        int32_t base[2], len[2];
+        int32_t base[2], len[2], last[2];
         double N[2];
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
             const int32_t ii = i + u < i1 ? i + u : i1 - 1;
             N[u] = __ldg(t.mden + ii);
-            search_window(t, __ldg(t.ment + ii), hb, base[u], len[u]);
+            const int4 e = __ldg(t.ment + ii);
+            last[u] = e.x + e.y - 2;
+            search_window(t, e, hb, base[u], len[u]);
         }
         for (int s = 0; s < t.search_steps; ++s) {
             search_step(t.E, base[0], len[0], eb);
@@ -104,12 +158,8 @@ __device__ __forceinline__ void macro_transport(const Tables& t, int32_t m, doub
         double c[2], a[2], v[2] = {0.0, 0.0};
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
-            const int64_t p = base[u];
-            const double f = fraction_transport(t, E, p);
-            const double ss = interp_transport(sig_at<T>(t.sigma, p * nc + cs),
-                                               sig_at<T>(t.sigma, (p + 1) * nc + cs), f);
-            const double sai = interp_transport(sig_at<T>(t.sigma, p * nc + ca),
-                                                sig_at<T>(t.sigma, (p + 1) * nc + ca), f);
+            double ss, sai, sf = 0.0;
+            species_transport<T, NF>(t, E, base[u], last[u], ss, sai, sf);
 #if MCX_TRANSPORT_FMA
             a[u] = N[u] * sai;
             c[u] = fma(N[u], ss, a[u]);
@@ -117,9 +167,7 @@ __device__ __forceinline__ void macro_transport(const Tables& t, int32_t m, doub
             c[u] = N[u] * (ss + sai);
             a[u] = N[u] * sai;
 #endif
-            if (NF)
-                v[u] = N[u] * interp_transport(sig_at<T>(t.sigma, p * nc + cf),
-                                               sig_at<T>(t.sigma, (p + 1) * nc + cf), f);
+            if (NF) v[u] = N[u] * sf;
         }
         st = st + c[0];
         sa = sa + a[0];
