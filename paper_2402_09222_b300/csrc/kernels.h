@@ -32,8 +32,10 @@ int launch_xs_indices(const Tables& t, int64_t n, const double* E, const int32_t
                       int32_t max_species, int32_t* kout, int grid, cudaStream_t st);
 int launch_build_hash(const Tables& t, int32_t* hidx, int grid, cudaStream_t st);
 // Per interval and channel (s[k+1] - s[k]) / (g[k+1] - g[k]) from the device
-// sigma table (0 at a species' last point), into slope [n_points][n_ch].
-int launch_build_slopes(const Tables& t, double* slope, int grid, cudaStream_t st);
+// sigma table (0 at a species' last point), into slope [n_points][n_ch]; and
+// per point the total t = s_scatter + s_absorb with its slope into ttot
+// (libraries with the transport's channels, else zeros).
+int launch_build_slopes(const Tables& t, double* slope, double2* ttot, int grid, cudaStream_t st);
 // Widest hash window (in grid points, window end inclusive) into *out (device int).
 int launch_hash_max_window(const Tables& t, int32_t* out, int grid, cudaStream_t st);
 int launch_xs_backward(const Tables& t, int64_t n, const double* E, const int32_t* mat,

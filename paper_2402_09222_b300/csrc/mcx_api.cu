@@ -114,6 +114,7 @@ struct TableStore {
     double* E = nullptr;
     double* winv = nullptr;   // per interval 1 / (g[k+1] - g[k]) (transport)
     double* slope = nullptr;  // per interval and channel, from the device sigma table (transport)
+    double2* ttot = nullptr;  // per point total of scatter and absorption and its slope (transport)
     float4* frec = nullptr;
     void* sigma = nullptr;
     double* awr = nullptr;
@@ -136,6 +137,7 @@ struct TableStore {
         dev_free(E);
         dev_free(winv);
         dev_free(slope);
+        dev_free(ttot);
         dev_free(frec);
         if (sigma) cudaFree(sigma);
         dev_free(awr);
@@ -1071,6 +1073,7 @@ int mcx_load_xs_tables(mcx_problem* p, int32_t n_species, const int64_t* goff, c
     // energies in 16-byte pairs and may read one entry past a species' end
     if ((rc = dev_alloc(&ts->goff, (size_t)n_species + 1)) || (rc = dev_alloc(&ts->E, (size_t)P + 2)) ||
         (rc = dev_alloc(&ts->winv, (size_t)P)) || (rc = dev_alloc(&ts->slope, (size_t)P * n_ch)) ||
+        (rc = dev_alloc(&ts->ttot, (size_t)P)) ||
         (rc = dev_alloc(&ts->frec, (size_t)P * frec_w)) ||
         (rc = dev_alloc(&ts->awr, (size_t)n_species)) || (rc = dev_alloc(&ts->moff, (size_t)n_materials + 1)) ||
         (rc = dev_alloc(&ts->msp, (size_t)nnz)) || (rc = dev_alloc(&ts->mden, (size_t)nnz)) ||
@@ -1115,6 +1118,7 @@ int mcx_load_xs_tables(mcx_problem* p, int32_t n_species, const int64_t* goff, c
     v.E = ts->E;
     v.winv = ts->winv;
     v.slope = ts->slope;
+    v.ttot = ts->ttot;
     v.frec = ts->frec;
     v.frec_w = frec_w;
     v.sigma = ts->sigma;
@@ -1129,7 +1133,7 @@ int mcx_load_xs_tables(mcx_problem* p, int32_t n_species, const int64_t* goff, c
     ts->emax = emax;
     ts->nnz = nnz;
     ts->h_moff.assign(moff, moff + n_materials + 1);
-    if (launch_build_slopes(v, ts->slope, p->sm_count * 8, nullptr) || cudaDeviceSynchronize() != cudaSuccess)
+    if (launch_build_slopes(v, ts->slope, ts->ttot, p->sm_count * 8, nullptr) || cudaDeviceSynchronize() != cudaSuccess)
         return bail(fail(MCX_ERR_CUDA, "slope table build failed"));
     if ((rc = build_hash(ts, hash_bins, p->sm_count)) != MCX_OK) return bail(rc);
     drop_graph(p);
@@ -1205,7 +1209,7 @@ int mcx_update_tables_device(mcx_problem* p, const double* mat_dens, const doubl
                              ts->frec, (cudaStream_t)stream))
         return fail(MCX_ERR_CUDA, "table update launch failed");
     // the transport's interval slopes follow the new sigma table, on the same stream
-    if (sigma && launch_build_slopes(ts->view, ts->slope, p->sm_count * 8, (cudaStream_t)stream))
+    if (sigma && launch_build_slopes(ts->view, ts->slope, ts->ttot, p->sm_count * 8, (cudaStream_t)stream))
         return fail(MCX_ERR_CUDA, "slope table launch failed");
     return MCX_OK;
 }

@@ -47,6 +47,7 @@ struct Tables {
     const double* E = nullptr;
     const double* winv = nullptr;   // per interval 1 / (g[k+1] - g[k])
     const double* slope = nullptr;  // per interval and channel (s[k+1] - s[k]) / (g[k+1] - g[k]) (transport)
+    const double2* ttot = nullptr;  // per point {s_scatter + s_absorb, its interval slope} (transport)
     const float4* frec = nullptr;   // fast-path point records, frec_w float4 each
     int32_t frec_w = 0;
     const void* sigma = nullptr;

@@ -897,15 +897,14 @@ __global__ void __launch_bounds__(1024) k_collide(LoopConfig c, Tables t, Partic
                 else lo = mid + 1;
             }
             const int32_t j = __ldg(t.msp + i0 + lo);
-            double ss_j, sa_j;
+            double st_j, sa_j;
             {
                 const int64_t k = species_index(t, j, eb, hb);
                 const int64_t g0 = __ldg(t.goff + j);
                 const int64_t last = __ldg(t.goff + j + 1) - 2;
                 double unused = 0.0;
-                species_transport<T, false>(t, E, g0 + k, last, ss_j, sa_j, unused);
+                species_transport<T, false>(t, E, g0 + k, last, st_j, sa_j, unused);
             }
-            const double st_j = ss_j + sa_j;
             uint8_t fl = (uint8_t)(P.flags[slot] & ~PF_COLLIDE);
             if (xi2 * st_j < sa_j) {
                 dies = true;

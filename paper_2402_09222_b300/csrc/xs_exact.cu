@@ -145,10 +145,35 @@ __global__ void k_build_slopes(Tables t, double* __restrict__ slope)
     }
 }
 
-int launch_build_slopes(const Tables& t, double* slope, int grid, cudaStream_t st)
+template <typename T>
+__device__ __forceinline__ double total_at(const Tables& t, int64_t p)
 {
-    if (t.precision == MCX_FP32) k_build_slopes<float><<<grid, 256, 0, st>>>(t, slope);
-    else k_build_slopes<double><<<grid, 256, 0, st>>>(t, slope);
+    return sig_at<T>(t.sigma, p * t.n_ch + t.ch_scatter) + sig_at<T>(t.sigma, p * t.n_ch + t.ch_absorb);
+}
+
+template <typename T>
+__global__ void k_build_totals(Tables t, double2* __restrict__ ttot)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < t.n_points; p += stride) {
+        const double s0 = total_at<T>(t, p);
+        double v = 0.0;
+        if (t.winv[p] != 0.0) v = (total_at<T>(t, p + 1) - s0) / (t.E[p + 1] - t.E[p]);
+        ttot[p] = make_double2(s0, v);
+    }
+}
+
+int launch_build_slopes(const Tables& t, double* slope, double2* ttot, int grid, cudaStream_t st)
+{
+    const bool tr = t.ch_scatter >= 0 && t.ch_scatter < t.n_ch && t.ch_absorb >= 0 && t.ch_absorb < t.n_ch;
+    if (t.precision == MCX_FP32) {
+        k_build_slopes<float><<<grid, 256, 0, st>>>(t, slope);
+        if (tr) k_build_totals<float><<<grid, 256, 0, st>>>(t, ttot);
+    } else {
+        k_build_slopes<double><<<grid, 256, 0, st>>>(t, slope);
+        if (tr) k_build_totals<double><<<grid, 256, 0, st>>>(t, ttot);
+    }
+    if (!tr && cudaMemsetAsync(ttot, 0, sizeof(double2) * (size_t)t.n_points, st) != cudaSuccess) return -1;
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
