@@ -89,6 +89,24 @@ def test_config1_fp32_tables(mcx):
     assert_tallies_close(g, ref)
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_source_above_the_grids(mcx, precision):
+    """A source at 5e7 eV, above every species' grid (top 2e7): the first
+    lookups fall in the grids' last intervals, where the transport lookup
+    clamps the interpolation fraction to 1 instead of using the stored
+    slopes; history-matched against the oracle's clamped definition."""
+    prob = synth.config1_problem(3000)
+    prob.E0 = 5.0e7
+    ref_prob = synth.config1_problem(3000)
+    ref_prob.E0 = 5.0e7
+    if precision:
+        ref_prob.lib = prob.lib.fp32_rounded()
+    ref = oracle.transport(ref_prob, seed=13, history_debug=True, n_threads=8)
+    g = run_gpu(mcx, prob, precision=precision, pif=1000, seed=13, mode=1, sort_period=0)
+    assert np.array_equal(g["ncoll"], ref["ncoll"])
+    assert_tallies_close(g, ref)
+
+
 @pytest.fixture(scope="module")
 def lattice():
     prob = synth.config3_problem(n_histories=5000)
