@@ -118,6 +118,7 @@ struct TableStore {
     float4* frec = nullptr;
     void* sigma = nullptr;
     double* awr = nullptr;
+    double* inv_a1sq = nullptr;   // per species 1 / (A + 1)^2
     int32_t* moff = nullptr;
     int32_t* msp = nullptr;
     double* mden = nullptr;
@@ -141,6 +142,7 @@ struct TableStore {
         dev_free(frec);
         if (sigma) cudaFree(sigma);
         dev_free(awr);
+        dev_free(inv_a1sq);
         dev_free(moff);
         dev_free(msp);
         dev_free(mden);
@@ -1069,13 +1071,16 @@ int mcx_load_xs_tables(mcx_problem* p, int32_t n_species, const int64_t* goff, c
     std::vector<double> winv((size_t)P, 0.0);
     for (int32_t s2 = 0; s2 < n_species; ++s2)
         for (int64_t k = goff[s2]; k + 1 < goff[s2 + 1]; ++k) winv[k] = 1.0 / (energies[k + 1] - energies[k]);
+    // elastic kinematics: E' = E (A^2 + 2 A mu + 1) / (A + 1)^2 multiplies by this
+    std::vector<double> inv_a1sq((size_t)n_species);
+    for (int32_t s2 = 0; s2 < n_species; ++s2) inv_a1sq[s2] = 1.0 / ((awr[s2] + 1.0) * (awr[s2] + 1.0));
     // two padding entries past the last energy: the staged lookup copies FP64
     // energies in 16-byte pairs and may read one entry past a species' end
     if ((rc = dev_alloc(&ts->goff, (size_t)n_species + 1)) || (rc = dev_alloc(&ts->E, (size_t)P + 2)) ||
         (rc = dev_alloc(&ts->winv, (size_t)P)) || (rc = dev_alloc(&ts->slope, (size_t)P * n_ch)) ||
         (rc = dev_alloc(&ts->ttot, (size_t)P)) ||
         (rc = dev_alloc(&ts->frec, (size_t)P * frec_w)) ||
-        (rc = dev_alloc(&ts->awr, (size_t)n_species)) || (rc = dev_alloc(&ts->moff, (size_t)n_materials + 1)) ||
+        (rc = dev_alloc(&ts->awr, (size_t)n_species)) || (rc = dev_alloc(&ts->inv_a1sq, (size_t)n_species)) || (rc = dev_alloc(&ts->moff, (size_t)n_materials + 1)) ||
         (rc = dev_alloc(&ts->msp, (size_t)nnz)) || (rc = dev_alloc(&ts->mden, (size_t)nnz)) ||
         (rc = dev_alloc(&ts->ment, (size_t)nnz)))
         return bail(rc);
@@ -1090,6 +1095,7 @@ int mcx_load_xs_tables(mcx_problem* p, int32_t n_species, const int64_t* goff, c
               cudaMemcpy(ts->winv, winv.data(), 8 * P, cudaMemcpyHostToDevice) == cudaSuccess &&
               cudaMemcpy(ts->frec, rec.data(), sizeof(float) * rec.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
               cudaMemcpy(ts->awr, awr, 8 * n_species, cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaMemcpy(ts->inv_a1sq, inv_a1sq.data(), 8 * n_species, cudaMemcpyHostToDevice) == cudaSuccess &&
               cudaMemcpy(ts->moff, moff, 4 * (n_materials + 1), cudaMemcpyHostToDevice) == cudaSuccess &&
               cudaMemcpy(ts->msp, msp, 4 * nnz, cudaMemcpyHostToDevice) == cudaSuccess &&
               cudaMemcpy(ts->mden, mden, 8 * nnz, cudaMemcpyHostToDevice) == cudaSuccess &&
@@ -1123,6 +1129,7 @@ int mcx_load_xs_tables(mcx_problem* p, int32_t n_species, const int64_t* goff, c
     v.frec_w = frec_w;
     v.sigma = ts->sigma;
     v.awr = ts->awr;
+    v.inv_a1sq = ts->inv_a1sq;
     v.moff = ts->moff;
     v.msp = ts->msp;
     v.mden = ts->mden;

@@ -52,6 +52,7 @@ struct Tables {
     int32_t frec_w = 0;
     const void* sigma = nullptr;
     const double* awr = nullptr;
+    const double* inv_a1sq = nullptr;   // per species 1 / (A + 1)^2 (elastic kinematics)
     const int32_t* moff = nullptr;
     const int32_t* msp = nullptr;
     const double* mden = nullptr;

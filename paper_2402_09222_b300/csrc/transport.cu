@@ -48,6 +48,12 @@
 #ifndef MCX_TRANSPORT_RECIP_DIR
 #define MCX_TRANSPORT_RECIP_DIR 1
 #endif
+// Elastic kinematics with the stored 1 / (A + 1)^2 and the rotation from one
+// reciprocal square root (rotate_raw): FP64 divisions and square roots are
+// multi-instruction sequences on B300's 1/64-rate FP64 pipe.
+#ifndef MCX_TRANSPORT_KINEMATICS
+#define MCX_TRANSPORT_KINEMATICS 1
+#endif
 
 namespace mcx {
 
@@ -165,6 +171,29 @@ __device__ __forceinline__ void azimuth(uint2 key, uint64_t h, uint32_t& n, doub
     }
     c = 1.0;
     s = 0.0;
+}
+
+// The same draws as azimuth, unnormalised: (a^2 - b^2, 2 a b) = rho (cos phi,
+// sin phi) and rho, so that the rotation can fold 1 / rho into its one
+// reciprocal square root.
+__device__ __forceinline__ void azimuth_raw(uint2 key, uint64_t h, uint32_t& n, double& c, double& s,
+                                           double& rho)
+{
+    for (int t = 0; t < MAX_AZIMUTH_TRIES; ++t) {
+        const double a = 2.0 * uniform_at(key, h, n) - 1.0;
+        const double b = 2.0 * uniform_at(key, h, n + 1) - 1.0;
+        n += 2;
+        const double r = a * a + b * b;
+        if (r > 0.0 && r <= 1.0) {
+            c = a * a - b * b;
+            s = 2.0 * a * b;
+            rho = r;
+            return;
+        }
+    }
+    c = 1.0;
+    s = 0.0;
+    rho = 1.0;
 }
 
 // Fission-spectrum energy: the Maxwellian sqrt(E) exp(-E/T), a Gamma(3/2, T)
@@ -310,6 +339,31 @@ __device__ __forceinline__ int32_t region_of(const ProblemDev& pd, const State& 
     return q.inpin ? q.ci * pd.lattice_n + q.cj : pd.lattice_n * pd.lattice_n;
 }
 
+// rotate() with (c, s) = rho (cos phi, sin phi) unnormalised: with
+// m = 1 - mu^2 and t = 1 - w0^2 (or 1 - v0^2), the factor sin(theta) /
+// (sqrt(t) rho) the rotation needs is m / sqrt(m t rho^2) -- one reciprocal
+// square root in place of two square roots and two divisions (the same
+// rotation up to rounding).
+__device__ __forceinline__ void rotate_raw(double& u, double& v, double& w, double mu, double c, double s,
+                                           double rho)
+{
+    const double u0 = u, v0 = v, w0 = w;
+    const double m = fma(-mu, mu, 1.0);
+    const bool wz = fabs(w0) < 0.9999;
+    const double t = wz ? fma(-w0, w0, 1.0) : fma(-v0, v0, 1.0);
+    const double aq = m > 0.0 ? m * rsqrt(m * t * (rho * rho)) : 0.0;
+    if (wz) {
+        u = fma(mu, u0, aq * fma(u0 * w0, c, -(v0 * s)));
+        v = fma(mu, v0, aq * fma(v0 * w0, c, u0 * s));
+        w = fma(mu, w0, -(aq * t * c));
+    } else {
+        u = fma(mu, u0, aq * fma(u0 * v0, c, w0 * s));
+        v = fma(mu, v0, -(aq * t * c));
+        w = fma(mu, w0, aq * fma(v0 * w0, c, -(u0 * s)));
+    }
+}
+
+#if !MCX_TRANSPORT_KINEMATICS
 __device__ __forceinline__ void rotate(double& u, double& v, double& w, double mu, double c, double s)
 {
     const double u0 = u, v0 = v, w0 = w;
@@ -342,6 +396,7 @@ __device__ __forceinline__ void rotate(double& u, double& v, double& w, double m
     }
 #endif
 }
+#endif
 
 __device__ __forceinline__ int64_t batch_of(const ProblemDev& pd, int64_t h)
 {
@@ -913,8 +968,12 @@ __global__ void __launch_bounds__(1024) k_collide(LoopConfig c, Tables t, Partic
                 const double A = __ldg(t.awr + j);
                 const double mu = 2.0 * xi3 - 1.0;
                 const double num = A * A + 2.0 * A * mu + 1.0;
+#if MCX_TRANSPORT_KINEMATICS
+                const double E_new = (E * num) * __ldg(t.inv_a1sq + j);   // (A + 1)^-2 stored per species
+#else
                 const double den = (A + 1.0) * (A + 1.0);
                 const double E_new = E * (num / den);
+#endif
                 if (E_new < pd.E_cut) {
                     dies = true;
                     outcome = OUT_CUTOFF;
@@ -926,10 +985,16 @@ __global__ void __launch_bounds__(1024) k_collide(LoopConfig c, Tables t, Partic
 #endif
                     if (mu_lab > 1.0) mu_lab = 1.0;
                     if (mu_lab < -1.0) mu_lab = -1.0;
+                    double u = P.u[slot], v = P.v[slot], w = P.w[slot];
+#if MCX_TRANSPORT_KINEMATICS
+                    double cr, sr, rho;
+                    azimuth_raw(pd.key, h, n, cr, sr, rho);
+                    rotate_raw(u, v, w, mu_lab, cr, sr, rho);
+#else
                     double cphi, sphi;
                     azimuth(pd.key, h, n, cphi, sphi);
-                    double u = P.u[slot], v = P.v[slot], w = P.w[slot];
                     rotate(u, v, w, mu_lab, cphi, sphi);
+#endif
                     P.u[slot] = u;
                     P.v[slot] = v;
                     P.w[slot] = w;
