@@ -54,6 +54,11 @@
 #ifndef MCX_TRANSPORT_KINEMATICS
 #define MCX_TRANSPORT_KINEMATICS 1
 #endif
+// The lookup kernel takes a warp per particle when the queue holds at most
+// one particle per warp of its grid (macro_transport_warp).
+#ifndef MCX_TRANSPORT_WARP_TAIL
+#define MCX_TRANSPORT_WARP_TAIL 1
+#endif
 
 namespace mcx {
 
@@ -672,6 +677,32 @@ __global__ void __launch_bounds__(1024) k_lookup(LoopConfig c, Tables t, Particl
     const int adv = RQ_ADV0 + ctl->adv_recv;
     const int64_t count = src.n;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+#if MCX_TRANSPORT_WARP_TAIL
+    // Few lookups (the tail of the loop): one warp per particle, all of them
+    // in one round of the grid; the same values as the per-thread path.
+    if (count * 32 <= stride) {
+        const int lane = lane_id();
+        const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+        if (w < count) {   // the whole warp
+            const int64_t slot = src_at(src, w);
+            const uint8_t f = P.flags[slot];
+            const bool act = (f & PF_NEED_XS) != 0;
+            if (act) {
+                double st, sa, nf = 0.0;
+                macro_transport_warp<T, EIG>(t, P.mat[slot], P.E[slot], st, sa, P.cum + slot * P.cum_stride,
+                                             &nf);
+                if (lane == 0) {
+                    if (EIG) P.sig_nf[slot] = nf;
+                    P.sig_t[slot] = st;
+                    P.sig_a[slot] = sa;
+                    P.flags[slot] = f & (uint8_t)~PF_NEED_XS;
+                }
+            }
+            if (fq) ring_push(P, ctl, adv, act && lane == 0, slot);
+        }
+        return;
+    }
+#endif
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < count; base += stride) {
         const int64_t i = base + threadIdx.x;
         int64_t slot = -1;

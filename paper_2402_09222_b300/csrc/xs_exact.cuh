@@ -193,4 +193,45 @@ __device__ __forceinline__ void macro_transport(const Tables& t, int32_t m, doub
     if (NF) *sig_nf = nf;
 }
 
+// macro_transport for one particle on a whole converged warp, for when few
+// particles need a lookup (the tail of an event loop, where one thread's
+// chain of dependent loads over a material's species is the latency of the
+// whole iteration): lane s evaluates species i0 + s, i0 + 32 + s, ... (all
+// their load chains in flight at once), then every lane adds the terms in
+// species order with the same fused multiply-adds -- bit-identical to
+// macro_transport; lane 0 stores the running sums.
+template <typename T, bool NF = false>
+__device__ __forceinline__ void macro_transport_warp(const Tables& t, int32_t m, double E, double& sig_t,
+                                                     double& sig_a, double* cum, double* sig_nf = nullptr)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t eb = search_key(E);
+    const int32_t hb = t.H > 0 ? hash_bin(t, E, eb) : 0;
+    const int32_t i0 = __ldg(t.moff + m), i1 = __ldg(t.moff + m + 1);
+    double st = 0.0, sa = 0.0, nf = 0.0;
+    for (int32_t i = i0; i < i1; i += 32) {
+        const int32_t ii = i + lane;
+        double N = 0.0, c = 0.0, a = 0.0, v = 0.0;
+        if (ii < i1) {
+            N = __ldg(t.mden + ii);
+            const int4 e = __ldg(t.ment + ii);
+            int32_t base, len;
+            search_window(t, e, hb, base, len);
+            for (int s = 0; s < t.search_steps; ++s) search_step(t.E, base, len, eb);
+            species_transport<T, NF>(t, E, base, e.x + e.y - 2, c, a, v);
+        }
+        const int n = i1 - i < 32 ? i1 - i : 32;
+        for (int s = 0; s < n; ++s) {
+            const double Ns = __shfl_sync(0xffffffffu, N, s);
+            st = fma(Ns, __shfl_sync(0xffffffffu, c, s), st);
+            sa = fma(Ns, __shfl_sync(0xffffffffu, a, s), sa);
+            if (NF) nf = fma(Ns, __shfl_sync(0xffffffffu, v, s), nf);
+            if (lane == 0) cum[i + s - i0] = st;
+        }
+    }
+    sig_t = st;
+    sig_a = sa;
+    if (NF) *sig_nf = nf;
+}
+
 }  // namespace mcx
