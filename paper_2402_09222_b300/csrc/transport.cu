@@ -1242,25 +1242,49 @@ __global__ void k_sort_scan(LoopConfig c, Particles P, RunCtl* ctl)
     }
 }
 
+// Scatter into the binned list.  Each round a block takes blockDim.x *
+// kSortPer entries; their ranks within the round come from a shared-memory
+// histogram, and one global atomic per non-empty bin reserves the round's
+// range of that bin (instead of one per distinct key per warp, all
+// contending on the same few hundred counters).  The order inside a bin is
+// free: no result depends on it.
+constexpr int kSortPer = 8;
 __global__ void k_sort_scatter(LoopConfig c, Particles P, RunCtl* ctl, int which)
 {
+    extern __shared__ uint32_t sh[];
     if (!ctl->sorted) return;
     const Src src = sort_source(P, ctl, which);
     const int64_t n = src.n;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
-        const int64_t i = base + threadIdx.x;
-        const bool valid = i < n;
-        const unsigned vm = __ballot_sync(FULL, valid);
-        if (!valid) continue;
-        const int32_t s = (int32_t)src_at(src, i);
-        const int key = sort_key(c, P.E[s], P.mat[s]);
-        const unsigned grp = __match_any_sync(vm, key);
-        const int leader = __ffs(grp) - 1;
-        uint32_t pos = 0u;
-        if (lane_id() == leader) pos = atomicAdd(&P.bins[key], (uint32_t)__popc(grp));
-        pos = __shfl_sync(grp, pos, leader);
-        P.q_sorted[pos + __popc(grp & lanes_below())] = s;
+    const int nb = c.n_sort_bins;
+    const int64_t tile = (int64_t)blockDim.x * kSortPer;
+    for (int64_t base = (int64_t)blockIdx.x * tile; base < n; base += (int64_t)gridDim.x * tile) {
+        for (int b = threadIdx.x; b < nb; b += blockDim.x) sh[b] = 0u;
+        __syncthreads();
+        int32_t sl[kSortPer];
+        int key[kSortPer];
+        uint32_t rank[kSortPer];
+#pragma unroll
+        for (int r = 0; r < kSortPer; ++r) {
+            const int64_t i = base + (int64_t)r * blockDim.x + threadIdx.x;
+            key[r] = -1;
+            sl[r] = 0;
+            rank[r] = 0u;
+            if (i < n) {
+                sl[r] = (int32_t)src_at(src, i);
+                key[r] = sort_key(c, P.E[sl[r]], P.mat[sl[r]]);
+                rank[r] = atomicAdd(&sh[key[r]], 1u);
+            }
+        }
+        __syncthreads();
+        for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+            const uint32_t cnt = sh[b];
+            if (cnt) sh[b] = atomicAdd(&P.bins[b], cnt);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < kSortPer; ++r)
+            if (key[r] >= 0) P.q_sorted[sh[key[r]] + rank[r]] = sl[r];
+        __syncthreads();
     }
 }
 
@@ -1281,7 +1305,7 @@ static int launch_sort(const LoopConfig& c, const Particles& P, RunCtl* ctl, int
     k_sort_decide<<<1, 1, 0, st>>>(c, ctl, which);
     k_sort_count<<<c.grid, c.block, sizeof(uint32_t) * c.n_sort_bins, st>>>(c, P, ctl, which);
     k_sort_scan<<<1, 1024, 0, st>>>(c, P, ctl);
-    k_sort_scatter<<<c.grid, c.block, 0, st>>>(c, P, ctl, which);
+    k_sort_scatter<<<c.grid, c.block, sizeof(uint32_t) * c.n_sort_bins, st>>>(c, P, ctl, which);
     return 4;
 }
 
