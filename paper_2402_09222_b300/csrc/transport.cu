@@ -54,6 +54,11 @@
 #ifndef MCX_TRANSPORT_KINEMATICS
 #define MCX_TRANSPORT_KINEMATICS 1
 #endif
+// A flight divides once: the surface candidates and the collision distance
+// are compared as quotients by cross-multiplication (surface_candidate).
+#ifndef MCX_TRANSPORT_ONE_DIV
+#define MCX_TRANSPORT_ONE_DIV 1
+#endif
 // The lookup kernel takes a warp per particle when the queue holds at most
 // one particle per warp of its grid (macro_transport_warp).
 #ifndef MCX_TRANSPORT_WARP_TAIL
@@ -221,6 +226,7 @@ struct State {
     int32_t ci, cj, inpin;
 };
 
+#if !MCX_TRANSPORT_ONE_DIV
 // Distance to the nearest surface along the flight.  Candidates are compared
 // in a fixed order with strict '<' (earlier candidates win ties).
 __device__ double surface_distance(const ProblemDev& pd, const State& q, int& surf)
@@ -303,6 +309,56 @@ __device__ double surface_distance(const ProblemDev& pd, const State& q, int& su
     }
     if (d < 0.0) d = 0.0;
     return d;
+}
+#endif
+
+// The same candidates as surface_distance, in the same order and with the
+// same strict '<' between them, each kept as a quotient t = num / den with
+// den > 0 and compared by cross-multiplication (t1 < t2 iff num1 den2 <
+// num2 den1), so that a flight divides once, for the distance it takes.
+// Returns den = 0 when no surface is ahead.
+__device__ void surface_candidate(const ProblemDev& pd, const State& q, int& surf, double& num, double& den)
+{
+    num = 0.0;
+    den = 0.0;
+    surf = S_NONE;
+    auto offer = [&](double n, double m, int s) {
+        if (den == 0.0 || n * den < num * m) {
+            num = n;
+            den = m;
+            surf = s;
+        }
+    };
+    if (pd.geometry == MCX_GEOM_INFINITE) return;
+    if (pd.geometry == MCX_GEOM_SLAB) {
+        if (q.u > 0.0) offer(pd.slab_length - q.x, q.u, S_XHI);
+        else if (q.u < 0.0) offer(q.x, -q.u, S_XLO);
+        return;
+    }
+    if (q.w > 0.0) offer(pd.height - q.z, q.w, S_ZTOP);
+    else if (q.w < 0.0) offer(q.z, -q.w, S_ZBOT);
+    const double cx = __ldg(pd.lat_centre + q.ci);
+    const double cy = __ldg(pd.lat_centre + q.cj);
+    const double dx = q.x - cx, dy = q.y - cy;
+    const double a = fma(q.u, q.u, q.v * q.v);
+    const double k = fma(dx, q.u, dy * q.v);
+    const double c = fma(dx, dx, fma(dy, dy, -(pd.radius * pd.radius)));
+    if (q.inpin) {
+        if (a > 0.0) {
+            double disc = fma(k, k, -(a * c));
+            if (disc < 0.0) disc = 0.0;
+            offer(-k + sqrt(disc), a, S_CYL);
+        }
+    } else if (a > 0.0 && k < 0.0) {
+        const double disc = fma(k, k, -(a * c));
+        if (disc >= 0.0) offer(-k - sqrt(disc), a, S_CYL);
+    }
+    if (!q.inpin) {
+        if (q.u > 0.0) offer(__ldg(pd.lat_plane + q.ci + 1) - q.x, q.u, S_XHI);
+        else if (q.u < 0.0) offer(q.x - __ldg(pd.lat_plane + q.ci), -q.u, S_XLO);
+        if (q.v > 0.0) offer(__ldg(pd.lat_plane + q.cj + 1) - q.y, q.v, S_YHI);
+        else if (q.v < 0.0) offer(q.y - __ldg(pd.lat_plane + q.cj), -q.v, S_YLO);
+    }
 }
 
 // Logical crossing; returns the outcome if the particle leaves, else -1.
@@ -774,11 +830,31 @@ __global__ void __launch_bounds__(1024) k_advance(LoopConfig c, Particles P, con
             n += 1;
             const double sig_t = P.sig_t[slot], sig_a = P.sig_a[slot];
             m = P.mat[slot];
-            const double dcol = sig_t > 0.0 ? -log(xi) / sig_t : INF;
             int surf;
+#if MCX_TRANSPORT_ONE_DIV
+            // collide iff the surface's t = num / den exceeds L / Sigma_t
+            // (num Sigma_t > L den, den > 0): one division, for the distance taken
+            const double L = -log(xi);
+            double sn, sd;
+            surface_candidate(pd, q, surf, sn, sd);
+            bool collide;
+            if (!(sig_t > 0.0)) collide = false;
+            else if (sd == 0.0) collide = true;
+            else collide = !(sn * sig_t <= L * sd);
+            if (collide) {
+                d = L / sig_t;
+            } else if (sd == 0.0) {
+                d = INF;
+            } else {
+                d = sn / sd;
+                if (d < 0.0) d = 0.0;
+            }
+#else
+            const double dcol = sig_t > 0.0 ? -log(xi) / sig_t : INF;
             const double dsurf = surface_distance(pd, q, surf);
             const bool collide = !(dsurf <= dcol);
             d = collide ? dcol : dsurf;
+#endif
             uint8_t fl = P.flags[slot];
             if (isinf(d)) {
                 dies = true;
