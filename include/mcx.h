@@ -391,6 +391,12 @@ int mcx_xs_lookup_backward(mcx_problem* p, int64_t n, const double* E, const int
 int mcx_debug_uniforms(uint64_t seed, uint32_t problem_id, uint64_t hist, uint32_t first,
                        int64_t n, double* out, void* stream);
 
+/* Test hook: the flight length -ln x as the transport computes it (a
+ * table-driven logarithm, Tang 1990) and as the CUDA library computes it,
+ * for n values x in [2^-53, 1) (the range of the uniforms; others are out of
+ * its domain) in a DEVICE buffer; out [n][2] (DEVICE) receives the pairs. */
+int mcx_debug_neg_log(const double* x, int64_t n, double* out, void* stream);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* mcx_last_error(void);
 

@@ -44,6 +44,7 @@ int launch_xs_backward(const Tables& t, int64_t n, const double* E, const int32_
 int launch_update_tables(const Tables& t, const double* dens_src, int64_t nnz, double* mden,
                          int4* ment, const double* sig_src, void* sigma, float4* frec,
                          cudaStream_t st);
+int launch_debug_neg_log(const double* x, int64_t n, double* out, cudaStream_t st);
 int launch_debug_uniforms(uint2 key, uint64_t hist, uint32_t first, int64_t n, double* out,
                           cudaStream_t st);
 

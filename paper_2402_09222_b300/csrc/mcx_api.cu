@@ -1511,6 +1511,17 @@ int mcx_debug_uniforms(uint64_t seed, uint32_t problem_id, uint64_t hist, uint32
     return MCX_OK;
 }
 
+int mcx_debug_neg_log(const double* x, int64_t n, double* out, void* stream)
+{
+    g_err.clear();
+    if (n < 0) return fail(MCX_ERR_ARG, "n must be >= 0");
+    if (n == 0) return MCX_OK;
+    if (!x || !out) return fail(MCX_ERR_ARG, "NULL buffer");
+    if (launch_debug_neg_log(x, n, out, (cudaStream_t)stream))
+        return fail(MCX_ERR_CUDA, "logarithm kernel launch failed");
+    return MCX_OK;
+}
+
 int mcx_run_eigenvalue(mcx_problem* p, int64_t n_per_gen, int32_t n_generations, int32_t n_inactive,
                        double k0, double T_fission, int64_t particles_in_flight, uint64_t seed,
                        double* gen_out, void* stream)

@@ -59,6 +59,11 @@
 #ifndef MCX_TRANSPORT_ONE_DIV
 #define MCX_TRANSPORT_ONE_DIV 1
 #endif
+// The flight length -ln(xi) from a table-driven logarithm (neg_log_uniform)
+// instead of the library's.
+#ifndef MCX_TRANSPORT_TABLE_LOG
+#define MCX_TRANSPORT_TABLE_LOG 1
+#endif
 // The lookup kernel takes a warp per particle when the queue holds at most
 // one particle per warp of its grid (macro_transport_warp).
 #ifndef MCX_TRANSPORT_WARP_TAIL
@@ -156,6 +161,52 @@ __device__ __forceinline__ void warp_add(double* a, double v, bool on)
     double s = on ? v : 0.0;
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
     if (lane_id() == __ffs(m) - 1) atomicAdd(a, s);
+}
+
+// -ln x for a uniform x in [2^-53, 1) (uniform_at's range), by Tang's
+// table-driven method (P. T. P. Tang, ACM Trans. Math. Softw. 16, 378,
+// 1990): x = 2^-t (F + f) with F = 1 + j/256 the leading 8 bits of the
+// mantissa (so f = m - F is exact), and -ln x = t ln 2 - ln F - ln(1 + r),
+// r = f / F < 2^-8, the last from its Taylor series to r^6 (remainder below
+// 2^-59).  The table holds ln F_j, 1 / F_j and t ln 2, computed on the device
+// with the library's logarithm and division.  About ten FP64 operations; the
+// error is an ulp or two of max(1, -ln x) -- like the library's against the
+// host's, not relative near x = 1 where -ln x is tiny (a flight of ~1e-16
+// cm may come out a few 1e-17 cm longer or shorter).
+constexpr int kNlN = 256;                     // table intervals of the mantissa
+constexpr int kNlSize = 2 * kNlN + 64;        // ln F_j, 1 / F_j, t ln 2 (t < 64)
+__device__ double g_nlog[kNlSize];
+
+__global__ void k_init_nlog()
+{
+    for (int i = threadIdx.x; i < kNlSize; i += blockDim.x) {
+        double v;
+        if (i < kNlN) v = log(1.0 + i / 256.0);
+        else if (i < 2 * kNlN) v = 1.0 / (1.0 + (i - kNlN) / 256.0);
+        else v = log(ldexp(1.0, i - 2 * kNlN));
+        g_nlog[i] = v;
+    }
+}
+
+__device__ __forceinline__ double neg_log_uniform(double x)
+{
+#if MCX_TRANSPORT_TABLE_LOG
+    const uint64_t b = (uint64_t)__double_as_longlong(x);
+    const int t = 1023 - (int)(b >> 52);                  // 1 .. 53 for x in [2^-53, 1)
+    const uint64_t top = b & 0x000FF00000000000ull;       // leading 8 mantissa bits
+    const int j = (int)(top >> 44);
+    const double m = __longlong_as_double((long long)((b & 0x000FFFFFFFFFFFFFull) | 0x3FF0000000000000ull));
+    const double F = __longlong_as_double((long long)(top | 0x3FF0000000000000ull));
+    const double r = (m - F) * __ldg(&g_nlog[kNlN + j]);
+    double q = fma(r, -1.0 / 6.0, 0.2);
+    q = fma(r, q, -0.25);
+    q = fma(r, q, 1.0 / 3.0);
+    q = fma(r, q, -0.5);
+    q = fma(r, q, 1.0);
+    return (__ldg(&g_nlog[2 * kNlN + t]) - __ldg(&g_nlog[j])) - r * q;
+#else
+    return -log(x);
+#endif
 }
 
 // Azimuth (cos phi, sin phi) by rejection on pairs (2u-1, 2u-1) inside the
@@ -834,7 +885,7 @@ __global__ void __launch_bounds__(1024) k_advance(LoopConfig c, Particles P, con
 #if MCX_TRANSPORT_ONE_DIV
             // collide iff the surface's t = num / den exceeds L / Sigma_t
             // (num Sigma_t > L den, den > 0): one division, for the distance taken
-            const double L = -log(xi);
+            const double L = neg_log_uniform(xi);
             double sn, sd;
             surface_candidate(pd, q, surf, sn, sd);
             bool collide;
@@ -1369,6 +1420,7 @@ __global__ void k_sort_scatter(LoopConfig c, Particles P, RunCtl* ctl, int which
 int launch_run_init(const LoopConfig& c, const Particles& P, RunCtl* ctl, long long total,
                     int n_prob, long long max_iters, cudaStream_t st)
 {
+    k_init_nlog<<<1, 256, 0, st>>>();   // the flight-length table (same values every time)
     k_run_init<<<c.grid, 256, 0, st>>>(P, ctl, total, n_prob, max_iters, c.mode);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
@@ -1441,6 +1493,23 @@ __global__ void k_debug_uniforms(uint2 key, uint64_t hist, uint32_t first, int64
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
         out[i] = uniform_at(key, hist, first + (uint32_t)i);
+}
+
+__global__ void k_debug_neg_log(const double* __restrict__ x, int64_t n, double* __restrict__ out)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        out[2 * i] = neg_log_uniform(x[i]);
+        out[2 * i + 1] = -log(x[i]);
+    }
+}
+
+int launch_debug_neg_log(const double* x, int64_t n, double* out, cudaStream_t st)
+{
+    k_init_nlog<<<1, 256, 0, st>>>();
+    const int grid = (int)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024);
+    k_debug_neg_log<<<grid > 0 ? grid : 1, 256, 0, st>>>(x, n, out);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 int launch_debug_uniforms(uint2 key, uint64_t hist, uint32_t first, int64_t n, double* out,

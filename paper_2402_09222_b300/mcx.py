@@ -101,6 +101,7 @@ _sig("mcx_xs_lookup_host", C.c_int, _vp, _i64, _vp, _vp, _vp, _i32)
 _sig("mcx_xs_indices", C.c_int, _vp, _i64, _vp, _vp, _i32, _vp, _vp)
 _sig("mcx_xs_lookup_backward", C.c_int, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp)
 _sig("mcx_debug_uniforms", C.c_int, C.c_uint64, C.c_uint32, C.c_uint64, C.c_uint32, _i64, _vp, _vp)
+_sig("mcx_debug_neg_log", C.c_int, _vp, _i64, _vp, _vp)
 
 
 def _check(rc: int):
@@ -398,6 +399,16 @@ def batch_run(problems, n_hist, particles_in_flight: int, seed: int, stream=None
     nh = np.ascontiguousarray(n_hist, np.int64)
     _check(_lib.mcx_batch_run(len(problems), C.cast(arr, _vp), _np_ptr(nh), particles_in_flight,
                               seed, _stream_ptr(stream)))
+
+
+def debug_neg_log(x):
+    """(-ln x as the transport computes it, as the CUDA library does) for a
+    device FP64 tensor x of uniforms in [2^-53, 1); returns an [n, 2] tensor."""
+    import torch
+    out = torch.empty((x.numel(), 2), dtype=torch.float64, device=x.device)
+    _check(_lib.mcx_debug_neg_log(_dev_ptr(x, torch.float64, "x"), x.numel(), _vp(out.data_ptr()),
+                                  _stream_ptr(None)))
+    return out
 
 
 def debug_uniforms(seed: int, problem_id: int, hist: int, n: int, first: int = 0, device: int = 0):

@@ -55,3 +55,24 @@ def test_philox_core_equals_curand(torch_cuda):
     # and the raw words agree with the oracle's implementation
     for i in range(0, n, 211):
         assert np.array_equal(oracle.philox4x32_10(ctr[i], key[i]), w[i])
+
+
+def test_flight_length_logarithm(torch_cuda):
+    """The transport's table-driven -ln x (Tang 1990) on 1e6 uniforms of a
+    history stream and on the ends of its range (2^-53, around 1/2, 1 - 2^-53)
+    and at table boundaries: within 3 ulp of max(1, -ln x) of the host's
+    logarithm, as the CUDA library's own is within 1 ulp of it."""
+    from paper_2402_09222_b300 import mcx
+    torch = torch_cuda
+    u = mcx.debug_uniforms(7, 0, 123, 1_000_000)
+    edge = [2.0**-53, 3 * 2.0**-53, 2.0**-20, 0.25, 0.5 - 2.0**-54, 0.5, 0.5 + 2.0**-53, 0.75,
+            1 / 3, 1 - 2.0**-53, 1 - 2.0**-40, (1 + 1 / 256) / 2, (1 + 255 / 256) / 2 - 2.0**-53]
+    x = torch.cat([u, torch.tensor(edge, dtype=torch.float64, device=u.device)])
+    out = mcx.debug_neg_log(x).cpu().numpy()
+    ref = -np.log(x.cpu().numpy())
+    scale = np.maximum(1.0, ref) * 2.0**-52
+    err_table = np.abs(out[:, 0] - ref) / scale
+    err_lib = np.abs(out[:, 1] - ref) / scale
+    assert err_lib.max() <= 1.0, err_lib.max()
+    assert err_table.max() <= 3.0, err_table.max()
+    assert np.all(out[:, 0] > 0)
