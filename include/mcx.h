@@ -56,7 +56,10 @@ extern "C" {
 /* Event logic (Sec. 5.1, "queuing logic"). */
 #define MCX_QUEUELESS 0       /* every event kernel visits every slot */
 #define MCX_QUEUED 1          /* every event kernel runs each iteration over its
-                                 device-built compacted queue */
+                                 device-built compacted queue (the flight,
+                                 whose queue holds every live particle, over
+                                 the slots while at least three quarters of
+                                 them are live) */
 #define MCX_QUEUED_FULLEST 2  /* the paper's queued policy, decided on the device:
                                  each step runs only the event kernel whose
                                  queue (needs lookup / flight / collision /

@@ -847,7 +847,14 @@ __global__ void __launch_bounds__(1024) k_advance(LoopConfig c, Particles P, con
     if (fq && ctl->sel != SEL_ADV) return;
     const int par = ctl->parity;
     Src src = all_slots(P);
-    if (queued) src = plain_list(P.q_adv[par], ctl->n_adv[par]);
+    // Queued mode: the list holds every live particle (each flies once per
+    // iteration); when it covers at least three quarters of the slots the
+    // flight scans the slots instead (coalesced state loads, not the order
+    // the previous kernels wrote the list in); the tail of the loop, and the
+    // emptying slots of an eigenvalue generation, read the list
+    // (1.402e7 -> 1.467e7 particles/s against always scanning; eigenvalue
+    // 5.03e6 -> 6.04e6).
+    if (queued && (int64_t)ctl->n_adv[par] * 4 < P.cap * 3) src = plain_list(P.q_adv[par], ctl->n_adv[par]);
     else if (fq) src = ring_segment(P, ctl);
     const int adv = RQ_ADV0 + ctl->adv_recv;   // the ring not being read
     const int64_t count = src.n;
