@@ -36,6 +36,10 @@ int launch_build_hash(const Tables& t, int32_t* hidx, int grid, cudaStream_t st)
 // per point the total t = s_scatter + s_absorb with its slope into ttot
 // (libraries with the transport's channels, else zeros).
 int launch_build_slopes(const Tables& t, double* slope, double2* ttot, int grid, cudaStream_t st);
+// The transport's per-point values (grid energy, total, absorption, nu-
+// fission and their slopes, from E, ttot, slope and sigma) as FP32 pairs into
+// tpair [n_points][t.tpair_w], and the nnz densities as pairs into mden2.
+int launch_build_pairs(const Tables& t, float4* tpair, float2* mden2, int64_t nnz, int grid, cudaStream_t st);
 // Widest hash window (in grid points, window end inclusive) into *out (device int).
 int launch_hash_max_window(const Tables& t, int32_t* out, int grid, cudaStream_t st);
 int launch_xs_backward(const Tables& t, int64_t n, const double* E, const int32_t* mat,

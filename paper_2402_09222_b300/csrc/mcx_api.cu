@@ -115,6 +115,8 @@ struct TableStore {
     double* winv = nullptr;   // per interval 1 / (g[k+1] - g[k]) (transport)
     double* slope = nullptr;  // per interval and channel, from the device sigma table (transport)
     double2* ttot = nullptr;  // per point total of scatter and absorption and its slope (transport)
+    float4* tpair = nullptr;  // the transport's values as FP32 pairs
+    float2* mden2 = nullptr;  // densities as FP32 pairs
     float4* frec = nullptr;
     void* sigma = nullptr;
     double* awr = nullptr;
@@ -139,6 +141,8 @@ struct TableStore {
         dev_free(winv);
         dev_free(slope);
         dev_free(ttot);
+        dev_free(tpair);
+        dev_free(mden2);
         dev_free(frec);
         if (sigma) cudaFree(sigma);
         dev_free(awr);
@@ -1079,6 +1083,7 @@ int mcx_load_xs_tables(mcx_problem* p, int32_t n_species, const int64_t* goff, c
     if ((rc = dev_alloc(&ts->goff, (size_t)n_species + 1)) || (rc = dev_alloc(&ts->E, (size_t)P + 2)) ||
         (rc = dev_alloc(&ts->winv, (size_t)P)) || (rc = dev_alloc(&ts->slope, (size_t)P * n_ch)) ||
         (rc = dev_alloc(&ts->ttot, (size_t)P)) ||
+        (rc = dev_alloc(&ts->tpair, (size_t)P * (n_ch == 2 ? 3 : 4))) || (rc = dev_alloc(&ts->mden2, (size_t)nnz)) ||
         (rc = dev_alloc(&ts->frec, (size_t)P * frec_w)) ||
         (rc = dev_alloc(&ts->awr, (size_t)n_species)) || (rc = dev_alloc(&ts->inv_a1sq, (size_t)n_species)) || (rc = dev_alloc(&ts->moff, (size_t)n_materials + 1)) ||
         (rc = dev_alloc(&ts->msp, (size_t)nnz)) || (rc = dev_alloc(&ts->mden, (size_t)nnz)) ||
@@ -1125,6 +1130,9 @@ int mcx_load_xs_tables(mcx_problem* p, int32_t n_species, const int64_t* goff, c
     v.winv = ts->winv;
     v.slope = ts->slope;
     v.ttot = ts->ttot;
+    v.tpair = ts->tpair;
+    v.tpair_w = n_ch == 2 ? 3 : 4;
+    v.mden2 = ts->mden2;
     v.frec = ts->frec;
     v.frec_w = frec_w;
     v.sigma = ts->sigma;
@@ -1140,7 +1148,9 @@ int mcx_load_xs_tables(mcx_problem* p, int32_t n_species, const int64_t* goff, c
     ts->emax = emax;
     ts->nnz = nnz;
     ts->h_moff.assign(moff, moff + n_materials + 1);
-    if (launch_build_slopes(v, ts->slope, ts->ttot, p->sm_count * 8, nullptr) || cudaDeviceSynchronize() != cudaSuccess)
+    if (launch_build_slopes(v, ts->slope, ts->ttot, p->sm_count * 8, nullptr) ||
+        launch_build_pairs(v, ts->tpair, ts->mden2, ts->nnz ? ts->nnz : nnz, p->sm_count * 8, nullptr) ||
+        cudaDeviceSynchronize() != cudaSuccess)
         return bail(fail(MCX_ERR_CUDA, "slope table build failed"));
     if ((rc = build_hash(ts, hash_bins, p->sm_count)) != MCX_OK) return bail(rc);
     drop_graph(p);
@@ -1200,6 +1210,9 @@ int mcx_set_densities(mcx_problem* p, const double* mden, int64_t nnz)
     for (int64_t i = 0; i < nnz; ++i) ts->h_ment[i].w = float_bits((float)mden[i]);
     CUDA_TRY(cudaMemcpy(ts->mden, mden, 8 * nnz, cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(ts->ment, ts->h_ment.data(), sizeof(int4) * nnz, cudaMemcpyHostToDevice));
+    if (launch_build_pairs(ts->view, ts->tpair, ts->mden2, nnz, p->sm_count * 8, nullptr))
+        return fail(MCX_ERR_CUDA, "pair table launch failed");
+    CUDA_TRY(cudaDeviceSynchronize());
     return MCX_OK;
 }
 
@@ -1218,6 +1231,8 @@ int mcx_update_tables_device(mcx_problem* p, const double* mat_dens, const doubl
     // the transport's interval slopes follow the new sigma table, on the same stream
     if (sigma && launch_build_slopes(ts->view, ts->slope, ts->ttot, p->sm_count * 8, (cudaStream_t)stream))
         return fail(MCX_ERR_CUDA, "slope table launch failed");
+    if (launch_build_pairs(ts->view, ts->tpair, ts->mden2, ts->nnz, p->sm_count * 8, (cudaStream_t)stream))
+        return fail(MCX_ERR_CUDA, "pair table launch failed");
     return MCX_OK;
 }
 

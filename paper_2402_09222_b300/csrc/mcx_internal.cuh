@@ -48,6 +48,13 @@ struct Tables {
     const double* winv = nullptr;   // per interval 1 / (g[k+1] - g[k])
     const double* slope = nullptr;  // per interval and channel (s[k+1] - s[k]) / (g[k+1] - g[k]) (transport)
     const double2* ttot = nullptr;  // per point {s_scatter + s_absorb, its interval slope} (transport)
+    // Transport values as FP32 pairs (hi, lo = the rest), tpair_w float4 per
+    // point: {g, total}, {total slope, absorption}, {absorption slope,
+    // nu-fission}, {nu-fission slope, 0, 0}; and per material entry the
+    // density as a pair.
+    const float4* tpair = nullptr;
+    int32_t tpair_w = 0;
+    const float2* mden2 = nullptr;
     const float4* frec = nullptr;   // fast-path point records, frec_w float4 each
     int32_t frec_w = 0;
     const void* sigma = nullptr;

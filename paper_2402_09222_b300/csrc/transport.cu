@@ -796,8 +796,13 @@ __global__ void __launch_bounds__(1024) k_lookup(LoopConfig c, Tables t, Particl
             const bool act = (f & PF_NEED_XS) != 0;
             if (act) {
                 double st, sa, nf = 0.0;
+#if MCX_TRANSPORT_PAIRS
+                macro_transport_pair_warp<EIG>(t, P.mat[slot], P.E[slot], st, sa,
+                                               reinterpret_cast<float2*>(P.cum + slot * P.cum_stride), &nf);
+#else
                 macro_transport_warp<T, EIG>(t, P.mat[slot], P.E[slot], st, sa, P.cum + slot * P.cum_stride,
                                              &nf);
+#endif
                 if (lane == 0) {
                     if (EIG) P.sig_nf[slot] = nf;
                     P.sig_t[slot] = st;
@@ -820,6 +825,16 @@ __global__ void __launch_bounds__(1024) k_lookup(LoopConfig c, Tables t, Particl
             if (f & PF_NEED_XS) {
                 act = true;
                 double st, sa;
+#if MCX_TRANSPORT_PAIRS
+                float2* cum2 = reinterpret_cast<float2*>(P.cum + slot * P.cum_stride);
+                if (EIG) {
+                    double nf;
+                    macro_transport_pair<true>(t, P.mat[slot], P.E[slot], st, sa, cum2, &nf);
+                    P.sig_nf[slot] = nf;
+                } else {
+                    macro_transport_pair<false>(t, P.mat[slot], P.E[slot], st, sa, cum2);
+                }
+#else
                 if (EIG) {
                     double nf;
                     macro_transport<T, true>(t, P.mat[slot], P.E[slot], st, sa,
@@ -828,6 +843,7 @@ __global__ void __launch_bounds__(1024) k_lookup(LoopConfig c, Tables t, Particl
                 } else {
                     macro_transport<T>(t, P.mat[slot], P.E[slot], st, sa, P.cum + slot * P.cum_stride);
                 }
+#endif
                 P.sig_t[slot] = st;
                 P.sig_a[slot] = sa;
                 P.flags[slot] = f & (uint8_t)~PF_NEED_XS;
@@ -1108,14 +1124,27 @@ __global__ void __launch_bounds__(1024) k_collide(LoopConfig c, Tables t, Partic
             // if none.  C is non-decreasing and non-negative, so a binary
             // search on the bit patterns finds the first C_i > target.
             const int32_t i0 = __ldg(t.moff + m), n_sp = __ldg(t.moff + m + 1) - i0;
+            int32_t lo = 0, hi = n_sp - 1;
+#if MCX_TRANSPORT_PAIRS
+            // C_i are normalised FP32 pairs, so their order is the order of
+            // (hi, lo); the target is compared as a pair too
+            const float2* cum2 = reinterpret_cast<const float2*>(P.cum + slot * P.cum_stride);
+            const float2 tp = energy_pair(target);
+            while (lo < hi) {
+                const int32_t mid = (lo + hi) >> 1;
+                const float2 cm = cum2[mid];
+                if (tp.x < cm.x || (tp.x == cm.x && tp.y < cm.y)) hi = mid;
+                else lo = mid + 1;
+            }
+#else
             const double* cum = P.cum + slot * P.cum_stride;
             const int64_t tb = ebits(target);
-            int32_t lo = 0, hi = n_sp - 1;
             while (lo < hi) {
                 const int32_t mid = (lo + hi) >> 1;
                 if (tb < ebits(cum[mid])) hi = mid;
                 else lo = mid + 1;
             }
+#endif
             const int32_t j = __ldg(t.msp + i0 + lo);
             double st_j, sa_j;
             {

@@ -177,6 +177,49 @@ int launch_build_slopes(const Tables& t, double* slope, double2* ttot, int grid,
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
+// x as an FP32 pair: hi = x rounded to FP32, lo = the rest rounded to FP32.
+__device__ __forceinline__ float2 split_pair(double x)
+{
+    const float h = (float)x;
+    return make_float2(h, (float)(x - (double)h));
+}
+
+template <typename T>
+__global__ void k_build_pairs(Tables t, float4* __restrict__ tpair, float2* __restrict__ mden2, int64_t nnz)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int nc = t.n_ch, ca = t.ch_absorb, cf = t.ch_nu_fission;
+    const bool tr = t.ch_scatter >= 0 && t.ch_scatter < nc && ca >= 0 && ca < nc;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < t.n_points; p += stride) {
+        const float2 g = split_pair(t.E[p]);
+        float2 tot = make_float2(0.f, 0.f), slt = tot, sa = tot, sla = tot, sf = tot, slf = tot;
+        if (tr) {
+            tot = split_pair(t.ttot[p].x);
+            slt = split_pair(t.ttot[p].y);
+            sa = split_pair(sig_at<T>(t.sigma, p * nc + ca));
+            sla = split_pair(t.slope[p * nc + ca]);
+            if (cf >= 0 && cf < nc) {
+                sf = split_pair(sig_at<T>(t.sigma, p * nc + cf));
+                slf = split_pair(t.slope[p * nc + cf]);
+            }
+        }
+        float4* q = tpair + p * t.tpair_w;
+        q[0] = make_float4(g.x, g.y, tot.x, tot.y);
+        q[1] = make_float4(slt.x, slt.y, sa.x, sa.y);
+        q[2] = make_float4(sla.x, sla.y, sf.x, sf.y);
+        if (t.tpair_w > 3) q[3] = make_float4(slf.x, slf.y, 0.f, 0.f);
+    }
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nnz; i += stride)
+        mden2[i] = split_pair(t.mden[i]);
+}
+
+int launch_build_pairs(const Tables& t, float4* tpair, float2* mden2, int64_t nnz, int grid, cudaStream_t st)
+{
+    if (t.precision == MCX_FP32) k_build_pairs<float><<<grid, 256, 0, st>>>(t, tpair, mden2, nnz);
+    else k_build_pairs<double><<<grid, 256, 0, st>>>(t, tpair, mden2, nnz);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
 int launch_update_tables(const Tables& t, const double* dens_src, int64_t nnz, double* mden,
                          int4* ment, const double* sig_src, void* sigma, float4* frec,
                          cudaStream_t st)

@@ -140,10 +140,11 @@ __device__ __forceinline__ void species_transport(const Tables& t, double E, int
 // the other, in species order, so every sum is the sequential FP64 value.  With NF the nu-fission
 // sum nuSigma_f = sum_i N_i nu sigma_f,i is formed the same way.
 // Species whose load chains (entry, hash window, search probes, records) are
-// in flight together per thread: 2 measured fastest on the 17x17 lattice
-// (886 ms per 1e7 histories; 3: 906 ms, 4: 905 ms at 64 registers).
+// in flight together per thread.  With FP64 sums 2 measured fastest on the
+// 17x17 lattice (886 ms per 1e7 histories; 3: 906, 4: 905); with the FP32-pair
+// sums below, which leave the FP64 pipe, 4 (652 ms; 2: 665, 3: 665).
 #ifndef MCX_TRANSPORT_INFLIGHT
-#define MCX_TRANSPORT_INFLIGHT 2
+#define MCX_TRANSPORT_INFLIGHT 4
 #endif
 template <typename T, bool NF = false>
 __device__ __forceinline__ void macro_transport(const Tables& t, int32_t m, double E,
@@ -232,6 +233,184 @@ __device__ __forceinline__ void macro_transport_warp(const Tables& t, int32_t m,
     sig_t = st;
     sig_a = sa;
     if (NF) *sig_nf = nf;
+}
+
+// ---------------------------------------------------------------------------
+// The transport lookup in FP32 pairs ("double-float": a value is (hi, lo)
+// with hi = RN(hi + lo)).  Knuth's TwoSum gives a sum's rounding error
+// exactly and a fused multiply-add a product's, so a + b c comes out within
+// a few 2^-48 of |a| + |b c| -- about 2^-44 relative where a and b c do not
+// cancel -- using FP32 operations only, which B300 runs at 64 times its
+// FP64 rate.  Energies, the grid search (FP64 bit patterns) and every tally
+// stay FP64; Sigma_t, Sigma_a (and nuSigma_f) and the running sums C_i carry
+// ~1e-12 relative against the FP64 sums, so a decision (a flight against a
+// surface, the species of a collision) changes only if a random number falls
+// that close to its threshold.  The collision re-evaluates its chosen
+// species in FP64 (species_transport).
+#ifndef MCX_TRANSPORT_PAIRS
+#define MCX_TRANSPORT_PAIRS 1
+#endif
+
+__device__ __forceinline__ float2 pair_two_sum(float a, float b)
+{
+    const float s = a + b;
+    const float bp = s - a;
+    return make_float2(s, (a - (s - bp)) + (b - bp));
+}
+
+// a - b
+__device__ __forceinline__ float2 pair_sub(float2 a, float2 b)
+{
+    const float2 s = pair_two_sum(a.x, -b.x);
+    const float e = s.y + (a.y - b.y);
+    const float h = s.x + e;
+    return make_float2(h, e - (h - s.x));
+}
+
+// a + b c
+__device__ __forceinline__ float2 pair_fma(float2 a, float2 b, float2 c)
+{
+    const float p = b.x * c.x;
+    float pe = fmaf(b.x, c.x, -p);
+    pe = fmaf(b.x, c.y, fmaf(b.y, c.x, pe));
+    const float2 s = pair_two_sum(a.x, p);
+    const float e = s.y + (a.y + pe);
+    const float h = s.x + e;
+    return make_float2(h, e - (h - s.x));
+}
+
+// Exact FP32 -> FP64 widening with integer operations for a finite value of
+// either sign (a pair's low part may be negative); zero and subnormals take
+// the conversion instruction.
+__device__ __forceinline__ double widen_signed(float f)
+{
+    const uint32_t u = __float_as_uint(f);
+    const uint32_t m = u & 0x7FFFFFFFu;
+    const uint32_t e = m >> 23;
+    if (e == 0u) return (double)f;
+    const uint32_t hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((m & 0x7FFFFFu) >> 3);
+    return __hiloint2double((int)hi, (int)(u << 29));
+}
+
+// hi + lo in FP64 (one FP64 add)
+__device__ __forceinline__ double pair_value(float2 v) { return widen_signed(v.x) + widen_signed(v.y); }
+
+// E as a pair: hi = E rounded to FP32, lo = the rest
+__device__ __forceinline__ float2 energy_pair(double E)
+{
+    const float h = (float)E;
+    return make_float2(h, (float)(E - widen_signed(h)));
+}
+
+// Total, absorption (and with NF nu-fission) of one species at the energy
+// pair Ep (key eb), its interval starting at point p, `last` its last
+// interval: s[p] + (E - g[p]) slope[p] with E - g[p] clamped to [0, the
+// interval] as the clamped fraction is.
+template <bool NF>
+__device__ __forceinline__ void species_pair(const Tables& t, float2 Ep, int64_t eb, int64_t p, int64_t last,
+                                             float2& tot, float2& sa, float2& sf)
+{
+    const float4* q = t.tpair + p * t.tpair_w;
+    const float4 q0 = __ldg(q), q1 = __ldg(q + 1), q2 = __ldg(q + 2);
+    float2 Ex = Ep;
+    if (p == last && eb >= ebits(__ldg(t.E + p + 1))) {   // at or above the grid's top
+        const float4 qn = __ldg(q + t.tpair_w);
+        Ex = make_float2(qn.x, qn.y);
+    }
+    float2 d = pair_sub(Ex, make_float2(q0.x, q0.y));
+    if (d.x < 0.f) d = make_float2(0.f, 0.f);                // below the grid
+    tot = pair_fma(make_float2(q0.z, q0.w), d, make_float2(q1.x, q1.y));
+    sa = pair_fma(make_float2(q1.z, q1.w), d, make_float2(q2.x, q2.y));
+    if (NF) {
+        const float4 q3 = __ldg(q + 3);
+        sf = pair_fma(make_float2(q2.z, q2.w), d, make_float2(q3.x, q3.y));
+    }
+}
+
+// macro_transport in pairs: the same species, search and order; C_i stored
+// as pairs (cum2) for the collision's comparison.
+template <bool NF = false>
+__device__ __forceinline__ void macro_transport_pair(const Tables& t, int32_t m, double E, double& sig_t,
+                                                     double& sig_a, float2* cum2, double* sig_nf = nullptr)
+{
+    constexpr int TU = MCX_TRANSPORT_INFLIGHT;
+    const int64_t eb = search_key(E);
+    const int32_t hb = t.H > 0 ? hash_bin(t, E, eb) : 0;
+    const float2 Ep = energy_pair(E);
+    const int32_t i0 = __ldg(t.moff + m), i1 = __ldg(t.moff + m + 1);
+    float2 st = make_float2(0.f, 0.f), sa = st, nf = st;
+    for (int32_t i = i0; i < i1; i += TU) {
+        int32_t base[TU], len[TU], last[TU];
+        float2 N[TU];
+#pragma unroll
+        for (int u = 0; u < TU; ++u) {
+            const int32_t ii = i + u < i1 ? i + u : i1 - 1;
+            N[u] = __ldg(t.mden2 + ii);
+            const int4 e = __ldg(t.ment + ii);
+            last[u] = e.x + e.y - 2;
+            search_window(t, e, hb, base[u], len[u]);
+        }
+        for (int s = 0; s < t.search_steps; ++s) {
+#pragma unroll
+            for (int u = 0; u < TU; ++u) search_step(t.E, base[u], len[u], eb);
+        }
+        float2 c[TU], a[TU], v[TU];
+#pragma unroll
+        for (int u = 0; u < TU; ++u) {
+            v[u] = make_float2(0.f, 0.f);
+            species_pair<NF>(t, Ep, eb, base[u], last[u], c[u], a[u], v[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < TU; ++u) {
+            if (u == 0 || i + u < i1) {
+                st = pair_fma(st, N[u], c[u]);
+                sa = pair_fma(sa, N[u], a[u]);
+                if (NF) nf = pair_fma(nf, N[u], v[u]);
+                cum2[i + u - i0] = st;
+            }
+        }
+    }
+    sig_t = pair_value(st);
+    sig_a = pair_value(sa);
+    if (NF) *sig_nf = pair_value(nf);
+}
+
+// macro_transport_pair on a whole converged warp (lanes over species, the
+// sums in species order by every lane): the same values.
+template <bool NF = false>
+__device__ __forceinline__ void macro_transport_pair_warp(const Tables& t, int32_t m, double E, double& sig_t,
+                                                          double& sig_a, float2* cum2, double* sig_nf = nullptr)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t eb = search_key(E);
+    const int32_t hb = t.H > 0 ? hash_bin(t, E, eb) : 0;
+    const float2 Ep = energy_pair(E);
+    const int32_t i0 = __ldg(t.moff + m), i1 = __ldg(t.moff + m + 1);
+    float2 st = make_float2(0.f, 0.f), sa = st, nf = st;
+    for (int32_t i = i0; i < i1; i += 32) {
+        const int32_t ii = i + lane;
+        float2 N = make_float2(0.f, 0.f), c = N, a = N, v = N;
+        if (ii < i1) {
+            N = __ldg(t.mden2 + ii);
+            const int4 e = __ldg(t.ment + ii);
+            int32_t base, len;
+            search_window(t, e, hb, base, len);
+            for (int s = 0; s < t.search_steps; ++s) search_step(t.E, base, len, eb);
+            species_pair<NF>(t, Ep, eb, base, e.x + e.y - 2, c, a, v);
+        }
+        const int n = i1 - i < 32 ? i1 - i : 32;
+        for (int s = 0; s < n; ++s) {
+            const float2 Ns = make_float2(__shfl_sync(0xffffffffu, N.x, s), __shfl_sync(0xffffffffu, N.y, s));
+            st = pair_fma(st, Ns, make_float2(__shfl_sync(0xffffffffu, c.x, s), __shfl_sync(0xffffffffu, c.y, s)));
+            sa = pair_fma(sa, Ns, make_float2(__shfl_sync(0xffffffffu, a.x, s), __shfl_sync(0xffffffffu, a.y, s)));
+            if (NF)
+                nf = pair_fma(nf, Ns, make_float2(__shfl_sync(0xffffffffu, v.x, s), __shfl_sync(0xffffffffu, v.y, s)));
+            if (lane == 0) cum2[i + s - i0] = st;
+        }
+    }
+    sig_t = pair_value(st);
+    sig_a = pair_value(sa);
+    if (NF) *sig_nf = pair_value(nf);
 }
 
 }  // namespace mcx
