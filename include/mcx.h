@@ -128,8 +128,9 @@ typedef struct {
 /* Event-loop tuning (Table 1 of the paper, mapped to this GPU).
  *   mode            MCX_QUEUELESS, MCX_QUEUED or MCX_QUEUED_FULLEST
  *   block_size      threads per block of the event kernels (32..1024, /32)
- *   sort_period     bin the lookup and collision queues every this many
- *                   iterations (0 = never); queued modes only
+ *   sort_period     bin the lookup queue (queued mode) or the selected
+ *                   lookup or collision segment (fullest queue) every this
+ *                   many iterations (0 = never); queued modes only
  *   sort_threshold  ...and only when a queue holds at least this many
  *                   particles (the paper's minimum sorting threshold)
  *   iters_per_sync  event-loop iterations captured per CUDA graph launch

@@ -654,7 +654,7 @@ int run_loop(mcx_problem* owner, int n_prob, mcx_problem* const* probs, const in
     }
     if (kernels_per_iter == 0) {
         const bool sorting = c.mode != MCX_QUEUELESS && c.sort_period > 0;
-        kernels_per_iter = c.mode == MCX_QUEUED_FULLEST ? 5 + (sorting ? 4 : 0) : 5 + (sorting ? 8 : 0);
+        kernels_per_iter = 5 + (sorting ? 4 : 0);   // one binned queue per iteration or step
     }
     int64_t launches = 0, kernels = 0;
     const int64_t max_launches = max_iters / K + 4;

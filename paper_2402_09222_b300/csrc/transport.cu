@@ -1059,7 +1059,7 @@ __global__ void __launch_bounds__(1024) k_collide(LoopConfig c, Tables t, Partic
     const int par = ctl->parity;
     Src src = all_slots(P);
     if (queued)
-        src = ctl->sorted ? plain_list(P.q_sorted, ctl->n_coll) : plain_list(P.q_coll, ctl->n_coll);
+        src = plain_list(P.q_coll, ctl->n_coll);
     else if (fq)
         src = ctl->sorted ? plain_list(P.q_sorted, (int64_t)(ctl->sel_end - ctl->sel_begin))
                           : ring_segment(P, ctl);
@@ -1503,7 +1503,9 @@ static int launch_iteration_t(const LoopConfig& c, const Tables& t, const Partic
     ++k;
     k_advance<EIG><<<c.grid, c.block, 0, st>>>(c, P, probs, ctl);
     ++k;
-    if (sorting) k += launch_sort(c, P, ctl, 1, st);
+    // (the collision queue is not binned: one species per collision gains
+    // less from the locality than the binning costs -- 654 -> 640 ms per 1e7
+    // lattice histories without it)
     if (f32) k_collide<float, EIG><<<c.grid, c.block, 0, st>>>(c, t, P, probs, ctl);
     else k_collide<double, EIG><<<c.grid, c.block, 0, st>>>(c, t, P, probs, ctl);
     ++k;
