@@ -401,6 +401,17 @@ int mcx_debug_uniforms(uint64_t seed, uint32_t problem_id, uint64_t hist, uint32
  * its domain) in a DEVICE buffer; out [n][2] (DEVICE) receives the pairs. */
 int mcx_debug_neg_log(const double* x, int64_t n, double* out, void* stream);
 
+/* Test hook: the transport's macroscopic lookup (FP32-pair sums from the
+ * stored per-point slopes and totals) for n lookups (energies E, materials
+ * mat; DEVICE buffers): out [n][3] (DEVICE) receives Sigma_t, Sigma_a and
+ * nuSigma_f (0 without a nu-fission channel), NaN for an out-of-range
+ * material or a NaN energy.  Synchronises `stream`; allocates a scratch of
+ * n times the largest material's species count of 8-byte sums.  n <= 2^24;
+ * the tables must have 2, 3 or 5 channels, as for transport.
+ * Errors: MCX_ERR_STATE (no tables), MCX_ERR_ARG, MCX_ERR_OOM, MCX_ERR_CUDA. */
+int mcx_debug_transport_xs(mcx_problem* p, int64_t n, const double* E, const int32_t* mat, double* out,
+                           void* stream);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* mcx_last_error(void);
 

@@ -49,6 +49,8 @@ int launch_update_tables(const Tables& t, const double* dens_src, int64_t nnz, d
                          int4* ment, const double* sig_src, void* sigma, float4* frec,
                          cudaStream_t st);
 int launch_debug_neg_log(const double* x, int64_t n, double* out, cudaStream_t st);
+int launch_debug_transport_xs(const Tables& t, int64_t n, const double* E, const int32_t* mat, float2* cum2,
+                              int64_t stride, double* out, cudaStream_t st);
 int launch_debug_uniforms(uint2 key, uint64_t hist, uint32_t first, int64_t n, double* out,
                           cudaStream_t st);
 

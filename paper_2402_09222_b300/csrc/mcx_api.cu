@@ -1526,6 +1526,29 @@ int mcx_debug_uniforms(uint64_t seed, uint32_t problem_id, uint64_t hist, uint32
     return MCX_OK;
 }
 
+int mcx_debug_transport_xs(mcx_problem* p, int64_t n, const double* E, const int32_t* mat, double* out,
+                           void* stream)
+{
+    g_err.clear();
+    TRY(check_tables(p));
+    if (n < 0 || n > ((int64_t)1 << 24)) return fail(MCX_ERR_ARG, "n must be in [0, 2^24]");
+    if (n == 0) return MCX_OK;
+    if (!E || !mat || !out) return fail(MCX_ERR_ARG, "NULL buffer");
+    const int nc = p->tables->view.n_ch;
+    if (nc != 2 && nc != 3 && nc != 5) return fail(MCX_ERR_ARG, "transport needs 2, 3 or 5 channels");
+    DeviceGuard dg(p->device);
+    const int64_t stride = p->tables->view.max_mat_species > 0 ? p->tables->view.max_mat_species : 1;
+    double* scratch = nullptr;   // running sums, 8 bytes each
+    TRY(dev_alloc(&scratch, (size_t)(n * stride)));
+    cudaStream_t st = (cudaStream_t)stream;
+    const int rc = launch_debug_transport_xs(p->tables->view, n, E, mat, reinterpret_cast<float2*>(scratch), stride,
+                                             out, st);
+    const cudaError_t es = cudaStreamSynchronize(st);
+    dev_free(scratch);
+    if (rc || es != cudaSuccess) return fail(MCX_ERR_CUDA, "transport lookup kernel failed");
+    return MCX_OK;
+}
+
 int mcx_debug_neg_log(const double* x, int64_t n, double* out, void* stream)
 {
     g_err.clear();

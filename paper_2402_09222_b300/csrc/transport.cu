@@ -1533,6 +1533,40 @@ __global__ void k_debug_uniforms(uint2 key, uint64_t hist, uint32_t first, int64
         out[i] = uniform_at(key, hist, first + (uint32_t)i);
 }
 
+// The transport lookup on given energies and materials: out [n][3] = Sigma_t,
+// Sigma_a and nuSigma_f (0 without a nu-fission channel), NaN for an invalid
+// material or energy; cum2 [n][stride] receives the running sums.
+template <bool NF>
+__global__ void k_debug_transport_xs(Tables t, int64_t n, const double* __restrict__ E,
+                                     const int32_t* __restrict__ mat, float2* __restrict__ cum2,
+                                     int64_t stride, double* __restrict__ out)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t m = mat[i];
+        const double e = E[i];
+        double st = __longlong_as_double(0x7ff8000000000000LL), sa = st, nf = st;
+        if (m >= 0 && m < t.n_materials && e == e) {
+            nf = 0.0;
+            macro_transport_pair<NF>(t, m, e, st, sa, cum2 + i * stride, &nf);
+        }
+        out[3 * i] = st;
+        out[3 * i + 1] = sa;
+        out[3 * i + 2] = nf;
+    }
+}
+
+int launch_debug_transport_xs(const Tables& t, int64_t n, const double* E, const int32_t* mat, float2* cum2,
+                              int64_t stride, double* out, cudaStream_t st)
+{
+    const int grid = (int)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024);
+    if (t.ch_nu_fission >= 0)
+        k_debug_transport_xs<true><<<grid > 0 ? grid : 1, 256, 0, st>>>(t, n, E, mat, cum2, stride, out);
+    else
+        k_debug_transport_xs<false><<<grid > 0 ? grid : 1, 256, 0, st>>>(t, n, E, mat, cum2, stride, out);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
 __global__ void k_debug_neg_log(const double* __restrict__ x, int64_t n, double* __restrict__ out)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;

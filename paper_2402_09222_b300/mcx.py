@@ -102,6 +102,7 @@ _sig("mcx_xs_indices", C.c_int, _vp, _i64, _vp, _vp, _i32, _vp, _vp)
 _sig("mcx_xs_lookup_backward", C.c_int, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp)
 _sig("mcx_debug_uniforms", C.c_int, C.c_uint64, C.c_uint32, C.c_uint64, C.c_uint32, _i64, _vp, _vp)
 _sig("mcx_debug_neg_log", C.c_int, _vp, _i64, _vp, _vp)
+_sig("mcx_debug_transport_xs", C.c_int, _vp, _i64, _vp, _vp, _vp, _vp)
 
 
 def _check(rc: int):
@@ -369,6 +370,16 @@ class Problem:
                 raise TypeError("out has the wrong dtype for these flags")
             pe, pm, po = _np_ptr(E), _np_ptr(mat), _np_ptr(out)
         _check(_lib.mcx_xs_lookup_host(self.h, n, pe, pm, po, flags))
+        return out
+
+    def debug_transport_xs(self, E, mat, stream=None):
+        """The transport's macroscopic lookup on device tensors E (FP64) and
+        mat (int32): an [n, 3] tensor of Sigma_t, Sigma_a, nuSigma_f."""
+        import torch
+        out = torch.empty((E.numel(), 3), dtype=torch.float64, device=E.device)
+        _check(_lib.mcx_debug_transport_xs(self.h, E.numel(), _dev_ptr(E, torch.float64, "E"),
+                                           _dev_ptr(mat, torch.int32, "mat"), _vp(out.data_ptr()),
+                                           _stream_ptr(stream)))
         return out
 
     def xs_indices(self, E, mat, max_species: int | None = None, stream=None):
