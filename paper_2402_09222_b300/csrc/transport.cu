@@ -163,6 +163,53 @@ __device__ __forceinline__ void warp_add(double* a, double v, bool on)
     if (lane_id() == __ffs(m) - 1) atomicAdd(a, s);
 }
 
+#ifndef MCX_TALLY_TREE
+#define MCX_TALLY_TREE 1
+#endif
+#ifndef MCX_TRANSPORT_CONVERGED
+#define MCX_TRANSPORT_CONVERGED 1
+#endif
+#if MCX_TALLY_TREE
+// Lane holding the r-th (from 0) set bit of m; requires r < popc(m).
+__device__ __forceinline__ int nth_lane(unsigned m, int r)
+{
+    int pos = 0;
+#pragma unroll
+    for (int w = 16; w > 0; w >>= 1) {
+        const int c = __popc(m & ((1u << w) - 1u));
+        if (r >= c) {
+            r -= c;
+            m >>= w;
+            pos += w;
+        }
+    }
+    return pos;
+}
+
+// Sums of v[0..NV) over the lanes of each lane's group `grp` (the lanes with
+// an equal key, from __match_any_sync), left in the group's lowest lane.
+// Every lane of the converged warp calls it.  A shift-down tree over each
+// group's lanes in rank order: ceil(log2(largest group)) steps of one FP64
+// add per value, where summing the group's lanes one by one would take as
+// many steps as the largest group has lanes.
+template <int NV>
+__device__ __forceinline__ void group_sum(unsigned grp, double (&v)[NV])
+{
+    const int rank = __popc(grp & lanes_below());
+    const int size = __popc(grp);
+    const int most = (int)__reduce_max_sync(FULL, (unsigned)size);
+    for (int o = 1; o < most; o <<= 1) {
+        const bool has = rank + o < size;
+        const int src = has ? nth_lane(grp, rank + o) : lane_id();
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            const double w = __shfl_sync(FULL, v[k], src);
+            if (has) v[k] += w;
+        }
+    }
+}
+#endif
+
 // -ln x for a uniform x in [2^-53, 1) (uniform_at's range), by Tang's
 // table-driven method (P. T. P. Tang, ACM Trans. Math. Softw. 16, 378,
 // 1990): x = 2^-t (F + f) with F = 1 + j/256 the leading 8 bits of the
@@ -386,6 +433,34 @@ __device__ void surface_candidate(const ProblemDev& pd, const State& q, int& sur
         else if (q.u < 0.0) offer(q.x, -q.u, S_XLO);
         return;
     }
+#if MCX_TRANSPORT_CONVERGED
+    // Both directions of an axis, and both sides of the cylinder, in one
+    // code path with selected operands (the same values as the branches
+    // below): a warp that mixes directions or particles inside and outside
+    // the pins issues each FP64 operation once instead of once per branch.
+    {
+        const bool up = q.w > 0.0;
+        if (q.w != 0.0) offer(up ? pd.height - q.z : q.z, up ? q.w : -q.w, up ? S_ZTOP : S_ZBOT);
+    }
+    const double cx = __ldg(pd.lat_centre + q.ci);
+    const double cy = __ldg(pd.lat_centre + q.cj);
+    const double dx = q.x - cx, dy = q.y - cy;
+    const double a = fma(q.u, q.u, q.v * q.v);
+    const double k = fma(dx, q.u, dy * q.v);
+    const double c = fma(dx, dx, fma(dy, dy, -(pd.radius * pd.radius)));
+    {
+        const double disc = fma(k, k, -(a * c));
+        const double r = sqrt(disc < 0.0 ? 0.0 : disc);
+        if (a > 0.0 && (q.inpin || (k < 0.0 && disc >= 0.0))) offer(q.inpin ? -k + r : -k - r, a, S_CYL);
+    }
+    if (!q.inpin) {
+        const bool ux = q.u > 0.0, uy = q.v > 0.0;
+        const double px = __ldg(pd.lat_plane + q.ci + (ux ? 1 : 0));
+        const double py = __ldg(pd.lat_plane + q.cj + (uy ? 1 : 0));
+        if (q.u != 0.0) offer(ux ? px - q.x : q.x - px, ux ? q.u : -q.u, ux ? S_XHI : S_XLO);
+        if (q.v != 0.0) offer(uy ? py - q.y : q.y - py, uy ? q.v : -q.v, uy ? S_YHI : S_YLO);
+    }
+#else
     if (q.w > 0.0) offer(pd.height - q.z, q.w, S_ZTOP);
     else if (q.w < 0.0) offer(q.z, -q.w, S_ZBOT);
     const double cx = __ldg(pd.lat_centre + q.ci);
@@ -410,6 +485,7 @@ __device__ void surface_candidate(const ProblemDev& pd, const State& q, int& sur
         if (q.v > 0.0) offer(__ldg(pd.lat_plane + q.cj + 1) - q.y, q.v, S_YHI);
         else if (q.v < 0.0) offer(q.y - __ldg(pd.lat_plane + q.cj), -q.v, S_YLO);
     }
+#endif
 }
 
 // Logical crossing; returns the outcome if the particle leaves, else -1.
@@ -915,6 +991,15 @@ __global__ void __launch_bounds__(1024) k_advance(LoopConfig c, Particles P, con
             if (!(sig_t > 0.0)) collide = false;
             else if (sd == 0.0) collide = true;
             else collide = !(sn * sig_t <= L * sd);
+#if MCX_TRANSPORT_CONVERGED
+            // one division for the whole warp, collisions and crossings alike
+            if (!collide && sd == 0.0) {
+                d = INF;
+            } else {
+                d = (collide ? L : sn) / (collide ? sig_t : sd);
+                if (d < 0.0) d = 0.0;   // a collision's L / Sigma_t is positive
+            }
+#else
             if (collide) {
                 d = L / sig_t;
             } else if (sd == 0.0) {
@@ -923,6 +1008,7 @@ __global__ void __launch_bounds__(1024) k_advance(LoopConfig c, Particles P, con
                 d = sn / sd;
                 if (d < 0.0) d = 0.0;
             }
+#endif
 #else
             const double dcol = sig_t > 0.0 ? -log(xi) / sig_t : INF;
             const double dsurf = surface_distance(pd, q, surf);
@@ -996,6 +1082,29 @@ __global__ void __launch_bounds__(1024) k_advance(LoopConfig c, Particles P, con
         if (EIG) warp_add(&probs[0].eig->k_tl, k_tl, scored);
         // ---- warp-first tally reduction
         const unsigned sm = __ballot_sync(FULL, scored);
+#if MCX_TALLY_TREE
+        if (sm) {
+            // unscored lanes share the key 0, a group whose sums are not added
+            const unsigned grp = __match_any_sync(FULL, scored ? (unsigned long long)tal_flux : 0ull);
+            const bool lead = scored && lane_id() == __ffs(grp) - 1;
+            double v[2] = {scored ? d : 0.0, scored ? xabs : 0.0};
+            group_sum(grp, v);
+            if (lead) {
+                atomicAdd(tal_flux, v[0]);
+                atomicAdd(tal_abs, v[1]);
+            }
+            for (int mm = 0; mm < M; ++mm) {
+                double w[2] = {scored ? d * Wl[mm] : 0.0,
+                               scored ? xabs * Wl[mm] + (mm == m ? xabs : 0.0) : 0.0};
+                group_sum(grp, w);
+                if (lead) {
+                    const ProblemDev& pd = probs[pidx];
+                    atomicAdd(pd.dflux + tal_i * M + mm, w[0]);
+                    atomicAdd(pd.dabsorb + tal_i * M + mm, w[1]);
+                }
+            }
+        }
+#else
         if (scored) {
             const unsigned grp = __match_any_sync(sm, (unsigned long long)tal_flux);
             const int leader = __ffs(grp) - 1;
@@ -1027,6 +1136,7 @@ __global__ void __launch_bounds__(1024) k_advance(LoopConfig c, Particles P, con
                 }
             }
         }
+#endif
         finish_deaths<EIG>(dies, outcome, slot, pidx, probs, P, ctl, M, c.mode, par);
         if (queued) {
             int pos = warp_append(&ctl->n_coll, coll);
