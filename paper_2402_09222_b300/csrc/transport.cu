@@ -169,7 +169,6 @@ __device__ __forceinline__ void warp_add(double* a, double v, bool on)
 #ifndef MCX_TRANSPORT_CONVERGED
 #define MCX_TRANSPORT_CONVERGED 1
 #endif
-#if MCX_TALLY_TREE
 // Lane holding the r-th (from 0) set bit of m; requires r < popc(m).
 __device__ __forceinline__ int nth_lane(unsigned m, int r)
 {
@@ -208,7 +207,6 @@ __device__ __forceinline__ void group_sum(unsigned grp, double (&v)[NV])
         }
     }
 }
-#endif
 
 // -ln x for a uniform x in [2^-53, 1) (uniform_at's range), by Tang's
 // table-driven method (P. T. P. Tang, ACM Trans. Math. Softw. 16, 378,
@@ -695,21 +693,24 @@ __device__ void finish_deaths(bool dies, int outcome, int64_t slot, int32_t pidx
 {
     const unsigned dm = __ballot_sync(FULL, dies);
     if (dm == 0u) return;
+    const ProblemDev& pd = probs[pidx];
+    int64_t h = 0, b = 0;
+    double* a = nullptr;
     if (dies) {
-        const ProblemDev& pd = probs[pidx];
-        const int64_t h = P.hist[slot];
-        const int64_t b = batch_of(pd, h);
-        double* a = pd.outcome + b * N_OUT + outcome;
-        const unsigned grp = __match_any_sync(dm, (unsigned long long)a);
-        const int leader = __ffs(grp) - 1;
-        if (lane_id() == leader) atomicAdd(a, (double)__popc(grp));
-        for (int mm = 0; mm < M; ++mm) {
-            const double wv = P.W[(int64_t)mm * P.stride + slot];
-            double sum = 0.0;
-            for (unsigned g = grp; g; g &= g - 1u) sum += __shfl_sync(grp, wv, __ffs(g) - 1);
-            if (lane_id() == leader)
-                atomicAdd(pd.doutcome + (b * N_OUT + outcome) * M + mm, sum);
-        }
+        h = P.hist[slot];
+        b = batch_of(pd, h);
+        a = pd.outcome + b * N_OUT + outcome;
+    }
+    // lanes that do not die share the key 0, a group whose sums are not added
+    const unsigned grp = __match_any_sync(FULL, dies ? (unsigned long long)a : 0ull);
+    const bool lead = dies && lane_id() == __ffs(grp) - 1;
+    if (lead) atomicAdd(a, (double)__popc(grp));
+    for (int mm = 0; mm < M; ++mm) {
+        double wv[1] = {dies ? P.W[(int64_t)mm * P.stride + slot] : 0.0};
+        group_sum(grp, wv);
+        if (lead) atomicAdd(pd.doutcome + (b * N_OUT + outcome) * M + mm, wv[0]);
+    }
+    if (dies) {
         if (pd.ncoll_debug) pd.ncoll_debug[h - pd.first] = P.ncoll[slot];
         if (EIG && pd.site_count) pd.site_count[h - pd.first] = P.nsite[slot];
         P.flags[slot] = 0;
@@ -1333,18 +1334,14 @@ __global__ void __launch_bounds__(1024) k_collide(LoopConfig c, Tables t, Partic
         }
         // collision-count tally (+ derivative), warp-first
         const unsigned am = __ballot_sync(FULL, act);
-        if (act) {
-            const unsigned grp = __match_any_sync(am, (unsigned long long)tal_coll);
-            const int leader = __ffs(grp) - 1;
-            if (lane_id() == leader) atomicAdd(tal_coll, (double)__popc(grp));
-            if (M > 0) {
-                const ProblemDev& pd = probs[pidx];
-                for (int mm = 0; mm < M; ++mm) {
-                    const double wv = P.W[(int64_t)mm * P.stride + slot];
-                    double sum = 0.0;
-                    for (unsigned g = grp; g; g &= g - 1u) sum += __shfl_sync(grp, wv, __ffs(g) - 1);
-                    if (lane_id() == leader) atomicAdd(pd.doutcome + tal_i * M + mm, sum);
-                }
+        if (am) {
+            const unsigned grp = __match_any_sync(FULL, act ? (unsigned long long)tal_coll : 0ull);
+            const bool lead = act && lane_id() == __ffs(grp) - 1;
+            if (lead) atomicAdd(tal_coll, (double)__popc(grp));
+            for (int mm = 0; mm < M; ++mm) {
+                double wv[1] = {act ? P.W[(int64_t)mm * P.stride + slot] : 0.0};
+                group_sum(grp, wv);
+                if (lead) atomicAdd(probs[pidx].doutcome + tal_i * M + mm, wv[0]);
             }
         }
         finish_deaths<EIG>(dies, outcome, slot, pidx, probs, P, ctl, M, c.mode, par);
