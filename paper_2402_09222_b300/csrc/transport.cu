@@ -169,6 +169,32 @@ __device__ __forceinline__ void warp_add(double* a, double v, bool on)
 #ifndef MCX_TRANSPORT_CONVERGED
 #define MCX_TRANSPORT_CONVERGED 1
 #endif
+// Sign tests of a non-NaN double on its bit pattern: the answers of the
+// comparisons with zero (-0.0 included), on the integer pipes instead of
+// B300's FP64 pipe, which also executes FP64 comparisons and limits the flight.
+#ifndef MCX_TRANSPORT_INT_SIGN
+#define MCX_TRANSPORT_INT_SIGN 1
+#endif
+#if MCX_TRANSPORT_INT_SIGN
+__device__ __forceinline__ bool gt0(double x) { return __double_as_longlong(x) > 0; }
+__device__ __forceinline__ bool lt0(double x)
+{
+    const long long b = __double_as_longlong(x);
+    return b < 0 && b != (long long)0x8000000000000000ull;
+}
+__device__ __forceinline__ bool ge0(double x)
+{
+    const long long b = __double_as_longlong(x);
+    return b >= 0 || b == (long long)0x8000000000000000ull;
+}
+__device__ __forceinline__ bool ne0(double x) { return ((unsigned long long)__double_as_longlong(x) << 1) != 0ull; }
+#else
+__device__ __forceinline__ bool gt0(double x) { return x > 0.0; }
+__device__ __forceinline__ bool lt0(double x) { return x < 0.0; }
+__device__ __forceinline__ bool ge0(double x) { return x >= 0.0; }
+__device__ __forceinline__ bool ne0(double x) { return x != 0.0; }
+#endif
+
 // Lane holding the r-th (from 0) set bit of m; requires r < popc(m).
 __device__ __forceinline__ int nth_lane(unsigned m, int r)
 {
@@ -290,7 +316,7 @@ __device__ __forceinline__ void azimuth_raw(uint2 key, uint64_t h, uint32_t& n, 
         const double b = 2.0 * uniform_at(key, h, n + 1) - 1.0;
         n += 2;
         const double r = a * a + b * b;
-        if (r > 0.0 && r <= 1.0) {
+        if (gt0(r) && r <= 1.0) {
             c = a * a - b * b;
             s = 2.0 * a * b;
             rho = r;
@@ -419,7 +445,7 @@ __device__ void surface_candidate(const ProblemDev& pd, const State& q, int& sur
     den = 0.0;
     surf = S_NONE;
     auto offer = [&](double n, double m, int s) {
-        if (den == 0.0 || n * den < num * m) {
+        if (!ne0(den) || n * den < num * m) {
             num = n;
             den = m;
             surf = s;
@@ -437,8 +463,8 @@ __device__ void surface_candidate(const ProblemDev& pd, const State& q, int& sur
     // below): a warp that mixes directions or particles inside and outside
     // the pins issues each FP64 operation once instead of once per branch.
     {
-        const bool up = q.w > 0.0;
-        if (q.w != 0.0) offer(up ? pd.height - q.z : q.z, up ? q.w : -q.w, up ? S_ZTOP : S_ZBOT);
+        const bool up = gt0(q.w);
+        if (ne0(q.w)) offer(up ? pd.height - q.z : q.z, up ? q.w : -q.w, up ? S_ZTOP : S_ZBOT);
     }
     const double cx = __ldg(pd.lat_centre + q.ci);
     const double cy = __ldg(pd.lat_centre + q.cj);
@@ -448,15 +474,15 @@ __device__ void surface_candidate(const ProblemDev& pd, const State& q, int& sur
     const double c = fma(dx, dx, fma(dy, dy, -(pd.radius * pd.radius)));
     {
         const double disc = fma(k, k, -(a * c));
-        const double r = sqrt(disc < 0.0 ? 0.0 : disc);
-        if (a > 0.0 && (q.inpin || (k < 0.0 && disc >= 0.0))) offer(q.inpin ? -k + r : -k - r, a, S_CYL);
+        const double r = sqrt(lt0(disc) ? 0.0 : disc);
+        if (gt0(a) && (q.inpin || (lt0(k) && ge0(disc)))) offer(q.inpin ? -k + r : -k - r, a, S_CYL);
     }
     if (!q.inpin) {
-        const bool ux = q.u > 0.0, uy = q.v > 0.0;
+        const bool ux = gt0(q.u), uy = gt0(q.v);
         const double px = __ldg(pd.lat_plane + q.ci + (ux ? 1 : 0));
         const double py = __ldg(pd.lat_plane + q.cj + (uy ? 1 : 0));
-        if (q.u != 0.0) offer(ux ? px - q.x : q.x - px, ux ? q.u : -q.u, ux ? S_XHI : S_XLO);
-        if (q.v != 0.0) offer(uy ? py - q.y : q.y - py, uy ? q.v : -q.v, uy ? S_YHI : S_YLO);
+        if (ne0(q.u)) offer(ux ? px - q.x : q.x - px, ux ? q.u : -q.u, ux ? S_XHI : S_XLO);
+        if (ne0(q.v)) offer(uy ? py - q.y : q.y - py, uy ? q.v : -q.v, uy ? S_YHI : S_YLO);
     }
 #else
     if (q.w > 0.0) offer(pd.height - q.z, q.w, S_ZTOP);
@@ -537,7 +563,7 @@ __device__ __forceinline__ void rotate_raw(double& u, double& v, double& w, doub
     const double m = fma(-mu, mu, 1.0);
     const bool wz = fabs(w0) < 0.9999;
     const double t = wz ? fma(-w0, w0, 1.0) : fma(-v0, v0, 1.0);
-    const double aq = m > 0.0 ? m * rsqrt(m * t * (rho * rho)) : 0.0;
+    const double aq = gt0(m) ? m * rsqrt(m * t * (rho * rho)) : 0.0;
     if (wz) {
         u = fma(mu, u0, aq * fma(u0 * w0, c, -(v0 * s)));
         v = fma(mu, v0, aq * fma(v0 * w0, c, u0 * s));
@@ -990,15 +1016,15 @@ __global__ void __launch_bounds__(1024) k_advance(LoopConfig c, Particles P, con
             surface_candidate(pd, q, surf, sn, sd);
             bool collide;
             if (!(sig_t > 0.0)) collide = false;
-            else if (sd == 0.0) collide = true;
+            else if (!ne0(sd)) collide = true;
             else collide = !(sn * sig_t <= L * sd);
 #if MCX_TRANSPORT_CONVERGED
             // one division for the whole warp, collisions and crossings alike
-            if (!collide && sd == 0.0) {
+            if (!collide && !ne0(sd)) {
                 d = INF;
             } else {
                 d = (collide ? L : sn) / (collide ? sig_t : sd);
-                if (d < 0.0) d = 0.0;   // a collision's L / Sigma_t is positive
+                if (lt0(d)) d = 0.0;   // a collision's L / Sigma_t is positive
             }
 #else
             if (collide) {
