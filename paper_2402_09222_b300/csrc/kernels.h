@@ -192,6 +192,7 @@ struct RunCtl {
     int pad2;
     unsigned long long sel_begin, sel_end;
     long long sel_count[3];   // steps that ran the lookup / flight / collision kernel
+    unsigned long long lk_claim;  // queued mode: next unclaimed entry of the lookup queue
 };
 
 // Ring queues of the fullest-queue mode and the events that consume them.

@@ -169,6 +169,9 @@ __device__ __forceinline__ void warp_add(double* a, double v, bool on)
 #ifndef MCX_TRANSPORT_CONVERGED
 #define MCX_TRANSPORT_CONVERGED 1
 #endif
+#ifndef MCX_LOOKUP_CLAIM
+#define MCX_LOOKUP_CLAIM 1
+#endif
 // Sign tests of a non-NaN double on its bit pattern: the answers of the
 // comparisons with zero (-0.0 included), on the integer pipes instead of
 // B300's FP64 pipe, which also executes FP64 comparisons and limits the flight.
@@ -780,6 +783,7 @@ __global__ void k_run_init(Particles P, RunCtl* ctl, long long total, int n_prob
         ctl->n_coll = 0;
         ctl->sorted = 0;
         ctl->sort_which = 0;
+        ctl->lk_claim = 0ull;
         for (int r = 0; r < N_RQ; ++r) {
             ctl->rq_head[r] = 0ull;
             ctl->rq_tail[r] = 0ull;
@@ -871,6 +875,38 @@ __global__ void __launch_bounds__(1024) k_refill(LoopConfig c, Particles P, cons
     if (lane_id() == 0 && added) atomicAdd(&ctl->n_alive, added);
 }
 
+// The transport lookup of the particle in `slot` if it needs one: Sigma_t,
+// Sigma_a (nuSigma_f) and the running sums C_i; returns whether it did.
+template <typename T, bool EIG>
+__device__ __forceinline__ bool lookup_slot(const Tables& t, const Particles& P, int64_t slot)
+{
+    const uint8_t f = P.flags[slot];
+    if (!(f & PF_NEED_XS)) return false;
+    double st, sa;
+#if MCX_TRANSPORT_PAIRS
+    float2* cum2 = reinterpret_cast<float2*>(P.cum + slot * P.cum_stride);
+    if (EIG) {
+        double nf;
+        macro_transport_pair<true>(t, P.mat[slot], P.E[slot], st, sa, cum2, &nf);
+        P.sig_nf[slot] = nf;
+    } else {
+        macro_transport_pair<false>(t, P.mat[slot], P.E[slot], st, sa, cum2);
+    }
+#else
+    if (EIG) {
+        double nf;
+        macro_transport<T, true>(t, P.mat[slot], P.E[slot], st, sa, P.cum + slot * P.cum_stride, &nf);
+        P.sig_nf[slot] = nf;
+    } else {
+        macro_transport<T>(t, P.mat[slot], P.E[slot], st, sa, P.cum + slot * P.cum_stride);
+    }
+#endif
+    P.sig_t[slot] = st;
+    P.sig_a[slot] = sa;
+    P.flags[slot] = f & (uint8_t)~PF_NEED_XS;
+    return true;
+}
+
 template <typename T, bool EIG>
 __global__ void __launch_bounds__(1024) k_lookup(LoopConfig c, Tables t, Particles P, RunCtl* ctl)
 {
@@ -918,39 +954,31 @@ __global__ void __launch_bounds__(1024) k_lookup(LoopConfig c, Tables t, Particl
         return;
     }
 #endif
+#if MCX_LOOKUP_CLAIM
+    if (c.mode == MCX_QUEUED) {
+        // Warps claim 32-entry chunks of the (binned) queue front to back:
+        // the lookups in flight at any time sit in a narrow slice of
+        // (material, energy), and no warp idles while another still holds a
+        // grid-stride share.
+        const int lane = lane_id();
+        for (;;) {
+            unsigned long long b0 = 0ull;
+            if (lane == 0) b0 = atomicAdd(&ctl->lk_claim, 32ull);
+            const int64_t b = (int64_t)__shfl_sync(FULL, b0, 0);
+            if (b >= count) break;
+            const int64_t i = b + lane;
+            if (i < count) lookup_slot<T, EIG>(t, P, src_at(src, i));
+        }
+        return;
+    }
+#endif
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < count; base += stride) {
         const int64_t i = base + threadIdx.x;
         int64_t slot = -1;
         bool act = false;
         if (i < count) {
             slot = src_at(src, i);
-            const uint8_t f = P.flags[slot];
-            if (f & PF_NEED_XS) {
-                act = true;
-                double st, sa;
-#if MCX_TRANSPORT_PAIRS
-                float2* cum2 = reinterpret_cast<float2*>(P.cum + slot * P.cum_stride);
-                if (EIG) {
-                    double nf;
-                    macro_transport_pair<true>(t, P.mat[slot], P.E[slot], st, sa, cum2, &nf);
-                    P.sig_nf[slot] = nf;
-                } else {
-                    macro_transport_pair<false>(t, P.mat[slot], P.E[slot], st, sa, cum2);
-                }
-#else
-                if (EIG) {
-                    double nf;
-                    macro_transport<T, true>(t, P.mat[slot], P.E[slot], st, sa,
-                                             P.cum + slot * P.cum_stride, &nf);
-                    P.sig_nf[slot] = nf;
-                } else {
-                    macro_transport<T>(t, P.mat[slot], P.E[slot], st, sa, P.cum + slot * P.cum_stride);
-                }
-#endif
-                P.sig_t[slot] = st;
-                P.sig_a[slot] = sa;
-                P.flags[slot] = f & (uint8_t)~PF_NEED_XS;
-            }
+            act = lookup_slot<T, EIG>(t, P, slot);
         }
         if (fq) ring_push(P, ctl, adv, act, slot);
     }
@@ -1391,6 +1419,7 @@ __global__ void k_bookkeep(RunCtl* ctl)
     ctl->n_coll = 0;
     ctl->parity = p ^ 1;
     ctl->sorted = 0;
+    ctl->lk_claim = 0ull;
     if (!ctl->done) {
         ctl->iters += 1;
         if (ctl->n_alive == 0 && (long long)ctl->next >= ctl->total) {
