@@ -48,8 +48,8 @@ TRANSPORT_HIST = 10_000_000
 # chosen by paper_2402_09222_b300.tuner (random + coordinate descent, 40
 # evaluations on this workload, 1.5x-baseline time limit): 1.326 s against
 # 1.855 s for the default configuration (best of 5), +39.9 %
-TRANSPORT_TUNED = dict(precision=1, hash_bins=37_100, pif=1_298_000,
-                       tune=dict(mode=1, block_size=64, sort_period=1, sort_threshold=689_000))
+TRANSPORT_TUNED = dict(precision=1, hash_bins=37_100, pif=1_600_000,
+                       tune=dict(mode=1, block_size=256, sort_period=1, sort_threshold=400_000))
 TRANSPORT_PLAIN = dict(precision=0, hash_bins=0, pif=1_000_000, tune=dict(mode=0, block_size=256))
 TRANSPORT_FULLEST = dict(TRANSPORT_TUNED, tune=dict(TRANSPORT_TUNED["tune"], mode=2))
 WORKLOAD = ("macroscopic XS lookup, 355 species x 11,303 points x 5 channels, 12 materials "

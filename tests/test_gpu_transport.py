@@ -252,8 +252,8 @@ def test_config5_full_size_sampled(mcx):
     base = mcx.Problem(probs[0], flags=mcx.FLAG_HISTORY_DEBUG).load_tables(lib, mats, precision=mcx.FP32,
                                                                            hash_bins=4000)
     hs = [base] + [mcx.Problem(pr, flags=mcx.FLAG_HISTORY_DEBUG).share_tables(base) for pr in probs[1:]]
-    base.set_tuning(mode=1, block_size=64, sort_period=1, sort_threshold=689_000)
-    mcx.batch_run(hs, [pr.n_histories for pr in probs], particles_in_flight=1_298_000, seed=9)
+    base.set_tuning(mode=1, block_size=256, sort_period=1, sort_threshold=400_000)
+    mcx.batch_run(hs, [pr.n_histories for pr in probs], particles_in_flight=1_600_000, seed=9)
     lib32 = lib.fp32_rounded()
     rng = np.random.default_rng(17)
     matched = total = 0
