@@ -311,12 +311,37 @@ __device__ __forceinline__ void azimuth(uint2 key, uint64_t h, uint32_t& n, doub
 // The same draws as azimuth, unnormalised: (a^2 - b^2, 2 a b) = rho (cos phi,
 // sin phi) and rho, so that the rotation can fold 1 / rho into its one
 // reciprocal square root.
+#ifndef MCX_SIGNED_UNIFORM
+#define MCX_SIGNED_UNIFORM 1
+#endif
+// 2 u - 1 for u = uniform_at(key, hist, n), exactly: u = (2k + 1) 2^-53 makes
+// 2u - 1 = (2k + 1 - 2^52) 2^-52, an odd integer below 2^52 in magnitude
+// times 2^-52, which the FP64 multiply and subtract reproduce without
+// rounding; built here from that integer's bits as uniform_at builds u.
+__device__ __forceinline__ double uniform_signed(uint2 key, uint64_t hist, uint32_t n)
+{
+#if MCX_SIGNED_UNIFORM
+    const uint4 w = philox4x32_10(make_uint4(n >> 1, (uint32_t)hist, (uint32_t)(hist >> 32), 0u), key);
+    const uint32_t a = (n & 1u) ? w.z : w.x;
+    const uint32_t b = (n & 1u) ? w.w : w.y;
+    const uint64_t k = ((uint64_t)(a >> 6) << 26) | (uint64_t)(b >> 6);
+    const int64_t N = (int64_t)(2 * k + 1) - (int64_t)(1ull << 52);
+    const uint64_t sign = N < 0 ? 0x8000000000000000ull : 0ull;
+    const uint64_t M = (uint64_t)(N < 0 ? -N : N);   // odd, 1 <= M < 2^52
+    const int p = 63 - __clzll((long long)M);
+    const uint64_t mant = (M << (52 - p)) & 0x000FFFFFFFFFFFFFull;
+    return __longlong_as_double((long long)(sign | ((uint64_t)(p - 52 + 1023) << 52) | mant));
+#else
+    return 2.0 * uniform_at(key, hist, n) - 1.0;
+#endif
+}
+
 __device__ __forceinline__ void azimuth_raw(uint2 key, uint64_t h, uint32_t& n, double& c, double& s,
                                            double& rho)
 {
     for (int t = 0; t < MAX_AZIMUTH_TRIES; ++t) {
-        const double a = 2.0 * uniform_at(key, h, n) - 1.0;
-        const double b = 2.0 * uniform_at(key, h, n + 1) - 1.0;
+        const double a = uniform_signed(key, h, n);
+        const double b = uniform_signed(key, h, n + 1);
         n += 2;
         const double r = a * a + b * b;
         if (gt0(r) && r <= 1.0) {
