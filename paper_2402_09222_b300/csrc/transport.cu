@@ -283,34 +283,6 @@ __device__ __forceinline__ double neg_log_uniform(double x)
 #endif
 }
 
-// Azimuth (cos phi, sin phi) by rejection on pairs (2u-1, 2u-1) inside the
-// unit disc.
-__device__ __forceinline__ void azimuth(uint2 key, uint64_t h, uint32_t& n, double& c, double& s)
-{
-    for (int t = 0; t < MAX_AZIMUTH_TRIES; ++t) {
-        const double a = 2.0 * uniform_at(key, h, n) - 1.0;
-        const double b = 2.0 * uniform_at(key, h, n + 1) - 1.0;
-        n += 2;
-        const double rho = a * a + b * b;
-        if (rho > 0.0 && rho <= 1.0) {
-#if MCX_TRANSPORT_RECIP_DIR
-            const double r = 1.0 / rho;
-            c = (a * a - b * b) * r;
-            s = (2.0 * a * b) * r;
-#else
-            c = (a * a - b * b) / rho;
-            s = 2.0 * a * b / rho;
-#endif
-            return;
-        }
-    }
-    c = 1.0;
-    s = 0.0;
-}
-
-// The same draws as azimuth, unnormalised: (a^2 - b^2, 2 a b) = rho (cos phi,
-// sin phi) and rho, so that the rotation can fold 1 / rho into its one
-// reciprocal square root.
 #ifndef MCX_SIGNED_UNIFORM
 #define MCX_SIGNED_UNIFORM 1
 #endif
@@ -336,6 +308,34 @@ __device__ __forceinline__ double uniform_signed(uint2 key, uint64_t hist, uint3
 #endif
 }
 
+// Azimuth (cos phi, sin phi) by rejection on pairs (2u-1, 2u-1) inside the
+// unit disc.
+__device__ __forceinline__ void azimuth(uint2 key, uint64_t h, uint32_t& n, double& c, double& s)
+{
+    for (int t = 0; t < MAX_AZIMUTH_TRIES; ++t) {
+        const double a = uniform_signed(key, h, n);
+        const double b = uniform_signed(key, h, n + 1);
+        n += 2;
+        const double rho = a * a + b * b;
+        if (rho > 0.0 && rho <= 1.0) {
+#if MCX_TRANSPORT_RECIP_DIR
+            const double r = 1.0 / rho;
+            c = (a * a - b * b) * r;
+            s = (2.0 * a * b) * r;
+#else
+            c = (a * a - b * b) / rho;
+            s = 2.0 * a * b / rho;
+#endif
+            return;
+        }
+    }
+    c = 1.0;
+    s = 0.0;
+}
+
+// The same draws as azimuth, unnormalised: (a^2 - b^2, 2 a b) = rho (cos phi,
+// sin phi) and rho, so that the rotation can fold 1 / rho into its one
+// reciprocal square root.
 __device__ __forceinline__ void azimuth_raw(uint2 key, uint64_t h, uint32_t& n, double& c, double& s,
                                            double& rho)
 {
@@ -676,7 +676,7 @@ __device__ void init_particle(const Particles& P, int64_t slot, const ProblemDev
         q.ci = site.cell / ln;
         q.cj = site.cell % ln;
         q.inpin = site.inpin;
-        const double mu = 2.0 * uniform_at(key, h, n) - 1.0;
+        const double mu = uniform_signed(key, h, n);
         n += 1;
         double c, s;
         azimuth(key, h, n, c, s);
@@ -701,7 +701,7 @@ __device__ void init_particle(const Particles& P, int64_t slot, const ProblemDev
             q.z = 0.5 * pd.height;
             q.inpin = 1;
         }
-        const double mu = 2.0 * uniform_at(key, h, n) - 1.0;
+        const double mu = uniform_signed(key, h, n);
         n += 1;
         double c, s;
         azimuth(key, h, n, c, s);
@@ -1283,7 +1283,7 @@ __global__ void __launch_bounds__(1024) k_collide(LoopConfig c, Tables t, Partic
             tal_coll = pd.outcome + tal_i;
             const double xi1 = uniform_at(pd.key, h, n);
             const double xi2 = uniform_at(pd.key, h, n + 1);
-            const double xi3 = uniform_at(pd.key, h, n + 2);
+            const double mu = uniform_signed(pd.key, h, n + 2);   // 2 xi3 - 1
             n += 3;
             if (EIG) {
                 // fission sites of this collision, banked before the reaction
@@ -1350,7 +1350,6 @@ __global__ void __launch_bounds__(1024) k_collide(LoopConfig c, Tables t, Partic
                 outcome = OUT_ABSORBED;
             } else {
                 const double A = __ldg(t.awr + j);
-                const double mu = 2.0 * xi3 - 1.0;
                 const double num = A * A + 2.0 * A * mu + 1.0;
 #if MCX_TRANSPORT_KINEMATICS
                 const double E_new = (E * num) * __ldg(t.inv_a1sq + j);   // (A + 1)^-2 stored per species
