@@ -112,6 +112,7 @@ struct ProblemDev {
     int32_t n_ebins;
     int32_t M;           // materials with derivative tallies (0 = off)
     double pitch, radius, height, slab_length, half, E0, E_cut;
+    double radius2;      // radius * radius (the same product the flight would form)
     const int32_t* region_material;
     const double* lat_plane;   // lattice: x (and y) of cell plane i = -half + pitch i, i = 0..n
     const double* lat_centre;  // lattice: centre of cell i = -half + pitch (i + 1/2)

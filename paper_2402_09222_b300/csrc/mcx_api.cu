@@ -485,6 +485,7 @@ ProblemDev make_problem_dev(mcx_problem* p, uint64_t seed, int64_t first, bool d
     d.M = deriv ? p->M : 0;
     d.pitch = s.pitch;
     d.radius = s.radius;
+    d.radius2 = s.radius * s.radius;
     d.height = s.height;
     d.slab_length = s.slab_length;
     d.half = 0.5 * (double)d.lattice_n * s.pitch;

@@ -499,7 +499,7 @@ __device__ void surface_candidate(const ProblemDev& pd, const State& q, int& sur
     const double dx = q.x - cx, dy = q.y - cy;
     const double a = fma(q.u, q.u, q.v * q.v);
     const double k = fma(dx, q.u, dy * q.v);
-    const double c = fma(dx, dx, fma(dy, dy, -(pd.radius * pd.radius)));
+    const double c = fma(dx, dx, fma(dy, dy, -pd.radius2));
     {
         const double disc = fma(k, k, -(a * c));
         const double r = sqrt(lt0(disc) ? 0.0 : disc);
