@@ -152,7 +152,7 @@ struct Particles {
     double* W = nullptr;  // [MCX_MAX_DMAT][cap] (derivative runs)
     double* cum = nullptr;  // [cap][cum_stride]: running sums C_i of the last lookup, 8 bytes each
                             // (normalised FP32 pairs in the transport's pair form, else FP64)
-    int64_t cum_stride = 0; // >= the largest material's species count
+    int64_t cum_stride = 0; // >= the largest material's species count, a multiple of 4
     int64_t* hist = nullptr;
     uint32_t* rng_n = nullptr;
     uint32_t* ncoll = nullptr;

@@ -265,7 +265,9 @@ int ensure_particles(mcx_problem* p, int64_t cap, bool with_w, size_t n_bins, in
     int64_t want = cap > p->p_cap ? cap : p->p_cap;
     size_t bins = n_bins > p->bins_cap ? n_bins : p->bins_cap;
     bool w = with_w || p->p_has_w;
-    const int64_t cs = cum_stride > p->P.cum_stride ? cum_stride : p->P.cum_stride;
+    // rows padded to a multiple of 4 entries (32 bytes): the lookup stores
+    // four running sums at a time as two 16-byte vectors
+    const int64_t cs = ((cum_stride > p->P.cum_stride ? cum_stride : p->P.cum_stride) + 3) & ~(int64_t)3;
     free_particles(p);
     const size_t c = (size_t)want;
     auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
@@ -1538,8 +1540,9 @@ int mcx_debug_transport_xs(mcx_problem* p, int64_t n, const double* E, const int
     const int nc = p->tables->view.n_ch;
     if (nc != 2 && nc != 3 && nc != 5) return fail(MCX_ERR_ARG, "transport needs 2, 3 or 5 channels");
     DeviceGuard dg(p->device);
-    const int64_t stride = p->tables->view.max_mat_species > 0 ? p->tables->view.max_mat_species : 1;
-    double* scratch = nullptr;   // running sums, 8 bytes each
+    // running sums, 8 bytes each, rows of a multiple of 4 entries as the lookup stores them
+    const int64_t stride = ((p->tables->view.max_mat_species > 0 ? p->tables->view.max_mat_species : 1) + 3) & ~(int64_t)3;
+    double* scratch = nullptr;
     TRY(dev_alloc(&scratch, (size_t)(n * stride)));
     cudaStream_t st = (cudaStream_t)stream;
     const int rc = launch_debug_transport_xs(p->tables->view, n, E, mat, reinterpret_cast<float2*>(scratch), stride,

@@ -143,6 +143,9 @@ __device__ __forceinline__ void species_transport(const Tables& t, double E, int
 // in flight together per thread.  With FP64 sums 2 measured fastest on the
 // 17x17 lattice (886 ms per 1e7 histories; 3: 906, 4: 905); with the FP32-pair
 // sums below, which leave the FP64 pipe, 4 (652 ms; 2: 665, 3: 665).
+#ifndef MCX_CUM_VEC
+#define MCX_CUM_VEC 1
+#endif
 #ifndef MCX_TRANSPORT_INFLIGHT
 #define MCX_TRANSPORT_INFLIGHT 4
 #endif
@@ -366,9 +369,21 @@ __device__ __forceinline__ void macro_transport_pair(const Tables& t, int32_t m,
                 st = pair_fma(st, N[u], c[u]);
                 sa = pair_fma(sa, N[u], a[u]);
                 if (NF) nf = pair_fma(nf, N[u], v[u]);
+#if MCX_CUM_VEC && MCX_TRANSPORT_INFLIGHT == 4
+            }
+            c[u] = st;   // C_{i+u}; past the last species it repeats the sum
+        }
+        // the group's four sums as two 16-byte stores: cum2 rows hold a
+        // multiple of 4 entries and start 32-byte aligned, i - i0 is a
+        // multiple of 4, and entries past the material's species are never read
+        float4* row = reinterpret_cast<float4*>(cum2 + (i - i0));
+        row[0] = make_float4(c[0].x, c[0].y, c[1].x, c[1].y);
+        row[1] = make_float4(c[2].x, c[2].y, c[3].x, c[3].y);
+#else
                 cum2[i + u - i0] = st;
             }
         }
+#endif
     }
     sig_t = pair_value(st);
     sig_a = pair_value(sa);
