@@ -146,7 +146,8 @@ struct Particles {
     int64_t stride = 0;  // slots allocated (row stride of W)
     double *x = nullptr, *y = nullptr, *z = nullptr;
     double *u = nullptr, *v = nullptr, *w = nullptr;
-    double *E = nullptr, *sig_t = nullptr, *sig_a = nullptr;
+    double* E = nullptr;
+    double2* sig_ta = nullptr;  // {Sigma_t, Sigma_a} of the last lookup: one 16-byte store and load
     double* sig_nf = nullptr;   // nuSigma_f of the last lookup (eigenvalue runs)
     uint32_t* nsite = nullptr;  // sites banked by the slot's history so far
     double* W = nullptr;  // [MCX_MAX_DMAT][cap] (derivative runs)

@@ -299,8 +299,7 @@ int ensure_particles(mcx_problem* p, int64_t cap, bool with_w, size_t n_bins, in
     P.v = (double*)take(c * 8);
     P.w = (double*)take(c * 8);
     P.E = (double*)take(c * 8);
-    P.sig_t = (double*)take(c * 8);
-    P.sig_a = (double*)take(c * 8);
+    P.sig_ta = (double2*)take(c * 16);
     P.sig_nf = (double*)take(c * 8);
     P.W = w ? (double*)take(c * 8 * MCX_MAX_DMAT) : nullptr;
     P.cum = (double*)take(c * 8 * (size_t)cs);

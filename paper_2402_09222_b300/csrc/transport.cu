@@ -926,8 +926,7 @@ __device__ __forceinline__ bool lookup_slot(const Tables& t, const Particles& P,
         macro_transport<T>(t, P.mat[slot], P.E[slot], st, sa, P.cum + slot * P.cum_stride);
     }
 #endif
-    P.sig_t[slot] = st;
-    P.sig_a[slot] = sa;
+    P.sig_ta[slot] = make_double2(st, sa);
     P.flags[slot] = f & (uint8_t)~PF_NEED_XS;
     return true;
 }
@@ -969,8 +968,7 @@ __global__ void __launch_bounds__(1024) k_lookup(LoopConfig c, Tables t, Particl
 #endif
                 if (lane == 0) {
                     if (EIG) P.sig_nf[slot] = nf;
-                    P.sig_t[slot] = st;
-                    P.sig_a[slot] = sa;
+                    P.sig_ta[slot] = make_double2(st, sa);
                     P.flags[slot] = f & (uint8_t)~PF_NEED_XS;
                 }
             }
@@ -1058,7 +1056,8 @@ __global__ void __launch_bounds__(1024) k_advance(LoopConfig c, Particles P, con
             uint32_t n = P.rng_n[slot];
             const double xi = uniform_at(pd.key, h, n);
             n += 1;
-            const double sig_t = P.sig_t[slot], sig_a = P.sig_a[slot];
+            const double2 ta = P.sig_ta[slot];
+            const double sig_t = ta.x, sig_a = ta.y;
             m = P.mat[slot];
             int surf;
 #if MCX_TRANSPORT_ONE_DIV
@@ -1290,7 +1289,7 @@ __global__ void __launch_bounds__(1024) k_collide(LoopConfig c, Tables t, Partic
                 // is decided: floor(nuSigma_f / Sigma_t / k_norm + xi4)
                 const double xi4 = uniform_at(pd.key, h, n);
                 n += 1;
-                const double yield = P.sig_nf[slot] / P.sig_t[slot];
+                const double yield = P.sig_nf[slot] / P.sig_ta[slot].x;
                 k_col = yield;
                 const double fl = floor(yield / pd.k_norm + xi4);
                 const double lim = (double)pd.bank_cap + 1.0;   // overflow is reported, not looped on
@@ -1305,7 +1304,7 @@ __global__ void __launch_bounds__(1024) k_collide(LoopConfig c, Tables t, Partic
             }
             const double E = P.E[slot];
             const int32_t m = P.mat[slot];
-            const double target = xi1 * P.sig_t[slot];
+            const double target = xi1 * P.sig_ta[slot].x;
             const int64_t eb = search_key(E);
             const int32_t hb = t.H > 0 ? hash_bin(t, E, eb) : 0;
             // species choice: the first i with target < C_i, C_i the running
