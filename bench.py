@@ -52,6 +52,9 @@ TRANSPORT_TUNED = dict(precision=1, hash_bins=37_100, pif=1_600_000,
                        tune=dict(mode=1, block_size=256, sort_period=1, sort_threshold=400_000))
 TRANSPORT_PLAIN = dict(precision=0, hash_bins=0, pif=1_000_000, tune=dict(mode=0, block_size=256))
 TRANSPORT_FULLEST = dict(TRANSPORT_TUNED, tune=dict(TRANSPORT_TUNED["tune"], mode=2))
+# the 64 uneven lattices of the batched workload in one event loop
+BATCHED_TUNED = dict(precision=1, hash_bins=4000, pif=TRANSPORT_TUNED["pif"],
+                     tune=dict(TRANSPORT_TUNED["tune"]))
 WORKLOAD = ("macroscopic XS lookup, 355 species x 11,303 points x 5 channels, 12 materials "
             "(4-321 species), 1e8 lookups per step")
 
@@ -381,15 +384,16 @@ def time_batched(mcx, synth, seed=9):
     total = sum(p.n_histories for p in probs)
     res = {"config": f"64 lattices, n in 3..17, {total:,} histories, 12 materials of 4-321 species"}
     # tuned: one persistent loop, shared FP32 tables
-    base = mcx.Problem(probs[0]).load_tables(lib, mats, precision=1, hash_bins=4000)
+    spec = BATCHED_TUNED
+    base = mcx.Problem(probs[0]).load_tables(lib, mats, precision=spec["precision"], hash_bins=spec["hash_bins"])
     hs = [base] + [mcx.Problem(pr).share_tables(base) for pr in probs[1:]]
-    base.set_tuning(**TRANSPORT_TUNED["tune"])
+    base.set_tuning(**spec["tune"])
     nh = [pr.n_histories for pr in probs]
-    mcx.batch_run(hs, [max(1, n // 50) for n in nh], TRANSPORT_TUNED["pif"], seed)   # warm-up
+    mcx.batch_run(hs, [max(1, n // 50) for n in nh], spec["pif"], seed)   # warm-up
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     a.record()
-    mcx.batch_run(hs, nh, TRANSPORT_TUNED["pif"], seed)
+    mcx.batch_run(hs, nh, spec["pif"], seed)
     b.record()
     torch.cuda.synchronize()
     ms = a.elapsed_time(b)

@@ -349,8 +349,11 @@ int mcx_xs_lookup_ordered(mcx_problem* p, int64_t n, const double* E, const int3
  * MCX_STATIC_MAX_BINS bins (energy buckets per material are reduced to fit),
  * and more materials than that fail with MCX_ERR_ARG.
  * The first call on a device looks up the scratch's device address (a
- * one-time set-up per device); make that first call before any stream
- * capture.  All calls on a device share the one scratch: calls that overlap
+ * one-time set-up per device) and keeps it for the life of the process;
+ * make that first call before any stream capture, and do not use the entry
+ * point on a device after cudaDeviceReset (or any other teardown of its
+ * primary context) in the same process: the scratch may then live at
+ * another address.  All calls on a device share the one scratch: calls that overlap
  * on the GPU (e.g. on two streams at once) race and give wrong results; order
  * them on one stream or with events.
  * Errors: MCX_ERR_ARG, MCX_ERR_STATE, MCX_ERR_CUDA. */

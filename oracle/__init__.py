@@ -204,6 +204,24 @@ def transport(prob, seed: int, first: int = 0, count: int | None = None, n_threa
     return res
 
 
+def transport_histories(prob, seed: int, hist_ids, n_threads: int = 1) -> np.ndarray:
+    """Collision counts of the listed histories, each run alone from its own
+    Philox stream (exactly what a full run gives for that history: a history
+    depends only on the problem, the seed and its id).  Calls run in a
+    thread pool (the C call releases the interpreter lock)."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    ids = [int(h) for h in np.asarray(hist_ids).ravel()]
+
+    def one(h):
+        return int(transport(prob, seed=seed, first=h, count=1, history_debug=True)["ncoll"][0])
+
+    if n_threads <= 1:
+        return np.array([one(h) for h in ids], np.uint32)
+    with ThreadPoolExecutor(max_workers=n_threads) as ex:
+        return np.array(list(ex.map(one, ids, chunksize=64)), np.uint32)
+
+
 def _channels(lib_):
     """(scatter, absorb, nu-fission) channel indices of a 2-, 3- or 5-channel
     library (2: scatter, absorb; 3: + nu-fission; 5: total, scatter, absorb,

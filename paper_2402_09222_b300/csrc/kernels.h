@@ -67,6 +67,7 @@ struct LookupView {
     SortParams sort;
     int device = 0;
     int grid = 0;
+    int sm_count = 0;
 };
 
 }  // namespace mcx

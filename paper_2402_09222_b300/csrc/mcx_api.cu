@@ -840,6 +840,7 @@ int problem_lookup_view(const mcx_problem* p, LookupView* v)
     v->sort = lookup_sort_params(ts, MCX_STATIC_MAX_BINS);
     v->device = p->device;
     v->grid = lookup_grid(p);
+    v->sm_count = p->sm_count;
     return MCX_OK;
 }
 int set_error(int code, const char* msg) { return fail(code, "%s", msg); }

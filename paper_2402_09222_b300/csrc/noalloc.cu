@@ -11,7 +11,10 @@
 // not acceptable.  For them, mcx_xs_lookup_binned_static does the same work
 // with its scratch in file-scope device arrays of fixed size, created when
 // the library is loaded onto a device and held by that device until the
-// process exits (about 4.05 MB per device).
+// process exits (about 4.05 MB per device).  The arrays' device addresses
+// are looked up once per device and kept for the life of the process, so
+// the entry point must not be used on a device after cudaDeviceReset (or
+// any other teardown of its primary context) in the same process.
 #include <mutex>
 
 #include "kernels.h"
@@ -21,6 +24,9 @@ namespace {
 // Scratch shared by every call of the entry point on a device.
 static __device__ __align__(256) int32_t g_static_perm[MCX_STATIC_MAX_LOOKUPS];
 static __device__ __align__(256) uint32_t g_static_bins[MCX_STATIC_MAX_BINS + 1];
+// Chunk counter of the fast lookup's in-order sweep of the binned order
+// (zeroed on the stream by every launch).
+static __device__ __align__(256) unsigned long long g_static_work;
 
 constexpr int kMaxDevices = 64;
 
@@ -28,6 +34,7 @@ struct ScratchAddr {
     bool ready = false;
     int32_t* perm = nullptr;
     uint32_t* bins = nullptr;
+    unsigned long long* work = nullptr;
 };
 
 ScratchAddr g_addr[kMaxDevices];
@@ -51,8 +58,13 @@ int scratch_on(int dev, ScratchAddr* out)
         cudaError_t e2 = cudaGetSymbolAddress(&pb, g_static_bins);
         if (e2 != cudaSuccess)
             return mcx::set_error(MCX_ERR_CUDA, cudaGetErrorString(e2));
+        void* pw = nullptr;
+        cudaError_t e3 = cudaGetSymbolAddress(&pw, g_static_work);
+        if (e3 != cudaSuccess)
+            return mcx::set_error(MCX_ERR_CUDA, cudaGetErrorString(e3));
         a.perm = static_cast<int32_t*>(pp);
         a.bins = static_cast<uint32_t*>(pb);
+        a.work = static_cast<unsigned long long*>(pw);
         a.ready = true;
     }
     *out = a;
@@ -87,12 +99,16 @@ extern "C" int mcx_xs_lookup_binned_static(mcx_problem* p, int64_t n, const doub
     rc = scratch_on(v.device, &a);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (rc == MCX_OK) {
-        // the bin counters are cleared inside launch_lookup_sort (they keep the
-        // previous call's contents otherwise); the permutation is fully rewritten
+        // the bin counters are cleared inside launch_lookup_sort and the chunk
+        // counter inside launch_xs_lookup_fast (they keep the previous call's
+        // contents otherwise); the permutation is fully rewritten.  The fast
+        // form sweeps the binned order front to back with chunk-claiming
+        // warps on one resident grid, as the allocating binned lookup does.
         if (mcx::launch_lookup_sort(v.sort, n, E, mat, a.bins, a.perm, v.grid, st))
             rc = mcx::set_error(MCX_ERR_CUDA, "binning launch failed");
         else if ((flags & MCX_LOOKUP_FAST)
-                     ? mcx::launch_xs_lookup_fast(v.tables, n, E, mat, a.perm, out, false, v.grid, st)
+                     ? mcx::launch_xs_lookup_fast(v.tables, n, E, mat, a.perm, out, false,
+                                                  v.sm_count * mcx::kFastBlocksPerSm, st, a.work)
                      : mcx::launch_xs_lookup_exact(v.tables, n, E, mat, a.perm, out, v.grid, st))
             rc = mcx::set_error(MCX_ERR_CUDA, "lookup launch failed");
     }

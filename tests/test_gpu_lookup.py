@@ -174,25 +174,35 @@ def test_backward_matches_oracle_adjoint(torch_cuda):
 
 def test_config2_full_size_sampled(torch_cuda):
     """355 species x 11,303 points, 12 materials, 1e8 lookups with FP32 tables
-    in the benchmark's tuned launch (fast arithmetic, hash 4000, binning);
-    20,000 sampled outputs checked against the oracle, and the exact FP64
+    in exactly the launch the benchmark times (its hash-bin count, binning
+    into a caller-held permutation, then the fast lookup over the binned
+    order with chunk-claiming warps); 20,000 sampled outputs checked against
+    the oracle on the FP32-rounded tables, and the exact FP64 full-search
     path on the same sample bit for bit."""
+    import bench
     from paper_2402_09222_b300 import mcx
     torch = torch_cuda
-    lib = synth.species_library(355, 11_303, 1236)
-    mats = synth.lookup_materials(355, 1236)
-    n = 100_000_000
-    E, mat = synth.lookup_inputs(n, mats.n_materials, 1336)
+    lib, mats, E, mat = bench.workload_inputs(0)
+    n = len(E)
+    assert n == 100_000_000
     dE, dm = _dev(torch, E, torch.float64), _dev(torch, mat, torch.int32)
     idx = np.random.default_rng(5).choice(n, 20_000, replace=False)
-    p32 = _handle(lib, mats, mcx.FP32, 4000)
-    out = p32.xs_lookup(dE, dm, flags=mcx.LOOKUP_FAST | mcx.LOOKUP_SORT)
+    p32 = _handle(lib, mats, bench.TUNED["precision"], bench.TUNED["hash_bins"])
+    out = torch.empty((n, 5), dtype=torch.float64, device="cuda")
+    perm = torch.empty(n, dtype=torch.int32, device="cuda")
+    p32.xs_sort(dE, dm, perm)
+    p32.xs_lookup_ordered(dE, dm, perm, out=out, flags=bench.TUNED["flags"])
     got = out[torch.as_tensor(idx, device="cuda")].cpu().numpy()
     ref = oracle.xs_lookup(lib.fp32_rounded(), mats, E[idx], mat[idx], n_threads=8)
     rel = np.abs(got - ref) / np.maximum(np.abs(ref), 1e-300)
     assert np.all((ref == 0) <= (got == 0)), "an exactly-zero channel came out non-zero"
     assert rel.max() <= FAST_RTOL, rel.max()
-    del out
+    # the permutation is a permutation, and sorted by (material, energy bucket)
+    pm = perm.cpu().numpy()
+    assert pm.min() == 0 and pm.max() == n - 1 and np.bincount(pm, minlength=n).max() == 1
+    assert np.all(np.diff(mat[pm].astype(np.int64)) >= 0)
+    del out, perm
+    p32.close()
     p64 = _handle(lib, mats, mcx.FP64, 0)
     out64 = p64.xs_lookup(dE, dm)
     got64 = out64[torch.as_tensor(idx, device="cuda")].cpu().numpy()

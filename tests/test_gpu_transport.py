@@ -9,6 +9,7 @@ numerical characteristics; sorting only improves locality).
 import numpy as np
 import pytest
 
+import bench   # the launch settings the benchmark times
 import oracle
 from paper_2402_09222_b300 import synth
 
@@ -220,19 +221,55 @@ def test_batched_uneven_problems(mcx, mode):
             assert_tallies_close(h.tallies(), ref)
 
 
+N_SAMPLED = 10_000
+MATCH_MIN = 0.9999
+
+
+def _assert_batch_matches(g, ref, b, ncoll_match):
+    """Tallies of batch b against the oracle's run of that batch alone:
+    within 1e-9 relative where every history's collision count matched,
+    else within 3 standard errors (from the spread of the GPU's batches)."""
+    for k in ("flux", "absorb", "outcome"):
+        got, want = g[k][b], ref[k][b]
+        if ncoll_match:
+            scale = max(np.abs(want).max(), 1e-300)
+            np.testing.assert_allclose(got, want, rtol=TALLY_RTOL, atol=TALLY_RTOL * scale, err_msg=k)
+        else:
+            se = g[k].std(axis=0, ddof=1)
+            assert np.all(np.abs(got - want) <= 3 * se + 1e-9 * np.abs(want)), k
+
+
 @pytest.mark.parametrize("mode", [1, 2])
 def test_config3_full_size_sampled(mcx, mode):
-    """1e7 histories of the 17x17 lattice in the benchmark's launch; sampled
-    histories re-run one by one in the oracle; balance checked on the whole."""
-    prob = synth.config3_problem(n_histories=10_000_000)
-    g = run_gpu(mcx, prob, precision=mcx.FP32, pif=2_000_000, seed=31, mode=mode, sort_period=4,
-                sort_threshold=20_000)
-    rp = synth.config3_problem(n_histories=10_000_000, lib=prob.lib.fp32_rounded())
-    rng = np.random.default_rng(6)
-    idx = np.sort(rng.choice(prob.n_histories, 300, replace=False))
-    ref = np.array([oracle.transport(rp, seed=31, first=int(h), count=1, history_debug=True)["ncoll"][0]
-                    for h in idx])
-    assert np.mean(g["ncoll"][idx] == ref) >= 0.99
+    """1e7 histories of the 17x17 lattice in exactly the launch the benchmark
+    times (FP32 tables, its hash bins, particles in flight, block size, sort
+    period and threshold; mode 2 is the fullest-queue variant of the same
+    settings).  10,000 sampled histories re-run one by one in the oracle
+    (FP32-rounded tables) must match their collision counts at >= 99.99 %
+    (a flight-length logarithm one ulp away from the host's can flip a
+    collision-versus-surface decision); the first batch (500,000 contiguous
+    histories) is run whole in the oracle and its tallies compared; the
+    outcome balance holds on the whole run."""
+    import os
+    spec = bench.TRANSPORT_TUNED if mode == 1 else bench.TRANSPORT_FULLEST
+    n = bench.TRANSPORT_HIST
+    prob = synth.config3_problem(n_histories=n)
+    g = run_gpu(mcx, prob, precision=spec["precision"], H=spec["hash_bins"], pif=spec["pif"], seed=5,
+                **spec["tune"])
+    rp = synth.config3_problem(n_histories=n, lib=prob.lib.fp32_rounded())
+    cores = os.cpu_count() or 1
+    idx = np.sort(np.random.default_rng(6).choice(n, N_SAMPLED, replace=False))
+    ref = oracle.transport_histories(rp, 5, idx, n_threads=cores)
+    rate = float(np.mean(g["ncoll"][idx] == ref))
+    print(f"\nconfig3 mode {mode}: sampled collision-count match {rate:.6f} "
+          f"({int(np.sum(g['ncoll'][idx] != ref))} of {N_SAMPLED} differ)")
+    assert rate >= MATCH_MIN, rate
+    nb = n // prob.n_batches
+    rb = oracle.transport(rp, seed=5, first=0, count=nb, history_debug=True, n_threads=cores)
+    same = g["ncoll"][:nb] == rb["ncoll"]
+    print(f"config3 mode {mode}: batch 0 ({nb} histories) collision-count match {np.mean(same):.6f}")
+    assert np.mean(same) >= MATCH_MIN
+    _assert_batch_matches(g, rb, 0, bool(same.all()))
     out = g["outcome"].sum(0)
     assert out[:4].sum() == prob.n_histories
     assert out[4] == g["ncoll"].sum()
@@ -242,34 +279,54 @@ def test_config3_full_size_sampled(mcx, mode):
 
 def test_config5_full_size_sampled(mcx):
     """The 64 uneven lattices of the batched benchmark (2.76e7 histories) in
-    one event loop with the benchmark's launch settings: sampled histories of
-    every problem re-run one by one in the oracle (FP32-rounded tables) match
-    their collision counts, and each problem's histories all end in its own
-    outcome tallies."""
-    lib = synth.species_library(355, 11_303, 1236).channels([synth.CH_SCATTER, synth.CH_ABSORB])
-    mats = synth.lookup_materials(355, 1236)
+    one event loop with the benchmark's own settings: 10,000 histories
+    sampled over the problems (in proportion to their sizes) re-run one by
+    one in the oracle (FP32-rounded tables) match their collision counts at
+    >= 99.99 %, the smallest problem is compared whole (tallies too), and
+    each problem's histories all end in its own outcome tallies."""
+    import os
+    spec = bench.BATCHED_TUNED
+    lib = synth.species_library(bench.N_SPECIES, bench.N_POINTS, bench.LIB_SEED).channels(
+        [synth.CH_SCATTER, synth.CH_ABSORB])
+    mats = synth.lookup_materials(bench.N_SPECIES, bench.MAT_SEED)
     probs = synth.config5_problems(lib, mats, n_problems=64)
-    base = mcx.Problem(probs[0], flags=mcx.FLAG_HISTORY_DEBUG).load_tables(lib, mats, precision=mcx.FP32,
-                                                                           hash_bins=4000)
+    base = mcx.Problem(probs[0], flags=mcx.FLAG_HISTORY_DEBUG).load_tables(
+        lib, mats, precision=spec["precision"], hash_bins=spec["hash_bins"])
     hs = [base] + [mcx.Problem(pr, flags=mcx.FLAG_HISTORY_DEBUG).share_tables(base) for pr in probs[1:]]
-    base.set_tuning(mode=1, block_size=256, sort_period=1, sort_threshold=400_000)
-    mcx.batch_run(hs, [pr.n_histories for pr in probs], particles_in_flight=1_600_000, seed=9)
+    base.set_tuning(**spec["tune"])
+    nh = np.array([pr.n_histories for pr in probs])
+    mcx.batch_run(hs, list(nh), particles_in_flight=spec["pif"], seed=9)
     lib32 = lib.fp32_rounded()
+    cores = os.cpu_count() or 1
     rng = np.random.default_rng(17)
+    picks = np.sort(rng.choice(int(nh.sum()), N_SAMPLED, replace=False))
+    starts = np.concatenate([[0], np.cumsum(nh)])
     matched = total = 0
-    for h, pr in zip(hs, probs):
+    smallest = int(np.argmin(nh))
+    for i, (h, pr) in enumerate(zip(hs, probs)):
         nc = h.history_debug(pr.n_histories)
-        out = h.tallies()["outcome"].sum(0)
+        tal = h.tallies()
+        out = tal["outcome"].sum(0)
         assert out[:4].sum() == pr.n_histories
         assert out[4] == nc.sum()
         rp = synth.Problem(pr.geometry, lib32, pr.mats, lattice_n=pr.lattice_n,
                            region_material=pr.region_material, problem_id=pr.problem_id,
                            n_histories=pr.n_histories)
-        for hh in rng.choice(pr.n_histories, 4, replace=False):
-            ref = oracle.transport(rp, seed=9, first=int(hh), count=1, history_debug=True)["ncoll"][0]
-            matched += int(nc[hh] == ref)
-            total += 1
-    assert matched / total >= 0.99, (matched, total)
+        mine = picks[(picks >= starts[i]) & (picks < starts[i + 1])] - starts[i]
+        if len(mine):
+            ref = oracle.transport_histories(rp, 9, mine, n_threads=cores)
+            matched += int(np.sum(nc[mine] == ref))
+            total += len(mine)
+        if i == smallest:
+            whole = oracle.transport(rp, seed=9, history_debug=True, n_threads=cores)
+            same = nc == whole["ncoll"]
+            assert np.mean(same) >= MATCH_MIN
+            if same.all():
+                assert_tallies_close(tal, whole)
+    rate = matched / total
+    print(f"\nconfig5: sampled collision-count match {rate:.6f} ({total - matched} of {total} differ)")
+    assert total == N_SAMPLED
+    assert rate >= MATCH_MIN, (matched, total)
     for h in hs:
         h.close()
 

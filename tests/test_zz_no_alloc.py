@@ -38,19 +38,31 @@ def _call(torch, mcx, f, h, E, mat, flags):
 
 
 @pytest.mark.parametrize("flags", [0, 1])
-def test_static_scratch_matches_allocating_binned_lookup(env, flags):
+def test_static_scratch_matches_the_oracle_and_the_allocating_lookup(env, flags):
+    """Against the oracle on the FP32-rounded tables (the exact form bit for
+    bit, the fast form within 1e-6 relative) and against the allocating
+    binned lookup, on two calls in a row: a full-capacity batch, then a
+    smaller one over a different material mix (stale scratch must not leak
+    through)."""
+    import oracle
     torch, mcx, f = env
     lib = synth.species_library(60, 900, 501)
     mats = synth.lookup_materials(60, 502, n_materials=9)
     h = mcx.Problem(None).load_tables(lib, mats, precision=mcx.FP32, hash_bins=4000)
-    # two calls in a row with different batches: a large one, then a smaller
-    # one over a different material mix (stale scratch must not leak through)
+    lib32 = lib.fp32_rounded()
     for n, seed, n_mat in ((MAX_LOOKUPS, 503, 9), (123_457, 504, 4)):
         E, mat = synth.lookup_inputs(n, n_mat, seed)
         dE = torch.as_tensor(E, device="cuda")
         dm = torch.as_tensor(mat, device="cuda")
-        ref = h.xs_lookup(dE, dm, flags=flags | mcx.LOOKUP_SORT)
         got = _call(torch, mcx, f, h, dE, dm, flags)
+        want = oracle.xs_lookup(lib32, mats, E, mat, n_threads=8)
+        g = got.cpu().numpy()
+        if flags & mcx.LOOKUP_FAST:
+            rel = np.abs(g - want) / np.maximum(np.abs(want), 1e-300)
+            assert rel.max() <= FAST_RTOL, rel.max()
+        else:
+            assert np.array_equal(g.view(np.uint64), want.view(np.uint64))
+        ref = h.xs_lookup(dE, dm, flags=flags | mcx.LOOKUP_SORT)
         torch.testing.assert_close(got, ref, rtol=FAST_RTOL, atol=0.0)
 
 
