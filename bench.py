@@ -226,7 +226,9 @@ def time_derivatives(mcx, synth, lib3, n=2_000_000, seed=13, n_lookups=10_000_00
             "with_derivative_tallies": res["derivatives"],
             "overhead": res["plain"] / res["derivatives"] - 1.0,
             "lookup_backward": {"lookups_per_s": n_lookups / (a.elapsed_time(b) / 1e3),
-                                "form": "natural order, FP64 atomics into dsigma and ddensity"}}
+                                "form": "binned (material, log-E bucket); per warp and species, FP64 sums per "
+                                        "grid interval before one atomic per point and channel; densities summed "
+                                        "per block in shared memory"}}
 
 
 def run_reference(args, rank: int, world: int):

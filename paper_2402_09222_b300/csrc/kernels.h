@@ -45,6 +45,13 @@ int launch_hash_max_window(const Tables& t, int32_t* out, int grid, cudaStream_t
 int launch_xs_backward(const Tables& t, int64_t n, const double* E, const int32_t* mat,
                        const double* grad_out, double* grad_dens, double* grad_sigma, int grid,
                        cudaStream_t st);
+// The same adjoint over a binned order perm (lookups sorted by material and
+// log-energy bucket): warps of one material aggregate their contributions
+// per species and grid interval before the atomics (nnz material entries;
+// work: a chunk counter, zeroed by the launch).
+int launch_xs_backward_binned(const Tables& t, int64_t nnz, int64_t n, const double* E, const int32_t* mat,
+                              const int32_t* perm, const double* grad_out, double* grad_dens,
+                              double* grad_sigma, int sm_count, unsigned long long* work, cudaStream_t st);
 int launch_update_tables(const Tables& t, const double* dens_src, int64_t nnz, double* mden,
                          int4* ment, const double* sig_src, void* sigma, float4* frec,
                          cudaStream_t st);

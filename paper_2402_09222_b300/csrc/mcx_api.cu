@@ -748,6 +748,17 @@ int sort_device(mcx_problem* p, int64_t n, const double* E, const int32_t* mat, 
     return MCX_OK;
 }
 
+// Two chunk counters of in-order sweeps over binned orders and the staged
+// lookup kernel's error word.
+int ensure_work_ctr(mcx_problem* p)
+{
+    if (!p->work_ctr) {
+        TRY(dev_alloc(&p->work_ctr, 3));
+        CUDA_TRY(cudaMemset(p->work_ctr, 0, 3 * sizeof(unsigned long long)));
+    }
+    return MCX_OK;
+}
+
 // Lookup on device buffers, queued on `st`, in the order `perm` (or natural).
 // A binned order (perm != nullptr) on the fast path is swept in order by
 // warps claiming chunks from a counter (slot `ctr` of the problem's two),
@@ -760,10 +771,7 @@ int lookup_device_ordered(mcx_problem* p, int64_t n, const double* E, const int3
     const TableStore* ts = p->tables;
     unsigned long long* work = nullptr;
     if (perm && (flags & MCX_LOOKUP_FAST)) {
-        if (!p->work_ctr) {
-            TRY(dev_alloc(&p->work_ctr, 3));   // two chunk counters and the staged kernel's error word
-            CUDA_TRY(cudaMemset(p->work_ctr, 0, 3 * sizeof(unsigned long long)));
-        }
+        TRY(ensure_work_ctr(p));
         work = p->work_ctr + ctr;
     }
     int r = -2;
@@ -1511,9 +1519,14 @@ int mcx_xs_lookup_backward(mcx_problem* p, int64_t n, const double* E, const int
     if (n == 0) return MCX_OK;
     if (!E || !mat || !grad_out || !grad_dens || !grad_sigma) return fail(MCX_ERR_ARG, "NULL buffer");
     DeviceGuard dg(p->device);
-    if (launch_xs_backward(p->tables->view, n, E, mat, grad_out, grad_dens, grad_sigma, lookup_grid(p),
-                           (cudaStream_t)stream))
-        return fail(MCX_ERR_CUDA, "backward kernel launch failed");
+    cudaStream_t st = (cudaStream_t)stream;
+    // binned order, then warps that aggregate per species and grid interval
+    TRY(ensure_lookup_scratch(p, n, 0));
+    TRY(sort_device(p, n, E, mat, p->perm, st));
+    TRY(ensure_work_ctr(p));
+    if (launch_xs_backward_binned(p->tables->view, p->tables->nnz, n, E, mat, p->perm, grad_out, grad_dens,
+                                  grad_sigma, p->sm_count, p->work_ctr, st))
+        return fail(MCX_ERR_CUDA, "backward kernel launch failed: %s", cudaGetErrorString(cudaGetLastError()));
     return MCX_OK;
 }
 

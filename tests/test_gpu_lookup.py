@@ -172,6 +172,44 @@ def test_backward_matches_oracle_adjoint(torch_cuda):
     np.testing.assert_allclose(gs, gs_ref, rtol=1e-11, atol=1e-11 * np.abs(gs_ref).max())
 
 
+@pytest.mark.parametrize("precision,n_ch", [("fp64", 5), ("fp32", 5), ("fp32", 2), ("fp64", 1)])
+def test_backward_binned_dense_and_edge_cases(torch_cuda, precision, n_ch):
+    """The binned, per-warp aggregated adjoint against the oracle's sequential
+    adjoint: 1e6 lookups dense enough that most warps sit inside one grid
+    interval of every species (the closed form from the warp's totals), plus
+    warps that straddle grid points and edge energies: exact grid points,
+    below and above every grid (clamped fractions), zero, negative and
+    infinite energies, NaN energies and out-of-range materials (which must
+    contribute nothing), and a ragged tail."""
+    from paper_2402_09222_b300 import mcx
+    torch = torch_cuda
+    full = synth.species_library(40, 700, 221)
+    lib = full.channels(list(range(n_ch))) if n_ch != 5 else full
+    mats = synth.lookup_materials(40, 222, n_materials=5)
+    rng = np.random.default_rng(223)
+    n = 1_000_003
+    E, mat = synth.lookup_inputs(n, mats.n_materials, 224)
+    # half of the lookups crowd into a few narrow energy windows
+    centres = np.exp(rng.uniform(np.log(1e-3), np.log(1e6), 64))
+    half = n // 2
+    E[:half] = centres[rng.integers(0, 64, half)] * (1.0 + 1e-5 * rng.standard_normal(half))
+    E[half:half + 2000] = lib.energies[rng.integers(0, len(lib.energies), 2000)]
+    E[half + 2000:half + 2010] = [1e-9, 1e-6, 0.0, -1.0, -0.0, 3e7, 1e12, np.inf, 9.99e-6, 2e7]
+    E[half + 3000:half + 3005] = np.nan
+    mat[half + 4000:half + 4003] = [-1, mats.n_materials, 1 << 20]
+    G = rng.normal(size=(n, lib.n_ch))
+    ok = ~np.isnan(E) & (mat >= 0) & (mat < mats.n_materials)
+    ref_lib = lib if precision == "fp64" else lib.fp32_rounded()
+    gd_ref, gs_ref = oracle.xs_lookup_backward(ref_lib, mats, E[ok], mat[ok], G[ok])
+    p = _handle(lib, mats, mcx.FP64 if precision == "fp64" else mcx.FP32, 4000)
+    gd, gs = p.xs_lookup_backward(_dev(torch, E, torch.float64), _dev(torch, mat, torch.int32),
+                                  _dev(torch, G, torch.float64))
+    gd, gs = gd.cpu().numpy(), gs.cpu().numpy()
+    np.testing.assert_allclose(gd, gd_ref, rtol=1e-11, atol=1e-11 * np.abs(gd_ref).max())
+    np.testing.assert_allclose(gs, gs_ref, rtol=1e-11, atol=1e-11 * np.abs(gs_ref).max())
+    p.close()
+
+
 def test_config2_full_size_sampled(torch_cuda):
     """355 species x 11,303 points, 12 materials, 1e8 lookups with FP32 tables
     in exactly the launch the benchmark times (its hash-bin count, binning
