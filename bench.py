@@ -136,6 +136,31 @@ def algorithmic_bytes(mats, mat, sigma_bytes: int, n_ch: int = 5) -> float:
     return species_visits * (16 + 2 * n_ch * sigma_bytes) + len(mat) * (8 + 4 + 8 * n_ch)
 
 
+def compulsory_bytes(lib, mats, n: int, n_ch: int = 5, hash_bins: int = None) -> float:
+    """Bytes one binned launch cannot avoid moving: per lookup the energy (8),
+    material (4), permutation entry (4) and output row (8 n_ch); once per
+    launch every point record (32 B, FP32) and hash-window column (4 B per
+    bin) of the species the materials hold."""
+    H = TUNED["hash_bins"] if hash_bins is None else hash_bins
+    used = np.unique(mats.species)
+    pts = float(sum(lib.grid_offsets[s + 1] - lib.grid_offsets[s] for s in used))
+    return n * (8 + 4 + 4 + 8 * n_ch) + pts * 32 + len(used) * (H + 1) * 4
+
+
+def lookup_traffic():
+    """DRAM bytes per launch of the binned lookup kernel at this workload,
+    from the ncu summary in profiles/ -- only while the kernel source and the
+    hash-bin count are those the capture measured."""
+    path = os.path.join(ROOT, "profiles", "lookup_traffic.json")
+    if not os.path.exists(path):
+        return None
+    tr = json.load(open(path))
+    if (tr.get("kernel_source_hash") != kernel_source_hash() or tr.get("hash_bins") != TUNED["hash_bins"]
+            or N_LOOKUPS != 100_000_000):
+        return None
+    return tr
+
+
 def cpu_baseline(lib, mats, E, mat, n_sample: int = 8_000_000, n_single: int = 200_000):
     import oracle
     cores = os.cpu_count() or 1
@@ -195,8 +220,10 @@ def time_derivatives(mcx, synth, lib3, n=2_000_000, seed=13, n_lookups=10_000_00
     import torch
     prob = synth.config3_problem(n_histories=n, lib=lib3)
     res = {}
-    for name, flags in (("plain", 0), ("derivatives", mcx.FLAG_DERIVATIVES)):
-        p = mcx.make_problem(prob, precision=1, hash_bins=TRANSPORT_TUNED["hash_bins"], flags=flags)
+    dtal = {}
+    for name, flags, prec in (("plain", 0, 1), ("derivatives", mcx.FLAG_DERIVATIVES, 1),
+                              ("derivatives_fp64", mcx.FLAG_DERIVATIVES, 0)):
+        p = mcx.make_problem(prob, precision=prec, hash_bins=TRANSPORT_TUNED["hash_bins"], flags=flags)
         p.set_tuning(**TRANSPORT_TUNED["tune"])
         p.run(count=n // 10, particles_in_flight=TRANSPORT_TUNED["pif"], seed=seed)
         p.zero_tallies()
@@ -207,6 +234,8 @@ def time_derivatives(mcx, synth, lib3, n=2_000_000, seed=13, n_lookups=10_000_00
         b.record()
         torch.cuda.synchronize()
         res[name] = n / (a.elapsed_time(b) / 1e3)
+        if flags:
+            dtal[prec] = p.tallies()["dabsorb"]
         p.close()
     lib = synth.species_library(N_SPECIES, N_POINTS, LIB_SEED)
     mats = synth.lookup_materials(N_SPECIES, MAT_SEED)
@@ -222,9 +251,11 @@ def time_derivatives(mcx, synth, lib3, n=2_000_000, seed=13, n_lookups=10_000_00
     b.record()
     torch.cuda.synchronize()
     q.close()
+    B = dtal[1].shape[0]
     return {"unit": "particles/s", "histories": n, "plain": res["plain"],
             "with_derivative_tallies": res["derivatives"],
             "overhead": res["plain"] / res["derivatives"] - 1.0,
+            "fp32_vs_fp64_tables_dabsorb_se": tally_z(dtal[1].reshape(B, -1), dtal[0].reshape(B, -1)),
             "lookup_backward": {"lookups_per_s": n_lookups / (a.elapsed_time(b) / 1e3),
                                 "form": "binned (material, log-E bucket); per warp and species, FP64 sums per "
                                         "grid interval before one atomic per point and channel; densities summed "
@@ -278,11 +309,67 @@ def time_transport(mcx, synth, lib3, spec, seed, reps=1):
         ms = a.elapsed_time(b)
         best = ms if best is None else min(best, ms)
     st = p.stats()
-    out = p.tallies()["outcome"].sum(0)
+    tal = p.tallies()
+    out = tal["outcome"].sum(0)
     p.close()
     return {"particles_per_s": TRANSPORT_HIST / (best / 1e3), "ms": best,
             "collisions_per_history": float(out[4] / TRANSPORT_HIST),
-            "iterations": st["iterations"], "kernels": st["kernels"]}
+            "iterations": st["iterations"], "kernels": st["kernels"], "_tallies": tal}
+
+
+# Algorithmic HBM bytes per event of the transport's event kernels: the
+# particle-state fields each kernel reads and writes in the structure-of-
+# arrays layout (table gathers are L2-resident and queue appends are left
+# out).  Lookup: queue entry 4, E 8, material 4, flags 1 + 1, {Sigma_t,
+# Sigma_a} 16, plus 8 bytes per running-sum entry it stores (rows of the
+# material's species count rounded up to 4).  Flight: flags 1, problem 4,
+# x y z u v w 48, cell 4, history 8, draw counter 4, {Sigma_t, Sigma_a} 16,
+# material 4 read; x y z 24, draw counter 4, flags 1 written.  Collision:
+# queue entry 4, flags 1, problem 4, E 8, material 4, u v w 24, history 8,
+# draw counter 4, collision count 4, one 32-byte sector of the running sums
+# read; E 8, u v w 24, draw counter 4, collision count 4, flags 1 written.
+EVENT_BYTES = {"lookup": 34, "flight": 118, "collision": 138}
+
+
+def transport_roofline(mcx, synth, lib3, peak, seed=5):
+    """Per event kernel of the tuned lattice transport: device time from a
+    run with kernel timing on (plain launches with CUDA events around each
+    kernel), events counted on the device, algorithmic bytes per event
+    (EVENT_BYTES), achieved GB/s and the fraction of the HBM peak."""
+    spec = TRANSPORT_TUNED
+    prob = synth.config3_problem(n_histories=TRANSPORT_HIST, lib=lib3)
+    p = mcx.make_problem(prob, precision=spec["precision"], hash_bins=spec["hash_bins"])
+    p.set_tuning(**spec["tune"])
+    p.set_kernel_timing(True)
+    p.run(count=TRANSPORT_HIST // 10, particles_in_flight=spec["pif"], seed=seed)   # warm-up
+    p.zero_tallies()
+    p.run(particles_in_flight=spec["pif"], seed=seed)
+    ks = p.kernel_stats()
+    p.close()
+    ev = ks["events"]
+    nbytes = {"lookup": EVENT_BYTES["lookup"] * ev["lookups"] + 8 * ev["row_entries"],
+              "flight": EVENT_BYTES["flight"] * ev["flights"],
+              "collision": EVENT_BYTES["collision"] * ev["collisions"]}
+    counts = {"lookup": ev["lookups"], "flight": ev["flights"], "collision": ev["collisions"]}
+    res = {"config": "17x17 lattice, 1e7 histories, tuned settings, kernel timing on (no graphs)"}
+    for k in ("lookup", "flight", "collision"):
+        ms = ks["ms"][k]
+        ach = nbytes[k] / (ms / 1e3) / 1e9
+        res[k] = {"bound": "hbm", "events": counts[k], "bytes_per_event": nbytes[k] / max(counts[k], 1),
+                  "kernel_ms_total": ms, "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak}
+    return res
+
+
+def tally_z(a, b):
+    """max and median over bins of |mean_a - mean_b| in standard errors of the
+    difference of the two batch means (per-batch tallies [B][bins])."""
+    B = a.shape[0]
+    se = np.sqrt(a.var(axis=0, ddof=1) / B + b.var(axis=0, ddof=1) / B)
+    d = np.abs(a.sum(0) - b.sum(0)) / B
+    m = se > 0
+    z = d[m] / se[m]
+    return {"max": float(z.max()) if z.size else 0.0, "median": float(np.median(z)) if z.size else 0.0,
+            "bins": int(m.sum())}
 
 
 def time_large_library(mcx, synth, dE, dm, mat, out, perm, stream, reps=3):
@@ -428,6 +515,7 @@ def run_leg(args):
     TRANSPORT_HIST = args.histories
     if args.workload == "transport":
         r = time_transport(mcx, synth, synth.config3_library(), TRANSPORT_TUNED, seed=5)
+        r.pop("_tallies")
     else:
         r = time_eigenvalue(mcx, synth, n=args.histories)
     print(json.dumps({"workload": args.workload, **r}), flush=True)
@@ -512,26 +600,41 @@ def main():
 
     peak, peak_kind = measured_peaks()
     alg = algorithmic_bytes(mats, mat, 4)
+    comp = compulsory_bytes(lib, mats, len(mat))
     lk = sum(lookup_ms) / len(lookup_ms)
-    achieved = alg / (lk / 1e3) / 1e9
-    roofline = {"bound": "hbm", "kernel": "k_xs_lookup_fast<float> (binned order)",
+    tr = lookup_traffic()
+    traffic = tr["dram_bytes_per_launch"] if tr else None
+    # the roof: HBM; achieved = DRAM bytes one launch moved (ncu, this kernel
+    # source) over the launch's CUDA-event time
+    achieved = traffic / (lk / 1e3) / 1e9 if traffic else comp / (lk / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": "k_xs_lookup_warp2 (binned order)",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic,
+                "frac_basis": ("DRAM bytes per launch (ncu dram__bytes_read + write, this kernel source) / "
+                               "the launch's CUDA-event time" if traffic else
+                               "compulsory bytes / the launch's CUDA-event time (no current ncu traffic)"),
                 "peak_source": f"{peak_kind} HBM copy bandwidth (MEASURED_PEAKS.json)" if peak_kind == "measured"
                 else "fallback 6400 GB/s",
-                "traffic": None, "algorithmic_bytes_per_launch": alg,
-                "lookup_kernel_ms": lk, "sort_ms": sum(sort_ms) / len(sort_ms)}
-    tpath = os.path.join(ROOT, "profiles", "lookup_traffic.json")
-    if os.path.exists(tpath):
-        tr = json.load(open(tpath))
-        if (tr.get("kernel_source_hash") == kernel_source_hash()
-                and tr.get("hash_bins") == TUNED["hash_bins"] and N_LOOKUPS == 100_000_000):
-            roofline["traffic"] = tr["dram_bytes_per_launch"]
-            # what DRAM actually carried per second in that launch
-            roofline["dram_achieved"] = tr["dram_bytes_per_launch"] / (lk / 1e3) / 1e9
-            roofline["dram_frac"] = roofline["dram_achieved"] / peak
+                "lookup_kernel_ms": lk, "sort_ms": sum(sort_ms) / len(sort_ms),
+                "compulsory_bytes_per_launch": comp,
+                "compulsory_frac": comp / (lk / 1e3) / 1e9 / peak,
+                "work_rate_GBs": alg / (lk / 1e3) / 1e9,
+                "algorithmic_bytes_per_launch": alg}
+    if tr:
+        roofline["traffic_source"] = tr.get("source")
+        if tr.get("issue_active_frac") is not None:
+            roofline["issue_active_frac"] = tr["issue_active_frac"]
+    roofline["note"] = ("frac: DRAM traffic measured by ncu over the kernel's own time. compulsory_bytes: the "
+                        "inputs, permutation and outputs once plus every table record and hash window the "
+                        "materials touch once. work_rate_GBs: the definition's bytes (every species' "
+                        "records and energies per lookup, 4,568 B per lookup on average) per second; binning "
+                        "lets a warp's lookups share each species' records, so that rate is not an HBM figure "
+                        "and exceeds the peak. issue_active_frac: the share of cycles the kernel issued an "
+                        "instruction (ncu, a 2e7-lookup capture): the binned kernel is bound by instruction "
+                        "issue and load latency, not by HBM")
 
-    # the same kernel on the natural (unbinned) order, where every species'
-    # records are a real gather from L2/HBM: the roofline of the gather itself
+    # the same kernel family on the natural (unbinned) order, where every
+    # species' records are a real gather from L2/HBM: the per-lane kernel
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     p.xs_lookup_ordered(dE, dm, None, out=out, flags=TUNED["flags"])
     a.record(stream)
@@ -539,20 +642,15 @@ def main():
     b.record(stream)
     torch.cuda.synchronize()
     nat_ms = a.elapsed_time(b)
-    nat = alg / (nat_ms / 1e3) / 1e9
-    roofline["natural_order"] = {"lookup_kernel_ms": nat_ms, "achieved": nat, "frac": nat / peak,
-                                 "lookups_per_s": N_LOOKUPS / (nat_ms / 1e3)}
-    if roofline["traffic"] is not None and tr.get("natural_dram_bytes_per_launch"):
+    roofline["natural_order"] = {"kernel": "k_xs_lookup_fast (per-lane form)", "lookup_kernel_ms": nat_ms,
+                                 "lookups_per_s": N_LOOKUPS / (nat_ms / 1e3),
+                                 "work_rate_GBs": alg / (nat_ms / 1e3) / 1e9}
+    if tr and tr.get("natural_dram_bytes_per_launch"):
         nd = tr["natural_dram_bytes_per_launch"]
-        roofline["natural_order"].update(traffic=nd, dram_achieved=nd / (nat_ms / 1e3) / 1e9,
-                                         dram_frac=nd / (nat_ms / 1e3) / 1e9 / peak)
-    roofline["note"] = ("achieved/frac count the definition's bytes (every species' records gathered per "
-                        "lookup); binning makes a warp's 32 lookups share each species' bracketing records, "
-                        "so that rate exceeds HBM while the DRAM traffic measured (`traffic`, "
-                        "`dram_achieved`) is ~8 % of those bytes: the binned kernel is bound by the latency "
-                        "of its dependent L1/L2 loads; unbinned, the same kernel runs DRAM at ~82 % of peak")
+        roofline["natural_order"].update(traffic=nd, achieved=nd / (nat_ms / 1e3) / 1e9,
+                                         frac=nd / (nat_ms / 1e3) / 1e9 / peak)
 
-    line = {"metric": "XS lookups/s (tuned lookup; particles/s of the transport in 'transport')",
+    line = {"metric": "XS lookups/s",
             "value": value, "unit": "lookups/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32 tables, f64 energies and search",
@@ -609,18 +707,57 @@ def main():
         del Eh, mh, oh32, out32
     if rank == 0 and world == 1 and not args.no_extras:
         # plain form: FP64 tables, exact arithmetic, full binary search, natural order
+        # the tuned output (FP32 tables, fast arithmetic, binned) for the precision block
+        p.xs_sort(dE, dm, perm)
+        p.xs_lookup_ordered(dE, dm, perm, out=out, flags=TUNED["flags"])
+        out64 = torch.empty_like(out)
         pp = mcx.Problem(None, device=local).load_tables(lib, mats, precision=0, hash_bins=0)
-        pp.xs_lookup(dE, dm, out=out)
+        pp.xs_lookup(dE, dm, out=out64)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        pp.xs_lookup(dE, dm, out=out)
+        pp.xs_lookup(dE, dm, out=out64)
         b.record(stream)
         torch.cuda.synchronize()
         pms = a.elapsed_time(b)
         line["plain"] = {"lookups_per_s": N_LOOKUPS / (pms / 1e3), "ms": pms,
                          "form": "FP64 tables, exact FP64 arithmetic, full binary search, unsorted",
-                         "achieved_alg_GBs": algorithmic_bytes(mats, mat, 8) / (pms / 1e3) / 1e9}
+                         "work_rate_GBs": algorithmic_bytes(mats, mat, 8) / (pms / 1e3) / 1e9}
         pp.close()
+        # FP64 against FP32 tables at equal algorithm (hash grid, binned order,
+        # exact arithmetic), and the errors of FP32 tables against the FP64
+        # definition (the plain form's outputs equal the definition bit for bit)
+        p64 = mcx.Problem(None, device=local).load_tables(lib, mats, precision=0, hash_bins=TUNED["hash_bins"])
+        out_e = torch.empty_like(out)
+
+        def timed_exact(h, o):
+            h.xs_lookup_ordered(dE, dm, perm, out=o, flags=mcx.LOOKUP_EXACT)
+            a.record(stream)
+            h.xs_lookup_ordered(dE, dm, perm, out=o, flags=mcx.LOOKUP_EXACT)
+            b.record(stream)
+            torch.cuda.synchronize()
+            return a.elapsed_time(b)
+
+        ms64 = timed_exact(p64, out_e)
+        p64.close()
+        ms32 = timed_exact(p, out_e)
+
+        def rel_err(o):
+            r = ((o - out64).abs() / out64.abs().clamp_min(1e-300))
+            return {"max": [float(x) for x in r.max(0).values.cpu()],
+                    "median": [float(x) for x in r.median(0).values.cpu()]}
+
+        line["precision_error"] = {
+            "reference": "FP64 tables, exact arithmetic, full search (equal to the FP64 definition bit for bit)",
+            "channels": ["total", "scatter", "absorb", "fission", "nu-fission"],
+            "lookup_fp32_tables_exact": rel_err(out_e),
+            "lookup_fp32_tables_fast_binned": rel_err(out),
+            "bound": "2^-24 = 5.96e-8 (exact) and 1e-6 + 2^-24 (fast), relative"}
+        line["fp64_vs_fp32_tables"] = {
+            "form": "exact arithmetic, 68,400 hash bins, binned order (the same permutation)",
+            "fp64_tables": {"ms": ms64, "lookups_per_s": N_LOOKUPS / (ms64 / 1e3)},
+            "fp32_tables": {"ms": ms32, "lookups_per_s": N_LOOKUPS / (ms32 / 1e3)},
+            "fp32_tables_fast_arithmetic": {"ms": lk, "lookups_per_s": N_LOOKUPS / (lk / 1e3)}}
+        del out64, out_e
         # transport, 17x17 lattice, 1e7 histories
         lib3 = synth.config3_library()
         line["transport"] = {
@@ -631,9 +768,16 @@ def main():
             # the same settings with the fullest-queue policy decided on the device
             "tuned_fullest_queue": time_transport(mcx, synth, lib3, TRANSPORT_FULLEST, seed=5),
         }
+        tt, tp = line["transport"]["tuned"].pop("_tallies"), line["transport"]["plain"].pop("_tallies")
+        line["transport"]["tuned_fullest_queue"].pop("_tallies", None)
+        line["precision_error"]["lattice_tallies_fp32_vs_fp64_tables_se"] = {
+            k: tally_z(tt[k], tp[k]) for k in ("flux", "absorb")}
+        line["transport"]["roofline"] = transport_roofline(mcx, synth, lib3, peak)
         line["transport"]["cpu_baseline"] = cpu_transport(synth, lib3)
         line["transport"]["inflight_sweep"] = time_inflight_sweep(mcx, synth, lib3)
         line["derivatives"] = time_derivatives(mcx, synth, lib3)
+        line["precision_error"]["derivative_tallies_fp32_vs_fp64_tables_se"] = \
+            line["derivatives"].pop("fp32_vs_fp64_tables_dabsorb_se")
         line["infinite_medium"] = time_infinite_medium(mcx, synth)
         line["eigenvalue"] = time_eigenvalue(mcx, synth)
         line["large_library"] = time_large_library(mcx, synth, dE, dm, mat, out, perm, stream)

@@ -290,6 +290,21 @@ int mcx_zero_tallies(mcx_problem* p);
  * pointer, n <= that run's n_histories.  Synchronous. */
 int mcx_read_history_debug(mcx_problem* p, uint32_t* ncoll, int64_t n);
 
+/* Kernel timing (an instrument of this library, no counterpart in the
+ * paper): with on = 1, later runs of the handle launch their event loop
+ * without graph capture and record CUDA events around the lookup, flight and
+ * collision kernels of every iteration (a run is slower than with graphs; its
+ * results are the same).  Errors: MCX_ERR_ARG. */
+int mcx_set_kernel_timing(mcx_problem* p, int32_t on);
+
+/* After a run with kernel timing on: ms[3] = summed device time of the
+ * lookup, flight and collision kernels (-1 when timing was off); counts[4] =
+ * lookups, flights and collisions of the run and the summed lengths of the
+ * running-sum rows the lookups wrote (each material's species count rounded
+ * up to a multiple of 4), in the queued mode (MCX_QUEUED); -1 in the other
+ * modes.  The counts are kept for every run.  Errors: MCX_ERR_ARG. */
+int mcx_last_kernel_stats(const mcx_problem* p, double* ms, int64_t* counts);
+
 /* Event-loop statistics of the last run: out[0] iterations (steps in
  * MCX_QUEUED_FULLEST), out[1] graph launches, out[2] kernel launches, and
  * when n >= 6, out[3..5] the steps that selected the lookup, flight and

@@ -203,6 +203,9 @@ struct RunCtl {
     unsigned long long sel_begin, sel_end;
     long long sel_count[3];   // steps that ran the lookup / flight / collision kernel
     unsigned long long lk_claim;  // queued mode: next unclaimed entry of the lookup queue
+    // queued mode, kernel timing runs: lookups, flights and collisions of the
+    // run, and the lookups' running-sum rows (species counts rounded up to 4)
+    long long ev_count[4];
 };
 
 // Ring queues of the fullest-queue mode and the events that consume them.
@@ -224,9 +227,13 @@ struct LoopConfig {
 
 // Kernels of one event-loop iteration, issued on `st` (capturable).
 // Returns the number of kernels launched, or -1 on a launch error.
+// ev (kernel timing runs, plain launches only): four events recorded around
+// the lookup, flight and collision kernels (before the lookup, after each);
+// in the queued mode the iteration then also counts the lookups' running-sum
+// rows into ctl->ev_count[3] (before the first event).
 int launch_iteration(const LoopConfig& c, const Tables& t, const Particles& P,
                      const ProblemDev* probs, const int64_t* work_off, RunCtl* ctl,
-                     cudaStream_t st);
+                     cudaStream_t st, const cudaEvent_t* ev = nullptr);
 // Reset the particle buffer and loop control for a run of `total` work items.
 // Fission bank of an eigenvalue generation (eigen.cu): per-history site
 // offsets (exclusive scan of the counts; tile_sum needs bank_scan_tiles(n) + 1

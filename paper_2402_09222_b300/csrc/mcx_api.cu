@@ -215,6 +215,11 @@ struct mcx_problem {
     unsigned long long* work_ctr = nullptr;  // chunk counters of the binned fast lookup (2)
     int64_t h_buf_cap = 0;
     int64_t stats[6] = {0, 0, 0, 0, 0, 0};
+    // kernel timing runs: plain launches with events around the event kernels
+    int kernel_timing = 0;
+    std::vector<cudaEvent_t> kt_ev;   // 4 per iteration of one sync window
+    double kt_ms[3] = {0.0, 0.0, 0.0};
+    int64_t kt_count[4] = {0, 0, 0, 0};
     // eigenvalue runs: staging bank, ordered bank, next source, per-history
     // site counts and offsets, per-generation accumulators
     EigenCtl* e_ctl = nullptr;
@@ -661,19 +666,37 @@ int run_loop(mcx_problem* owner, int n_prob, mcx_problem* const* probs, const in
     int64_t launches = 0, kernels = 0;
     const int64_t max_launches = max_iters / K + 4;
     int status = MCX_OK;
+    const bool timing = owner->kernel_timing != 0;
+    if (timing) {
+        while ((int)owner->kt_ev.size() < 4 * K) {
+            cudaEvent_t e = nullptr;
+            CUDA_TRY(cudaEventCreate(&e));
+            owner->kt_ev.push_back(e);
+        }
+        for (int e = 0; e < 3; ++e) owner->kt_ms[e] = 0.0;
+    }
     const auto t_start = std::chrono::steady_clock::now();
     for (;;) {
-        if (tu.use_graph) {
+        if (tu.use_graph && !timing) {
             CUDA_TRY(cudaGraphLaunch(owner->gexec, st));
         } else {
             for (int k = 0; k < K; ++k)
-                if (launch_iteration(c, t, owner->P, owner->d_probs, owner->d_work_off, owner->d_ctl, st) < 0)
+                if (launch_iteration(c, t, owner->P, owner->d_probs, owner->d_work_off, owner->d_ctl, st,
+                                     timing ? owner->kt_ev.data() + 4 * k : nullptr) < 0)
                     return fail(MCX_ERR_CUDA, "event kernel launch failed");
         }
         ++launches;
         kernels += (int64_t)K * kernels_per_iter;
         CUDA_TRY(cudaMemcpyAsync(owner->h_ctl, owner->d_ctl, sizeof(RunCtl), cudaMemcpyDeviceToHost, st));
         CUDA_TRY(cudaStreamSynchronize(st));
+        if (timing) {
+            for (int k = 0; k < K; ++k)
+                for (int e = 0; e < 3; ++e) {
+                    float ms = 0.f;
+                    CUDA_TRY(cudaEventElapsedTime(&ms, owner->kt_ev[4 * k + e], owner->kt_ev[4 * k + e + 1]));
+                    owner->kt_ms[e] += ms;
+                }
+        }
         if (owner->h_ctl->error) {
             status = owner->h_ctl->error == MCX_ERR_ITER_LIMIT
                          ? fail(MCX_ERR_ITER_LIMIT, "event loop reached its cap of %lld iterations",
@@ -698,6 +721,7 @@ int run_loop(mcx_problem* owner, int n_prob, mcx_problem* const* probs, const in
     owner->stats[2] = kernels;
     for (int e = 0; e < 3; ++e)
         owner->stats[3 + e] = c.mode == MCX_QUEUED_FULLEST ? owner->h_ctl->sel_count[e] : 0;
+    for (int e = 0; e < 4; ++e) owner->kt_count[e] = c.mode == MCX_QUEUED ? owner->h_ctl->ev_count[e] : -1;
     CUDA_TRY(cudaEventRecord(owner->ev_b, st));
     CUDA_TRY(cudaStreamWaitEvent(us, owner->ev_b, 0));
     return status;
@@ -954,6 +978,8 @@ void mcx_destroy(mcx_problem* p)
     if (!p) return;
     DeviceGuard dg(p->device);
     if (p->stream) cudaStreamSynchronize(p->stream);
+    for (cudaEvent_t e : p->kt_ev) cudaEventDestroy(e);
+    p->kt_ev.clear();
     drop_graph(p);
     release_tables(p);
     free_particles(p);
@@ -1379,6 +1405,25 @@ int mcx_read_history_debug(mcx_problem* p, uint32_t* ncoll, int64_t n)
     DeviceGuard dg(p->device);
     CUDA_TRY(cudaStreamSynchronize(p->stream));
     CUDA_TRY(cudaMemcpy(ncoll, p->ncoll_debug, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost));
+    return MCX_OK;
+}
+
+int mcx_set_kernel_timing(mcx_problem* p, int32_t on)
+{
+    g_err.clear();
+    TRY(check_handle(p));
+    if (on != 0 && on != 1) return fail(MCX_ERR_ARG, "on must be 0 or 1");
+    p->kernel_timing = on;
+    return MCX_OK;
+}
+
+int mcx_last_kernel_stats(const mcx_problem* p, double* ms, int64_t* counts)
+{
+    g_err.clear();
+    TRY(check_handle(p));
+    if (!ms || !counts) return fail(MCX_ERR_ARG, "NULL buffer");
+    for (int e = 0; e < 3; ++e) ms[e] = p->kernel_timing ? p->kt_ms[e] : -1.0;
+    for (int e = 0; e < 4; ++e) counts[e] = p->kt_count[e];
     return MCX_OK;
 }
 

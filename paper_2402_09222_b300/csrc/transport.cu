@@ -820,6 +820,7 @@ __global__ void k_run_init(Particles P, RunCtl* ctl, long long total, int n_prob
         ctl->sel_begin = 0ull;
         ctl->sel_end = 0ull;
         for (int e = 0; e < 3; ++e) ctl->sel_count[e] = 0;
+        for (int e = 0; e < 4; ++e) ctl->ev_count[e] = 0;
     }
 }
 
@@ -1436,6 +1437,9 @@ __global__ void __launch_bounds__(1024) k_collide(LoopConfig c, Tables t, Partic
 __global__ void k_bookkeep(RunCtl* ctl)
 {
     const int p = ctl->parity;
+    ctl->ev_count[0] += ctl->n_xs[p];
+    ctl->ev_count[1] += ctl->n_adv[p];
+    ctl->ev_count[2] += ctl->n_coll;
     ctl->n_xs[p] = 0;
     ctl->n_adv[p] = 0;
     ctl->n_dead[p] = 0;
@@ -1452,6 +1456,22 @@ __global__ void k_bookkeep(RunCtl* ctl)
             ctl->done = 1;
         }
     }
+}
+
+// Kernel timing runs (queued mode): the running-sum row lengths this
+// iteration's lookups will write, each material's species count rounded up
+// to a multiple of 4 (the rows are stored four entries at a time).
+__global__ void k_census(Particles P, const int32_t* __restrict__ moff, RunCtl* ctl)
+{
+    const int par = ctl->parity;
+    const int64_t n = ctl->n_xs[par];
+    long long s = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t m = P.mat[P.q_xs[par][i]];
+        s += ((long long)(__ldg(moff + m + 1) - __ldg(moff + m)) + 3) & ~3LL;
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
+    if ((threadIdx.x & 31) == 0 && s) atomicAdd((unsigned long long*)&ctl->ev_count[3], (unsigned long long)s);
 }
 
 // Fullest-queue mode: retire the free-slot ring the refill just drained, stop
@@ -1661,7 +1681,7 @@ static int launch_sort(const LoopConfig& c, const Particles& P, RunCtl* ctl, int
 template <bool EIG>
 static int launch_iteration_t(const LoopConfig& c, const Tables& t, const Particles& P,
                               const ProblemDev* probs, const int64_t* work_off, RunCtl* ctl,
-                              cudaStream_t st)
+                              cudaStream_t st, const cudaEvent_t* ev)
 {
     int k = 0;
     const bool sorting = c.mode != MCX_QUEUELESS && c.sort_period > 0 && c.n_sort_bins > 0;
@@ -1673,27 +1693,38 @@ static int launch_iteration_t(const LoopConfig& c, const Tables& t, const Partic
         k_fq_select<<<1, 1, 0, st>>>(ctl, (long long)P.cap);
         ++k;
         if (sorting) k += launch_sort(c, P, ctl, 2, st);
+        if (ev) cudaEventRecord(ev[0], st);
         if (f32) k_lookup<float, EIG><<<c.grid, c.block, 0, st>>>(c, t, P, ctl);
         else k_lookup<double, EIG><<<c.grid, c.block, 0, st>>>(c, t, P, ctl);
+        if (ev) cudaEventRecord(ev[1], st);
         k_advance<EIG><<<c.grid, c.block, 0, st>>>(c, P, probs, ctl);
+        if (ev) cudaEventRecord(ev[2], st);
         if (f32) k_collide<float, EIG><<<c.grid, c.block, 0, st>>>(c, t, P, probs, ctl);
         else k_collide<double, EIG><<<c.grid, c.block, 0, st>>>(c, t, P, probs, ctl);
+        if (ev) cudaEventRecord(ev[3], st);
         k += 3;
         if (cudaGetLastError() != cudaSuccess) return -1;
         return k;
     }
     if (sorting) k += launch_sort(c, P, ctl, 0, st);
+    if (ev) {
+        if (c.mode == MCX_QUEUED) k_census<<<c.grid, 256, 0, st>>>(P, t.moff, ctl);
+        cudaEventRecord(ev[0], st);
+    }
     if (f32) k_lookup<float, EIG><<<c.grid, c.block, 0, st>>>(c, t, P, ctl);
     else k_lookup<double, EIG><<<c.grid, c.block, 0, st>>>(c, t, P, ctl);
     ++k;
+    if (ev) cudaEventRecord(ev[1], st);
     k_advance<EIG><<<c.grid, c.block, 0, st>>>(c, P, probs, ctl);
     ++k;
+    if (ev) cudaEventRecord(ev[2], st);
     // (the collision queue is not binned: one species per collision gains
     // less from the locality than the binning costs -- 654 -> 640 ms per 1e7
     // lattice histories without it)
     if (f32) k_collide<float, EIG><<<c.grid, c.block, 0, st>>>(c, t, P, probs, ctl);
     else k_collide<double, EIG><<<c.grid, c.block, 0, st>>>(c, t, P, probs, ctl);
     ++k;
+    if (ev) cudaEventRecord(ev[3], st);
     k_bookkeep<<<1, 1, 0, st>>>(ctl);
     ++k;
     if (cudaGetLastError() != cudaSuccess) return -1;
@@ -1704,10 +1735,10 @@ static int launch_iteration_t(const LoopConfig& c, const Tables& t, const Partic
 // that bank fission sites, fixed-source runs the ones without that code.
 int launch_iteration(const LoopConfig& c, const Tables& t, const Particles& P,
                      const ProblemDev* probs, const int64_t* work_off, RunCtl* ctl,
-                     cudaStream_t st)
+                     cudaStream_t st, const cudaEvent_t* ev)
 {
-    return c.eigen ? launch_iteration_t<true>(c, t, P, probs, work_off, ctl, st)
-                   : launch_iteration_t<false>(c, t, P, probs, work_off, ctl, st);
+    return c.eigen ? launch_iteration_t<true>(c, t, P, probs, work_off, ctl, st, ev)
+                   : launch_iteration_t<false>(c, t, P, probs, work_off, ctl, st, ev);
 }
 
 // Philox uniforms of one history stream (test hook).

@@ -89,6 +89,8 @@ _sig("mcx_read_tallies", C.c_int, _vp, _i32, _vp, _i64)
 _sig("mcx_zero_tallies", C.c_int, _vp)
 _sig("mcx_read_history_debug", C.c_int, _vp, _vp, _i64)
 _sig("mcx_last_run_stats", C.c_int, _vp, _vp, _i32)
+_sig("mcx_set_kernel_timing", C.c_int, _vp, _i32)
+_sig("mcx_last_kernel_stats", C.c_int, _vp, _vp, _vp)
 _sig("mcx_run_eigenvalue", C.c_int, _vp, _i64, _i32, _i32, C.c_double, C.c_double, _i64, C.c_uint64,
      _vp, _vp)
 _sig("mcx_fission_bank_size", C.c_int, _vp, C.POINTER(_i64))
@@ -282,6 +284,21 @@ class Problem:
         out = np.zeros(n, np.uint32)
         _check(_lib.mcx_read_history_debug(self.h, _np_ptr(out), n))
         return out
+
+    def set_kernel_timing(self, on: bool = True):
+        """Later runs launch without graphs and time each event kernel."""
+        _check(_lib.mcx_set_kernel_timing(self.h, 1 if on else 0))
+        return self
+
+    def kernel_stats(self) -> dict:
+        """Device ms of the lookup, flight and collision kernels of the last
+        run (kernel timing on) and its event counts (queued mode)."""
+        ms = np.zeros(3)
+        cnt = np.zeros(4, np.int64)
+        _check(_lib.mcx_last_kernel_stats(self.h, _np_ptr(ms), _np_ptr(cnt)))
+        return {"ms": dict(lookup=float(ms[0]), flight=float(ms[1]), collision=float(ms[2])),
+                "events": dict(lookups=int(cnt[0]), flights=int(cnt[1]), collisions=int(cnt[2]),
+                               row_entries=int(cnt[3]))}
 
     def stats(self) -> dict:
         out = np.zeros(6, np.int64)

@@ -106,3 +106,14 @@ def test_tuning_validation_without_device():
     t = mcx.Tune()
     mcx._lib.mcx_default_tuning(C.byref(t))
     assert (t.mode, t.block_size) == (0, 256)
+
+
+def test_kernel_timing_calls_validate_their_arguments():
+    import ctypes as C
+    from paper_2402_09222_b300 import mcx
+    lib = C.CDLL(mcx.LIB_PATH)
+    lib.mcx_set_kernel_timing.argtypes = [C.c_void_p, C.c_int32]
+    lib.mcx_last_kernel_stats.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.mcx_last_error.restype = C.c_char_p
+    assert lib.mcx_set_kernel_timing(None, 1) != 0
+    assert lib.mcx_last_kernel_stats(None, None, None) != 0

@@ -354,3 +354,32 @@ def test_simulated_allocation_failures_are_errors_and_leave_handles_usable(mcx, 
     p.run(particles_in_flight=1000, seed=7)
     assert_tallies_close(p.tallies(), ref)
     p.close()
+
+
+def test_kernel_timing_mode_changes_nothing(mcx, lattice):
+    """With kernel timing on (plain launches, events around the event
+    kernels) the run is history-matched as before; the per-kernel times are
+    positive and the event counts add up (queued mode)."""
+    prob, ref = lattice
+    p = mcx.make_problem(prob, flags=mcx.FLAG_HISTORY_DEBUG)
+    p.set_tuning(mode=1, sort_period=1, sort_threshold=0)
+    p.set_kernel_timing(True)
+    p.run(particles_in_flight=1234, seed=11)
+    nc = p.history_debug(prob.n_histories)
+    assert np.mean(nc == ref["ncoll"]) >= 0.9999
+    g = p.tallies()
+    if np.array_equal(nc, ref["ncoll"]):
+        assert_tallies_close(g, ref)
+    ks = p.kernel_stats()
+    assert all(v > 0 for v in ks["ms"].values()), ks
+    ev = ks["events"]
+    assert ev["collisions"] == int(g["outcome"][:, 4].sum())
+    assert ev["lookups"] >= prob.n_histories and ev["flights"] >= max(ev["collisions"], prob.n_histories)
+    sizes = np.diff(prob.mats.offsets)
+    assert 4 * ev["lookups"] <= ev["row_entries"] <= ((sizes.max() + 3) // 4 * 4) * ev["lookups"]
+    p.set_kernel_timing(False)
+    p.zero_tallies()
+    p.run(particles_in_flight=1234, seed=11)
+    assert p.kernel_stats()["ms"]["lookup"] == -1.0
+    assert np.array_equal(p.history_debug(prob.n_histories), nc)
+    p.close()
