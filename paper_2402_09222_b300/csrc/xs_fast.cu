@@ -21,6 +21,8 @@
 // accumulated compensated (~1u).  All terms are non-negative, so the errors
 // do not amplify: each output is within ~15u = 9e-7 of the FP64 definition,
 // under the 1e-6 bound (the largest measured on 1e6 samples: 3.7e-7).
+#include <cstdlib>
+
 #include "kernels.h"
 
 namespace mcx {
@@ -562,13 +564,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
     return ok != 0u;
 }
 
-// Wait for the phase of `parity` to complete, for at most kStWaitCycles.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
+// Wait for the phase of `parity` to complete, for at most `limit` cycles.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long limit = kStWaitCycles)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity))
-        if (clock64() - t0 > kStWaitCycles) return false;
+        if (clock64() - t0 > limit) return false;
     return true;
 }
 
@@ -738,7 +740,8 @@ __global__ void __launch_bounds__(kStThreads, MCX_STAGED_BLOCKS) k_xs_lookup_sta
                                                                     const int32_t* __restrict__ perm,
                                                                     OutT* __restrict__ out,
                                                                     unsigned long long* __restrict__ work,
-                                                                    unsigned int* __restrict__ err)
+                                                                    unsigned int* __restrict__ err,
+                                                                    long long wait_cycles, int stall)
 {
     using LY = StageLayout<W>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -766,7 +769,7 @@ __global__ void __launch_bounds__(kStThreads, MCX_STAGED_BLOCKS) k_xs_lookup_sta
         for (int k = 0;; ++k) {
             const int s = k % kStStages, use = k / kStStages;
             if (use > 0) {
-                if (!mbar_wait(&empty[s], (uint32_t)((use - 1) & 1))) {
+                if (!mbar_wait(&empty[s], (uint32_t)((use - 1) & 1), wait_cycles)) {
                     failed = true;
                     break;
                 }
@@ -784,6 +787,10 @@ __global__ void __launch_bounds__(kStThreads, MCX_STAGED_BLOCKS) k_xs_lookup_sta
                 }
                 break;
             }
+            // test hook: the first chunk is claimed but never staged nor
+            // signalled, so the consumers' wait on it runs out (no copies
+            // are in flight for it)
+            if (stall && k == 0) continue;
             const int bytes = producer_fill<W>(t, sp, n, Ein, mat, perm, (long long)b, stage, &full[s]);
             if (bytes > 0) {
                 issued[s] = true;
@@ -802,7 +809,7 @@ __global__ void __launch_bounds__(kStThreads, MCX_STAGED_BLOCKS) k_xs_lookup_sta
     const int c = threadIdx.x - 32;
     for (int k = 0;; ++k) {
         const int s = k % kStStages, use = k / kStStages;
-        if (!mbar_wait(&full[s], (uint32_t)(use & 1))) {
+        if (!mbar_wait(&full[s], (uint32_t)(use & 1), wait_cycles)) {
             if (lane == 0) atomicExch(err, 1u);
             break;
         }
@@ -958,8 +965,14 @@ static int launch_staged_nc(const Tables& t, const SortParams& sp, int64_t n, co
     if (cudaFuncSetAttribute(k_xs_lookup_staged<W, kFastUnroll, NC, OutT>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return -1;
+    // MCX_TEST_STAGED_STALL=1 (a test hook): the producers leave their first
+    // chunk unstaged and every wait is limited to about 0.1 ms, so the
+    // consumers' bounded waits run out and report through *err
+    const char* hook = std::getenv("MCX_TEST_STAGED_STALL");
+    const int stall = hook && hook[0] == '1' ? 1 : 0;
+    const long long wait_cycles = stall ? 200000LL : kStWaitCycles;
     k_xs_lookup_staged<W, kFastUnroll, NC, OutT><<<grid, kStThreads, smem, st>>>(t, sp, n, E, mat, perm, out, work,
-                                                                                 err);
+                                                                                 err, wait_cycles, stall);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

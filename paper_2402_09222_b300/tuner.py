@@ -426,6 +426,43 @@ def transport_objective(prob, seed: int = 1, precision: int = 1, device: int = 0
     return objective
 
 
+def batched_objective(lib, mats, probs, seed: int = 9, precision: int = 1, device: int = 0):
+    """Seconds of one event loop over many problems (mcx_batch_run: one global
+    work list, shared tables) under a configuration; the tuning of the first
+    handle governs the loop.  Hash-bin changes rebuild the shared tables'
+    hash grid in place."""
+    import torch
+    from . import mcx
+    base = mcx.Problem(probs[0], device=device).load_tables(lib, mats, precision=precision, hash_bins=4000)
+    hs = [base] + [mcx.Problem(pr, device=device).share_tables(base) for pr in probs[1:]]
+    nh = [pr.n_histories for pr in probs]
+    state = {"H": 4000}
+
+    def objective(cfg: dict, limit: float) -> float:
+        if cfg["hash_bins"] != state["H"]:
+            base.set_hash_bins(cfg["hash_bins"])
+            state["H"] = cfg["hash_bins"]
+        base.set_tuning(mode=cfg["mode"], block_size=cfg["block_size"],
+                        sort_period=cfg.get("sort_period", 0), sort_threshold=cfg.get("sort_threshold", 0),
+                        time_limit_s=limit)
+        for h in hs:
+            h.zero_tallies()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        try:
+            mcx.batch_run(hs, nh, cfg["particles_in_flight"], seed)
+        except mcx.McxError as e:
+            if e.code == mcx.ERR_TIMEOUT:
+                raise TimeoutError(str(e)) from e
+            raise
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / 1e3
+
+    return objective
+
+
 def lookup_objective(lib, mats, E, mat, precision: int = 1, device: int = 0, fast: bool = True):
     """Seconds of one binned-or-not lookup pass over device inputs E, mat."""
     import torch
@@ -461,10 +498,10 @@ def lookup_objective(lib, mats, E, mat, precision: int = 1, device: int = 0, fas
 
 
 def main(argv=None):
-    """python -m paper_2402_09222_b300.tuner --workload transport|lookup ..."""
+    """python -m paper_2402_09222_b300.tuner --workload transport|lookup|batched ..."""
     import argparse
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
-    ap.add_argument("--workload", choices=["transport", "lookup"], default="transport")
+    ap.add_argument("--workload", choices=["transport", "lookup", "batched"], default="transport")
     ap.add_argument("--histories", type=int, default=10_000_000)
     ap.add_argument("--lookups", type=int, default=100_000_000)
     ap.add_argument("--strategy", choices=["random+cd", "bo"], default="random+cd")
@@ -482,6 +519,13 @@ def main(argv=None):
         prob = synth.config3_problem(n_histories=args.histories)
         space = transport_space(device_scheduling=args.device_scheduling)
         obj = transport_objective(prob, seed=5, precision=1, metric=args.metric)
+    elif args.workload == "batched":
+        # 64 uneven lattices over the 12-material set (the batched workload)
+        lib = synth.species_library(355, 11_303, 1236).channels([synth.CH_SCATTER, synth.CH_ABSORB])
+        mats = synth.lookup_materials(355, 1236)
+        probs = synth.config5_problems(lib, mats, n_problems=64)
+        space = transport_space(device_scheduling=args.device_scheduling)
+        obj = batched_objective(lib, mats, probs, seed=9)
     else:
         lib = synth.species_library(355, 11_303, 1236)
         mats = synth.lookup_materials(355, 1236)

@@ -330,6 +330,34 @@ def test_staged_lookup_matches_the_direct_form_bit_for_bit(torch_cuda, n_ch, H):
     p.close()
 
 
+def test_staged_lookup_wait_that_runs_out_is_reported(torch_cuda, monkeypatch):
+    """The staged lookup's mbarrier waits are bounded.  With the test hook
+    MCX_TEST_STAGED_STALL=1 the producers leave their first chunk unstaged
+    and unsignalled (no copy is issued for it) and the waits are limited to
+    about 0.1 ms, so the consumers' waits run out: mcx_check_device must
+    report it, clear the flag, and the handle must compute correctly
+    afterwards."""
+    from paper_2402_09222_b300 import mcx
+    torch = torch_cuda
+    lib = synth.species_library(120, 3000, 111)
+    mats = synth.lookup_materials(120, 112, n_materials=9)
+    E, mat = synth.lookup_inputs(300_017, mats.n_materials, 113)
+    p = _handle(lib, mats, mcx.FP32, 4000)
+    dE, dm = _dev(torch, E, torch.float64), _dev(torch, mat, torch.int32)
+    perm = p.xs_sort(dE, dm)
+    monkeypatch.setenv("MCX_TEST_STAGED_STALL", "1")
+    p.xs_lookup_ordered(dE, dm, perm, flags=mcx.LOOKUP_FAST | mcx.LOOKUP_STAGED)
+    with pytest.raises(mcx.McxError, match="TIMEOUT"):
+        p.check_device()
+    monkeypatch.delenv("MCX_TEST_STAGED_STALL")
+    p.check_device()   # the flag was cleared
+    staged = p.xs_lookup_ordered(dE, dm, perm, flags=mcx.LOOKUP_FAST | mcx.LOOKUP_STAGED)
+    p.check_device()
+    direct = p.xs_lookup_ordered(dE, dm, perm, flags=mcx.LOOKUP_FAST)
+    assert torch.equal(staged.view(torch.int64), direct.view(torch.int64))
+    p.close()
+
+
 def test_staged_lookup_on_the_benchmark_tables(torch_cuda):
     """355 species x 11,303 points, materials up to 321 species, 4e6 binned
     lookups: staged and direct forms agree bit for bit."""

@@ -341,6 +341,57 @@ def test_pure_absorber_infinite_medium():
     assert np.count_nonzero(r["flux"].sum(0)) == 1
 
 
+def _two_species_flat(s1, a1, N1, s2, a2, N2, n_hist=20_000, A=1e6):
+    """An infinite medium of two species with constant cross sections; a huge
+    mass ratio keeps the energy (and so the cross sections) fixed."""
+    g = np.array([synth.E_MIN, synth.E_MAX])
+    lib = synth.Library(np.array([0, 2, 4], np.int64), np.concatenate([g, g]),
+                        np.array([[s1, a1], [s1, a1], [s2, a2], [s2, a2]]), np.array([A, A]))
+    mats = synth.make_materials([[0, 1]], [[N1, N2]])
+    return synth.infinite_problem(lib, mats, n_hist, E_cut=0.0)
+
+
+@pytest.mark.parametrize("case", [
+    # pure scatterer + pure absorber: a collision absorbs iff species 2 is
+    # chosen, P = N2 a2 / (N1 s1 + N2 a2) = 1 / 7
+    (3.0, 0.0, 2.0, 0.0, 2.0, 0.5, 1.0 / 7.0),
+    # both mixed: P(absorb) = sum_j P(j) a_j / t_j = Sigma_a / Sigma_t = 3.5 / 8
+    (2.0, 1.0, 2.0, 1.0, 3.0, 0.5, 3.5 / 8.0),
+])
+def test_species_selection_sets_the_absorption_probability(case):
+    """Species selection (Sec. 5.1 lookup feeding the collision; reading 7):
+    species j is chosen with probability N_j sigma_t,j / Sigma_t and absorbs
+    with sigma_a,j / sigma_t,j, so with flat cross sections every collision
+    absorbs with probability Sigma_a / Sigma_t and the collision count is
+    geometric with that parameter.  A running sum without the densities
+    gives 4/7 and 19/32, an exclusive running sum 1 and 3/4, the scattering
+    cross section in the absorption test 6/7 and 9/16."""
+    s1, a1, N1, s2, a2, N2, p = case
+    prob = _two_species_flat(s1, a1, N1, s2, a2, N2)
+    r = oracle.transport(prob, seed=31, history_debug=True)
+    n = r["ncoll"].astype(float)
+    assert abs(p - (N1 * a1 + N2 * a2) / (N1 * (s1 + a1) + N2 * (s2 + a2))) < 1e-15
+    _within_se(n.mean(), 1 / p, math.sqrt((1 - p) / p ** 2 / len(n)))
+    # every history ends absorbed; absorptions per collision = p
+    assert r["outcome"][:, oracle.OUT_ABSORBED].sum() == len(n)
+    coll = r["outcome"][:, oracle.OUT_COLLISIONS].sum()
+    _within_se(len(n) / coll, p, math.sqrt(p * (1 - p) / coll))
+
+
+def test_config1_flux_lands_in_the_source_energy_bin():
+    """A pure absorber never changes the particle's energy, so the whole
+    track-length flux of the 50-bin energy tally (log-spaced over
+    [1e-5, 2e7] eV) lands in the bin holding E0 = 2e6 eV: bin
+    floor(50 ln(E0 / 1e-5) / ln(2e7 / 1e-5)) = 45."""
+    prob = _flat_infinite(0.0, 0.7, n_hist=2000)
+    r = oracle.transport(prob, seed=11)
+    k = int(math.floor(50 * math.log(2e6 / 1e-5) / math.log(2e7 / 1e-5)))
+    assert k == 45
+    flux = r["flux"].sum(0)
+    assert flux[k] > 0 and np.count_nonzero(flux) == 1
+    assert r["absorb"].sum(0)[k] > 0 and np.count_nonzero(r["absorb"].sum(0)) == 1
+
+
 def test_collision_count_is_geometric():
     Ss, Sa = 2.0, 0.5
     prob = _flat_infinite(Ss, Sa, n_hist=20_000, E_cut=0.0)
