@@ -1098,6 +1098,13 @@ int mcx_load_xs_tables(mcx_problem* p, int32_t n_species, const int64_t* goff, c
     }
     for (int s2 = 0; s2 < n_species; ++s2)
         if (goff[s2 + 1] - goff[s2] > max_points) max_points = (int32_t)(goff[s2 + 1] - goff[s2]);
+    // reciprocal interval widths for the transport lookup's fraction (0 after
+    // a species' last point, which never starts an interval)
+    std::vector<double> winv((size_t)P, 0.0);
+    for (int32_t s2 = 0; s2 < n_species; ++s2)
+        for (int64_t k = goff[s2]; k + 1 < goff[s2 + 1]; ++k) winv[k] = 1.0 / (energies[k + 1] - energies[k]);
+    // fast-path point records {g_hi, g_lo, sigma_0 .. sigma_{n_ch-1}, ...};
+    // two-float4 records end with the FP32 reciprocal interval width
     const int frec_w = n_ch <= 2 ? 1 : 2;
     std::vector<float> rec((size_t)P * 4 * frec_w, 0.f);
     for (int64_t i = 0; i < P; ++i) {
@@ -1106,12 +1113,8 @@ int mcx_load_xs_tables(mcx_problem* p, int32_t n_species, const int64_t* goff, c
         r[0] = hi;
         r[1] = (float)(energies[i] - (double)hi);
         for (int c = 0; c < n_ch; ++c) r[2 + c] = (float)sigma[i * n_ch + c];
+        if (frec_w == 2) r[7] = (float)winv[i];
     }
-    // reciprocal interval widths for the transport lookup's fraction (0 after
-    // a species' last point, which never starts an interval)
-    std::vector<double> winv((size_t)P, 0.0);
-    for (int32_t s2 = 0; s2 < n_species; ++s2)
-        for (int64_t k = goff[s2]; k + 1 < goff[s2 + 1]; ++k) winv[k] = 1.0 / (energies[k + 1] - energies[k]);
     // elastic kinematics: E' = E (A^2 + 2 A mu + 1) / (A + 1)^2 multiplies by this
     std::vector<double> inv_a1sq((size_t)n_species);
     for (int32_t s2 = 0; s2 < n_species; ++s2) inv_a1sq[s2] = 1.0 / ((awr[s2] + 1.0) * (awr[s2] + 1.0));

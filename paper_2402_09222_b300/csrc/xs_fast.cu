@@ -14,13 +14,19 @@
 //   w1 = (E - g[k]) / (g[k+1] - g[k]),  w0 = (g[k+1] - E) / (g[k+1] - g[k])
 //   sigma = w0 * s[k] + w1 * s[k+1]          (both terms >= 0: no cancellation)
 //   Sigma_r accumulated as an unevaluated FP32 pair (hi, lo) with TwoSum.
-// Error budget (u = 2^-24): the distances a, b carry ~2u, a + b one more,
-// the fast division 2 ulp and the two weight products one each, so a weight
-// is within ~6u; the U species' 2U weighted terms of a group are added with
-// fused multiply-adds (2U roundings, 8u at U = 4) and the groups are
-// accumulated compensated (~1u).  All terms are non-negative, so the errors
-// do not amplify: each output is within ~15u = 9e-7 of the FP64 definition,
-// under the 1e-6 bound (the largest measured on 1e6 samples: 3.7e-7).
+// Records of 3-5 channels also carry r = float(1 / (g[k+1] - g[k])), and the
+// weights are w1 = N sat(a r), w0 = N sat(b r) with a = E - g[k], b =
+// g[k+1] - E from the pairs and sat() the saturation to [0, 1] (the clamp of
+// energies outside the grid); records of 1-2 channels have no spare slot and
+// divide instead: w1 = (N / (a + b)) a, w0 = (N / (a + b)) b.
+// Error budget (u = 2^-24): the distances a, b carry ~2u; r half a unit, the
+// two products one each, so a weight is within ~4u (~6u with the fast
+// division: a + b one more, the division 2 ulp); the U species' 2U weighted
+// terms of a group are added with fused multiply-adds (2U roundings, 8u at
+// U = 4) and the groups are accumulated compensated (~1u).  All terms are
+// non-negative, so the errors do not amplify: each output is within ~13u =
+// 7.7e-7 (~15u = 9e-7 dividing) of the FP64 definition, under the 1e-6 bound
+// (the largest measured on 1e8 outputs: 4.6e-7).
 #include <cstdlib>
 
 #include "kernels.h"
@@ -37,6 +43,11 @@ namespace {
 #endif
 #ifndef MCX_FAST_MIN_BLOCKS
 #define MCX_FAST_MIN_BLOCKS 4
+#endif
+// Records of two float4 (3 to 5 channels) carry the FP32 reciprocal of their
+// interval's width in their spare last slot, so the weights need no division.
+#ifndef MCX_FAST_RINV
+#define MCX_FAST_RINV 1
 #endif
 // Fast division for the density-scaled weight (<= 2 ulp): measured 9 % faster
 // than an IEEE-rounded reciprocal and still inside the 1e-6 budget.
@@ -168,14 +179,25 @@ template <int W, int NC>
 __device__ __forceinline__ void species_term(const float (&r0)[4 * W], const float (&r1)[4 * W], float E_hi,
                                              float E_lo, float N, float (&part)[NC])
 {
-    const float a = fmaxf((E_hi - r0[0]) + (E_lo - r0[1]), 0.f);
-    const float b = fmaxf((r1[0] - E_hi) + (r1[1] - E_lo), 0.f);
+    float w0, w1;
+    if constexpr (W == 2 && MCX_FAST_RINV) {
+        // records of two float4 carry 1 / (g[k+1] - g[k]) in their last slot:
+        // the fractions are the distances times it, saturated to [0, 1]
+        // (which is the clamp of energies outside the grid), no division
+        const float rw = r0[7];
+        w1 = N * __saturatef(((E_hi - r0[0]) + (E_lo - r0[1])) * rw);
+        w0 = N * __saturatef(((r1[0] - E_hi) + (r1[1] - E_lo)) * rw);
+    } else {
+        const float a = fmaxf((E_hi - r0[0]) + (E_lo - r0[1]), 0.f);
+        const float b = fmaxf((r1[0] - E_hi) + (r1[1] - E_lo), 0.f);
 #if MCX_FAST_FDIV
-    const float nw = __fdividef(N, a + b);   // <= 2 ulp: within the budget above
+        const float nw = __fdividef(N, a + b);   // <= 2 ulp: within the budget above
 #else
-    const float nw = N * __frcp_rn(a + b);
+        const float nw = N * __frcp_rn(a + b);
 #endif
-    const float w1 = nw * a, w0 = nw * b;
+        w1 = nw * a;
+        w0 = nw * b;
+    }
 #pragma unroll
     for (int r = 0; r < NC; ++r) {
 #if MCX_FAST_FMA2
@@ -411,13 +433,14 @@ __global__ void __launch_bounds__(256, MCX_FAST2_MIN_BLOCKS) k_xs_lookup_warp2(T
                     float p0[NC], p1[NC];
 #pragma unroll
                     for (int c = 0; c < NC; ++c) p0[c] = p1[c] = 0.f;
+                    const bool full = i + U <= i1;   // no padded slot in this group
 #pragma unroll
                     for (int u = 0; u < U; ++u) {
-                        const int32_t src = (i + u < i1 ? i + u : i1 - 1) - g0;
+                        const int32_t src = (full || i + u < i1 ? i + u : i1 - 1) - g0;
                         const int32_t b = __shfl_sync(FULLM, kb, src);
                         const int32_t d = __shfl_sync(FULLM, kd, src);
                         const float Nu = __shfl_sync(FULLM, Nq, src);
-                        const float N = i + u < i1 ? Nu : 0.f;
+                        const float N = full || i + u < i1 ? Nu : 0.f;
                         float r0[4 * W], r1[4 * W];
                         if (d > 0) {
                             int32_t bb = b, len = d + 1;
