@@ -346,7 +346,8 @@ __global__ void __launch_bounds__(256, MCX_FAST_MIN_BLOCKS) k_xs_lookup_fast(Tab
 // shrink it); chunks of 256 or 512 lookups 27.9 and 29.3 ms; each lane's
 // output rows and search keys parked in shared memory to relieve the
 // registers 26.9 ms; FP32 -> FP64 widening of the outputs with integer
-// operations instead of the FP64 pipe, no change.
+// operations instead of the FP64 pipe, no change; the rows and keys re-read
+// from the permutation when needed instead of held, 62.8 ms.
 template <int W, int U, int NC, typename OutT>
 __global__ void __launch_bounds__(256, MCX_FAST2_MIN_BLOCKS) k_xs_lookup_warp2(Tables t, int64_t n, const double* __restrict__ Ein,
                                                          const int32_t* __restrict__ mat,
