@@ -152,6 +152,28 @@ def compulsory_bytes(lib, mats, n: int, n_ch: int = 5, hash_bins: int = None) ->
     return n * (8 + 4 + 4 + 8 * n_ch) + pts * 32 + len(used) * (H + 1) * 4
 
 
+def host_link_bandwidth(host_buf, dev_buf, nbytes: int = 1 << 30) -> dict:
+    """Pinned host <-> device copy bandwidth (GB/s, one direction at a time,
+    best of 3), the bound of the end-to-end path: its 4 GB of FP64 outputs
+    leave through the device-to-host direction."""
+    import torch
+    del host_buf   # a dedicated pinned buffer: views of another may copy through a pageable path
+    hb = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    db = dev_buf.view(torch.uint8)[:nbytes]
+    res = {}
+    for name, (dst, src) in (("h2d", (db, hb)), ("d2h", (hb, db))):
+        best = None
+        for _ in range(3):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            dst.copy_(src, non_blocking=True)
+            torch.cuda.synchronize()
+            s = time.perf_counter() - t0
+            best = s if best is None else min(best, s)
+        res[name + "_GBs"] = nbytes / best / 1e9
+    return res
+
+
 def lookup_traffic():
     """DRAM bytes per launch of the binned lookup kernel at this workload,
     from the ncu summary in profiles/ -- only while the kernel source and the
@@ -683,7 +705,8 @@ def main():
             e2e_s = shard.max_over_ranks(e2e_s)
         line["e2e"] = {"value": world * N_LOOKUPS / e2e_s, "unit": "lookups/s",
                        "h2d_bytes_per_step": N_LOOKUPS * 12, "d2h_bytes_per_step": N_LOOKUPS * 40,
-                       "path": "mcx_xs_lookup_host, pinned host buffers, 8M-lookup chunks binned and looked up on 2 streams"}
+                       "path": "mcx_xs_lookup_host, pinned host buffers, 8M-lookup chunks binned and looked up on 2 streams",
+                       "host_link": host_link_bandwidth(oh, out)}
         del oh
         # the same with FP32 outputs (the compensated sums rounded once; still
         # within 1e-6 of the definition): half the device-to-host bytes
