@@ -378,6 +378,23 @@ def test_species_selection_sets_the_absorption_probability(case):
     _within_se(len(n) / coll, p, math.sqrt(p * (1 - p) / coll))
 
 
+@pytest.mark.parametrize("N,B", [(2000, 20), (1999, 20), (37, 5)])
+def test_histories_fall_in_batches_by_floor_h_B_over_N(N, B):
+    """History h scores into batch floor(h B / N) (reading 10): every history
+    ends in exactly one outcome, so batch b holds exactly the histories
+    ceil(b N / B) .. ceil((b + 1) N / B) - 1 -- N/B each when B divides N.
+    Histories taken modulo B, or floor(h B / (N + 1)), give other counts."""
+    prob = _flat_infinite(0.0, 0.7, n_hist=N, B=B)
+    r = oracle.transport(prob, seed=3)
+    per_batch = r["outcome"][:, :4].sum(1)
+    want = np.array([math.ceil((b + 1) * N / B) - math.ceil(b * N / B) for b in range(B)])
+    assert np.array_equal(per_batch, want)
+    # and a run of a sub-range scores only into the batches of its histories
+    r2 = oracle.transport(prob, seed=3, first=N // 2, count=N - N // 2)
+    got = np.nonzero(r2["outcome"][:, :4].sum(1))[0]
+    assert got.min() == (N // 2) * B // N and got.max() == B - 1
+
+
 def test_config1_flux_lands_in_the_source_energy_bin():
     """A pure absorber never changes the particle's energy, so the whole
     track-length flux of the 50-bin energy tally (log-spaced over
