@@ -166,6 +166,21 @@ int sm_count_of(int device)
 
 }  // namespace
 
+// Host-path pipeline of mcx_xs_lookup_host: chunks of kHostChunk lookups go
+// round-robin over kHostSlots streams, each with its own staging and binning
+// scratch (copy in, bin, look up, copy out), so the device-to-host copies of
+// one chunk overlap the copy-in and compute of the next ones.
+#ifndef MCX_HOST_SLOTS
+#define MCX_HOST_SLOTS 3
+#endif
+#ifndef MCX_HOST_CHUNK
+#define MCX_HOST_CHUNK (4 << 20)
+#endif
+constexpr int kHostSlots = MCX_HOST_SLOTS;
+constexpr int64_t kHostChunk = MCX_HOST_CHUNK;
+static_assert(kHostSlots >= 1 && kHostSlots <= 4, "host pipeline slots: 1 to 4 streams");
+constexpr int kWorkCtrs = 4;   // chunk counters (>= kHostSlots), then the error word
+
 struct mcx_problem {
     mcx_problem_desc desc{};
     std::vector<int32_t> region_material;
@@ -212,7 +227,8 @@ struct mcx_problem {
     int64_t perm_cap = 0;
     size_t lbins_cap = 0;
     double* h_buf = nullptr;  // host-path device staging
-    unsigned long long* work_ctr = nullptr;  // chunk counters of the binned fast lookup (2)
+    unsigned long long* work_ctr = nullptr;  // chunk counters of the binned fast lookup, then the staged kernel's error word
+    cudaStream_t hstream[2] = {nullptr, nullptr};   // host-path pipeline streams beyond stream and stream2
     int64_t h_buf_cap = 0;
     int64_t stats[6] = {0, 0, 0, 0, 0, 0};
     // kernel timing runs: plain launches with events around the event kernels
@@ -789,13 +805,14 @@ int sort_device(mcx_problem* p, int64_t n, const double* E, const int32_t* mat, 
     return MCX_OK;
 }
 
-// Two chunk counters of in-order sweeps over binned orders and the staged
-// lookup kernel's error word.
+// Chunk counters of in-order sweeps over binned orders (one per stream that
+// may run a binned lookup: the device paths use counter 0, the host path one
+// per pipeline slot), then the staged lookup kernel's error word.
 int ensure_work_ctr(mcx_problem* p)
 {
     if (!p->work_ctr) {
-        TRY(dev_alloc(&p->work_ctr, 3));
-        CUDA_TRY(cudaMemset(p->work_ctr, 0, 3 * sizeof(unsigned long long)));
+        TRY(dev_alloc(&p->work_ctr, kWorkCtrs + 1));
+        CUDA_TRY(cudaMemset(p->work_ctr, 0, (kWorkCtrs + 1) * sizeof(unsigned long long)));
     }
     return MCX_OK;
 }
@@ -819,7 +836,7 @@ int lookup_device_ordered(mcx_problem* p, int64_t n, const double* E, const int3
     if (work && (flags & MCX_LOOKUP_STAGED))
         r = launch_xs_lookup_staged(ts->view, lookup_sort_params(ts), n, E, mat, perm, out, out32,
                                     p->sm_count, st, work,
-                                    reinterpret_cast<unsigned int*>(p->work_ctr + 2));
+                                    reinterpret_cast<unsigned int*>(p->work_ctr + kWorkCtrs));
     if (r == -2) {
         const int grid = work ? p->sm_count * kFastBlocksPerSm : lookup_grid(p);
         r = (flags & MCX_LOOKUP_FAST)
@@ -1031,6 +1048,8 @@ void mcx_destroy(mcx_problem* p)
     if (p->ev_b) cudaEventDestroy(p->ev_b);
     if (p->stream) cudaStreamDestroy(p->stream);
     if (p->stream2) cudaStreamDestroy(p->stream2);
+    for (cudaStream_t& hs : p->hstream)
+        if (hs) cudaStreamDestroy(hs);
     delete p;
 }
 
@@ -1518,23 +1537,26 @@ int mcx_xs_lookup_host(mcx_problem* p, int64_t n, const double* E_host, const in
     DeviceGuard dg(p->device);
     const TableStore* ts = p->tables;
     const int nc = ts->view.n_ch;
-    const int64_t chunk = n < (int64_t)(8 << 20) ? n : (int64_t)(8 << 20);
+    const int64_t chunk = n < (int64_t)kHostChunk ? n : (int64_t)kHostChunk;
     const SortParams sp = lookup_sort_params(ts);
     const int64_t nbins = (int64_t)sp.n_materials * sp.n_ebuckets + 1;
-    // staging per stream (in doubles): E [chunk], mat [chunk int32], out
+    // staging per slot (in doubles): E [chunk], mat [chunk int32], out
     // [chunk * nc], binning permutation [chunk int32], bin counters [nbins]
     const int64_t per = chunk * (4 + nc) + nbins;
-    if (p->h_buf_cap < 2 * per) {
+    if (p->h_buf_cap < kHostSlots * per) {
         dev_free(p->h_buf);
         p->h_buf_cap = 0;
-        TRY(dev_alloc(&p->h_buf, (size_t)(2 * per)));
-        p->h_buf_cap = 2 * per;
+        TRY(dev_alloc(&p->h_buf, (size_t)(kHostSlots * per)));
+        p->h_buf_cap = kHostSlots * per;
     }
-    cudaStream_t ss[2] = {p->stream, p->stream2};
+    for (cudaStream_t& hs : p->hstream)
+        if (!hs) CUDA_TRY(cudaStreamCreateWithFlags(&hs, cudaStreamNonBlocking));
+    cudaStream_t ss[4] = {p->stream, p->stream2, p->hstream[0], p->hstream[1]};
     for (int64_t off = 0, c = 0; off < n; off += chunk, ++c) {
         const int64_t m = n - off < chunk ? n - off : chunk;
-        cudaStream_t st = ss[c & 1];
-        double* base = p->h_buf + (c & 1) * per;
+        const int slot = (int)(c % kHostSlots);
+        cudaStream_t st = ss[slot];
+        double* base = p->h_buf + slot * per;
         double* dE = base;
         int32_t* dM = (int32_t*)(base + chunk);
         double* dO = base + 2 * chunk;
@@ -1549,12 +1571,11 @@ int mcx_xs_lookup_host(mcx_problem* p, int64_t n, const double* E_host, const in
             perm = dP;
         }
         TRY(lookup_device_ordered(p, m, dE, dM, perm, dO,
-                                  flags & (MCX_LOOKUP_FAST | MCX_LOOKUP_STAGED | MCX_LOOKUP_OUT32), st, (int)(c & 1)));
+                                  flags & (MCX_LOOKUP_FAST | MCX_LOOKUP_STAGED | MCX_LOOKUP_OUT32), st, slot));
         CUDA_TRY(cudaMemcpyAsync(static_cast<char*>(out_host) + (size_t)off * nc * es, dO, es * m * nc,
                                  cudaMemcpyDeviceToHost, st));
     }
-    CUDA_TRY(cudaStreamSynchronize(ss[0]));
-    CUDA_TRY(cudaStreamSynchronize(ss[1]));
+    for (int k = 0; k < kHostSlots; ++k) CUDA_TRY(cudaStreamSynchronize(ss[k]));
     if (flags & MCX_LOOKUP_STAGED) return mcx_check_device(p, nullptr);
     return MCX_OK;
 }
@@ -1745,9 +1766,9 @@ int mcx_check_device(mcx_problem* p, void* stream)
     DeviceGuard dg(p->device);
     unsigned long long w = 0ull;
     CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
-    CUDA_TRY(cudaMemcpy(&w, p->work_ctr + 2, sizeof(w), cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemcpy(&w, p->work_ctr + kWorkCtrs, sizeof(w), cudaMemcpyDeviceToHost));
     if (w == 0ull) return MCX_OK;
-    CUDA_TRY(cudaMemset(p->work_ctr + 2, 0, sizeof(w)));
+    CUDA_TRY(cudaMemset(p->work_ctr + kWorkCtrs, 0, sizeof(w)));
     return fail(MCX_ERR_TIMEOUT, "a staged lookup kernel gave up waiting on its pipeline");
 }
 
