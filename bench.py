@@ -159,7 +159,8 @@ def host_link_bandwidth(host_buf, dev_buf, nbytes: int = 1 << 30) -> dict:
     import torch
     del host_buf   # a dedicated pinned buffer: views of another may copy through a pageable path
     hb = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
-    db = dev_buf.view(torch.uint8)[:nbytes]
+    db = dev_buf.reshape(-1).view(torch.uint8)[:nbytes]
+    assert db.numel() == nbytes and hb.numel() == nbytes
     res = {}
     for name, (dst, src) in (("h2d", (db, hb)), ("d2h", (hb, db))):
         best = None
