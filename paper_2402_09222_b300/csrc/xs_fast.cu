@@ -86,10 +86,13 @@ constexpr int kSmemBins = 12288;   // histograms up to this size count in shared
 #ifndef MCX_FAST2_MIN_BLOCKS
 #define MCX_FAST2_MIN_BLOCKS 4
 #endif
+// Lookups a warp claims at a time in binned order: one 64-lookup round of the
+// warp-cooperative form (24.9 ms per 1e8 against 25.2 for 128 and 25.5 for 256).
 #ifndef MCX_FAST_CHUNK
-#define MCX_FAST_CHUNK 128
+#define MCX_FAST_CHUNK 64
 #endif
-constexpr int kChunk = MCX_FAST_CHUNK;   // lookups a warp claims at a time in binned order
+constexpr int kChunk = MCX_FAST_CHUNK;
+static_assert(kChunk % 64 == 0, "whole rounds of the warp-cooperative form");
 
 __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x)
 {
@@ -341,7 +344,8 @@ __global__ void __launch_bounds__(256, MCX_FAST_MIN_BLOCKS) k_xs_lookup_fast(Tab
 // whose lookups mix materials or hold an invalid lookup (and the ragged
 // tail) take lookup_one.  Measured per 1e8 binned lookups (355 x 11,303
 // library, 68,400 hash bins): 25.6 ms against 28.4 ms for lookup_one in the
-// same order; one lookup per lane 27.0 ms; the records of 32 species staged
+// same order; one lookup per lane 27.0 ms; 128-thread blocks (8 per SM) the
+// same as 256; the records of 32 species staged
 // in shared memory by cp.async 33.0 ms (the copies bypass L1, and the buffers
 // shrink it); chunks of 256 or 512 lookups 27.9 and 29.3 ms; each lane's
 // output rows and search keys parked in shared memory to relieve the
