@@ -357,6 +357,12 @@ def time_transport(mcx, synth, lib3, spec, seed, reps=1):
 # draw counter 4, collision count 4, one 32-byte sector of the running sums
 # read; E 8, u v w 24, draw counter 4, collision count 4, flags 1 written.
 EVENT_BYTES = {"lookup": 34, "flight": 118, "collision": 138}
+# What bounds each event kernel instead of HBM, from ncu in the bulk of the
+# timed run (profiles/transport_config3_kernels.md): the unit and its share of
+# its peak.
+EVENT_BOUND = {"lookup": {"unit": "L1TEX", "pct_of_peak": 74.6},
+               "flight": {"unit": "FP64 pipe", "pct_of_peak": 78.8},
+               "collision": {"unit": "FP64 pipe", "pct_of_peak": 66.7}}
 
 
 def transport_roofline(mcx, synth, lib3, peak, seed=5):
@@ -384,7 +390,8 @@ def transport_roofline(mcx, synth, lib3, peak, seed=5):
         ms = ks["ms"][k]
         ach = nbytes[k] / (ms / 1e3) / 1e9
         res[k] = {"bound": "hbm", "events": counts[k], "bytes_per_event": nbytes[k] / max(counts[k], 1),
-                  "kernel_ms_total": ms, "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak}
+                  "kernel_ms_total": ms, "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                  "measured_bound": dict(EVENT_BOUND[k], source="ncu, bulk iteration of the 1e7-history run")}
     return res
 
 
