@@ -2,6 +2,8 @@
 // (mcx_api.cu) and the kernel translation units.  Not part of the public ABI.
 #pragma once
 
+#include <cmath>
+
 #include "mcx_internal.cuh"
 
 namespace mcx {
@@ -21,6 +23,27 @@ struct SortParams {
     int32_t n_ebuckets = 1;
     float ln_lo = 0.f, scale = 0.f;  // bucket = (ln E - ln_lo) * scale
 };
+
+// Lookups per (material, log-energy bucket) the binning of a lookup batch
+// aims at on average.  A warp's 64-lookup round then spans about one bucket,
+// so the fewer grid points a bucket holds, the fewer species' bracketing
+// intervals a round straddles; finer buckets leave rounds spanning several.
+constexpr int64_t kLookupsPerBucket = 128;
+
+// Binning parameters of a batch of n lookups over n_materials materials with
+// energies in [emin, emax]: n / (n_materials * kLookupsPerBucket) buckets per
+// material (at least 1), at most max_bins bins in all.
+inline SortParams lookup_sort_params(int n_materials, double emin, double emax, int64_t n, int64_t max_bins)
+{
+    SortParams sp;
+    sp.n_materials = n_materials;
+    int64_t nb = n / ((int64_t)n_materials * kLookupsPerBucket);
+    if (nb > max_bins / n_materials) nb = max_bins / n_materials;
+    sp.n_ebuckets = nb < 1 ? 1 : (int32_t)nb;
+    sp.ln_lo = (float)std::log(emin);
+    sp.scale = (float)((double)sp.n_ebuckets / (std::log(emax) - std::log(emin)));
+    return sp;
+}
 
 // The TMA-staged form of the binned fast lookup (perm and work required; err
 // receives 1 if a bounded wait ran out).  Returns -2 when a material is too
@@ -62,8 +85,10 @@ int launch_debug_uniforms(uint2 key, uint64_t hist, uint32_t first, int64_t n, d
                           cudaStream_t st);
 
 // Counting sort of lookups by key = material * n_ebuckets + log-energy bucket.
-// Scratch: bins [n_materials * n_ebuckets + 1] uint32.  perm receives the
+// Scratch: bins [n_materials * n_ebuckets + 1 + kSortScanParts] uint32 (the
+// counters, then the part sums of the multi-block scan).  perm receives the
 // lookup indices in bin order.
+constexpr int kSortScanParts = 1024;
 int launch_lookup_sort(const SortParams& sp, int64_t n, const double* E, const int32_t* mat,
                        uint32_t* bins, int32_t* perm, int grid, cudaStream_t st);
 
@@ -75,6 +100,7 @@ struct LookupView {
     int device = 0;
     int grid = 0;
     int sm_count = 0;
+    double emin = 0.0, emax = 0.0;   // energy range of the binning
 };
 
 }  // namespace mcx

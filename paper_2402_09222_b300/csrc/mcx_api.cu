@@ -773,32 +773,24 @@ int ensure_lookup_scratch(mcx_problem* p, int64_t n, size_t)
     return MCX_OK;
 }
 
-// Binning of lookups: 16384 log-energy buckets per material (about one per
-// grid interval of the benchmark's 11,303-point grids, so a warp of binned
-// lookups mostly shares its bracketing points), fewer when materials x
-// buckets would exceed max_bins.
-SortParams lookup_sort_params(const TableStore* ts, int64_t max_bins = (int64_t)1 << 21)
+// Binning of a batch of n lookups (about kLookupsPerBucket lookups per
+// material and log-energy bucket), at most max_bins bins.
+SortParams batch_sort_params(const TableStore* ts, int64_t n, int64_t max_bins = (int64_t)1 << 21)
 {
-    SortParams sp;
-    sp.n_materials = ts->view.n_materials;
-    sp.n_ebuckets = 16384;
-    while (sp.n_ebuckets > 1 && (int64_t)sp.n_materials * sp.n_ebuckets > max_bins) sp.n_ebuckets >>= 1;
-    sp.ln_lo = (float)std::log(ts->emin);
-    sp.scale = (float)((double)sp.n_ebuckets / (std::log(ts->emax) - std::log(ts->emin)));
-    return sp;
+    return lookup_sort_params(ts->view.n_materials, ts->emin, ts->emax, n, max_bins);
 }
 
 // Bin lookups into perm (device, [n]); bins scratch owned by the problem.
 int sort_device(mcx_problem* p, int64_t n, const double* E, const int32_t* mat, int32_t* perm,
                 cudaStream_t st)
 {
-    const SortParams sp = lookup_sort_params(p->tables);
-    const size_t nb = (size_t)sp.n_materials * sp.n_ebuckets;
-    if (p->lbins_cap < nb + 1) {
+    const SortParams sp = batch_sort_params(p->tables, n);
+    const size_t nb = (size_t)sp.n_materials * sp.n_ebuckets + 1 + kSortScanParts;
+    if (p->lbins_cap < nb) {
         dev_free(p->lbins);
         p->lbins_cap = 0;
-        TRY(dev_alloc(&p->lbins, nb + 1));
-        p->lbins_cap = nb + 1;
+        TRY(dev_alloc(&p->lbins, nb));
+        p->lbins_cap = nb;
     }
     if (launch_lookup_sort(sp, n, E, mat, p->lbins, perm, lookup_grid(p), st))
         return fail(MCX_ERR_CUDA, "lookup sort launch failed");
@@ -834,7 +826,7 @@ int lookup_device_ordered(mcx_problem* p, int64_t n, const double* E, const int3
     }
     int r = -2;
     if (work && (flags & MCX_LOOKUP_STAGED))
-        r = launch_xs_lookup_staged(ts->view, lookup_sort_params(ts), n, E, mat, perm, out, out32,
+        r = launch_xs_lookup_staged(ts->view, batch_sort_params(ts, n), n, E, mat, perm, out, out32,
                                     p->sm_count, st, work,
                                     reinterpret_cast<unsigned int*>(p->work_ctr + kWorkCtrs));
     if (r == -2) {
@@ -903,7 +895,9 @@ int problem_lookup_view(const mcx_problem* p, LookupView* v)
     TRY(check_tables(p));
     const TableStore* ts = p->tables;
     v->tables = ts->view;
-    v->sort = lookup_sort_params(ts, MCX_STATIC_MAX_BINS);
+    v->sort = batch_sort_params(ts, MCX_STATIC_MAX_LOOKUPS, MCX_STATIC_MAX_BINS);
+    v->emin = ts->emin;
+    v->emax = ts->emax;
     v->device = p->device;
     v->grid = lookup_grid(p);
     v->sm_count = p->sm_count;
@@ -1538,11 +1532,12 @@ int mcx_xs_lookup_host(mcx_problem* p, int64_t n, const double* E_host, const in
     const TableStore* ts = p->tables;
     const int nc = ts->view.n_ch;
     const int64_t chunk = n < (int64_t)kHostChunk ? n : (int64_t)kHostChunk;
-    const SortParams sp = lookup_sort_params(ts);
-    const int64_t nbins = (int64_t)sp.n_materials * sp.n_ebuckets + 1;
+    const SortParams sp = batch_sort_params(ts, chunk);
+    const int64_t nbins = (int64_t)sp.n_materials * sp.n_ebuckets + 1 + kSortScanParts;
     // staging per slot (in doubles): E [chunk], mat [chunk int32], out
-    // [chunk * nc], binning permutation [chunk int32], bin counters [nbins]
-    const int64_t per = chunk * (4 + nc) + nbins;
+    // [chunk * nc], binning permutation [chunk int32], bin scratch [nbins
+    // uint32, rounded up to whole doubles]
+    const int64_t per = chunk * (4 + nc) + (nbins + 1) / 2;
     if (p->h_buf_cap < kHostSlots * per) {
         dev_free(p->h_buf);
         p->h_buf_cap = 0;

@@ -23,7 +23,7 @@ namespace {
 
 // Scratch shared by every call of the entry point on a device.
 static __device__ __align__(256) int32_t g_static_perm[MCX_STATIC_MAX_LOOKUPS];
-static __device__ __align__(256) uint32_t g_static_bins[MCX_STATIC_MAX_BINS + 1];
+static __device__ __align__(256) uint32_t g_static_bins[MCX_STATIC_MAX_BINS + 1 + mcx::kSortScanParts];
 // Chunk counter of the fast lookup's in-order sweep of the binned order
 // (zeroed on the stream by every launch).
 static __device__ __align__(256) unsigned long long g_static_work;
@@ -86,7 +86,8 @@ extern "C" int mcx_xs_lookup_binned_static(mcx_problem* p, int64_t n, const doub
                               "n exceeds MCX_STATIC_MAX_LOOKUPS (1048576) of the static-scratch lookup; "
                               "split the batch or use mcx_xs_lookup");
     if (flags & ~MCX_LOOKUP_FAST) return mcx::set_error(MCX_ERR_ARG, "flags may hold MCX_LOOKUP_FAST only");
-    const int64_t nbins = (int64_t)v.sort.n_materials * v.sort.n_ebuckets;
+    const mcx::SortParams sp = mcx::lookup_sort_params(v.sort.n_materials, v.emin, v.emax, n, MCX_STATIC_MAX_BINS);
+    const int64_t nbins = (int64_t)sp.n_materials * sp.n_ebuckets;
     if (nbins > MCX_STATIC_MAX_BINS)
         return mcx::set_error(MCX_ERR_ARG, "too many materials for the static bin array");
     if (n == 0) return MCX_OK;
@@ -104,7 +105,7 @@ extern "C" int mcx_xs_lookup_binned_static(mcx_problem* p, int64_t n, const doub
         // contents otherwise); the permutation is fully rewritten.  The fast
         // form sweeps the binned order front to back with chunk-claiming
         // warps on one resident grid, as the allocating binned lookup does.
-        if (mcx::launch_lookup_sort(v.sort, n, E, mat, a.bins, a.perm, v.grid, st))
+        if (mcx::launch_lookup_sort(sp, n, E, mat, a.bins, a.perm, v.grid, st))
             rc = mcx::set_error(MCX_ERR_CUDA, "binning launch failed");
         else if ((flags & MCX_LOOKUP_FAST)
                      ? mcx::launch_xs_lookup_fast(v.tables, n, E, mat, a.perm, out, false,

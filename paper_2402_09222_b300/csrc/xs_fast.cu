@@ -888,37 +888,71 @@ __global__ void k_lookup_sort_count_global(SortParams sp, int64_t n, const doubl
         atomicAdd(&bins[lookup_key(sp, __ldg(E + l), __ldg(mat + l))], 1u);
 }
 
-__global__ void k_exclusive_scan(uint32_t* __restrict__ bins, int nb)
+// Exclusive scan of the bin counters in two launches over parts of `seg`
+// consecutive bins: each part sums its bins into part[], then each part adds
+// the sums of the parts before it and scans its own bins from there.
+
+// Sum of v over a block of 1024 threads (valid in thread 0).
+__device__ __forceinline__ uint32_t block_sum_1024(uint32_t v, uint32_t* red)
 {
+    v = __reduce_add_sync(FULL, v);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    uint32_t s = 0u;
+    if (threadIdx.x < 32) s = __reduce_add_sync(FULL, red[threadIdx.x]);
+    return s;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_part_sums(const uint32_t* __restrict__ bins, int nb, int seg,
+                                                         uint32_t* __restrict__ part)
+{
+    __shared__ uint32_t red[32];
+    const int i0 = blockIdx.x * seg;
+    const int i1 = min(nb, i0 + seg);
+    uint32_t v = 0u;
+    for (int i = i0 + threadIdx.x; i < i1; i += 1024) v += bins[i];
+    v = block_sum_1024(v, red);
+    if (threadIdx.x == 0) part[blockIdx.x] = v;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_parts(uint32_t* __restrict__ bins, int nb, int seg,
+                                                     const uint32_t* __restrict__ part)
+{
+    __shared__ uint32_t red[32];
     __shared__ uint32_t warp_sums[32];
     __shared__ uint32_t carry;
-    const int lane = threadIdx.x & 31;
-    if (threadIdx.x == 0) carry = 0u;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // offset of this part: the sum of the parts before it
+    uint32_t v = 0u;
+    for (int j = threadIdx.x; j < (int)blockIdx.x; j += 1024) v += part[j];
+    v = block_sum_1024(v, red);
+    if (threadIdx.x == 0) carry = v;
     __syncthreads();
-    for (int base = 0; base < nb; base += blockDim.x) {
+    const int i0 = blockIdx.x * seg;
+    const int i1 = min(nb, i0 + seg);
+    for (int base = i0; base < i1; base += 1024) {
         const int i = base + threadIdx.x;
-        const uint32_t v = i < nb ? bins[i] : 0u;
-        uint32_t x = v;
+        const uint32_t c = i < i1 ? bins[i] : 0u;
+        uint32_t x = c;
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t y = __shfl_up_sync(FULL, x, o);
             if (lane >= o) x += y;
         }
-        if (lane == 31) warp_sums[threadIdx.x >> 5] = x;
+        if (lane == 31) warp_sums[warp] = x;
         __syncthreads();
-        if (threadIdx.x < 32) {
-            const int nw = blockDim.x >> 5;
-            uint32_t s = threadIdx.x < nw ? warp_sums[threadIdx.x] : 0u;
+        if (warp == 0) {
+            uint32_t s = warp_sums[lane];
             for (int o = 1; o < 32; o <<= 1) {
                 const uint32_t y = __shfl_up_sync(FULL, s, o);
                 if (lane >= o) s += y;
             }
-            if (threadIdx.x < nw) warp_sums[threadIdx.x] = s;
+            warp_sums[lane] = s;
         }
         __syncthreads();
-        const uint32_t before = (threadIdx.x >> 5) ? warp_sums[(threadIdx.x >> 5) - 1] : 0u;
-        if (i < nb) bins[i] = carry + before + x - v;
+        const uint32_t before = warp ? warp_sums[warp - 1] : 0u;
+        if (i < i1) bins[i] = carry + before + x - c;
         __syncthreads();
-        if (threadIdx.x == blockDim.x - 1) carry += before + x;
+        if (threadIdx.x == 1023) carry += before + x;
         __syncthreads();
     }
 }
@@ -1040,7 +1074,13 @@ int launch_lookup_sort(const SortParams& sp, int64_t n, const double* E, const i
         k_lookup_sort_count<<<grid, 512, sizeof(uint32_t) * nb, st>>>(sp, n, E, mat, bins);
     else
         k_lookup_sort_count_global<<<grid, 256, 0, st>>>(sp, n, E, mat, bins);
-    k_exclusive_scan<<<1, 1024, 0, st>>>(bins, nb);
+    // parts of whole 1024-bin steps, at most kSortScanParts of them
+    int seg = (nb + kSortScanParts - 1) / kSortScanParts;
+    seg = (seg + 1023) / 1024 * 1024;
+    const int parts = (nb + seg - 1) / seg;
+    uint32_t* part = bins + nb + 1;
+    k_scan_part_sums<<<parts, 1024, 0, st>>>(bins, nb, seg, part);
+    k_scan_parts<<<parts, 1024, 0, st>>>(bins, nb, seg, part);
     k_lookup_sort_scatter<<<grid, 256, 0, st>>>(sp, n, E, mat, bins, perm);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }

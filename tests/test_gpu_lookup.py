@@ -97,6 +97,39 @@ def test_binning_changes_nothing(torch_cuda, small_case, flags):
     assert np.array_equal(a.view(np.uint64), b.view(np.uint64))
 
 
+def _assert_binned(E, mat, pm, lib, n_materials):
+    """pm is a permutation of 0..n-1 grouped by material and, within a
+    material, ordered by log E up to one bucket: n / (materials x 128) equal
+    log-energy buckets per material over the library's energy range (energies
+    outside it fall into the end buckets)."""
+    n = len(E)
+    assert np.array_equal(np.sort(pm), np.arange(n))
+    m = mat[pm].astype(np.int64)
+    assert np.all(np.diff(m) >= 0)
+    lo, hi = np.log(lib.energies.min()), np.log(lib.energies.max())
+    nb = max(1, min(n // (n_materials * 128), (1 << 21) // n_materials))
+    width = (hi - lo) / nb
+    x = np.clip(np.log(E[pm]), lo, hi)
+    starts = np.flatnonzero(np.r_[True, np.diff(m) != 0])
+    for a, b in zip(starts, np.r_[starts[1:], n]):
+        drop = np.maximum.accumulate(x[a:b]) - x[a:b]
+        assert drop.max() <= width * (1 + 1e-4) + 1e-5, (drop.max(), width)
+
+
+@pytest.mark.parametrize("n", [1, 777, 3_000_017, 20_000_000])
+def test_binning_orders_by_material_then_log_energy(torch_cuda, n):
+    """mcx_xs_sort over 12 materials: at 2e7 lookups 13,020 buckets per
+    material, 156,240 bins, whose counters are scanned in 153 parts."""
+    torch = torch_cuda
+    lib = synth.species_library(20, 200, 141)
+    mats = synth.lookup_materials(20, 142, n_materials=12)
+    E, mat = synth.lookup_inputs(n, mats.n_materials, 143)
+    p = _handle(lib, mats, 1, 1000)
+    perm = p.xs_sort(_dev(torch, E, torch.float64), _dev(torch, mat, torch.int32))
+    _assert_binned(E, mat, perm.cpu().numpy(), lib, mats.n_materials)
+    p.close()
+
+
 def test_degenerate_inputs(torch_cuda, small_case):
     from paper_2402_09222_b300 import mcx
     torch = torch_cuda
@@ -236,9 +269,7 @@ def test_config2_full_size_sampled(torch_cuda):
     assert np.all((ref == 0) <= (got == 0)), "an exactly-zero channel came out non-zero"
     assert rel.max() <= FAST_RTOL, rel.max()
     # the permutation is a permutation, and sorted by (material, energy bucket)
-    pm = perm.cpu().numpy()
-    assert pm.min() == 0 and pm.max() == n - 1 and np.bincount(pm, minlength=n).max() == 1
-    assert np.all(np.diff(mat[pm].astype(np.int64)) >= 0)
+    _assert_binned(E, mat, perm.cpu().numpy(), lib, mats.n_materials)
     del out, perm
     p32.close()
     p64 = _handle(lib, mats, mcx.FP64, 0)
