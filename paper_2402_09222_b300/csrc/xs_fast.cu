@@ -880,12 +880,37 @@ __global__ void k_lookup_sort_count(SortParams sp, int64_t n, const double* __re
 
 // The same count with the histogram in global memory, for bin counts that do
 // not fit in shared memory.
+// Bin key of lookup l for a warp-wide binning step (keys of lanes past n are
+// negative and distinct), and whether two neighbouring lanes share a key: only
+// then do the kernels below aggregate equal keys with a warp match, which
+// costs more than the atomics it saves on well-spread keys.
+__device__ __forceinline__ int warp_bin_key(const SortParams& sp, const double* E, const int32_t* mat,
+                                            int64_t l, int64_t n, int lane, bool& dup)
+{
+    const int key = l < n ? lookup_key(sp, __ldg(E + l), __ldg(mat + l)) : -1 - lane;
+    const int prev = __shfl_up_sync(FULL, key, 1);
+    dup = __any_sync(FULL, lane > 0 && prev == key);
+    return key;
+}
+
 __global__ void k_lookup_sort_count_global(SortParams sp, int64_t n, const double* __restrict__ E,
                                            const int32_t* __restrict__ mat, uint32_t* __restrict__ bins)
 {
-    for (int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; l < n;
-         l += (int64_t)gridDim.x * blockDim.x)
-        atomicAdd(&bins[lookup_key(sp, __ldg(E + l), __ldg(mat + l))], 1u);
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
+        const int64_t l = base + threadIdx.x;
+        const unsigned vm = __ballot_sync(FULL, l < n);
+        bool dup;
+        const int key = warp_bin_key(sp, E, mat, l, n, lane, dup);
+        if (l >= n) continue;
+        if (!dup) {
+            atomicAdd(&bins[key], 1u);
+        } else {
+            const unsigned grp = __match_any_sync(vm, key);
+            if (lane == __ffs(grp) - 1) atomicAdd(&bins[key], (uint32_t)__popc(grp));
+        }
+    }
 }
 
 // Exclusive scan of the bin counters in two launches over parts of `seg`
@@ -967,8 +992,13 @@ __global__ void k_lookup_sort_scatter(SortParams sp, int64_t n, const double* __
         const int64_t l = base + threadIdx.x;
         const bool valid = l < n;
         const unsigned vm = __ballot_sync(FULL, valid);
+        bool dup;
+        const int key = warp_bin_key(sp, E, mat, l, n, lane, dup);
         if (!valid) continue;
-        const int key = lookup_key(sp, __ldg(E + l), __ldg(mat + l));
+        if (!dup) {
+            perm[atomicAdd(&bins[key], 1u)] = (int32_t)l;
+            continue;
+        }
         const unsigned grp = __match_any_sync(vm, key);
         const int leader = __ffs(grp) - 1;
         uint32_t pos = 0u;

@@ -130,6 +130,31 @@ def test_binning_orders_by_material_then_log_energy(torch_cuda, n):
     p.close()
 
 
+@pytest.mark.parametrize("layout", ["one_bin", "sorted", "pairs"])
+def test_binning_of_concentrated_and_presorted_batches(torch_cuda, layout):
+    """Batches whose neighbouring lookups share bins (the binning kernels'
+    warp-aggregated path): every lookup in one bin, a batch already sorted by
+    energy, and equal neighbours in pairs; 3e6 lookups over 12 materials."""
+    torch = torch_cuda
+    lib = synth.species_library(20, 200, 151)
+    mats = synth.lookup_materials(20, 152, n_materials=12)
+    n = 3_000_017
+    E, mat = synth.lookup_inputs(n, mats.n_materials, 153)
+    if layout == "one_bin":
+        E[:] = 1.0
+        mat[:] = 5
+    elif layout == "sorted":
+        o = np.lexsort((E, mat))
+        E, mat = E[o], mat[o]
+    else:
+        E[1::2] = E[:-1:2]
+        mat[1::2] = mat[:-1:2]
+    p = _handle(lib, mats, 1, 1000)
+    pm = p.xs_sort(_dev(torch, E, torch.float64), _dev(torch, mat, torch.int32)).cpu().numpy()
+    _assert_binned(E, mat, pm, lib, mats.n_materials)
+    p.close()
+
+
 def test_degenerate_inputs(torch_cuda, small_case):
     from paper_2402_09222_b300 import mcx
     torch = torch_cuda
