@@ -334,9 +334,9 @@ int mcx_xs_lookup(mcx_problem* p, int64_t n, const double* E, const int32_t* mat
 /* Binning of lookups by material and energy (Sec. 5.1: sorting so that
  * neighbouring threads work on the same material and nearby energies):
  * perm (int32 [n], DEVICE) receives 0..n-1 ordered by (material, bucket of
- * log E) with n / (materials x 128) equal buckets per material over the
+ * log E) with n / (materials x 192) equal buckets per material over the
  * library's energy range (at least 1; fewer when materials x buckets would
- * exceed 2^21 bins), so about 128 lookups per bucket.  Order within a bucket
+ * exceed 2^21 bins), so about 192 lookups per bucket.  Order within a bucket
  * is unspecified.  E and mat are
  * DEVICE pointers.  Uses a small library-owned bin array (allocated on first
  * use).  Errors: MCX_ERR_ARG, MCX_ERR_STATE, MCX_ERR_CUDA, MCX_ERR_OOM. */
@@ -402,8 +402,9 @@ int mcx_xs_indices(mcx_problem* p, int64_t n, const double* E, const int32_t* ma
  * for every lookup l whose material holds entry j (species s, density N_j).
  * grad_dens [nnz] and grad_sigma [P][n_ch] are FP64 DEVICE buffers that are
  * accumulated into (zero them first).  E, mat, grad_out are DEVICE pointers.
- * The lookups are binned first (material, log-energy bucket) into the
- * handle's scratch, allocated on first use as for MCX_LOOKUP_SORT; warps of
+ * The lookups are binned first (material, log-energy bucket; finer than
+ * mcx_xs_sort's, about 8 lookups per bucket) into the handle's scratch,
+ * allocated on first use as for MCX_LOOKUP_SORT; warps of
  * one material then sum their contributions per species and grid interval
  * (exact FP64 fractions, sums over energy-sorted lanes) before one atomic
  * per point and channel, and the density gradients per block before one

@@ -28,16 +28,27 @@ struct SortParams {
 // aims at on average.  A warp's 64-lookup round then spans about one bucket,
 // so the fewer grid points a bucket holds, the fewer species' bracketing
 // intervals a round straddles; finer buckets leave rounds spanning several.
-constexpr int64_t kLookupsPerBucket = 128;
+#ifndef MCX_LOOKUPS_PER_BUCKET
+#define MCX_LOOKUPS_PER_BUCKET 192
+#endif
+constexpr int64_t kLookupsPerBucket = MCX_LOOKUPS_PER_BUCKET;
+
+// The same for the binned backward, whose warps take 32 lookups at a time
+// and gain from the narrowest energy span per warp (measured best at 8).
+#ifndef MCX_BACKWARD_LOOKUPS_PER_BUCKET
+#define MCX_BACKWARD_LOOKUPS_PER_BUCKET 8
+#endif
+constexpr int64_t kBackwardLookupsPerBucket = MCX_BACKWARD_LOOKUPS_PER_BUCKET;
 
 // Binning parameters of a batch of n lookups over n_materials materials with
-// energies in [emin, emax]: n / (n_materials * kLookupsPerBucket) buckets per
+// energies in [emin, emax]: n / (n_materials * per_bucket) buckets per
 // material (at least 1), at most max_bins bins in all.
-inline SortParams lookup_sort_params(int n_materials, double emin, double emax, int64_t n, int64_t max_bins)
+inline SortParams lookup_sort_params(int n_materials, double emin, double emax, int64_t n, int64_t max_bins,
+                                     int64_t per_bucket = kLookupsPerBucket)
 {
     SortParams sp;
     sp.n_materials = n_materials;
-    int64_t nb = n / ((int64_t)n_materials * kLookupsPerBucket);
+    int64_t nb = n / ((int64_t)n_materials * per_bucket);
     if (nb > max_bins / n_materials) nb = max_bins / n_materials;
     sp.n_ebuckets = nb < 1 ? 1 : (int32_t)nb;
     sp.ln_lo = (float)std::log(emin);

@@ -775,16 +775,18 @@ int ensure_lookup_scratch(mcx_problem* p, int64_t n, size_t)
 
 // Binning of a batch of n lookups (about kLookupsPerBucket lookups per
 // material and log-energy bucket), at most max_bins bins.
-SortParams batch_sort_params(const TableStore* ts, int64_t n, int64_t max_bins = (int64_t)1 << 21)
+SortParams batch_sort_params(const TableStore* ts, int64_t n, int64_t max_bins = (int64_t)1 << 21,
+                             int64_t per_bucket = kLookupsPerBucket)
 {
-    return lookup_sort_params(ts->view.n_materials, ts->emin, ts->emax, n, max_bins);
+    return lookup_sort_params(ts->view.n_materials, ts->emin, ts->emax, n, max_bins, per_bucket);
 }
 
-// Bin lookups into perm (device, [n]); bins scratch owned by the problem.
+// Bin lookups into perm (device, [n]), about per_bucket lookups per bin;
+// bins scratch owned by the problem.
 int sort_device(mcx_problem* p, int64_t n, const double* E, const int32_t* mat, int32_t* perm,
-                cudaStream_t st)
+                cudaStream_t st, int64_t per_bucket = kLookupsPerBucket)
 {
-    const SortParams sp = batch_sort_params(p->tables, n);
+    const SortParams sp = batch_sort_params(p->tables, n, (int64_t)1 << 21, per_bucket);
     const size_t nb = (size_t)sp.n_materials * sp.n_ebuckets + 1 + kSortScanParts;
     if (p->lbins_cap < nb) {
         dev_free(p->lbins);
@@ -1603,7 +1605,7 @@ int mcx_xs_lookup_backward(mcx_problem* p, int64_t n, const double* E, const int
     cudaStream_t st = (cudaStream_t)stream;
     // binned order, then warps that aggregate per species and grid interval
     TRY(ensure_lookup_scratch(p, n, 0));
-    TRY(sort_device(p, n, E, mat, p->perm, st));
+    TRY(sort_device(p, n, E, mat, p->perm, st, kBackwardLookupsPerBucket));
     TRY(ensure_work_ctr(p));
     if (launch_xs_backward_binned(p->tables->view, p->tables->nnz, n, E, mat, p->perm, grad_out, grad_dens,
                                   grad_sigma, p->sm_count, p->work_ctr, st))

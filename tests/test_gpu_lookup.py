@@ -99,7 +99,7 @@ def test_binning_changes_nothing(torch_cuda, small_case, flags):
 
 def _assert_binned(E, mat, pm, lib, n_materials):
     """pm is a permutation of 0..n-1 grouped by material and, within a
-    material, ordered by log E up to one bucket: n / (materials x 128) equal
+    material, ordered by log E up to one bucket: n / (materials x 192) equal
     log-energy buckets per material over the library's energy range (energies
     outside it fall into the end buckets)."""
     n = len(E)
@@ -107,7 +107,7 @@ def _assert_binned(E, mat, pm, lib, n_materials):
     m = mat[pm].astype(np.int64)
     assert np.all(np.diff(m) >= 0)
     lo, hi = np.log(lib.energies.min()), np.log(lib.energies.max())
-    nb = max(1, min(n // (n_materials * 128), (1 << 21) // n_materials))
+    nb = max(1, min(n // (n_materials * 192), (1 << 21) // n_materials))
     width = (hi - lo) / nb
     x = np.clip(np.log(E[pm]), lo, hi)
     starts = np.flatnonzero(np.r_[True, np.diff(m) != 0])
@@ -116,17 +116,23 @@ def _assert_binned(E, mat, pm, lib, n_materials):
         assert drop.max() <= width * (1 + 1e-4) + 1e-5, (drop.max(), width)
 
 
-@pytest.mark.parametrize("n", [1, 777, 3_000_017, 20_000_000])
+@pytest.mark.parametrize("n", [1, 777, 1_000_003, 3_000_017, 20_000_000])
 def test_binning_orders_by_material_then_log_energy(torch_cuda, n):
-    """mcx_xs_sort over 12 materials: at 2e7 lookups 13,020 buckets per
-    material, 156,240 bins, whose counters are scanned in 153 parts."""
+    """mcx_xs_sort over 12 materials: 1e6 lookups, 5,208 bins counted in
+    shared memory; 3e6, 15,624 bins counted in global memory; 2e7, 8,680
+    buckets per material, 104,160 bins, whose counters are scanned in 102
+    parts.  A NaN energy takes the first bucket, energies outside the grid
+    the end buckets."""
     torch = torch_cuda
     lib = synth.species_library(20, 200, 141)
     mats = synth.lookup_materials(20, 142, n_materials=12)
     E, mat = synth.lookup_inputs(n, mats.n_materials, 143)
+    if n >= 3:
+        E[:3] = [np.nan, 1e-9, 1e9]
     p = _handle(lib, mats, 1, 1000)
     perm = p.xs_sort(_dev(torch, E, torch.float64), _dev(torch, mat, torch.int32))
-    _assert_binned(E, mat, perm.cpu().numpy(), lib, mats.n_materials)
+    Ec = np.where(np.isnan(E), lib.energies.min(), E)
+    _assert_binned(Ec, mat, perm.cpu().numpy(), lib, mats.n_materials)
     p.close()
 
 
