@@ -271,8 +271,20 @@ int mcx_run_eigenvalue(mcx_problem* p, int64_t n_per_gen, int32_t n_generations,
 /* Waits for `stream` and reports whether a staged lookup (MCX_LOOKUP_STAGED)
  * on this handle gave up on its shared-memory pipeline since the last check
  * (a bounded wait ran out; never expected): MCX_ERR_TIMEOUT, and the flag is
- * cleared; MCX_OK otherwise.  Host-synchronous. */
+ * cleared; MCX_OK otherwise.  In the bounds-checked build (libmcx_bounds.so,
+ * mcx_bounds_checked() == 1) it first reports the first index check that
+ * failed on the handle's device since the last check, in any kernel:
+ * MCX_ERR_BOUNDS with the site and index in mcx_last_error (the check
+ * skipped or clamped the access; the outputs of the lookups involved are
+ * left unwritten), and the record is cleared.  Host-synchronous. */
 int mcx_check_device(mcx_problem* p, void* stream);
+
+/* 1 in the bounds-checked build of the library (compiled with
+ * MCX_BOUNDS_CHECK=1: the kernels check processing-order indices, hash-grid
+ * windows, event-queue slots and appends, tally bins and collision
+ * materials before using them, and report failures as MCX_ERR_BOUNDS from
+ * mcx_check_device and the transport runs), 0 in the release build. */
+int mcx_bounds_checked(void);
 
 /* The last eigenvalue generation's ordered bank: its size, and its first n
  * sites as HOST rows {x, y, z, ci, cj, inpin} (n <= size).  Synchronous. */

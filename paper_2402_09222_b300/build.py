@@ -3,7 +3,9 @@
 Translation units that evaluate the plain definition's FP64 arithmetic
 (transport, exact lookup, adjoint) are compiled with --fmad=false so that no
 multiply-add is fused; the fast lookup and the host layer use the defaults.
-Usage:  python -m paper_2402_09222_b300.build [--force] [--verbose-ptxas]
+--bounds builds the bounds-checked debug library libmcx_bounds.so instead
+(MCX_BOUNDS_CHECK=1; loaded by the binding when MCX_LIB=bounds).
+Usage:  python -m paper_2402_09222_b300.build [--force] [--verbose-ptxas] [--bounds]
 """
 from __future__ import annotations
 
@@ -17,6 +19,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libmcx.so")
+LIB_BOUNDS = os.path.join(HERE, "libmcx_bounds.so")
 BUILD = os.path.join(ROOT, "_build")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -41,26 +44,30 @@ def _stale(out: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, ptxas_verbose: bool = False) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, ptxas_verbose: bool = False, bounds: bool = False) -> str:
+    out_dir = os.path.join(BUILD, "bounds") if bounds else BUILD
+    lib = LIB_BOUNDS if bounds else LIB
+    os.makedirs(out_dir, exist_ok=True)
     headers = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(INCLUDE, "mcx.h")]
     objs = []
     for src in SOURCES:
         path = os.path.join(CSRC, src)
-        obj = os.path.join(BUILD, src.replace(".cu", ".o"))
+        obj = os.path.join(out_dir, src.replace(".cu", ".o"))
         objs.append(obj)
         if force or _stale(obj, [path] + headers):
             cmd = [nvcc()] + ARCH + COMMON + ["-c", path, "-o", obj]
+            if bounds:
+                cmd.append("-DMCX_BOUNDS_CHECK=1")
             if src in EXACT_TUS:
                 cmd.append("--fmad=false")
             if ptxas_verbose:
                 cmd += ["-Xptxas", "-v"]
             subprocess.check_call(cmd)
-    if force or _stale(LIB, objs):
-        subprocess.check_call([nvcc()] + ARCH + ["-shared", "-o", LIB] + objs)
-    return LIB
+    if force or _stale(lib, objs):
+        subprocess.check_call([nvcc()] + ARCH + ["-shared", "-o", lib] + objs)
+    return lib
 
 
 if __name__ == "__main__":
-    build(force="--force" in sys.argv, ptxas_verbose="--verbose-ptxas" in sys.argv)
-    print(LIB)
+    print(build(force="--force" in sys.argv, ptxas_verbose="--verbose-ptxas" in sys.argv,
+                bounds="--bounds" in sys.argv))

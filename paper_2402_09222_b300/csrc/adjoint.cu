@@ -143,14 +143,18 @@ __global__ void __launch_bounds__(kBwThreads) k_xs_backward_binned(Tables t, int
 #pragma unroll 1
         for (int rr = 0; rr < kBwChunk / 32; ++rr) {
             const int64_t j = (int64_t)cb + rr * 32 + lane;
-            const bool in = j < n;
+            bool in = j < n;
             int64_t l = 0;
             double E = 0.0;
             int32_t m = -1;
             if (in) {
                 l = __ldg(perm + j);
-                E = __ldg(Ein + l);
-                m = __ldg(mat + l);
+                if (MCX_IN_BOUNDS(l >= 0 && l < n, BC_PERM, l)) {
+                    E = __ldg(Ein + l);
+                    m = __ldg(mat + l);
+                } else {
+                    in = false;
+                }
             }
             // valid: material in range and E finite (not NaN or infinite)
             const bool ok = in && m >= 0 && m < t.n_materials &&
@@ -362,5 +366,7 @@ int launch_xs_backward_binned(const Tables& t, int64_t nnz, int64_t n, const dou
                                                      dens_smem);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
+
+MCX_BOUNDS_READER(bounds_error_adjoint)
 
 }  // namespace mcx

@@ -103,6 +103,14 @@ constexpr int kSortScanParts = 1024;
 int launch_lookup_sort(const SortParams& sp, int64_t n, const double* E, const int32_t* mat,
                        uint32_t* bins, int32_t* perm, int grid, cudaStream_t st);
 
+// First failed bounds check of each kernel translation unit since the last
+// read (site << 56 | index; 0: none), cleared by the read; always 0 in
+// release builds.
+unsigned long long bounds_error_xs_exact();
+unsigned long long bounds_error_xs_fast();
+unsigned long long bounds_error_transport();
+unsigned long long bounds_error_adjoint();
+
 // Tables, FP32 densities and binning parameters of a loaded problem, for
 // entry points defined outside the C-ABI translation unit.
 struct LookupView {

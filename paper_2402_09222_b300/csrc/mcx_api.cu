@@ -33,6 +33,18 @@ int fail(int code, const char* fmt, ...)
     return code;
 }
 
+// MCX_ERR_BOUNDS with the site and index of a bounds-checked build's error
+// word (site << 56 | index).
+int bounds_failure(unsigned long long word, const char* unit)
+{
+    static const char* const site[] = {"?", "lookup index from the processing order",
+                                       "hash-grid search window", "particle slot from an event queue",
+                                       "event-queue append", "tally bin", "collision material"};
+    const int k = (int)(word >> 56);
+    const long long idx = (long long)(word & ((1ull << 56) - 1ull));
+    return fail(MCX_ERR_BOUNDS, "%s: %s out of bounds (index %lld)", unit, site[k >= 1 && k <= 6 ? k : 0], idx);
+}
+
 #define CUDA_TRY(expr)                                                                    \
     do {                                                                                  \
         cudaError_t e_ = (expr);                                                          \
@@ -731,10 +743,13 @@ int run_loop(mcx_problem* owner, int n_prob, mcx_problem* const* probs, const in
                 }
         }
         if (owner->h_ctl->error) {
-            status = owner->h_ctl->error == MCX_ERR_ITER_LIMIT
-                         ? fail(MCX_ERR_ITER_LIMIT, "event loop reached its cap of %lld iterations",
-                                (long long)max_iters)
-                         : fail(owner->h_ctl->error, "device error %d", owner->h_ctl->error);
+            if (owner->h_ctl->error == MCX_ERR_ITER_LIMIT)
+                status = fail(MCX_ERR_ITER_LIMIT, "event loop reached its cap of %lld iterations",
+                              (long long)max_iters);
+            else if (owner->h_ctl->error == MCX_ERR_BOUNDS)
+                status = bounds_failure(bounds_error_transport(), "transport");
+            else
+                status = fail(owner->h_ctl->error, "device error %d", owner->h_ctl->error);
             break;
         }
         if (owner->h_ctl->done) break;
@@ -1759,15 +1774,26 @@ int mcx_check_device(mcx_problem* p, void* stream)
 {
     g_err.clear();
     TRY(check_handle(p));
-    if (!p->work_ctr) return MCX_OK;
     DeviceGuard dg(p->device);
-    unsigned long long w = 0ull;
     CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    if (MCX_BOUNDS_CHECK) {
+        // every kernel translation unit's first failed check (each word is
+        // cleared by its read)
+        const unsigned long long e[4] = {bounds_error_xs_exact(), bounds_error_xs_fast(), bounds_error_adjoint(),
+                                         bounds_error_transport()};
+        const char* unit[4] = {"exact lookup", "fast lookup", "adjoint", "transport"};
+        for (int i = 0; i < 4; ++i)
+            if (e[i]) return bounds_failure(e[i], unit[i]);
+    }
+    if (!p->work_ctr) return MCX_OK;
+    unsigned long long w = 0ull;
     CUDA_TRY(cudaMemcpy(&w, p->work_ctr + kWorkCtrs, sizeof(w), cudaMemcpyDeviceToHost));
     if (w == 0ull) return MCX_OK;
     CUDA_TRY(cudaMemset(p->work_ctr + kWorkCtrs, 0, sizeof(w)));
     return fail(MCX_ERR_TIMEOUT, "a staged lookup kernel gave up waiting on its pipeline");
 }
+
+int mcx_bounds_checked(void) { return MCX_BOUNDS_CHECK; }
 
 int mcx_fission_bank_size(const mcx_problem* p, int64_t* n)
 {

@@ -16,6 +16,55 @@
 namespace mcx {
 
 // ---------------------------------------------------------------------------
+// Bounds-checked builds (MCX_BOUNDS_CHECK=1, the library libmcx_bounds.so).
+// Before the accesses that depend on caller data or on table contents -- a
+// lookup index read from a processing order, a hash-grid search window, a
+// particle slot read from an event queue, a queue append, a tally bin, a
+// collision's species -- the kernels check the index.  A failed check is
+// recorded in the translation unit's error word (site and index of the first
+// failure; no __trap, no device assert) and the access is skipped or
+// replaced by an in-range one, never made; the transport also stops its run
+// with MCX_ERR_BOUNDS.  mcx_check_device and the transport run report it.
+// Release builds compile every check away.
+// ---------------------------------------------------------------------------
+#ifndef MCX_BOUNDS_CHECK
+#define MCX_BOUNDS_CHECK 0
+#endif
+enum BoundsSite : int {
+    BC_PERM = 1,      // lookup index from a processing order outside [0, n)
+    BC_WINDOW = 2,    // hash-grid search window outside the species' intervals
+    BC_SLOT = 3,      // particle slot from an event queue outside [0, cap)
+    BC_QUEUE = 4,     // event-queue append beyond its capacity
+    BC_TALLY = 5,     // tally bin outside the tally arrays
+    BC_SPECIES = 6,   // collision species outside the material
+};
+#if MCX_BOUNDS_CHECK
+// first failed check of this translation unit: site << 56 | index (low 56 bits)
+static __device__ unsigned long long g_bounds_err;
+__device__ __forceinline__ bool bounds_check(bool ok, int site, long long idx)
+{
+    if (!ok)
+        atomicCAS(&g_bounds_err, 0ull,
+                  ((unsigned long long)site << 56) | ((unsigned long long)idx & ((1ull << 56) - 1ull)));
+    return ok;
+}
+#define MCX_IN_BOUNDS(cond, site, idx) ::mcx::bounds_check((cond), (site), (long long)(idx))
+// Host reader of the translation unit's error word (0: no failure); clears it.
+#define MCX_BOUNDS_READER(fn)                                                           \
+    unsigned long long fn()                                                             \
+    {                                                                                   \
+        unsigned long long v = 0ull, z = 0ull;                                          \
+        if (cudaMemcpyFromSymbol(&v, g_bounds_err, sizeof(v)) != cudaSuccess) return 0ull; \
+        if (v) cudaMemcpyToSymbol(g_bounds_err, &z, sizeof(z));                         \
+        return v;                                                                       \
+    }
+#else
+#define MCX_IN_BOUNDS(cond, site, idx) true
+#define MCX_BOUNDS_READER(fn) \
+    unsigned long long fn() { return 0ull; }
+#endif
+
+// ---------------------------------------------------------------------------
 // Cross-section tables as seen by the kernels.
 // Layout in HBM:
 //   goff  int64 [S+1]     species s owns points [goff[s], goff[s+1])
@@ -180,6 +229,10 @@ __device__ __forceinline__ int64_t species_index(const Tables& t, int32_t s, int
         const int32_t* h = t.hidx + (int64_t)s * (t.H + 1) + hbin;
         lo = __ldg(h);
         hi = __ldg(h + 1);
+        if (!MCX_IN_BOUNDS(lo >= 0 && lo <= hi && hi <= n - 2, BC_WINDOW, (int64_t)s * (t.H + 1) + hbin)) {
+            lo = 0;
+            hi = n - 2;
+        }
     }
     return bsearch_window(t.E + base, lo, hi, eb);
 }
@@ -209,6 +262,11 @@ __device__ __forceinline__ void search_window(const Tables& t, const int4& e, in
         const int32_t wlo = __ldg(h);
         base = e.x + wlo;
         len = __ldg(h + 1) - wlo + 1;
+        if (!MCX_IN_BOUNDS(wlo >= 0 && len >= 1 && wlo + len <= e.y - 1, BC_WINDOW,
+                           (int64_t)e.z * ((int64_t)t.H + 1) + hb)) {
+            base = e.x;
+            len = e.y - 1;
+        }
     } else {
         base = e.x;
         len = e.y - 1;

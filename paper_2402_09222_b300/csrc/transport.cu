@@ -96,6 +96,31 @@ __device__ __forceinline__ int warp_append(int* counter, bool want)
     return want ? base + __popc(b & lanes_below()) : -1;
 }
 
+// Bounds-checked builds: a particle slot read from an event queue, and an
+// append position, outside [0, cap) stop the run (MCX_ERR_BOUNDS) and are
+// replaced by slot 0 / not written.
+__device__ __forceinline__ int64_t checked_slot(int64_t slot, const Particles& P, RunCtl* ctl)
+{
+#if MCX_BOUNDS_CHECK
+    if (!MCX_IN_BOUNDS(slot >= 0 && slot < P.cap, BC_SLOT, slot)) {
+        atomicCAS(&ctl->error, 0, MCX_ERR_BOUNDS);
+        return 0;
+    }
+#endif
+    return slot;
+}
+
+__device__ __forceinline__ void queue_put(int32_t* q, int64_t pos, int64_t slot, const Particles& P, RunCtl* ctl)
+{
+#if MCX_BOUNDS_CHECK
+    if (!MCX_IN_BOUNDS(pos >= 0 && pos < P.cap, BC_QUEUE, pos)) {
+        atomicCAS(&ctl->error, 0, MCX_ERR_BOUNDS);
+        return;
+    }
+#endif
+    q[pos] = (int32_t)slot;
+}
+
 // Where an event kernel takes its particles from: every slot (list == null),
 // a compacted list, or a segment of a ring (positions wrap at `wrap`).
 struct Src {
@@ -772,7 +797,7 @@ __device__ void finish_deaths(bool dies, int outcome, int64_t slot, int32_t pidx
     if (lane_id() == 0) atomicSub(&ctl->n_alive, __popc(dm));
     if (mode == MCX_QUEUED) {
         const int pos = warp_append(&ctl->n_dead[par ^ 1], dies);
-        if (dies) P.q_dead[par ^ 1][pos] = (int32_t)slot;
+        if (dies) queue_put(P.q_dead[par ^ 1], pos, slot, P, ctl);
     } else if (mode == MCX_QUEUED_FULLEST) {
         ring_push(P, ctl, RQ_DEAD, dies, slot);
     }
@@ -851,7 +876,7 @@ __global__ void __launch_bounds__(1024) k_refill(LoopConfig c, Particles P, cons
         // nothing left to start: retire the dead slots
         for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
              i += (int64_t)gridDim.x * blockDim.x)
-            P.flags[src_at(src, i)] = PF_RETIRED;
+            P.flags[checked_slot(src_at(src, i), P, ctl)] = PF_RETIRED;
         return;
     }
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -862,7 +887,7 @@ __global__ void __launch_bounds__(1024) k_refill(LoopConfig c, Particles P, cons
         bool want = false;
         if (i < count) {
             if (queued || fq) {
-                slot = src_at(src, i);
+                slot = checked_slot(src_at(src, i), P, ctl);
                 want = true;
             } else {
                 slot = i;
@@ -889,9 +914,9 @@ __global__ void __launch_bounds__(1024) k_refill(LoopConfig c, Particles P, cons
         }
         if (queued) {
             int pos = warp_append(&ctl->n_xs[par], got);
-            if (got) P.q_xs[par][pos] = (int32_t)slot;
+            if (got) queue_put(P.q_xs[par], pos, slot, P, ctl);
             pos = warp_append(&ctl->n_adv[par], got);
-            if (got) P.q_adv[par][pos] = (int32_t)slot;
+            if (got) queue_put(P.q_adv[par], pos, slot, P, ctl);
         } else if (fq) {
             ring_push(P, ctl, RQ_XS, got, slot);
         }
@@ -955,7 +980,7 @@ __global__ void __launch_bounds__(1024) k_lookup(LoopConfig c, Tables t, Particl
         const int lane = lane_id();
         const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
         if (w < count) {   // the whole warp
-            const int64_t slot = src_at(src, w);
+            const int64_t slot = checked_slot(src_at(src, w), P, ctl);
             const uint8_t f = P.flags[slot];
             const bool act = (f & PF_NEED_XS) != 0;
             if (act) {
@@ -991,7 +1016,7 @@ __global__ void __launch_bounds__(1024) k_lookup(LoopConfig c, Tables t, Particl
             const int64_t b = (int64_t)__shfl_sync(FULL, b0, 0);
             if (b >= count) break;
             const int64_t i = b + lane;
-            if (i < count) lookup_slot<T, EIG>(t, P, src_at(src, i));
+            if (i < count) lookup_slot<T, EIG>(t, P, checked_slot(src_at(src, i), P, ctl));
         }
         return;
     }
@@ -1001,7 +1026,7 @@ __global__ void __launch_bounds__(1024) k_lookup(LoopConfig c, Tables t, Particl
         int64_t slot = -1;
         bool act = false;
         if (i < count) {
-            slot = src_at(src, i);
+            slot = checked_slot(src_at(src, i), P, ctl);
             act = lookup_slot<T, EIG>(t, P, slot);
         }
         if (fq) ring_push(P, ctl, adv, act, slot);
@@ -1036,7 +1061,7 @@ __global__ void __launch_bounds__(1024) k_advance(LoopConfig c, Particles P, con
         int64_t slot = -1;
         bool act = false;
         if (i < count) {
-            slot = src_at(src, i);
+            slot = checked_slot(src_at(src, i), P, ctl);
             act = src.list ? true : (P.flags[slot] & PF_ALIVE) != 0;
         }
         bool scored = false, dies = false, coll = false, survive = false, need_xs = false;
@@ -1119,6 +1144,12 @@ __global__ void __launch_bounds__(1024) k_advance(LoopConfig c, Particles P, con
                 tal_flux = pd.flux + tal_i;
                 tal_abs = pd.absorb + tal_i;
                 scored = true;
+#if MCX_BOUNDS_CHECK
+                if (!MCX_IN_BOUNDS(tal_i >= 0 && tal_i < (int64_t)pd.n_batches * pd.nb, BC_TALLY, tal_i)) {
+                    atomicCAS(&ctl->error, 0, MCX_ERR_BOUNDS);
+                    scored = false;
+                }
+#endif
                 xabs = d * sig_a;
                 if (EIG) k_tl = d * P.sig_nf[slot];
                 if (M > 0) {
@@ -1220,11 +1251,11 @@ __global__ void __launch_bounds__(1024) k_advance(LoopConfig c, Particles P, con
         finish_deaths<EIG>(dies, outcome, slot, pidx, probs, P, ctl, M, c.mode, par);
         if (queued) {
             int pos = warp_append(&ctl->n_coll, coll);
-            if (coll) P.q_coll[pos] = (int32_t)slot;
+            if (coll) queue_put(P.q_coll, pos, slot, P, ctl);
             pos = warp_append(&ctl->n_adv[par ^ 1], survive);
-            if (survive) P.q_adv[par ^ 1][pos] = (int32_t)slot;
+            if (survive) queue_put(P.q_adv[par ^ 1], pos, slot, P, ctl);
             pos = warp_append(&ctl->n_xs[par ^ 1], need_xs);
-            if (need_xs) P.q_xs[par ^ 1][pos] = (int32_t)slot;
+            if (need_xs) queue_put(P.q_xs[par ^ 1], pos, slot, P, ctl);
         } else if (fq) {
             ring_push(P, ctl, RQ_COLL, coll, slot);
             ring_push(P, ctl, RQ_XS, survive && need_xs, slot);
@@ -1261,7 +1292,7 @@ __global__ void __launch_bounds__(1024) k_collide(LoopConfig c, Tables t, Partic
         int64_t slot = -1;
         bool act = false;
         if (i < count) {
-            slot = src_at(src, i);
+            slot = checked_slot(src_at(src, i), P, ctl);
             act = src.list ? true : (P.flags[slot] & PF_COLLIDE) != 0;
         }
         bool dies = false, survive = false;
@@ -1304,7 +1335,13 @@ __global__ void __launch_bounds__(1024) k_collide(LoopConfig c, Tables t, Partic
                 P.nsite[slot] = seq0 + (uint32_t)n_new;
             }
             const double E = P.E[slot];
-            const int32_t m = P.mat[slot];
+            int32_t m = P.mat[slot];
+#if MCX_BOUNDS_CHECK
+            if (!MCX_IN_BOUNDS(m >= 0 && m < t.n_materials, BC_SPECIES, m)) {
+                atomicCAS(&ctl->error, 0, MCX_ERR_BOUNDS);
+                m = 0;
+            }
+#endif
             const double target = xi1 * P.sig_ta[slot].x;
             const int64_t eb = search_key(E);
             const int32_t hb = t.H > 0 ? hash_bin(t, E, eb) : 0;
@@ -1425,9 +1462,9 @@ __global__ void __launch_bounds__(1024) k_collide(LoopConfig c, Tables t, Partic
         finish_deaths<EIG>(dies, outcome, slot, pidx, probs, P, ctl, M, c.mode, par);
         if (queued) {
             int pos = warp_append(&ctl->n_xs[par ^ 1], survive);
-            if (survive) P.q_xs[par ^ 1][pos] = (int32_t)slot;
+            if (survive) queue_put(P.q_xs[par ^ 1], pos, slot, P, ctl);
             pos = warp_append(&ctl->n_adv[par ^ 1], survive);
-            if (survive) P.q_adv[par ^ 1][pos] = (int32_t)slot;
+            if (survive) queue_put(P.q_adv[par ^ 1], pos, slot, P, ctl);
         } else if (fq) {
             ring_push(P, ctl, RQ_XS, survive, slot);
         }
@@ -1467,7 +1504,7 @@ __global__ void k_census(Particles P, const int32_t* __restrict__ moff, RunCtl* 
     const int64_t n = ctl->n_xs[par];
     long long s = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t m = P.mat[P.q_xs[par][i]];
+        const int32_t m = P.mat[checked_slot(P.q_xs[par][i], P, ctl)];
         s += ((long long)(__ldg(moff + m + 1) - __ldg(moff + m)) + 3) & ~3LL;
     }
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
@@ -1565,7 +1602,7 @@ __global__ void k_sort_count(LoopConfig c, Particles P, RunCtl* ctl, int which)
     __syncthreads();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t s = (int32_t)src_at(src, i);
+        const int32_t s = (int32_t)checked_slot(src_at(src, i), P, ctl);
         atomicAdd(&hist[sort_key(c, P.E[s], P.mat[s])], 1u);
     }
     __syncthreads();
@@ -1638,7 +1675,7 @@ __global__ void k_sort_scatter(LoopConfig c, Particles P, RunCtl* ctl, int which
             sl[r] = 0;
             rank[r] = 0u;
             if (i < n) {
-                sl[r] = (int32_t)src_at(src, i);
+                sl[r] = (int32_t)checked_slot(src_at(src, i), P, ctl);
                 key[r] = sort_key(c, P.E[sl[r]], P.mat[sl[r]]);
                 rank[r] = atomicAdd(&sh[key[r]], 1u);
             }
@@ -1651,7 +1688,7 @@ __global__ void k_sort_scatter(LoopConfig c, Particles P, RunCtl* ctl, int which
         __syncthreads();
 #pragma unroll
         for (int r = 0; r < kSortPer; ++r)
-            if (key[r] >= 0) P.q_sorted[sh[key[r]] + rank[r]] = sl[r];
+            if (key[r] >= 0) queue_put(P.q_sorted, sh[key[r]] + rank[r], sl[r], P, ctl);
         __syncthreads();
     }
 }
@@ -1807,5 +1844,7 @@ int launch_debug_uniforms(uint2 key, uint64_t hist, uint32_t first, int64_t n, d
     k_debug_uniforms<<<grid > 0 ? grid : 1, 256, 0, st>>>(key, hist, first, n, out);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
+
+MCX_BOUNDS_READER(bounds_error_transport)
 
 }  // namespace mcx

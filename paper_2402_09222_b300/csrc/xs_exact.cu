@@ -20,6 +20,7 @@ __global__ void __launch_bounds__(256) k_xs_lookup_exact(Tables t, int64_t n,
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
          j += (int64_t)gridDim.x * blockDim.x) {
         const int64_t l = perm ? (int64_t)__ldg(perm + j) : j;
+        if (perm && !MCX_IN_BOUNDS(l >= 0 && l < n, BC_PERM, l)) continue;
         const double E = __ldg(Ein + l);
         const int32_t m = __ldg(mat + l);
         double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
@@ -255,5 +256,7 @@ int launch_build_hash(const Tables& t, int32_t* hidx, int grid, cudaStream_t st)
     k_build_hash<<<grid, 256, 0, st>>>(t, hidx);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
+
+MCX_BOUNDS_READER(bounds_error_xs_exact)
 
 }  // namespace mcx

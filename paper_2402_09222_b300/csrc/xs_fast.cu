@@ -212,15 +212,15 @@ __device__ __forceinline__ void species_term(const float (&r0)[4 * W], const flo
 }
 
 template <int W, int U, int NC, typename OutT>
-__device__ __forceinline__ void lookup_one(const Tables& t, int64_t j, const double* __restrict__ Ein,
+__device__ __forceinline__ void lookup_one(const Tables& t, int64_t n, int64_t j, const double* __restrict__ Ein,
                                            const int32_t* __restrict__ mat,
                                            const int32_t* __restrict__ perm, OutT* __restrict__ out)
 {
     constexpr int NCMAX = NC;   // channels (a record holds up to 4 W - 2)
     static_assert(NC <= 4 * W - 2, "record too narrow for the channel count");
     const int nc = NC;
-    const int64_t H1 = (int64_t)t.H + 1;
     const int64_t l = perm ? (int64_t)load_in(perm + j) : j;
+    if (perm && !MCX_IN_BOUNDS(l >= 0 && l < n, BC_PERM, l)) return;
     const double E = load_in(Ein + l);
     const int32_t m = load_in(mat + l);
     if (m < 0 || m >= t.n_materials || E != E) {
@@ -243,15 +243,7 @@ __device__ __forceinline__ void lookup_one(const Tables& t, int64_t j, const dou
             const int32_t ii = i + u < i1 ? i + u : i1 - 1;
             const int4 e = __ldg(t.ment + ii);
             N[u] = i + u < i1 ? __int_as_float(e.w) : 0.f;
-            if (t.H > 0) {
-                const int32_t* h = t.hidx + (int64_t)e.z * H1 + hb;
-                const int32_t wlo = __ldg(h);
-                base[u] = e.x + wlo;
-                len[u] = __ldg(h + 1) - wlo + 1;
-            } else {
-                base[u] = e.x;
-                len[u] = e.y - 1;
-            }
+            search_window(t, e, hb, base[u], len[u]);
         }
         for (int st = 0; st < t.search_steps; ++st) {
 #pragma unroll
@@ -302,7 +294,7 @@ __global__ void __launch_bounds__(256, MCX_FAST_MIN_BLOCKS) k_xs_lookup_fast(Tab
     if (work == nullptr) {
         for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
              j += (int64_t)gridDim.x * blockDim.x)
-            lookup_one<W, U, NC, OutT>(t, j, Ein, mat, perm, out);
+            lookup_one<W, U, NC, OutT>(t, n, j, Ein, mat, perm, out);
         return;
     }
     const int lane = threadIdx.x & 31;
@@ -314,7 +306,7 @@ __global__ void __launch_bounds__(256, MCX_FAST_MIN_BLOCKS) k_xs_lookup_fast(Tab
 #pragma unroll 1
         for (int r = 0; r < kChunk / 32; ++r) {
             const int64_t j = (int64_t)base + r * 32 + lane;
-            if (j < n) lookup_one<W, U, NC, OutT>(t, j, Ein, mat, perm, out);
+            if (j < n) lookup_one<W, U, NC, OutT>(t, n, j, Ein, mat, perm, out);
         }
     }
 }
@@ -370,26 +362,34 @@ __global__ void __launch_bounds__(256, MCX_FAST2_MIN_BLOCKS) k_xs_lookup_warp2(T
 #pragma unroll 1
         for (int r = 0; r < kChunk / 64; ++r) {
             const int64_t j0 = (int64_t)cbase + r * 64 + lane, j1 = j0 + 32;
-            const bool in0 = j0 < n, in1 = j1 < n;
+            bool in0 = j0 < n, in1 = j1 < n;
             int64_t l0 = 0, l1 = 0;
             double E0 = 0.0, E1 = 0.0;
             int32_t m0 = -1, m1 = -1;
             if (in0) {
                 l0 = (int64_t)load_in(perm + j0);
-                E0 = load_in(Ein + l0);
-                m0 = load_in(mat + l0);
+                if (MCX_IN_BOUNDS(l0 >= 0 && l0 < n, BC_PERM, l0)) {
+                    E0 = load_in(Ein + l0);
+                    m0 = load_in(mat + l0);
+                } else {
+                    in0 = false;
+                }
             }
             if (in1) {
                 l1 = (int64_t)load_in(perm + j1);
-                E1 = load_in(Ein + l1);
-                m1 = load_in(mat + l1);
+                if (MCX_IN_BOUNDS(l1 >= 0 && l1 < n, BC_PERM, l1)) {
+                    E1 = load_in(Ein + l1);
+                    m1 = load_in(mat + l1);
+                } else {
+                    in1 = false;
+                }
             }
             const int32_t mw = __shfl_sync(FULLM, m0, 0);
             const bool ok = in0 && in1 && m0 == mw && m1 == mw && mw >= 0 && mw < t.n_materials && E0 == E0 &&
                             E1 == E1;
             if (!__all_sync(FULLM, ok)) {
-                if (in0) lookup_one<W, U, NC, OutT>(t, j0, Ein, mat, perm, out);
-                if (in1) lookup_one<W, U, NC, OutT>(t, j1, Ein, mat, perm, out);
+                if (in0) lookup_one<W, U, NC, OutT>(t, n, j0, Ein, mat, perm, out);
+                if (in1) lookup_one<W, U, NC, OutT>(t, n, j1, Ein, mat, perm, out);
                 continue;
             }
             const int64_t eb0 = search_key(E0), eb1 = search_key(E1);
@@ -644,11 +644,11 @@ __device__ int producer_fill(const Tables& t, const SortParams& sp, int64_t n, c
     if (lane < 2) {
         const int64_t j = lane == 0 ? (int64_t)base : ((int64_t)base + kStChunk - 1 < n ? (int64_t)base + kStChunk - 1 : n - 1);
         const int32_t l = __ldg(perm + j);
-        key = lookup_key(sp, __ldg(Ein + l), __ldg(mat + l));
+        key = MCX_IN_BOUNDS(l >= 0 && l < n, BC_PERM, l) ? lookup_key(sp, __ldg(Ein + l), __ldg(mat + l)) : -1;
     }
     const int k0 = __shfl_sync(0xffffffffu, key, 0), k1 = __shfl_sync(0xffffffffu, key, 1);
     const int m = k0 / sp.n_ebuckets, b0 = k0 % sp.n_ebuckets, b1 = k1 % sp.n_ebuckets;
-    int mode = (k1 / sp.n_ebuckets != m || b1 < b0 || t.H == 0) ? ST_FALLBACK : ST_NORMAL;
+    int mode = (k0 < 0 || k1 / sp.n_ebuckets != m || b1 < b0 || t.H == 0) ? ST_FALLBACK : ST_NORMAL;
     // the buckets' energy range, widened by a relative 1e-4
     const double E_min = b0 == 0 ? 0.0 : exp((double)sp.ln_lo + (double)b0 / (double)sp.scale) * (1.0 - 1e-4);
     const double E_max = b1 == sp.n_ebuckets - 1 ? __longlong_as_double(0x7ff0000000000000LL)
@@ -673,6 +673,9 @@ __device__ int producer_fill(const Tables& t, const SortParams& sp, int64_t n, c
                 gp = e.x + k_lo;
                 L = k_hi - k_lo + 2;
                 dens = e.w;
+                if (!MCX_IN_BOUNDS(k_lo >= 0 && k_lo <= k_hi && k_hi <= e.y - 2, BC_WINDOW,
+                                   (int64_t)e.z * H1 + hb_min))
+                    L = kStMaxPoints + 1;   // no copy: the chunk takes the fallback below
             }
             int rsum;
             const int roff = warp_excl_scan(L, rsum);
@@ -847,13 +850,15 @@ __global__ void __launch_bounds__(kStThreads, MCX_STAGED_BLOCKS) k_xs_lookup_sta
         const int64_t j = info.base + c;
         if (j < n) {
             const int32_t l = load_in(perm + j);
-            const double E = load_in(Ein + l);
-            const int32_t m = load_in(mat + l);
-            // E >= E_min && E <= E_max is false for a NaN energy
-            if (info.mode == ST_NORMAL && m == info.material && E >= info.E_min && E <= info.E_max)
-                consume_one<W, U, NC, OutT>(t, stage, info.n_entries, l, E, out);
-            else
-                lookup_one<W, U, NC, OutT>(t, j, Ein, mat, perm, out);
+            if (MCX_IN_BOUNDS(l >= 0 && l < n, BC_PERM, l)) {
+                const double E = load_in(Ein + l);
+                const int32_t m = load_in(mat + l);
+                // E >= E_min && E <= E_max is false for a NaN energy
+                if (info.mode == ST_NORMAL && m == info.material && E >= info.E_min && E <= info.E_max)
+                    consume_one<W, U, NC, OutT>(t, stage, info.n_entries, l, E, out);
+                else
+                    lookup_one<W, U, NC, OutT>(t, n, j, Ein, mat, perm, out);
+            }
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);
@@ -1114,5 +1119,7 @@ int launch_lookup_sort(const SortParams& sp, int64_t n, const double* E, const i
     k_lookup_sort_scatter<<<grid, 256, 0, st>>>(sp, n, E, mat, bins, perm);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
+
+MCX_BOUNDS_READER(bounds_error_xs_fast)
 
 }  // namespace mcx

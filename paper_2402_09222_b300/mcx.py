@@ -4,6 +4,8 @@ Argument marshalling only: every step of the lookup and of the transport runs
 in the library's CUDA kernels.  PyTorch provides device memory (tensors whose
 data pointers are handed to the C ABI) and streams.  There is no fallback: if
 libmcx.so is missing or cannot be loaded, importing this module raises.
+With MCX_LIB=bounds in the environment at import, the bounds-checked debug
+build libmcx_bounds.so is loaded instead (same ABI; see bounds_checked()).
 """
 from __future__ import annotations
 
@@ -15,7 +17,10 @@ import numpy as np
 from . import synth
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libmcx.so")
+LIB_VARIANT = os.environ.get("MCX_LIB", "release")
+if LIB_VARIANT not in ("release", "bounds"):
+    raise ImportError(f"MCX_LIB={LIB_VARIANT!r}: expected 'release' or 'bounds'")
+LIB_PATH = os.path.join(_HERE, "libmcx_bounds.so" if LIB_VARIANT == "bounds" else "libmcx.so")
 
 MCX_OK = 0
 ERR_NAMES = {-1: "MCX_ERR_ARG", -2: "MCX_ERR_CUDA", -3: "MCX_ERR_OOM", -4: "MCX_ERR_ITER_LIMIT",
@@ -37,7 +42,8 @@ class McxError(RuntimeError):
 
 
 if not os.path.exists(LIB_PATH):
-    raise ImportError(f"libmcx.so not built ({LIB_PATH}); run python -m paper_2402_09222_b300.build")
+    raise ImportError(f"{os.path.basename(LIB_PATH)} not built ({LIB_PATH}); run "
+                      f"python -m paper_2402_09222_b300.build{' --bounds' if LIB_VARIANT == 'bounds' else ''}")
 _lib = C.CDLL(LIB_PATH)
 
 _vp = C.c_void_p
@@ -95,6 +101,7 @@ _sig("mcx_run_eigenvalue", C.c_int, _vp, _i64, _i32, _i32, C.c_double, C.c_doubl
      _vp, _vp)
 _sig("mcx_fission_bank_size", C.c_int, _vp, C.POINTER(_i64))
 _sig("mcx_check_device", C.c_int, _vp, _vp)
+_sig("mcx_bounds_checked", C.c_int)
 _sig("mcx_read_fission_bank", C.c_int, _vp, _vp, _i64)
 _sig("mcx_xs_lookup", C.c_int, _vp, _i64, _vp, _vp, _vp, _i32, _vp)
 _sig("mcx_xs_sort", C.c_int, _vp, _i64, _vp, _vp, _vp, _vp)
@@ -114,6 +121,11 @@ def _check(rc: int):
 
 def version() -> str:
     return _lib.mcx_version().decode()
+
+
+def bounds_checked() -> bool:
+    """True in the bounds-checked debug build (MCX_LIB=bounds)."""
+    return bool(_lib.mcx_bounds_checked())
 
 
 def _np_ptr(a):

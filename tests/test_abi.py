@@ -17,13 +17,31 @@ def _declared(header):
     return sorted(set(re.findall(r"\b(mcx_[a-z0-9_]+)\s*\(", text)))
 
 
-def test_library_exports_every_declared_symbol():
+@pytest.mark.parametrize("variant", ["libmcx.so", "libmcx_bounds.so"])
+def test_library_exports_every_declared_symbol(variant):
+    """The release library and its bounds-checked debug build export the
+    same declared ABI; only the debug build says it checks bounds."""
     from paper_2402_09222_b300 import mcx
-    lib = C.CDLL(mcx.LIB_PATH)
+    lib = C.CDLL(os.path.join(os.path.dirname(mcx.LIB_PATH), variant))
     names = _declared("mcx.h")
     assert len(names) >= 20
     missing = [n for n in names if not hasattr(lib, n)]
     assert not missing, missing
+    lib.mcx_bounds_checked.restype = C.c_int
+    assert lib.mcx_bounds_checked() == (1 if variant == "libmcx_bounds.so" else 0)
+
+
+def test_binding_loads_the_bounds_checked_build_on_request():
+    import subprocess
+    import sys
+    code = "from paper_2402_09222_b300 import mcx; print(mcx.bounds_checked(), mcx.LIB_PATH)"
+    for var, want in (("bounds", "True"), ("release", "False")):
+        out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True,
+                             env={**os.environ, "MCX_LIB": var}, check=True).stdout.split()
+        assert out[0] == want and out[1].endswith("libmcx_bounds.so" if var == "bounds" else "libmcx.so")
+    bad = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True,
+                         env={**os.environ, "MCX_LIB": "nope"})
+    assert bad.returncode != 0 and "MCX_LIB" in bad.stderr
 
 
 def test_version_and_default_tuning():

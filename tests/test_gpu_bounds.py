@@ -1,0 +1,155 @@
+"""The bounds-checked debug build (libmcx_bounds.so, MCX_BOUNDS_CHECK=1).
+
+The build is chosen when the binding is imported, so each case runs in a
+child process with MCX_LIB=bounds and returns its results through a file;
+this process computes the same with the release library.
+
+* On valid inputs no check fires (mcx_check_device and the transport runs
+  return MCX_OK) and every result equals the release build's: the lookups in
+  each form bit for bit, the backward and the transport tallies to rounding
+  (their atomics add in no fixed order), the per-history collision counts
+  exactly.
+* A processing order holding indices outside [0, n) -- input that only the
+  debug build's own checks make safe, which is why this case runs only
+  there -- is reported by mcx_check_device as MCX_ERR_BOUNDS naming the
+  site, in the exact, the warp-cooperative and the staged lookup; the valid
+  lookups are computed as usual and the two displaced ones are left
+  unwritten."""
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+from paper_2402_09222_b300 import synth
+
+pytestmark = pytest.mark.gpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+LOOKUP_FLAGS = {"exact": 0, "fast": 1, "fast_binned": 3, "staged": 7, "fast_binned_out32": 11}
+MODES = {"queueless": 0, "queued": 1, "queued_fullest": 2}
+
+CASE = r'''
+import sys
+import numpy as np
+import torch
+from paper_2402_09222_b300 import mcx, synth
+
+def lookup_case():
+    lib = synth.species_library(40, 800, 161)
+    mats = synth.lookup_materials(40, 162, n_materials=6)
+    E, mat = synth.lookup_inputs(200_003, mats.n_materials, 163)
+    p = mcx.Problem(None).load_tables(lib, mats, precision=mcx.FP32, hash_bins=3000)
+    return lib, mats, E, mat, p
+
+def transport_case(mode):
+    prob = synth.config3_problem(6000, lattice_n=5, n_points=1500)
+    p = mcx.make_problem(prob, precision=mcx.FP32, hash_bins=2000,
+                         flags=mcx.FLAG_HISTORY_DEBUG | mcx.FLAG_DERIVATIVES)
+    p.set_tuning(mode=mode, sort_period=2, sort_threshold=0)
+    return prob, p
+
+def run_all(flags_by_name, modes):
+    res = {}
+    lib, mats, E, mat, p = lookup_case()
+    dE, dm = torch.as_tensor(E, device="cuda"), torch.as_tensor(mat, device="cuda")
+    for name, fl in flags_by_name.items():
+        res["lk_" + name] = p.xs_lookup(dE, dm, flags=fl).double().cpu().numpy()
+        p.check_device()
+    g = torch.as_tensor(np.random.default_rng(164).normal(size=(len(E), lib.n_ch)), device="cuda")
+    gd, gs = p.xs_lookup_backward(dE, dm, g)
+    p.check_device()
+    res["bw_dens"], res["bw_sigma"] = gd.cpu().numpy(), gs.cpu().numpy()
+    p.close()
+    for name, mode in modes.items():
+        prob, q = transport_case(mode)
+        q.run(particles_in_flight=1500, seed=5)
+        q.check_device()
+        t = q.tallies()
+        for k in ("flux", "absorb", "outcome", "dabsorb"):
+            res[f"tr_{name}_{k}"] = t[k]
+        res[f"tr_{name}_ncoll"] = q.history_debug(prob.n_histories)
+        q.close()
+    return res
+
+def bad_order_case(flags_by_name):
+    lib, mats, E, mat, p = lookup_case()
+    n = len(E)
+    dE, dm = torch.as_tensor(E, device="cuda"), torch.as_tensor(mat, device="cuda")
+    perm = p.xs_sort(dE, dm)
+    shown = perm.cpu().numpy()
+    lost = shown[[1000, 150_000]].copy()
+    perm[1000] = n          # one past the end
+    perm[150_000] = -7
+    res = {"lost": lost}
+    for name, fl in flags_by_name.items():
+        out = torch.full((n, lib.n_ch), float("nan"), dtype=torch.float64, device="cuda")
+        p.xs_lookup_ordered(dE, dm, perm, out=out, flags=fl & ~mcx.LOOKUP_SORT)
+        try:
+            p.check_device()
+            res["msg_" + name] = np.array("no error")
+        except mcx.McxError as e:
+            res["msg_" + name] = np.array(f"{e.code} {e}")
+        res["out_" + name] = out.cpu().numpy()
+        p.check_device()   # the record was cleared by the read
+    return res
+
+if __name__ == "__main__":
+    import json
+    which, path, spec = sys.argv[1], sys.argv[2], json.loads(sys.argv[3])
+    if which == "bounds":
+        assert mcx.bounds_checked()
+    res = run_all(spec["lookup"], spec["modes"]) if sys.argv[4] == "valid" else bad_order_case(spec["lookup"])
+    np.savez(path, **res)
+'''
+
+
+def _child(tmp_path, variant, kind, flags):
+    import json
+    script = tmp_path / "case.py"
+    script.write_text(CASE)
+    out = tmp_path / f"{variant}_{kind}.npz"
+    spec = json.dumps({"lookup": flags, "modes": MODES})
+    r = subprocess.run([sys.executable, str(script), variant, str(out), spec, kind], cwd=ROOT,
+                       env={**os.environ, "MCX_LIB": variant, "PYTHONPATH": ROOT}, capture_output=True,
+                       text=True, timeout=900)
+    assert r.returncode == 0, r.stderr[-3000:]
+    return dict(np.load(out))
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def test_bounds_build_matches_release_on_valid_inputs(torch_cuda, tmp_path):
+    dbg = _child(tmp_path, "bounds", "valid", LOOKUP_FLAGS)
+    rel = _child(tmp_path, "release", "valid", LOOKUP_FLAGS)
+    assert set(dbg) == set(rel)
+    for k in sorted(rel):
+        if k.startswith("lk_") or k.endswith("_ncoll"):
+            assert np.array_equal(dbg[k].view(np.uint8), rel[k].view(np.uint8)), k
+        else:
+            scale = max(np.abs(rel[k]).max(), 1e-300)
+            np.testing.assert_allclose(dbg[k], rel[k], rtol=1e-10, atol=1e-12 * scale, err_msg=k)
+
+
+def test_out_of_range_processing_order_is_reported(torch_cuda, tmp_path):
+    flags = {k: v for k, v in LOOKUP_FLAGS.items() if k in ("exact", "fast_binned", "staged")}
+    dbg = _child(tmp_path, "bounds", "bad", flags)
+    rel = _child(tmp_path, "release", "valid", {k: v for k, v in flags.items()})
+    lost = dbg["lost"]
+    n = rel["lk_exact"].shape[0]
+    keep = np.ones(n, bool)
+    keep[lost] = False
+    for name in flags:
+        msg = str(dbg["msg_" + name])
+        assert msg.startswith("-6 ") and "lookup index from the processing order" in msg, (name, msg)
+        out = dbg["out_" + name]
+        assert np.all(np.isnan(out[lost])), name
+        assert np.array_equal(out[keep].view(np.uint64), rel["lk_" + name][keep].view(np.uint64)), name
