@@ -826,13 +826,14 @@ def main():
 
 
 def kernel_source_hash() -> str:
-    """Hash of the lookup kernel's source with comments and blank space
-    removed: the recorded DRAM traffic stays valid across comment edits and
-    reads null after any change to the code."""
+    """Hash of the lookup kernel's source and of the binning parameters that
+    set the order it reads in, with comments and blank space removed: the
+    recorded DRAM traffic stays valid across comment edits and reads null
+    after any change to the code."""
     import hashlib
     import re
     h = hashlib.sha256()
-    for f in ("xs_fast.cu", "mcx_internal.cuh"):
+    for f in ("xs_fast.cu", "mcx_internal.cuh", "kernels.h"):
         src = open(os.path.join(ROOT, "paper_2402_09222_b300", "csrc", f)).read()
         src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
         src = re.sub(r"//[^\n]*", "", src)
