@@ -6,9 +6,10 @@ this process computes the same with the release library.
 
 * On valid inputs no check fires (mcx_check_device and the transport runs
   return MCX_OK) and every result equals the release build's: the lookups in
-  each form bit for bit, the backward and the transport tallies to rounding
-  (their atomics add in no fixed order), the per-history collision counts
-  exactly.
+  each form (device and host buffers) bit for bit, the backward and the
+  transport tallies to rounding (their atomics add in no fixed order), the
+  per-history collision counts of fixed-source, batched and eigenvalue runs
+  and the eigenvalue's ordered fission bank exactly.
 * A processing order holding indices outside [0, n) -- input that only the
   debug build's own checks make safe, which is why this case runs only
   there -- is reported by mcx_check_device as MCX_ERR_BOUNDS naming the
@@ -72,6 +73,33 @@ def run_all(flags_by_name, modes):
             res[f"tr_{name}_{k}"] = t[k]
         res[f"tr_{name}_ncoll"] = q.history_debug(prob.n_histories)
         q.close()
+    # the host-buffer lookup (chunked device pipeline, binned per chunk)
+    lib, mats, E, mat, p = lookup_case()
+    res["lk_host"] = p.xs_lookup_host(E, mat, flags=mcx.LOOKUP_FAST | mcx.LOOKUP_SORT)
+    p.check_device()
+    p.close()
+    # eigenvalue generations (the transport kernels' fission instantiations)
+    eig = synth.eigen_problem(3000, lattice_n=9, n_points=2000)
+    q = mcx.make_problem(eig, precision=mcx.FP32, hash_bins=2000)
+    q.set_tuning(mode=1, sort_period=2, sort_threshold=0)
+    r = q.run_eigenvalue(3000, n_generations=3, n_inactive=1, k0=0.04, particles_in_flight=1500, seed=6)
+    q.check_device()
+    res["eig_sites"] = r["sites"]
+    res["eig_k"] = r["k"]
+    res["eig_bank"] = q.fission_bank()
+    q.close()
+    # batched uneven problems sharing one table set
+    blib = synth.species_library(30, 900, 171).channels([synth.CH_SCATTER, synth.CH_ABSORB])
+    bmats = synth.lookup_materials(30, 172, n_materials=5)
+    probs = synth.config5_problems(blib, bmats, n_problems=5, seed=173, hist_lo=100, hist_hi=2000)
+    base = mcx.Problem(probs[0], flags=mcx.FLAG_HISTORY_DEBUG).load_tables(blib, bmats, hash_bins=800)
+    hs = [base] + [mcx.Problem(pr, flags=mcx.FLAG_HISTORY_DEBUG).share_tables(base) for pr in probs[1:]]
+    base.set_tuning(mode=2, sort_period=2, sort_threshold=0)
+    mcx.batch_run(hs, [pr.n_histories for pr in probs], particles_in_flight=1500, seed=8)
+    for i, (h, pr) in enumerate(zip(hs, probs)):
+        h.check_device()
+        res[f"batch{i}_ncoll"] = h.history_debug(pr.n_histories)
+        res[f"batch{i}_flux"] = h.tallies()["flux"]
     return res
 
 def bad_order_case(flags_by_name):
@@ -132,7 +160,7 @@ def test_bounds_build_matches_release_on_valid_inputs(torch_cuda, tmp_path):
     rel = _child(tmp_path, "release", "valid", LOOKUP_FLAGS)
     assert set(dbg) == set(rel)
     for k in sorted(rel):
-        if k.startswith("lk_") or k.endswith("_ncoll"):
+        if k.startswith("lk_") or k.endswith("_ncoll") or k in ("eig_sites", "eig_k", "eig_bank"):
             assert np.array_equal(dbg[k].view(np.uint8), rel[k].view(np.uint8)), k
         else:
             scale = max(np.abs(rel[k]).max(), 1e-300)
