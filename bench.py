@@ -713,7 +713,7 @@ def main():
             e2e_s = shard.max_over_ranks(e2e_s)
         line["e2e"] = {"value": world * N_LOOKUPS / e2e_s, "unit": "lookups/s",
                        "h2d_bytes_per_step": N_LOOKUPS * 12, "d2h_bytes_per_step": N_LOOKUPS * 40,
-                       "path": "mcx_xs_lookup_host, pinned host buffers, 8M-lookup chunks binned and looked up on 2 streams",
+                       "path": "mcx_xs_lookup_host, pinned host buffers, 2M-lookup chunks binned and looked up on 3 streams",
                        "host_link": host_link_bandwidth(oh, out)}
         del oh
         # the same with FP32 outputs (the compensated sums rounded once; still

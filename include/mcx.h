@@ -392,8 +392,10 @@ int mcx_xs_lookup_binned_static(mcx_problem* p, int64_t n, const double* E, cons
                                 double* out, int32_t flags, void* stream);
 
 /* The same lookup from HOST buffers: copies in, computes and copies out in
- * chunks of up to 8M lookups pipelined over two streams (with MCX_LOOKUP_SORT
- * each chunk is binned on the device); synchronous.  out_host is FP64
+ * chunks of up to 2M lookups pipelined over three streams (with
+ * MCX_LOOKUP_SORT each chunk is binned on the device); synchronous.  Device
+ * staging of about 3 x 2M x (32 + 8 n_ch) bytes is allocated on first use and
+ * kept with the handle.  out_host is FP64
  * [n][n_ch], or FP32 with MCX_LOOKUP_OUT32 (half the device-to-host bytes,
  * which bound this path).  Host buffers should be pinned (cudaHostAlloc /
  * torch pin_memory) for full copy speed. */

@@ -221,6 +221,27 @@ def test_host_path_matches_device_path(torch_cuda, small_case):
     assert torch.equal(host3, dev.cpu())
 
 
+@pytest.mark.parametrize("flags", [1, 3, 9, 11])
+def test_host_path_over_several_pipeline_chunks(torch_cuda, flags):
+    """7,000,003 lookups from pinned host buffers: four 2M-lookup chunks over
+    the three pipeline streams (the first stream's staging reused, a ragged
+    last chunk), binned per chunk or not, FP64 or FP32 outputs; equal to the
+    device path bit for bit."""
+    from paper_2402_09222_b300 import mcx
+    torch = torch_cuda
+    lib = synth.species_library(30, 600, 221)
+    mats = synth.lookup_materials(30, 222, n_materials=7)
+    E, mat = synth.lookup_inputs(7_000_003, mats.n_materials, 223)
+    E[[5, 2_097_152, 6_999_999]] = [np.nan, 1e-9, 1e9]
+    mat[[7, 4_194_304]] = [-1, mats.n_materials]
+    p = _handle(lib, mats, 1, 2000)
+    dev = p.xs_lookup(_dev(torch, E, torch.float64), _dev(torch, mat, torch.int32), flags=flags).cpu()
+    host = p.xs_lookup_host(torch.as_tensor(E).pin_memory(), torch.as_tensor(mat).pin_memory(), flags=flags)
+    assert host.dtype == dev.dtype
+    assert torch.equal(host.view(torch.uint8), dev.view(torch.uint8))
+    p.close()
+
+
 def test_backward_matches_oracle_adjoint(torch_cuda):
     torch = torch_cuda
     lib = synth.species_library(12, 300, 211)
