@@ -103,6 +103,28 @@ __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x)
     lo += e;
 }
 
+// two_sum_acc on two independent sums at once with packed FP32 adds (each
+// element rounds exactly as the scalar form does, so the results agree bit
+// for bit).
+#ifndef MCX_FAST_PACKED
+#define MCX_FAST_PACKED 1
+#endif
+__device__ __forceinline__ void two_sum_acc2(float2& hi, float2& lo, float2 x)
+{
+#if MCX_FAST_PACKED
+    // a - b as fma(b, -1, a): the product is exact, so one rounding, as in a - b
+    const float2 m1 = make_float2(-1.f, -1.f);
+    const float2 s = __fadd2_rn(hi, x);
+    const float2 bp = __ffma2_rn(hi, m1, s);
+    const float2 e = __fadd2_rn(__ffma2_rn(__ffma2_rn(bp, m1, s), m1, hi), __ffma2_rn(bp, m1, x));
+    hi = s;
+    lo = __fadd2_rn(lo, e);
+#else
+    two_sum_acc(hi.x, lo.x, x.x);
+    two_sum_acc(hi.y, lo.y, x.y);
+#endif
+}
+
 // One thread per lookup; the material's species are taken U at a time so
 // that the U independent chains of loads (window, search probes, point
 // records) overlap.  The search inside a window [lo, hi] keeps a candidate
@@ -178,11 +200,10 @@ __device__ __forceinline__ void store_nan(float* p) { store_stream(p, __int_as_f
 // (point k) and r1 (point k + 1), the lookup energy as the FP32 pair
 // (E_hi, E_lo) and the FP32 density N.  Shared by every form of the fast
 // lookup, so they agree bit for bit.
-template <int W, int NC>
-__device__ __forceinline__ void species_term(const float (&r0)[4 * W], const float (&r1)[4 * W], float E_hi,
-                                             float E_lo, float N, float (&part)[NC])
+template <int W>
+__device__ __forceinline__ void species_weights(const float (&r0)[4 * W], const float (&r1)[4 * W], float E_hi,
+                                                float E_lo, float N, float& w0, float& w1)
 {
-    float w0, w1;
     if constexpr (W == 2 && MCX_FAST_RINV) {
         // records of two float4 carry 1 / (g[k+1] - g[k]) in their last slot:
         // the fractions are the distances times it, saturated to [0, 1]
@@ -201,6 +222,14 @@ __device__ __forceinline__ void species_term(const float (&r0)[4 * W], const flo
         w1 = nw * a;
         w0 = nw * b;
     }
+}
+
+template <int W, int NC>
+__device__ __forceinline__ void species_term(const float (&r0)[4 * W], const float (&r1)[4 * W], float E_hi,
+                                             float E_lo, float N, float (&part)[NC])
+{
+    float w0, w1;
+    species_weights<W>(r0, r1, E_hi, E_lo, N, w0, w1);
 #pragma unroll
     for (int r = 0; r < NC; ++r) {
 #if MCX_FAST_FMA2
@@ -208,6 +237,81 @@ __device__ __forceinline__ void species_term(const float (&r0)[4 * W], const flo
 #else
         part[r] += fmaf(w0, r0[2 + r], w1 * r1[2 + r]);
 #endif
+    }
+}
+
+// species_term for two lookups that share the species' records, their
+// partial sums held as pairs (first lookup, second lookup): the channel
+// updates as packed fused multiply-adds, each element the scalar form's.
+#ifndef MCX_FAST_PACKED_TERM
+#define MCX_FAST_PACKED_TERM 1
+#endif
+#ifndef MCX_FAST_PACKED_W
+#define MCX_FAST_PACKED_W 1
+#endif
+template <int W, int NC>
+__device__ __forceinline__ void species_term_pair(const float (&r0)[4 * W], const float (&r1)[4 * W], float Eh0,
+                                                  float El0, float Eh1, float El1, float N, float2 (&part)[NC])
+{
+    static_assert(MCX_FAST_FMA2, "the pair form follows the two-FMA channel update");
+#if MCX_FAST_PACKED_TERM && MCX_FAST_PACKED_W
+    // species_weights for both lookups with packed operations: a - b as
+    // fma(b, -1, a) (exact product, one rounding), the clamp per element
+    float2 w0, w1;
+    if constexpr (W == 2 && MCX_FAST_RINV) {
+        const float2 m1 = make_float2(-1.f, -1.f);
+        const float2 Eh = make_float2(Eh0, Eh1), El = make_float2(El0, El1);
+        const float2 rw = make_float2(r0[7], r0[7]), Np = make_float2(N, N);
+        float2 f1 = __fmul2_rn(__fadd2_rn(__ffma2_rn(make_float2(r0[0], r0[0]), m1, Eh),
+                                          __ffma2_rn(make_float2(r0[1], r0[1]), m1, El)), rw);
+        float2 f0 = __fmul2_rn(__fadd2_rn(__ffma2_rn(Eh, m1, make_float2(r1[0], r1[0])),
+                                          __ffma2_rn(El, m1, make_float2(r1[1], r1[1]))), rw);
+        f1 = make_float2(__saturatef(f1.x), __saturatef(f1.y));
+        f0 = make_float2(__saturatef(f0.x), __saturatef(f0.y));
+        w1 = __fmul2_rn(Np, f1);
+        w0 = __fmul2_rn(Np, f0);
+    } else {
+        float w0a, w1a, w0b, w1b;
+        species_weights<W>(r0, r1, Eh0, El0, N, w0a, w1a);
+        species_weights<W>(r0, r1, Eh1, El1, N, w0b, w1b);
+        w0 = make_float2(w0a, w0b);
+        w1 = make_float2(w1a, w1b);
+    }
+#pragma unroll
+    for (int r = 0; r < NC; ++r)
+        part[r] = __ffma2_rn(w1, make_float2(r1[2 + r], r1[2 + r]),
+                             __ffma2_rn(w0, make_float2(r0[2 + r], r0[2 + r]), part[r]));
+#else
+    float w0a, w1a, w0b, w1b;
+    species_weights<W>(r0, r1, Eh0, El0, N, w0a, w1a);
+    species_weights<W>(r0, r1, Eh1, El1, N, w0b, w1b);
+#if MCX_FAST_PACKED_TERM
+    const float2 w0 = make_float2(w0a, w0b), w1 = make_float2(w1a, w1b);
+#pragma unroll
+    for (int r = 0; r < NC; ++r)
+        part[r] = __ffma2_rn(w1, make_float2(r1[2 + r], r1[2 + r]),
+                             __ffma2_rn(w0, make_float2(r0[2 + r], r0[2 + r]), part[r]));
+#else
+#pragma unroll
+    for (int r = 0; r < NC; ++r) {
+        part[r].x = fmaf(w1a, r1[2 + r], fmaf(w0a, r0[2 + r], part[r].x));
+        part[r].y = fmaf(w1b, r1[2 + r], fmaf(w0b, r0[2 + r], part[r].y));
+    }
+#endif
+#endif
+}
+
+// species_term into one element of pair partial sums (lookups whose records differ).
+template <int W, int NC, bool SECOND>
+__device__ __forceinline__ void species_term_half(const float (&r0)[4 * W], const float (&r1)[4 * W], float E_hi,
+                                                  float E_lo, float N, float2 (&part)[NC])
+{
+    float w0, w1;
+    species_weights<W>(r0, r1, E_hi, E_lo, N, w0, w1);
+#pragma unroll
+    for (int r = 0; r < NC; ++r) {
+        float& v = SECOND ? part[r].y : part[r].x;
+        v = fmaf(w1, r1[2 + r], fmaf(w0, r0[2 + r], v));
     }
 }
 
@@ -343,7 +447,11 @@ __global__ void __launch_bounds__(256, MCX_FAST_MIN_BLOCKS) k_xs_lookup_fast(Tab
 // output rows and search keys parked in shared memory to relieve the
 // registers 26.9 ms; FP32 -> FP64 widening of the outputs with integer
 // operations instead of the FP64 pipe, no change; the rows and keys re-read
-// from the permutation when needed instead of held, 62.8 ms.
+// from the permutation when needed instead of held, 62.8 ms.  With binning
+// at about 192 lookups per bucket (22.8 ms), the lane's two lookups are
+// paired in packed FP32 instructions (B300's two-wide add, multiply and
+// fused multiply-add, each element rounded as the scalar operation): the
+// compensated sums 22.6 ms, the channel updates 22.3 ms, the weights 22.2 ms.
 template <int W, int U, int NC, typename OutT>
 __global__ void __launch_bounds__(256, MCX_FAST2_MIN_BLOCKS) k_xs_lookup_warp2(Tables t, int64_t n, const double* __restrict__ Ein,
                                                          const int32_t* __restrict__ mat,
@@ -402,9 +510,9 @@ __global__ void __launch_bounds__(256, MCX_FAST2_MIN_BLOCKS) k_xs_lookup_warp2(T
             }
             const int32_t hb_lo = t.H > 0 ? hash_bin(t, __longlong_as_double(eb_lo), eb_lo) : 0;
             int32_t hb_hi = -1;
-            float hi0[NC], lo0[NC], hi1[NC], lo1[NC];
+            float2 hi[NC], lo[NC];   // (lookup j0, lookup j1) per channel
 #pragma unroll
-            for (int c = 0; c < NC; ++c) hi0[c] = lo0[c] = hi1[c] = lo1[c] = 0.f;
+            for (int c = 0; c < NC; ++c) hi[c] = lo[c] = make_float2(0.f, 0.f);
             const float Eh0 = (float)E0, El0 = (float)(E0 - (double)Eh0);
             const float Eh1 = (float)E1, El1 = (float)(E1 - (double)Eh1);
             const int32_t i0 = __ldg(t.moff + mw), i1 = __ldg(t.moff + mw + 1);
@@ -435,9 +543,9 @@ __global__ void __launch_bounds__(256, MCX_FAST2_MIN_BLOCKS) k_xs_lookup_warp2(T
                 }
                 const int32_t gend = i1 < g0 + 32 ? i1 : g0 + 32;
                 for (int32_t i = g0; i < gend; i += U) {
-                    float p0[NC], p1[NC];
+                    float2 pp[NC];   // partial sums (lookup j0, lookup j1)
 #pragma unroll
-                    for (int c = 0; c < NC; ++c) p0[c] = p1[c] = 0.f;
+                    for (int c = 0; c < NC; ++c) pp[c] = make_float2(0.f, 0.f);
                     const bool full = i + U <= i1;   // no padded slot in this group
 #pragma unroll
                     for (int u = 0; u < U; ++u) {
@@ -451,29 +559,25 @@ __global__ void __launch_bounds__(256, MCX_FAST2_MIN_BLOCKS) k_xs_lookup_warp2(T
                             int32_t bb = b, len = d + 1;
                             while (len > 1) search_step(t.E, bb, len, eb0);
                             load_records<W>(t.frec, bb, r0, r1);
-                            species_term<W, NC>(r0, r1, Eh0, El0, N, p0);
+                            species_term_half<W, NC, false>(r0, r1, Eh0, El0, N, pp);
                             bb = b;
                             len = d + 1;
                             while (len > 1) search_step(t.E, bb, len, eb1);
                             load_records<W>(t.frec, bb, r0, r1);
-                            species_term<W, NC>(r0, r1, Eh1, El1, N, p1);
+                            species_term_half<W, NC, true>(r0, r1, Eh1, El1, N, pp);
                         } else {
                             load_records<W>(t.frec, b, r0, r1);
-                            species_term<W, NC>(r0, r1, Eh0, El0, N, p0);
-                            species_term<W, NC>(r0, r1, Eh1, El1, N, p1);
+                            species_term_pair<W, NC>(r0, r1, Eh0, El0, Eh1, El1, N, pp);
                         }
                     }
 #pragma unroll
-                    for (int c = 0; c < NC; ++c) {
-                        two_sum_acc(hi0[c], lo0[c], p0[c]);
-                        two_sum_acc(hi1[c], lo1[c], p1[c]);
-                    }
+                    for (int c = 0; c < NC; ++c) two_sum_acc2(hi[c], lo[c], pp[c]);
                 }
             }
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
-                store_out(out + l0 * NC + c, hi0[c], lo0[c]);
-                store_out(out + l1 * NC + c, hi1[c], lo1[c]);
+                store_out(out + l0 * NC + c, hi[c].x, lo[c].x);
+                store_out(out + l1 * NC + c, hi[c].y, lo[c].y);
             }
         }
     }
