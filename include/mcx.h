@@ -346,10 +346,10 @@ int mcx_xs_lookup(mcx_problem* p, int64_t n, const double* E, const int32_t* mat
 /* Binning of lookups by material and energy (Sec. 5.1: sorting so that
  * neighbouring threads work on the same material and nearby energies):
  * perm (int32 [n], DEVICE) receives 0..n-1 ordered by (material, bucket of
- * log E) with n / (materials x 192) equal buckets per material over the
- * library's energy range (at least 1; fewer when materials x buckets would
- * exceed 2^21 bins), so about 192 lookups per bucket.  Order within a bucket
- * is unspecified.  E and mat are
+ * log E) with max(n / (materials x 192), 16384) equal buckets per material
+ * over the library's energy range (fewer when materials x buckets would
+ * exceed 2^21 bins; at least 1), so about 192 lookups per bucket in large
+ * batches.  Order within a bucket is unspecified.  E and mat are
  * DEVICE pointers.  Uses a small library-owned bin array (allocated on first
  * use).  Errors: MCX_ERR_ARG, MCX_ERR_STATE, MCX_ERR_CUDA, MCX_ERR_OOM. */
 int mcx_xs_sort(mcx_problem* p, int64_t n, const double* E, const int32_t* mat, int32_t* perm,
@@ -392,10 +392,10 @@ int mcx_xs_lookup_binned_static(mcx_problem* p, int64_t n, const double* E, cons
                                 double* out, int32_t flags, void* stream);
 
 /* The same lookup from HOST buffers: copies in, computes and copies out in
- * chunks of up to 2M lookups pipelined over three streams (with
- * MCX_LOOKUP_SORT each chunk is binned on the device); synchronous.  Device
- * staging of about 3 x 2M x (32 + 8 n_ch) bytes is allocated on first use and
- * kept with the handle.  out_host is FP64
+ * chunks of up to 2M lookups (4M with MCX_LOOKUP_OUT32) pipelined over three
+ * streams (with MCX_LOOKUP_SORT each chunk is binned on the device);
+ * synchronous.  Device staging of about 3 x chunk x (32 + 8 n_ch) bytes is
+ * allocated on first use and kept with the handle.  out_host is FP64
  * [n][n_ch], or FP32 with MCX_LOOKUP_OUT32 (half the device-to-host bytes,
  * which bound this path).  Host buffers should be pinned (cudaHostAlloc /
  * torch pin_memory) for full copy speed. */

@@ -40,15 +40,25 @@ constexpr int64_t kLookupsPerBucket = MCX_LOOKUPS_PER_BUCKET;
 #endif
 constexpr int64_t kBackwardLookupsPerBucket = MCX_BACKWARD_LOOKUPS_PER_BUCKET;
 
+// Buckets per material of a lookup batch at least: below n = materials x
+// per_bucket x this, a warp's 64 lookups span several grid intervals however
+// fine the buckets, and finer buckets cost little at that size (1e8 lookups
+// from host buffers in 4M-lookup chunks with FP32 outputs: 43.2 ms against
+// 49.9 ms at n / (materials x 192) buckets).
+#ifndef MCX_MIN_LOOKUP_EBUCKETS
+#define MCX_MIN_LOOKUP_EBUCKETS 16384
+#endif
 // Binning parameters of a batch of n lookups over n_materials materials with
 // energies in [emin, emax]: n / (n_materials * per_bucket) buckets per
-// material (at least 1), at most max_bins bins in all.
+// material, at least MCX_MIN_LOOKUP_EBUCKETS, at most max_bins bins in all
+// (and at least 1 bucket).
 inline SortParams lookup_sort_params(int n_materials, double emin, double emax, int64_t n, int64_t max_bins,
                                      int64_t per_bucket = kLookupsPerBucket)
 {
     SortParams sp;
     sp.n_materials = n_materials;
     int64_t nb = n / ((int64_t)n_materials * per_bucket);
+    if (nb < MCX_MIN_LOOKUP_EBUCKETS) nb = MCX_MIN_LOOKUP_EBUCKETS;
     if (nb > max_bins / n_materials) nb = max_bins / n_materials;
     sp.n_ebuckets = nb < 1 ? 1 : (int32_t)nb;
     sp.ln_lo = (float)std::log(emin);

@@ -181,17 +181,22 @@ int sm_count_of(int device)
 // Host-path pipeline of mcx_xs_lookup_host: chunks of kHostChunk lookups go
 // round-robin over kHostSlots streams, each with its own staging and binning
 // scratch (copy in, bin, look up, copy out), so the device-to-host copies of
-// one chunk overlap the copy-in and compute of the next ones.  1e8 lookups,
-// FP64 outputs (5.2 GB over the host link): 2M-lookup chunks on 3 streams
-// 74.1-74.6 ms, 4M 75.2, 1M on 4 streams 82-87; 4 streams of 2M 74.1-74.3.
+// one chunk overlap the copy-in and compute of the next ones.  1e8 lookups
+// on 3 streams: FP64 outputs (5.2 GB over the host link, which bounds them)
+// 73.6 ms in 2M-lookup chunks, 74.6 in 4M; FP32 outputs (3.2 GB; the
+// per-chunk lookups weigh more) 43.2 ms in 4M chunks, 48.5 in 2M.
 #ifndef MCX_HOST_SLOTS
 #define MCX_HOST_SLOTS 3
 #endif
 #ifndef MCX_HOST_CHUNK
 #define MCX_HOST_CHUNK (2 << 20)
 #endif
+#ifndef MCX_HOST_CHUNK32
+#define MCX_HOST_CHUNK32 (4 << 20)
+#endif
 constexpr int kHostSlots = MCX_HOST_SLOTS;
 constexpr int64_t kHostChunk = MCX_HOST_CHUNK;
+constexpr int64_t kHostChunk32 = MCX_HOST_CHUNK32;
 static_assert(kHostSlots >= 1 && kHostSlots <= 4, "host pipeline slots: 1 to 4 streams");
 constexpr int kWorkCtrs = 4;   // chunk counters (>= kHostSlots), then the error word
 
@@ -1550,7 +1555,8 @@ int mcx_xs_lookup_host(mcx_problem* p, int64_t n, const double* E_host, const in
     DeviceGuard dg(p->device);
     const TableStore* ts = p->tables;
     const int nc = ts->view.n_ch;
-    const int64_t chunk = n < (int64_t)kHostChunk ? n : (int64_t)kHostChunk;
+    const int64_t most = (flags & MCX_LOOKUP_OUT32) ? kHostChunk32 : kHostChunk;
+    const int64_t chunk = n < most ? n : most;
     const SortParams sp = batch_sort_params(ts, chunk);
     const int64_t nbins = (int64_t)sp.n_materials * sp.n_ebuckets + 1 + kSortScanParts;
     // staging per slot (in doubles): E [chunk], mat [chunk int32], out
