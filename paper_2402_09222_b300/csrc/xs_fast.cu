@@ -456,7 +456,8 @@ __global__ void __launch_bounds__(256, MCX_FAST_MIN_BLOCKS) k_xs_lookup_fast(Tab
 // fused multiply-add, each element rounded as the scalar operation): the
 // compensated sums 22.6 ms, the channel updates 22.3 ms, the weights 22.2 ms;
 // each lane's search keys and output rows parked in shared memory, so that
-// the species loop spills half as much, 22.47 -> 22.27 ms on one box.
+// the species loop spills half as much, 22.47 -> 22.27 ms on one box (with
+// 3 blocks per SM and no spills at all, 23.58 ms against 22.24).
 template <int W, int U, int NC, typename OutT>
 __global__ void __launch_bounds__(256, MCX_FAST2_MIN_BLOCKS) k_xs_lookup_warp2(Tables t, int64_t n, const double* __restrict__ Ein,
                                                          const int32_t* __restrict__ mat,
