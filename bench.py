@@ -37,6 +37,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 N_LOOKUPS = 100_000_000
+E2E_CALLS = 3        # timed end-to-end calls from host buffers (after one untimed call)
 N_SPECIES, N_POINTS = 355, 11_303
 LIB_SEED, MAT_SEED, INPUT_SEED = 1236, 1236, 1336
 # FP32 tables, fast arithmetic, binned; hash bins from a sweep of the tuner's
@@ -702,28 +703,32 @@ def main():
         Eh = torch.as_tensor(E).pin_memory()
         mh = torch.as_tensor(mat).pin_memory()
         oh = torch.empty((N_LOOKUPS, 5), dtype=torch.float64).pin_memory()
-        p.xs_lookup_host(Eh[:1_000_000], mh[:1_000_000], oh[:1_000_000], flags=TUNED["flags"] | mcx.LOOKUP_SORT)
+        # one untimed full-size call (it allocates the pipeline's staging),
+        # then the mean of E2E_CALLS timed calls
+        p.xs_lookup_host(Eh, mh, oh, flags=TUNED["flags"] | mcx.LOOKUP_SORT)
         if world > 1:
             dist.barrier()
         t0w = time.perf_counter()
-        p.xs_lookup_host(Eh, mh, oh, flags=TUNED["flags"] | mcx.LOOKUP_SORT)
-        e2e_s = time.perf_counter() - t0w
+        for _ in range(E2E_CALLS):
+            p.xs_lookup_host(Eh, mh, oh, flags=TUNED["flags"] | mcx.LOOKUP_SORT)
+        e2e_s = (time.perf_counter() - t0w) / E2E_CALLS
         if world > 1:
             from paper_2402_09222_b300 import shard
             e2e_s = shard.max_over_ranks(e2e_s)
         line["e2e"] = {"value": world * N_LOOKUPS / e2e_s, "unit": "lookups/s",
                        "h2d_bytes_per_step": N_LOOKUPS * 12, "d2h_bytes_per_step": N_LOOKUPS * 40,
-                       "path": "mcx_xs_lookup_host, pinned host buffers, 2M-lookup chunks binned and looked up on 3 streams",
+                       "path": "mcx_xs_lookup_host, pinned host buffers, 2M-lookup chunks binned and looked up on 3 streams; mean of 3 calls after one untimed call",
                        "host_link": host_link_bandwidth(oh, out)}
         del oh
         # the same with FP32 outputs (the compensated sums rounded once; still
         # within 1e-6 of the definition): half the device-to-host bytes
         oh32 = torch.empty((N_LOOKUPS, 5), dtype=torch.float32).pin_memory()
         f32 = TUNED["flags"] | mcx.LOOKUP_SORT | mcx.LOOKUP_OUT32
-        p.xs_lookup_host(Eh[:1_000_000], mh[:1_000_000], oh32[:1_000_000], flags=f32)
-        t0w = time.perf_counter()
         p.xs_lookup_host(Eh, mh, oh32, flags=f32)
-        e2e32 = time.perf_counter() - t0w
+        t0w = time.perf_counter()
+        for _ in range(E2E_CALLS):
+            p.xs_lookup_host(Eh, mh, oh32, flags=f32)
+        e2e32 = (time.perf_counter() - t0w) / E2E_CALLS
         if world > 1:
             e2e32 = shard.max_over_ranks(e2e32)
         out32 = torch.empty((N_LOOKUPS, 5), dtype=torch.float32, device="cuda")
@@ -736,7 +741,8 @@ def main():
         torch.cuda.synchronize()
         line["fp32_outputs"] = {
             "e2e": {"value": world * N_LOOKUPS / e2e32, "unit": "lookups/s", "h2d_bytes_per_step": N_LOOKUPS * 12,
-                    "d2h_bytes_per_step": N_LOOKUPS * 20},
+                    "d2h_bytes_per_step": N_LOOKUPS * 20,
+                    "path": "4M-lookup chunks on 3 streams; mean of 3 calls after one untimed call"},
             "device_step_lookups_per_s": N_LOOKUPS / (a32.elapsed_time(b32) / 1e3),
             "note": "MCX_LOOKUP_OUT32: outputs rounded once to FP32 (within the 1e-6 bound); "
                     "the headline value keeps FP64 outputs"}
