@@ -113,6 +113,22 @@ constexpr int kSortScanParts = 1024;
 int launch_lookup_sort(const SortParams& sp, int64_t n, const double* E, const int32_t* mat,
                        uint32_t* bins, int32_t* perm, int grid, cudaStream_t st);
 
+// The same binning in two levels (coarse bins of 512 consecutive bins,
+// counted per tile of lookups in shared memory; then each coarse bin sorted
+// by its fine bins in shared memory): no global atomic per lookup.  Scratch:
+// place [lookup_sort2_place_words] uint32, keys [n] uint32, tidx [n] int32,
+// tfine [n] uint16.
+// Returns -2 when the batch's tiles x coarse bins exceed 2^28 or its coarse
+// bins 2048 (use launch_lookup_sort), -1 on a launch error.
+#ifndef MCX_BIN2_MIN_LOOKUPS
+#define MCX_BIN2_MIN_LOOKUPS (1 << 22)
+#endif
+constexpr int64_t kBin2MinLookups = MCX_BIN2_MIN_LOOKUPS;   // batches from this size take it
+size_t lookup_sort2_place_words(const SortParams& sp, int64_t n);
+int launch_lookup_sort2(const SortParams& sp, int64_t n, const double* E, const int32_t* mat, uint32_t* place,
+                        uint32_t* keys, int32_t* tidx, uint16_t* tfine, int32_t* perm, int sm_count,
+                        cudaStream_t st);
+
 // First failed bounds check of each kernel translation unit since the last
 // read (site << 56 | index; 0: none), cleared by the read; always 0 in
 // release builds.

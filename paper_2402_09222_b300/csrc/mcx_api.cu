@@ -243,8 +243,10 @@ struct mcx_problem {
     // lookup scratch
     int32_t* perm = nullptr;
     uint32_t* lbins = nullptr;
+    int32_t* bin2 = nullptr;   // two-level binning: bin keys [n], lookup indices [n], fine bins [n] uint16
     int64_t perm_cap = 0;
     size_t lbins_cap = 0;
+    size_t bin2_cap = 0;
     double* h_buf = nullptr;  // host-path device staging
     unsigned long long* work_ctr = nullptr;  // chunk counters of the binned fast lookup, then the staged kernel's error word
     cudaStream_t hstream[2] = {nullptr, nullptr};   // host-path pipeline streams beyond stream and stream2
@@ -809,12 +811,37 @@ int sort_device(mcx_problem* p, int64_t n, const double* E, const int32_t* mat, 
                 cudaStream_t st, int64_t per_bucket = kLookupsPerBucket)
 {
     const SortParams sp = batch_sort_params(p->tables, n, (int64_t)1 << 21, per_bucket);
-    const size_t nb = (size_t)sp.n_materials * sp.n_ebuckets + 1 + kSortScanParts;
+    // large batches: the two-level binning (no global atomic per lookup)
+    const bool two = n >= kBin2MinLookups;
+    const size_t nb = two ? lookup_sort2_place_words(sp, n)
+                          : (size_t)sp.n_materials * sp.n_ebuckets + 1 + kSortScanParts;
     if (p->lbins_cap < nb) {
         dev_free(p->lbins);
         p->lbins_cap = 0;
         TRY(dev_alloc(&p->lbins, nb));
         p->lbins_cap = nb;
+    }
+    if (two) {
+        const size_t words = 2 * (size_t)n + ((size_t)n + 1) / 2;   // keys, indices, fine bins
+        if (p->bin2_cap < words) {
+            dev_free(p->bin2);
+            p->bin2_cap = 0;
+            TRY(dev_alloc(&p->bin2, words));
+            p->bin2_cap = words;
+        }
+        const int r = launch_lookup_sort2(sp, n, E, mat, p->lbins, reinterpret_cast<uint32_t*>(p->bin2),
+                                          p->bin2 + n, reinterpret_cast<uint16_t*>(p->bin2 + 2 * n), perm,
+                                          p->sm_count, st);
+        if (r == 0) return MCX_OK;
+        if (r == -1) return fail(MCX_ERR_CUDA, "lookup binning launch failed");
+        // r == -2: too many tiles x coarse bins; the one-level sort below
+        const size_t nb1 = (size_t)sp.n_materials * sp.n_ebuckets + 1 + kSortScanParts;
+        if (p->lbins_cap < nb1) {
+            dev_free(p->lbins);
+            p->lbins_cap = 0;
+            TRY(dev_alloc(&p->lbins, nb1));
+            p->lbins_cap = nb1;
+        }
     }
     if (launch_lookup_sort(sp, n, E, mat, p->lbins, perm, lookup_grid(p), st))
         return fail(MCX_ERR_CUDA, "lookup sort launch failed");
@@ -1050,6 +1077,7 @@ void mcx_destroy(mcx_problem* p)
     dev_free(p->ncoll_debug);
     dev_free(p->perm);
     dev_free(p->lbins);
+    dev_free(p->bin2);
     dev_free(p->h_buf);
     dev_free(p->work_ctr);
     dev_free(p->e_ctl);

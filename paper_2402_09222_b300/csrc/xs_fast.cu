@@ -1009,6 +1009,28 @@ __global__ void __launch_bounds__(kStThreads, MCX_STAGED_BLOCKS) k_xs_lookup_sta
 
 constexpr unsigned FULL = 0xffffffffu;
 
+// Two-level binning: lookups per tile of passes 0 and A, lookups per
+// sub-tile of pass B, fine bins per coarse bin (as bits), and the resident
+// blocks per SM passes A and B are compiled for.  Per 1e8 lookups (binning
+// time by CUDA events): tile 8192 / sub-tile 8192 / 2 / 2 blocks 2.11 ms,
+// 8192 / 4096 / 2 / 3 2.05 ms, 4096 / 8192 / 3 / 2 2.22 ms, 8192 / 8192 /
+// 2 / 3 2.13 ms; the one-level sort 2.63 ms on a like box.
+#ifndef MCX_BIN2_TILE
+#define MCX_BIN2_TILE 8192
+#endif
+#ifndef MCX_BIN2_SUB
+#define MCX_BIN2_SUB 4096
+#endif
+#ifndef MCX_BIN2_A_BLOCKS
+#define MCX_BIN2_A_BLOCKS 2
+#endif
+#ifndef MCX_BIN2_B_BLOCKS
+#define MCX_BIN2_B_BLOCKS 3
+#endif
+constexpr int kBinTile = MCX_BIN2_TILE;
+constexpr int kBinSub = MCX_BIN2_SUB;
+constexpr int kBinFineBits = 9;
+
 
 __global__ void k_lookup_sort_count(SortParams sp, int64_t n, const double* __restrict__ E,
                                     const int32_t* __restrict__ mat, uint32_t* __restrict__ bins)
@@ -1155,6 +1177,210 @@ __global__ void k_lookup_sort_scatter(SortParams sp, int64_t n, const double* __
     }
 }
 
+// ------------------------------------------------------ two-level binning
+// The same binning for large batches without a global atomic per lookup.
+// The bin key splits into a coarse bin (key >> kBinFineBits, at most a few
+// thousand) and a fine bin (the low bits).  Pass 0 counts each tile's
+// lookups per coarse bin in shared memory into cnt[coarse * n_tiles + tile];
+// an exclusive scan of that matrix gives every (coarse bin, tile) its place.
+// Pass A re-reads each tile, takes places within the tile's runs by
+// shared-memory atomics and writes the lookup index and its fine bin there
+// (a tile's runs are short and filled at once, so L2 merges the partial
+// writes).  Pass B gives each coarse bin to one block, which counts its fine
+// bins in shared memory and scatters the indices into the final order.
+__global__ void __launch_bounds__(512) k_bin2_count(SortParams sp, int64_t n, const double* __restrict__ E,
+                                                   const int32_t* __restrict__ mat, int n_coarse, int n_tiles,
+                                                   uint32_t* __restrict__ cnt, uint32_t* __restrict__ keys)
+{
+    extern __shared__ uint32_t h[];   // [n_coarse]
+    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        for (int i = threadIdx.x; i < n_coarse; i += blockDim.x) h[i] = 0u;
+        __syncthreads();
+        const int64_t base = (int64_t)tile * kBinTile;
+        for (int k = threadIdx.x; k < kBinTile; k += blockDim.x) {
+            const int64_t l = base + k;
+            if (l < n) {
+                const uint32_t key = (uint32_t)lookup_key(sp, __ldg(E + l), __ldg(mat + l));
+                keys[l] = key;
+                atomicAdd(&h[key >> kBinFineBits], 1u);
+            }
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < n_coarse; i += blockDim.x) cnt[(int64_t)i * n_tiles + tile] = h[i];
+        __syncthreads();
+    }
+}
+
+// Exclusive scan, in place, of a[0, m) in shared memory for m <= 4 x
+// blockDim.x (blockDim.x a multiple of 32, at most 1024); every thread calls it.
+__device__ __forceinline__ void smem_exclusive_scan(uint32_t* a, int m, uint32_t* warp_sums)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int i0 = threadIdx.x * 4;
+    uint32_t v[4], t = 0u;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        v[q] = i0 + q < m ? a[i0 + q] : 0u;
+        t += v[q];
+    }
+    uint32_t x = t;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(FULL, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < nw ? warp_sums[lane] : 0u;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(FULL, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < nw) warp_sums[lane] = w;
+    }
+    __syncthreads();
+    uint32_t run = (warp ? warp_sums[warp - 1] : 0u) + x - t;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        if (i0 + q < m) a[i0 + q] = run;
+        run += v[q];
+    }
+    __syncthreads();
+}
+
+constexpr int kBin2Threads = 512;
+constexpr int kBin2PerThread = kBinTile / kBin2Threads;
+
+// Pass A, one tile at a time: the tile's lookups are ranked by coarse bin in
+// shared memory, staged in that order, and written out as contiguous runs.
+__global__ void __launch_bounds__(kBin2Threads, MCX_BIN2_A_BLOCKS) k_bin2_scatter(int64_t n, const uint32_t* __restrict__ keys,
+                                                              int n_coarse, int n_tiles,
+                                                              const uint32_t* __restrict__ place,
+                                                              int32_t* __restrict__ tidx,
+                                                              uint16_t* __restrict__ tfine)
+{
+    extern __shared__ uint32_t sm[];
+    uint32_t* cur = sm;                                    // [n_coarse] first place of (bin, tile)
+    uint32_t* lst = sm + n_coarse;                         // [n_coarse] tile-local counts, then starts
+    uint32_t* skey = sm + 2 * n_coarse;                    // [kBinTile] staged keys
+    int32_t* sidx = reinterpret_cast<int32_t*>(skey + kBinTile);   // [kBinTile] staged indices
+    __shared__ uint32_t warp_sums[32];
+    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        for (int i = threadIdx.x; i < n_coarse; i += blockDim.x) {
+            cur[i] = place[(int64_t)i * n_tiles + tile];
+            lst[i] = 0u;
+        }
+        __syncthreads();
+        const int64_t base = (int64_t)tile * kBinTile;
+        const int cnt = n - base < kBinTile ? (int)(n - base) : kBinTile;
+        uint32_t key[kBin2PerThread], rk[kBin2PerThread];
+#pragma unroll
+        for (int j = 0; j < kBin2PerThread; ++j) {
+            const int k = threadIdx.x + j * kBin2Threads;
+            key[j] = 0u;
+            rk[j] = 0u;
+            if (k < cnt) {
+                key[j] = __ldg(keys + base + k);
+                rk[j] = atomicAdd(&lst[key[j] >> kBinFineBits], 1u);
+            }
+        }
+        __syncthreads();
+        smem_exclusive_scan(lst, n_coarse, warp_sums);
+#pragma unroll
+        for (int j = 0; j < kBin2PerThread; ++j) {
+            const int k = threadIdx.x + j * kBin2Threads;
+            if (k < cnt) {
+                const uint32_t slot = lst[key[j] >> kBinFineBits] + rk[j];
+                skey[slot] = key[j];
+                sidx[slot] = (int32_t)(base + k);
+            }
+        }
+        __syncthreads();
+        for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
+            const uint32_t kk = skey[k];
+            const uint32_t c = kk >> kBinFineBits;
+            const uint32_t pos = cur[c] + ((uint32_t)k - lst[c]);
+            tidx[pos] = sidx[k];
+            tfine[pos] = (uint16_t)(kk & ((1u << kBinFineBits) - 1u));
+        }
+        __syncthreads();
+    }
+}
+
+// Pass B: coarse bin c holds places [place[c * n_tiles], place[(c + 1) *
+// n_tiles]) (n for the last), the same range in the final order.  One block
+// per coarse bin counts its fine bins, then takes the range in sub-tiles of
+// kBinSub: each is ranked by fine bin in shared memory, staged, and written
+// out as contiguous runs.
+constexpr int kBin2FineThreads = 1 << kBinFineBits;    // one fine bin per thread
+constexpr int kBin2FinePerThread = kBinSub / kBin2FineThreads;
+__global__ void __launch_bounds__(kBin2FineThreads, MCX_BIN2_B_BLOCKS) k_bin2_fine(int64_t n, int n_coarse, int n_tiles,
+                                                               const uint32_t* __restrict__ place,
+                                                               const int32_t* __restrict__ tidx,
+                                                               const uint16_t* __restrict__ tfine,
+                                                               int32_t* __restrict__ perm)
+{
+    constexpr int F = kBin2FineThreads;
+    extern __shared__ uint32_t sm[];
+    uint32_t* fcur = sm;                               // [F] next place of each fine bin in the range
+    uint32_t* lst = sm + F;                            // [F] sub-tile counts, then starts
+    int32_t* sidx = reinterpret_cast<int32_t*>(sm + 2 * F);            // [kBinSub] staged indices
+    uint16_t* sfine = reinterpret_cast<uint16_t*>(sidx + kBinSub);    // [kBinSub] staged fine bins
+    __shared__ uint32_t warp_sums[32];
+    for (int c = blockIdx.x; c < n_coarse; c += gridDim.x) {
+        const int64_t s0 = place[(int64_t)c * n_tiles];
+        const int64_t s1 = c + 1 < n_coarse ? (int64_t)place[(int64_t)(c + 1) * n_tiles] : n;
+        fcur[threadIdx.x] = 0u;
+        __syncthreads();
+        for (int64_t e = s0 + threadIdx.x; e < s1; e += F) atomicAdd(&fcur[__ldg(tfine + e)], 1u);
+        __syncthreads();
+        smem_exclusive_scan(fcur, F, warp_sums);
+        for (int64_t sub = s0; sub < s1; sub += kBinSub) {
+            const int cnt = s1 - sub < kBinSub ? (int)(s1 - sub) : kBinSub;
+            lst[threadIdx.x] = 0u;
+            __syncthreads();
+            // per element its rank within its fine bin (< kBinSub) above the
+            // fine bin's kBinFineBits bits
+            static_assert(kBinSub <= (1 << (32 - kBinFineBits)), "rank and fine bin share a word");
+            uint32_t fr[kBin2FinePerThread];
+            int32_t ix[kBin2FinePerThread];
+#pragma unroll
+            for (int j = 0; j < kBin2FinePerThread; ++j) {
+                const int k = threadIdx.x + j * F;
+                fr[j] = 0u;
+                ix[j] = 0;
+                if (k < cnt) {
+                    const uint32_t fb = __ldg(tfine + sub + k);
+                    ix[j] = __ldg(tidx + sub + k);
+                    fr[j] = (atomicAdd(&lst[fb], 1u) << kBinFineBits) | fb;
+                }
+            }
+            __syncthreads();
+            const uint32_t mine = lst[threadIdx.x];   // this sub-tile's count of fine bin threadIdx.x
+            __syncthreads();
+            smem_exclusive_scan(lst, F, warp_sums);
+#pragma unroll
+            for (int j = 0; j < kBin2FinePerThread; ++j) {
+                const int k = threadIdx.x + j * F;
+                if (k < cnt) {
+                    const uint32_t fb = fr[j] & ((1u << kBinFineBits) - 1u);
+                    const uint32_t slot = lst[fb] + (fr[j] >> kBinFineBits);
+                    sidx[slot] = ix[j];
+                    sfine[slot] = (uint16_t)fb;
+                }
+            }
+            __syncthreads();
+            for (int k = threadIdx.x; k < cnt; k += F) {
+                const uint32_t fb = sfine[k];
+                perm[s0 + fcur[fb] + ((uint32_t)k - lst[fb])] = sidx[k];
+            }
+            __syncthreads();
+            fcur[threadIdx.x] += mine;
+            __syncthreads();
+        }
+    }
+}
+
 }  // namespace
 
 template <typename OutT>
@@ -1242,6 +1468,18 @@ int launch_xs_lookup_staged(const Tables& t, const SortParams& sp, int64_t n, co
                  : launch_staged_t(t, sp, n, E, mat, perm, static_cast<double*>(out), grid, st, work, err);
 }
 
+// Exclusive scan of bins[0, nb) (part sums at bins + nb + 1): parts of
+// whole 1024-bin steps, at most kSortScanParts of them.
+static void launch_bin_scan(uint32_t* bins, int nb, cudaStream_t st)
+{
+    int seg = (nb + kSortScanParts - 1) / kSortScanParts;
+    seg = (seg + 1023) / 1024 * 1024;
+    const int parts = (nb + seg - 1) / seg;
+    uint32_t* part = bins + nb + 1;
+    k_scan_part_sums<<<parts, 1024, 0, st>>>(bins, nb, seg, part);
+    k_scan_parts<<<parts, 1024, 0, st>>>(bins, nb, seg, part);
+}
+
 int launch_lookup_sort(const SortParams& sp, int64_t n, const double* E, const int32_t* mat,
                        uint32_t* bins, int32_t* perm, int grid, cudaStream_t st)
 {
@@ -1251,14 +1489,52 @@ int launch_lookup_sort(const SortParams& sp, int64_t n, const double* E, const i
         k_lookup_sort_count<<<grid, 512, sizeof(uint32_t) * nb, st>>>(sp, n, E, mat, bins);
     else
         k_lookup_sort_count_global<<<grid, 256, 0, st>>>(sp, n, E, mat, bins);
-    // parts of whole 1024-bin steps, at most kSortScanParts of them
-    int seg = (nb + kSortScanParts - 1) / kSortScanParts;
-    seg = (seg + 1023) / 1024 * 1024;
-    const int parts = (nb + seg - 1) / seg;
-    uint32_t* part = bins + nb + 1;
-    k_scan_part_sums<<<parts, 1024, 0, st>>>(bins, nb, seg, part);
-    k_scan_parts<<<parts, 1024, 0, st>>>(bins, nb, seg, part);
+    launch_bin_scan(bins, nb, st);
     k_lookup_sort_scatter<<<grid, 256, 0, st>>>(sp, n, E, mat, bins, perm);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+namespace {
+struct Bin2Plan {
+    int n_coarse, n_tiles;
+    int64_t cells;   // n_coarse x n_tiles
+};
+Bin2Plan bin2_plan(const SortParams& sp, int64_t n)
+{
+    Bin2Plan b;
+    const int64_t nbins = (int64_t)sp.n_materials * sp.n_ebuckets;
+    b.n_coarse = (int)((nbins + (1 << kBinFineBits) - 1) >> kBinFineBits);
+    b.n_tiles = (int)((n + kBinTile - 1) / kBinTile);
+    b.cells = (int64_t)b.n_coarse * b.n_tiles;
+    return b;
+}
+}  // namespace
+
+size_t lookup_sort2_place_words(const SortParams& sp, int64_t n)
+{
+    return (size_t)bin2_plan(sp, n).cells + 1 + kSortScanParts;
+}
+
+int launch_lookup_sort2(const SortParams& sp, int64_t n, const double* E, const int32_t* mat, uint32_t* place,
+                        uint32_t* keys, int32_t* tidx, uint16_t* tfine, int32_t* perm, int sm_count,
+                        cudaStream_t st)
+{
+    const Bin2Plan b = bin2_plan(sp, n);
+    // the tile scan covers 4 coarse bins per thread of pass A
+    if (n < 1 || b.cells > ((int64_t)1 << 28) || b.n_coarse > 4 * kBin2Threads) return -2;
+    const size_t smem = sizeof(uint32_t) * (size_t)b.n_coarse;
+    const size_t smem_a = sizeof(uint32_t) * (2 * (size_t)b.n_coarse + 2 * kBinTile);
+    const size_t smem_b = sizeof(uint32_t) * 2 * kBin2FineThreads + (sizeof(int32_t) + sizeof(uint16_t)) * kBinSub;
+    if (cudaFuncSetAttribute(k_bin2_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_a) != cudaSuccess ||
+        cudaFuncSetAttribute(k_bin2_fine, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b) != cudaSuccess)
+        return -1;
+    const int g = b.n_tiles < sm_count * 4 ? b.n_tiles : sm_count * 4;
+    k_bin2_count<<<g, 512, smem, st>>>(sp, n, E, mat, b.n_coarse, b.n_tiles, place, keys);
+    launch_bin_scan(place, (int)b.cells, st);
+    const int ga = b.n_tiles < sm_count * MCX_BIN2_A_BLOCKS ? b.n_tiles : sm_count * MCX_BIN2_A_BLOCKS;
+    k_bin2_scatter<<<ga, kBin2Threads, smem_a, st>>>(n, keys, b.n_coarse, b.n_tiles, place, tidx, tfine);
+    const int gb = b.n_coarse < sm_count * MCX_BIN2_B_BLOCKS ? b.n_coarse : sm_count * MCX_BIN2_B_BLOCKS;
+    k_bin2_fine<<<gb, kBin2FineThreads, smem_b, st>>>(n, b.n_coarse, b.n_tiles, place, tidx, tfine, perm);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

@@ -117,13 +117,15 @@ def _assert_binned(E, mat, pm, lib, n_materials):
         assert drop.max() <= width * (1 + 1e-4) + 1e-5, (drop.max(), width)
 
 
-@pytest.mark.parametrize("n", [1, 777, 1_000_003, 50_000_017])
+@pytest.mark.parametrize("n", [1, 777, 1_000_003, 4_194_304, 50_000_017])
 def test_binning_orders_by_material_then_log_energy(torch_cuda, n):
     """mcx_xs_sort over 12 materials: up to 37.7e6 lookups the floor of
-    16,384 buckets per material (196,608 bins, counters scanned in 192
-    parts); 5e7 lookups, 21,701 buckets per material (260,412 bins, 255
-    parts).  A NaN energy takes the first bucket, energies outside the grid
-    the end buckets.  (Counting in shared memory, at most 12,288 bins, is the
+    16,384 buckets per material (196,608 bins); 5e7 lookups, 21,701 buckets
+    per material (260,412 bins).  Below 2^22 lookups the one-level counting
+    sort (counters scanned in 192 parts), from 2^22 the two-level one (384
+    coarse bins x 512 tiles of 8192 lookups at 2^22; 509 x 6104 at 5e7).  A
+    NaN energy takes the first bucket, energies outside the grid the end
+    buckets.  (Counting in shared memory, at most 12,288 bins, is the
     static-scratch entry point's, tested with it.)"""
     torch = torch_cuda
     lib = synth.species_library(20, 200, 141)
@@ -138,15 +140,17 @@ def test_binning_orders_by_material_then_log_energy(torch_cuda, n):
     p.close()
 
 
+@pytest.mark.parametrize("n", [3_000_017, 5_000_011])
 @pytest.mark.parametrize("layout", ["one_bin", "sorted", "pairs"])
-def test_binning_of_concentrated_and_presorted_batches(torch_cuda, layout):
-    """Batches whose neighbouring lookups share bins (the binning kernels'
-    warp-aggregated path): every lookup in one bin, a batch already sorted by
-    energy, and equal neighbours in pairs; 3e6 lookups over 12 materials."""
+def test_binning_of_concentrated_and_presorted_batches(torch_cuda, layout, n):
+    """Batches whose neighbouring lookups share bins: every lookup in one bin,
+    a batch already sorted by energy, and equal neighbours in pairs, over 12
+    materials; 3e6 lookups take the one-level sort (its warp-aggregated
+    path), 5e6 the two-level one (every lookup of a one-bin batch in one
+    coarse bin)."""
     torch = torch_cuda
     lib = synth.species_library(20, 200, 151)
     mats = synth.lookup_materials(20, 152, n_materials=12)
-    n = 3_000_017
     E, mat = synth.lookup_inputs(n, mats.n_materials, 153)
     if layout == "one_bin":
         E[:] = 1.0
