@@ -140,6 +140,21 @@ def test_binning_orders_by_material_then_log_energy(torch_cuda, n):
     p.close()
 
 
+def test_binning_with_too_many_coarse_bins_takes_the_one_level_sort(torch_cuda):
+    """4.2e6 lookups over 120 materials: 16,384 buckets per material, 1.97e6
+    bins, 3,840 coarse bins of 512 -- more than the two-level binning's 2,048,
+    so the one-level counting sort bins the batch."""
+    torch = torch_cuda
+    lib = synth.species_library(150, 200, 161)
+    mats = synth.lookup_materials(150, 162, n_materials=120)
+    n = 4_200_007
+    E, mat = synth.lookup_inputs(n, mats.n_materials, 163)
+    p = _handle(lib, mats, 1, 1000)
+    perm = p.xs_sort(_dev(torch, E, torch.float64), _dev(torch, mat, torch.int32))
+    _assert_binned(E, mat, perm.cpu().numpy(), lib, mats.n_materials)
+    p.close()
+
+
 @pytest.mark.parametrize("n", [3_000_017, 5_000_011])
 @pytest.mark.parametrize("layout", ["one_bin", "sorted", "pairs"])
 def test_binning_of_concentrated_and_presorted_batches(torch_cuda, layout, n):
