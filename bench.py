@@ -692,7 +692,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32 tables, f64 energies and search",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "tables": "FP32", "hash_bins": TUNED["hash_bins"],
-                       "arithmetic": "fast (<=1e-6 rel)", "binning": "material x log-E buckets, ~192 lookups each",
+                       "arithmetic": "fast (<=1e-6 rel)", "binning": "material x log-E buckets, ~128 lookups each, in two levels",
                        "l2": "inputs 1.2 GB + outputs 4 GB per step exceed the 126 MB L2",
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
             "roofline": roofline, "gpu_launches": 5 * args.steps,

@@ -346,9 +346,9 @@ int mcx_xs_lookup(mcx_problem* p, int64_t n, const double* E, const int32_t* mat
 /* Binning of lookups by material and energy (Sec. 5.1: sorting so that
  * neighbouring threads work on the same material and nearby energies):
  * perm (int32 [n], DEVICE) receives 0..n-1 ordered by (material, bucket of
- * log E) with max(n / (materials x 192), 16384) equal buckets per material
+ * log E) with max(n / (materials x 128), 16384) equal buckets per material
  * over the library's energy range (fewer when materials x buckets would
- * exceed 2^21 bins; at least 1), so about 192 lookups per bucket in large
+ * exceed 2^21 bins; at least 1), so about 128 lookups per bucket in large
  * batches.  Order within a bucket is unspecified.  E and mat are
  * DEVICE pointers.  Uses a small library-owned bin array (allocated on first
  * use).  Errors: MCX_ERR_ARG, MCX_ERR_STATE, MCX_ERR_CUDA, MCX_ERR_OOM. */

@@ -25,11 +25,14 @@ struct SortParams {
 };
 
 // Lookups per (material, log-energy bucket) the binning of a lookup batch
-// aims at on average.  A warp's 64-lookup round then spans about one bucket,
-// so the fewer grid points a bucket holds, the fewer species' bracketing
-// intervals a round straddles; finer buckets leave rounds spanning several.
+// aims at on average.  A warp's 64-lookup round then spans one or two
+// buckets, so the fewer grid points a bucket holds, the fewer species'
+// bracketing intervals a round straddles; finer buckets leave rounds spanning
+// several.  1e8 lookups, two-level binning: 96 / 112 / 128 / 160 / 192 per
+// bucket give 24.07 / 23.92 / 23.89 / 24.21 / 24.13 ms per step (the last two
+// on different boxes: 128 and 160 gave 24.21 where 192 gave 24.40).
 #ifndef MCX_LOOKUPS_PER_BUCKET
-#define MCX_LOOKUPS_PER_BUCKET 192
+#define MCX_LOOKUPS_PER_BUCKET 128
 #endif
 constexpr int64_t kLookupsPerBucket = MCX_LOOKUPS_PER_BUCKET;
 

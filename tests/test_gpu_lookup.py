@@ -99,7 +99,7 @@ def test_binning_changes_nothing(torch_cuda, small_case, flags):
 
 def _assert_binned(E, mat, pm, lib, n_materials):
     """pm is a permutation of 0..n-1 grouped by material and, within a
-    material, ordered by log E up to one bucket: max(n / (materials x 192),
+    material, ordered by log E up to one bucket: max(n / (materials x 128),
     16,384) equal log-energy buckets per material over the library's energy
     range, at most 2^21 bins (energies outside it fall into the end
     buckets)."""
@@ -108,7 +108,7 @@ def _assert_binned(E, mat, pm, lib, n_materials):
     m = mat[pm].astype(np.int64)
     assert np.all(np.diff(m) >= 0)
     lo, hi = np.log(lib.energies.min()), np.log(lib.energies.max())
-    nb = max(1, min(max(n // (n_materials * 192), 16384), (1 << 21) // n_materials))
+    nb = max(1, min(max(n // (n_materials * 128), 16384), (1 << 21) // n_materials))
     width = (hi - lo) / nb
     x = np.clip(np.log(E[pm]), lo, hi)
     starts = np.flatnonzero(np.r_[True, np.diff(m) != 0])
@@ -119,11 +119,11 @@ def _assert_binned(E, mat, pm, lib, n_materials):
 
 @pytest.mark.parametrize("n", [1, 777, 1_000_003, 4_194_304, 50_000_017])
 def test_binning_orders_by_material_then_log_energy(torch_cuda, n):
-    """mcx_xs_sort over 12 materials: up to 37.7e6 lookups the floor of
-    16,384 buckets per material (196,608 bins); 5e7 lookups, 21,701 buckets
-    per material (260,412 bins).  Below 2^22 lookups the one-level counting
+    """mcx_xs_sort over 12 materials: up to 25.2e6 lookups the floor of
+    16,384 buckets per material (196,608 bins); 5e7 lookups, 32,552 buckets
+    per material (390,624 bins).  Below 2^22 lookups the one-level counting
     sort (counters scanned in 192 parts), from 2^22 the two-level one (384
-    coarse bins x 512 tiles of 8192 lookups at 2^22; 509 x 6104 at 5e7).  A
+    coarse bins x 512 tiles of 8192 lookups at 2^22; 763 x 6104 at 5e7).  A
     NaN energy takes the first bucket, energies outside the grid the end
     buckets.  (Counting in shared memory, at most 12,288 bins, is the
     static-scratch entry point's, tested with it.)"""
