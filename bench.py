@@ -361,9 +361,9 @@ EVENT_BYTES = {"lookup": 34, "flight": 118, "collision": 138}
 # What bounds each event kernel instead of HBM, from ncu in the bulk of the
 # timed run (profiles/transport_config3_kernels.md): the unit and its share of
 # its peak.
-EVENT_BOUND = {"lookup": {"unit": "L1TEX", "pct_of_peak": 74.6},
-               "flight": {"unit": "FP64 pipe", "pct_of_peak": 78.8},
-               "collision": {"unit": "FP64 pipe", "pct_of_peak": 66.7}}
+EVENT_BOUND = {"lookup": {"unit": "L1TEX (load latency: 10.9 long-scoreboard stalls per issue)", "pct_of_peak": 56.2},
+               "flight": {"unit": "FP64 pipe", "pct_of_peak": 81.3},
+               "collision": {"unit": "FP64 pipe", "pct_of_peak": 74.5}}
 
 
 def transport_roofline(mcx, synth, lib3, peak, seed=5):
