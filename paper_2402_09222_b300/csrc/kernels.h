@@ -117,12 +117,12 @@ int launch_lookup_sort(const SortParams& sp, int64_t n, const double* E, const i
                        uint32_t* bins, int32_t* perm, int grid, cudaStream_t st);
 
 // The same binning in two levels (coarse bins of 512 consecutive bins,
-// counted per tile of lookups in shared memory; then each coarse bin sorted
+// counted per tile of 16384 lookups in shared memory; then each coarse bin sorted
 // by its fine bins in shared memory): no global atomic per lookup.  Scratch:
 // place [lookup_sort2_place_words] uint32, keys [n] uint32, tidx [n] int32,
 // tfine [n] uint16.
-// Returns -2 when the batch's tiles x coarse bins exceed 2^28 or its coarse
-// bins 2048 (use launch_lookup_sort), -1 on a launch error.
+// Returns -2 when the batch's tiles x coarse bins exceed 2^28 (above 1e9
+// lookups; use launch_lookup_sort), -1 on a launch error.
 #ifndef MCX_BIN2_MIN_LOOKUPS
 #define MCX_BIN2_MIN_LOOKUPS (1 << 22)
 #endif

@@ -1012,17 +1012,21 @@ constexpr unsigned FULL = 0xffffffffu;
 // Two-level binning: lookups per tile of passes 0 and A, lookups per
 // sub-tile of pass B, fine bins per coarse bin (as bits), and the resident
 // blocks per SM passes A and B are compiled for.  Per 1e8 lookups (binning
-// time by CUDA events): tile 8192 / sub-tile 8192 / 2 / 2 blocks 2.11 ms,
-// 8192 / 4096 / 2 / 3 2.05 ms, 4096 / 8192 / 3 / 2 2.22 ms, 8192 / 8192 /
-// 2 / 3 2.13 ms; the one-level sort 2.63 ms on a like box.
+// time by CUDA events; 512-thread pass A unless noted): tile 8192 / sub-tile
+// 8192 / 2 / 2 blocks 2.11 ms, 8192 / 4096 / 2 / 3 2.05 ms, 4096 / 8192 /
+// 3 / 2 2.22 ms, 8192 / 8192 / 2 / 3 2.13 ms; at 128 lookups per bucket
+// 8192 / 4096 / 2 / 3 2.08 ms and 16384 / 4096 / 1 / 3 with a 1024-thread
+// pass A 2.02 ms (the setting: half the per-tile work per lookup, and a
+// tile scan that covers 4096 coarse bins, every bin count's); the one-level
+// sort 2.63 ms on a like box.
 #ifndef MCX_BIN2_TILE
-#define MCX_BIN2_TILE 8192
+#define MCX_BIN2_TILE 16384
 #endif
 #ifndef MCX_BIN2_SUB
 #define MCX_BIN2_SUB 4096
 #endif
 #ifndef MCX_BIN2_A_BLOCKS
-#define MCX_BIN2_A_BLOCKS 2
+#define MCX_BIN2_A_BLOCKS 1
 #endif
 #ifndef MCX_BIN2_B_BLOCKS
 #define MCX_BIN2_B_BLOCKS 3
@@ -1248,7 +1252,10 @@ __device__ __forceinline__ void smem_exclusive_scan(uint32_t* a, int m, uint32_t
     __syncthreads();
 }
 
-constexpr int kBin2Threads = 512;
+#ifndef MCX_BIN2_A_THREADS
+#define MCX_BIN2_A_THREADS 1024
+#endif
+constexpr int kBin2Threads = MCX_BIN2_A_THREADS;
 constexpr int kBin2PerThread = kBinTile / kBin2Threads;
 
 // Pass A, one tile at a time: the tile's lookups are ranked by coarse bin in

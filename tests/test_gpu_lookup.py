@@ -123,7 +123,7 @@ def test_binning_orders_by_material_then_log_energy(torch_cuda, n):
     16,384 buckets per material (196,608 bins); 5e7 lookups, 32,552 buckets
     per material (390,624 bins).  Below 2^22 lookups the one-level counting
     sort (counters scanned in 192 parts), from 2^22 the two-level one (384
-    coarse bins x 512 tiles of 8192 lookups at 2^22; 763 x 6104 at 5e7).  A
+    coarse bins x 256 tiles of 16384 lookups at 2^22; 763 x 3052 at 5e7).  A
     NaN energy takes the first bucket, energies outside the grid the end
     buckets.  (Counting in shared memory, at most 12,288 bins, is the
     static-scratch entry point's, tested with it.)"""
@@ -140,10 +140,10 @@ def test_binning_orders_by_material_then_log_energy(torch_cuda, n):
     p.close()
 
 
-def test_binning_with_too_many_coarse_bins_takes_the_one_level_sort(torch_cuda):
+def test_binning_with_many_coarse_bins(torch_cuda):
     """4.2e6 lookups over 120 materials: 16,384 buckets per material, 1.97e6
-    bins, 3,840 coarse bins of 512 -- more than the two-level binning's 2,048,
-    so the one-level counting sort bins the batch."""
+    bins, 3,840 coarse bins of 512 -- the two-level binning's tile scan then
+    covers nearly its 4,096."""
     torch = torch_cuda
     lib = synth.species_library(150, 200, 161)
     mats = synth.lookup_materials(150, 162, n_materials=120)
