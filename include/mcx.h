@@ -350,8 +350,13 @@ int mcx_xs_lookup(mcx_problem* p, int64_t n, const double* E, const int32_t* mat
  * over the library's energy range (fewer when materials x buckets would
  * exceed 2^21 bins; at least 1), so about 128 lookups per bucket in large
  * batches.  Order within a bucket is unspecified.  E and mat are
- * DEVICE pointers.  Uses a small library-owned bin array (allocated on first
- * use).  Errors: MCX_ERR_ARG, MCX_ERR_STATE, MCX_ERR_CUDA, MCX_ERR_OOM. */
+ * DEVICE pointers.  Batches of 2^22 lookups and more are binned in two
+ * levels (counts per tile and coarse bin in shared memory, then each coarse
+ * bin ranked by its fine bins in shared memory), smaller ones by a counting
+ * sort with global counters.  Uses library-owned scratch, allocated on first
+ * use and kept with the handle: the bin counters, and for two-level batches
+ * 10 bytes per lookup.  Errors: MCX_ERR_ARG, MCX_ERR_STATE, MCX_ERR_CUDA,
+ * MCX_ERR_OOM. */
 int mcx_xs_sort(mcx_problem* p, int64_t n, const double* E, const int32_t* mat, int32_t* perm,
                 void* stream);
 
