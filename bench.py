@@ -43,7 +43,10 @@ LIB_SEED, MAT_SEED, INPUT_SEED = 1236, 1236, 1336
 # FP32 tables, fast arithmetic, binned; hash bins from a sweep of the tuner's
 # range on this step (best of 5: 4000 bins 39.1 ms, 45600 35.6 ms, 68400
 # 33.3 ms, 100000 33.5 ms, 200000 34.3 ms)
-TUNED = dict(precision=1, hash_bins=68_400, flags=1)
+# flags: fast arithmetic with the round-linear sums (MCX_LOOKUP_FAST |
+# MCX_LOOKUP_LINEAR); PER_LOOKUP_FLAGS is the bit-identical per-lookup form
+TUNED = dict(precision=1, hash_bins=68_400, flags=17)
+PER_LOOKUP_FLAGS = 1
 PLAIN = dict(precision=0, hash_bins=0, flags=0)           # FP64 tables, exact, full binary search
 TRANSPORT_HIST = 10_000_000
 # chosen by paper_2402_09222_b300.tuner (random + coordinate descent, 40
@@ -643,7 +646,7 @@ def main():
     # the roof: HBM; achieved = DRAM bytes one launch moved (ncu, this kernel
     # source) over the launch's CUDA-event time
     achieved = traffic / (lk / 1e3) / 1e9 if traffic else comp / (lk / 1e3) / 1e9
-    roofline = {"bound": "hbm", "kernel": "k_xs_lookup_warp2 (binned order)",
+    roofline = {"bound": "hbm", "kernel": "k_xs_lookup_warp2, round-linear sums (binned order)",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic,
                 "frac_basis": ("DRAM bytes per launch (ncu dram__bytes_read + write, this kernel source) / "
@@ -681,6 +684,17 @@ def main():
     roofline["natural_order"] = {"kernel": "k_xs_lookup_fast (per-lane form)", "lookup_kernel_ms": nat_ms,
                                  "lookups_per_s": N_LOOKUPS / (nat_ms / 1e3),
                                  "work_rate_GBs": alg / (nat_ms / 1e3) / 1e9}
+    # the bit-identical per-lookup form on the same binned order (every
+    # species' term per lookup), beside the round-linear sums timed above
+    p.xs_lookup_ordered(dE, dm, perm, out=out, flags=PER_LOOKUP_FLAGS)
+    a.record(stream)
+    p.xs_lookup_ordered(dE, dm, perm, out=out, flags=PER_LOOKUP_FLAGS)
+    b.record(stream)
+    torch.cuda.synchronize()
+    pl_ms = a.elapsed_time(b)
+    roofline["per_lookup_form"] = {"kernel": "k_xs_lookup_warp2, per-lookup sums (bit-identical to the "
+                                             "per-lane form)", "lookup_kernel_ms": pl_ms,
+                                   "lookups_per_s": N_LOOKUPS / (pl_ms / 1e3)}
     if tr and tr.get("natural_dram_bytes_per_launch"):
         nd = tr["natural_dram_bytes_per_launch"]
         roofline["natural_order"].update(traffic=nd, achieved=nd / (nat_ms / 1e3) / 1e9,
@@ -783,8 +797,8 @@ def main():
         p64.close()
         ms32 = timed_exact(p, out_e)
 
-        def rel_err(o):
-            r = ((o - out64).abs() / out64.abs().clamp_min(1e-300))
+        def rel_err(o, ref=out64):
+            r = ((o - ref).abs() / ref.abs().clamp_min(1e-300))
             return {"max": [float(x) for x in r.max(0).values.cpu()],
                     "median": [float(x) for x in r.median(0).values.cpu()]}
 
@@ -793,6 +807,7 @@ def main():
             "channels": ["total", "scatter", "absorb", "fission", "nu-fission"],
             "lookup_fp32_tables_exact": rel_err(out_e),
             "lookup_fp32_tables_fast_binned": rel_err(out),
+            "fast_binned_vs_exact_on_fp32_tables": rel_err(out, out_e),
             "bound": "2^-24 = 5.96e-8 (exact) and 1e-6 + 2^-24 (fast), relative"}
         line["fp64_vs_fp32_tables"] = {
             "form": "exact arithmetic, 68,400 hash bins, binned order (the same permutation)",

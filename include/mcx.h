@@ -75,6 +75,16 @@ extern "C" {
 #define MCX_LOOKUP_OUT32 8  /* with FAST: out holds FP32 values (the compensated
                                sum rounded once; still within 1e-6 relative),
                                half the output bytes */
+#define MCX_LOOKUP_LINEAR 16 /* with FAST and a binned order: per 64-lookup
+                               round, the species whose grid interval holds
+                               every lookup of the round (or whose grid has one
+                               point inside the round's energy range) are summed
+                               once per round as one linear function of E (plus
+                               a hinge at that point), the rest per lookup.
+                               Within the same 1e-6 relative bound as FAST, but
+                               not bit-identical to it, and the last bits depend
+                               on which lookups share a round.  Ignored with
+                               STAGED. */
 
 /* Problem flags. */
 #define MCX_FLAG_DERIVATIVES 1   /* likelihood-ratio density-derivative tallies */

@@ -13,11 +13,15 @@ int launch_xs_lookup_exact(const Tables& t, int64_t n, const double* E, const in
                            const int32_t* perm, double* out, int grid, cudaStream_t st);
 // resident 256-thread blocks per SM of the fast lookup (its register cap)
 constexpr int kFastBlocksPerSm = 4;
+// the same for the round-linear form (MCX_LOOKUP_LINEAR)
+constexpr int kLinBlocksPerSm = 3;
 // work: a device counter for in-order chunked scheduling of binned orders
-// (zeroed by the launch), or nullptr for a grid-stride loop.
+// (zeroed by the launch), or nullptr for a grid-stride loop.  linear: on a
+// binned order with a work counter, the round-linear sums (within the fast
+// bound, not bit-identical to the per-lookup sums).
 int launch_xs_lookup_fast(const Tables& t, int64_t n, const double* E, const int32_t* mat,
                           const int32_t* perm, void* out, bool out32, int grid, cudaStream_t st,
-                          unsigned long long* work = nullptr);
+                          unsigned long long* work = nullptr, bool linear = false);
 struct SortParams {
     int32_t n_materials = 1;
     int32_t n_ebuckets = 1;

@@ -881,9 +881,11 @@ int lookup_device_ordered(mcx_problem* p, int64_t n, const double* E, const int3
                                     p->sm_count, st, work,
                                     reinterpret_cast<unsigned int*>(p->work_ctr + kWorkCtrs));
     if (r == -2) {
-        const int grid = work ? p->sm_count * kFastBlocksPerSm : lookup_grid(p);
+        const int grid =
+            work ? p->sm_count * ((flags & MCX_LOOKUP_LINEAR) ? kLinBlocksPerSm : kFastBlocksPerSm) : lookup_grid(p);
         r = (flags & MCX_LOOKUP_FAST)
-                ? launch_xs_lookup_fast(ts->view, n, E, mat, perm, out, out32, grid, st, work)
+                ? launch_xs_lookup_fast(ts->view, n, E, mat, perm, out, out32, grid, st, work,
+                                        (flags & MCX_LOOKUP_LINEAR) != 0)
                 : launch_xs_lookup_exact(ts->view, n, E, mat, perm, static_cast<double*>(out), lookup_grid(p), st);
     }
     if (r) return fail(MCX_ERR_CUDA, "lookup launch failed: %s", cudaGetErrorString(cudaGetLastError()));
@@ -901,7 +903,7 @@ int lookup_device(mcx_problem* p, int64_t n, const double* E, const int32_t* mat
         perm = p->perm;
     }
     return lookup_device_ordered(p, n, E, mat, perm, out,
-                                 flags & (MCX_LOOKUP_FAST | MCX_LOOKUP_STAGED | MCX_LOOKUP_OUT32), st);
+                                 flags & (MCX_LOOKUP_FAST | MCX_LOOKUP_STAGED | MCX_LOOKUP_OUT32 | MCX_LOOKUP_LINEAR), st);
 }
 
 // Eigenvalue scratch: per-history arrays for N histories and a staging and
@@ -1529,10 +1531,10 @@ int mcx_xs_lookup(mcx_problem* p, int64_t n, const double* E, const int32_t* mat
     TRY(check_tables(p));
     if (n < 0) return fail(MCX_ERR_ARG, "n must be >= 0");
     if (n >= ((int64_t)1 << 31)) return fail(MCX_ERR_ARG, "n must be < 2^31");
-    if (flags & ~(MCX_LOOKUP_FAST | MCX_LOOKUP_SORT | MCX_LOOKUP_STAGED | MCX_LOOKUP_OUT32))
+    if (flags & ~(MCX_LOOKUP_FAST | MCX_LOOKUP_SORT | MCX_LOOKUP_STAGED | MCX_LOOKUP_OUT32 | MCX_LOOKUP_LINEAR))
         return fail(MCX_ERR_ARG, "unknown lookup flags");
-    if ((flags & MCX_LOOKUP_OUT32) && !(flags & MCX_LOOKUP_FAST))
-        return fail(MCX_ERR_ARG, "MCX_LOOKUP_OUT32 needs MCX_LOOKUP_FAST");
+    if ((flags & (MCX_LOOKUP_OUT32 | MCX_LOOKUP_LINEAR)) && !(flags & MCX_LOOKUP_FAST))
+        return fail(MCX_ERR_ARG, "MCX_LOOKUP_OUT32 and MCX_LOOKUP_LINEAR need MCX_LOOKUP_FAST");
     if (n == 0) return MCX_OK;
     if (!E || !mat || !out) return fail(MCX_ERR_ARG, "NULL buffer");
     DeviceGuard dg(p->device);
@@ -1557,10 +1559,11 @@ int mcx_xs_lookup_ordered(mcx_problem* p, int64_t n, const double* E, const int3
     g_err.clear();
     TRY(check_tables(p));
     if (n < 0 || n >= ((int64_t)1 << 31)) return fail(MCX_ERR_ARG, "n out of range");
-    if (flags & ~(MCX_LOOKUP_FAST | MCX_LOOKUP_STAGED | MCX_LOOKUP_OUT32))
-        return fail(MCX_ERR_ARG, "flags may hold MCX_LOOKUP_FAST, MCX_LOOKUP_STAGED and MCX_LOOKUP_OUT32 only");
-    if ((flags & MCX_LOOKUP_OUT32) && !(flags & MCX_LOOKUP_FAST))
-        return fail(MCX_ERR_ARG, "MCX_LOOKUP_OUT32 needs MCX_LOOKUP_FAST");
+    if (flags & ~(MCX_LOOKUP_FAST | MCX_LOOKUP_STAGED | MCX_LOOKUP_OUT32 | MCX_LOOKUP_LINEAR))
+        return fail(MCX_ERR_ARG,
+                    "flags may hold MCX_LOOKUP_FAST, MCX_LOOKUP_STAGED, MCX_LOOKUP_OUT32 and MCX_LOOKUP_LINEAR only");
+    if ((flags & (MCX_LOOKUP_OUT32 | MCX_LOOKUP_LINEAR)) && !(flags & MCX_LOOKUP_FAST))
+        return fail(MCX_ERR_ARG, "MCX_LOOKUP_OUT32 and MCX_LOOKUP_LINEAR need MCX_LOOKUP_FAST");
     if (n == 0) return MCX_OK;
     if (!E || !mat || !out) return fail(MCX_ERR_ARG, "NULL buffer");
     DeviceGuard dg(p->device);
@@ -1573,10 +1576,10 @@ int mcx_xs_lookup_host(mcx_problem* p, int64_t n, const double* E_host, const in
     g_err.clear();
     TRY(check_tables(p));
     if (n < 0 || n >= ((int64_t)1 << 31)) return fail(MCX_ERR_ARG, "n out of range");
-    if (flags & ~(MCX_LOOKUP_FAST | MCX_LOOKUP_SORT | MCX_LOOKUP_STAGED | MCX_LOOKUP_OUT32))
+    if (flags & ~(MCX_LOOKUP_FAST | MCX_LOOKUP_SORT | MCX_LOOKUP_STAGED | MCX_LOOKUP_OUT32 | MCX_LOOKUP_LINEAR))
         return fail(MCX_ERR_ARG, "unknown lookup flags");
-    if ((flags & MCX_LOOKUP_OUT32) && !(flags & MCX_LOOKUP_FAST))
-        return fail(MCX_ERR_ARG, "MCX_LOOKUP_OUT32 needs MCX_LOOKUP_FAST");
+    if ((flags & (MCX_LOOKUP_OUT32 | MCX_LOOKUP_LINEAR)) && !(flags & MCX_LOOKUP_FAST))
+        return fail(MCX_ERR_ARG, "MCX_LOOKUP_OUT32 and MCX_LOOKUP_LINEAR need MCX_LOOKUP_FAST");
     if (n == 0) return MCX_OK;
     if (!E_host || !mat_host || !out_host) return fail(MCX_ERR_ARG, "NULL buffer");
     const size_t es = (flags & MCX_LOOKUP_OUT32) ? sizeof(float) : sizeof(double);
@@ -1619,7 +1622,7 @@ int mcx_xs_lookup_host(mcx_problem* p, int64_t n, const double* E_host, const in
             perm = dP;
         }
         TRY(lookup_device_ordered(p, m, dE, dM, perm, dO,
-                                  flags & (MCX_LOOKUP_FAST | MCX_LOOKUP_STAGED | MCX_LOOKUP_OUT32), st, slot));
+                                  flags & (MCX_LOOKUP_FAST | MCX_LOOKUP_STAGED | MCX_LOOKUP_OUT32 | MCX_LOOKUP_LINEAR), st, slot));
         CUDA_TRY(cudaMemcpyAsync(static_cast<char*>(out_host) + (size_t)off * nc * es, dO, es * m * nc,
                                  cudaMemcpyDeviceToHost, st));
     }

@@ -89,6 +89,22 @@ constexpr int kSmemBins = 12288;   // histograms up to this size count in shared
 #ifndef MCX_FAST2_MIN_BLOCKS
 #define MCX_FAST2_MIN_BLOCKS 4
 #endif
+// The round-linear form has less work per species and more state per round:
+// with 3 blocks per SM (80 registers, no spills) per 1e8 binned lookups
+// 16.23 ms against 17.12 at 4 blocks (5 blocks: 18.11).
+#ifndef MCX_LIN_MIN_BLOCKS
+#define MCX_LIN_MIN_BLOCKS 3
+#endif
+static_assert(MCX_LIN_MIN_BLOCKS == kLinBlocksPerSm && MCX_FAST2_MIN_BLOCKS == kFastBlocksPerSm,
+              "the launch grid sizes match the kernels' register caps");
+// Each warp's 64 output rows of a round leave through shared memory: lane k
+// of a store instruction writes value k of the round's rows laid end to end,
+// so a row's values go out in one or two instructions whose lanes share its
+// sectors, instead of one 8-byte store per value to 32 scattered rows (per
+// 1e8 binned lookups the stores alone cost 7.3 ms that way).
+#ifndef MCX_FAST_ROWSTAGE
+#define MCX_FAST_ROWSTAGE 1
+#endif
 // Lookups a warp claims at a time in binned order: one 64-lookup round of the
 // warp-cooperative form (24.9 ms per 1e8 against 25.2 for 128 and 25.5 for 256).
 #ifndef MCX_FAST_CHUNK
@@ -196,6 +212,12 @@ __device__ __forceinline__ void store_stream(V* p, V v)
 // hi + lo (exact), or that value rounded once to FP32.
 __device__ __forceinline__ void store_out(double* p, float hi, float lo) { store_stream(p, (double)hi + (double)lo); }
 __device__ __forceinline__ void store_out(float* p, float hi, float lo) { store_stream(p, hi + lo); }
+template <typename OutT>
+__device__ __forceinline__ OutT out_value(float hi, float lo);
+template <>
+__device__ __forceinline__ double out_value<double>(float hi, float lo) { return (double)hi + (double)lo; }
+template <>
+__device__ __forceinline__ float out_value<float>(float hi, float lo) { return hi + lo; }
 __device__ __forceinline__ void store_nan(double* p) { store_stream(p, __longlong_as_double(0x7ff8000000000000LL)); }
 __device__ __forceinline__ void store_nan(float* p) { store_stream(p, __int_as_float(0x7fc00000)); }
 
@@ -315,6 +337,129 @@ __device__ __forceinline__ void species_term_half(const float (&r0)[4 * W], cons
     for (int r = 0; r < NC; ++r) {
         float& v = SECOND ? part[r].y : part[r].x;
         v = fmaf(w1, r1[2 + r], fmaf(w0, r0[2 + r], v));
+    }
+}
+
+// ------------------------------------------------------------------------
+// Round-linear sums (MCX_LOOKUP_LINEAR on a binned order).
+//
+// Inside one grid interval [g_k, g_k+1] a species' term
+// N (s_k + (E - g_k) / (g_k+1 - g_k) (s_k+1 - s_k)) is linear in E, and the
+// interpolant is continuous at every grid point.  A binned round's 64
+// lookups lie in one material and a narrow range [E_min, E_max].  When that
+// range holds no point of a species (strictly inside one interval) the
+// species adds a + b x to the lookup at E, x = E - E_min, where a is its term
+// at E_min and b its slope; when the range holds exactly one point g of the
+// species it adds a + b x + db max(0, x - (g - E_min)), db the change of
+// slope at g.  The a and b of such species are summed once per round (lanes
+// over species) instead of once per lookup; each lookup then takes one
+// multiply-add per channel, plus one per hinge (db) in its range.
+//
+// A species keeps the per-lookup form when the range holds two or more of
+// its points, reaches outside its grid (the clamps are not linear), or when
+// any channel's slope times the range width exceeds 1/kLinSlopeBound of its
+// term at E_min: there a + b x could cancel.  Under that bound every term
+// and partial sum stays within a small factor of the species' term, so the
+// FP32 roundings cost a few ulps of the term, as in the per-lookup form;
+// the totals are compensated sums as there.  The outputs differ from the
+// per-lookup form's by rounding only, and they depend on which lookups share
+// a round (the binned order within a bucket is not fixed).
+constexpr float kLinSlopeBound = 16.f;
+// rounds of materials with fewer species take the per-lookup form for all
+// of them: the per-round reduction would cost more than it saves
+#ifndef MCX_LIN_MIN_SPECIES
+#define MCX_LIN_MIN_SPECIES 8
+#endif
+
+// 1 / (g_k+1 - g_k) in FP32 from the bracketing records: stored in the
+// record's last slot by the two-float4 layout, computed from the energy
+// pairs otherwise.
+template <int W>
+__device__ __forceinline__ float interval_rinv(const float (&r0)[4 * W], const float (&r1)[4 * W])
+{
+    if constexpr (W == 2 && MCX_FAST_RINV)
+        return r0[7];
+    else
+        return __frcp_rn((r1[0] - r0[0]) + (r1[1] - r0[1]));
+}
+
+template <int W>
+__device__ __forceinline__ void load_record(const float4* __restrict__ rec, int32_t p, float (&r)[4 * W])
+{
+#if MCX_FAST_LD256
+    if constexpr (W == 2) {
+        ld256(rec + (int64_t)p * 2, r);
+        return;
+    }
+#endif
+    const float4* q = rec + (int64_t)p * W;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        const float4 a = __ldg(q + w);
+        r[4 * w] = a.x; r[4 * w + 1] = a.y; r[4 * w + 2] = a.z; r[4 * w + 3] = a.w;
+    }
+}
+
+// The linear pieces of one species for a round starting at E_ref (FP32 pair
+// Erh + Erl) and spanning span16 / kLinSlopeBound: the term a at E_ref, the
+// slope b of interval kb and, with d = 1, the change of slope db at point
+// kb + 1.  False when a slope breaks the cancellation bound.
+template <int W, int NC>
+__device__ __forceinline__ bool species_linear(const float4* __restrict__ rec, int32_t kb, int32_t d, float N,
+                                               float Erh, float Erl, float span16, float (&a)[NC],
+                                               float (&b)[NC], float (&db)[NC])
+{
+    float r0[4 * W], r1[4 * W];
+    load_records<W>(rec, kb, r0, r1);
+    float w0, w1;
+    species_weights<W>(r0, r1, Erh, Erl, N, w0, w1);
+    const float nr0 = N * interval_rinv<W>(r0, r1);
+    bool ok = true;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        a[c] = fmaf(w1, r1[2 + c], w0 * r0[2 + c]);
+        b[c] = nr0 * (r1[2 + c] - r0[2 + c]);
+        ok = ok && fabsf(b[c]) * span16 <= a[c];
+        db[c] = 0.f;
+    }
+    if (d == 1) {
+        float r2[4 * W];
+        load_record<W>(rec, kb + 2, r2);
+        const float nr1 = N * interval_rinv<W>(r1, r2);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const float b1 = nr1 * (r2[2 + c] - r1[2 + c]);
+            ok = ok && fabsf(b1) * span16 <= a[c];
+            db[c] = b1 - b[c];
+        }
+    }
+    return ok;
+}
+
+// One species of a lookup pair in the per-lookup form: records of interval b
+// shared by both lookups, or (d > 0: the round's range holds d grid points)
+// each lookup's own interval found among b .. b + d with its search key
+// (read from *peb0, *peb1 only then); the terms go to pp.
+template <int W, int NC>
+__device__ __forceinline__ void species_pair(const Tables& t, int32_t b, int32_t d, float N,
+                                             const volatile int64_t* peb0, const volatile int64_t* peb1, float Eh0,
+                                             float El0, float Eh1, float El1, float2 (&pp)[NC])
+{
+    float r0[4 * W], r1[4 * W];
+    if (d > 0) {
+        const int64_t eb0 = *peb0, eb1 = *peb1;   // the lookups' search keys
+        int32_t bb = b, len = d + 1;
+        while (len > 1) search_step(t.E, bb, len, eb0);
+        load_records<W>(t.frec, bb, r0, r1);
+        species_term_half<W, NC, false>(r0, r1, Eh0, El0, N, pp);
+        bb = b;
+        len = d + 1;
+        while (len > 1) search_step(t.E, bb, len, eb1);
+        load_records<W>(t.frec, bb, r0, r1);
+        species_term_half<W, NC, true>(r0, r1, Eh1, El1, N, pp);
+    } else {
+        load_records<W>(t.frec, b, r0, r1);
+        species_term_pair<W, NC>(r0, r1, Eh0, El0, Eh1, El1, N, pp);
     }
 }
 
@@ -458,14 +603,15 @@ __global__ void __launch_bounds__(256, MCX_FAST_MIN_BLOCKS) k_xs_lookup_fast(Tab
 // each lane's search keys and output rows parked in shared memory, so that
 // the species loop spills half as much, 22.47 -> 22.27 ms on one box (with
 // 3 blocks per SM and no spills at all, 23.58 ms against 22.24).
-template <int W, int U, int NC, typename OutT>
-__global__ void __launch_bounds__(256, MCX_FAST2_MIN_BLOCKS) k_xs_lookup_warp2(Tables t, int64_t n, const double* __restrict__ Ein,
+template <int W, int U, int NC, typename OutT, bool LIN>
+__global__ void __launch_bounds__(256, LIN ? MCX_LIN_MIN_BLOCKS : MCX_FAST2_MIN_BLOCKS) k_xs_lookup_warp2(Tables t, int64_t n, const double* __restrict__ Ein,
                                                          const int32_t* __restrict__ mat,
                                                          const int32_t* __restrict__ perm,
                                                          OutT* __restrict__ out,
                                                          unsigned long long* __restrict__ work)
 {
     static_assert(32 % U == 0, "species groups of U must tile the 32-species blocks");
+    static_assert(!LIN || MCX_FAST_PARK, "the round-linear form keeps its per-lane sums in shared memory");
     const unsigned FULLM = 0xffffffffu;
     const int lane = threadIdx.x & 31;
 #if MCX_FAST_PARK
@@ -478,6 +624,13 @@ __global__ void __launch_bounds__(256, MCX_FAST2_MIN_BLOCKS) k_xs_lookup_warp2(T
     volatile int64_t* park_eb1 = &s_park_eb[threadIdx.x >> 5][1][lane];
     volatile int32_t* park_l0 = &s_park_l[threadIdx.x >> 5][0][lane];
     volatile int32_t* park_l1 = &s_park_l[threadIdx.x >> 5][1][lane];
+    // round-linear form: each lane's sums over its linear species, the terms
+    // a as a compensated pair (slots c and NC + c), the slopes b (2 NC + c)
+    __shared__ float s_lin[256 / 32][LIN ? 3 * NC : 1][32];
+    volatile float* lin_acc = &s_lin[threadIdx.x >> 5][0][lane];
+#if MCX_FAST_ROWSTAGE
+    __shared__ OutT s_rows[256 / 32][64 * NC];   // a round's output rows, end to end
+#endif
 #endif
     for (;;) {
         unsigned long long cbase = 0ull;
@@ -546,6 +699,23 @@ __global__ void __launch_bounds__(256, MCX_FAST2_MIN_BLOCKS) k_xs_lookup_warp2(T
             const float Eh0 = (float)E0, El0 = (float)(E0 - (double)Eh0);
             const float Eh1 = (float)E1, El1 = (float)(E1 - (double)Eh1);
             const int32_t i0 = __ldg(t.moff + mw), i1 = __ldg(t.moff + mw + 1);
+            // round-linear form: x = E - E_min per lookup, E_min as an FP32
+            // pair, kLinSlopeBound times the round's energy range
+            bool lin_round = false, any_lin = false;
+            float2 x01 = make_float2(0.f, 0.f);
+            float Erh = 0.f, Erl = 0.f, span16 = 0.f;
+            if constexpr (LIN) {
+                lin_round = i1 - i0 >= MCX_LIN_MIN_SPECIES;
+                if (lin_round) {
+                    const double Eref = __longlong_as_double(eb_lo);
+                    x01 = make_float2((float)(E0 - Eref), (float)(E1 - Eref));
+                    Erh = (float)Eref;
+                    Erl = (float)(Eref - (double)Erh);
+                    span16 = kLinSlopeBound * (float)(__longlong_as_double(eb_hi) - Eref);
+#pragma unroll
+                    for (int q = 0; q < 3 * NC; ++q) lin_acc[32 * q] = 0.f;
+                }
+            }
             for (int32_t g0 = i0; g0 < i1; g0 += 32) {
                 int32_t kb = 0, kd = 0;
                 float Nq = 0.f;
@@ -569,6 +739,75 @@ __global__ void __launch_bounds__(256, MCX_FAST2_MIN_BLOCKS) k_xs_lookup_warp2(T
                         for (int st = 0; st < t.search_steps; ++st)
                             if (ln1 > 1) search_step(t.E, b1, ln1, eb_hi);
                         kd = b1 - kb;
+                    }
+                }
+                bool linq = false;   // this lane's species is summed in linear form
+                if constexpr (LIN) {
+                    if (lin_round) {
+                        float a[NC], b[NC], db[NC];
+                        float xbp = 0.f;
+                        bool hinge = false;
+                        // one interval or one interior point in [E_min, E_max], inside the grid
+                        if (g0 + lane < i1 && kd <= 1 && ebits(__ldg(t.E + kb)) <= eb_lo &&
+                            eb_hi <= ebits(__ldg(t.E + kb + kd + 1))) {
+                            linq = species_linear<W, NC>(t.frec, kb, kd, Nq, Erh, Erl, span16, a, b, db);
+                            if (linq) {
+#pragma unroll
+                                for (int c = 0; c < NC; ++c) {
+                                    float h = lin_acc[32 * c], l = lin_acc[32 * (NC + c)];
+                                    two_sum_acc(h, l, a[c]);
+                                    lin_acc[32 * c] = h;
+                                    lin_acc[32 * (NC + c)] = l;
+                                    lin_acc[32 * (2 * NC + c)] = lin_acc[32 * (2 * NC + c)] + b[c];
+                                }
+                                hinge = kd == 1;
+                                if (hinge) xbp = (float)(__ldg(t.E + kb + 1) - __longlong_as_double(eb_lo));
+                            }
+                        }
+                        any_lin = any_lin || __any_sync(FULLM, linq);
+                        // each hinge's db max(0, x - x_g) for both lookups of every lane
+                        unsigned hm = __ballot_sync(FULLM, hinge);
+                        if (hm) {
+                            float2 ph[NC];
+#pragma unroll
+                            for (int c = 0; c < NC; ++c) ph[c] = make_float2(0.f, 0.f);
+                            while (hm) {
+                                const int src = __ffs(hm) - 1;
+                                hm &= hm - 1;
+                                const float xb = __shfl_sync(FULLM, xbp, src);
+                                const float2 h = make_float2(fmaxf(x01.x - xb, 0.f), fmaxf(x01.y - xb, 0.f));
+#pragma unroll
+                                for (int c = 0; c < NC; ++c) {
+                                    const float dc = __shfl_sync(FULLM, db[c], src);
+                                    ph[c] = __ffma2_rn(make_float2(dc, dc), h, ph[c]);
+                                }
+                            }
+#pragma unroll
+                            for (int c = 0; c < NC; ++c) two_sum_acc2(hi[c], lo[c], ph[c]);
+                        }
+                        // the other species per lookup, U at a time
+                        unsigned fm = __ballot_sync(FULLM, g0 + lane < i1 && !linq);
+                        int32_t prev = 0;
+                        while (fm) {
+                            float2 pp[NC];
+#pragma unroll
+                            for (int c = 0; c < NC; ++c) pp[c] = make_float2(0.f, 0.f);
+#pragma unroll
+                            for (int u = 0; u < U; ++u) {
+                                const bool v = fm != 0u;
+                                const int32_t src = v ? __ffs(fm) - 1 : prev;
+                                prev = src;
+                                fm &= fm - 1u;
+                                const int32_t b = __shfl_sync(FULLM, kb, src);
+                                const int32_t d = __shfl_sync(FULLM, kd, src);
+                                const float Nu = __shfl_sync(FULLM, Nq, src);
+                                species_pair<W, NC>(t, b, d, v ? Nu : 0.f, park_eb0, park_eb1, Eh0, El0, Eh1, El1,
+                                                    pp);
+                            }
+#pragma unroll
+                            for (int c = 0; c < NC; ++c) two_sum_acc2(hi[c], lo[c], pp[c]);
+                        }
+                        continue;
                     }
                 }
                 const int32_t gend = i1 < g0 + 32 ? i1 : g0 + 32;
@@ -607,6 +846,59 @@ __global__ void __launch_bounds__(256, MCX_FAST2_MIN_BLOCKS) k_xs_lookup_warp2(T
                     for (int c = 0; c < NC; ++c) two_sum_acc2(hi[c], lo[c], pp[c]);
                 }
             }
+            if constexpr (LIN) {
+                if (any_lin) {
+                    // the round's sums over every lane's linear species (the
+                    // butterfly leaves the same totals in every lane: each
+                    // merge is commutative and the two-sum error is exact)
+                    float Ah[NC], Al[NC], Bs[NC];
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) {
+                        Ah[c] = lin_acc[32 * c];
+                        Al[c] = lin_acc[32 * (NC + c)];
+                        Bs[c] = lin_acc[32 * (2 * NC + c)];
+                    }
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+                        for (int c = 0; c < NC; ++c) {
+                            const float h2 = __shfl_xor_sync(FULLM, Ah[c], o);
+                            const float l2 = __shfl_xor_sync(FULLM, Al[c], o);
+                            const float b2 = __shfl_xor_sync(FULLM, Bs[c], o);
+                            const float s2 = Ah[c] + h2;
+                            const float bp = s2 - Ah[c];
+                            const float e2 = (Ah[c] - (s2 - bp)) + (h2 - bp);
+                            Ah[c] = s2;
+                            Al[c] = (Al[c] + l2) + e2;
+                            Bs[c] = Bs[c] + b2;
+                        }
+                    }
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) {
+                        two_sum_acc2(hi[c], lo[c], make_float2(Ah[c], Ah[c]));
+                        lo[c] = __fadd2_rn(lo[c], make_float2(Al[c], Al[c]));
+                        two_sum_acc2(hi[c], lo[c], __fmul2_rn(x01, make_float2(Bs[c], Bs[c])));
+                    }
+                }
+            }
+#if MCX_FAST_PARK && MCX_FAST_ROWSTAGE
+            {
+                OutT* rows = s_rows[threadIdx.x >> 5];
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    rows[lane * NC + c] = out_value<OutT>(hi[c].x, lo[c].x);
+                    rows[(32 + lane) * NC + c] = out_value<OutT>(hi[c].y, lo[c].y);
+                }
+                __syncwarp();
+#pragma unroll
+                for (int q = lane; q < 64 * NC; q += 32) {
+                    const int row = q / NC;
+                    const int64_t l = s_park_l[threadIdx.x >> 5][row >> 5][row & 31];
+                    store_stream(out + l * NC + (q - row * NC), rows[q]);
+                }
+                __syncwarp();
+            }
+#else
 #if MCX_FAST_PARK
             const int64_t r0 = *park_l0, r1 = *park_l1;
 #else
@@ -617,6 +909,7 @@ __global__ void __launch_bounds__(256, MCX_FAST2_MIN_BLOCKS) k_xs_lookup_warp2(T
                 store_out(out + r0 * NC + c, hi[c].x, lo[c].x);
                 store_out(out + r1 * NC + c, hi[c].y, lo[c].y);
             }
+#endif
         }
     }
 }
@@ -1390,23 +1683,30 @@ __global__ void __launch_bounds__(kBin2FineThreads, MCX_BIN2_B_BLOCKS) k_bin2_fi
 
 }  // namespace
 
+template <bool LIN, typename OutT>
+static int launch_warp2_t(const Tables& t, int64_t n, const double* E, const int32_t* mat, const int32_t* perm,
+                          OutT* out, int grid, cudaStream_t st, unsigned long long* work)
+{
+    switch (t.n_ch) {
+    case 1: k_xs_lookup_warp2<1, kFastUnroll, 1, OutT, LIN><<<grid, 256, 0, st>>>(t, n, E, mat, perm, out, work); break;
+    case 2: k_xs_lookup_warp2<1, kFastUnroll, 2, OutT, LIN><<<grid, 256, 0, st>>>(t, n, E, mat, perm, out, work); break;
+    case 3: k_xs_lookup_warp2<2, kFastUnroll, 3, OutT, LIN><<<grid, 256, 0, st>>>(t, n, E, mat, perm, out, work); break;
+    case 4: k_xs_lookup_warp2<2, kFastUnroll, 4, OutT, LIN><<<grid, 256, 0, st>>>(t, n, E, mat, perm, out, work); break;
+    case 5: k_xs_lookup_warp2<2, kFastUnroll, 5, OutT, LIN><<<grid, 256, 0, st>>>(t, n, E, mat, perm, out, work); break;
+    default: return -1;
+    }
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
 template <typename OutT>
 static int launch_fast_t(const Tables& t, int64_t n, const double* E, const int32_t* mat, const int32_t* perm,
-                         OutT* out, int grid, cudaStream_t st, unsigned long long* work)
+                         OutT* out, int grid, cudaStream_t st, unsigned long long* work, bool linear)
 {
     // one instantiation per channel count: no work on unused record slots
 #if MCX_FAST_WARP
-    if (perm && work) {
-        switch (t.n_ch) {
-        case 1: k_xs_lookup_warp2<1, kFastUnroll, 1, OutT><<<grid, 256, 0, st>>>(t, n, E, mat, perm, out, work); break;
-        case 2: k_xs_lookup_warp2<1, kFastUnroll, 2, OutT><<<grid, 256, 0, st>>>(t, n, E, mat, perm, out, work); break;
-        case 3: k_xs_lookup_warp2<2, kFastUnroll, 3, OutT><<<grid, 256, 0, st>>>(t, n, E, mat, perm, out, work); break;
-        case 4: k_xs_lookup_warp2<2, kFastUnroll, 4, OutT><<<grid, 256, 0, st>>>(t, n, E, mat, perm, out, work); break;
-        case 5: k_xs_lookup_warp2<2, kFastUnroll, 5, OutT><<<grid, 256, 0, st>>>(t, n, E, mat, perm, out, work); break;
-        default: return -1;
-        }
-        return cudaGetLastError() == cudaSuccess ? 0 : -1;
-    }
+    if (perm && work)
+        return linear ? launch_warp2_t<true>(t, n, E, mat, perm, out, grid, st, work)
+                      : launch_warp2_t<false>(t, n, E, mat, perm, out, grid, st, work);
 #endif
     switch (t.n_ch) {
     case 1: k_xs_lookup_fast<1, kFastUnroll, 1, OutT><<<grid, 256, 0, st>>>(t, n, E, mat, perm, out, work); break;
@@ -1421,11 +1721,11 @@ static int launch_fast_t(const Tables& t, int64_t n, const double* E, const int3
 
 int launch_xs_lookup_fast(const Tables& t, int64_t n, const double* E, const int32_t* mat,
                           const int32_t* perm, void* out, bool out32, int grid, cudaStream_t st,
-                          unsigned long long* work)
+                          unsigned long long* work, bool linear)
 {
     if (work && cudaMemsetAsync(work, 0, sizeof(unsigned long long), st) != cudaSuccess) return -1;
-    return out32 ? launch_fast_t(t, n, E, mat, perm, static_cast<float*>(out), grid, st, work)
-                 : launch_fast_t(t, n, E, mat, perm, static_cast<double*>(out), grid, st, work);
+    return out32 ? launch_fast_t(t, n, E, mat, perm, static_cast<float*>(out), grid, st, work, linear)
+                 : launch_fast_t(t, n, E, mat, perm, static_cast<double*>(out), grid, st, work, linear);
 }
 
 template <int W, int NC, typename OutT>

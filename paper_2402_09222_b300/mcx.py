@@ -28,7 +28,7 @@ ERR_NAMES = {-1: "MCX_ERR_ARG", -2: "MCX_ERR_CUDA", -3: "MCX_ERR_OOM", -4: "MCX_
 ERR_ITER_LIMIT, ERR_TIMEOUT = -4, -7
 FP64, FP32 = 0, 1
 QUEUELESS, QUEUED, QUEUED_FULLEST = 0, 1, 2
-LOOKUP_EXACT, LOOKUP_FAST, LOOKUP_SORT, LOOKUP_STAGED, LOOKUP_OUT32 = 0, 1, 2, 4, 8
+LOOKUP_EXACT, LOOKUP_FAST, LOOKUP_SORT, LOOKUP_STAGED, LOOKUP_OUT32, LOOKUP_LINEAR = 0, 1, 2, 4, 8, 16
 FLAG_DERIVATIVES, FLAG_HISTORY_DEBUG = 1, 2
 TALLY_FLUX, TALLY_ABSORB, TALLY_OUTCOME, TALLY_DFLUX, TALLY_DABSORB, TALLY_DOUTCOME = range(6)
 GEOM_NONE = 3
