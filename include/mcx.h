@@ -85,6 +85,8 @@ extern "C" {
                                not bit-identical to it, and the last bits depend
                                on which lookups share a round.  Ignored with
                                STAGED. */
+#define MCX_LOOKUP_BINNED_INPUTS 32 /* mcx_xs_lookup_ordered only: E and mat
+                               are already in the processing order (see there) */
 
 /* Problem flags. */
 #define MCX_FLAG_DERIVATIVES 1   /* likelihood-ratio density-derivative tallies */
@@ -370,12 +372,28 @@ int mcx_xs_lookup(mcx_problem* p, int64_t n, const double* E, const int32_t* mat
 int mcx_xs_sort(mcx_problem* p, int64_t n, const double* E, const int32_t* mat, int32_t* perm,
                 void* stream);
 
+/* mcx_xs_sort that also hands over the inputs in the binned order:
+ * E_binned[j] = E[perm[j]] and mat_binned[j] = mat[perm[j]] (FP64 [n] and
+ * int32 [n], DEVICE, caller-owned, not aliasing E or mat), for
+ * mcx_xs_lookup_ordered with MCX_LOOKUP_BINNED_INPUTS, which then reads them
+ * in sequence instead of through the permutation.  Two-level batches carry
+ * each energy and material with its index through both binning passes
+ * (12 more bytes per lookup of library-owned scratch, 22 in all); smaller
+ * batches gather them after the sort.  Errors as mcx_xs_sort. */
+int mcx_xs_sort_inputs(mcx_problem* p, int64_t n, const double* E, const int32_t* mat, int32_t* perm,
+                       double* E_binned, int32_t* mat_binned, void* stream);
+
 /* mcx_xs_lookup processing the lookups in the order perm (a permutation of
  * 0..n-1, e.g. from mcx_xs_sort; NULL = natural order).  Results land in each
- * lookup's own row of out, so the order changes no value.  flags may hold
- * MCX_LOOKUP_FAST, MCX_LOOKUP_STAGED (applies to a binned perm with
- * MCX_LOOKUP_FAST; mcx_check_device reports a pipeline that gave up) and
- * MCX_LOOKUP_OUT32.  DEVICE pointers. */
+ * lookup's own row of out, so the order changes no value (with
+ * MCX_LOOKUP_LINEAR: within its bound).  flags may hold MCX_LOOKUP_FAST,
+ * MCX_LOOKUP_STAGED (applies to a binned perm with MCX_LOOKUP_FAST;
+ * mcx_check_device reports a pipeline that gave up), MCX_LOOKUP_OUT32,
+ * MCX_LOOKUP_LINEAR and MCX_LOOKUP_BINNED_INPUTS (with MCX_LOOKUP_FAST and a
+ * perm, not with MCX_LOOKUP_STAGED: E and mat are given in the processing
+ * order, lookup j taking E[j] and mat[j] and writing row perm[j] of out, as
+ * mcx_xs_sort_inputs produces them; the results equal those from the
+ * original E and mat bit for bit).  DEVICE pointers. */
 int mcx_xs_lookup_ordered(mcx_problem* p, int64_t n, const double* E, const int32_t* mat,
                           const int32_t* perm, void* out, int32_t flags, void* stream);
 

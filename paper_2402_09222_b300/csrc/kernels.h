@@ -18,10 +18,12 @@ constexpr int kLinBlocksPerSm = 3;
 // work: a device counter for in-order chunked scheduling of binned orders
 // (zeroed by the launch), or nullptr for a grid-stride loop.  linear: on a
 // binned order with a work counter, the round-linear sums (within the fast
-// bound, not bit-identical to the per-lookup sums).
+// bound, not bit-identical to the per-lookup sums).  inputs_binned: E and mat
+// are given in the processing order (lookup j has E[j], mat[j] and writes
+// row perm[j]); binned orders with a work counter only.
 int launch_xs_lookup_fast(const Tables& t, int64_t n, const double* E, const int32_t* mat,
                           const int32_t* perm, void* out, bool out32, int grid, cudaStream_t st,
-                          unsigned long long* work = nullptr, bool linear = false);
+                          unsigned long long* work = nullptr, bool linear = false, bool inputs_binned = false);
 struct SortParams {
     int32_t n_materials = 1;
     int32_t n_ebuckets = 1;
@@ -132,9 +134,22 @@ int launch_lookup_sort(const SortParams& sp, int64_t n, const double* E, const i
 #endif
 constexpr int64_t kBin2MinLookups = MCX_BIN2_MIN_LOOKUPS;   // batches from this size take it
 size_t lookup_sort2_place_words(const SortParams& sp, int64_t n);
+// With a carry, every lookup's energy and material follow its index through
+// both passes (coarse-order scratch tE [n] double, tM [n] int32) into the
+// binned order: Eb[j] = E[perm[j]], Mb[j] = mat[perm[j]].
+struct Bin2Carry {
+    double* tE;
+    int32_t* tM;
+    double* Eb;
+    int32_t* Mb;
+};
 int launch_lookup_sort2(const SortParams& sp, int64_t n, const double* E, const int32_t* mat, uint32_t* place,
                         uint32_t* keys, int32_t* tidx, uint16_t* tfine, int32_t* perm, int sm_count,
-                        cudaStream_t st);
+                        cudaStream_t st, const Bin2Carry* carry = nullptr);
+// Eb[j] = E[perm[j]], Mb[j] = mat[perm[j]] by a gather (NaN and -1 for an
+// index outside [0, n)).
+int launch_gather_inputs(int64_t n, const int32_t* perm, const double* E, const int32_t* mat, double* Eb,
+                         int32_t* Mb, int grid, cudaStream_t st);
 
 // First failed bounds check of each kernel translation unit since the last
 // read (site << 56 | index; 0: none), cleared by the read; always 0 in

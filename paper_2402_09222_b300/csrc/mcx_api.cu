@@ -806,10 +806,14 @@ SortParams batch_sort_params(const TableStore* ts, int64_t n, int64_t max_bins =
 }
 
 // Bin lookups into perm (device, [n]), about per_bucket lookups per bin;
-// bins scratch owned by the problem.
+// bins scratch owned by the problem.  With Eb and Mb (device, [n]) also the
+// energies and materials in the binned order: carried through the two-level
+// passes, or gathered after the one-level sort.
 int sort_device(mcx_problem* p, int64_t n, const double* E, const int32_t* mat, int32_t* perm,
-                cudaStream_t st, int64_t per_bucket = kLookupsPerBucket)
+                cudaStream_t st, int64_t per_bucket = kLookupsPerBucket, double* Eb = nullptr,
+                int32_t* Mb = nullptr)
 {
+    const bool carry = Eb != nullptr && Mb != nullptr;
     const SortParams sp = batch_sort_params(p->tables, n, (int64_t)1 << 21, per_bucket);
     // large batches: the two-level binning (no global atomic per lookup)
     const bool two = n >= kBin2MinLookups;
@@ -822,16 +826,21 @@ int sort_device(mcx_problem* p, int64_t n, const double* E, const int32_t* mat, 
         p->lbins_cap = nb;
     }
     if (two) {
-        const size_t words = 2 * (size_t)n + ((size_t)n + 1) / 2;   // keys, indices, fine bins
+        // keys, indices, fine bins; with a carry then (from an even word, for
+        // 8-byte alignment) the coarse-order energies and materials
+        const size_t base = 2 * (size_t)n + ((size_t)n + 1) / 2;
+        const size_t e_off = (base + 1) & ~(size_t)1;
+        const size_t words = carry ? e_off + 3 * (size_t)n : base;
         if (p->bin2_cap < words) {
             dev_free(p->bin2);
             p->bin2_cap = 0;
             TRY(dev_alloc(&p->bin2, words));
             p->bin2_cap = words;
         }
+        const Bin2Carry cy{reinterpret_cast<double*>(p->bin2 + e_off), p->bin2 + e_off + 2 * (size_t)n, Eb, Mb};
         const int r = launch_lookup_sort2(sp, n, E, mat, p->lbins, reinterpret_cast<uint32_t*>(p->bin2),
                                           p->bin2 + n, reinterpret_cast<uint16_t*>(p->bin2 + 2 * n), perm,
-                                          p->sm_count, st);
+                                          p->sm_count, st, carry ? &cy : nullptr);
         if (r == 0) return MCX_OK;
         if (r == -1) return fail(MCX_ERR_CUDA, "lookup binning launch failed");
         // r == -2: too many tiles x coarse bins; the one-level sort below
@@ -845,6 +854,8 @@ int sort_device(mcx_problem* p, int64_t n, const double* E, const int32_t* mat, 
     }
     if (launch_lookup_sort(sp, n, E, mat, p->lbins, perm, lookup_grid(p), st))
         return fail(MCX_ERR_CUDA, "lookup sort launch failed");
+    if (carry && launch_gather_inputs(n, perm, E, mat, Eb, Mb, lookup_grid(p), st))
+        return fail(MCX_ERR_CUDA, "input gather launch failed");
     return MCX_OK;
 }
 
@@ -885,7 +896,7 @@ int lookup_device_ordered(mcx_problem* p, int64_t n, const double* E, const int3
             work ? p->sm_count * ((flags & MCX_LOOKUP_LINEAR) ? kLinBlocksPerSm : kFastBlocksPerSm) : lookup_grid(p);
         r = (flags & MCX_LOOKUP_FAST)
                 ? launch_xs_lookup_fast(ts->view, n, E, mat, perm, out, out32, grid, st, work,
-                                        (flags & MCX_LOOKUP_LINEAR) != 0)
+                                        (flags & MCX_LOOKUP_LINEAR) != 0, (flags & MCX_LOOKUP_BINNED_INPUTS) != 0)
                 : launch_xs_lookup_exact(ts->view, n, E, mat, perm, static_cast<double*>(out), lookup_grid(p), st);
     }
     if (r) return fail(MCX_ERR_CUDA, "lookup launch failed: %s", cudaGetErrorString(cudaGetLastError()));
@@ -1553,17 +1564,34 @@ int mcx_xs_sort(mcx_problem* p, int64_t n, const double* E, const int32_t* mat, 
     return sort_device(p, n, E, mat, perm, (cudaStream_t)stream);
 }
 
+int mcx_xs_sort_inputs(mcx_problem* p, int64_t n, const double* E, const int32_t* mat, int32_t* perm,
+                       double* E_binned, int32_t* mat_binned, void* stream)
+{
+    g_err.clear();
+    TRY(check_tables(p));
+    if (n < 0 || n >= ((int64_t)1 << 31)) return fail(MCX_ERR_ARG, "n out of range");
+    if (n == 0) return MCX_OK;
+    if (!E || !mat || !perm || !E_binned || !mat_binned) return fail(MCX_ERR_ARG, "NULL buffer");
+    DeviceGuard dg(p->device);
+    return sort_device(p, n, E, mat, perm, (cudaStream_t)stream, kLookupsPerBucket, E_binned, mat_binned);
+}
+
 int mcx_xs_lookup_ordered(mcx_problem* p, int64_t n, const double* E, const int32_t* mat,
                           const int32_t* perm, void* out, int32_t flags, void* stream)
 {
     g_err.clear();
     TRY(check_tables(p));
     if (n < 0 || n >= ((int64_t)1 << 31)) return fail(MCX_ERR_ARG, "n out of range");
-    if (flags & ~(MCX_LOOKUP_FAST | MCX_LOOKUP_STAGED | MCX_LOOKUP_OUT32 | MCX_LOOKUP_LINEAR))
-        return fail(MCX_ERR_ARG,
-                    "flags may hold MCX_LOOKUP_FAST, MCX_LOOKUP_STAGED, MCX_LOOKUP_OUT32 and MCX_LOOKUP_LINEAR only");
+    if (flags & ~(MCX_LOOKUP_FAST | MCX_LOOKUP_STAGED | MCX_LOOKUP_OUT32 | MCX_LOOKUP_LINEAR |
+                  MCX_LOOKUP_BINNED_INPUTS))
+        return fail(MCX_ERR_ARG, "flags may hold MCX_LOOKUP_FAST, MCX_LOOKUP_STAGED, MCX_LOOKUP_OUT32, "
+                                 "MCX_LOOKUP_LINEAR and MCX_LOOKUP_BINNED_INPUTS only");
     if ((flags & (MCX_LOOKUP_OUT32 | MCX_LOOKUP_LINEAR)) && !(flags & MCX_LOOKUP_FAST))
         return fail(MCX_ERR_ARG, "MCX_LOOKUP_OUT32 and MCX_LOOKUP_LINEAR need MCX_LOOKUP_FAST");
+    if ((flags & MCX_LOOKUP_BINNED_INPUTS) &&
+        (!(flags & MCX_LOOKUP_FAST) || (flags & MCX_LOOKUP_STAGED) || !perm))
+        return fail(MCX_ERR_ARG, "MCX_LOOKUP_BINNED_INPUTS needs MCX_LOOKUP_FAST, a permutation and no "
+                                 "MCX_LOOKUP_STAGED");
     if (n == 0) return MCX_OK;
     if (!E || !mat || !out) return fail(MCX_ERR_ARG, "NULL buffer");
     DeviceGuard dg(p->device);

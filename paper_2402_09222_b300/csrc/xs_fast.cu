@@ -466,15 +466,17 @@ __device__ __forceinline__ void species_pair(const Tables& t, int32_t b, int32_t
 template <int W, int U, int NC, typename OutT>
 __device__ __forceinline__ void lookup_one(const Tables& t, int64_t n, int64_t j, const double* __restrict__ Ein,
                                            const int32_t* __restrict__ mat,
-                                           const int32_t* __restrict__ perm, OutT* __restrict__ out)
+                                           const int32_t* __restrict__ perm, OutT* __restrict__ out,
+                                           bool inb = false)
 {
     constexpr int NCMAX = NC;   // channels (a record holds up to 4 W - 2)
     static_assert(NC <= 4 * W - 2, "record too narrow for the channel count");
     const int nc = NC;
     const int64_t l = perm ? (int64_t)load_in(perm + j) : j;
     if (perm && !MCX_IN_BOUNDS(l >= 0 && l < n, BC_PERM, l)) return;
-    const double E = load_in(Ein + l);
-    const int32_t m = load_in(mat + l);
+    // inb: the inputs are given in the processing order
+    const double E = load_in(Ein + (inb ? j : l));
+    const int32_t m = load_in(mat + (inb ? j : l));
     if (m < 0 || m >= t.n_materials || E != E) {
         for (int r = 0; r < nc; ++r) store_nan(out + l * nc + r);
         return;
@@ -608,7 +610,7 @@ __global__ void __launch_bounds__(256, LIN ? MCX_LIN_MIN_BLOCKS : MCX_FAST2_MIN_
                                                          const int32_t* __restrict__ mat,
                                                          const int32_t* __restrict__ perm,
                                                          OutT* __restrict__ out,
-                                                         unsigned long long* __restrict__ work)
+                                                         unsigned long long* __restrict__ work, bool inb)
 {
     static_assert(32 % U == 0, "species groups of U must tile the 32-species blocks");
     static_assert(!LIN || MCX_FAST_PARK, "the round-linear form keeps its per-lane sums in shared memory");
@@ -647,8 +649,8 @@ __global__ void __launch_bounds__(256, LIN ? MCX_LIN_MIN_BLOCKS : MCX_FAST2_MIN_
             if (in0) {
                 l0 = (int64_t)load_in(perm + j0);
                 if (MCX_IN_BOUNDS(l0 >= 0 && l0 < n, BC_PERM, l0)) {
-                    E0 = load_in(Ein + l0);
-                    m0 = load_in(mat + l0);
+                    E0 = load_in(Ein + (inb ? j0 : l0));
+                    m0 = load_in(mat + (inb ? j0 : l0));
                 } else {
                     in0 = false;
                 }
@@ -656,8 +658,8 @@ __global__ void __launch_bounds__(256, LIN ? MCX_LIN_MIN_BLOCKS : MCX_FAST2_MIN_
             if (in1) {
                 l1 = (int64_t)load_in(perm + j1);
                 if (MCX_IN_BOUNDS(l1 >= 0 && l1 < n, BC_PERM, l1)) {
-                    E1 = load_in(Ein + l1);
-                    m1 = load_in(mat + l1);
+                    E1 = load_in(Ein + (inb ? j1 : l1));
+                    m1 = load_in(mat + (inb ? j1 : l1));
                 } else {
                     in1 = false;
                 }
@@ -666,8 +668,8 @@ __global__ void __launch_bounds__(256, LIN ? MCX_LIN_MIN_BLOCKS : MCX_FAST2_MIN_
             const bool ok = in0 && in1 && m0 == mw && m1 == mw && mw >= 0 && mw < t.n_materials && E0 == E0 &&
                             E1 == E1;
             if (!__all_sync(FULLM, ok)) {
-                if (in0) lookup_one<W, U, NC, OutT>(t, n, j0, Ein, mat, perm, out);
-                if (in1) lookup_one<W, U, NC, OutT>(t, n, j1, Ein, mat, perm, out);
+                if (in0) lookup_one<W, U, NC, OutT>(t, n, j0, Ein, mat, perm, out, inb);
+                if (in1) lookup_one<W, U, NC, OutT>(t, n, j1, Ein, mat, perm, out, inb);
                 continue;
             }
 #if MCX_FAST_PARK
@@ -1553,11 +1555,20 @@ constexpr int kBin2PerThread = kBinTile / kBin2Threads;
 
 // Pass A, one tile at a time: the tile's lookups are ranked by coarse bin in
 // shared memory, staged in that order, and written out as contiguous runs.
+// CARRY: each lookup's energy and material travel with its index into the
+// coarse order, so that the final order can hand them to the lookup in
+// sequence instead of through the permutation; the write-out reads them by
+// index from the tile's own 16,384-lookup window of E and mat, which the
+// loop touches in a short time (cache hits after the first touch of a line).
+template <bool CARRY>
 __global__ void __launch_bounds__(kBin2Threads, MCX_BIN2_A_BLOCKS) k_bin2_scatter(int64_t n, const uint32_t* __restrict__ keys,
                                                               int n_coarse, int n_tiles,
                                                               const uint32_t* __restrict__ place,
                                                               int32_t* __restrict__ tidx,
-                                                              uint16_t* __restrict__ tfine)
+                                                              uint16_t* __restrict__ tfine,
+                                                              const double* __restrict__ E,
+                                                              const int32_t* __restrict__ mat,
+                                                              double* __restrict__ tE, int32_t* __restrict__ tM)
 {
     extern __shared__ uint32_t sm[];
     uint32_t* cur = sm;                                    // [n_coarse] first place of (bin, tile)
@@ -1596,12 +1607,22 @@ __global__ void __launch_bounds__(kBin2Threads, MCX_BIN2_A_BLOCKS) k_bin2_scatte
             }
         }
         __syncthreads();
-        for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
-            const uint32_t kk = skey[k];
-            const uint32_t c = kk >> kBinFineBits;
-            const uint32_t pos = cur[c] + ((uint32_t)k - lst[c]);
-            tidx[pos] = sidx[k];
-            tfine[pos] = (uint16_t)(kk & ((1u << kBinFineBits) - 1u));
+        // unrolled over the thread's slots, so that the carried loads overlap
+#pragma unroll
+        for (int j = 0; j < kBin2PerThread; ++j) {
+            const int k = threadIdx.x + j * kBin2Threads;
+            if (k < cnt) {
+                const uint32_t kk = skey[k];
+                const uint32_t c = kk >> kBinFineBits;
+                const uint32_t pos = cur[c] + ((uint32_t)k - lst[c]);
+                const int32_t ix = sidx[k];
+                tidx[pos] = ix;
+                tfine[pos] = (uint16_t)(kk & ((1u << kBinFineBits) - 1u));
+                if constexpr (CARRY) {
+                    tE[pos] = __ldg(E + ix);
+                    tM[pos] = __ldg(mat + ix);
+                }
+            }
         }
         __syncthreads();
     }
@@ -1609,23 +1630,33 @@ __global__ void __launch_bounds__(kBin2Threads, MCX_BIN2_A_BLOCKS) k_bin2_scatte
 
 // Pass B: coarse bin c holds places [place[c * n_tiles], place[(c + 1) *
 // n_tiles]) (n for the last), the same range in the final order.  One block
-// per coarse bin counts its fine bins, then takes the range in sub-tiles of
-// kBinSub: each is ranked by fine bin in shared memory, staged, and written
-// out as contiguous runs.
+// per coarse bin counts its fine bins, then takes the range in sub-tiles:
+// each is ranked by fine bin in shared memory, staged, and written out as
+// contiguous runs.  CARRY: the energies and materials in the coarse order
+// (tE, tM) follow their indices into the final order (Eb, Mb): the staging
+// keeps each entry's offset in the sub-tile, and the write-out reads them
+// from the sub-tile's window of tE and tM.
 constexpr int kBin2FineThreads = 1 << kBinFineBits;    // one fine bin per thread
-constexpr int kBin2FinePerThread = kBinSub / kBin2FineThreads;
+template <bool CARRY>
 __global__ void __launch_bounds__(kBin2FineThreads, MCX_BIN2_B_BLOCKS) k_bin2_fine(int64_t n, int n_coarse, int n_tiles,
                                                                const uint32_t* __restrict__ place,
                                                                const int32_t* __restrict__ tidx,
                                                                const uint16_t* __restrict__ tfine,
-                                                               int32_t* __restrict__ perm)
+                                                               int32_t* __restrict__ perm,
+                                                               const double* __restrict__ tE,
+                                                               const int32_t* __restrict__ tM,
+                                                               double* __restrict__ Eb, int32_t* __restrict__ Mb)
 {
     constexpr int F = kBin2FineThreads;
+    constexpr int kSub = kBinSub;
+    constexpr int kPer = kSub / F;
+    static_assert(kSub <= 65536, "sub-tile offsets are 16-bit");
     extern __shared__ uint32_t sm[];
     uint32_t* fcur = sm;                               // [F] next place of each fine bin in the range
     uint32_t* lst = sm + F;                            // [F] sub-tile counts, then starts
-    int32_t* sidx = reinterpret_cast<int32_t*>(sm + 2 * F);            // [kBinSub] staged indices
-    uint16_t* sfine = reinterpret_cast<uint16_t*>(sidx + kBinSub);    // [kBinSub] staged fine bins
+    int32_t* sidx = reinterpret_cast<int32_t*>(sm + 2 * F);            // [kSub] staged indices
+    uint16_t* sfine = reinterpret_cast<uint16_t*>(sidx + kSub);       // [kSub] staged fine bins
+    uint16_t* sorig = sfine + kSub;                                   // CARRY: [kSub] offsets in the sub-tile
     __shared__ uint32_t warp_sums[32];
     for (int c = blockIdx.x; c < n_coarse; c += gridDim.x) {
         const int64_t s0 = place[(int64_t)c * n_tiles];
@@ -1635,17 +1666,17 @@ __global__ void __launch_bounds__(kBin2FineThreads, MCX_BIN2_B_BLOCKS) k_bin2_fi
         for (int64_t e = s0 + threadIdx.x; e < s1; e += F) atomicAdd(&fcur[__ldg(tfine + e)], 1u);
         __syncthreads();
         smem_exclusive_scan(fcur, F, warp_sums);
-        for (int64_t sub = s0; sub < s1; sub += kBinSub) {
-            const int cnt = s1 - sub < kBinSub ? (int)(s1 - sub) : kBinSub;
+        for (int64_t sub = s0; sub < s1; sub += kSub) {
+            const int cnt = s1 - sub < kSub ? (int)(s1 - sub) : kSub;
             lst[threadIdx.x] = 0u;
             __syncthreads();
-            // per element its rank within its fine bin (< kBinSub) above the
+            // per element its rank within its fine bin (< kSub) above the
             // fine bin's kBinFineBits bits
             static_assert(kBinSub <= (1 << (32 - kBinFineBits)), "rank and fine bin share a word");
-            uint32_t fr[kBin2FinePerThread];
-            int32_t ix[kBin2FinePerThread];
+            uint32_t fr[kPer];
+            int32_t ix[kPer];
 #pragma unroll
-            for (int j = 0; j < kBin2FinePerThread; ++j) {
+            for (int j = 0; j < kPer; ++j) {
                 const int k = threadIdx.x + j * F;
                 fr[j] = 0u;
                 ix[j] = 0;
@@ -1660,19 +1691,29 @@ __global__ void __launch_bounds__(kBin2FineThreads, MCX_BIN2_B_BLOCKS) k_bin2_fi
             __syncthreads();
             smem_exclusive_scan(lst, F, warp_sums);
 #pragma unroll
-            for (int j = 0; j < kBin2FinePerThread; ++j) {
+            for (int j = 0; j < kPer; ++j) {
                 const int k = threadIdx.x + j * F;
                 if (k < cnt) {
                     const uint32_t fb = fr[j] & ((1u << kBinFineBits) - 1u);
                     const uint32_t slot = lst[fb] + (fr[j] >> kBinFineBits);
                     sidx[slot] = ix[j];
                     sfine[slot] = (uint16_t)fb;
+                    if constexpr (CARRY) sorig[slot] = (uint16_t)k;
                 }
             }
             __syncthreads();
-            for (int k = threadIdx.x; k < cnt; k += F) {
-                const uint32_t fb = sfine[k];
-                perm[s0 + fcur[fb] + ((uint32_t)k - lst[fb])] = sidx[k];
+#pragma unroll
+            for (int j = 0; j < kPer; ++j) {
+                const int k = threadIdx.x + j * F;
+                if (k < cnt) {
+                    const uint32_t fb = sfine[k];
+                    const int64_t pos = s0 + fcur[fb] + ((uint32_t)k - lst[fb]);
+                    perm[pos] = sidx[k];
+                    if constexpr (CARRY) {
+                        Eb[pos] = __ldg(tE + sub + sorig[k]);
+                        Mb[pos] = __ldg(tM + sub + sorig[k]);
+                    }
+                }
             }
             __syncthreads();
             fcur[threadIdx.x] += mine;
@@ -1681,18 +1722,36 @@ __global__ void __launch_bounds__(kBin2FineThreads, MCX_BIN2_B_BLOCKS) k_bin2_fi
     }
 }
 
+// CARRY on the one-level path: the energies and materials in the binned
+// order by a gather through the permutation (batches below the two-level
+// size, whose inputs mostly sit in L2).
+__global__ void k_gather_inputs(int64_t n, const int32_t* __restrict__ perm, const double* __restrict__ E,
+                                const int32_t* __restrict__ mat, double* __restrict__ Eb, int32_t* __restrict__ Mb)
+{
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t l = __ldg(perm + j);
+        if (MCX_IN_BOUNDS(l >= 0 && l < n, BC_PERM, l)) {
+            Eb[j] = __ldg(E + l);
+            Mb[j] = __ldg(mat + l);
+        } else {
+            Eb[j] = __longlong_as_double(0x7ff8000000000000LL);
+            Mb[j] = -1;
+        }
+    }
+}
+
 }  // namespace
 
 template <bool LIN, typename OutT>
 static int launch_warp2_t(const Tables& t, int64_t n, const double* E, const int32_t* mat, const int32_t* perm,
-                          OutT* out, int grid, cudaStream_t st, unsigned long long* work)
+                          OutT* out, int grid, cudaStream_t st, unsigned long long* work, bool inb)
 {
     switch (t.n_ch) {
-    case 1: k_xs_lookup_warp2<1, kFastUnroll, 1, OutT, LIN><<<grid, 256, 0, st>>>(t, n, E, mat, perm, out, work); break;
-    case 2: k_xs_lookup_warp2<1, kFastUnroll, 2, OutT, LIN><<<grid, 256, 0, st>>>(t, n, E, mat, perm, out, work); break;
-    case 3: k_xs_lookup_warp2<2, kFastUnroll, 3, OutT, LIN><<<grid, 256, 0, st>>>(t, n, E, mat, perm, out, work); break;
-    case 4: k_xs_lookup_warp2<2, kFastUnroll, 4, OutT, LIN><<<grid, 256, 0, st>>>(t, n, E, mat, perm, out, work); break;
-    case 5: k_xs_lookup_warp2<2, kFastUnroll, 5, OutT, LIN><<<grid, 256, 0, st>>>(t, n, E, mat, perm, out, work); break;
+    case 1: k_xs_lookup_warp2<1, kFastUnroll, 1, OutT, LIN><<<grid, 256, 0, st>>>(t, n, E, mat, perm, out, work, inb); break;
+    case 2: k_xs_lookup_warp2<1, kFastUnroll, 2, OutT, LIN><<<grid, 256, 0, st>>>(t, n, E, mat, perm, out, work, inb); break;
+    case 3: k_xs_lookup_warp2<2, kFastUnroll, 3, OutT, LIN><<<grid, 256, 0, st>>>(t, n, E, mat, perm, out, work, inb); break;
+    case 4: k_xs_lookup_warp2<2, kFastUnroll, 4, OutT, LIN><<<grid, 256, 0, st>>>(t, n, E, mat, perm, out, work, inb); break;
+    case 5: k_xs_lookup_warp2<2, kFastUnroll, 5, OutT, LIN><<<grid, 256, 0, st>>>(t, n, E, mat, perm, out, work, inb); break;
     default: return -1;
     }
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
@@ -1700,14 +1759,15 @@ static int launch_warp2_t(const Tables& t, int64_t n, const double* E, const int
 
 template <typename OutT>
 static int launch_fast_t(const Tables& t, int64_t n, const double* E, const int32_t* mat, const int32_t* perm,
-                         OutT* out, int grid, cudaStream_t st, unsigned long long* work, bool linear)
+                         OutT* out, int grid, cudaStream_t st, unsigned long long* work, bool linear, bool inb)
 {
     // one instantiation per channel count: no work on unused record slots
 #if MCX_FAST_WARP
     if (perm && work)
-        return linear ? launch_warp2_t<true>(t, n, E, mat, perm, out, grid, st, work)
-                      : launch_warp2_t<false>(t, n, E, mat, perm, out, grid, st, work);
+        return linear ? launch_warp2_t<true>(t, n, E, mat, perm, out, grid, st, work, inb)
+                      : launch_warp2_t<false>(t, n, E, mat, perm, out, grid, st, work, inb);
 #endif
+    if (inb) return -1;   // binned inputs: the chunk-claiming warp forms only
     switch (t.n_ch) {
     case 1: k_xs_lookup_fast<1, kFastUnroll, 1, OutT><<<grid, 256, 0, st>>>(t, n, E, mat, perm, out, work); break;
     case 2: k_xs_lookup_fast<1, kFastUnroll, 2, OutT><<<grid, 256, 0, st>>>(t, n, E, mat, perm, out, work); break;
@@ -1721,11 +1781,12 @@ static int launch_fast_t(const Tables& t, int64_t n, const double* E, const int3
 
 int launch_xs_lookup_fast(const Tables& t, int64_t n, const double* E, const int32_t* mat,
                           const int32_t* perm, void* out, bool out32, int grid, cudaStream_t st,
-                          unsigned long long* work, bool linear)
+                          unsigned long long* work, bool linear, bool inputs_binned)
 {
     if (work && cudaMemsetAsync(work, 0, sizeof(unsigned long long), st) != cudaSuccess) return -1;
-    return out32 ? launch_fast_t(t, n, E, mat, perm, static_cast<float*>(out), grid, st, work, linear)
-                 : launch_fast_t(t, n, E, mat, perm, static_cast<double*>(out), grid, st, work, linear);
+    return out32 ? launch_fast_t(t, n, E, mat, perm, static_cast<float*>(out), grid, st, work, linear, inputs_binned)
+                 : launch_fast_t(t, n, E, mat, perm, static_cast<double*>(out), grid, st, work, linear,
+                                 inputs_binned);
 }
 
 template <int W, int NC, typename OutT>
@@ -1824,24 +1885,45 @@ size_t lookup_sort2_place_words(const SortParams& sp, int64_t n)
 
 int launch_lookup_sort2(const SortParams& sp, int64_t n, const double* E, const int32_t* mat, uint32_t* place,
                         uint32_t* keys, int32_t* tidx, uint16_t* tfine, int32_t* perm, int sm_count,
-                        cudaStream_t st)
+                        cudaStream_t st, const Bin2Carry* carry)
 {
     const Bin2Plan b = bin2_plan(sp, n);
     // the tile scan covers 4 coarse bins per thread of pass A
     if (n < 1 || b.cells > ((int64_t)1 << 28) || b.n_coarse > 4 * kBin2Threads) return -2;
+    const bool cy = carry != nullptr;
     const size_t smem = sizeof(uint32_t) * (size_t)b.n_coarse;
     const size_t smem_a = sizeof(uint32_t) * (2 * (size_t)b.n_coarse + 2 * kBinTile);
-    const size_t smem_b = sizeof(uint32_t) * 2 * kBin2FineThreads + (sizeof(int32_t) + sizeof(uint16_t)) * kBinSub;
-    if (cudaFuncSetAttribute(k_bin2_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_a) != cudaSuccess ||
-        cudaFuncSetAttribute(k_bin2_fine, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b) != cudaSuccess)
+    const size_t smem_b = sizeof(uint32_t) * 2 * kBin2FineThreads + (sizeof(int32_t) + sizeof(uint16_t)) * kBinSub +
+                          (cy ? sizeof(uint16_t) * kBinSub : 0);
+    const void* ka = cy ? (const void*)k_bin2_scatter<true> : (const void*)k_bin2_scatter<false>;
+    const void* kb = cy ? (const void*)k_bin2_fine<true> : (const void*)k_bin2_fine<false>;
+    if (cudaFuncSetAttribute(ka, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_a) != cudaSuccess ||
+        cudaFuncSetAttribute(kb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b) != cudaSuccess)
         return -1;
     const int g = b.n_tiles < sm_count * 4 ? b.n_tiles : sm_count * 4;
     k_bin2_count<<<g, 512, smem, st>>>(sp, n, E, mat, b.n_coarse, b.n_tiles, place, keys);
     launch_bin_scan(place, (int)b.cells, st);
     const int ga = b.n_tiles < sm_count * MCX_BIN2_A_BLOCKS ? b.n_tiles : sm_count * MCX_BIN2_A_BLOCKS;
-    k_bin2_scatter<<<ga, kBin2Threads, smem_a, st>>>(n, keys, b.n_coarse, b.n_tiles, place, tidx, tfine);
     const int gb = b.n_coarse < sm_count * MCX_BIN2_B_BLOCKS ? b.n_coarse : sm_count * MCX_BIN2_B_BLOCKS;
-    k_bin2_fine<<<gb, kBin2FineThreads, smem_b, st>>>(n, b.n_coarse, b.n_tiles, place, tidx, tfine, perm);
+    if (cy) {
+        k_bin2_scatter<true><<<ga, kBin2Threads, smem_a, st>>>(n, keys, b.n_coarse, b.n_tiles, place, tidx, tfine, E,
+                                                               mat, carry->tE, carry->tM);
+        k_bin2_fine<true><<<gb, kBin2FineThreads, smem_b, st>>>(n, b.n_coarse, b.n_tiles, place, tidx, tfine, perm,
+                                                                carry->tE, carry->tM, carry->Eb, carry->Mb);
+    } else {
+        k_bin2_scatter<false><<<ga, kBin2Threads, smem_a, st>>>(n, keys, b.n_coarse, b.n_tiles, place, tidx, tfine,
+                                                                nullptr, nullptr, nullptr, nullptr);
+        k_bin2_fine<false><<<gb, kBin2FineThreads, smem_b, st>>>(n, b.n_coarse, b.n_tiles, place, tidx, tfine, perm,
+                                                                 nullptr, nullptr, nullptr, nullptr);
+    }
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int launch_gather_inputs(int64_t n, const int32_t* perm, const double* E, const int32_t* mat, double* Eb,
+                         int32_t* Mb, int grid, cudaStream_t st)
+{
+    if (n < 1) return 0;
+    k_gather_inputs<<<grid, 256, 0, st>>>(n, perm, E, mat, Eb, Mb);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

@@ -29,6 +29,7 @@ ERR_ITER_LIMIT, ERR_TIMEOUT = -4, -7
 FP64, FP32 = 0, 1
 QUEUELESS, QUEUED, QUEUED_FULLEST = 0, 1, 2
 LOOKUP_EXACT, LOOKUP_FAST, LOOKUP_SORT, LOOKUP_STAGED, LOOKUP_OUT32, LOOKUP_LINEAR = 0, 1, 2, 4, 8, 16
+LOOKUP_BINNED_INPUTS = 32
 FLAG_DERIVATIVES, FLAG_HISTORY_DEBUG = 1, 2
 TALLY_FLUX, TALLY_ABSORB, TALLY_OUTCOME, TALLY_DFLUX, TALLY_DABSORB, TALLY_DOUTCOME = range(6)
 GEOM_NONE = 3
@@ -105,6 +106,7 @@ _sig("mcx_bounds_checked", C.c_int)
 _sig("mcx_read_fission_bank", C.c_int, _vp, _vp, _i64)
 _sig("mcx_xs_lookup", C.c_int, _vp, _i64, _vp, _vp, _vp, _i32, _vp)
 _sig("mcx_xs_sort", C.c_int, _vp, _i64, _vp, _vp, _vp, _vp)
+_sig("mcx_xs_sort_inputs", C.c_int, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp)
 _sig("mcx_xs_lookup_ordered", C.c_int, _vp, _i64, _vp, _vp, _vp, _vp, _i32, _vp)
 _sig("mcx_xs_lookup_host", C.c_int, _vp, _i64, _vp, _vp, _vp, _i32)
 _sig("mcx_xs_indices", C.c_int, _vp, _i64, _vp, _vp, _i32, _vp, _vp)
@@ -363,6 +365,25 @@ class Problem:
                                 _dev_ptr(mat, torch.int32, "mat"), _dev_ptr(perm, torch.int32, "perm"),
                                 _stream_ptr(stream)))
         return perm
+
+    def xs_sort_inputs(self, E, mat, perm=None, E_binned=None, mat_binned=None, stream=None):
+        """Binning permutation plus the energies and materials in the binned
+        order (for xs_lookup_ordered with LOOKUP_BINNED_INPUTS)."""
+        import torch
+        n = E.numel()
+        if perm is None:
+            perm = torch.empty(n, dtype=torch.int32, device=E.device)
+        if E_binned is None:
+            E_binned = torch.empty(n, dtype=torch.float64, device=E.device)
+        if mat_binned is None:
+            mat_binned = torch.empty(n, dtype=torch.int32, device=E.device)
+        if perm.numel() < n or E_binned.numel() < n or mat_binned.numel() < n or mat.numel() != n:
+            raise ValueError("mat, perm, E_binned and mat_binned must hold n = E.numel() entries")
+        _check(_lib.mcx_xs_sort_inputs(self.h, n, _dev_ptr(E, torch.float64, "E"),
+                                       _dev_ptr(mat, torch.int32, "mat"), _dev_ptr(perm, torch.int32, "perm"),
+                                       _dev_ptr(E_binned, torch.float64, "E_binned"),
+                                       _dev_ptr(mat_binned, torch.int32, "mat_binned"), _stream_ptr(stream)))
+        return perm, E_binned, mat_binned
 
     def xs_lookup_ordered(self, E, mat, perm, out=None, flags: int = LOOKUP_EXACT, stream=None):
         """Lookup processed in the order `perm` (None: natural order)."""

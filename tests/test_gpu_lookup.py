@@ -319,8 +319,9 @@ def test_backward_binned_dense_and_edge_cases(torch_cuda, precision, n_ch):
 def test_config2_full_size_sampled(torch_cuda):
     """355 species x 11,303 points, 12 materials, 1e8 lookups with FP32 tables
     in exactly the launch the benchmark times (its hash-bin count, binning
-    into a caller-held permutation, then the fast lookup over the binned
-    order with chunk-claiming warps); 20,000 sampled outputs checked against
+    into a caller-held permutation with the inputs carried into the binned
+    order, then the round-linear fast lookup over it with chunk-claiming
+    warps); 20,000 sampled outputs checked against
     the oracle on the FP32-rounded tables, and the exact FP64 full-search
     path on the same sample bit for bit."""
     import bench
@@ -334,8 +335,9 @@ def test_config2_full_size_sampled(torch_cuda):
     p32 = _handle(lib, mats, bench.TUNED["precision"], bench.TUNED["hash_bins"])
     out = torch.empty((n, 5), dtype=torch.float64, device="cuda")
     perm = torch.empty(n, dtype=torch.int32, device="cuda")
-    p32.xs_sort(dE, dm, perm)
-    p32.xs_lookup_ordered(dE, dm, perm, out=out, flags=bench.TUNED["flags"])
+    perm, Eb, mb = p32.xs_sort_inputs(dE, dm, perm)
+    p32.xs_lookup_ordered(Eb, mb, perm, out=out, flags=bench.TUNED["flags"] | mcx.LOOKUP_BINNED_INPUTS)
+    del Eb, mb
     got = out[torch.as_tensor(idx, device="cuda")].cpu().numpy()
     ref = oracle.xs_lookup(lib.fp32_rounded(), mats, E[idx], mat[idx], n_threads=8)
     rel = np.abs(got - ref) / np.maximum(np.abs(ref), 1e-300)

@@ -145,3 +145,42 @@ def test_linear_form_host_path_over_several_chunks(torch_cuda, out32):
     ref = oracle.xs_lookup(lib.fp32_rounded(), mats, E[idx], mat[idx], n_threads=8)
     _check(host[idx], ref)
     p.close()
+
+
+@pytest.mark.parametrize("n", [777, 1_000_003, 4_194_304 + 4_321])
+def test_sort_inputs_and_lookups_from_binned_inputs(torch_cuda, n):
+    """mcx_xs_sort_inputs hands over E[perm] and mat[perm] exactly (one-level
+    batches gather them, two-level ones carry them through both passes),
+    and a lookup reading them in the processing order gives the results of
+    the same lookup through the permutation bit for bit, in every form."""
+    from paper_2402_09222_b300 import mcx
+    from test_gpu_lookup import _assert_binned
+    torch = torch_cuda
+    lib = synth.species_library(30, 600, 731)
+    mats = synth.lookup_materials(30, 732, n_materials=7)
+    E, mat = banded_inputs(lib, mats.n_materials, n, 733)
+    p = _handle(lib, mats, mcx.FP32, 2000)
+    # the order: binned as mcx_xs_sort bins
+    perm, Eb, mb = p.xs_sort_inputs(_dev(torch, E, torch.float64), _dev(torch, mat, torch.int32))
+    _assert_binned(E, mat, perm.cpu().numpy(), lib, mats.n_materials)
+    # invalid lookups among them
+    E[[3, n // 2]] = [np.nan, 1e12]
+    mat[[5, n - 1]] = [-1, mats.n_materials]
+    dE, dm = _dev(torch, E, torch.float64), _dev(torch, mat, torch.int32)
+    perm, Eb, mb = p.xs_sort_inputs(dE, dm, perm, Eb, mb)
+    pm = perm.cpu().numpy()
+    assert np.array_equal(np.sort(pm), np.arange(n))
+    assert np.array_equal(Eb.cpu().numpy().view(np.uint64), E[pm].view(np.uint64))
+    assert np.array_equal(mb.cpu().numpy(), mat[pm])
+    F, L, O = mcx.LOOKUP_FAST, mcx.LOOKUP_LINEAR, mcx.LOOKUP_OUT32
+    for flags in (F, F | L, F | L | O):
+        a = p.xs_lookup_ordered(dE, dm, perm, flags=flags).cpu().numpy()
+        b = p.xs_lookup_ordered(Eb, mb, perm, flags=flags | mcx.LOOKUP_BINNED_INPUTS).cpu().numpy()
+        assert np.array_equal(a.view(np.uint8), b.view(np.uint8)), flags
+        assert np.all(np.isnan(b[[5, n - 1]]))
+    for bad in (mcx.LOOKUP_BINNED_INPUTS, F | mcx.LOOKUP_STAGED | mcx.LOOKUP_BINNED_INPUTS):
+        with pytest.raises(mcx.McxError, match="ARG"):
+            p.xs_lookup_ordered(Eb, mb, perm, flags=bad)
+    with pytest.raises(mcx.McxError, match="ARG"):
+        p.xs_lookup_ordered(Eb, mb, None, flags=F | mcx.LOOKUP_BINNED_INPUTS)
+    p.close()
