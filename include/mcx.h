@@ -373,13 +373,14 @@ int mcx_xs_sort(mcx_problem* p, int64_t n, const double* E, const int32_t* mat, 
                 void* stream);
 
 /* mcx_xs_sort that also hands over the inputs in the binned order:
- * E_binned[j] = E[perm[j]] and mat_binned[j] = mat[perm[j]] (FP64 [n] and
- * int32 [n], DEVICE, caller-owned, not aliasing E or mat), for
- * mcx_xs_lookup_ordered with MCX_LOOKUP_BINNED_INPUTS, which then reads them
- * in sequence instead of through the permutation.  Two-level batches carry
- * each energy and material with its index through both binning passes
- * (12 more bytes per lookup of library-owned scratch, 22 in all); smaller
- * batches gather them after the sort.  Errors as mcx_xs_sort. */
+ * E_binned[j] = E[perm[j]] and mat_binned[j] = mat[perm[j]], or -1 where
+ * that material id is outside [0, n_materials) (FP64 [n] and int32 [n],
+ * DEVICE, caller-owned, not aliasing E or mat), for mcx_xs_lookup_ordered
+ * with MCX_LOOKUP_BINNED_INPUTS, which then reads them in sequence instead
+ * of through the permutation.  Two-level batches carry each energy with its
+ * index through both binning passes (8 more bytes per lookup of
+ * library-owned scratch, 18 in all) and take the material from its bin;
+ * smaller batches gather them after the sort.  Errors as mcx_xs_sort. */
 int mcx_xs_sort_inputs(mcx_problem* p, int64_t n, const double* E, const int32_t* mat, int32_t* perm,
                        double* E_binned, int32_t* mat_binned, void* stream);
 

@@ -134,22 +134,22 @@ int launch_lookup_sort(const SortParams& sp, int64_t n, const double* E, const i
 #endif
 constexpr int64_t kBin2MinLookups = MCX_BIN2_MIN_LOOKUPS;   // batches from this size take it
 size_t lookup_sort2_place_words(const SortParams& sp, int64_t n);
-// With a carry, every lookup's energy and material follow its index through
-// both passes (coarse-order scratch tE [n] double, tM [n] int32) into the
-// binned order: Eb[j] = E[perm[j]], Mb[j] = mat[perm[j]].
+// With a carry, every lookup's energy follows its index through both passes
+// (coarse-order scratch tE [n] double) into the binned order, and its
+// material is taken from its bin: Eb[j] = E[perm[j]], Mb[j] = mat[perm[j]]
+// (-1 for a material id outside [0, n_materials)).
 struct Bin2Carry {
     double* tE;
-    int32_t* tM;
     double* Eb;
     int32_t* Mb;
 };
 int launch_lookup_sort2(const SortParams& sp, int64_t n, const double* E, const int32_t* mat, uint32_t* place,
                         uint32_t* keys, int32_t* tidx, uint16_t* tfine, int32_t* perm, int sm_count,
                         cudaStream_t st, const Bin2Carry* carry = nullptr);
-// Eb[j] = E[perm[j]], Mb[j] = mat[perm[j]] by a gather (NaN and -1 for an
-// index outside [0, n)).
-int launch_gather_inputs(int64_t n, const int32_t* perm, const double* E, const int32_t* mat, double* Eb,
-                         int32_t* Mb, int grid, cudaStream_t st);
+// Eb[j] = E[perm[j]], Mb[j] = mat[perm[j]] by a gather (-1 for a material
+// id outside [0, n_materials); NaN and -1 for an index outside [0, n)).
+int launch_gather_inputs(int64_t n, const int32_t* perm, const double* E, const int32_t* mat, int n_materials,
+                         double* Eb, int32_t* Mb, int grid, cudaStream_t st);
 
 // First failed bounds check of each kernel translation unit since the last
 // read (site << 56 | index; 0: none), cleared by the read; always 0 in

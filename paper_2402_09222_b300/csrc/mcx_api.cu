@@ -827,17 +827,17 @@ int sort_device(mcx_problem* p, int64_t n, const double* E, const int32_t* mat, 
     }
     if (two) {
         // keys, indices, fine bins; with a carry then (from an even word, for
-        // 8-byte alignment) the coarse-order energies and materials
+        // 8-byte alignment) the coarse-order energies
         const size_t base = 2 * (size_t)n + ((size_t)n + 1) / 2;
         const size_t e_off = (base + 1) & ~(size_t)1;
-        const size_t words = carry ? e_off + 3 * (size_t)n : base;
+        const size_t words = carry ? e_off + 2 * (size_t)n : base;
         if (p->bin2_cap < words) {
             dev_free(p->bin2);
             p->bin2_cap = 0;
             TRY(dev_alloc(&p->bin2, words));
             p->bin2_cap = words;
         }
-        const Bin2Carry cy{reinterpret_cast<double*>(p->bin2 + e_off), p->bin2 + e_off + 2 * (size_t)n, Eb, Mb};
+        const Bin2Carry cy{reinterpret_cast<double*>(p->bin2 + e_off), Eb, Mb};
         const int r = launch_lookup_sort2(sp, n, E, mat, p->lbins, reinterpret_cast<uint32_t*>(p->bin2),
                                           p->bin2 + n, reinterpret_cast<uint16_t*>(p->bin2 + 2 * n), perm,
                                           p->sm_count, st, carry ? &cy : nullptr);
@@ -854,7 +854,7 @@ int sort_device(mcx_problem* p, int64_t n, const double* E, const int32_t* mat, 
     }
     if (launch_lookup_sort(sp, n, E, mat, p->lbins, perm, lookup_grid(p), st))
         return fail(MCX_ERR_CUDA, "lookup sort launch failed");
-    if (carry && launch_gather_inputs(n, perm, E, mat, Eb, Mb, lookup_grid(p), st))
+    if (carry && launch_gather_inputs(n, perm, E, mat, sp.n_materials, Eb, Mb, lookup_grid(p), st))
         return fail(MCX_ERR_CUDA, "input gather launch failed");
     return MCX_OK;
 }

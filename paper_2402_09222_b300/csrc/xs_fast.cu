@@ -188,6 +188,9 @@ __device__ __forceinline__ void load_records<2>(const float4* __restrict__ rec, 
 }
 #endif
 
+// Brings the 32-byte sector at p into L2 (no register result, no wait).
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
 template <typename V>
 __device__ __forceinline__ V load_in(const V* p)
 {
@@ -917,6 +920,11 @@ __global__ void __launch_bounds__(256, LIN ? MCX_LIN_MIN_BLOCKS : MCX_FAST2_MIN_
 }
 
 // Bin key of a lookup: material major, then the log-energy bucket.
+// Two-level binning's stored keys: the bin key, and in bit 31 whether the
+// lookup's material id is out of range; tfine keeps that bit in its bit 15.
+constexpr uint32_t kKeyInvalid = 0x80000000u;
+constexpr uint16_t kFineInvalid = 0x8000u;
+
 __device__ __forceinline__ int lookup_key(const SortParams& sp, double E, int32_t m)
 {
     const float fb = (logf((float)E) - sp.ln_lo) * sp.scale;
@@ -1499,8 +1507,10 @@ __global__ void __launch_bounds__(512) k_bin2_count(SortParams sp, int64_t n, co
         for (int k = threadIdx.x; k < kBinTile; k += blockDim.x) {
             const int64_t l = base + k;
             if (l < n) {
-                const uint32_t key = (uint32_t)lookup_key(sp, __ldg(E + l), __ldg(mat + l));
-                keys[l] = key;
+                const int32_t m = __ldg(mat + l);
+                const uint32_t key = (uint32_t)lookup_key(sp, __ldg(E + l), m);
+                // bit 31: a material id outside [0, n_materials) (binned with material 0)
+                keys[l] = key | (m < 0 || m >= sp.n_materials ? kKeyInvalid : 0u);
                 atomicAdd(&h[key >> kBinFineBits], 1u);
             }
         }
@@ -1555,11 +1565,13 @@ constexpr int kBin2PerThread = kBinTile / kBin2Threads;
 
 // Pass A, one tile at a time: the tile's lookups are ranked by coarse bin in
 // shared memory, staged in that order, and written out as contiguous runs.
-// CARRY: each lookup's energy and material travel with its index into the
-// coarse order, so that the final order can hand them to the lookup in
-// sequence instead of through the permutation; the write-out reads them by
-// index from the tile's own 16,384-lookup window of E and mat, which the
-// loop touches in a short time (cache hits after the first touch of a line).
+// The fine bin goes out with the invalid-material bit of the key (bit 15).
+// CARRY: each lookup's energy travels with its index into the coarse order
+// (tE), so that the final order can hand it to the lookup in sequence
+// instead of through the permutation; the energies are loaded in index
+// order and staged in slot order in place of the keys, which the write-out
+// re-reads from the tile's (cache-hot) window.  The material is not carried:
+// pass B derives it from the bin.
 template <bool CARRY>
 __global__ void __launch_bounds__(kBin2Threads, MCX_BIN2_A_BLOCKS) k_bin2_scatter(int64_t n, const uint32_t* __restrict__ keys,
                                                               int n_coarse, int n_tiles,
@@ -1567,14 +1579,16 @@ __global__ void __launch_bounds__(kBin2Threads, MCX_BIN2_A_BLOCKS) k_bin2_scatte
                                                               int32_t* __restrict__ tidx,
                                                               uint16_t* __restrict__ tfine,
                                                               const double* __restrict__ E,
-                                                              const int32_t* __restrict__ mat,
-                                                              double* __restrict__ tE, int32_t* __restrict__ tM)
+                                                              double* __restrict__ tE)
 {
     extern __shared__ uint32_t sm[];
     uint32_t* cur = sm;                                    // [n_coarse] first place of (bin, tile)
     uint32_t* lst = sm + n_coarse;                         // [n_coarse] tile-local counts, then starts
-    uint32_t* skey = sm + 2 * n_coarse;                    // [kBinTile] staged keys
-    int32_t* sidx = reinterpret_cast<int32_t*>(skey + kBinTile);   // [kBinTile] staged indices
+    int32_t* sidx = reinterpret_cast<int32_t*>(sm + 2 * n_coarse);   // [kBinTile] staged indices
+    // [kBinTile] staged keys, or with CARRY staged energies (8-byte aligned:
+    // 2 n_coarse + kBinTile words precede them, an even count)
+    uint32_t* skey = reinterpret_cast<uint32_t*>(sidx + kBinTile);
+    double* sE = reinterpret_cast<double*>(sidx + kBinTile);
     __shared__ uint32_t warp_sums[32];
     for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         for (int i = threadIdx.x; i < n_coarse; i += blockDim.x) {
@@ -1592,7 +1606,7 @@ __global__ void __launch_bounds__(kBin2Threads, MCX_BIN2_A_BLOCKS) k_bin2_scatte
             rk[j] = 0u;
             if (k < cnt) {
                 key[j] = __ldg(keys + base + k);
-                rk[j] = atomicAdd(&lst[key[j] >> kBinFineBits], 1u);
+                rk[j] = atomicAdd(&lst[(key[j] & ~kKeyInvalid) >> kBinFineBits], 1u);
             }
         }
         __syncthreads();
@@ -1601,27 +1615,26 @@ __global__ void __launch_bounds__(kBin2Threads, MCX_BIN2_A_BLOCKS) k_bin2_scatte
         for (int j = 0; j < kBin2PerThread; ++j) {
             const int k = threadIdx.x + j * kBin2Threads;
             if (k < cnt) {
-                const uint32_t slot = lst[key[j] >> kBinFineBits] + rk[j];
-                skey[slot] = key[j];
+                const uint32_t slot = lst[(key[j] & ~kKeyInvalid) >> kBinFineBits] + rk[j];
                 sidx[slot] = (int32_t)(base + k);
+                if constexpr (CARRY)
+                    sE[slot] = load_in(E + base + k);
+                else
+                    skey[slot] = key[j];
             }
         }
         __syncthreads();
-        // unrolled over the thread's slots, so that the carried loads overlap
 #pragma unroll
         for (int j = 0; j < kBin2PerThread; ++j) {
             const int k = threadIdx.x + j * kBin2Threads;
             if (k < cnt) {
-                const uint32_t kk = skey[k];
-                const uint32_t c = kk >> kBinFineBits;
-                const uint32_t pos = cur[c] + ((uint32_t)k - lst[c]);
                 const int32_t ix = sidx[k];
+                const uint32_t kk = CARRY ? __ldg(keys + ix) : skey[k];
+                const uint32_t c = (kk & ~kKeyInvalid) >> kBinFineBits;
+                const uint32_t pos = cur[c] + ((uint32_t)k - lst[c]);
                 tidx[pos] = ix;
-                tfine[pos] = (uint16_t)(kk & ((1u << kBinFineBits) - 1u));
-                if constexpr (CARRY) {
-                    tE[pos] = __ldg(E + ix);
-                    tM[pos] = __ldg(mat + ix);
-                }
+                tfine[pos] = (uint16_t)((kk & ((1u << kBinFineBits) - 1u)) | (kk & kKeyInvalid ? kFineInvalid : 0u));
+                if constexpr (CARRY) tE[pos] = sE[k];
             }
         }
         __syncthreads();
@@ -1630,58 +1643,60 @@ __global__ void __launch_bounds__(kBin2Threads, MCX_BIN2_A_BLOCKS) k_bin2_scatte
 
 // Pass B: coarse bin c holds places [place[c * n_tiles], place[(c + 1) *
 // n_tiles]) (n for the last), the same range in the final order.  One block
-// per coarse bin counts its fine bins, then takes the range in sub-tiles:
-// each is ranked by fine bin in shared memory, staged, and written out as
-// contiguous runs.  CARRY: the energies and materials in the coarse order
-// (tE, tM) follow their indices into the final order (Eb, Mb): the staging
-// keeps each entry's offset in the sub-tile, and the write-out reads them
-// from the sub-tile's window of tE and tM.
+// per coarse bin counts its fine bins, then takes the range in sub-tiles of
+// kBinSub: each is ranked by fine bin in shared memory, staged, and written
+// out as contiguous runs.  CARRY: the energies in the coarse order (tE) are
+// staged with their indices and follow them into the final order (Eb); the
+// material comes from the bin, (c * 512 + fine bin) / n_ebuckets, or -1 for
+// a lookup whose material id was out of range (Mb).
 constexpr int kBin2FineThreads = 1 << kBinFineBits;    // one fine bin per thread
+constexpr int kBin2FinePerThread = kBinSub / kBin2FineThreads;
 template <bool CARRY>
 __global__ void __launch_bounds__(kBin2FineThreads, MCX_BIN2_B_BLOCKS) k_bin2_fine(int64_t n, int n_coarse, int n_tiles,
                                                                const uint32_t* __restrict__ place,
                                                                const int32_t* __restrict__ tidx,
                                                                const uint16_t* __restrict__ tfine,
                                                                int32_t* __restrict__ perm,
-                                                               const double* __restrict__ tE,
-                                                               const int32_t* __restrict__ tM,
+                                                               const double* __restrict__ tE, int n_ebuckets,
                                                                double* __restrict__ Eb, int32_t* __restrict__ Mb)
 {
     constexpr int F = kBin2FineThreads;
-    constexpr int kSub = kBinSub;
-    constexpr int kPer = kSub / F;
-    static_assert(kSub <= 65536, "sub-tile offsets are 16-bit");
+    constexpr uint16_t kFineMask = (1u << kBinFineBits) - 1u;
     extern __shared__ uint32_t sm[];
     uint32_t* fcur = sm;                               // [F] next place of each fine bin in the range
     uint32_t* lst = sm + F;                            // [F] sub-tile counts, then starts
-    int32_t* sidx = reinterpret_cast<int32_t*>(sm + 2 * F);            // [kSub] staged indices
-    uint16_t* sfine = reinterpret_cast<uint16_t*>(sidx + kSub);       // [kSub] staged fine bins
-    uint16_t* sorig = sfine + kSub;                                   // CARRY: [kSub] offsets in the sub-tile
+    int32_t* sidx = reinterpret_cast<int32_t*>(sm + 2 * F);            // [kBinSub] staged indices
+    // CARRY: [kBinSub] staged energies (2 F + kBinSub words precede them: even)
+    double* sE = reinterpret_cast<double*>(sidx + kBinSub);
+    uint16_t* sfine = reinterpret_cast<uint16_t*>(sE + (CARRY ? kBinSub : 0));   // [kBinSub] staged fine bins
     __shared__ uint32_t warp_sums[32];
     for (int c = blockIdx.x; c < n_coarse; c += gridDim.x) {
         const int64_t s0 = place[(int64_t)c * n_tiles];
         const int64_t s1 = c + 1 < n_coarse ? (int64_t)place[(int64_t)(c + 1) * n_tiles] : n;
         fcur[threadIdx.x] = 0u;
         __syncthreads();
-        for (int64_t e = s0 + threadIdx.x; e < s1; e += F) atomicAdd(&fcur[__ldg(tfine + e)], 1u);
+        for (int64_t e = s0 + threadIdx.x; e < s1; e += F) atomicAdd(&fcur[__ldg(tfine + e) & kFineMask], 1u);
         __syncthreads();
         smem_exclusive_scan(fcur, F, warp_sums);
-        for (int64_t sub = s0; sub < s1; sub += kSub) {
-            const int cnt = s1 - sub < kSub ? (int)(s1 - sub) : kSub;
+        for (int64_t sub = s0; sub < s1; sub += kBinSub) {
+            const int cnt = s1 - sub < kBinSub ? (int)(s1 - sub) : kBinSub;
             lst[threadIdx.x] = 0u;
             __syncthreads();
-            // per element its rank within its fine bin (< kSub) above the
+            // per element its rank within its fine bin (< kBinSub) above the
             // fine bin's kBinFineBits bits
             static_assert(kBinSub <= (1 << (32 - kBinFineBits)), "rank and fine bin share a word");
-            uint32_t fr[kPer];
-            int32_t ix[kPer];
+            uint32_t fr[kBin2FinePerThread];
+            int32_t ix[kBin2FinePerThread];
+            uint16_t tf[kBin2FinePerThread];
 #pragma unroll
-            for (int j = 0; j < kPer; ++j) {
+            for (int j = 0; j < kBin2FinePerThread; ++j) {
                 const int k = threadIdx.x + j * F;
                 fr[j] = 0u;
                 ix[j] = 0;
+                tf[j] = 0;
                 if (k < cnt) {
-                    const uint32_t fb = __ldg(tfine + sub + k);
+                    tf[j] = __ldg(tfine + sub + k);
+                    const uint32_t fb = tf[j] & kFineMask;
                     ix[j] = __ldg(tidx + sub + k);
                     fr[j] = (atomicAdd(&lst[fb], 1u) << kBinFineBits) | fb;
                 }
@@ -1691,27 +1706,30 @@ __global__ void __launch_bounds__(kBin2FineThreads, MCX_BIN2_B_BLOCKS) k_bin2_fi
             __syncthreads();
             smem_exclusive_scan(lst, F, warp_sums);
 #pragma unroll
-            for (int j = 0; j < kPer; ++j) {
+            for (int j = 0; j < kBin2FinePerThread; ++j) {
                 const int k = threadIdx.x + j * F;
                 if (k < cnt) {
                     const uint32_t fb = fr[j] & ((1u << kBinFineBits) - 1u);
                     const uint32_t slot = lst[fb] + (fr[j] >> kBinFineBits);
                     sidx[slot] = ix[j];
-                    sfine[slot] = (uint16_t)fb;
-                    if constexpr (CARRY) sorig[slot] = (uint16_t)k;
+                    sfine[slot] = tf[j];
+                    if constexpr (CARRY) sE[slot] = load_in(tE + sub + k);
                 }
             }
             __syncthreads();
 #pragma unroll
-            for (int j = 0; j < kPer; ++j) {
+            for (int j = 0; j < kBin2FinePerThread; ++j) {
                 const int k = threadIdx.x + j * F;
                 if (k < cnt) {
-                    const uint32_t fb = sfine[k];
+                    const uint32_t tfk = sfine[k];
+                    const uint32_t fb = tfk & kFineMask;
                     const int64_t pos = s0 + fcur[fb] + ((uint32_t)k - lst[fb]);
                     perm[pos] = sidx[k];
                     if constexpr (CARRY) {
-                        Eb[pos] = __ldg(tE + sub + sorig[k]);
-                        Mb[pos] = __ldg(tM + sub + sorig[k]);
+                        Eb[pos] = sE[k];
+                        Mb[pos] = (tfk & kFineInvalid) ? -1
+                                                       : (int32_t)((((uint32_t)c << kBinFineBits) | fb) /
+                                                                   (uint32_t)n_ebuckets);
                     }
                 }
             }
@@ -1724,15 +1742,18 @@ __global__ void __launch_bounds__(kBin2FineThreads, MCX_BIN2_B_BLOCKS) k_bin2_fi
 
 // CARRY on the one-level path: the energies and materials in the binned
 // order by a gather through the permutation (batches below the two-level
-// size, whose inputs mostly sit in L2).
+// size, whose inputs mostly sit in L2); a material id outside [0,
+// n_materials) becomes -1, as the two-level path writes it.
 __global__ void k_gather_inputs(int64_t n, const int32_t* __restrict__ perm, const double* __restrict__ E,
-                                const int32_t* __restrict__ mat, double* __restrict__ Eb, int32_t* __restrict__ Mb)
+                                const int32_t* __restrict__ mat, int n_materials, double* __restrict__ Eb,
+                                int32_t* __restrict__ Mb)
 {
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
         const int64_t l = __ldg(perm + j);
         if (MCX_IN_BOUNDS(l >= 0 && l < n, BC_PERM, l)) {
             Eb[j] = __ldg(E + l);
-            Mb[j] = __ldg(mat + l);
+            const int32_t m = __ldg(mat + l);
+            Mb[j] = m >= 0 && m < n_materials ? m : -1;
         } else {
             Eb[j] = __longlong_as_double(0x7ff8000000000000LL);
             Mb[j] = -1;
@@ -1892,9 +1913,13 @@ int launch_lookup_sort2(const SortParams& sp, int64_t n, const double* E, const 
     if (n < 1 || b.cells > ((int64_t)1 << 28) || b.n_coarse > 4 * kBin2Threads) return -2;
     const bool cy = carry != nullptr;
     const size_t smem = sizeof(uint32_t) * (size_t)b.n_coarse;
-    const size_t smem_a = sizeof(uint32_t) * (2 * (size_t)b.n_coarse + 2 * kBinTile);
+    // pass A: counts and starts, staged indices, staged keys (or with the
+    // carry staged energies); pass B: counts and starts, staged indices and
+    // fine bins (and with the carry energies)
+    const size_t smem_a = sizeof(uint32_t) * (2 * (size_t)b.n_coarse + kBinTile) +
+                          (cy ? sizeof(double) : sizeof(uint32_t)) * kBinTile;
     const size_t smem_b = sizeof(uint32_t) * 2 * kBin2FineThreads + (sizeof(int32_t) + sizeof(uint16_t)) * kBinSub +
-                          (cy ? sizeof(uint16_t) * kBinSub : 0);
+                          (cy ? sizeof(double) * kBinSub : 0);
     const void* ka = cy ? (const void*)k_bin2_scatter<true> : (const void*)k_bin2_scatter<false>;
     const void* kb = cy ? (const void*)k_bin2_fine<true> : (const void*)k_bin2_fine<false>;
     if (cudaFuncSetAttribute(ka, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_a) != cudaSuccess ||
@@ -1907,23 +1932,23 @@ int launch_lookup_sort2(const SortParams& sp, int64_t n, const double* E, const 
     const int gb = b.n_coarse < sm_count * MCX_BIN2_B_BLOCKS ? b.n_coarse : sm_count * MCX_BIN2_B_BLOCKS;
     if (cy) {
         k_bin2_scatter<true><<<ga, kBin2Threads, smem_a, st>>>(n, keys, b.n_coarse, b.n_tiles, place, tidx, tfine, E,
-                                                               mat, carry->tE, carry->tM);
+                                                               carry->tE);
         k_bin2_fine<true><<<gb, kBin2FineThreads, smem_b, st>>>(n, b.n_coarse, b.n_tiles, place, tidx, tfine, perm,
-                                                                carry->tE, carry->tM, carry->Eb, carry->Mb);
+                                                                carry->tE, sp.n_ebuckets, carry->Eb, carry->Mb);
     } else {
         k_bin2_scatter<false><<<ga, kBin2Threads, smem_a, st>>>(n, keys, b.n_coarse, b.n_tiles, place, tidx, tfine,
-                                                                nullptr, nullptr, nullptr, nullptr);
+                                                                nullptr, nullptr);
         k_bin2_fine<false><<<gb, kBin2FineThreads, smem_b, st>>>(n, b.n_coarse, b.n_tiles, place, tidx, tfine, perm,
-                                                                 nullptr, nullptr, nullptr, nullptr);
+                                                                 nullptr, sp.n_ebuckets, nullptr, nullptr);
     }
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-int launch_gather_inputs(int64_t n, const int32_t* perm, const double* E, const int32_t* mat, double* Eb,
-                         int32_t* Mb, int grid, cudaStream_t st)
+int launch_gather_inputs(int64_t n, const int32_t* perm, const double* E, const int32_t* mat, int n_materials,
+                         double* Eb, int32_t* Mb, int grid, cudaStream_t st)
 {
     if (n < 1) return 0;
-    k_gather_inputs<<<grid, 256, 0, st>>>(n, perm, E, mat, Eb, Mb);
+    k_gather_inputs<<<grid, 256, 0, st>>>(n, perm, E, mat, n_materials, Eb, Mb);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

@@ -149,8 +149,9 @@ def test_linear_form_host_path_over_several_chunks(torch_cuda, out32):
 
 @pytest.mark.parametrize("n", [777, 1_000_003, 4_194_304 + 4_321])
 def test_sort_inputs_and_lookups_from_binned_inputs(torch_cuda, n):
-    """mcx_xs_sort_inputs hands over E[perm] and mat[perm] exactly (one-level
-    batches gather them, two-level ones carry them through both passes),
+    """mcx_xs_sort_inputs hands over E[perm] exactly and mat[perm] (-1 for an
+    id out of range; one-level batches gather them, two-level ones carry the
+    energies through both passes and take the material from the bin),
     and a lookup reading them in the processing order gives the results of
     the same lookup through the permutation bit for bit, in every form."""
     from paper_2402_09222_b300 import mcx
@@ -171,7 +172,8 @@ def test_sort_inputs_and_lookups_from_binned_inputs(torch_cuda, n):
     pm = perm.cpu().numpy()
     assert np.array_equal(np.sort(pm), np.arange(n))
     assert np.array_equal(Eb.cpu().numpy().view(np.uint64), E[pm].view(np.uint64))
-    assert np.array_equal(mb.cpu().numpy(), mat[pm])
+    valid = (mat[pm] >= 0) & (mat[pm] < mats.n_materials)
+    assert np.array_equal(mb.cpu().numpy(), np.where(valid, mat[pm], -1))
     F, L, O = mcx.LOOKUP_FAST, mcx.LOOKUP_LINEAR, mcx.LOOKUP_OUT32
     for flags in (F, F | L, F | L | O):
         a = p.xs_lookup_ordered(dE, dm, perm, flags=flags).cpu().numpy()
