@@ -33,7 +33,7 @@ LOOKUP_FLAGS = {"exact": 0, "fast": 1, "fast_binned": 3, "staged": 7, "fast_binn
                 "fast_binned_linear": 19}
 # the round-linear sums depend on which lookups share a round, and the order
 # within a bin is not fixed: compared within the fast bound, not bit for bit
-NOT_BITWISE = ("lk_fast_binned_linear",)
+NOT_BITWISE = ("lk_fast_binned_linear", "lk_binned_inputs_linear")
 MODES = {"queueless": 0, "queued": 1, "queued_fullest": 2}
 
 CASE = r'''
@@ -68,6 +68,20 @@ def run_all(flags_by_name, modes):
     p.check_device()
     res["bw_dens"], res["bw_sigma"] = gd.cpu().numpy(), gs.cpu().numpy()
     p.close()
+    # two-level binning handing the inputs over in the binned order (4.3M
+    # lookups, invalid material ids among them), and lookups reading them
+    blib = synth.species_library(20, 400, 165)
+    bmats = synth.lookup_materials(20, 166, n_materials=5)
+    bE, bm = synth.lookup_inputs(4_300_001, bmats.n_materials, 167)
+    bm[[11, 2_000_000]] = [-1, bmats.n_materials]
+    bp = mcx.Problem(None).load_tables(blib, bmats, precision=mcx.FP32, hash_bins=1000)
+    perm, Eb, mb = bp.xs_sort_inputs(torch.as_tensor(bE, device="cuda"), torch.as_tensor(bm, device="cuda"))
+    bp.check_device()
+    for name, fl in (("fast", mcx.LOOKUP_FAST), ("linear", mcx.LOOKUP_FAST | mcx.LOOKUP_LINEAR)):
+        res["lk_binned_inputs_" + name] = bp.xs_lookup_ordered(Eb, mb, perm,
+                                                               flags=fl | mcx.LOOKUP_BINNED_INPUTS).cpu().numpy()
+        bp.check_device()
+    bp.close()
     for name, mode in modes.items():
         prob, q = transport_case(mode)
         q.run(particles_in_flight=1500, seed=5)
