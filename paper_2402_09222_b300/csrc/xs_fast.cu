@@ -1658,9 +1658,30 @@ __global__ void __launch_bounds__(kBin2Threads, MCX_BIN2_A_BLOCKS) k_bin2_scatte
 // material comes from the bin, (c * 512 + fine bin) / n_ebuckets, or -1 for
 // a lookup whose material id was out of range (Mb).
 constexpr int kBin2FineThreads = 1 << kBinFineBits;    // one fine bin per thread
-constexpr int kBin2FinePerThread = kBinSub / kBin2FineThreads;
+// With the carry, pass B takes larger sub-tiles so that each fine bin's run
+// per sub-tile is longer (fewer partially written sectors at the run ends):
+// blocks of MCX_BIN2_B_CARRY_THREADS threads (the first 512 also keep one
+// fine bin each), MCX_BIN2_B_CARRY_SUB lookups per sub-tile.
+#ifndef MCX_BIN2_B_CARRY_THREADS
+#define MCX_BIN2_B_CARRY_THREADS 1024
+#endif
+#ifndef MCX_BIN2_B_CARRY_SUB
+#define MCX_BIN2_B_CARRY_SUB 8192
+#endif
+#ifndef MCX_BIN2_B_CARRY_BLOCKS
+#define MCX_BIN2_B_CARRY_BLOCKS 1
+#endif
 template <bool CARRY>
-__global__ void __launch_bounds__(kBin2FineThreads, MCX_BIN2_B_BLOCKS) k_bin2_fine(int64_t n, int n_coarse, int n_tiles,
+struct Bin2Fine {
+    static constexpr int kThreads = CARRY ? MCX_BIN2_B_CARRY_THREADS : kBin2FineThreads;
+    static constexpr int kSub = CARRY ? MCX_BIN2_B_CARRY_SUB : kBinSub;
+    static constexpr int kBlocks = CARRY ? MCX_BIN2_B_CARRY_BLOCKS : MCX_BIN2_B_BLOCKS;
+    static constexpr int kPer = kSub / kThreads;
+    static_assert(kSub % kThreads == 0 && kThreads >= kBin2FineThreads && kThreads <= 1024, "pass B shape");
+    static_assert(kSub <= (1 << (32 - kBinFineBits)), "rank and fine bin share a word");
+};
+template <bool CARRY>
+__global__ void __launch_bounds__(Bin2Fine<CARRY>::kThreads, Bin2Fine<CARRY>::kBlocks) k_bin2_fine(int64_t n, int n_coarse, int n_tiles,
                                                                const uint32_t* __restrict__ place,
                                                                const int32_t* __restrict__ tidx,
                                                                const uint16_t* __restrict__ tfine,
@@ -1669,36 +1690,37 @@ __global__ void __launch_bounds__(kBin2FineThreads, MCX_BIN2_B_BLOCKS) k_bin2_fi
                                                                double* __restrict__ Eb, int32_t* __restrict__ Mb)
 {
     constexpr int F = kBin2FineThreads;
+    constexpr int T = Bin2Fine<CARRY>::kThreads, kSub = Bin2Fine<CARRY>::kSub, kPer = Bin2Fine<CARRY>::kPer;
     constexpr uint16_t kFineMask = (1u << kBinFineBits) - 1u;
+    const bool bin_owner = threadIdx.x < F;            // thread keeps fine bin threadIdx.x
     extern __shared__ uint32_t sm[];
     uint32_t* fcur = sm;                               // [F] next place of each fine bin in the range
     uint32_t* lst = sm + F;                            // [F] sub-tile counts, then starts
-    int32_t* sidx = reinterpret_cast<int32_t*>(sm + 2 * F);            // [kBinSub] staged indices
-    // CARRY: [kBinSub] staged energies (2 F + kBinSub words precede them: even)
-    double* sE = reinterpret_cast<double*>(sidx + kBinSub);
-    uint16_t* sfine = reinterpret_cast<uint16_t*>(sE + (CARRY ? kBinSub : 0));   // [kBinSub] staged fine bins
+    int32_t* sidx = reinterpret_cast<int32_t*>(sm + 2 * F);            // [kSub] staged indices
+    // CARRY: [kSub] staged energies (2 F + kSub words precede them: even)
+    double* sE = reinterpret_cast<double*>(sidx + kSub);
+    uint16_t* sfine = reinterpret_cast<uint16_t*>(sE + (CARRY ? kSub : 0));   // [kSub] staged fine bins
     __shared__ uint32_t warp_sums[32];
     for (int c = blockIdx.x; c < n_coarse; c += gridDim.x) {
         const int64_t s0 = place[(int64_t)c * n_tiles];
         const int64_t s1 = c + 1 < n_coarse ? (int64_t)place[(int64_t)(c + 1) * n_tiles] : n;
-        fcur[threadIdx.x] = 0u;
+        if (bin_owner) fcur[threadIdx.x] = 0u;
         __syncthreads();
-        for (int64_t e = s0 + threadIdx.x; e < s1; e += F) atomicAdd(&fcur[__ldg(tfine + e) & kFineMask], 1u);
+        for (int64_t e = s0 + threadIdx.x; e < s1; e += T) atomicAdd(&fcur[__ldg(tfine + e) & kFineMask], 1u);
         __syncthreads();
         smem_exclusive_scan(fcur, F, warp_sums);
-        for (int64_t sub = s0; sub < s1; sub += kBinSub) {
-            const int cnt = s1 - sub < kBinSub ? (int)(s1 - sub) : kBinSub;
-            lst[threadIdx.x] = 0u;
+        for (int64_t sub = s0; sub < s1; sub += kSub) {
+            const int cnt = s1 - sub < kSub ? (int)(s1 - sub) : kSub;
+            if (bin_owner) lst[threadIdx.x] = 0u;
             __syncthreads();
-            // per element its rank within its fine bin (< kBinSub) above the
+            // per element its rank within its fine bin (< kSub) above the
             // fine bin's kBinFineBits bits
-            static_assert(kBinSub <= (1 << (32 - kBinFineBits)), "rank and fine bin share a word");
-            uint32_t fr[kBin2FinePerThread];
-            int32_t ix[kBin2FinePerThread];
-            uint16_t tf[kBin2FinePerThread];
+            uint32_t fr[kPer];
+            int32_t ix[kPer];
+            uint16_t tf[kPer];
 #pragma unroll
-            for (int j = 0; j < kBin2FinePerThread; ++j) {
-                const int k = threadIdx.x + j * F;
+            for (int j = 0; j < kPer; ++j) {
+                const int k = threadIdx.x + j * T;
                 fr[j] = 0u;
                 ix[j] = 0;
                 tf[j] = 0;
@@ -1710,12 +1732,13 @@ __global__ void __launch_bounds__(kBin2FineThreads, MCX_BIN2_B_BLOCKS) k_bin2_fi
                 }
             }
             __syncthreads();
-            const uint32_t mine = lst[threadIdx.x];   // this sub-tile's count of fine bin threadIdx.x
+            // this sub-tile's count of fine bin threadIdx.x
+            const uint32_t mine = bin_owner ? lst[threadIdx.x] : 0u;
             __syncthreads();
             smem_exclusive_scan(lst, F, warp_sums);
 #pragma unroll
-            for (int j = 0; j < kBin2FinePerThread; ++j) {
-                const int k = threadIdx.x + j * F;
+            for (int j = 0; j < kPer; ++j) {
+                const int k = threadIdx.x + j * T;
                 if (k < cnt) {
                     const uint32_t fb = fr[j] & ((1u << kBinFineBits) - 1u);
                     const uint32_t slot = lst[fb] + (fr[j] >> kBinFineBits);
@@ -1726,8 +1749,8 @@ __global__ void __launch_bounds__(kBin2FineThreads, MCX_BIN2_B_BLOCKS) k_bin2_fi
             }
             __syncthreads();
 #pragma unroll
-            for (int j = 0; j < kBin2FinePerThread; ++j) {
-                const int k = threadIdx.x + j * F;
+            for (int j = 0; j < kPer; ++j) {
+                const int k = threadIdx.x + j * T;
                 if (k < cnt) {
                     const uint32_t tfk = sfine[k];
                     const uint32_t fb = tfk & kFineMask;
@@ -1742,7 +1765,7 @@ __global__ void __launch_bounds__(kBin2FineThreads, MCX_BIN2_B_BLOCKS) k_bin2_fi
                 }
             }
             __syncthreads();
-            fcur[threadIdx.x] += mine;
+            if (bin_owner) fcur[threadIdx.x] += mine;
             __syncthreads();
         }
     }
@@ -1926,8 +1949,9 @@ int launch_lookup_sort2(const SortParams& sp, int64_t n, const double* E, const 
     // fine bins (and with the carry energies)
     const size_t smem_a = sizeof(uint32_t) * (2 * (size_t)b.n_coarse + kBinTile) +
                           (cy ? sizeof(double) : sizeof(uint32_t)) * kBinTile;
-    const size_t smem_b = sizeof(uint32_t) * 2 * kBin2FineThreads + (sizeof(int32_t) + sizeof(uint16_t)) * kBinSub +
-                          (cy ? sizeof(double) * kBinSub : 0);
+    const size_t sub_b = cy ? Bin2Fine<true>::kSub : Bin2Fine<false>::kSub;
+    const size_t smem_b = sizeof(uint32_t) * 2 * kBin2FineThreads + (sizeof(int32_t) + sizeof(uint16_t)) * sub_b +
+                          (cy ? sizeof(double) * sub_b : 0);
     const void* ka = cy ? (const void*)k_bin2_scatter<true> : (const void*)k_bin2_scatter<false>;
     const void* kb = cy ? (const void*)k_bin2_fine<true> : (const void*)k_bin2_fine<false>;
     if (cudaFuncSetAttribute(ka, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_a) != cudaSuccess ||
@@ -1937,16 +1961,17 @@ int launch_lookup_sort2(const SortParams& sp, int64_t n, const double* E, const 
     k_bin2_count<<<g, 512, smem, st>>>(sp, n, E, mat, b.n_coarse, b.n_tiles, place, keys);
     launch_bin_scan(place, (int)b.cells, st);
     const int ga = b.n_tiles < sm_count * MCX_BIN2_A_BLOCKS ? b.n_tiles : sm_count * MCX_BIN2_A_BLOCKS;
-    const int gb = b.n_coarse < sm_count * MCX_BIN2_B_BLOCKS ? b.n_coarse : sm_count * MCX_BIN2_B_BLOCKS;
+    const int bpb = cy ? Bin2Fine<true>::kBlocks : Bin2Fine<false>::kBlocks;
+    const int gb = b.n_coarse < sm_count * bpb ? b.n_coarse : sm_count * bpb;
     if (cy) {
         k_bin2_scatter<true><<<ga, kBin2Threads, smem_a, st>>>(n, keys, b.n_coarse, b.n_tiles, place, tidx, tfine, E,
                                                                carry->tE);
-        k_bin2_fine<true><<<gb, kBin2FineThreads, smem_b, st>>>(n, b.n_coarse, b.n_tiles, place, tidx, tfine, perm,
+        k_bin2_fine<true><<<gb, Bin2Fine<true>::kThreads, smem_b, st>>>(n, b.n_coarse, b.n_tiles, place, tidx, tfine, perm,
                                                                 carry->tE, sp.n_ebuckets, carry->Eb, carry->Mb);
     } else {
         k_bin2_scatter<false><<<ga, kBin2Threads, smem_a, st>>>(n, keys, b.n_coarse, b.n_tiles, place, tidx, tfine,
                                                                 nullptr, nullptr);
-        k_bin2_fine<false><<<gb, kBin2FineThreads, smem_b, st>>>(n, b.n_coarse, b.n_tiles, place, tidx, tfine, perm,
+        k_bin2_fine<false><<<gb, Bin2Fine<false>::kThreads, smem_b, st>>>(n, b.n_coarse, b.n_tiles, place, tidx, tfine, perm,
                                                                  nullptr, sp.n_ebuckets, nullptr, nullptr);
     }
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
