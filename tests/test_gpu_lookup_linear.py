@@ -186,3 +186,27 @@ def test_sort_inputs_and_lookups_from_binned_inputs(torch_cuda, n):
     with pytest.raises(mcx.McxError, match="ARG"):
         p.xs_lookup_ordered(Eb, mb, None, flags=F | mcx.LOOKUP_BINNED_INPUTS)
     p.close()
+
+
+def test_sort_inputs_with_many_coarse_bins(torch_cuda):
+    """120 materials x 16,384 buckets (3,840 coarse bins: pass A's staging
+    at its largest) handing the inputs over; the round-linear lookup on
+    them within the bound."""
+    from paper_2402_09222_b300 import mcx
+    from test_gpu_lookup import _assert_binned
+    torch = torch_cuda
+    lib = synth.species_library(60, 300, 741)
+    mats = synth.lookup_materials(60, 742, n_materials=120)
+    E, mat = banded_inputs(lib, mats.n_materials, 4_300_007, 743)
+    p = _handle(lib, mats, mcx.FP32, 1000)
+    dE, dm = _dev(torch, E, torch.float64), _dev(torch, mat, torch.int32)
+    perm, Eb, mb = p.xs_sort_inputs(dE, dm)
+    pm = perm.cpu().numpy()
+    _assert_binned(E, mat, pm, lib, mats.n_materials)
+    assert np.array_equal(Eb.cpu().numpy().view(np.uint64), E[pm].view(np.uint64))
+    assert np.array_equal(mb.cpu().numpy(), mat[pm])
+    out = p.xs_lookup_ordered(Eb, mb, perm, flags=mcx.LOOKUP_FAST | mcx.LOOKUP_LINEAR
+                              | mcx.LOOKUP_BINNED_INPUTS).cpu().numpy()
+    idx = np.random.default_rng(9).choice(len(E), 40_000, replace=False)
+    _check(out[idx], oracle.xs_lookup(lib.fp32_rounded(), mats, E[idx], mat[idx], n_threads=8))
+    p.close()
