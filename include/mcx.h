@@ -350,7 +350,10 @@ int mcx_last_run_stats(const mcx_problem* p, int64_t* out, int32_t n);
  * order, sums from +0.0, no fused multiply-add); MCX_LOOKUP_FAST stays within
  * 1e-6 relative of it; MCX_LOOKUP_SORT first bins the lookups by material and
  * log-energy (results unchanged; uses library-owned scratch memory sized for
- * n).  A material id out of range gives NaN outputs for that lookup.
+ * n); MCX_LOOKUP_LINEAR with FAST and SORT sums per 64-lookup round where it
+ * can (within the same bound, last bits depending on the order within a
+ * bin); MCX_LOOKUP_OUT32 writes FP32 outputs.  A material id out of range
+ * gives NaN outputs for that lookup.
  * Errors: MCX_ERR_ARG, MCX_ERR_STATE, MCX_ERR_CUDA, MCX_ERR_OOM. */
 int mcx_xs_lookup(mcx_problem* p, int64_t n, const double* E, const int32_t* mat, void* out,
                   int32_t flags, void* stream);
