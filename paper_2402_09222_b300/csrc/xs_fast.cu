@@ -614,7 +614,12 @@ __global__ void __launch_bounds__(256, MCX_FAST_MIN_BLOCKS) k_xs_lookup_fast(Tab
 // compensated sums 22.6 ms, the channel updates 22.3 ms, the weights 22.2 ms;
 // each lane's search keys and output rows parked in shared memory, so that
 // the species loop spills half as much, 22.47 -> 22.27 ms on one box (with
-// 3 blocks per SM and no spills at all, 23.58 ms against 22.24).
+// 3 blocks per SM and no spills at all, 23.58 ms against 22.24).  Later:
+// each round's output rows leave through shared memory (MCX_FAST_ROWSTAGE,
+// 21.8 -> 20.3 ms), and with the inputs in the binned order (inb) 18.4 ms.
+// LIN: the round-linear sums above (the same prologue, searches and
+// per-lookup body for the species they leave), 3 blocks per SM, warps
+// claiming 256 lookups at a time: 10.25 ms per 1e8 on binned inputs.
 template <int W, int U, int NC, typename OutT, bool LIN>
 __global__ void __launch_bounds__(256, LIN ? MCX_LIN_MIN_BLOCKS : MCX_FAST2_MIN_BLOCKS) k_xs_lookup_warp2(Tables t, int64_t n, const double* __restrict__ Ein,
                                                          const int32_t* __restrict__ mat,
