@@ -350,7 +350,9 @@ int mcx_last_run_stats(const mcx_problem* p, int64_t* out, int32_t n);
  * order, sums from +0.0, no fused multiply-add); MCX_LOOKUP_FAST stays within
  * 1e-6 relative of it; MCX_LOOKUP_SORT first bins the lookups by material and
  * log-energy (results unchanged; uses library-owned scratch memory sized for
- * n); MCX_LOOKUP_LINEAR with FAST and SORT sums per 64-lookup round where it
+ * n; with MCX_LOOKUP_FAST from 2^22 lookups the binning also hands the
+ * energies and materials over in the binned order, as mcx_xs_sort_inputs,
+ * 12 more bytes per lookup of scratch); MCX_LOOKUP_LINEAR with FAST and SORT sums per 64-lookup round where it
  * can (within the same bound, last bits depending on the order within a
  * bin); MCX_LOOKUP_OUT32 writes FP32 outputs.  A material id out of range
  * gives NaN outputs for that lookup.

@@ -244,7 +244,10 @@ struct mcx_problem {
     int32_t* perm = nullptr;
     uint32_t* lbins = nullptr;
     int32_t* bin2 = nullptr;   // two-level binning: bin keys [n], lookup indices [n], fine bins [n] uint16
+    double* bin_E = nullptr;   // energies and materials handed over in the binned order [n]
+    int32_t* bin_M = nullptr;
     int64_t perm_cap = 0;
+    int64_t bin_in_cap = 0;
     size_t lbins_cap = 0;
     size_t bin2_cap = 0;
     double* h_buf = nullptr;  // host-path device staging
@@ -908,13 +911,27 @@ int lookup_device(mcx_problem* p, int64_t n, const double* E, const int32_t* mat
                   int32_t flags, cudaStream_t st)
 {
     const int32_t* perm = nullptr;
+    const int32_t pass = flags & (MCX_LOOKUP_FAST | MCX_LOOKUP_STAGED | MCX_LOOKUP_OUT32 | MCX_LOOKUP_LINEAR);
     if (flags & MCX_LOOKUP_SORT) {
         TRY(ensure_lookup_scratch(p, n, 0));
+        // large fast batches: the binning hands the inputs over in the binned
+        // order, and the lookup reads them in sequence (the same results)
+        if ((flags & MCX_LOOKUP_FAST) && !(flags & MCX_LOOKUP_STAGED) && n >= kBin2MinLookups) {
+            if (p->bin_in_cap < n) {
+                dev_free(p->bin_E);
+                dev_free(p->bin_M);
+                p->bin_in_cap = 0;
+                TRY(dev_alloc(&p->bin_E, (size_t)n));
+                TRY(dev_alloc(&p->bin_M, (size_t)n));
+                p->bin_in_cap = n;
+            }
+            TRY(sort_device(p, n, E, mat, p->perm, st, kLookupsPerBucket, p->bin_E, p->bin_M));
+            return lookup_device_ordered(p, n, p->bin_E, p->bin_M, p->perm, out, pass | MCX_LOOKUP_BINNED_INPUTS, st);
+        }
         TRY(sort_device(p, n, E, mat, p->perm, st));
         perm = p->perm;
     }
-    return lookup_device_ordered(p, n, E, mat, perm, out,
-                                 flags & (MCX_LOOKUP_FAST | MCX_LOOKUP_STAGED | MCX_LOOKUP_OUT32 | MCX_LOOKUP_LINEAR), st);
+    return lookup_device_ordered(p, n, E, mat, perm, out, pass, st);
 }
 
 // Eigenvalue scratch: per-history arrays for N histories and a staging and
@@ -1089,6 +1106,8 @@ void mcx_destroy(mcx_problem* p)
     dev_free(p->d_ctl);
     dev_free(p->ncoll_debug);
     dev_free(p->perm);
+    dev_free(p->bin_E);
+    dev_free(p->bin_M);
     dev_free(p->lbins);
     dev_free(p->bin2);
     dev_free(p->h_buf);
