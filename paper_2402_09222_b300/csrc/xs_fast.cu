@@ -413,14 +413,17 @@ __device__ __forceinline__ void load_record(const float4* __restrict__ rec, int3
 // The linear pieces of one species for a round starting at E_ref (FP32 pair
 // Erh + Erl) and spanning span16 / kLinSlopeBound: the term a at E_ref, the
 // slope b of interval kb and, with d = 1, the change of slope db at point
-// kb + 1.  False when a slope breaks the cancellation bound.
+// kb + 1 (whose energy pair comes back in g1h + g1l).  False when a slope
+// breaks the cancellation bound.
 template <int W, int NC>
 __device__ __forceinline__ bool species_linear(const float4* __restrict__ rec, int32_t kb, int32_t d, float N,
                                                float Erh, float Erl, float span16, float (&a)[NC],
-                                               float (&b)[NC], float (&db)[NC])
+                                               float (&b)[NC], float (&db)[NC], float& g1h, float& g1l)
 {
     float r0[4 * W], r1[4 * W];
     load_records<W>(rec, kb, r0, r1);
+    g1h = r1[0];
+    g1l = r1[1];
     float w0, w1;
     species_weights<W>(r0, r1, Erh, Erl, N, w0, w1);
     const float nr0 = N * interval_rinv<W>(r0, r1);
@@ -726,9 +729,13 @@ __global__ void __launch_bounds__(256, LIN ? MCX_LIN_MIN_BLOCKS : MCX_FAST2_MIN_
                 lin_round = i1 - i0 >= MCX_LIN_MIN_SPECIES;
                 if (lin_round) {
                     const double Eref = __longlong_as_double(eb_lo);
-                    x01 = make_float2((float)(E0 - Eref), (float)(E1 - Eref));
                     Erh = (float)Eref;
                     Erl = (float)(Eref - (double)Erh);
+                    // from the FP32 pairs: where a species is linear every energy of
+                    // the round lies within two of its grid intervals of E_min, so
+                    // the high parts' difference is exact (Sterbenz) and the sum
+                    // rounds once, as the FP64 difference rounded to FP32 would
+                    x01 = make_float2((Eh0 - Erh) + (El0 - Erl), (Eh1 - Erh) + (El1 - Erl));
                     span16 = kLinSlopeBound * (float)(__longlong_as_double(eb_hi) - Eref);
 #pragma unroll
                     for (int q = 0; q < 3 * NC; ++q) lin_acc[32 * q] = 0.f;
@@ -765,10 +772,15 @@ __global__ void __launch_bounds__(256, LIN ? MCX_LIN_MIN_BLOCKS : MCX_FAST2_MIN_
                         float a[NC], b[NC], db[NC];
                         float xbp = 0.f;
                         bool hinge = false;
-                        // one interval or one interior point in [E_min, E_max], inside the grid
-                        if (g0 + lane < i1 && kd <= 1 && ebits(__ldg(t.E + kb)) <= eb_lo &&
-                            eb_hi <= ebits(__ldg(t.E + kb + kd + 1))) {
-                            linq = species_linear<W, NC>(t.frec, kb, kd, Nq, Erh, Erl, span16, a, b, db);
+                        // one interval or one interior point in [E_min, E_max], inside the
+                        // grid: the searches are exact (kb and kb + kd the largest k with
+                        // g[k] <= E_min and <= E_max), so g[kb] <= E_min holds unless kb is
+                        // the grid's first point, and E_max < g[kb + kd + 1] unless kb + kd
+                        // is its last interval; only there are the points read
+                        if (g0 + lane < i1 && kd <= 1 && (kb > e.x || ebits(__ldg(t.E + kb)) <= eb_lo) &&
+                            (kb + kd < e.x + e.y - 2 || eb_hi <= ebits(__ldg(t.E + kb + kd + 1)))) {
+                            float g1h, g1l;   // point kb + 1 as its FP32 pair
+                            linq = species_linear<W, NC>(t.frec, kb, kd, Nq, Erh, Erl, span16, a, b, db, g1h, g1l);
                             if (linq) {
 #pragma unroll
                                 for (int c = 0; c < NC; ++c) {
@@ -779,7 +791,7 @@ __global__ void __launch_bounds__(256, LIN ? MCX_LIN_MIN_BLOCKS : MCX_FAST2_MIN_
                                     lin_acc[32 * (2 * NC + c)] = lin_acc[32 * (2 * NC + c)] + b[c];
                                 }
                                 hinge = kd == 1;
-                                if (hinge) xbp = (float)(__ldg(t.E + kb + 1) - __longlong_as_double(eb_lo));
+                                if (hinge) xbp = (g1h - Erh) + (g1l - Erl);   // as x01
                             }
                         }
                         any_lin = any_lin || __any_sync(FULLM, linq);
