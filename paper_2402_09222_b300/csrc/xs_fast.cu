@@ -757,13 +757,26 @@ __global__ void __launch_bounds__(256, LIN ? MCX_LIN_MIN_BLOCKS : MCX_FAST2_MIN_
                     far = b0 < e.x + e.y - 2 && ebits(__ldg(t.E + b0 + 1)) <= eb_hi;
                 }
                 if (__any_sync(FULLM, far)) {
-                    if (hb_hi < 0) hb_hi = t.H > 0 ? hash_bin(t, __longlong_as_double(eb_hi), eb_hi) : 0;
+                    // kd: points of the species in (E_min, E_max].  With one (the
+                    // common case) the largest k with g[k] <= E_max is kb + 1, known
+                    // from g[kb + 2] > E_max (or kb + 1 the last interval); the
+                    // search at E_max runs only for two or more
+                    bool more = false;
                     if (far) {
-                        int32_t b1, ln1;
-                        search_window(t, e, hb_hi, b1, ln1);
-                        for (int st = 0; st < t.search_steps; ++st)
-                            if (ln1 > 1) search_step(t.E, b1, ln1, eb_hi);
-                        kd = b1 - kb;
+                        if (kb + 1 == e.x + e.y - 2 || ebits(__ldg(t.E + kb + 2)) > eb_hi)
+                            kd = 1;
+                        else
+                            more = true;
+                    }
+                    if (__any_sync(FULLM, more)) {
+                        if (hb_hi < 0) hb_hi = t.H > 0 ? hash_bin(t, __longlong_as_double(eb_hi), eb_hi) : 0;
+                        if (more) {
+                            int32_t b1, ln1;
+                            search_window(t, e, hb_hi, b1, ln1);
+                            for (int st = 0; st < t.search_steps; ++st)
+                                if (ln1 > 1) search_step(t.E, b1, ln1, eb_hi);
+                            kd = b1 - kb;
+                        }
                     }
                 }
                 bool linq = false;   // this lane's species is summed in linear form
