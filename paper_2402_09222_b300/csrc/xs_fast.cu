@@ -375,6 +375,10 @@ __device__ __forceinline__ void species_term_half(const float (&r0)[4 * W], cons
 // per-lookup form's by rounding only, and they depend on which lookups share
 // a round (the binned order within a bucket is not fixed).
 constexpr float kLinSlopeBound = 16.f;
+// species of a material whose grid index a warp keeps from one round of its
+// chunk to the next (the round's E_min moves by about half a bucket, so the
+// index stays or moves by one: two or three grid reads instead of a search)
+constexpr int kLinKbCap = 384;
 // rounds of materials with fewer species take the per-lookup form for all
 // of them: the per-round reduction would cost more than it saves
 #ifndef MCX_LIN_MIN_SPECIES
@@ -648,6 +652,9 @@ __global__ void __launch_bounds__(256, LIN ? MCX_LIN_MIN_BLOCKS : MCX_FAST2_MIN_
     // a as a compensated pair (slots c and NC + c), the slopes b (2 NC + c)
     __shared__ float s_lin[256 / 32][LIN ? 3 * NC : 1][32];
     volatile float* lin_acc = &s_lin[threadIdx.x >> 5][0][lane];
+    // round-linear form: each species' grid index of the warp's previous
+    // round (the next round of a chunk starts its search there)
+    __shared__ int32_t s_kb[256 / 32][LIN ? kLinKbCap : 1];
 #if MCX_FAST_ROWSTAGE
     __shared__ OutT s_rows[256 / 32][64 * NC];   // a round's output rows, end to end
 #endif
@@ -658,8 +665,11 @@ __global__ void __launch_bounds__(256, LIN ? MCX_LIN_MIN_BLOCKS : MCX_FAST2_MIN_
         if (lane == 0) cbase = atomicAdd(work, (unsigned long long)kCh);
         cbase = __shfl_sync(FULLM, cbase, 0);
         if ((int64_t)cbase >= n) break;
+        int32_t prev_mw = -1;   // material of the warp's previous round-linear round in this chunk
 #pragma unroll 1
         for (int r = 0; r < kCh / 64; ++r) {
+            const int32_t pm = prev_mw;
+            prev_mw = -1;
             const int64_t j0 = (int64_t)cbase + r * 64 + lane, j1 = j0 + 32;
             bool in0 = j0 < n, in1 = j1 < n;
             int64_t l0 = 0, l1 = 0;
@@ -739,8 +749,10 @@ __global__ void __launch_bounds__(256, LIN ? MCX_LIN_MIN_BLOCKS : MCX_FAST2_MIN_
                     span16 = kLinSlopeBound * (float)(__longlong_as_double(eb_hi) - Eref);
 #pragma unroll
                     for (int q = 0; q < 3 * NC; ++q) lin_acc[32 * q] = 0.f;
+                    prev_mw = mw;
                 }
             }
+            const bool reuse = LIN && lin_round && pm == mw;
             for (int32_t g0 = i0; g0 < i1; g0 += 32) {
                 int32_t kb = 0, kd = 0;
                 float Nq = 0.f;
@@ -749,12 +761,54 @@ __global__ void __launch_bounds__(256, LIN ? MCX_LIN_MIN_BLOCKS : MCX_FAST2_MIN_
                 if (g0 + lane < i1) {
                     e = __ldg(t.ment + g0 + lane);
                     Nq = __int_as_float(e.w);
-                    int32_t b0, ln0;
-                    search_window(t, e, hb_lo, b0, ln0);
-                    for (int st = 0; st < t.search_steps; ++st)
-                        if (ln0 > 1) search_step(t.E, b0, ln0, eb_lo);
+                    const int32_t last = e.x + e.y - 2;
+                    int32_t b0 = 0, ln0 = 1;
+                    bool got = false;
+                    int64_t gnx = 0;   // g[b0 + 1] as its bit pattern, where known
+                    const int32_t si = g0 - i0 + lane;
+                    if constexpr (LIN) {
+                        // the largest k with g[k] <= E_min near the previous round's
+                        // index kp: kp itself, kp + 1 or kp - 1, each decided exactly
+                        if (reuse && si < kLinKbCap) {
+                            const int32_t kp = s_kb[threadIdx.x >> 5][si];
+                            if (kp >= e.x && kp <= last) {
+                                const int64_t gk = ebits(__ldg(t.E + kp)), gk1 = ebits(__ldg(t.E + kp + 1));
+                                if (gk <= eb_lo) {
+                                    if (kp == last || eb_lo < gk1) {
+                                        b0 = kp;
+                                        gnx = gk1;
+                                        got = true;
+                                    } else if (kp + 1 == last) {
+                                        b0 = last;   // g[last] <= E_min: the last interval
+                                        got = true;
+                                    } else {
+                                        const int64_t gk2 = ebits(__ldg(t.E + kp + 2));
+                                        if (eb_lo < gk2) {
+                                            b0 = kp + 1;
+                                            gnx = gk2;
+                                            got = true;
+                                        }
+                                    }
+                                } else if (kp > e.x) {
+                                    if (ebits(__ldg(t.E + kp - 1)) <= eb_lo) {
+                                        b0 = kp - 1;
+                                        gnx = gk;
+                                        got = true;
+                                    }
+                                }
+                            }
+                        }
+                    }
+                    if (!got) {
+                        search_window(t, e, hb_lo, b0, ln0);
+                        for (int st = 0; st < t.search_steps; ++st)
+                            if (ln0 > 1) search_step(t.E, b0, ln0, eb_lo);
+                        if (b0 < last) gnx = ebits(__ldg(t.E + b0 + 1));
+                    }
                     kb = b0;
-                    far = b0 < e.x + e.y - 2 && ebits(__ldg(t.E + b0 + 1)) <= eb_hi;
+                    far = b0 < last && gnx <= eb_hi;
+                    if constexpr (LIN)
+                        if (lin_round && si < kLinKbCap) s_kb[threadIdx.x >> 5][si] = b0;
                 }
                 if (__any_sync(FULLM, far)) {
                     // kd: points of the species in (E_min, E_max].  With one (the
