@@ -722,7 +722,7 @@ __global__ void __launch_bounds__(256, LIN ? MCX_LIN_MIN_BLOCKS : MCX_FAST2_MIN_
                 eb_lo = a < eb_lo ? a : eb_lo;
                 eb_hi = b > eb_hi ? b : eb_hi;
             }
-            const int32_t hb_lo = t.H > 0 ? hash_bin(t, __longlong_as_double(eb_lo), eb_lo) : 0;
+            int32_t hb_lo = -1;   // hash bin of E_min, found when a search first needs it
             int32_t hb_hi = -1;
             float2 hi[NC], lo[NC];   // (lookup j0, lookup j1) per channel
 #pragma unroll
@@ -800,6 +800,7 @@ __global__ void __launch_bounds__(256, LIN ? MCX_LIN_MIN_BLOCKS : MCX_FAST2_MIN_
                         }
                     }
                     if (!got) {
+                        if (hb_lo < 0) hb_lo = t.H > 0 ? hash_bin(t, __longlong_as_double(eb_lo), eb_lo) : 0;
                         search_window(t, e, hb_lo, b0, ln0);
                         for (int st = 0; st < t.search_steps; ++st)
                             if (ln0 > 1) search_step(t.E, b0, ln0, eb_lo);
